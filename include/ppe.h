@@ -1,0 +1,166 @@
+/*
+ * ppe.h -- C ABI of the GB300 pressure-Poisson (PPE) hot path.
+ *
+ * The library solves the pressure Poisson equation of a fractional-step
+ * immersed-boundary flow solver,
+ *
+ *     M dp = S                                   (Sec. 2.1 Eq. 6; Sec. 2.2 Eq. 10)
+ *
+ * on a 2-D tensor-product, cell-centred, non-uniform Cartesian grid with
+ * homogeneous Neumann walls.  M is the variable-spacing 5-point Laplacian
+ * D*G: the face gradient is (p[i+1]-p[i]) / ((dx[i]+dx[i+1])/2) and the
+ * divergence divides the net face flux by the cell width.  Internally the
+ * symmetric positive semidefinite form A = -V*M, b = -V*S (V = dx[i]*dy[j])
+ * is solved, with the constant null space projected out.
+ *
+ * Solvers (Sec. 2.2, Sec. 2.5):
+ *   PPE_MODE_PCG     Jacobi-preconditioned conjugate gradient.
+ *   PPE_MODE_HYBRID  HyDEA: up to num_cg CG-type iterations alternate with up
+ *                    to num_dlsm deep-learning line-search (DLSM) steps
+ *                    e = NN(r), alpha = r.e / e.(A e), x += alpha e
+ *                    (Eqs. 11-12), until the residual criterion holds.
+ *
+ * Conventions for every call:
+ *   - Fields are row-major [ny][nx] (x index contiguous), FP64 unless stated.
+ *   - "device" pointers are CUDA global-memory pointers on the current device;
+ *     "host" pointers are ordinary host memory.
+ *   - Streams are passed as `void*` holding a cudaStream_t (NULL = legacy
+ *     default stream).
+ *   - Every call returns a ppe_status and never aborts the process.  On
+ *     failure ppe_last_error() returns a message for the calling thread.
+ *   - Handles are not thread-safe; distinct handles may be used concurrently
+ *     on distinct streams.
+ */
+#ifndef PPE_GB300_H
+#define PPE_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PPE_API __attribute__((visibility("default")))
+#else
+#define PPE_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PPE_OK = 0,
+    PPE_ERR_ARG = 1,               /* invalid argument (null, size, layout)            */
+    PPE_ERR_CUDA = 2,              /* a CUDA runtime/driver call failed                */
+    PPE_ERR_NOMEM = 3,             /* device or host allocation failed                 */
+    PPE_ERR_INCOMPATIBLE_RHS = 4,  /* |sum V*S| > 1e-6 * sum |V*S|: no Neumann solution */
+    PPE_ERR_NOT_CONVERGED = 5,     /* iteration cap reached; x holds the best iterate   */
+    PPE_ERR_TIMEOUT = 6,           /* a bounded device-side wait expired               */
+    PPE_ERR_NAN = 7,               /* non-finite value met inside the solve            */
+    PPE_ERR_NO_NET = 8,            /* hybrid mode requested without a network          */
+    PPE_ERR_FORMAT = 9             /* malformed weights file                           */
+} ppe_status;
+
+typedef enum { PPE_BC_NEUMANN = 0 } ppe_bc;          /* dp: zero normal flux on all walls */
+typedef enum { PPE_MODE_PCG = 0, PPE_MODE_HYBRID = 1 } ppe_mode;
+typedef enum {
+    PPE_PREC_FP64 = 0,   /* every inner vector and operation in FP64                        */
+    PPE_PREC_MIXED = 1   /* FP32 inner iterations, FP64 true residual + iterative refinement */
+} ppe_precision;
+
+typedef struct ppe_grid ppe_grid;
+typedef struct ppe_net ppe_net;
+
+/* Per-solve report.  Iteration counts follow the paper's convention: a
+ * CG-type iteration or a DLSM step each count as one iteration. */
+typedef struct {
+    int32_t status;         /* ppe_status of the solve                                  */
+    int32_t iters_pcg;      /* CG-type iterations                                        */
+    int32_t iters_dlsm;     /* DLSM steps applied                                        */
+    int32_t dlsm_skipped;   /* DLSM directions rejected by the curvature guard           */
+    int32_t refinements;    /* FP64 true-residual evaluations                            */
+    int32_t fell_back;      /* 1 if hybrid mode exhausted its budget and finished as PCG */
+    int32_t net_calls;      /* network inferences run                                    */
+    int32_t launches;       /* solver-kernel launches                                    */
+    double rel_res_true;    /* ||P(b - A x)|| / ||P b|| in FP64 at exit                  */
+    double incompat;        /* |sum b| / sum |b| before projection                       */
+    double ms_total;        /* wall time of the call on its stream (ms)                  */
+    double ms_net;          /* part of ms_total spent in network inference (ms)          */
+} ppe_solve_info;
+
+/* Solver options; ppe_default_options() fills the defaults shown. */
+typedef struct {
+    int32_t max_iters;      /* cap on CG-type + DLSM iterations per solve (200000)            */
+    int32_t num_cg;         /* Num_CG-type: CG iterations per hybrid cycle (3; Sec. 2.2)      */
+    int32_t num_dlsm;       /* Num_DLSM: DLSM steps per hybrid cycle (2; Sec. 2.2)            */
+    int32_t hybrid_budget;  /* iterations after which hybrid mode continues as plain PCG      */
+    double inner_rtol;      /* MIXED: residual reduction of each FP32 inner solve (1e-5)      */
+    double dlsm_guard;      /* skip a DLSM step if e.Ae <= guard * e.e * max(diag A) (1e-10)   */
+    int32_t blocks_per_sm;  /* persistent-kernel CTAs per SM (0 = automatic)                  */
+    int32_t reserved[7];
+} ppe_solve_opts;
+
+PPE_API void ppe_default_options(ppe_solve_opts *opts);
+
+/*
+ * Create a grid handle.
+ *   nx, ny   cell counts (>= 1 each; nx*ny < 2^31)
+ *   dx, dy   host arrays of nx / ny positive, finite cell widths (copied)
+ *   bc       PPE_BC_NEUMANN
+ *   mask     nullable host array [ny][nx] of 0/1 body flags (copied).  The
+ *            operator never depends on it (Sec. 2.6: the PPE matrix of the
+ *            decoupled IB projection method is body-independent); it is kept
+ *            for the network's optional use and for reporting.
+ *   out      receives the handle.  The handle owns its device workspaces
+ *            (allocated here, on the current device) until ppe_destroy_grid.
+ */
+PPE_API ppe_status ppe_create_grid(int nx, int ny, const double *dx, const double *dy,
+                           ppe_bc bc, const uint8_t *mask, ppe_grid **out);
+PPE_API void ppe_destroy_grid(ppe_grid *grid);
+PPE_API ppe_status ppe_grid_shape(const ppe_grid *grid, int *nx, int *ny);
+PPE_API ppe_status ppe_set_options(ppe_grid *grid, const ppe_solve_opts *opts);
+
+/*
+ * y = A x with A = -V*M the volume-scaled operator (Sec. 2.1 Eq. 6, scaled
+ * by -V to make it symmetric), FP64.  x, y: device [ny][nx]; may not alias.
+ */
+PPE_API ppe_status ppe_apply(ppe_grid *grid, const double *x_dev, double *y_dev, void *stream);
+
+/*
+ * Solve M x = S (Eq. 10) to ||P(b - A x)|| <= tol_rel * ||P b||.
+ *   rhs_dev  device [ny][nx]: the source S (e.g. (D u* - bc2) / dt).  Must be
+ *            compatible: |sum V*S| <= 1e-6 * sum |V*S|; smaller defects are
+ *            projected out and reported in info->incompat.
+ *   x_dev    device [ny][nx]: in: initial guess (warm start), out: the
+ *            solution with zero volume-weighted mean.  On
+ *            PPE_ERR_NOT_CONVERGED it holds the best iterate.
+ *   tol_rel  relative residual target (> 0), e.g. 1e-8.
+ *   mode     PPE_MODE_PCG or PPE_MODE_HYBRID (needs net attached to grid).
+ *   precision PPE_PREC_FP64 or PPE_PREC_MIXED.
+ *   net      nullable for PCG; for HYBRID a network attached with net_attach.
+ *   stream   cudaStream_t as void*.  The call synchronises that stream
+ *            before it returns (the report is read back).
+ *   info     nullable; receives the report.
+ */
+PPE_API ppe_status ppe_solve(ppe_grid *grid, const double *rhs_dev, double *x_dev,
+                     double tol_rel, ppe_mode mode, ppe_precision precision,
+                     ppe_net *net, void *stream, ppe_solve_info *info);
+
+/*
+ * Solve n independent systems in one persistent launch (Sec. 2.2 applied to
+ * a batch).  grids[i], rhs_dev[i], x_dev[i] as in ppe_solve.  Systems retire
+ * independently when converged.  info: nullable array of n reports.
+ */
+PPE_API ppe_status ppe_solve_batch(int n, ppe_grid *const *grids, const double *const *rhs_dev,
+                           double *const *x_dev, double tol_rel, ppe_mode mode,
+                           ppe_precision precision, ppe_net *net, void *stream,
+                           ppe_solve_info *info);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+PPE_API const char *ppe_last_error(void);
+/* Library build identification, e.g. "ppe-gb300 sm_103a". */
+PPE_API const char *ppe_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PPE_GB300_H */

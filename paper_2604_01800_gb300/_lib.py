@@ -1,0 +1,96 @@
+"""ctypes binding of ``include/ppe.h`` (argument marshalling only).
+
+Every computation runs inside ``lib/libppe_gb300.so``.  Loading fails loudly
+when the library has not been built: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+_lib = None
+
+PPE_OK, PPE_ERR_ARG, PPE_ERR_CUDA, PPE_ERR_NOMEM, PPE_ERR_INCOMPATIBLE_RHS = 0, 1, 2, 3, 4
+PPE_ERR_NOT_CONVERGED, PPE_ERR_TIMEOUT, PPE_ERR_NAN, PPE_ERR_NO_NET, PPE_ERR_FORMAT = 5, 6, 7, 8, 9
+PPE_MODE_PCG, PPE_MODE_HYBRID = 0, 1
+PPE_PREC_FP64, PPE_PREC_MIXED = 0, 1
+PPE_BC_NEUMANN = 0
+
+STATUS_NAMES = {0: "PPE_OK", 1: "PPE_ERR_ARG", 2: "PPE_ERR_CUDA", 3: "PPE_ERR_NOMEM",
+                4: "PPE_ERR_INCOMPATIBLE_RHS", 5: "PPE_ERR_NOT_CONVERGED", 6: "PPE_ERR_TIMEOUT",
+                7: "PPE_ERR_NAN", 8: "PPE_ERR_NO_NET", 9: "PPE_ERR_FORMAT"}
+
+
+class ppe_solve_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iters_pcg", ctypes.c_int32), ("iters_dlsm", ctypes.c_int32),
+                ("dlsm_skipped", ctypes.c_int32), ("refinements", ctypes.c_int32), ("fell_back", ctypes.c_int32),
+                ("net_calls", ctypes.c_int32), ("launches", ctypes.c_int32), ("rel_res_true", ctypes.c_double),
+                ("incompat", ctypes.c_double), ("ms_total", ctypes.c_double), ("ms_net", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ppe_solve_opts(ctypes.Structure):
+    _fields_ = [("max_iters", ctypes.c_int32), ("num_cg", ctypes.c_int32), ("num_dlsm", ctypes.c_int32),
+                ("hybrid_budget", ctypes.c_int32), ("inner_rtol", ctypes.c_double), ("dlsm_guard", ctypes.c_double),
+                ("blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+
+
+class PPEError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+# (name, restype, argtypes) of every exported symbol
+_P = ctypes.c_void_p
+_SIGS = [
+    ("ppe_default_options", None, [ctypes.POINTER(ppe_solve_opts)]),
+    ("ppe_create_grid", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _P, ctypes.c_int, _P, ctypes.POINTER(_P)]),
+    ("ppe_destroy_grid", None, [_P]),
+    ("ppe_grid_shape", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    ("ppe_set_options", ctypes.c_int, [_P, ctypes.POINTER(ppe_solve_opts)]),
+    ("ppe_apply", ctypes.c_int, [_P, _P, _P, _P]),
+    ("ppe_solve", ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.c_int, ctypes.c_int, _P, _P,
+                                 ctypes.POINTER(ppe_solve_info)]),
+    ("ppe_solve_batch", ctypes.c_int, [ctypes.c_int, _P, _P, _P, ctypes.c_double, ctypes.c_int, ctypes.c_int, _P,
+                                       _P, ctypes.POINTER(ppe_solve_info)]),
+    ("ppe_last_error", ctypes.c_char_p, []),
+    ("ppe_version", ctypes.c_char_p, []),
+]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load the CUDA library (building it first if allowed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing:
+        path = _build.build()
+    if not os.path.exists(path):
+        raise ImportError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    L = ctypes.CDLL(path)
+    for name, res, args in _SIGS:
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def exported_names():
+    return [s[0] for s in _SIGS]
+
+
+def check(status: int, what: str = ""):
+    if status != PPE_OK:
+        msg = load().ppe_last_error().decode(errors="replace")
+        raise PPEError(status, f"{what}: {msg}" if what else msg)

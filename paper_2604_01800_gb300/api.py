@@ -1,0 +1,130 @@
+"""Python face of the C ABI: same names as ``include/ppe.h``.
+
+Each function only marshals arguments (torch CUDA tensors -> device
+pointers, the current torch stream -> ``cudaStream_t``) and calls into the
+CUDA library.  PyTorch supplies device memory and streams; nothing here
+computes.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import (PPE_MODE_HYBRID, PPE_MODE_PCG, PPE_PREC_FP64, PPE_PREC_MIXED, PPEError, check,
+                   ppe_solve_info, ppe_solve_opts)
+
+__all__ = ["Grid", "ppe_create_grid", "ppe_destroy_grid", "ppe_apply", "ppe_solve", "ppe_solve_batch",
+           "ppe_set_options", "ppe_default_options", "PPE_MODE_PCG", "PPE_MODE_HYBRID", "PPE_PREC_FP64",
+           "PPE_PREC_MIXED", "PPEError"]
+
+
+def _stream(stream):
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _dptr(t: torch.Tensor, dtype=torch.float64, numel=None):
+    if not (t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise ValueError(f"expected a contiguous CUDA {dtype} tensor")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"expected {numel} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Grid:
+    """Owning wrapper of a ``ppe_grid*``."""
+
+    def __init__(self, handle, nx, ny):
+        self.handle = handle
+        self.nx, self.ny = nx, ny
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def close(self):
+        if self.handle:
+            _lib.load().ppe_destroy_grid(self.handle)
+            self.handle = None
+
+    @property
+    def shape(self):
+        return (self.ny, self.nx)
+
+
+def ppe_create_grid(dx, dy, mask=None, bc: int = 0) -> Grid:
+    L = _lib.load()
+    dx = np.ascontiguousarray(dx, dtype=np.float64)
+    dy = np.ascontiguousarray(dy, dtype=np.float64)
+    mptr = None
+    if mask is not None:
+        mask = np.ascontiguousarray(mask, dtype=np.uint8)
+        mptr = mask.ctypes.data_as(ctypes.c_void_p)
+    h = ctypes.c_void_p()
+    st = L.ppe_create_grid(dx.size, dy.size, dx.ctypes.data_as(ctypes.c_void_p), dy.ctypes.data_as(ctypes.c_void_p),
+                           bc, mptr, ctypes.byref(h))
+    check(st, "ppe_create_grid")
+    return Grid(h, dx.size, dy.size)
+
+
+def ppe_destroy_grid(grid: Grid):
+    grid.close()
+
+
+def ppe_default_options() -> ppe_solve_opts:
+    o = ppe_solve_opts()
+    _lib.load().ppe_default_options(ctypes.byref(o))
+    return o
+
+
+def ppe_set_options(grid: Grid, opts: ppe_solve_opts | None = None, **kw):
+    o = opts if opts is not None else ppe_default_options()
+    for k, v in kw.items():
+        setattr(o, k, v)
+    check(_lib.load().ppe_set_options(grid.handle, ctypes.byref(o)), "ppe_set_options")
+    return o
+
+
+def ppe_apply(grid: Grid, x: torch.Tensor, y: torch.Tensor, stream=None):
+    n = grid.nx * grid.ny
+    check(_lib.load().ppe_apply(grid.handle, _dptr(x, numel=n), _dptr(y, numel=n), _stream(stream)), "ppe_apply")
+    return y
+
+
+def ppe_solve(grid: Grid, rhs: torch.Tensor, x: torch.Tensor, tol_rel: float = 1e-8, mode: int = PPE_MODE_PCG,
+              precision: int = PPE_PREC_MIXED, net=None, stream=None, raise_on_error: bool = True) -> dict:
+    """Solve M x = rhs in place of ``x``; returns the info report as a dict."""
+    n = grid.nx * grid.ny
+    info = ppe_solve_info()
+    nh = None if net is None else net.handle
+    st = _lib.load().ppe_solve(grid.handle, _dptr(rhs, numel=n), _dptr(x, numel=n), float(tol_rel), int(mode),
+                               int(precision), nh, _stream(stream), ctypes.byref(info))
+    d = info.as_dict()
+    d["status"] = st
+    if raise_on_error and st != _lib.PPE_OK:
+        check(st, "ppe_solve")
+    return d
+
+
+def ppe_solve_batch(grids, rhs, xs, tol_rel: float = 1e-8, mode: int = PPE_MODE_PCG,
+                    precision: int = PPE_PREC_MIXED, net=None, stream=None, raise_on_error: bool = True):
+    n = len(grids)
+    G = (ctypes.c_void_p * n)(*[g.handle for g in grids])
+    R = (ctypes.c_void_p * n)(*[_dptr(r, numel=g.nx * g.ny).value for r, g in zip(rhs, grids)])
+    X = (ctypes.c_void_p * n)(*[_dptr(x, numel=g.nx * g.ny).value for x, g in zip(xs, grids)])
+    infos = (ppe_solve_info * n)()
+    nh = None if net is None else net.handle
+    st = _lib.load().ppe_solve_batch(n, ctypes.cast(G, ctypes.c_void_p), ctypes.cast(R, ctypes.c_void_p),
+                                     ctypes.cast(X, ctypes.c_void_p), float(tol_rel), int(mode), int(precision), nh,
+                                     _stream(stream), infos)
+    if raise_on_error and st != _lib.PPE_OK:
+        check(st, "ppe_solve_batch")
+    return [i.as_dict() for i in infos], st

@@ -1,0 +1,399 @@
+// Host side of the C ABI: grid handles, the FP64 operator, and the solve
+// drivers that launch the persistent solver kernel.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "net_iface.h"
+
+namespace ppe {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string &msg) { g_err = msg; }
+void clear_error() { g_err.clear(); }
+
+ppe_status cuda_status(cudaError_t e, const char *what)
+{
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    if (e == cudaErrorMemoryAllocation) return PPE_ERR_NOMEM;
+    return PPE_ERR_CUDA;
+}
+
+static ppe_status arg_error(const std::string &msg)
+{
+    set_error(msg);
+    return PPE_ERR_ARG;
+}
+
+// y = A x in FP64 (plain one-thread-per-cell kernel; reference operator).
+__global__ void apply_kernel(int nx, int ny, const double *__restrict__ dx, const double *__restrict__ dy,
+                             const double *__restrict__ fx, const double *__restrict__ fy,
+                             const double *__restrict__ x, double *__restrict__ y)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= nx || j >= ny) return;
+    size_t k = (size_t)j * nx + i;
+    double c = x[k];
+    double xe = i + 1 < nx ? x[k + 1] : 0.0, xw = i > 0 ? x[k - 1] : 0.0;
+    double xn = j + 1 < ny ? x[k + nx] : 0.0, xs = j > 0 ? x[k - nx] : 0.0;
+    double ax = fx[i + 1] * (c - xe) + fx[i] * (c - xw);
+    double ay = fy[j + 1] * (c - xn) + fy[j] * (c - xs);
+    y[k] = dy[j] * ax + dx[i] * ay;
+}
+
+static int g_spin_limit_ms = 2000;
+
+}  // namespace ppe
+
+using namespace ppe;
+
+extern "C" {
+
+const char *ppe_last_error(void) { return g_err.c_str(); }
+const char *ppe_version(void) { return "ppe-gb300 0.1 sm_103a"; }
+
+void ppe_default_options(ppe_solve_opts *o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->max_iters = 200000;
+    o->num_cg = 3;
+    o->num_dlsm = 2;
+    o->hybrid_budget = 20000;
+    o->inner_rtol = 1e-5;
+    o->dlsm_guard = 1e-10;
+    o->blocks_per_sm = 1;
+}
+
+void ppe_destroy_grid(ppe_grid *g)
+{
+    if (!g) return;
+    net_release_grid(g);
+    cudaFree(g->dx); cudaFree(g->dy); cudaFree(g->fx); cudaFree(g->fy);
+    cudaFree(g->dx32); cudaFree(g->dy32); cudaFree(g->fx32); cudaFree(g->fy32);
+    cudaFree(g->vec); cudaFree(g->e);
+    cudaFree(g->sys_dev); cudaFree(g->st_dev); cudaFree(g->tile_sys_dev); cudaFree(g->partials_dev);
+    cudaFree(g->ctl_dev);
+    if (g->st_host) cudaFreeHost(g->st_host);
+    delete g;
+}
+
+ppe_status ppe_create_grid(int nx, int ny, const double *dx, const double *dy, ppe_bc bc,
+                           const uint8_t *mask, ppe_grid **out)
+{
+    clear_error();
+    if (!out) return arg_error("ppe_create_grid: out is NULL");
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || (long long)nx * ny >= (1LL << 31)) return arg_error("ppe_create_grid: bad nx/ny");
+    if (!dx || !dy) return arg_error("ppe_create_grid: dx/dy NULL");
+    if (bc != PPE_BC_NEUMANN) return arg_error("ppe_create_grid: only PPE_BC_NEUMANN is supported");
+    for (int i = 0; i < nx; ++i)
+        if (!(dx[i] > 0.0) || !std::isfinite(dx[i])) return arg_error("ppe_create_grid: dx must be positive and finite");
+    for (int j = 0; j < ny; ++j)
+        if (!(dy[j] > 0.0) || !std::isfinite(dy[j])) return arg_error("ppe_create_grid: dy must be positive and finite");
+
+    ppe_grid *g = new ppe_grid();
+    g->nx = nx; g->ny = ny;
+    g->pitch = round_up(nx, PITCH_ALIGN);
+    g->tiles_x = (nx + TILE_X - 1) / TILE_X;
+    g->tiles_y = (ny + TILE_Y - 1) / TILE_Y;
+    g->hdx.assign(dx, dx + nx);
+    g->hdy.assign(dy, dy + ny);
+    if (mask) g->hmask.assign(mask, mask + (size_t)nx * ny);
+    ppe_default_options(&g->opts);
+    cudaGetDevice(&g->device);
+    g->lx = 0; for (double v : g->hdx) g->lx += v;
+    g->ly = 0; for (double v : g->hdy) g->ly += v;
+
+    // face coefficients 2 / (w_left + w_right), zero at the walls
+    std::vector<double> fx(nx + 1, 0.0), fy(ny + 1, 0.0);
+    for (int i = 1; i < nx; ++i) fx[i] = 2.0 / (dx[i - 1] + dx[i]);
+    for (int j = 1; j < ny; ++j) fy[j] = 2.0 / (dy[j - 1] + dy[j]);
+    double dmax = 0.0;
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i)
+            dmax = std::max(dmax, dy[j] * (fx[i] + fx[i + 1]) + dx[i] * (fy[j] + fy[j + 1]));
+    g->diag_max = dmax;
+    std::vector<float> dx32(dx, dx + nx), dy32(dy, dy + ny), fx32(fx.begin(), fx.end()), fy32(fy.begin(), fy.end());
+
+    auto fail = [&](ppe_status s) { ppe_destroy_grid(g); return s; };
+#define G_ALLOC(ptr, bytes)                                                              \
+    do {                                                                                 \
+        cudaError_t _e = cudaMalloc((void **)&(ptr), (bytes));                           \
+        if (_e != cudaSuccess) return fail(cuda_status(_e, "cudaMalloc(grid)"));         \
+    } while (0)
+#define G_COPY(dst, src, bytes)                                                          \
+    do {                                                                                 \
+        cudaError_t _e = cudaMemcpy((dst), (src), (bytes), cudaMemcpyHostToDevice);      \
+        if (_e != cudaSuccess) return fail(cuda_status(_e, "cudaMemcpy(grid)"));         \
+    } while (0)
+    G_ALLOC(g->dx, nx * 8); G_COPY(g->dx, dx, nx * 8);
+    G_ALLOC(g->dy, ny * 8); G_COPY(g->dy, dy, ny * 8);
+    G_ALLOC(g->fx, (nx + 1) * 8); G_COPY(g->fx, fx.data(), (nx + 1) * 8);
+    G_ALLOC(g->fy, (ny + 1) * 8); G_COPY(g->fy, fy.data(), (ny + 1) * 8);
+    G_ALLOC(g->dx32, nx * 4); G_COPY(g->dx32, dx32.data(), nx * 4);
+    G_ALLOC(g->dy32, ny * 4); G_COPY(g->dy32, dy32.data(), ny * 4);
+    G_ALLOC(g->fx32, (nx + 1) * 4); G_COPY(g->fx32, fx32.data(), (nx + 1) * 4);
+    G_ALLOC(g->fy32, (ny + 1) * 4); G_COPY(g->fy32, fy32.data(), (ny + 1) * 4);
+    size_t vbytes = (size_t)g->pitch * ny * 8;
+    G_ALLOC(g->vec, vbytes * 6);
+    char *base = (char *)g->vec;
+    g->r[0] = base; g->r[1] = base + vbytes; g->s[0] = base + 2 * vbytes; g->s[1] = base + 3 * vbytes;
+    g->p = base + 4 * vbytes; g->d = base + 5 * vbytes;
+    G_ALLOC(g->e, (size_t)g->pitch * ny * 4);
+    {
+        cudaError_t _e = cudaMemset(g->e, 0, (size_t)g->pitch * ny * 4);
+        if (_e != cudaSuccess) return fail(cuda_status(_e, "cudaMemset(e)"));
+    }
+    int ntiles = g->tiles_x * g->tiles_y;
+    G_ALLOC(g->sys_dev, sizeof(SysDesc));
+    G_ALLOC(g->st_dev, sizeof(SysState));
+    G_ALLOC(g->tile_sys_dev, ntiles * sizeof(int32_t));
+    {
+        cudaError_t _e = cudaMemset(g->tile_sys_dev, 0, ntiles * sizeof(int32_t));
+        if (_e != cudaSuccess) return fail(cuda_status(_e, "cudaMemset(tile_sys)"));
+    }
+    G_ALLOC(g->partials_dev, (size_t)ntiles * NPART * sizeof(double));
+    G_ALLOC(g->ctl_dev, sizeof(Control));
+    {
+        cudaError_t _e = cudaMallocHost((void **)&g->st_host, sizeof(SysState) + sizeof(Control));
+        if (_e != cudaSuccess) return fail(cuda_status(_e, "cudaMallocHost"));
+    }
+#undef G_ALLOC
+#undef G_COPY
+    *out = g;
+    return PPE_OK;
+}
+
+ppe_status ppe_grid_shape(const ppe_grid *g, int *nx, int *ny)
+{
+    if (!g) return arg_error("ppe_grid_shape: NULL grid");
+    if (nx) *nx = g->nx;
+    if (ny) *ny = g->ny;
+    return PPE_OK;
+}
+
+ppe_status ppe_set_options(ppe_grid *g, const ppe_solve_opts *o)
+{
+    clear_error();
+    if (!g || !o) return arg_error("ppe_set_options: NULL argument");
+    if (o->max_iters < 1 || o->num_cg < 1 || o->num_dlsm < 1 || o->hybrid_budget < 0 ||
+        !(o->inner_rtol > 0.0 && o->inner_rtol < 1.0) || !(o->dlsm_guard >= 0.0) || o->blocks_per_sm < 0)
+        return arg_error("ppe_set_options: option out of range");
+    g->opts = *o;
+    return PPE_OK;
+}
+
+ppe_status ppe_apply(ppe_grid *g, const double *x, double *y, void *stream)
+{
+    clear_error();
+    if (!g || !x || !y) return arg_error("ppe_apply: NULL argument");
+    if (x == y) return arg_error("ppe_apply: x and y may not alias");
+    dim3 blk(32, 8), grd((g->nx + 31) / 32, (g->ny + 7) / 8);
+    apply_kernel<<<grd, blk, 0, (cudaStream_t)stream>>>(g->nx, g->ny, g->dx, g->dy, g->fx, g->fy, x, y);
+    PPE_CUDA_TRY(cudaGetLastError());
+    return PPE_OK;
+}
+
+}  // extern "C"
+
+namespace ppe {
+
+static SysDesc make_desc(const ppe_grid *g, const double *rhs, double *x, double tol, ppe_mode mode,
+                         ppe_precision prec, int tile0)
+{
+    SysDesc sd;
+    std::memset(&sd, 0, sizeof(sd));
+    sd.nx = g->nx; sd.ny = g->ny; sd.pitch = g->pitch; sd.tiles_x = g->tiles_x;
+    sd.tile0 = tile0; sd.ntiles = g->tiles_x * g->tiles_y;
+    sd.mode = mode; sd.precision = prec;
+    sd.max_iters = g->opts.max_iters; sd.num_cg = g->opts.num_cg; sd.num_dlsm = g->opts.num_dlsm;
+    sd.hybrid_budget = g->opts.hybrid_budget;
+    sd.tol = tol;
+    sd.inner_rtol = prec == PPE_PREC_MIXED ? g->opts.inner_rtol : 1e-300;
+    sd.dlsm_guard = g->opts.dlsm_guard;
+    sd.diag_max = g->diag_max;
+    sd.n_cells = (double)g->nx * (double)g->ny;
+    sd.dx = g->dx; sd.dy = g->dy; sd.fx = g->fx; sd.fy = g->fy;
+    sd.dx32 = g->dx32; sd.dy32 = g->dy32; sd.fx32 = g->fx32; sd.fy32 = g->fy32;
+    sd.f = rhs; sd.x = x;
+    sd.r[0] = g->r[0]; sd.r[1] = g->r[1]; sd.s[0] = g->s[0]; sd.s[1] = g->s[1];
+    sd.p = g->p; sd.d = g->d; sd.e = g->e;
+    return sd;
+}
+
+static void fill_info(ppe_solve_info *info, const SysState &s, double ms, double ms_net, int launches)
+{
+    if (!info) return;
+    std::memset(info, 0, sizeof(*info));
+    info->status = s.status;
+    info->iters_pcg = s.it_pcg;
+    info->iters_dlsm = s.it_dlsm;
+    info->dlsm_skipped = s.dlsm_skipped;
+    info->refinements = s.refinements;
+    info->fell_back = s.fell_back;
+    info->net_calls = s.net_calls;
+    info->launches = launches;
+    info->rel_res_true = s.relres;
+    info->incompat = s.incompat;
+    info->ms_total = ms;
+    info->ms_net = ms_net;
+}
+
+// Drive one persistent launch sequence over n systems described on the device.
+static ppe_status drive(int n, ppe_grid *const *grids, SysDesc *sys_dev, SysState *st_dev, int32_t *tile_sys_dev,
+                        double *partials_dev, Control *ctl_dev, SysState *st_host, int ntiles, bool fp64,
+                        ppe_mode mode, ppe_net *net, cudaStream_t stream, ppe_solve_info *info)
+{
+    int bps = grids[0]->opts.blocks_per_sm;
+    int maxb = solver_max_blocks(fp64, bps);
+    if (maxb < 1) return cuda_status(cudaErrorInvalidConfiguration, "solver occupancy");
+    int blocks = std::min(maxb, ntiles);
+    SolverArgs a;
+    a.sys = sys_dev; a.st = st_dev; a.tile_sys = tile_sys_dev; a.partials = partials_dev; a.ctl = ctl_dev;
+    a.nsys = n; a.ntiles = ntiles;
+    a.spin_limit_ns = (int64_t)g_spin_limit_ms * 1000000LL;
+
+    cudaEvent_t ev0, ev1;
+    PPE_CUDA_TRY(cudaEventCreate(&ev0));
+    PPE_CUDA_TRY(cudaEventCreate(&ev1));
+    PPE_CUDA_TRY(cudaEventRecord(ev0, stream));
+    PPE_CUDA_TRY(cudaMemsetAsync(st_dev, 0, sizeof(SysState) * n, stream));
+    int launches = 0;
+    double ms_net = 0.0;
+    ppe_status status = PPE_OK;
+    Control ctl_host;
+    std::vector<SysState> st(n);
+    for (int round = 0;; ++round) {
+        PPE_CUDA_TRY(cudaMemsetAsync(ctl_dev, 0, sizeof(Control), stream));
+        status = launch_solver_resume(a, fp64, blocks, stream, round > 0 ? 1 : 0);
+        if (status != PPE_OK) break;
+        ++launches;
+        PPE_CUDA_TRY(cudaMemcpyAsync(st.data(), st_dev, sizeof(SysState) * n, cudaMemcpyDeviceToHost, stream));
+        PPE_CUDA_TRY(cudaMemcpyAsync(&ctl_host, ctl_dev, sizeof(Control), cudaMemcpyDeviceToHost, stream));
+        PPE_CUDA_TRY(cudaStreamSynchronize(stream));
+        if (ctl_host.err) {
+            set_error("solver kernel: bounded grid-barrier wait expired");
+            status = (ppe_status)ctl_host.err;
+            break;
+        }
+        bool any_net = false;
+        for (int s = 0; s < n; ++s) any_net |= st[s].phase == PH_NET;
+        if (!any_net) break;
+        if (!net) { set_error("hybrid solve without a network"); status = PPE_ERR_NO_NET; break; }
+        float t = 0.f;
+        for (int s = 0; s < n; ++s) {
+            if (st[s].phase != PH_NET) continue;
+            ppe_status ns = net_direction(net, grids[s], sys_dev + s, st_dev + s, fp64, stream, &t);
+            if (ns != PPE_OK) { status = ns; break; }
+            ms_net += t;
+        }
+        if (status != PPE_OK) break;
+        if (launches > 1000000) { status = PPE_ERR_NOT_CONVERGED; break; }
+    }
+    float ms = 0.f;
+    cudaEventRecord(ev1, stream);
+    cudaEventSynchronize(ev1);
+    cudaEventElapsedTime(&ms, ev0, ev1);
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    if (status != PPE_OK) return status;
+    ppe_status worst = PPE_OK;
+    for (int s = 0; s < n; ++s) {
+        fill_info(info ? info + s : nullptr, st[s], ms, ms_net, launches);
+        if (st[s].status != PPE_OK && worst == PPE_OK) worst = (ppe_status)st[s].status;
+    }
+    if (worst != PPE_OK) {
+        char buf[160];
+        std::snprintf(buf, sizeof buf, "solve finished with status %d (relres %.3e)", (int)worst, st[0].relres);
+        set_error(buf);
+    }
+    (void)mode;
+    return worst;
+}
+
+static ppe_status check_solve_args(ppe_grid *g, const double *rhs, double *x, double tol, ppe_mode mode,
+                                   ppe_precision prec, ppe_net *net)
+{
+    if (!g || !rhs || !x) return arg_error("ppe_solve: NULL grid, rhs or x");
+    if (!(tol > 0.0) || !std::isfinite(tol)) return arg_error("ppe_solve: tol_rel must be positive");
+    if (mode != PPE_MODE_PCG && mode != PPE_MODE_HYBRID) return arg_error("ppe_solve: bad mode");
+    if (prec != PPE_PREC_FP64 && prec != PPE_PREC_MIXED) return arg_error("ppe_solve: bad precision");
+    if (mode == PPE_MODE_HYBRID && !net) {
+        set_error("ppe_solve: hybrid mode needs a network");
+        return PPE_ERR_NO_NET;
+    }
+    if (mode == PPE_MODE_HYBRID) return net_check_grid(net, g);
+    return PPE_OK;
+}
+
+}  // namespace ppe
+
+extern "C" {
+
+ppe_status ppe_solve(ppe_grid *g, const double *rhs, double *x, double tol, ppe_mode mode, ppe_precision prec,
+                     ppe_net *net, void *stream, ppe_solve_info *info)
+{
+    clear_error();
+    PPE_TRY(check_solve_args(g, rhs, x, tol, mode, prec, net));
+    cudaStream_t st = (cudaStream_t)stream;
+    SysDesc sd = make_desc(g, rhs, x, tol, mode, prec, 0);
+    PPE_CUDA_TRY(cudaMemcpyAsync(g->sys_dev, &sd, sizeof(sd), cudaMemcpyHostToDevice, st));
+    ppe_grid *gs[1] = {g};
+    return drive(1, gs, g->sys_dev, g->st_dev, g->tile_sys_dev, g->partials_dev, g->ctl_dev, g->st_host,
+                 sd.ntiles, prec == PPE_PREC_FP64, mode, net, st, info);
+}
+
+ppe_status ppe_solve_batch(int n, ppe_grid *const *grids, const double *const *rhs, double *const *x, double tol,
+                           ppe_mode mode, ppe_precision prec, ppe_net *net, void *stream, ppe_solve_info *info)
+{
+    clear_error();
+    if (n < 1 || !grids || !rhs || !x) return arg_error("ppe_solve_batch: bad arguments");
+    for (int i = 0; i < n; ++i) PPE_TRY(check_solve_args(grids[i], rhs[i], x[i], tol, mode, prec, net));
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < i; ++k)
+            if (grids[i] == grids[k]) return arg_error("ppe_solve_batch: a grid handle may appear only once");
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<SysDesc> sds(n);
+    std::vector<int32_t> tile_sys;
+    int ntiles = 0;
+    for (int i = 0; i < n; ++i) {
+        sds[i] = make_desc(grids[i], rhs[i], x[i], tol, mode, prec, ntiles);
+        for (int t = 0; t < sds[i].ntiles; ++t) tile_sys.push_back(i);
+        ntiles += sds[i].ntiles;
+    }
+    SysDesc *sys_dev = nullptr;
+    SysState *st_dev = nullptr;
+    int32_t *ts_dev = nullptr;
+    double *part_dev = nullptr;
+    Control *ctl_dev = nullptr;
+    ppe_status status = PPE_OK;
+    auto cleanup = [&]() {
+        cudaFree(sys_dev); cudaFree(st_dev); cudaFree(ts_dev); cudaFree(part_dev); cudaFree(ctl_dev);
+    };
+    if (cudaMalloc(&sys_dev, sizeof(SysDesc) * n) != cudaSuccess || cudaMalloc(&st_dev, sizeof(SysState) * n) != cudaSuccess ||
+        cudaMalloc(&ts_dev, sizeof(int32_t) * ntiles) != cudaSuccess ||
+        cudaMalloc(&part_dev, sizeof(double) * NPART * (size_t)ntiles) != cudaSuccess ||
+        cudaMalloc(&ctl_dev, sizeof(Control)) != cudaSuccess) {
+        cleanup();
+        set_error("ppe_solve_batch: device allocation failed");
+        return PPE_ERR_NOMEM;
+    }
+    cudaMemcpyAsync(sys_dev, sds.data(), sizeof(SysDesc) * n, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(ts_dev, tile_sys.data(), sizeof(int32_t) * ntiles, cudaMemcpyHostToDevice, st);
+    status = drive(n, grids, sys_dev, st_dev, ts_dev, part_dev, ctl_dev, nullptr, ntiles, prec == PPE_PREC_FP64,
+                   mode, net, st, info);
+    cudaStreamSynchronize(st);
+    cleanup();
+    return status;
+}
+
+}  // extern "C"

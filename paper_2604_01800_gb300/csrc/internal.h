@@ -1,0 +1,132 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/ppe.h"
+
+namespace ppe {
+
+// ---------------------------------------------------------------------------
+// error reporting
+// ---------------------------------------------------------------------------
+void set_error(const std::string &msg);
+void clear_error();
+ppe_status cuda_status(cudaError_t e, const char *what);
+
+#define PPE_CUDA_TRY(call)                                                     \
+    do {                                                                       \
+        cudaError_t _e = (call);                                               \
+        if (_e != cudaSuccess) return ::ppe::cuda_status(_e, #call);           \
+    } while (0)
+
+#define PPE_TRY(call)                                                          \
+    do {                                                                       \
+        ppe_status _s = (call);                                                \
+        if (_s != PPE_OK) return _s;                                           \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// tiling of the persistent solver kernel
+// ---------------------------------------------------------------------------
+constexpr int TILE_X = 128;                 // cells per tile row (4 per lane)
+constexpr int TILE_Y = 8;                   // rows per tile (one warp each)
+constexpr int SOLVER_THREADS = 32 * TILE_Y;
+constexpr int NPART = 6;                    // FP64 partial sums per tile
+constexpr int PITCH_ALIGN = 32;             // inner-vector row pitch (elements)
+
+inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
+
+// Phases of the per-system state machine run by the solver kernel.
+enum Phase : int32_t {
+    PH_INIT = 0,      // b statistics: sum, sum of squares, sum of magnitudes
+    PH_RES = 1,       // FP64 true residual of x + d (iterative refinement)
+    PH_RESTART = 2,   // start of a CG-type phase: u = D^-1 r, w = A u, dots
+    PH_ITER = 3,      // one single-reduction PCG iteration
+    PH_NET = 4,       // waiting for a network direction (kernel yields)
+    PH_DLSM_DOT = 5,  // DLSM: r.e, e.Ae, e.e
+    PH_DLSM_UPD = 6,  // DLSM: d += alpha e, r -= alpha A e
+    PH_FINAL1 = 7,    // fold d into x; volume-weighted sum of x
+    PH_FINAL2 = 8,    // remove the volume-weighted mean
+    PH_DONE = 9
+};
+
+// Static description of one system (device memory, written by the host).
+struct SysDesc {
+    int32_t nx, ny, pitch, tiles_x, tile0, ntiles;
+    int32_t mode, precision;              // ppe_mode, ppe_precision
+    int32_t max_iters, num_cg, num_dlsm, hybrid_budget;
+    double tol, inner_rtol, dlsm_guard, diag_max;
+    double n_cells;                       // nx*ny as double
+    const double *dx, *dy;                // widths [nx], [ny]
+    const double *fx, *fy;                // face coefficients [nx+1], [ny+1]; 0 at walls
+    const float *dx32, *dy32, *fx32, *fy32;
+    const double *f;                      // source S [ny][nx] (caller)
+    double *x;                            // solution [ny][nx] (caller)
+    void *r[2], *s[2], *p, *d;            // inner vectors [ny][pitch], FP32 or FP64
+    float *e;                             // DLSM direction [ny][pitch]
+};
+
+// Mutable per-system state (device memory, owned by the solver kernel).
+struct SysState {
+    int32_t phase, status;
+    int32_t it_pcg, it_dlsm, dlsm_skipped, refinements, it_total;
+    int32_t cg_count, dlsm_count, fell_back, net_calls;
+    int32_t has_d, fold_d, reset_d, first, cur, zero_x, pad_;
+    double alpha, beta, gamma, mu, mu_b, bnorm, tau, rnorm, relres, incompat;
+    double alpha_d, xmean, rho;
+};
+
+// Global control block of one persistent launch.
+struct Control {
+    uint32_t bar_count;
+    uint32_t bar_gen;
+    int32_t err;           // PPE_ERR_TIMEOUT etc.
+    int32_t exit_kernel;   // 1: every live system waits for the network or is done
+    int32_t any_net;       // 1: at least one system waits for the network
+    int32_t pad[3];
+};
+
+struct SolverArgs {
+    SysDesc *sys;
+    SysState *st;
+    const int32_t *tile_sys;   // tile -> system
+    double *partials;          // [ntiles][NPART]
+    Control *ctl;
+    int32_t nsys, ntiles;
+    int64_t spin_limit_ns;
+};
+
+ppe_status launch_solver_resume(const SolverArgs &a, bool fp64, int grid_blocks, cudaStream_t stream,
+                                int resume);
+int solver_max_blocks(bool fp64, int blocks_per_sm_req);
+
+}  // namespace ppe
+
+// The grid handle (opaque in the public header).
+struct ppe_grid {
+    int nx = 0, ny = 0, pitch = 0, tiles_x = 0, tiles_y = 0;
+    double lx = 0, ly = 0, diag_max = 0;
+    std::vector<double> hdx, hdy;
+    std::vector<uint8_t> hmask;
+    ppe_solve_opts opts{};
+    int device = 0;
+    // device copies
+    double *dx = nullptr, *dy = nullptr, *fx = nullptr, *fy = nullptr;
+    float *dx32 = nullptr, *dy32 = nullptr, *fx32 = nullptr, *fy32 = nullptr;
+    void *vec = nullptr;                 // 6 inner vectors, 8 bytes per element
+    float *e = nullptr;                  // DLSM direction
+    void *r[2] = {nullptr, nullptr}, *s[2] = {nullptr, nullptr}, *p = nullptr, *d = nullptr;
+    // single-system launch resources
+    ppe::SysDesc *sys_dev = nullptr;
+    ppe::SysState *st_dev = nullptr;
+    int32_t *tile_sys_dev = nullptr;
+    double *partials_dev = nullptr;
+    ppe::Control *ctl_dev = nullptr;
+    ppe::SysState *st_host = nullptr;    // pinned
+    void *net_cache = nullptr;           // per-network data for this grid (owned by the net)
+    const void *net_owner = nullptr;
+};

@@ -1,0 +1,179 @@
+"""Parity of the CUDA solver path (through the C ABI) with the FP64 oracle.
+
+Bars (from the hot-path target): true relative residual <= 1e-8 evaluated by
+the oracle on the GPU's answer, and solution relative L2 error <= 1e-6
+against the oracle's reference solution (solved to 1e-11), for both plain
+FP64 PCG and mixed FP32/FP64 PCG.  The FP64 operator is compared entry by
+entry: both sides evaluate the same five products per row, so only the
+summation order differs (bound 1e-13 relative to the row scale).
+"""
+import functools
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from paper_2604_01800_gb300 import inputs as I  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+SOL_TOL = 1e-6
+RES_TOL = 1e-8
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_01800_gb300 import api as A
+    return A
+
+
+def _dev(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+@functools.lru_cache(maxsize=None)
+def _ref(key):
+    w = _WORK[key]()
+    x, info, st = oracle.solve(w.dx, w.dy, w.f, tol_rel=1e-11)
+    return w, x
+
+
+def _ragged(nx, ny, seed):
+    g = I.rng(seed)
+    dx, dy = I.random_spacing(nx, g), I.random_spacing(ny, g)
+    return I.Workload(f"ragged{nx}x{ny}", dx, dy, I.gaussian_rhs(dx, dy, g, 6))
+
+
+_WORK = {
+    "c1": lambda: I.config1(0),
+    "c1b": lambda: I.config1(1),
+    "c2": lambda: I.config2(0),
+    "c3": lambda: I.config3(0),
+    "r37x300": lambda: _ragged(37, 300, 5),
+    "r129x131": lambda: _ragged(129, 131, 6),
+    "r5x7": lambda: _ragged(5, 7, 7),
+    "r1x50": lambda: _ragged(1, 50, 8),
+    "r260x9": lambda: _ragged(260, 9, 9),
+}
+
+
+@pytest.mark.parametrize("nx,ny,seed", [(5, 7, 1), (33, 17, 2), (130, 9, 3), (200, 150, 4), (1, 1, 5), (1, 40, 6)])
+def test_apply_matches_oracle(api, nx, ny, seed):
+    g0 = I.rng(seed)
+    dx, dy = g0.uniform(0.1, 2.0, nx), g0.uniform(0.1, 2.0, ny)
+    x = g0.standard_normal((ny, nx))
+    grid = api.ppe_create_grid(dx, dy)
+    y = torch.zeros(ny, nx, dtype=torch.float64, device="cuda")
+    api.ppe_apply(grid, _dev(x), y)
+    torch.cuda.synchronize()
+    yo = oracle.apply(dx, dy, x)
+    A = oracle.CSR(dx, dy)
+    rowscale = np.abs(A.scipy()).dot(np.abs(x).reshape(-1)).reshape(ny, nx) + 1e-300
+    assert np.max(np.abs(y.cpu().numpy() - yo) / rowscale) <= 1e-13
+
+
+def _check(api, key, prec, x0=None, **opts):
+    w, xo = _ref(key)
+    grid = api.ppe_create_grid(w.dx, w.dy, w.mask)
+    if opts:
+        api.ppe_set_options(grid, **opts)
+    rhs = _dev(w.f)
+    x = _dev(x0) if x0 is not None else torch.zeros_like(rhs)
+    info = api.ppe_solve(grid, rhs, x, RES_TOL, api.PPE_MODE_PCG, prec)
+    xg = x.cpu().numpy()
+    rr = oracle.true_relres(w.dx, w.dy, w.f, xg)
+    err = np.linalg.norm(xg - xo) / np.linalg.norm(xo)
+    V = np.outer(w.dy, w.dx)
+    assert info["status"] == 0, info
+    assert rr <= RES_TOL * 1.05, (rr, info)
+    assert err <= SOL_TOL, (err, info)
+    assert abs((V * xg).sum()) <= 1e-12 * np.abs(V * xg).sum() + 1e-300
+    # the device's own FP64 residual report agrees with the oracle's evaluation
+    assert abs(info["rel_res_true"] - rr) <= 1e-3 * rr + 1e-15
+    return info
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("key", ["c1", "r37x300", "r129x131", "r5x7", "r1x50", "r260x9"])
+def test_solve_small(api, key, prec):
+    _check(api, key, api.PPE_PREC_FP64 if prec == "fp64" else api.PPE_PREC_MIXED)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_solve_config2_512(api, prec):
+    info = _check(api, "c2", api.PPE_PREC_FP64 if prec == "fp64" else api.PPE_PREC_MIXED)
+    if prec == "mixed":
+        assert info["refinements"] >= 2
+
+
+def test_solve_config3_cylinder_mask(api):
+    _check(api, "c3", api.PPE_PREC_MIXED)
+
+
+def test_warm_start(api):
+    w, xo = _ref("c1b")
+    x0 = xo + 0.01 * I.rng(3).standard_normal(xo.shape)
+    info = _check(api, "c1b", api.PPE_PREC_MIXED, x0=x0)
+    cold = _check(api, "c1b", api.PPE_PREC_MIXED)
+    assert info["iters_pcg"] < cold["iters_pcg"]
+
+
+def test_incompatible_rhs(api):
+    w = I.config1(0)
+    grid = api.ppe_create_grid(w.dx, w.dy)
+    x = torch.zeros(w.ny, w.nx, dtype=torch.float64, device="cuda")
+    info = api.ppe_solve(grid, _dev(w.f + 1.0), x, 1e-8, api.PPE_MODE_PCG, api.PPE_PREC_MIXED,
+                         raise_on_error=False)
+    assert info["status"] == api._lib.PPE_ERR_INCOMPATIBLE_RHS
+    assert info["incompat"] > 1e-6
+
+
+def test_zero_rhs(api):
+    w = I.config1(0)
+    grid = api.ppe_create_grid(w.dx, w.dy)
+    x = torch.ones(w.ny, w.nx, dtype=torch.float64, device="cuda")
+    info = api.ppe_solve(grid, torch.zeros_like(x), x, 1e-8, api.PPE_MODE_PCG, api.PPE_PREC_MIXED)
+    assert info["status"] == 0 and float(x.abs().max()) == 0.0
+
+
+def test_iteration_cap_reports_not_converged(api):
+    w = I.config1(0)
+    grid = api.ppe_create_grid(w.dx, w.dy)
+    api.ppe_set_options(grid, max_iters=5)
+    x = torch.zeros(w.ny, w.nx, dtype=torch.float64, device="cuda")
+    info = api.ppe_solve(grid, _dev(w.f), x, 1e-8, api.PPE_MODE_PCG, api.PPE_PREC_MIXED, raise_on_error=False)
+    assert info["status"] == api._lib.PPE_ERR_NOT_CONVERGED
+    assert np.all(np.isfinite(x.cpu().numpy()))
+
+
+def test_batch_matches_single(api):
+    keys = ["c1", "r37x300", "r129x131", "r5x7", "r260x9"]
+    grids, rhs, xs, refs = [], [], [], []
+    for k in keys:
+        w, xo = _ref(k)
+        grids.append(api.ppe_create_grid(w.dx, w.dy))
+        rhs.append(_dev(w.f))
+        xs.append(torch.zeros_like(rhs[-1]))
+        refs.append((w, xo))
+    infos, st = api.ppe_solve_batch(grids, rhs, xs, RES_TOL, api.PPE_MODE_PCG, api.PPE_PREC_MIXED)
+    assert st == 0
+    for (w, xo), x, info in zip(refs, xs, infos):
+        xg = x.cpu().numpy()
+        assert info["status"] == 0
+        assert oracle.true_relres(w.dx, w.dy, w.f, xg) <= RES_TOL * 1.05
+        assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= SOL_TOL
+
+
+def test_repeatable_bitwise(api):
+    w, _ = _ref("r129x131")
+    grid = api.ppe_create_grid(w.dx, w.dy)
+    outs = []
+    for _ in range(2):
+        x = torch.zeros(w.ny, w.nx, dtype=torch.float64, device="cuda")
+        api.ppe_solve(grid, _dev(w.f), x, RES_TOL, api.PPE_MODE_PCG, api.PPE_PREC_MIXED)
+        outs.append(x.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
