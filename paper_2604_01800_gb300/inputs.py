@@ -263,8 +263,8 @@ def random_spacing(n: int, g: np.random.Generator, length: float = 1.0,
     """One axis of a random stretched grid: tanh with ``beta ~ U(0.5, 2.5)``
     or a refined box (centre ``U(0.2, 0.8)``, width ``U(0.1, 0.4)``, growth
     ``U(1.02, 1.08)``), each with probability 1/2."""
-    if g.uniform() < 0.5 and box_bias is None:
-        return tanh_spacing(n, g.uniform(0.5, 2.5), length)
+    if (g.uniform() < 0.5 and box_bias is None) or n < 8:
+        return tanh_spacing(n, g.uniform(0.5, 2.5), length) if n > 1 else np.full(1, length)
     c = g.uniform(0.2, 0.8) if box_bias is None else box_bias
     w = g.uniform(0.1, 0.4)
     a, b = max(0.02, c - w / 2), min(0.98, c + w / 2)
