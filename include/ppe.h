@@ -160,6 +160,54 @@ PPE_API const char *ppe_last_error(void);
 /* Library build identification, e.g. "ppe-gb300 sm_103a". */
 PPE_API const char *ppe_version(void);
 
+/* ------------------------------------------------------------------------
+ * Grid-spacing-aware DeepONet (Sec. 2.4): U-Net branch of Mesh-Convs whose
+ * inputs are scaled by eta = exp(-Phi(Delta)^2) (Eqs. 16-17), Delta being the
+ * level-K map of distances to the four neighbours; coordinate trunk; output
+ * sum_c branch_c * trunk_c + bias.
+ * ------------------------------------------------------------------------ */
+#define PPE_NET_MAX_LEVELS 6
+typedef struct {
+    int32_t levels;                          /* U-Net levels (2..6)                         */
+    int32_t widths[PPE_NET_MAX_LEVELS];      /* channels per level (multiples of 16)        */
+    int32_t c_last;                          /* branch / trunk feature count                 */
+    int32_t trunk_hidden[2];                 /* trunk MLP hidden widths (2 -> h0 -> h1 -> c_last) */
+    int32_t phi_hidden;                      /* hidden width of each Mesh-Conv weight network */
+    int32_t mesh_conv;                       /* 1: Mesh-Conv; 0: standard convolution (eta = 1) */
+    int32_t reserved[4];
+} ppe_net_config;
+
+/* Defaults: 4 levels, widths 32/64/128/256, c_last 100, trunk 100/200,
+ * phi_hidden 16, mesh_conv 1. */
+PPE_API void net_default_config(ppe_net_config *cfg);
+/* Create a network with seeded initial parameters (host-side generator). */
+PPE_API ppe_status net_create(const ppe_net_config *cfg, uint64_t seed, ppe_net **out);
+PPE_API void net_destroy(ppe_net *net);
+/* Number of FP32 parameters; the flat order is: for every Mesh-Conv in
+ * execution order (enc0a, enc0b, ..., up{L-2}, dec{L-2}a, dec{L-2}b, ..., dec0b)
+ * w[Cout][Cin][3][3], b[Cout], phi1.w[H][4], phi1.b[H], phi2.w[H], phi2.b[1];
+ * then head.w[c_last][w0], head.b[c_last]; trunk0.w[h0][2], trunk0.b[h0],
+ * trunk1.w[h1][h0], trunk1.b[h1], trunk2.w[c_last][h1], trunk2.b[c_last];
+ * out.b[1]. */
+PPE_API ppe_status net_param_count(const ppe_net *net, int64_t *count);
+PPE_API ppe_status net_get_config(const ppe_net *net, ppe_net_config *cfg);
+/* Copy parameters in/out (host FP32 arrays of net_param_count entries). */
+PPE_API ppe_status net_set_params(ppe_net *net, const float *params, int64_t count);
+PPE_API ppe_status net_get_params(const ppe_net *net, float *params, int64_t count);
+/* Binary weights file: magic "PPENET01", config, step, parameters, Adam
+ * moments, CRC32.  net_load returns PPE_ERR_FORMAT for a malformed file. */
+PPE_API ppe_status net_save(const ppe_net *net, const char *path);
+PPE_API ppe_status net_load(const char *path, ppe_net **out);
+/* Build the per-grid caches (distance maps, eta per layer, trunk features)
+ * for this grid; required before net_infer / hybrid solves on it. */
+PPE_API ppe_status net_attach(ppe_net *net, ppe_grid *grid);
+/* e = NN(r) on the grid (Sec. 2.2 Eq. 11's e^NN).  r_dev, e_dev: device FP32
+ * [ny][nx].  The network sees r exactly as given (the solver feeds r/||r||). */
+PPE_API ppe_status net_infer(ppe_net *net, ppe_grid *grid, const float *r_dev, float *e_dev, void *stream);
+/* Same for a batch of `batch` inputs stored back to back ([batch][ny][nx]). */
+PPE_API ppe_status net_infer_batch(ppe_net *net, ppe_grid *grid, int batch, const float *r_dev, float *e_dev,
+                                   void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -93,7 +93,8 @@ def _check(api, key, prec, x0=None, **opts):
     assert err <= SOL_TOL, (err, info)
     assert abs((V * xg).sum()) <= 1e-12 * np.abs(V * xg).sum() + 1e-300
     # the device's own FP64 residual report agrees with the oracle's evaluation
-    assert abs(info["rel_res_true"] - rr) <= 1e-3 * rr + 1e-15
+    # (below ~1e-11 both evaluations are dominated by FP64 rounding of b - A x)
+    assert abs(info["rel_res_true"] - rr) <= 1e-3 * rr + 1e-11
     return info
 
 
