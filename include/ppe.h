@@ -208,6 +208,14 @@ PPE_API ppe_status net_infer(ppe_net *net, ppe_grid *grid, const float *r_dev, f
 PPE_API ppe_status net_infer_batch(ppe_net *net, ppe_grid *grid, int batch, const float *r_dev, float *e_dev,
                                    void *stream);
 
+/* Test hook: one 3x3 convolution (zero padding 1, no activation) of a BF16
+ * NHWC input in_bf16 [B][H][W][cin] with packed BF16 weights
+ * w_bf16 [cout][9][cin] (tap = 3*ky + kx) and FP32 bias [cout] (nullable);
+ * FP32 output out [B][H][W][cout].  impl 0: tensor-core (tcgen05) kernel,
+ * 1: CUDA-core kernel.  All pointers are device pointers. */
+PPE_API ppe_status ppe_debug_conv3x3(const void *in_bf16, const void *w_bf16, const float *bias, int B, int H, int W,
+                                     int cin, int cout, float *out, int impl, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -39,6 +39,12 @@ class ppe_solve_opts(ctypes.Structure):
                 ("blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
 
 
+class ppe_net_config(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int32), ("widths", ctypes.c_int32 * 6), ("c_last", ctypes.c_int32),
+                ("trunk_hidden", ctypes.c_int32 * 2), ("phi_hidden", ctypes.c_int32), ("mesh_conv", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
+
+
 class PPEError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -58,6 +64,20 @@ _SIGS = [
                                  ctypes.POINTER(ppe_solve_info)]),
     ("ppe_solve_batch", ctypes.c_int, [ctypes.c_int, _P, _P, _P, ctypes.c_double, ctypes.c_int, ctypes.c_int, _P,
                                        _P, ctypes.POINTER(ppe_solve_info)]),
+    ("net_default_config", None, [ctypes.POINTER(ppe_net_config)]),
+    ("net_create", ctypes.c_int, [ctypes.POINTER(ppe_net_config), ctypes.c_uint64, ctypes.POINTER(_P)]),
+    ("net_destroy", None, [_P]),
+    ("net_param_count", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
+    ("net_get_config", ctypes.c_int, [_P, ctypes.POINTER(ppe_net_config)]),
+    ("net_set_params", ctypes.c_int, [_P, _P, ctypes.c_int64]),
+    ("net_get_params", ctypes.c_int, [_P, _P, ctypes.c_int64]),
+    ("net_save", ctypes.c_int, [_P, ctypes.c_char_p]),
+    ("net_load", ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(_P)]),
+    ("net_attach", ctypes.c_int, [_P, _P]),
+    ("net_infer", ctypes.c_int, [_P, _P, _P, _P, _P]),
+    ("net_infer_batch", ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P, _P]),
+    ("ppe_debug_conv3x3", ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int, _P, ctypes.c_int, _P]),
     ("ppe_last_error", ctypes.c_char_p, []),
     ("ppe_version", ctypes.c_char_p, []),
 ]

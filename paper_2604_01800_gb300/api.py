@@ -16,7 +16,7 @@ from . import _lib
 from ._lib import (PPE_MODE_HYBRID, PPE_MODE_PCG, PPE_PREC_FP64, PPE_PREC_MIXED, PPEError, check,
                    ppe_solve_info, ppe_solve_opts)
 
-__all__ = ["Grid", "ppe_create_grid", "ppe_destroy_grid", "ppe_apply", "ppe_solve", "ppe_solve_batch",
+__all__ = ["Net", "net_create", "net_load", "net_default_config", "Grid", "ppe_create_grid", "ppe_destroy_grid", "ppe_apply", "ppe_solve", "ppe_solve_batch",
            "ppe_set_options", "ppe_default_options", "PPE_MODE_PCG", "PPE_MODE_HYBRID", "PPE_PREC_FP64",
            "PPE_PREC_MIXED", "PPEError"]
 
@@ -128,3 +128,92 @@ def ppe_solve_batch(grids, rhs, xs, tol_rel: float = 1e-8, mode: int = PPE_MODE_
     if raise_on_error and st != _lib.PPE_OK:
         check(st, "ppe_solve_batch")
     return [i.as_dict() for i in infos], st
+
+
+# ---------------------------------------------------------------------------
+# network
+# ---------------------------------------------------------------------------
+
+def net_default_config(**kw) -> _lib.ppe_net_config:
+    c = _lib.ppe_net_config()
+    _lib.load().net_default_config(ctypes.byref(c))
+    for k, v in kw.items():
+        if k == "widths":
+            c.levels = len(v)
+            for i in range(6):
+                c.widths[i] = v[i] if i < len(v) else 0
+        elif k == "trunk_hidden":
+            c.trunk_hidden[0], c.trunk_hidden[1] = v
+        else:
+            setattr(c, k, v)
+    return c
+
+
+class Net:
+    """Owning wrapper of a ``ppe_net*``."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def close(self):
+        if self.handle:
+            _lib.load().net_destroy(self.handle)
+            self.handle = None
+
+    @property
+    def param_count(self) -> int:
+        n = ctypes.c_int64()
+        check(_lib.load().net_param_count(self.handle, ctypes.byref(n)), "net_param_count")
+        return n.value
+
+    def config(self) -> _lib.ppe_net_config:
+        c = _lib.ppe_net_config()
+        check(_lib.load().net_get_config(self.handle, ctypes.byref(c)), "net_get_config")
+        return c
+
+    def set_params(self, flat: np.ndarray):
+        flat = np.ascontiguousarray(flat, dtype=np.float32)
+        check(_lib.load().net_set_params(self.handle, flat.ctypes.data_as(ctypes.c_void_p), flat.size), "net_set_params")
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.param_count, dtype=np.float32)
+        check(_lib.load().net_get_params(self.handle, out.ctypes.data_as(ctypes.c_void_p), out.size), "net_get_params")
+        return out
+
+    def save(self, path: str):
+        check(_lib.load().net_save(self.handle, path.encode()), "net_save")
+
+    def attach(self, grid: Grid):
+        check(_lib.load().net_attach(self.handle, grid.handle), "net_attach")
+
+    def infer(self, grid: Grid, r: torch.Tensor, e: torch.Tensor, stream=None):
+        n = grid.nx * grid.ny
+        b = r.numel() // n
+        check(_lib.load().net_infer_batch(self.handle, grid.handle, b, _dptr(r, torch.float32, b * n),
+                                          _dptr(e, torch.float32, b * n), _stream(stream)), "net_infer")
+        return e
+
+
+def net_create(cfg=None, seed: int = 0) -> Net:
+    cfg = cfg if cfg is not None else net_default_config()
+    h = ctypes.c_void_p()
+    check(_lib.load().net_create(ctypes.byref(cfg), seed, ctypes.byref(h)), "net_create")
+    return Net(h)
+
+
+def net_load(path: str) -> Net:
+    h = ctypes.c_void_p()
+    check(_lib.load().net_load(path.encode(), ctypes.byref(h)), "net_load")
+    return Net(h)
+
+
+def flatten_params(P: dict, cfg) -> np.ndarray:
+    """Flatten a name -> array dict in the library's parameter order."""
+    from .inputs import net_param_shapes
+    return np.concatenate([np.asarray(P[k], np.float32).reshape(-1) for k in net_param_shapes(cfg)])
