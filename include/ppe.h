@@ -93,9 +93,10 @@ typedef struct {
     int32_t num_cg;         /* Num_CG-type: CG iterations per hybrid cycle (3; Sec. 2.2)      */
     int32_t num_dlsm;       /* Num_DLSM: DLSM steps per hybrid cycle (2; Sec. 2.2)            */
     int32_t hybrid_budget;  /* iterations after which hybrid mode continues as plain PCG      */
-    double inner_rtol;      /* MIXED: residual reduction of each FP32 inner solve (1e-5)      */
+    double inner_rtol;      /* MIXED: FP32 residual drop that triggers an FP64 residual
+                               replacement (0.1)                                              */
     double dlsm_guard;      /* skip a DLSM step if e.Ae <= guard * e.e * max(diag A) (1e-10)   */
-    int32_t blocks_per_sm;  /* persistent-kernel CTAs per SM (0 = automatic)                  */
+    int32_t blocks_per_sm;  /* persistent-kernel CTAs per SM (2; 0 = as many as fit)          */
     int32_t reserved[7];
 } ppe_solve_opts;
 

@@ -68,9 +68,9 @@ void ppe_default_options(ppe_solve_opts *o)
     o->num_cg = 3;
     o->num_dlsm = 2;
     o->hybrid_budget = 20000;
-    o->inner_rtol = 1e-5;
+    o->inner_rtol = 0.1;
     o->dlsm_guard = 1e-10;
-    o->blocks_per_sm = 1;
+    o->blocks_per_sm = 2;
 }
 
 void ppe_destroy_grid(ppe_grid *g)
@@ -80,9 +80,8 @@ void ppe_destroy_grid(ppe_grid *g)
     cudaFree(g->dx); cudaFree(g->dy); cudaFree(g->fx); cudaFree(g->fy);
     cudaFree(g->dx32); cudaFree(g->dy32); cudaFree(g->fx32); cudaFree(g->fy32);
     cudaFree(g->vec); cudaFree(g->e);
-    cudaFree(g->sys_dev); cudaFree(g->st_dev); cudaFree(g->tile_sys_dev); cudaFree(g->partials_dev);
+    cudaFree(g->sys_dev); cudaFree(g->st_dev); cudaFree(g->ranges_dev); cudaFree(g->partials_dev);
     cudaFree(g->ctl_dev);
-    if (g->st_host) cudaFreeHost(g->st_host);
     delete g;
 }
 
@@ -156,17 +155,10 @@ ppe_status ppe_create_grid(int nx, int ny, const double *dx, const double *dy, p
     int ntiles = g->tiles_x * g->tiles_y;
     G_ALLOC(g->sys_dev, sizeof(SysDesc));
     G_ALLOC(g->st_dev, sizeof(SysState));
-    G_ALLOC(g->tile_sys_dev, ntiles * sizeof(int32_t));
-    {
-        cudaError_t _e = cudaMemset(g->tile_sys_dev, 0, ntiles * sizeof(int32_t));
-        if (_e != cudaSuccess) return fail(cuda_status(_e, "cudaMemset(tile_sys)"));
-    }
-    G_ALLOC(g->partials_dev, (size_t)ntiles * NPART * sizeof(double));
+    g->ranges_blocks = ntiles;
+    G_ALLOC(g->ranges_dev, (size_t)ntiles * sizeof(BlockRange));
+    G_ALLOC(g->partials_dev, (size_t)(ntiles + 1) * NPART * sizeof(double));
     G_ALLOC(g->ctl_dev, sizeof(Control));
-    {
-        cudaError_t _e = cudaMallocHost((void **)&g->st_host, sizeof(SysState) + sizeof(Control));
-        if (_e != cudaSuccess) return fail(cuda_status(_e, "cudaMallocHost"));
-    }
 #undef G_ALLOC
 #undef G_COPY
     *out = g;
@@ -218,7 +210,7 @@ static SysDesc make_desc(const ppe_grid *g, const double *rhs, double *x, double
     sd.max_iters = g->opts.max_iters; sd.num_cg = g->opts.num_cg; sd.num_dlsm = g->opts.num_dlsm;
     sd.hybrid_budget = g->opts.hybrid_budget;
     sd.tol = tol;
-    sd.inner_rtol = prec == PPE_PREC_MIXED ? g->opts.inner_rtol : 1e-300;
+    sd.ru_delta = prec == PPE_PREC_MIXED ? g->opts.inner_rtol : 0.0;
     sd.dlsm_guard = g->opts.dlsm_guard;
     sd.diag_max = g->diag_max;
     sd.n_cells = (double)g->nx * (double)g->ny;
@@ -248,18 +240,58 @@ static void fill_info(ppe_solve_info *info, const SysState &s, double ms, double
     info->ms_net = ms_net;
 }
 
-// Drive one persistent launch sequence over n systems described on the device.
-static ppe_status drive(int n, ppe_grid *const *grids, SysDesc *sys_dev, SysState *st_dev, int32_t *tile_sys_dev,
-                        double *partials_dev, Control *ctl_dev, SysState *st_host, int ntiles, bool fp64,
-                        ppe_mode mode, ppe_net *net, cudaStream_t stream, ppe_solve_info *info)
+// Split the tiles of n systems into contiguous block ranges (at most SMAX
+// systems per block, at most max_blocks blocks) and assign the partial-sum
+// slots of every system.
+static bool plan_blocks(std::vector<SysDesc> &sds, int max_blocks, std::vector<BlockRange> &ranges, int &nslots)
 {
-    int bps = grids[0]->opts.blocks_per_sm;
-    int maxb = solver_max_blocks(fp64, bps);
-    if (maxb < 1) return cuda_status(cudaErrorInvalidConfiguration, "solver occupancy");
-    int blocks = std::min(maxb, ntiles);
+    int total = 0;
+    for (auto &d : sds) total += d.ntiles;
+    std::vector<int> sys_of(total);
+    for (size_t s = 0; s < sds.size(); ++s)
+        for (int t = 0; t < sds[s].ntiles; ++t) sys_of[sds[s].tile0 + t] = (int)s;
+    for (int chunk = std::max(1, (total + max_blocks - 1) / max_blocks);; ++chunk) {
+        ranges.clear();
+        int t = 0;
+        while (t < total) {
+            BlockRange r;
+            r.t0 = t;
+            r.s0 = sys_of[t];
+            int e = t;
+            while (e < total && e - t < chunk && sys_of[e] - r.s0 < SMAX) ++e;
+            r.t1 = e;
+            r.s1 = sys_of[e - 1];
+            ranges.push_back(r);
+            t = e;
+        }
+        if ((int)ranges.size() <= max_blocks) break;
+        if (chunk > total) return false;
+    }
+    nslots = 0;
+    for (size_t s = 0; s < sds.size(); ++s) {
+        int first = -1, last = -1;
+        for (size_t b = 0; b < ranges.size(); ++b)
+            if ((int)s >= ranges[b].s0 && (int)s <= ranges[b].s1) {
+                if (first < 0) first = (int)b;
+                last = (int)b;
+            }
+        sds[s].blk0 = first;
+        sds[s].nparts = last - first + 1;
+        sds[s].part0 = nslots;
+        nslots += sds[s].nparts;
+    }
+    return true;
+}
+
+// Drive the persistent launches of n systems until every one is done; run
+// the network between launches for the systems that wait for a direction.
+static ppe_status drive(int n, ppe_grid *const *grids, SysDesc *sys_dev, SysState *st_dev, BlockRange *ranges_dev,
+                        int blocks, double *partials_dev, Control *ctl_dev, bool fp64, ppe_net *net,
+                        cudaStream_t stream, ppe_solve_info *info)
+{
     SolverArgs a;
-    a.sys = sys_dev; a.st = st_dev; a.tile_sys = tile_sys_dev; a.partials = partials_dev; a.ctl = ctl_dev;
-    a.nsys = n; a.ntiles = ntiles;
+    a.sys = sys_dev; a.st = st_dev; a.ranges = ranges_dev; a.partials = partials_dev; a.ctl = ctl_dev;
+    a.nsys = n; a.ntiles = 0;
     a.spin_limit_ns = (int64_t)g_spin_limit_ms * 1000000LL;
 
     cudaEvent_t ev0, ev1;
@@ -272,8 +304,11 @@ static ppe_status drive(int n, ppe_grid *const *grids, SysDesc *sys_dev, SysStat
     ppe_status status = PPE_OK;
     Control ctl_host;
     std::vector<SysState> st(n);
+    int active = n;
     for (int round = 0;; ++round) {
-        PPE_CUDA_TRY(cudaMemsetAsync(ctl_dev, 0, sizeof(Control), stream));
+        std::memset(&ctl_host, 0, sizeof ctl_host);
+        ctl_host.active0 = active;
+        PPE_CUDA_TRY(cudaMemcpyAsync(ctl_dev, &ctl_host, sizeof(Control), cudaMemcpyHostToDevice, stream));
         status = launch_solver_resume(a, fp64, blocks, stream, round > 0 ? 1 : 0);
         if (status != PPE_OK) break;
         ++launches;
@@ -285,9 +320,9 @@ static ppe_status drive(int n, ppe_grid *const *grids, SysDesc *sys_dev, SysStat
             status = (ppe_status)ctl_host.err;
             break;
         }
-        bool any_net = false;
-        for (int s = 0; s < n; ++s) any_net |= st[s].phase == PH_NET;
-        if (!any_net) break;
+        active = 0;
+        for (int s = 0; s < n; ++s) active += st[s].phase == PH_NET;
+        if (!active) break;
         if (!net) { set_error("hybrid solve without a network"); status = PPE_ERR_NO_NET; break; }
         float t = 0.f;
         for (int s = 0; s < n; ++s) {
@@ -297,7 +332,7 @@ static ppe_status drive(int n, ppe_grid *const *grids, SysDesc *sys_dev, SysStat
             ms_net += t;
         }
         if (status != PPE_OK) break;
-        if (launches > 1000000) { status = PPE_ERR_NOT_CONVERGED; break; }
+        if (launches > 10000000) { status = PPE_ERR_NOT_CONVERGED; break; }
     }
     float ms = 0.f;
     cudaEventRecord(ev1, stream);
@@ -316,7 +351,6 @@ static ppe_status drive(int n, ppe_grid *const *grids, SysDesc *sys_dev, SysStat
         std::snprintf(buf, sizeof buf, "solve finished with status %d (relres %.3e)", (int)worst, st[0].relres);
         set_error(buf);
     }
-    (void)mode;
     return worst;
 }
 
@@ -345,11 +379,19 @@ ppe_status ppe_solve(ppe_grid *g, const double *rhs, double *x, double tol, ppe_
     clear_error();
     PPE_TRY(check_solve_args(g, rhs, x, tol, mode, prec, net));
     cudaStream_t st = (cudaStream_t)stream;
-    SysDesc sd = make_desc(g, rhs, x, tol, mode, prec, 0);
-    PPE_CUDA_TRY(cudaMemcpyAsync(g->sys_dev, &sd, sizeof(sd), cudaMemcpyHostToDevice, st));
+    std::vector<SysDesc> sds(1, make_desc(g, rhs, x, tol, mode, prec, 0));
+    bool fp64 = prec == PPE_PREC_FP64;
+    int maxb = std::min(solver_max_blocks(fp64, g->opts.blocks_per_sm), g->ranges_blocks);
+    if (maxb < 1) return cuda_status(cudaErrorInvalidConfiguration, "solver occupancy");
+    std::vector<BlockRange> ranges;
+    int nslots = 0;
+    if (!plan_blocks(sds, maxb, ranges, nslots)) return arg_error("ppe_solve: cannot partition tiles");
+    PPE_CUDA_TRY(cudaMemcpyAsync(g->sys_dev, sds.data(), sizeof(SysDesc), cudaMemcpyHostToDevice, st));
+    PPE_CUDA_TRY(cudaMemcpyAsync(g->ranges_dev, ranges.data(), sizeof(BlockRange) * ranges.size(),
+                                 cudaMemcpyHostToDevice, st));
     ppe_grid *gs[1] = {g};
-    return drive(1, gs, g->sys_dev, g->st_dev, g->tile_sys_dev, g->partials_dev, g->ctl_dev, g->st_host,
-                 sd.ntiles, prec == PPE_PREC_FP64, mode, net, st, info);
+    return drive(1, gs, g->sys_dev, g->st_dev, g->ranges_dev, (int)ranges.size(), g->partials_dev, g->ctl_dev, fp64,
+                 net, st, info);
 }
 
 ppe_status ppe_solve_batch(int n, ppe_grid *const *grids, const double *const *rhs, double *const *x, double tol,
@@ -363,34 +405,36 @@ ppe_status ppe_solve_batch(int n, ppe_grid *const *grids, const double *const *r
             if (grids[i] == grids[k]) return arg_error("ppe_solve_batch: a grid handle may appear only once");
     cudaStream_t st = (cudaStream_t)stream;
     std::vector<SysDesc> sds(n);
-    std::vector<int32_t> tile_sys;
     int ntiles = 0;
     for (int i = 0; i < n; ++i) {
         sds[i] = make_desc(grids[i], rhs[i], x[i], tol, mode, prec, ntiles);
-        for (int t = 0; t < sds[i].ntiles; ++t) tile_sys.push_back(i);
         ntiles += sds[i].ntiles;
     }
+    bool fp64 = prec == PPE_PREC_FP64;
+    int maxb = std::min(solver_max_blocks(fp64, grids[0]->opts.blocks_per_sm), ntiles);
+    std::vector<BlockRange> ranges;
+    int nslots = 0;
+    if (maxb < 1 || !plan_blocks(sds, maxb, ranges, nslots)) return arg_error("ppe_solve_batch: cannot partition");
     SysDesc *sys_dev = nullptr;
     SysState *st_dev = nullptr;
-    int32_t *ts_dev = nullptr;
+    BlockRange *rg_dev = nullptr;
     double *part_dev = nullptr;
     Control *ctl_dev = nullptr;
-    ppe_status status = PPE_OK;
     auto cleanup = [&]() {
-        cudaFree(sys_dev); cudaFree(st_dev); cudaFree(ts_dev); cudaFree(part_dev); cudaFree(ctl_dev);
+        cudaFree(sys_dev); cudaFree(st_dev); cudaFree(rg_dev); cudaFree(part_dev); cudaFree(ctl_dev);
     };
     if (cudaMalloc(&sys_dev, sizeof(SysDesc) * n) != cudaSuccess || cudaMalloc(&st_dev, sizeof(SysState) * n) != cudaSuccess ||
-        cudaMalloc(&ts_dev, sizeof(int32_t) * ntiles) != cudaSuccess ||
-        cudaMalloc(&part_dev, sizeof(double) * NPART * (size_t)ntiles) != cudaSuccess ||
+        cudaMalloc(&rg_dev, sizeof(BlockRange) * ranges.size()) != cudaSuccess ||
+        cudaMalloc(&part_dev, sizeof(double) * NPART * (size_t)nslots) != cudaSuccess ||
         cudaMalloc(&ctl_dev, sizeof(Control)) != cudaSuccess) {
         cleanup();
         set_error("ppe_solve_batch: device allocation failed");
         return PPE_ERR_NOMEM;
     }
     cudaMemcpyAsync(sys_dev, sds.data(), sizeof(SysDesc) * n, cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(ts_dev, tile_sys.data(), sizeof(int32_t) * ntiles, cudaMemcpyHostToDevice, st);
-    status = drive(n, grids, sys_dev, st_dev, ts_dev, part_dev, ctl_dev, nullptr, ntiles, prec == PPE_PREC_FP64,
-                   mode, net, st, info);
+    cudaMemcpyAsync(rg_dev, ranges.data(), sizeof(BlockRange) * ranges.size(), cudaMemcpyHostToDevice, st);
+    ppe_status status = drive(n, grids, sys_dev, st_dev, rg_dev, (int)ranges.size(), part_dev, ctl_dev, fp64, net, st,
+                              info);
     cudaStreamSynchronize(st);
     cleanup();
     return status;

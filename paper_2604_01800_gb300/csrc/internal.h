@@ -2,6 +2,8 @@
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include <algorithm>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -43,8 +45,8 @@ inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
 // Phases of the per-system state machine run by the solver kernel.
 enum Phase : int32_t {
     PH_INIT = 0,      // b statistics: sum, sum of squares, sum of magnitudes
-    PH_RES = 1,       // FP64 true residual of x + d (iterative refinement)
-    PH_RESTART = 2,   // start of a CG-type phase: u = D^-1 r, w = A u, dots
+    PH_RES = 1,       // FP64 true residual of x + d (residual replacement / refinement)
+    PH_RESTART = 2,   // u = D^-1 r, w = A u and the CG dots; fresh start or continuation
     PH_ITER = 3,      // one single-reduction PCG iteration
     PH_NET = 4,       // waiting for a network direction (kernel yields)
     PH_DLSM_DOT = 5,  // DLSM: r.e, e.Ae, e.e
@@ -54,12 +56,15 @@ enum Phase : int32_t {
     PH_DONE = 9
 };
 
+constexpr int SMAX = 8;   // systems one block may span
+
 // Static description of one system (device memory, written by the host).
 struct SysDesc {
     int32_t nx, ny, pitch, tiles_x, tile0, ntiles;
     int32_t mode, precision;              // ppe_mode, ppe_precision
     int32_t max_iters, num_cg, num_dlsm, hybrid_budget;
-    double tol, inner_rtol, dlsm_guard, diag_max;
+    int32_t part0, blk0, nparts, pad_;    // partial slots part0.. for blocks blk0..blk0+nparts-1
+    double tol, ru_delta, dlsm_guard, diag_max;
     double n_cells;                       // nx*ny as double
     const double *dx, *dy;                // widths [nx], [ny]
     const double *fx, *fy;                // face coefficients [nx+1], [ny+1]; 0 at walls
@@ -70,31 +75,38 @@ struct SysDesc {
     float *e;                             // DLSM direction [ny][pitch]
 };
 
-// Mutable per-system state (device memory, owned by the solver kernel).
+// Mutable per-system state.  Every block that works on a system keeps an
+// identical copy (each computes the same transition from the same partial
+// sums); the system's first block writes it back when the kernel returns.
 struct SysState {
     int32_t phase, status;
     int32_t it_pcg, it_dlsm, dlsm_skipped, refinements, it_total;
     int32_t cg_count, dlsm_count, fell_back, net_calls;
-    int32_t has_d, fold_d, reset_d, first, cur, zero_x, pad_;
-    double alpha, beta, gamma, mu, mu_b, bnorm, tau, rnorm, relres, incompat;
-    double alpha_d, xmean, rho;
+    int32_t has_d, fold_d, reset_d, first, cur, zero_x, keep_dir;
+    double alpha, beta, gamma, mu, mu_b, bnorm, target, rnorm, relres, incompat;
+    double alpha_d, xmean, rho, rho_ref;
+};
+
+// Tiles [t0, t1) of a block; they belong to systems s0..s1.
+struct BlockRange {
+    int32_t t0, t1, s0, s1;
 };
 
 // Global control block of one persistent launch.
+// Retirements are counted in two slots by step parity: a block can only add
+// to the slot of step s+2 after every block has read the slot of step s.
 struct Control {
-    uint32_t bar_count;
-    uint32_t bar_gen;
-    int32_t err;           // PPE_ERR_TIMEOUT etc.
-    int32_t exit_kernel;   // 1: every live system waits for the network or is done
-    int32_t any_net;       // 1: at least one system waits for the network
-    int32_t pad[3];
+    unsigned long long arrive;   // cumulative barrier arrivals
+    int32_t err;                 // PPE_ERR_TIMEOUT if a bounded wait expired
+    int32_t active0;             // systems with passes left at launch
+    int32_t retired[2];          // systems that stopped needing passes, by step parity
 };
 
 struct SolverArgs {
     SysDesc *sys;
     SysState *st;
-    const int32_t *tile_sys;   // tile -> system
-    double *partials;          // [ntiles][NPART]
+    const BlockRange *ranges;  // one per block
+    double *partials;          // [slots][NPART]
     Control *ctl;
     int32_t nsys, ntiles;
     int64_t spin_limit_ns;
@@ -123,10 +135,10 @@ struct ppe_grid {
     // single-system launch resources
     ppe::SysDesc *sys_dev = nullptr;
     ppe::SysState *st_dev = nullptr;
-    int32_t *tile_sys_dev = nullptr;
+    ppe::BlockRange *ranges_dev = nullptr;
+    int ranges_blocks = 0;
     double *partials_dev = nullptr;
     ppe::Control *ctl_dev = nullptr;
-    ppe::SysState *st_host = nullptr;    // pinned
     void *net_cache = nullptr;           // per-network data for this grid (owned by the net)
     const void *net_owner = nullptr;
 };

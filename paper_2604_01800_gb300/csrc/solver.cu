@@ -1,12 +1,17 @@
-// Persistent solver kernel: iterative refinement (FP64) around a
-// single-reduction Jacobi PCG (FP32 or FP64) with interleaved DLSM steps.
+// Persistent solver kernel: single-reduction Jacobi PCG (FP32 or FP64 inner
+// vectors) with FP64 residual replacement, interleaved DLSM steps, and the
+// compatibility projection / zero-mean normalisation of the Neumann problem.
 //
-// One cooperative launch runs the whole per-system state machine of every
-// system in a batch; grid-wide barriers separate the passes.  A pass sweeps
-// the tiles of every system once; each tile writes FP64 partial sums, and the
-// last block to reach the barrier reduces them (fixed order, so results are
-// reproducible) and advances each system's state.  The kernel returns when
-// every live system is done or waits for a network direction.
+// One cooperative launch runs the per-system state machine of every system of
+// a batch.  Each block owns a contiguous range of tiles (of one or a few
+// systems).  A step: every block runs the current pass of each of its systems
+// over its tiles and writes one FP64 partial-sum record per system, then
+// arrives at a grid-wide counter barrier.  After the barrier each block reads
+// the partial records of its systems (fixed order, so every block obtains the
+// same sums bit for bit) and advances its own copy of each system's state.
+// There is no serial finisher: a step costs one barrier plus one read of the
+// partial records.  The kernel returns when no system has a pass left (all
+// are done or wait for a network direction).
 //
 // Operator (Sec. 2.1 Eq. 6, volume-scaled): for cell (i,j)
 //   (A u)_ij = dy_j [fe_i (u_ij - u_E) + fw_i (u_ij - u_W)]
@@ -18,9 +23,14 @@
 //   p = u + beta p,  s = w + beta s  (s = A p),  x += alpha p,  r -= alpha s,
 //   gamma' = r.u, delta' = (A u).u, beta' = gamma'/gamma,
 //   alpha' = gamma' / (delta' - beta' gamma' / alpha).
-// Each block recomputes the new residual on a one-cell halo of its tile
-// (reading r two cells out) so that A u' is available in the same pass: one
-// grid barrier per iteration.
+// Each block recomputes the new residual on a one-cell ring around its tile
+// (reading r two cells out) so that A u' is available in the same pass.
+//
+// Mixed precision: the FP32 recursive residual is replaced by the FP64 true
+// residual b - A(x + d) whenever it has dropped by a factor ru_delta since
+// the last replacement, and before convergence is declared; the search
+// direction is kept across a replacement (reliable updates), so the FP32
+// iteration converges like the FP64 one.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -35,6 +45,8 @@ namespace {
 constexpr int WX = TILE_X + 4;     // tile window with a two-cell halo
 constexpr int WY = TILE_Y + 4;
 constexpr int WN = WX * WY;
+constexpr int NWARP = SOLVER_THREADS / 32;
+constexpr int NL = (WN + SOLVER_THREADS - 1) / SOLVER_THREADS;   // window loads per thread
 
 __device__ __forceinline__ uint64_t globaltimer_ns()
 {
@@ -43,16 +55,11 @@ __device__ __forceinline__ uint64_t globaltimer_ns()
     return t;
 }
 
-__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p)
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p)
 {
-    uint32_t v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
-}
-
-__device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v)
-{
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 template <typename T> __device__ __forceinline__ T ld_cg(const T *p) { return __ldcg(p); }
@@ -75,11 +82,11 @@ template <typename T> struct SmemT {
     Coef<double> cfd;
     Coef<float> cff;
     Work<T> w;
-    double red[NPART][TILE_Y];
-    SysDesc sd;
-    SysState st;
-    int32_t last;
-    uint32_t gen;
+    double red[NPART][NWARP];
+    SysDesc sd[SMAX];
+    SysState st[SMAX];
+    double tot[NPART];
+    int32_t live;
     int32_t go;
 };
 
@@ -133,113 +140,127 @@ __device__ __forceinline__ bool in_dom(const SysDesc &sd, int i, int j)
     return i >= 0 && j >= 0 && i < sd.nx && j < sd.ny;
 }
 
-// Block reduction of NPART values; thread k < NPART writes the tile partial.
-template <typename T, typename S>
-__device__ void block_partials(S &sm, T (&acc)[NPART], double *out)
+__device__ __forceinline__ bool in_ring1(int wi, int wj) { return wi >= 1 && wi < WX - 1 && wj >= 1 && wj < WY - 1; }
+
+// Warp-reduce the thread's tile sums and add them to lane 0's FP64 totals.
+template <typename T> __device__ __forceinline__ void warp_accumulate(const T (&t)[NPART], double (&acc)[NPART])
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int q = 0; q < NPART; ++q) {
-        T v = acc[q];
+        T v = t[q];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) sm.red[q][warp] = (double)v;
+        acc[q] += (double)v;
     }
-    __syncthreads();
-    if (threadIdx.x < NPART) {
-        double s = 0.0;
-        for (int w = 0; w < TILE_Y; ++w) s += sm.red[threadIdx.x][w];
-        out[threadIdx.x] = s;
-    }
-    __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
-// passes (one tile each)
+// passes over one tile; thread sums go to acc (lane 0 of each warp)
 // ---------------------------------------------------------------------------
 
 // b statistics: b = -V S
-template <typename T, typename S> __device__ void pass_init(S &sm, int i0, int j0, double *out)
+template <typename T, typename S> __device__ void pass_init(S &sm, const SysDesc &sd, int i0, int j0, double (&acc)[NPART])
 {
-    const SysDesc &sd = sm.sd;
-    double acc[NPART] = {0, 0, 0, 0, 0, 0};
+    double t[NPART] = {0, 0, 0, 0, 0, 0};
     const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
     int j = j0 + ty;
+#pragma unroll
     for (int c = 0; c < 4; ++c) {
         int i = i0 + tx + 32 * c;
         if (i < sd.nx && j < sd.ny) {
             double b = -sd.dx[i] * sd.dy[j] * sd.f[(size_t)j * sd.nx + i];
-            acc[0] += b; acc[1] += b * b; acc[2] += fabs(b);
+            t[0] += b; t[1] += b * b; t[2] += fabs(b);
         }
     }
-    block_partials(sm, acc, out);
+    warp_accumulate(t, acc);
 }
 
-// FP64 true residual r = (b - mu_b) - A (x + d); stores r into the inner buffer.
-template <typename T, typename S> __device__ void pass_res(S &sm, int i0, int j0, double *out)
+// FP64 true residual r = (b - mu_b) - A (x + d); stored into the inner buffer.
+template <typename T, typename S>
+__device__ void pass_res(S &sm, const SysDesc &sd, const SysState &st, int i0, int j0, double (&acc)[NPART])
 {
-    const SysDesc &sd = sm.sd;
-    const SysState &st = sm.st;
     Coef<double> &cf = sm.cfd;
     double *X = reinterpret_cast<double *>(&sm.w);
     load_coef<double>(cf, sd, i0, j0, sd.dx, sd.fx, sd.dy, sd.fy);
     const T *d = (const T *)sd.d;
-    for (int k = threadIdx.x; k < WN; k += blockDim.x) {
-        int wi = k % WX, wj = k / WX, i = i0 - 2 + wi, j = j0 - 2 + wj;
-        double v = 0.0;
-        if (wi >= 1 && wi < WX - 1 && wj >= 1 && wj < WY - 1 && in_dom(sd, i, j)) {
-            v = ld_cg(sd.x + (size_t)j * sd.nx + i);
-            if (st.has_d) v += (double)ld_cg(d + (size_t)j * sd.pitch + i);
+    double xv[NL];
+#pragma unroll
+    for (int q = 0; q < NL; ++q) {
+        int k = threadIdx.x + q * SOLVER_THREADS;
+        xv[q] = 0.0;
+        if (k < WN) {
+            int wi = k % WX, wj = k / WX, i = i0 - 2 + wi, j = j0 - 2 + wj;
+            if (in_ring1(wi, wj) && in_dom(sd, i, j)) {
+                xv[q] = ld_cg(sd.x + (size_t)j * sd.nx + i);
+                if (st.has_d) xv[q] += (double)ld_cg(d + (size_t)j * sd.pitch + i);
+            }
         }
-        X[k] = v;
+    }
+#pragma unroll
+    for (int q = 0; q < NL; ++q) {
+        int k = threadIdx.x + q * SOLVER_THREADS;
+        if (k < WN) X[k] = xv[q];
     }
     __syncthreads();
-    double acc[NPART] = {0, 0, 0, 0, 0, 0};
+    double t[NPART] = {0, 0, 0, 0, 0, 0};
     const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
     int j = j0 + ty, wj = ty + 2;
     T *r = (T *)sd.r[st.cur];
+#pragma unroll
     for (int c = 0; c < 4; ++c) {
         int i = i0 + tx + 32 * c, wi = tx + 32 * c + 2;
         if (i < sd.nx && j < sd.ny) {
             double b = -sd.dx[i] * sd.dy[j] * ld_cg(sd.f + (size_t)j * sd.nx + i) - st.mu_b;
             double rv = b - stencil<double>(cf, X, wi, wj);
             r[(size_t)j * sd.pitch + i] = (T)rv;
-            acc[0] += rv; acc[1] += rv * rv;
+            t[0] += rv; t[1] += rv * rv;
         }
     }
-    block_partials(sm, acc, out);
+    warp_accumulate(t, acc);
+    __syncthreads();
 }
 
-// Start of a CG-type phase: u = D^-1 (r - mu), w = A u; dots r.u, w.u, r.r, sum r.
-template <typename T, typename S> __device__ void pass_restart(S &sm, int i0, int j0, double *out)
+// u = D^-1 (r - mu), w = A u; dots r.u, w.u, r.r, sum r.  Folds d into x
+// when a replacement is pending.
+template <typename T, typename S>
+__device__ void pass_restart(S &sm, const SysDesc &sd, const SysState &st, int i0, int j0, double (&acc)[NPART])
 {
-    const SysDesc &sd = sm.sd;
-    const SysState &st = sm.st;
     Coef<T> &cf = coef_of<T>(sm);
     T *R = sm.w.a0, *U = sm.w.a1;
     load_coef_t<T>(sm, sd, i0, j0);
-    __syncthreads();
     const T *rin = (const T *)sd.r[st.cur];
     const T mu = (T)st.mu;
-    for (int k = threadIdx.x; k < WN; k += blockDim.x) {
-        int wi = k % WX, wj = k / WX, i = i0 - 2 + wi, j = j0 - 2 + wj;
-        T rv = 0;
-        if (wi >= 1 && wi < WX - 1 && wj >= 1 && wj < WY - 1 && in_dom(sd, i, j))
-            rv = ld_cg(rin + (size_t)j * sd.pitch + i) - mu;
-        R[k] = rv;
-        U[k] = rv * dinv_at<T>(cf, wi, wj);
+    T rv[NL];
+#pragma unroll
+    for (int q = 0; q < NL; ++q) {
+        int k = threadIdx.x + q * SOLVER_THREADS;
+        rv[q] = 0;
+        if (k < WN) {
+            int wi = k % WX, wj = k / WX, i = i0 - 2 + wi, j = j0 - 2 + wj;
+            if (in_ring1(wi, wj) && in_dom(sd, i, j)) rv[q] = ld_cg(rin + (size_t)j * sd.pitch + i) - mu;
+        }
     }
     __syncthreads();
-    T acc[NPART] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+    for (int q = 0; q < NL; ++q) {
+        int k = threadIdx.x + q * SOLVER_THREADS;
+        if (k < WN) {
+            R[k] = rv[q];
+            U[k] = rv[q] * dinv_at<T>(cf, k % WX, k / WX);
+        }
+    }
+    __syncthreads();
+    T t[NPART] = {0, 0, 0, 0, 0, 0};
     const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
     int j = j0 + ty, wj = ty + 2;
     T *dd = (T *)sd.d;
+#pragma unroll
     for (int c = 0; c < 4; ++c) {
         int i = i0 + tx + 32 * c, wi = tx + 32 * c + 2;
         if (i < sd.nx && j < sd.ny) {
             int k = wj * WX + wi;
             T w = stencil<T>(cf, U, wi, wj);
-            acc[0] += R[k] * U[k]; acc[1] += w * U[k]; acc[2] += R[k] * R[k]; acc[3] += R[k];
+            t[0] += R[k] * U[k]; t[1] += w * U[k]; t[2] += R[k] * R[k]; t[3] += R[k];
             if (st.reset_d) {
                 size_t gi = (size_t)j * sd.pitch + i;
                 if (st.fold_d) sd.x[(size_t)j * sd.nx + i] += (double)ld_cg(dd + gi);
@@ -247,18 +268,17 @@ template <typename T, typename S> __device__ void pass_restart(S &sm, int i0, in
             }
         }
     }
-    block_partials(sm, acc, out);
+    warp_accumulate(t, acc);
+    __syncthreads();
 }
 
 // One single-reduction PCG iteration.
-template <typename T, typename S> __device__ void pass_iter(S &sm, int i0, int j0, double *out)
+template <typename T, typename S>
+__device__ void pass_iter(S &sm, const SysDesc &sd, const SysState &st, int i0, int j0, double (&acc)[NPART])
 {
-    const SysDesc &sd = sm.sd;
-    const SysState &st = sm.st;
     Coef<T> &cf = coef_of<T>(sm);
     T *R = sm.w.a0, *U = sm.w.a1, *Sv = sm.w.a2, *Rn = sm.w.a3, *Un = sm.w.a4, *Sn = sm.w.a5;
     load_coef_t<T>(sm, sd, i0, j0);
-    __syncthreads();
     const int cur = st.cur;
     const T *rin = (const T *)sd.r[cur];
     const T *sin = (const T *)sd.s[cur];
@@ -268,24 +288,52 @@ template <typename T, typename S> __device__ void pass_iter(S &sm, int i0, int j
     T *dv = (T *)sd.d;
     const T mu = (T)st.mu, alpha = (T)st.alpha, beta = (T)st.beta;
     const bool first = st.first != 0;
-    for (int k = threadIdx.x; k < WN; k += blockDim.x) {
-        int wi = k % WX, wj = k / WX, i = i0 - 2 + wi, j = j0 - 2 + wj;
-        T rv = 0, sv = 0;
-        if (in_dom(sd, i, j)) {
-            size_t gi = (size_t)j * sd.pitch + i;
-            rv = ld_cg(rin + gi) - mu;
-            if (!first && wi >= 1 && wi < WX - 1 && wj >= 1 && wj < WY - 1) sv = ld_cg(sin + gi);
+    const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
+    const int j = j0 + ty, wj0 = ty + 2;
+    // issue every global load of this tile before using any of them
+    T rv[NL], sv[NL], pold[4], dold[4];
+#pragma unroll
+    for (int q = 0; q < NL; ++q) {
+        int k = threadIdx.x + q * SOLVER_THREADS;
+        rv[q] = 0; sv[q] = 0;
+        if (k < WN) {
+            int wi = k % WX, wj = k / WX, i = i0 - 2 + wi, jj = j0 - 2 + wj;
+            if (in_dom(sd, i, jj)) {
+                size_t gi = (size_t)jj * sd.pitch + i;
+                rv[q] = ld_cg(rin + gi);
+                if (!first && in_ring1(wi, wj)) sv[q] = ld_cg(sin + gi);
+            }
         }
-        R[k] = rv;
-        U[k] = rv * dinv_at<T>(cf, wi, wj);
-        Sv[k] = sv;
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        int i = i0 + tx + 32 * c;
+        pold[c] = 0; dold[c] = 0;
+        if (i < sd.nx && j < sd.ny) {
+            size_t gi = (size_t)j * sd.pitch + i;
+            if (!first) pold[c] = ld_cg(pv + gi);
+            dold[c] = ld_cg(dv + gi);
+        }
+    }
+    __syncthreads();   // coefficients visible
+#pragma unroll
+    for (int q = 0; q < NL; ++q) {
+        int k = threadIdx.x + q * SOLVER_THREADS;
+        if (k < WN) {
+            int wi = k % WX, wj = k / WX;
+            bool in = in_dom(sd, i0 - 2 + wi, j0 - 2 + wj);
+            T r = in ? rv[q] - mu : T(0);
+            R[k] = r;
+            U[k] = r * dinv_at<T>(cf, wi, wj);
+            Sv[k] = sv[q];
+        }
     }
     __syncthreads();
     // new residual on the tile and its one-cell ring
     for (int k = threadIdx.x; k < WN; k += blockDim.x) {
-        int wi = k % WX, wj = k / WX, i = i0 - 2 + wi, j = j0 - 2 + wj;
+        int wi = k % WX, wj = k / WX, i = i0 - 2 + wi, jj = j0 - 2 + wj;
         T rn = 0, un = 0, sn = 0;
-        if (wi >= 1 && wi < WX - 1 && wj >= 1 && wj < WY - 1 && in_dom(sd, i, j)) {
+        if (in_ring1(wi, wj) && in_dom(sd, i, jj)) {
             T w = stencil<T>(cf, U, wi, wj);
             sn = w + beta * Sv[k];
             rn = R[k] - alpha * sn;
@@ -294,76 +342,48 @@ template <typename T, typename S> __device__ void pass_iter(S &sm, int i0, int j
         Rn[k] = rn; Un[k] = un; Sn[k] = sn;
     }
     __syncthreads();
-    T acc[NPART] = {0, 0, 0, 0, 0, 0};
-    const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
-    int j = j0 + ty, wj = ty + 2;
+    T t[NPART] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
     for (int c = 0; c < 4; ++c) {
         int i = i0 + tx + 32 * c, wi = tx + 32 * c + 2;
         if (i < sd.nx && j < sd.ny) {
-            int k = wj * WX + wi;
+            int k = wj0 * WX + wi;
             size_t gi = (size_t)j * sd.pitch + i;
-            T pold = first ? T(0) : ld_cg(pv + gi);
-            T pn = U[k] + beta * pold;
+            T pn = U[k] + beta * pold[c];
             pv[gi] = pn;
-            dv[gi] = ld_cg(dv + gi) + alpha * pn;
+            dv[gi] = dold[c] + alpha * pn;
             sout[gi] = Sn[k];
             T rn = Rn[k], un = Un[k];
             rout[gi] = rn;
-            T wn = stencil<T>(cf, Un, wi, wj);
-            acc[0] += rn * un; acc[1] += wn * un; acc[2] += rn * rn; acc[3] += rn;
+            T wn = stencil<T>(cf, Un, wi, wj0);
+            t[0] += rn * un; t[1] += wn * un; t[2] += rn * rn; t[3] += rn;
         }
     }
-    block_partials(sm, acc, out);
-}
-
-// DLSM dots: r.e, e.(A e), e.e  (Eq. 11)
-template <typename T, typename S> __device__ void pass_dlsm_dot(S &sm, int i0, int j0, double *out)
-{
-    const SysDesc &sd = sm.sd;
-    const SysState &st = sm.st;
-    Coef<float> &cf = sm.cff;
-    float *E = reinterpret_cast<float *>(&sm.w);
-    load_coef<float>(cf, sd, i0, j0, sd.dx32, sd.fx32, sd.dy32, sd.fy32);
-    for (int k = threadIdx.x; k < WN; k += blockDim.x) {
-        int wi = k % WX, wj = k / WX, i = i0 - 2 + wi, j = j0 - 2 + wj;
-        float v = 0.f;
-        if (wi >= 1 && wi < WX - 1 && wj >= 1 && wj < WY - 1 && in_dom(sd, i, j))
-            v = ld_cg(sd.e + (size_t)j * sd.pitch + i);
-        E[k] = v;
-    }
+    warp_accumulate(t, acc);
     __syncthreads();
-    const T *rin = (const T *)sd.r[st.cur];
-    const T mu = (T)st.mu;
-    float acc[NPART] = {0, 0, 0, 0, 0, 0};
-    const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
-    int j = j0 + ty, wj = ty + 2;
-    for (int c = 0; c < 4; ++c) {
-        int i = i0 + tx + 32 * c, wi = tx + 32 * c + 2;
-        if (i < sd.nx && j < sd.ny) {
-            int k = wj * WX + wi;
-            float ev = E[k];
-            float rv = (float)(ld_cg(rin + (size_t)j * sd.pitch + i) - mu);
-            float q = stencil<float>(cf, E, wi, wj);
-            acc[0] += rv * ev; acc[1] += ev * q; acc[2] += ev * ev;
-        }
-    }
-    block_partials(sm, acc, out);
 }
 
-// DLSM update: d += alpha e, r_new = (r - mu) - alpha A e  (Eq. 12)
-template <typename T, typename S> __device__ void pass_dlsm_upd(S &sm, int i0, int j0, double *out)
+// DLSM dots r.e, e.(A e), e.e  (Eq. 11); with upd: d += alpha e, r_new = r - alpha A e (Eq. 12)
+template <typename T, typename S, bool UPD>
+__device__ void pass_dlsm(S &sm, const SysDesc &sd, const SysState &st, int i0, int j0, double (&acc)[NPART])
 {
-    const SysDesc &sd = sm.sd;
-    const SysState &st = sm.st;
     Coef<float> &cf = sm.cff;
     float *E = reinterpret_cast<float *>(&sm.w);
     load_coef<float>(cf, sd, i0, j0, sd.dx32, sd.fx32, sd.dy32, sd.fy32);
-    for (int k = threadIdx.x; k < WN; k += blockDim.x) {
-        int wi = k % WX, wj = k / WX, i = i0 - 2 + wi, j = j0 - 2 + wj;
-        float v = 0.f;
-        if (wi >= 1 && wi < WX - 1 && wj >= 1 && wj < WY - 1 && in_dom(sd, i, j))
-            v = ld_cg(sd.e + (size_t)j * sd.pitch + i);
-        E[k] = v;
+    float ev[NL];
+#pragma unroll
+    for (int q = 0; q < NL; ++q) {
+        int k = threadIdx.x + q * SOLVER_THREADS;
+        ev[q] = 0.f;
+        if (k < WN) {
+            int wi = k % WX, wj = k / WX, i = i0 - 2 + wi, j = j0 - 2 + wj;
+            if (in_ring1(wi, wj) && in_dom(sd, i, j)) ev[q] = ld_cg(sd.e + (size_t)j * sd.pitch + i);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < NL; ++q) {
+        int k = threadIdx.x + q * SOLVER_THREADS;
+        if (k < WN) E[k] = ev[q];
     }
     __syncthreads();
     const int cur = st.cur;
@@ -371,33 +391,41 @@ template <typename T, typename S> __device__ void pass_dlsm_upd(S &sm, int i0, i
     T *rout = (T *)sd.r[cur ^ 1];
     T *dv = (T *)sd.d;
     const T mu = (T)st.mu, alpha = (T)st.alpha_d;
-    T acc[NPART] = {0, 0, 0, 0, 0, 0};
+    T t[NPART] = {0, 0, 0, 0, 0, 0};
     const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
     int j = j0 + ty, wj = ty + 2;
+#pragma unroll
     for (int c = 0; c < 4; ++c) {
         int i = i0 + tx + 32 * c, wi = tx + 32 * c + 2;
         if (i < sd.nx && j < sd.ny) {
             int k = wj * WX + wi;
             size_t gi = (size_t)j * sd.pitch + i;
+            T e = (T)E[k];
             T q = (T)stencil<float>(cf, E, wi, wj);
-            T rn = (ld_cg(rin + gi) - mu) - alpha * q;
-            rout[gi] = rn;
-            dv[gi] = ld_cg(dv + gi) + alpha * (T)E[k];
-            acc[2] += rn * rn; acc[3] += rn;
+            T r = ld_cg(rin + gi) - mu;
+            if (UPD) {
+                T rn = r - alpha * q;
+                rout[gi] = rn;
+                dv[gi] = ld_cg(dv + gi) + alpha * e;
+                t[2] += rn * rn; t[3] += rn;
+            } else {
+                t[0] += r * e; t[1] += e * q; t[2] += e * e;
+            }
         }
     }
-    block_partials(sm, acc, out);
+    warp_accumulate(t, acc);
+    __syncthreads();
 }
 
 // Fold d into x (if pending) and accumulate sum V, sum V x.
-template <typename T, typename S> __device__ void pass_final1(S &sm, int i0, int j0, double *out)
+template <typename T, typename S>
+__device__ void pass_final1(S &sm, const SysDesc &sd, const SysState &st, int i0, int j0, double (&acc)[NPART])
 {
-    const SysDesc &sd = sm.sd;
-    const SysState &st = sm.st;
     const T *dd = (const T *)sd.d;
-    double acc[NPART] = {0, 0, 0, 0, 0, 0};
+    double t[NPART] = {0, 0, 0, 0, 0, 0};
     const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
     int j = j0 + ty;
+#pragma unroll
     for (int c = 0; c < 4; ++c) {
         int i = i0 + tx + 32 * c;
         if (i < sd.nx && j < sd.ny) {
@@ -406,19 +434,18 @@ template <typename T, typename S> __device__ void pass_final1(S &sm, int i0, int
             if (st.fold_d && !st.zero_x) x += (double)ld_cg(dd + (size_t)j * sd.pitch + i);
             sd.x[gx] = x;
             double v = sd.dx[i] * sd.dy[j];
-            acc[0] += v; acc[1] += v * x;
+            t[0] += v; t[1] += v * x;
         }
     }
-    block_partials(sm, acc, out);
+    warp_accumulate(t, acc);
 }
 
-template <typename T, typename S> __device__ void pass_final2(S &sm, int i0, int j0, double *out)
+template <typename T, typename S>
+__device__ void pass_final2(S &sm, const SysDesc &sd, const SysState &st, int i0, int j0, double (&acc)[NPART])
 {
-    const SysDesc &sd = sm.sd;
-    const SysState &st = sm.st;
-    double acc[NPART] = {0, 0, 0, 0, 0, 0};
     const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
     int j = j0 + ty;
+#pragma unroll
     for (int c = 0; c < 4; ++c) {
         int i = i0 + tx + 32 * c;
         if (i < sd.nx && j < sd.ny) {
@@ -426,53 +453,32 @@ template <typename T, typename S> __device__ void pass_final2(S &sm, int i0, int
             sd.x[gx] = ld_cg(sd.x + gx) - st.xmean;
         }
     }
-    block_partials(sm, acc, out);
 }
 
 // ---------------------------------------------------------------------------
-// finisher: reduce the partials of every system and advance its state
+// state machine
 // ---------------------------------------------------------------------------
 
-template <typename S>
-__device__ void reduce_system(S &sm, const double *partials, int tile0, int ntiles, double (&tot)[NPART])
+__device__ __forceinline__ bool is_pass_phase(int ph) { return ph != PH_NET && ph != PH_DONE; }
+
+__device__ __forceinline__ int iter_cap(const SysDesc &sd)
 {
-    double acc[NPART] = {0, 0, 0, 0, 0, 0};
-    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
-        const double *p = partials + (size_t)(tile0 + t) * NPART;
-#pragma unroll
-        for (int q = 0; q < NPART; ++q) acc[q] += ld_cg(p + q);
-    }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int q = 0; q < NPART; ++q) {
-        double v = acc[q];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) sm.red[q][warp] = v;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < NPART; ++q) {
-        double s = 0.0;
-        for (int w = 0; w < TILE_Y; ++w) s += sm.red[q][w];
-        tot[q] = s;
-    }
-    __syncthreads();
+    return sd.max_iters + (sd.mode == PPE_MODE_HYBRID ? sd.hybrid_budget : 0);
 }
 
-__device__ void enter_inner_converged(SysState &s)
+__device__ void to_res(SysState &s, int keep_dir)
 {
     s.has_d = 1;
+    s.keep_dir = keep_dir;
     s.phase = PH_RES;
 }
 
-// State transition of one system after a pass (runs on one thread).
-__device__ void advance(const SysDesc &sd, SysState &s, const double (&t)[NPART], bool resume_net)
+// Transition of one system after a pass; t holds the reduced partial sums.
+__device__ void advance(const SysDesc &sd, SysState &s, const double (&t)[NPART])
 {
     const double N = sd.n_cells;
-    int ph = s.phase;
-    if (ph == PH_NET && resume_net) ph = PH_DLSM_DOT;
-    switch (ph) {
+    const bool pcg_like = sd.mode == PPE_MODE_PCG || s.fell_back;
+    switch (s.phase) {
     case PH_INIT: {
         s.mu_b = t[0] / N;
         double bb = t[1] - N * s.mu_b * s.mu_b;
@@ -488,6 +494,8 @@ __device__ void advance(const SysDesc &sd, SysState &s, const double (&t)[NPART]
             s.phase = PH_FINAL1;
         } else {
             s.has_d = 0;
+            s.keep_dir = 0;
+            s.target = 0.9 * sd.tol * s.bnorm;
             s.phase = PH_RES;
         }
         break;
@@ -505,16 +513,12 @@ __device__ void advance(const SysDesc &sd, SysState &s, const double (&t)[NPART]
             s.phase = PH_FINAL1;
         } else if (s.relres <= sd.tol) {
             s.phase = PH_FINAL1;
-        } else if (s.it_total >= sd.max_iters + (sd.mode == PPE_MODE_HYBRID ? sd.hybrid_budget : 0) ||
-                   s.refinements > 200) {
+        } else if (s.it_total >= iter_cap(sd) || s.refinements > 5000) {
             s.status = PPE_ERR_NOT_CONVERGED;
             s.phase = PH_FINAL1;
         } else {
-            double tau = sd.inner_rtol * s.rnorm;
-            double floor_ = 0.5 * sd.tol * s.bnorm;
-            s.tau = tau > floor_ ? tau : floor_;
+            s.rho_ref = s.rnorm;
             s.reset_d = 1;
-            s.cg_count = 0;
             s.phase = PH_RESTART;
         }
         break;
@@ -526,15 +530,29 @@ __device__ void advance(const SysDesc &sd, SysState &s, const double (&t)[NPART]
         s.reset_d = 0;
         s.fold_d = 0;
         s.has_d = 1;
-        if (sqrt(s.rho) <= s.tau || !(t[1] > 0.0) || !isfinite(t[0] / t[1])) {
-            enter_inner_converged(s);
+        s.cg_count = 0;
+        if (sqrt(s.rho) <= s.target || !(t[1] > 0.0) || !(t[0] > 0.0)) {
+            to_res(s, 0);
             break;
         }
+        bool cont = s.keep_dir && s.gamma > 0.0 && s.alpha > 0.0;
+        if (cont) {
+            double beta = t[0] / s.gamma;
+            double denom = t[1] - beta * t[0] / s.alpha;
+            cont = denom > 0.0 && isfinite(beta);
+            if (cont) {
+                s.beta = beta;
+                s.alpha = t[0] / denom;
+                s.first = 0;
+            }
+        }
+        if (!cont) {
+            s.alpha = t[0] / t[1];
+            s.beta = 0.0;
+            s.first = 1;
+        }
         s.gamma = t[0];
-        s.alpha = t[0] / t[1];
-        s.beta = 0.0;
-        s.first = 1;
-        s.cg_count = 0;
+        s.keep_dir = 0;
         s.phase = PH_ITER;
         break;
     }
@@ -548,15 +566,17 @@ __device__ void advance(const SysDesc &sd, SysState &s, const double (&t)[NPART]
         s.first = 0;
         s.cg_count++;
         if (sd.mode == PPE_MODE_HYBRID && !s.fell_back && s.it_total >= sd.hybrid_budget) s.fell_back = 1;
-        if (sqrt(s.rho) <= s.tau || s.it_total >= sd.max_iters + (sd.mode == PPE_MODE_HYBRID ? sd.hybrid_budget : 0)) {
-            enter_inner_converged(s);
-            break;
-        }
+        double rn = sqrt(s.rho);
+        if (!isfinite(rn)) { to_res(s, 0); break; }
         double gnew = t[0];
         double beta = gnew / s.gamma;
         double denom = t[1] - beta * gnew / s.alpha;
-        if (!(denom > 0.0) || !isfinite(beta)) {       // breakdown: restart from the true residual
-            enter_inner_converged(s);
+        bool ok = denom > 0.0 && isfinite(beta) && gnew > 0.0;
+        if (rn <= s.target || s.it_total >= iter_cap(sd) || !ok ||
+            (pcg_like && rn <= sd.ru_delta * s.rho_ref)) {
+            // gamma and alpha of the direction in use stay the reference for the
+            // continuation after the residual replacement
+            to_res(s, pcg_like && ok ? 1 : 0);
             break;
         }
         s.beta = beta;
@@ -576,8 +596,9 @@ __device__ void advance(const SysDesc &sd, SysState &s, const double (&t)[NPART]
         double a = re / eq;
         if (!(eq > sd.dlsm_guard * ee * sd.diag_max) || !isfinite(a)) {
             s.dlsm_skipped++;
-            s.phase = PH_RESTART;          // back to the CG-type method
+            s.keep_dir = 0;
             s.reset_d = 0;
+            s.phase = PH_RESTART;
         } else {
             s.alpha_d = a;
             s.phase = PH_DLSM_UPD;
@@ -593,21 +614,22 @@ __device__ void advance(const SysDesc &sd, SysState &s, const double (&t)[NPART]
         s.rho = rr > 0.0 ? rr : 0.0;
         s.dlsm_count++;
         if (sd.mode == PPE_MODE_HYBRID && !s.fell_back && s.it_total >= sd.hybrid_budget) s.fell_back = 1;
-        if (sqrt(s.rho) <= s.tau) {
-            enter_inner_converged(s);
+        double rn = sqrt(s.rho);
+        if (rn <= s.target || s.it_total >= iter_cap(sd) || !isfinite(rn)) {
+            to_res(s, 0);
         } else if (s.dlsm_count < sd.num_dlsm && !s.fell_back) {
             s.phase = PH_NET;
         } else {
+            s.keep_dir = 0;
             s.reset_d = 0;
             s.phase = PH_RESTART;
         }
         break;
     }
-    case PH_FINAL1: {
+    case PH_FINAL1:
         s.xmean = t[1] / t[0];
         s.phase = PH_FINAL2;
         break;
-    }
     case PH_FINAL2:
         s.phase = PH_DONE;
         break;
@@ -616,126 +638,136 @@ __device__ void advance(const SysDesc &sd, SysState &s, const double (&t)[NPART]
     }
 }
 
-template <typename S> __device__ void copy_state_in(S &sm, const SolverArgs &a, int s)
-{
-    // state written by the finisher of the previous step: read through L2
-    const int32_t *src = reinterpret_cast<const int32_t *>(a.st + s);
-    int32_t *dst = reinterpret_cast<int32_t *>(&sm.st);
-    for (int k = threadIdx.x; k < (int)(sizeof(SysState) / 4); k += blockDim.x) dst[k] = ld_cg(src + k);
-    const int32_t *dsrc = reinterpret_cast<const int32_t *>(a.sys + s);
-    int32_t *ddst = reinterpret_cast<int32_t *>(&sm.sd);
-    for (int k = threadIdx.x; k < (int)(sizeof(SysDesc) / 4); k += blockDim.x) ddst[k] = dsrc[k];
-}
-
 template <typename T, typename S>
-__device__ void finisher(S &sm, const SolverArgs &a, bool resume_net)
+__device__ void run_pass(S &sm, int q, int ph, int t, double (&acc)[NPART])
 {
-    bool any_active = false, any_net = false;
-    for (int s = 0; s < a.nsys; ++s) {
-        __syncthreads();
-        copy_state_in(sm, a, s);
-        __syncthreads();
-        int ph = sm.st.phase;
-        if (ph == PH_DONE || (ph == PH_NET && !resume_net)) {
-            if (ph == PH_NET) any_net = true;
-            continue;
-        }
-        double tot[NPART];
-        reduce_system(sm, a.partials, sm.sd.tile0, sm.sd.ntiles, tot);
-        if (threadIdx.x == 0) {
-            SysState st = sm.st;
-            advance(sm.sd, st, tot, resume_net);
-            int32_t *dst = reinterpret_cast<int32_t *>(a.st + s);
-            const int32_t *src = reinterpret_cast<const int32_t *>(&st);
-            for (int k = 0; k < (int)(sizeof(SysState) / 4); ++k) dst[k] = src[k];
-            sm.st = st;
-        }
-        __syncthreads();
-        int nph = sm.st.phase;
-        if (nph == PH_NET) any_net = true;
-        else if (nph != PH_DONE) any_active = true;
+    const SysDesc &sd = sm.sd[q];
+    const SysState &st = sm.st[q];
+    int lt = t - sd.tile0;
+    int i0 = (lt % sd.tiles_x) * TILE_X, j0 = (lt / sd.tiles_x) * TILE_Y;
+    switch (ph) {
+    case PH_INIT: pass_init<T>(sm, sd, i0, j0, acc); break;
+    case PH_RES: pass_res<T>(sm, sd, st, i0, j0, acc); break;
+    case PH_RESTART: pass_restart<T>(sm, sd, st, i0, j0, acc); break;
+    case PH_ITER: pass_iter<T>(sm, sd, st, i0, j0, acc); break;
+    case PH_DLSM_DOT: pass_dlsm<T, S, false>(sm, sd, st, i0, j0, acc); break;
+    case PH_DLSM_UPD: pass_dlsm<T, S, true>(sm, sd, st, i0, j0, acc); break;
+    case PH_FINAL1: pass_final1<T>(sm, sd, st, i0, j0, acc); break;
+    case PH_FINAL2: pass_final2<T>(sm, sd, st, i0, j0, acc); break;
+    default: break;
     }
-    if (threadIdx.x == 0) {
-        a.ctl->exit_kernel = any_active ? 0 : 1;
-        a.ctl->any_net = any_net ? 1 : 0;
-    }
-}
-
-// Grid-wide barrier; the last block to arrive runs the finisher.  Waits are
-// bounded: on expiry the block records PPE_ERR_TIMEOUT and the kernel ends.
-template <typename T, typename S>
-__device__ bool barrier_and_finish(S &sm, const SolverArgs &a, bool resume_net)
-{
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t gen = ld_acquire_u32(&a.ctl->bar_gen);
-        __threadfence();
-        uint32_t prev = atomicAdd(&a.ctl->bar_count, 1u);
-        sm.last = (prev == gridDim.x - 1) ? 1 : 0;
-        sm.gen = gen;
-    }
-    __syncthreads();
-    if (sm.last) {
-        __threadfence();
-        finisher<T>(sm, a, resume_net);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            a.ctl->bar_count = 0;
-            __threadfence();
-            st_release_u32(&a.ctl->bar_gen, sm.gen + 1);
-        }
-    } else if (threadIdx.x == 0) {
-        uint64_t t0 = globaltimer_ns();
-        while (ld_acquire_u32(&a.ctl->bar_gen) == sm.gen) {
-            if ((int64_t)(globaltimer_ns() - t0) > a.spin_limit_ns) {
-                atomicExch(&a.ctl->err, (int32_t)PPE_ERR_TIMEOUT);
-                break;
-            }
-            __nanosleep(32);
-        }
-        __threadfence();
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int32_t err = ld_cg(&a.ctl->err);
-        int32_t ex = ld_cg(&a.ctl->exit_kernel);
-        sm.go = (err == 0 && ex == 0) ? 1 : 0;
-    }
-    __syncthreads();
-    return sm.go != 0;
 }
 
 template <typename T>
-__global__ void __launch_bounds__(SOLVER_THREADS, 1) solver_kernel(SolverArgs a, int resume_net)
+__global__ void __launch_bounds__(SOLVER_THREADS) solver_kernel(SolverArgs a, int resume_net)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SmemT<T> &sm = *reinterpret_cast<SmemT<T> *>(smem_raw);
-    bool resume = resume_net != 0;
-    for (int step = 0;; ++step) {
-        for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
-            int s = a.tile_sys[t];
+    const BlockRange br = a.ranges[blockIdx.x];
+    const int nq = br.s1 - br.s0 + 1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // per-system description and state of the systems this block works on
+    for (int q = 0; q < nq; ++q) {
+        const int32_t *dsrc = reinterpret_cast<const int32_t *>(a.sys + br.s0 + q);
+        int32_t *ddst = reinterpret_cast<int32_t *>(&sm.sd[q]);
+        for (int k = threadIdx.x; k < (int)(sizeof(SysDesc) / 4); k += blockDim.x) ddst[k] = dsrc[k];
+        const int32_t *ssrc = reinterpret_cast<const int32_t *>(a.st + br.s0 + q);
+        int32_t *sdst = reinterpret_cast<int32_t *>(&sm.st[q]);
+        for (int k = threadIdx.x; k < (int)(sizeof(SysState) / 4); k += blockDim.x) sdst[k] = ld_cg(ssrc + k);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && resume_net)
+        for (int q = 0; q < nq; ++q)
+            if (sm.st[q].phase == PH_NET) sm.st[q].phase = PH_DLSM_DOT;
+    __syncthreads();
+    int dec = 0;   // systems this block owns that stopped needing passes
+    int retired_seen[2] = {0, 0};
+    for (unsigned step = 1;; ++step) {
+        for (int q = 0; q < nq; ++q) {
+            const SysDesc &sd = sm.sd[q];
+            const int ph = sm.st[q].phase;
+            if (!is_pass_phase(ph)) continue;
+            double acc[NPART] = {0, 0, 0, 0, 0, 0};
+            int lo = max(br.t0, sd.tile0), hi = min(br.t1, sd.tile0 + sd.ntiles);
+            for (int t = lo; t < hi; ++t) run_pass<T>(sm, q, ph, t, acc);
+            if (lane == 0)
+#pragma unroll
+                for (int k = 0; k < NPART; ++k) sm.red[k][warp] = acc[k];
             __syncthreads();
-            copy_state_in(sm, a, s);
-            __syncthreads();
-            int ph = sm.st.phase;
-            if (ph == PH_NET && resume) ph = PH_DLSM_DOT;
-            int lt = t - sm.sd.tile0;
-            int i0 = (lt % sm.sd.tiles_x) * TILE_X, j0 = (lt / sm.sd.tiles_x) * TILE_Y;
-            double *out = a.partials + (size_t)t * NPART;
-            switch (ph) {
-            case PH_INIT: pass_init<T>(sm, i0, j0, out); break;
-            case PH_RES: pass_res<T>(sm, i0, j0, out); break;
-            case PH_RESTART: pass_restart<T>(sm, i0, j0, out); break;
-            case PH_ITER: pass_iter<T>(sm, i0, j0, out); break;
-            case PH_DLSM_DOT: pass_dlsm_dot<T>(sm, i0, j0, out); break;
-            case PH_DLSM_UPD: pass_dlsm_upd<T>(sm, i0, j0, out); break;
-            case PH_FINAL1: pass_final1<T>(sm, i0, j0, out); break;
-            case PH_FINAL2: pass_final2<T>(sm, i0, j0, out); break;
-            default: break;
+            if (threadIdx.x < NPART) {
+                double s = 0.0;
+                for (int w = 0; w < NWARP; ++w) s += sm.red[threadIdx.x][w];
+                a.partials[(size_t)(sd.part0 + (blockIdx.x - sd.blk0)) * NPART + threadIdx.x] = s;
             }
+            __syncthreads();
         }
-        if (!barrier_and_finish<T>(sm, a, resume)) break;
-        resume = false;
+        // grid barrier: publish retirements, arrive, wait for all blocks
+        if (threadIdx.x == 0) {
+            const int par = step & 1;
+            if (dec) atomicAdd(&a.ctl->retired[par], dec);
+            dec = 0;
+            __threadfence();
+            atomicAdd(&a.ctl->arrive, 1ull);
+            const unsigned long long need = (unsigned long long)step * gridDim.x;
+            uint64_t t0 = globaltimer_ns();
+            int go = 1;
+            while (ld_acquire_u64(&a.ctl->arrive) < need) {
+                if ((int64_t)(globaltimer_ns() - t0) > a.spin_limit_ns) {
+                    atomicExch(&a.ctl->err, (int32_t)PPE_ERR_TIMEOUT);
+                    go = 0;
+                    break;
+                }
+                __nanosleep(20);
+            }
+            __threadfence();
+            if (go && ld_cg(&a.ctl->err) != 0) go = 0;
+            int now = ld_cg(&a.ctl->retired[par]);
+            retired_seen[par] = now;
+            sm.live = (a.ctl->active0 - now - retired_seen[par ^ 1]) > 0 ? 1 : 0;
+            sm.go = go;
+        }
+        __syncthreads();
+        if (!sm.go) return;                               // timeout: states are not written back
+        if (!sm.live) break;
+        // advance every system this block works on (identically in every block)
+        for (int q = 0; q < nq; ++q) {
+            const SysDesc &sd = sm.sd[q];
+            if (!is_pass_phase(sm.st[q].phase)) continue;
+            double v[NPART] = {0, 0, 0, 0, 0, 0};
+            for (int b = threadIdx.x; b < sd.nparts; b += blockDim.x) {
+                const double *p = a.partials + (size_t)(sd.part0 + b) * NPART;
+#pragma unroll
+                for (int k = 0; k < NPART; ++k) v[k] += ld_cg(p + k);
+            }
+#pragma unroll
+            for (int k = 0; k < NPART; ++k) {
+                double x = v[k];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+                if (lane == 0) sm.red[k][warp] = x;
+            }
+            __syncthreads();
+            if (threadIdx.x < NPART) {
+                double s = 0.0;
+                for (int w = 0; w < NWARP; ++w) s += sm.red[threadIdx.x][w];
+                sm.tot[threadIdx.x] = s;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double tt[NPART];
+                for (int k = 0; k < NPART; ++k) tt[k] = sm.tot[k];
+                advance(sd, sm.st[q], tt);
+                if (!is_pass_phase(sm.st[q].phase) && (int)blockIdx.x == sd.blk0) ++dec;
+            }
+            __syncthreads();
+        }
+    }
+    // write back the states of the systems this block owns
+    for (int q = 0; q < nq; ++q) {
+        if ((int)blockIdx.x != sm.sd[q].blk0) continue;
+        const int32_t *src = reinterpret_cast<const int32_t *>(&sm.st[q]);
+        int32_t *dst = reinterpret_cast<int32_t *>(a.st + br.s0 + q);
+        for (int k = threadIdx.x; k < (int)(sizeof(SysState) / 4); k += blockDim.x) dst[k] = src[k];
     }
 }
 
