@@ -1,7 +1,402 @@
-// tcgen05 implicit-GEMM 3x3 convolution (placeholder until the kernel lands).
+// tcgen05 implicit-GEMM 3x3 convolution for sm_103a (the Mesh-Convs of the
+// DeepONet branch, Sec. 2.4).
+//
+// GEMM view of one CTA: M = 128 output pixels (a TW x TH patch of one image),
+// N = a slice of the output channels, K = 9 taps x Cin input channels.
+// For every (tap, channel block) the A tile is a TMA box load of the NHWC
+// activation tensor at the tap's shifted coordinates; coordinates outside the
+// image are zero-filled by the TMA unit, which is exactly the convolution's
+// zero padding.  The B tile is a TMA box load of the packed weights
+// [Cout][9*Cin] (K-major).  Both land in shared memory in the swizzled
+// K-major layout the tensor cores read; one elected thread issues
+// tcgen05.mma (BF16 x BF16 -> FP32) into a TMEM accumulator, and the four
+// warps read it back with tcgen05.ld for the fused epilogue (bias, GELU,
+// per-pixel Mesh-Conv weight of the consumer layer, BF16 stores).
+//
+// The input tensor arrives already multiplied by this layer's eta (the
+// producing kernel applies it), so the A operand is loaded as is.
+//
+// Every wait is bounded: on expiry the CTA records an error flag, skips the
+// remaining work, frees its TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 #include "net_internal.h"
+#include "net_kernels.cuh"
 
 namespace ppe {
-bool conv3x3_tc_supported(const ConvArgs &) { return false; }
-ppe_status conv3x3_tc(const ConvArgs &, cudaStream_t) { return PPE_ERR_ARG; }
+
+namespace {
+
+constexpr int TC_M = 128;
+constexpr int TC_MAX_STAGES = 8;
+constexpr long long TC_WAIT_NS = 1000000000LL;   // 1 s bound on every wait
+
+struct TcArgs {
+    int B, H, W, cin, cout, n_tile, tw, th, tiles_x, tiles_y, kblocks, stages, tmem_cols;
+    const float *bias;
+    Epi epi;
+    int *err;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t gtimer()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait; returns false (and raises the error flag) on expiry.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err)
+{
+    if (mbar_try(bar, parity)) return true;
+    uint64_t t0 = gtimer();
+    while (!mbar_try(bar, parity)) {
+        if ((long long)(gtimer() - t0) > TC_WAIT_NS) {
+            atomicExch(err, 1);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, uint32_t bar, int c0, int c1, int c2,
+                                            int c3)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6}], "
+        "[%2];" ::"r"(dst),
+        "l"((uint64_t)map), "r"(bar), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, uint32_t bar, int c0, int c1)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+            dst),
+        "l"((uint64_t)map), "r"(bar), "r"(c0), "r"(c1)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major operand in the swizzled
+// canonical layout: rows of SW bytes, 8-row atoms of 8*SW bytes.
+template <int SW> __device__ __forceinline__ uint64_t smem_desc(uint32_t addr)
+{
+    constexpr uint64_t layout = SW == 128 ? 2ull : (SW == 64 ? 4ull : 6ull);
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);            // start address
+    d |= (uint64_t)1 << 16;                              // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)((8 * SW) >> 4) << 32;                // stride byte offset: one 8-row atom
+    d |= (uint64_t)1 << 46;                              // descriptor version
+    d |= layout << 61;                                   // swizzle mode
+    return d;
+}
+
+// kind::f16 instruction descriptor: BF16 x BF16 -> FP32, both K-major.
+__device__ __forceinline__ uint32_t instr_desc(int n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int BK>
+__global__ void __launch_bounds__(128, 1)
+    conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs a)
+{
+    constexpr int SW = BK * 2;                 // swizzle span = row bytes
+    constexpr uint32_t A_BYTES = TC_M * BK * 2;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    const uint32_t b_bytes = (uint32_t)a.n_tile * BK * 2;
+    const uint32_t tx_bytes = A_BYTES + b_bytes;                      // bytes landed per stage
+    const uint32_t stage_bytes = (tx_bytes + 1023u) & ~1023u;         // 1024-aligned stage stride
+    const uint32_t bar0 = base + stage_bytes * a.stages;      // full[8], empty[8], acc
+    const uint32_t full0 = bar0, empty0 = bar0 + 8 * TC_MAX_STAGES, accb = bar0 + 16 * TC_MAX_STAGES;
+    const uint32_t tslot = accb + 8;
+    unsigned char *gbase = smem_raw + (base - raw);
+    uint32_t *tslot_ptr = reinterpret_cast<uint32_t *>(gbase + (tslot - base));
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tile = blockIdx.x % (a.tiles_x * a.tiles_y), img = blockIdx.x / (a.tiles_x * a.tiles_y);
+    const int x0 = (tile % a.tiles_x) * a.tw, y0 = (tile / a.tiles_x) * a.th;
+    const int n0 = blockIdx.y * a.n_tile;
+    const int cblocks = a.cin / BK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < a.stages; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        mbar_init(accb, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tslot),
+                     "r"(a.tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot_ptr;
+
+    if (warp == 0 && lane == 0) {
+        // producer: TMA loads of the A (activation) and B (weight) tiles
+        bool ok = true;
+        int armed = 0;
+        for (int kb = 0; kb < a.kblocks && ok; ++kb) {
+            int s = kb % a.stages;
+            uint32_t ph = (kb / a.stages) & 1;
+            ok = mbar_wait(empty0 + 8 * s, ph ^ 1, a.err);
+            if (!ok) break;
+            int tap = kb / cblocks, c0 = (kb % cblocks) * BK;
+            int ky = tap / 3, kx = tap % 3;
+            uint32_t sa = base + stage_bytes * s, sb = sa + A_BYTES;
+            mbar_expect_tx(full0 + 8 * s, tx_bytes);
+            tma_load_4d(sa, &tmA, full0 + 8 * s, c0, x0 + kx - 1, y0 + ky - 1, img);
+            tma_load_2d(sb, &tmB, full0 + 8 * s, tap * a.cin + c0, n0);
+            armed = kb + 1;
+        }
+        if (!ok) {
+            // let copies already in flight land before the CTA leaves
+            for (int kb = (armed > a.stages ? armed - a.stages : 0); kb < armed; ++kb)
+                mbar_wait(full0 + 8 * (kb % a.stages), (kb / a.stages) & 1, a.err);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        const uint32_t idesc = instr_desc(a.n_tile);
+        bool ok = true;
+        for (int kb = 0; kb < a.kblocks; ++kb) {
+            int s = kb % a.stages;
+            uint32_t ph = (kb / a.stages) & 1;
+            ok = mbar_wait(full0 + 8 * s, ph, a.err);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            uint32_t sa = base + stage_bytes * s, sb = sa + A_BYTES;
+#pragma unroll
+            for (int k = 0; k < BK / 16; ++k)
+                mma_bf16(tmem, smem_desc<SW>(sa + 32 * k), smem_desc<SW>(sb + 32 * k), idesc, (kb | k) != 0);
+            mma_commit(empty0 + 8 * s);
+        }
+        mma_commit(accb);     // arrives once every MMA issued above has completed
+    }
+    __syncwarp();
+    // epilogue: thread (warp w, lane l) owns TMEM lane / output pixel 32 w + l
+    bool ok = mbar_wait(accb, 0, a.err);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int m = threadIdx.x;
+    const int px = x0 + m % a.tw, py = y0 + m / a.tw;
+    const bool valid = ok && px < a.W && py < a.H && *((volatile int *)a.err) == 0;
+    const size_t p = ((size_t)img * a.H + py) * a.W + px;
+    const int q = py * a.W + px;
+    for (int c = 0; c < a.n_tile; c += 16) {
+        float v[16];
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+        if (valid) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                int co = n0 + c + i;
+                float z = v[i] + (a.bias ? a.bias[co] : 0.f);
+                epi_store(a.epi, z, p, q, co, a.cout);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaDriverEntryPointQueryResult q;
+        void *p = nullptr;
+        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    });
+    return fn;
+}
+
+int *err_flag()
+{
+    static int *flag = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        if (cudaMalloc(&flag, sizeof(int)) == cudaSuccess) cudaMemset(flag, 0, sizeof(int));
+    });
+    return flag;
+}
+
+int pick_bk(int cin) { return cin % 64 == 0 ? 64 : (cin % 32 == 0 ? 32 : 16); }
+
+}  // namespace
+
+bool conv3x3_tc_supported(const ConvArgs &a)
+{
+    return a.cin % 16 == 0 && a.cout % 16 == 0 && a.cin >= 16 && a.cout >= 16 && a.H >= 1 && a.W >= 1 &&
+           a.B >= 1 && encode_fn() != nullptr;
+}
+
+ppe_status conv3x3_tc(const ConvArgs &a, cudaStream_t s)
+{
+    if (!conv3x3_tc_supported(a)) {
+        set_error("conv3x3_tc: unsupported shape");
+        return PPE_ERR_ARG;
+    }
+    auto encode = encode_fn();
+    int *err = err_flag();
+    if (!err) return cuda_status(cudaErrorMemoryAllocation, "conv3x3_tc error flag");
+    const int bk = pick_bk(a.cin);
+    // output patch of 128 pixels: TW x TH with TW a power of two <= 128
+    int tw = 8;
+    while (tw < a.W && tw < TC_M) tw *= 2;
+    int th = TC_M / tw;
+    // output-channel slice: the whole of Cout when it fits one MMA (<= 256)
+    int n_tile = a.cout;
+    while (n_tile > 256) n_tile /= 2;
+    if (a.cout % n_tile) n_tile = 16;
+    int tmem_cols = 32;
+    while (tmem_cols < n_tile) tmem_cols *= 2;
+    const int stage_bytes = ((TC_M + n_tile) * bk * 2 + 1023) / 1024 * 1024;
+    int stages = std::min(TC_MAX_STAGES, (200 * 1024) / stage_bytes);
+    if (stages < 2) stages = 2;
+    const size_t smem = (size_t)stage_bytes * stages + 1024 + 16 * TC_MAX_STAGES + 64;
+
+    CUtensorMap mA, mB;
+    CUtensorMapSwizzle sw = bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                     : (bk == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B);
+    {
+        cuuint64_t dims[4] = {(cuuint64_t)a.cin, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)a.B};
+        cuuint64_t strides[3] = {(cuuint64_t)a.cin * 2, (cuuint64_t)a.W * a.cin * 2, (cuuint64_t)a.H * a.W * a.cin * 2};
+        cuuint32_t box[4] = {(cuuint32_t)bk, (cuuint32_t)tw, (cuuint32_t)th, 1};
+        cuuint32_t es[4] = {1, 1, 1, 1};
+        CUresult r = encode(&mA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void *)a.in, dims, strides, box, es,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+            set_error("cuTensorMapEncodeTiled(activations) failed");
+            return PPE_ERR_CUDA;
+        }
+    }
+    {
+        cuuint64_t dims[2] = {(cuuint64_t)9 * a.cin, (cuuint64_t)a.cout};
+        cuuint64_t strides[1] = {(cuuint64_t)9 * a.cin * 2};
+        cuuint32_t box[2] = {(cuuint32_t)bk, (cuuint32_t)n_tile};
+        cuuint32_t es[2] = {1, 1};
+        CUresult r = encode(&mB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)a.w, dims, strides, box, es,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+            set_error("cuTensorMapEncodeTiled(weights) failed");
+            return PPE_ERR_CUDA;
+        }
+    }
+    TcArgs t;
+    t.B = a.B; t.H = a.H; t.W = a.W; t.cin = a.cin; t.cout = a.cout; t.n_tile = n_tile;
+    t.tw = tw; t.th = th;
+    t.tiles_x = (a.W + tw - 1) / tw;
+    t.tiles_y = (a.H + th - 1) / th;
+    t.kblocks = 9 * (a.cin / bk);
+    t.stages = stages;
+    t.tmem_cols = tmem_cols;
+    t.bias = a.bias;
+    t.epi = a.epi;
+    t.err = err;
+    dim3 grid(t.tiles_x * t.tiles_y * a.B, a.cout / n_tile);
+    cudaError_t e;
+    if (bk == 64) {
+        cudaFuncSetAttribute(conv_tc_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        conv_tc_kernel<64><<<grid, 128, smem, s>>>(mA, mB, t);
+    } else if (bk == 32) {
+        cudaFuncSetAttribute(conv_tc_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        conv_tc_kernel<32><<<grid, 128, smem, s>>>(mA, mB, t);
+    } else {
+        cudaFuncSetAttribute(conv_tc_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        conv_tc_kernel<16><<<grid, 128, smem, s>>>(mA, mB, t);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_status(e, "conv_tc_kernel launch");
+    return PPE_OK;
+}
+
+// Error flag raised by a tensor-core kernel whose bounded wait expired.
+int conv_tc_error()
+{
+    int *f = err_flag();
+    int v = 0;
+    if (f) cudaMemcpy(&v, f, sizeof(int), cudaMemcpyDeviceToHost);
+    return v;
+}
+
 }  // namespace ppe

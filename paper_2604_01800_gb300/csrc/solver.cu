@@ -145,13 +145,16 @@ __device__ __forceinline__ bool in_ring1(int wi, int wj) { return wi >= 1 && wi 
 // Warp-reduce the thread's tile sums and add them to lane 0's FP64 totals.
 template <typename T> __device__ __forceinline__ void warp_accumulate(const T (&t)[NPART], double (&acc)[NPART])
 {
+    T v[NPART];
 #pragma unroll
     for (int q = 0; q < NPART; ++q) {
-        T v = t[q];
+        v[q] = t[q];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        acc[q] += (double)v;
+        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
     }
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int q = 0; q < NPART; ++q) acc[q] += (double)v[q];
 }
 
 // ---------------------------------------------------------------------------
@@ -254,6 +257,8 @@ __device__ void pass_restart(S &sm, const SysDesc &sd, const SysState &st, int i
     const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
     int j = j0 + ty, wj = ty + 2;
     T *dd = (T *)sd.d;
+    const T *pv = (const T *)sd.p;
+    const T *sv = (const T *)sd.s[st.cur];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
         int i = i0 + tx + 32 * c, wi = tx + 32 * c + 2;
@@ -261,6 +266,11 @@ __device__ void pass_restart(S &sm, const SysDesc &sd, const SysState &st, int i
             int k = wj * WX + wi;
             T w = stencil<T>(cf, U, wi, wj);
             t[0] += R[k] * U[k]; t[1] += w * U[k]; t[2] += R[k] * R[k]; t[3] += R[k];
+            if (st.keep_dir) {   // continuation after a residual replacement: u.s and p.s of the kept direction
+                size_t gi = (size_t)j * sd.pitch + i;
+                T so = ld_cg(sv + gi);
+                t[4] += U[k] * so; t[5] += ld_cg(pv + gi) * so;
+            }
             if (st.reset_d) {
                 size_t gi = (size_t)j * sd.pitch + i;
                 if (st.fold_d) sd.x[(size_t)j * sd.nx + i] += (double)ld_cg(dd + gi);
@@ -357,6 +367,7 @@ __device__ void pass_iter(S &sm, const SysDesc &sd, const SysState &st, int i0, 
             rout[gi] = rn;
             T wn = stencil<T>(cf, Un, wi, wj0);
             t[0] += rn * un; t[1] += wn * un; t[2] += rn * rn; t[3] += rn;
+            t[4] += un * Sn[k]; t[5] += pn * Sn[k];
         }
     }
     warp_accumulate(t, acc);
@@ -524,25 +535,28 @@ __device__ void advance(const SysDesc &sd, SysState &s, const double (&t)[NPART]
         break;
     }
     case PH_RESTART: {
-        s.mu = t[3] / N;
-        double rr = t[2] - N * s.mu * s.mu;
+        // this pass summed r - mu; its mean is the further correction
+        double dmu = t[3] / N;
+        s.mu += dmu;
+        double rr = t[2] - N * dmu * dmu;
         s.rho = rr > 0.0 ? rr : 0.0;
         s.reset_d = 0;
         s.fold_d = 0;
         s.has_d = 1;
         s.cg_count = 0;
-        if (sqrt(s.rho) <= s.target || !(t[1] > 0.0) || !(t[0] > 0.0)) {
+        if (s.rho <= s.target * s.target || !(t[1] > 0.0) || !(t[0] > 0.0)) {
             to_res(s, 0);
             break;
         }
-        bool cont = s.keep_dir && s.gamma > 0.0 && s.alpha > 0.0;
+        bool cont = s.keep_dir && s.gamma > 0.0;
         if (cont) {
+            // p' = u + beta p: p'.A p' = u.Au + 2 beta u.(Ap) + beta^2 p.(Ap)
             double beta = t[0] / s.gamma;
-            double denom = t[1] - beta * t[0] / s.alpha;
-            cont = denom > 0.0 && isfinite(beta);
+            double pap = t[1] + beta * (2.0 * t[4] + beta * t[5]);
+            cont = pap > 0.0 && isfinite(beta);
             if (cont) {
                 s.beta = beta;
-                s.alpha = t[0] / denom;
+                s.alpha = t[0] / pap;
                 s.first = 0;
             }
         }
@@ -566,14 +580,15 @@ __device__ void advance(const SysDesc &sd, SysState &s, const double (&t)[NPART]
         s.first = 0;
         s.cg_count++;
         if (sd.mode == PPE_MODE_HYBRID && !s.fell_back && s.it_total >= sd.hybrid_budget) s.fell_back = 1;
-        double rn = sqrt(s.rho);
-        if (!isfinite(rn)) { to_res(s, 0); break; }
+        const double rho = s.rho;
+        if (!isfinite(rho)) { to_res(s, 0); break; }
         double gnew = t[0];
         double beta = gnew / s.gamma;
-        double denom = t[1] - beta * gnew / s.alpha;
+        // next direction p' = u' + beta p: p'.A p' = u'.Au' + 2 beta u'.(Ap) + beta^2 p.(Ap)
+        double denom = t[1] + beta * (2.0 * t[4] + beta * t[5]);
         bool ok = denom > 0.0 && isfinite(beta) && gnew > 0.0;
-        if (rn <= s.target || s.it_total >= iter_cap(sd) || !ok ||
-            (pcg_like && rn <= sd.ru_delta * s.rho_ref)) {
+        const double ru = sd.ru_delta * s.rho_ref;
+        if (rho <= s.target * s.target || s.it_total >= iter_cap(sd) || !ok || (pcg_like && rho <= ru * ru)) {
             // gamma and alpha of the direction in use stay the reference for the
             // continuation after the residual replacement
             to_res(s, pcg_like && ok ? 1 : 0);
@@ -614,8 +629,7 @@ __device__ void advance(const SysDesc &sd, SysState &s, const double (&t)[NPART]
         s.rho = rr > 0.0 ? rr : 0.0;
         s.dlsm_count++;
         if (sd.mode == PPE_MODE_HYBRID && !s.fell_back && s.it_total >= sd.hybrid_budget) s.fell_back = 1;
-        double rn = sqrt(s.rho);
-        if (rn <= s.target || s.it_total >= iter_cap(sd) || !isfinite(rn)) {
+        if (s.rho <= s.target * s.target || s.it_total >= iter_cap(sd) || !isfinite(s.rho)) {
             to_res(s, 0);
         } else if (s.dlsm_count < sd.num_dlsm && !s.fell_back) {
             s.phase = PH_NET;
@@ -733,24 +747,19 @@ __global__ void __launch_bounds__(SOLVER_THREADS) solver_kernel(SolverArgs a, in
         for (int q = 0; q < nq; ++q) {
             const SysDesc &sd = sm.sd[q];
             if (!is_pass_phase(sm.st[q].phase)) continue;
-            double v[NPART] = {0, 0, 0, 0, 0, 0};
-            for (int b = threadIdx.x; b < sd.nparts; b += blockDim.x) {
-                const double *p = a.partials + (size_t)(sd.part0 + b) * NPART;
+            if (warp == 0) {
+                double v[NPART] = {0, 0, 0, 0, 0, 0};
+                for (int b = lane; b < sd.nparts; b += 32) {
+                    const double *p = a.partials + (size_t)(sd.part0 + b) * NPART;
 #pragma unroll
-                for (int k = 0; k < NPART; ++k) v[k] += ld_cg(p + k);
-            }
+                    for (int k = 0; k < NPART; ++k) v[k] += ld_cg(p + k);
+                }
 #pragma unroll
-            for (int k = 0; k < NPART; ++k) {
-                double x = v[k];
+                for (int k = 0; k < NPART; ++k) {
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-                if (lane == 0) sm.red[k][warp] = x;
-            }
-            __syncthreads();
-            if (threadIdx.x < NPART) {
-                double s = 0.0;
-                for (int w = 0; w < NWARP; ++w) s += sm.red[threadIdx.x][w];
-                sm.tot[threadIdx.x] = s;
+                    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+                    if (lane == 0) sm.tot[k] = v[k];
+                }
             }
             __syncthreads();
             if (threadIdx.x == 0) {
