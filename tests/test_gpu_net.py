@@ -40,8 +40,8 @@ def _conv_case(api, B, H, W, cin, cout, impl, seed):
     b = g.standard_normal(cout).astype(np.float32)
     dx = torch.tensor(x, dtype=torch.bfloat16, device="cuda")
     dw = torch.tensor(w, dtype=torch.bfloat16, device="cuda")
-    db = torch.tensor(b, device="cuda")
-    out = torch.zeros(B, H, W, cout, device="cuda")
+    db = torch.tensor(b, dtype=torch.float32, device="cuda")
+    out = torch.zeros(B, H, W, cout, dtype=torch.float32, device="cuda")
     import ctypes
     L = api._lib.load()
     st = L.ppe_debug_conv3x3(ctypes.c_void_p(dx.data_ptr()), ctypes.c_void_p(dw.data_ptr()),
@@ -58,9 +58,11 @@ def _conv_case(api, B, H, W, cin, cout, impl, seed):
 
 
 @pytest.mark.parametrize("B,H,W,cin,cout", [(1, 16, 16, 16, 16), (2, 13, 21, 32, 48), (1, 8, 40, 64, 32),
-                                             (1, 32, 32, 256, 128)])
-def test_conv_simt_matches_oracle(api, B, H, W, cin, cout):
-    _conv_case(api, B, H, W, cin, cout, 1, 100 + H)
+                                             (1, 32, 32, 256, 128), (2, 64, 64, 64, 256), (1, 7, 9, 16, 16),
+                                             (3, 24, 40, 128, 64), (1, 256, 8, 32, 32)])
+@pytest.mark.parametrize("impl", [0, 1], ids=["tcgen05", "simt"])
+def test_conv_matches_oracle(api, B, H, W, cin, cout, impl):
+    _conv_case(api, B, H, W, cin, cout, impl, 100 + H)
 
 
 def _tiny_cfg():
@@ -92,7 +94,7 @@ def test_forward_matches_oracle(api, cfgname, nx, ny, B):
     R = g.standard_normal((B, ny, nx)).astype(np.float32)
     grid = api.ppe_create_grid(dx, dy)
     net.attach(grid)
-    r = torch.tensor(R, device="cuda")
+    r = torch.tensor(R, dtype=torch.float32, device="cuda")
     e = torch.zeros_like(r)
     net.infer(grid, r, e)
     torch.cuda.synchronize()

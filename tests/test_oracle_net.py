@@ -17,7 +17,6 @@ import oracle
 from oracle import net_oracle as N
 from paper_2604_01800_gb300 import inputs as I
 
-torch.set_default_dtype(torch.float64)
 
 CFG = I.NetConfig(widths=(4, 6, 8), c_last=5, trunk=(7, 9), phi_hidden=3)
 
@@ -78,15 +77,15 @@ def test_eta_is_one_for_zero_phi():
 
 def _torch_forward(P, dx, dy, R, mesh_conv=True):
     geo = N.Geometry(dx, dy, CFG.levels)
-    T = {k: torch.tensor(v.astype(np.float64), requires_grad=True) for k, v in P.items()}
+    T = {k: torch.tensor(v.astype(np.float64), dtype=torch.float64, requires_grad=True) for k, v in P.items()}
     H, W = geo.H, geo.W
-    x = torch.zeros(R.shape[0], 1, H, W)
-    x[:, 0, :geo.ny, :geo.nx] = torch.tensor(R)
-    maps = [torch.tensor(m) for m in geo.maps]
+    x = torch.zeros(R.shape[0], 1, H, W, dtype=torch.float64)
+    x[:, 0, :geo.ny, :geo.nx] = torch.tensor(R, dtype=torch.float64)
+    maps = [torch.tensor(m, dtype=torch.float64) for m in geo.maps]
 
     def eta(name, k):
         if not mesh_conv:
-            return torch.ones(maps[k].shape[1:])
+            return torch.ones(maps[k].shape[1:], dtype=torch.float64)
         D = maps[k].permute(1, 2, 0)                       # [H, W, 4]
         h = torch.tanh(F.linear(D, T[f"{name}.phi1.w"], T[f"{name}.phi1.b"]))
         phi = (h * T[f"{name}.phi2.w"]).sum(-1) + T[f"{name}.phi2.b"]
@@ -107,7 +106,8 @@ def _torch_forward(P, dx, dy, R, mesh_conv=True):
         x = torch.cat([x, skips[k]], 1)
         x = mconv(f"dec{k}b", k, mconv(f"dec{k}a", k, x))
     branch = F.conv2d(x, T["head.w"][:, :, None, None], T["head.b"])
-    xy = torch.stack(torch.meshgrid(torch.tensor(geo.yn), torch.tensor(geo.xn), indexing="ij")[::-1], -1)
+    xy = torch.stack(torch.meshgrid(torch.tensor(geo.yn, dtype=torch.float64), torch.tensor(geo.xn, dtype=torch.float64),
+                                   indexing="ij")[::-1], -1)
     t = xy
     depth = len(CFG.trunk) + 1
     for i in range(depth):
@@ -135,7 +135,8 @@ def test_conv_without_eta_is_library_conv():
     Wt = g.standard_normal((4, 3, 3, 3))
     b = g.standard_normal(4)
     Y = N.conv3x3(X, Wt, b)
-    Yt = F.conv2d(torch.tensor(X), torch.tensor(Wt), torch.tensor(b), padding=1).numpy()
+    Yt = F.conv2d(torch.tensor(X, dtype=torch.float64), torch.tensor(Wt, dtype=torch.float64),
+                  torch.tensor(b, dtype=torch.float64), padding=1).numpy()
     assert np.allclose(Y, Yt, rtol=1e-13, atol=1e-13)
 
 
@@ -148,8 +149,8 @@ def test_backward_matches_autograd(mesh_conv):
     R = I.rng(6).standard_normal((2, dy.size, dx.size))
     L, g = N.loss_and_grads(P, geo, A, R, CFG.widths, mesh_conv, len(CFG.trunk) + 1)
     et, T = _torch_forward(P, dx, dy, R, mesh_conv)
-    Ad = torch.tensor(A.dense())
-    res = torch.tensor(R).reshape(2, -1) - et.reshape(2, -1) @ Ad.T
+    Ad = torch.tensor(A.dense(), dtype=torch.float64)
+    res = torch.tensor(R, dtype=torch.float64).reshape(2, -1) - et.reshape(2, -1) @ Ad.T
     Lt = (res ** 2).mean()
     Lt.backward()
     assert abs(L - Lt.item()) <= 1e-12 * abs(L)
@@ -211,14 +212,14 @@ def test_sam_adam_step_matches_torch_optimizer():
         L0, Pcur, state = N.sam_adam_step(Pcur, state, geo, A, R, CFG.widths, hp, True, depth)
 
     # torch: SAM by hand around torch.optim.Adam with a cosine schedule
-    Ad = torch.tensor(A.dense())
-    T = {k: torch.tensor(v.astype(np.float64), requires_grad=True) for k, v in P.items()}
+    Ad = torch.tensor(A.dense(), dtype=torch.float64)
+    T = {k: torch.tensor(v.astype(np.float64), dtype=torch.float64, requires_grad=True) for k, v in P.items()}
     opt = torch.optim.Adam(T.values(), lr=hp["lr0"], betas=(hp["beta1"], hp["beta2"]), eps=hp["eps"])
     sched = torch.optim.lr_scheduler.CosineAnnealingLR(opt, T_max=hp["total"], eta_min=0.0)
 
     def loss_of(Pd):
         et, TT = _torch_forward(Pd, dx, dy, R)
-        res = torch.tensor(R).reshape(2, -1) - et.reshape(2, -1) @ Ad.T
+        res = torch.tensor(R, dtype=torch.float64).reshape(2, -1) - et.reshape(2, -1) @ Ad.T
         return (res ** 2).mean(), TT
 
     for _ in range(2):
