@@ -156,6 +156,18 @@ PPE_API ppe_status ppe_solve_batch(int n, ppe_grid *const *grids, const double *
                            ppe_precision precision, ppe_net *net, void *stream,
                            ppe_solve_info *info);
 
+/*
+ * Direction source for the DLSM steps in place of the network (validation
+ * with known directions, or a user's own predictor).  When set on a grid,
+ * hybrid solves on it call fn instead of the network: fn receives the
+ * normalised residual r_hat = (r - mean r) / ||r - mean r|| (device FP32
+ * [ny][nx], valid during the call) and must write the direction e (device
+ * FP32 [ny][nx]) in stream order on `stream` before returning.  fn = NULL
+ * removes the source.  The grid owns the two FP32 staging buffers.
+ */
+typedef void (*ppe_direction_fn)(void *user, const float *r_hat_dev, float *e_dev, int nx, int ny, void *stream);
+PPE_API ppe_status ppe_set_direction_source(ppe_grid *grid, ppe_direction_fn fn, void *user);
+
 /* Message describing the last failure on the calling thread ("" if none). */
 PPE_API const char *ppe_last_error(void);
 /* Library build identification, e.g. "ppe-gb300 sm_103a". */

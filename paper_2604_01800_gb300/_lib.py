@@ -45,6 +45,11 @@ class ppe_net_config(ctypes.Structure):
                 ("reserved", ctypes.c_int32 * 4)]
 
 
+# void (*)(void *user, const float *r_hat, float *e, int nx, int ny, void *stream)
+ppe_direction_fn = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                    ctypes.c_int, ctypes.c_void_p)
+
+
 class PPEError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -78,6 +83,7 @@ _SIGS = [
     ("net_infer_batch", ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P, _P]),
     ("ppe_debug_conv3x3", ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_int, _P, ctypes.c_int, _P]),
+    ("ppe_set_direction_source", ctypes.c_int, [_P, _P, _P]),
     ("ppe_last_error", ctypes.c_char_p, []),
     ("ppe_version", ctypes.c_char_p, []),
 ]

@@ -17,7 +17,7 @@ from ._lib import (PPE_MODE_HYBRID, PPE_MODE_PCG, PPE_PREC_FP64, PPE_PREC_MIXED,
                    ppe_solve_info, ppe_solve_opts)
 
 __all__ = ["Net", "net_create", "net_load", "net_default_config", "Grid", "ppe_create_grid", "ppe_destroy_grid", "ppe_apply", "ppe_solve", "ppe_solve_batch",
-           "ppe_set_options", "ppe_default_options", "PPE_MODE_PCG", "PPE_MODE_HYBRID", "PPE_PREC_FP64",
+           "ppe_set_options", "ppe_default_options", "ppe_set_direction_source", "PPE_MODE_PCG", "PPE_MODE_HYBRID", "PPE_PREC_FP64",
            "PPE_PREC_MIXED", "PPEError"]
 
 
@@ -91,6 +91,34 @@ def ppe_set_options(grid: Grid, opts: ppe_solve_opts | None = None, **kw):
         setattr(o, k, v)
     check(_lib.load().ppe_set_options(grid.handle, ctypes.byref(o)), "ppe_set_options")
     return o
+
+
+def ppe_set_direction_source(grid: Grid, fn):
+    """Install ``fn(r_hat, e, stream)`` (torch CUDA float32 tensors [ny, nx]
+    viewing the library's staging buffers) as the DLSM direction source of
+    ``grid``; ``None`` removes it."""
+    if fn is None:
+        grid._dir_cb = None
+        check(_lib.load().ppe_set_direction_source(grid.handle, None, None), "ppe_set_direction_source")
+        return
+
+    def tramp(user, r_ptr, e_ptr, nx, ny, stream_ptr):
+        n = nx * ny
+        r = _wrap_device(r_ptr, n).view(ny, nx)
+        e = _wrap_device(e_ptr, n).view(ny, nx)
+        fn(r, e, stream_ptr)
+
+    cb = _lib.ppe_direction_fn(tramp)
+    grid._dir_cb = cb                       # keep the trampoline alive
+    check(_lib.load().ppe_set_direction_source(grid.handle, ctypes.cast(cb, ctypes.c_void_p), None),
+          "ppe_set_direction_source")
+
+
+def _wrap_device(ptr, n):
+    """A float32 CUDA tensor viewing n elements at device address ptr."""
+    class _Iface:
+        __cuda_array_interface__ = {"shape": (n,), "typestr": "<f4", "data": (int(ptr), False), "version": 2}
+    return torch.as_tensor(_Iface(), device="cuda")
 
 
 def ppe_apply(grid: Grid, x: torch.Tensor, y: torch.Tensor, stream=None):

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -51,6 +52,28 @@ __global__ void apply_kernel(int nx, int ny, const double *__restrict__ dx, cons
 
 static int g_spin_limit_ms = 2000;
 
+// r_hat = (r - mu) / sqrt(rho) of a system's current residual, unpitched FP32.
+__global__ void rhat_kernel(const SysDesc *sd, const SysState *st, float *out)
+{
+    const int nx = sd->nx, ny = sd->ny;
+    const size_t n = (size_t)nx * ny;
+    const double scale = st->rho > 0.0 ? 1.0 / sqrt(st->rho) : 0.0;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+        size_t i = k % nx, j = k / nx, g = j * sd->pitch + i;
+        double v = sd->precision == PPE_PREC_FP64 ? ((const double *)sd->r[st->cur])[g]
+                                                  : (double)((const float *)sd->r[st->cur])[g];
+        out[k] = (float)((v - st->mu) * scale);
+    }
+}
+
+// e (pitched, solver layout) <- e_user (unpitched)
+__global__ void pitch_copy_kernel(const float *src, float *dst, int nx, int ny, int pitch)
+{
+    const size_t n = (size_t)nx * ny;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+        dst[(k / nx) * pitch + k % nx] = src[k];
+}
+
 }  // namespace ppe
 
 using namespace ppe;
@@ -82,6 +105,7 @@ void ppe_destroy_grid(ppe_grid *g)
     cudaFree(g->vec); cudaFree(g->e);
     cudaFree(g->sys_dev); cudaFree(g->st_dev); cudaFree(g->ranges_dev); cudaFree(g->partials_dev);
     cudaFree(g->ctl_dev);
+    cudaFree(g->dir_r); cudaFree(g->dir_e);
     delete g;
 }
 
@@ -181,6 +205,20 @@ ppe_status ppe_set_options(ppe_grid *g, const ppe_solve_opts *o)
         !(o->inner_rtol > 0.0 && o->inner_rtol < 1.0) || !(o->dlsm_guard >= 0.0) || o->blocks_per_sm < 0)
         return arg_error("ppe_set_options: option out of range");
     g->opts = *o;
+    return PPE_OK;
+}
+
+ppe_status ppe_set_direction_source(ppe_grid *g, ppe_direction_fn fn, void *user)
+{
+    clear_error();
+    if (!g) return arg_error("ppe_set_direction_source: NULL grid");
+    if (fn && !g->dir_r) {
+        size_t bytes = (size_t)g->nx * g->ny * sizeof(float);
+        PPE_CUDA_TRY(cudaMalloc(&g->dir_r, bytes));
+        PPE_CUDA_TRY(cudaMalloc(&g->dir_e, bytes));
+    }
+    g->dir_fn = fn;
+    g->dir_user = user;
     return PPE_OK;
 }
 
@@ -293,6 +331,12 @@ static ppe_status drive(int n, ppe_grid *const *grids, SysDesc *sys_dev, SysStat
     a.sys = sys_dev; a.st = st_dev; a.ranges = ranges_dev; a.partials = partials_dev; a.ctl = ctl_dev;
     a.nsys = n; a.ntiles = 0;
     a.spin_limit_ns = (int64_t)g_spin_limit_ms * 1000000LL;
+    a.prof = nullptr;
+    static const bool want_prof = std::getenv("PPE_SOLVER_PROFILE") != nullptr;
+    if (want_prof) {
+        PPE_CUDA_TRY(cudaMalloc(&a.prof, 4 * sizeof(unsigned long long)));
+        PPE_CUDA_TRY(cudaMemsetAsync(a.prof, 0, 4 * sizeof(unsigned long long), stream));
+    }
 
     cudaEvent_t ev0, ev1;
     PPE_CUDA_TRY(cudaEventCreate(&ev0));
@@ -323,16 +367,35 @@ static ppe_status drive(int n, ppe_grid *const *grids, SysDesc *sys_dev, SysStat
         active = 0;
         for (int s = 0; s < n; ++s) active += st[s].phase == PH_NET;
         if (!active) break;
-        if (!net) { set_error("hybrid solve without a network"); status = PPE_ERR_NO_NET; break; }
         float t = 0.f;
         for (int s = 0; s < n; ++s) {
             if (st[s].phase != PH_NET) continue;
-            ppe_status ns = net_direction(net, grids[s], sys_dev + s, st_dev + s, fp64, stream, &t);
+            ppe_grid *g = grids[s];
+            if (g->dir_fn) {
+                const int nb = (int)std::min<size_t>(1184, ((size_t)g->nx * g->ny + 255) / 256);
+                rhat_kernel<<<nb, 256, 0, stream>>>(sys_dev + s, st_dev + s, g->dir_r);
+                g->dir_fn(g->dir_user, g->dir_r, g->dir_e, g->nx, g->ny, (void *)stream);
+                pitch_copy_kernel<<<nb, 256, 0, stream>>>(g->dir_e, g->e, g->nx, g->ny, g->pitch);
+                cudaError_t ce = cudaGetLastError();
+                if (ce != cudaSuccess) { status = cuda_status(ce, "direction source"); break; }
+                continue;
+            }
+            if (!net) { set_error("hybrid solve without a network or direction source"); status = PPE_ERR_NO_NET; break; }
+            ppe_status ns = net_direction(net, g, sys_dev + s, st_dev + s, fp64, stream, &t);
             if (ns != PPE_OK) { status = ns; break; }
             ms_net += t;
         }
         if (status != PPE_OK) break;
         if (launches > 10000000) { status = PPE_ERR_NOT_CONVERGED; break; }
+    }
+    if (a.prof) {
+        unsigned long long pr[4] = {0, 0, 0, 0};
+        cudaMemcpyAsync(pr, a.prof, sizeof pr, cudaMemcpyDeviceToHost, stream);
+        cudaStreamSynchronize(stream);
+        double st_ = pr[3] ? (double)pr[3] : 1.0;
+        std::fprintf(stderr, "[solver profile] blocks=%d steps=%llu  per step: pass %.2f us, barrier %.2f us, advance %.2f us\n",
+                     blocks, pr[3], pr[0] / st_ / 1e3, pr[1] / st_ / 1e3, pr[2] / st_ / 1e3);
+        cudaFree(a.prof);
     }
     float ms = 0.f;
     cudaEventRecord(ev1, stream);
@@ -361,8 +424,9 @@ static ppe_status check_solve_args(ppe_grid *g, const double *rhs, double *x, do
     if (!(tol > 0.0) || !std::isfinite(tol)) return arg_error("ppe_solve: tol_rel must be positive");
     if (mode != PPE_MODE_PCG && mode != PPE_MODE_HYBRID) return arg_error("ppe_solve: bad mode");
     if (prec != PPE_PREC_FP64 && prec != PPE_PREC_MIXED) return arg_error("ppe_solve: bad precision");
+    if (mode == PPE_MODE_HYBRID && g->dir_fn) return PPE_OK;
     if (mode == PPE_MODE_HYBRID && !net) {
-        set_error("ppe_solve: hybrid mode needs a network");
+        set_error("ppe_solve: hybrid mode needs a network or a direction source");
         return PPE_ERR_NO_NET;
     }
     if (mode == PPE_MODE_HYBRID) return net_check_grid(net, g);

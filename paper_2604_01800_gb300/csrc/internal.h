@@ -110,6 +110,7 @@ struct SolverArgs {
     Control *ctl;
     int32_t nsys, ntiles;
     int64_t spin_limit_ns;
+    unsigned long long *prof;  // nullable: block 0 accumulates ns in pass / barrier / advance, and steps
 };
 
 ppe_status launch_solver_resume(const SolverArgs &a, bool fp64, int grid_blocks, cudaStream_t stream,
@@ -139,6 +140,9 @@ struct ppe_grid {
     int ranges_blocks = 0;
     double *partials_dev = nullptr;
     ppe::Control *ctl_dev = nullptr;
+    ppe_direction_fn dir_fn = nullptr;   // user direction source (replaces the network)
+    void *dir_user = nullptr;
+    float *dir_r = nullptr, *dir_e = nullptr;   // [ny][nx] staging for dir_fn
     void *net_cache = nullptr;           // per-network data for this grid (owned by the net)
     const void *net_owner = nullptr;
 };

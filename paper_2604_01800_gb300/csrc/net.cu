@@ -144,8 +144,10 @@ ppe_status net_alloc(ppe_net *n)
 // Re-pack BF16 conv weights from the FP32 master copy (active parameter set).
 ppe_status ensure_packed(ppe_net *n, const float *P, cudaStream_t s)
 {
-    uint64_t want = P == n->params ? n->version : ~0ull;
-    if (n->packed_version == want && n->packed_src == P) return PPE_OK;
+    // the master parameters are cached by version; any other set (the SAM
+    // perturbation) is packed every time
+    uint64_t want = P == n->params ? n->version : 0;
+    if (want && n->packed_version == want && n->packed_src == P) return PPE_OK;
     for (auto &l : n->layers)
         PPE_TRY(pack_conv_weights(P + l.off_w, n->wp + l.off_wp, n->wt + l.off_wt, l.cout, l.cin, s));
     n->packed_version = want;
@@ -345,8 +347,8 @@ ppe_status ensure_acts(ppe_net *n, NetCache *c, int B)
 // eta for every layer, trunk features, folded head (for parameters P).
 ppe_status refresh_cache(ppe_net *n, NetCache *c, const float *P, cudaStream_t s)
 {
-    uint64_t want = P == n->params ? n->version : ~0ull;
-    if (c->version == want && c->src == P) return PPE_OK;
+    uint64_t want = P == n->params ? n->version : 0;
+    if (want && c->version == want && c->src == P) return PPE_OK;
     const ppe_net_config &cf = n->cfg;
     for (size_t i = 0; i < n->layers.size(); ++i) {
         const ConvLayer &l = n->layers[i];

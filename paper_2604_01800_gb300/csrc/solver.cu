@@ -86,6 +86,7 @@ template <typename T> struct SmemT {
     SysDesc sd[SMAX];
     SysState st[SMAX];
     double tot[NPART];
+    double slot[SOLVER_THREADS][NPART];
     int32_t live;
     int32_t go;
 };
@@ -696,6 +697,8 @@ __global__ void __launch_bounds__(SOLVER_THREADS) solver_kernel(SolverArgs a, in
     __syncthreads();
     int dec = 0;   // systems this block owns that stopped needing passes
     int retired_seen[2] = {0, 0};
+    const bool prof = a.prof && blockIdx.x == 0 && threadIdx.x == 0;
+    uint64_t t_a = prof ? globaltimer_ns() : 0, t_b = 0, t_c = 0;
     for (unsigned step = 1;; ++step) {
         for (int q = 0; q < nq; ++q) {
             const SysDesc &sd = sm.sd[q];
@@ -716,6 +719,7 @@ __global__ void __launch_bounds__(SOLVER_THREADS) solver_kernel(SolverArgs a, in
             __syncthreads();
         }
         // grid barrier: publish retirements, arrive, wait for all blocks
+        if (prof) t_b = globaltimer_ns();
         if (threadIdx.x == 0) {
             const int par = step & 1;
             if (dec) atomicAdd(&a.ctl->retired[par], dec);
@@ -741,19 +745,30 @@ __global__ void __launch_bounds__(SOLVER_THREADS) solver_kernel(SolverArgs a, in
             sm.go = go;
         }
         __syncthreads();
+        if (prof) t_c = globaltimer_ns();
         if (!sm.go) return;                               // timeout: states are not written back
         if (!sm.live) break;
         // advance every system this block works on (identically in every block)
         for (int q = 0; q < nq; ++q) {
             const SysDesc &sd = sm.sd[q];
             if (!is_pass_phase(sm.st[q].phase)) continue;
-            if (warp == 0) {
-                double v[NPART] = {0, 0, 0, 0, 0, 0};
-                for (int b = lane; b < sd.nparts; b += 32) {
-                    const double *p = a.partials + (size_t)(sd.part0 + b) * NPART;
+            // one round of loads: thread b takes slot b (and b + blockDim ...)
+            double v[NPART] = {0, 0, 0, 0, 0, 0};
+            for (int b = threadIdx.x; b < sd.nparts; b += blockDim.x) {
+                const double *p = a.partials + (size_t)(sd.part0 + b) * NPART;
 #pragma unroll
-                    for (int k = 0; k < NPART; ++k) v[k] += ld_cg(p + k);
-                }
+                for (int k = 0; k < NPART; ++k) v[k] += ld_cg(p + k);
+            }
+#pragma unroll
+            for (int k = 0; k < NPART; ++k) sm.slot[threadIdx.x][k] = v[k];
+            __syncthreads();
+            if (warp == 0) {
+                const int nt = min((int)blockDim.x, sd.nparts);
+#pragma unroll
+                for (int k = 0; k < NPART; ++k) v[k] = 0.0;
+                for (int b = lane; b < nt; b += 32)
+#pragma unroll
+                    for (int k = 0; k < NPART; ++k) v[k] += sm.slot[b][k];
 #pragma unroll
                 for (int k = 0; k < NPART; ++k) {
 #pragma unroll
@@ -769,6 +784,14 @@ __global__ void __launch_bounds__(SOLVER_THREADS) solver_kernel(SolverArgs a, in
                 if (!is_pass_phase(sm.st[q].phase) && (int)blockIdx.x == sd.blk0) ++dec;
             }
             __syncthreads();
+        }
+        if (prof) {
+            uint64_t t_d = globaltimer_ns();
+            atomicAdd(&a.prof[0], (unsigned long long)(t_b - t_a));
+            atomicAdd(&a.prof[1], (unsigned long long)(t_c - t_b));
+            atomicAdd(&a.prof[2], (unsigned long long)(t_d - t_c));
+            atomicAdd(&a.prof[3], 1ull);
+            t_a = t_d;
         }
     }
     // write back the states of the systems this block owns
