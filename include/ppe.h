@@ -221,6 +221,37 @@ PPE_API ppe_status net_infer(ppe_net *net, ppe_grid *grid, const float *r_dev, f
 PPE_API ppe_status net_infer_batch(ppe_net *net, ppe_grid *grid, int batch, const float *r_dev, float *e_dev,
                                    void *stream);
 
+/* Training hyper-parameters (Sec. 2.4: Adam with SAM, cosine decay). */
+typedef struct {
+    double lr0;            /* initial learning rate (2e-4)                               */
+    int64_t total_steps;   /* length of the cosine schedule (steps)                      */
+    double rho;            /* SAM perturbation radius (2e-4); 0 disables SAM             */
+    double beta1, beta2;   /* Adam moment decay (0.9, 0.999)                             */
+    double eps;            /* Adam epsilon (1e-8)                                        */
+    int32_t reserved[8];
+} ppe_train_hparams;
+
+PPE_API void net_default_hparams(ppe_train_hparams *hp);
+/*
+ * One training step on a batch of `batch` right-hand sides R (device FP32
+ * [batch][ny][nx], each R made unit-norm by the caller, Eq. 14) on one grid:
+ * loss L = mean over the batch and the nx*ny cells of (R - A NN(R))^2 with
+ * A = -V M the volume-scaled operator (Eq. 18); gradient by the network's
+ * backward kernels; SAM perturbation w + rho g / ||g|| and a second
+ * gradient there; Adam update with learning rate
+ * 0.5 lr0 (1 + cos(pi t / total_steps)).  loss_out (host, nullable)
+ * receives L at the unperturbed weights; the call synchronises `stream`.
+ * The network must be attached to the grid.
+ */
+PPE_API ppe_status net_train_step(ppe_net *net, ppe_grid *grid, int batch, const float *R_dev,
+                                  const ppe_train_hparams *hp, void *stream, double *loss_out);
+/* Test hook: loss (Eq. 18) and its gradient at the current parameters
+ * (grad_host: nullable host FP32 array of net_param_count entries). */
+PPE_API ppe_status net_loss_grad(ppe_net *net, ppe_grid *grid, int batch, const float *R_dev, void *stream,
+                                 double *loss_out, float *grad_host);
+/* Number of optimiser steps taken (the t of the schedule). */
+PPE_API ppe_status net_get_step(const ppe_net *net, int64_t *step);
+
 /* Test hook: one 3x3 convolution (zero padding 1, no activation) of a BF16
  * NHWC input in_bf16 [B][H][W][cin] with packed BF16 weights
  * w_bf16 [cout][9][cin] (tap = 3*ky + kx) and FP32 bias [cout] (nullable);

@@ -50,6 +50,12 @@ ppe_direction_fn = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctyp
                                     ctypes.c_int, ctypes.c_void_p)
 
 
+class ppe_train_hparams(ctypes.Structure):
+    _fields_ = [("lr0", ctypes.c_double), ("total_steps", ctypes.c_int64), ("rho", ctypes.c_double),
+                ("beta1", ctypes.c_double), ("beta2", ctypes.c_double), ("eps", ctypes.c_double),
+                ("reserved", ctypes.c_int32 * 8)]
+
+
 class PPEError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -84,6 +90,11 @@ _SIGS = [
     ("ppe_debug_conv3x3", ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_int, _P, ctypes.c_int, _P]),
     ("ppe_set_direction_source", ctypes.c_int, [_P, _P, _P]),
+    ("net_default_hparams", None, [ctypes.POINTER(ppe_train_hparams)]),
+    ("net_train_step", ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.POINTER(ppe_train_hparams), _P,
+                                      ctypes.POINTER(ctypes.c_double)]),
+    ("net_loss_grad", ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P, ctypes.POINTER(ctypes.c_double), _P]),
+    ("net_get_step", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
     ("ppe_last_error", ctypes.c_char_p, []),
     ("ppe_version", ctypes.c_char_p, []),
 ]

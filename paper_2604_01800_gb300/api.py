@@ -220,12 +220,46 @@ class Net:
     def attach(self, grid: Grid):
         check(_lib.load().net_attach(self.handle, grid.handle), "net_attach")
 
+    def train_step(self, grid: Grid, R: torch.Tensor, hp=None, stream=None, **kw) -> float:
+        """One SAM + Adam step on the batch R [B, ny, nx] (float32, CUDA)."""
+        hp = hp if hp is not None else net_default_hparams(**kw)
+        n = grid.nx * grid.ny
+        b = R.numel() // n
+        loss = ctypes.c_double()
+        check(_lib.load().net_train_step(self.handle, grid.handle, b, _dptr(R, torch.float32, b * n), ctypes.byref(hp),
+                                         _stream(stream), ctypes.byref(loss)), "net_train_step")
+        return loss.value
+
+    def loss_grad(self, grid: Grid, R: torch.Tensor, stream=None):
+        """(loss, flat gradient) at the current parameters."""
+        n = grid.nx * grid.ny
+        b = R.numel() // n
+        loss = ctypes.c_double()
+        g = np.empty(self.param_count, dtype=np.float32)
+        check(_lib.load().net_loss_grad(self.handle, grid.handle, b, _dptr(R, torch.float32, b * n), _stream(stream),
+                                        ctypes.byref(loss), g.ctypes.data_as(ctypes.c_void_p)), "net_loss_grad")
+        return loss.value, g
+
+    @property
+    def step(self) -> int:
+        t = ctypes.c_int64()
+        check(_lib.load().net_get_step(self.handle, ctypes.byref(t)), "net_get_step")
+        return t.value
+
     def infer(self, grid: Grid, r: torch.Tensor, e: torch.Tensor, stream=None):
         n = grid.nx * grid.ny
         b = r.numel() // n
         check(_lib.load().net_infer_batch(self.handle, grid.handle, b, _dptr(r, torch.float32, b * n),
                                           _dptr(e, torch.float32, b * n), _stream(stream)), "net_infer")
         return e
+
+
+def net_default_hparams(**kw) -> _lib.ppe_train_hparams:
+    hp = _lib.ppe_train_hparams()
+    _lib.load().net_default_hparams(ctypes.byref(hp))
+    for k, v in kw.items():
+        setattr(hp, k, v)
+    return hp
 
 
 def net_create(cfg=None, seed: int = 0) -> Net:
@@ -245,3 +279,14 @@ def flatten_params(P: dict, cfg) -> np.ndarray:
     """Flatten a name -> array dict in the library's parameter order."""
     from .inputs import net_param_shapes
     return np.concatenate([np.asarray(P[k], np.float32).reshape(-1) for k in net_param_shapes(cfg)])
+
+
+def unflatten_params(flat: np.ndarray, cfg) -> dict:
+    """Inverse of flatten_params."""
+    from .inputs import net_param_shapes
+    out, off = {}, 0
+    for k, shp in net_param_shapes(cfg).items():
+        n = int(np.prod(shp))
+        out[k] = flat[off:off + n].reshape(shp)
+        off += n
+    return out

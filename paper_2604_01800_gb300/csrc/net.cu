@@ -162,6 +162,7 @@ ppe_status ensure_packed(ppe_net *n, const float *P, cudaStream_t s)
 static void free_cache(NetCache *c)
 {
     if (!c) return;
+    net_free_train(c);
     cudaFree(c->delta); cudaFree(c->eta); cudaFree(c->phi); cudaFree(c->xy); cudaFree(c->trunk);
     cudaFree(c->weff); cudaFree(c->ceff); cudaFree(c->act); cudaFree(c->grad_act); cudaFree(c->efull);
     cudaFree(c->red);

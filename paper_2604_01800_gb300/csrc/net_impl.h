@@ -43,7 +43,10 @@ struct NetCache {
     float *efull = nullptr;
     size_t efull_elems = 0;
     double *red = nullptr;
+    void *train = nullptr;                  // training workspace (net_train.cu)
 };
+
+void net_free_train(NetCache *c);
 
 int layer_index(const ppe_net *n, const std::string &name);
 ppe_status ensure_packed(ppe_net *n, const float *P, cudaStream_t s);

@@ -1,0 +1,692 @@
+// Training of the DeepONet on the GPU (Sec. 2.4): the unsupervised loss of
+// Eq. 18 through the volume-scaled PPE operator, hand-written backward
+// kernels for every forward step, and the SAM + Adam update with cosine
+// learning-rate decay.
+//
+// Backward of one Mesh-Conv layer Y = gelu(Z), Z = conv(eta * X) + b:
+//   dZ = dY * gelu'(Z);  db = sum dZ;  dW = sum dZ (x) (eta X) shifted;
+//   d(eta X) = conv of dZ with the transposed, flipped kernel (the forward
+//   convolution kernel run on repacked weights);  dX = eta d(eta X);
+//   d eta = sum_c X d(eta X) = sum_c (eta X) d(eta X) / eta;
+//   eta = exp(-Phi^2):  dPhi = -2 Phi eta d eta, then the weight network.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "net_iface.h"
+#include "net_impl.h"
+#include "net_kernels.cuh"
+#include "net_ops.h"
+
+namespace ppe {
+
+namespace {
+
+unsigned g1d(size_t n, int bs = 256)
+{
+    size_t g = (n + bs - 1) / bs;
+    if (g < 1) g = 1;
+    if (g > 16384) g = 16384;
+    return (unsigned)g;
+}
+
+// y = scale * A x for `batch` unpitched FP32 fields [ny][nx]
+__global__ void apply_f32_kernel(const float *__restrict__ x, float *__restrict__ y, int nx, int ny, int batch,
+                                 const float *__restrict__ dx, const float *__restrict__ dy,
+                                 const float *__restrict__ fx, const float *__restrict__ fy, float scale)
+{
+    const size_t N = (size_t)nx * ny;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < N * batch; k += (size_t)gridDim.x * blockDim.x) {
+        size_t c = k % N;
+        int i = c % nx, j = c / nx;
+        float v = x[k];
+        float xe = i + 1 < nx ? x[k + 1] : 0.f, xw = i > 0 ? x[k - 1] : 0.f;
+        float xn = j + 1 < ny ? x[k + nx] : 0.f, xs = j > 0 ? x[k - nx] : 0.f;
+        float ax = fx[i + 1] * (v - xe) + fx[i] * (v - xw);
+        float ay = fy[j + 1] * (v - xn) + fy[j] * (v - xs);
+        y[k] = scale * (dy[j] * ax + dx[i] * ay);
+    }
+}
+
+// res = R - Ae;  acc += sum res^2  (FP64)
+__global__ void residual_kernel(const float *__restrict__ R, const float *__restrict__ Ae, float *__restrict__ res,
+                                size_t n, double *acc)
+{
+    double s = 0.0;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+        float r = R[k] - Ae[k];
+        res[k] = r;
+        s += (double)r * r;
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    __shared__ double ws[32];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+        atomicAdd(acc, t);
+    }
+}
+
+// Backward of e = sum_c U0_c weff_c + ceff (cropped to nx x ny).
+__global__ void fold_bwd_kernel(const float *__restrict__ de, const bf16 *__restrict__ U0,
+                                const float *__restrict__ weff, int B, int H, int W, int C, int nx, int ny,
+                                float *__restrict__ dU0, float *__restrict__ dweff, float *__restrict__ dceff)
+{
+    const size_t HW = (size_t)H * W;
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < HW; q += (size_t)gridDim.x * blockDim.x) {
+        int x = q % W, y = q / W;
+        bool in = x < nx && y < ny;
+        float dc = 0.f;
+        for (int c = 0; c < C; ++c) {
+            float w = weff[c * HW + q], acc = 0.f;
+            for (int b = 0; b < B; ++b) {
+                float d = in ? de[((size_t)b * ny + y) * nx + x] : 0.f;
+                size_t p = (size_t)b * HW + q;
+                dU0[p * C + c] = d * w;
+                acc += d * __bfloat162float(U0[p * C + c]);
+            }
+            dweff[c * HW + q] = acc;
+        }
+        for (int b = 0; b < B; ++b) dc += in ? de[((size_t)b * ny + y) * nx + x] : 0.f;
+        dceff[q] = dc;
+    }
+}
+
+// dZ = dY * gelu'(Z) (BF16); db[c] += sum over pixels (C divides 256)
+__global__ void act_bwd_kernel(const float *__restrict__ dY, const bf16 *__restrict__ Z, bf16 *__restrict__ dZ,
+                               size_t n, int C, float *__restrict__ db)
+{
+    __shared__ float red[256];
+    float acc = 0.f;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+        float g = dY[k] * gelu_grad_f(__bfloat162float(Z[k]));
+        dZ[k] = __float2bfloat16_rn(g);
+        acc += g;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    if ((int)threadIdx.x < C) {
+        float s = 0.f;
+        for (int t = threadIdx.x; t < (int)blockDim.x; t += C) s += red[t];
+        atomicAdd(&db[threadIdx.x], s);
+    }
+}
+
+// dW[co][ci][tap] += sum_p dZ[p][co] * X[p + tap][ci]  (X: the layer's eta-weighted input)
+constexpr int WG_H = 8, WG_W = 16, WG_P = WG_H * WG_W;
+__global__ void __launch_bounds__(256) wgrad_kernel(const bf16 *__restrict__ dZ, const bf16 *__restrict__ X, int B,
+                                                    int H, int W, int cin, int cout, float *__restrict__ dW,
+                                                    int tiles_per_block)
+{
+    __shared__ float dzs[WG_P][33];
+    __shared__ float xs[(WG_H + 2) * (WG_W + 2)][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int co0 = blockIdx.x * 32, ci0 = blockIdx.y * 32;
+    const int tw = (W + WG_W - 1) / WG_W, th = (H + WG_H - 1) / WG_H;
+    const long total = (long)B * tw * th;
+    float acc[4][9];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int t = 0; t < 9; ++t) acc[j][t] = 0.f;
+    const long t0 = (long)blockIdx.z * tiles_per_block;
+    const long t1 = min(total, t0 + tiles_per_block);
+    for (long tile = t0; tile < t1; ++tile) {
+        int b = tile / (tw * th), r = tile % (tw * th);
+        int y0 = (r / tw) * WG_H, x0 = (r % tw) * WG_W;
+        __syncthreads();
+        for (int k = threadIdx.x; k < WG_P * 32; k += 256) {
+            int c = k % 32, p = k / 32;
+            int y = y0 + p / WG_W, x = x0 + p % WG_W;
+            float v = 0.f;
+            if (y < H && x < W && co0 + c < cout) v = __bfloat162float(dZ[(((size_t)b * H + y) * W + x) * cout + co0 + c]);
+            dzs[p][c] = v;
+        }
+        for (int k = threadIdx.x; k < (WG_H + 2) * (WG_W + 2) * 32; k += 256) {
+            int c = k % 32, p = k / 32;
+            int y = y0 - 1 + p / (WG_W + 2), x = x0 - 1 + p % (WG_W + 2);
+            float v = 0.f;
+            if (y >= 0 && y < H && x >= 0 && x < W && ci0 + c < cin)
+                v = __bfloat162float(X[(((size_t)b * H + y) * W + x) * cin + ci0 + c]);
+            xs[p][c] = v;
+        }
+        __syncthreads();
+        for (int p = 0; p < WG_P; ++p) {
+            float d = dzs[p][lane];
+            int py = p / WG_W, px = p % WG_W;
+#pragma unroll
+            for (int t = 0; t < 9; ++t) {
+                const float *xr = xs[(py + t / 3) * (WG_W + 2) + px + t % 3];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[j][t] = fmaf(d, xr[warp * 4 + j], acc[j][t]);
+            }
+        }
+    }
+    int co = co0 + lane;
+    if (co >= cout) return;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        int ci = ci0 + warp * 4 + j;
+        if (ci >= cin) continue;
+#pragma unroll
+        for (int t = 0; t < 9; ++t) atomicAdd(&dW[((size_t)co * cin + ci) * 9 + t], acc[j][t]);
+    }
+}
+
+// First layer (1 input channel X = eta R): dW[co][tap] and d(eta R)[p]
+__device__ __forceinline__ float rin_at(const float *R, int b, int y, int x, int nx, int ny)
+{
+    return (y >= 0 && x >= 0 && y < ny && x < nx) ? R[((size_t)b * ny + y) * nx + x] : 0.f;
+}
+
+__global__ void wgrad_in_kernel(const bf16 *__restrict__ dZ, const float *__restrict__ R, const float *__restrict__ eta,
+                                int B, int H, int W, int C, int nx, int ny, float *__restrict__ dW)
+{
+    const int co = threadIdx.x;   // blockDim.x == C
+    float acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    const size_t P = (size_t)B * H * W;
+    for (size_t p = blockIdx.x; p < P; p += gridDim.x) {
+        int x = p % W, y = (p / W) % H, b = p / ((size_t)W * H);
+        float d = __bfloat162float(dZ[p * C + co]);
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+            int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
+            float v = (yy >= 0 && xx >= 0 && yy < H && xx < W) ? rin_at(R, b, yy, xx, nx, ny) * eta[yy * W + xx] : 0.f;
+            acc[t] = fmaf(d, v, acc[t]);
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < 9; ++t) atomicAdd(&dW[co * 9 + t], acc[t]);
+}
+
+__global__ void dgrad_in_kernel(const bf16 *__restrict__ dZ, const float *__restrict__ Wt /*[C][9] FP32 OIHW*/,
+                                const float *__restrict__ R, int B, int H, int W, int C, int nx, int ny,
+                                float *__restrict__ deta)
+{
+    const size_t P = (size_t)B * H * W;
+    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < P; p += (size_t)gridDim.x * blockDim.x) {
+        int x = p % W, y = (p / W) % H, b = p / ((size_t)W * H);
+        float g = 0.f;   // d(eta R)[p] = sum_tap sum_co W[co][tap] dZ[p - offset(tap)][co]
+        for (int t = 0; t < 9; ++t) {
+            int yy = y - (t / 3 - 1), xx = x - (t % 3 - 1);
+            if (yy < 0 || xx < 0 || yy >= H || xx >= W) continue;
+            const bf16 *dz = dZ + (((size_t)b * H + yy) * W + xx) * C;
+            for (int co = 0; co < C; ++co) g = fmaf(Wt[co * 9 + t], __bfloat162float(dz[co]), g);
+        }
+        float r = rin_at(R, b, y, x, nx, ny);
+        atomicAdd(&deta[y * W + x], r * g);
+    }
+}
+
+// dX = eta d(eta X);  d eta += sum_c (eta X) d(eta X) / eta
+__global__ void eta_bwd_kernel(const float *__restrict__ dXb, const bf16 *__restrict__ Xb, const float *__restrict__ eta,
+                               size_t P, int HW, int C, float *__restrict__ dX, float *__restrict__ deta, int mesh)
+{
+    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < P; p += (size_t)gridDim.x * blockDim.x) {
+        int q = p % HW;
+        float e = eta[q], s = 0.f;
+        for (int c = 0; c < C; ++c) {
+            float g = dXb[p * C + c];
+            dX[p * C + c] = e * g;
+            s = fmaf(__bfloat162float(Xb[p * C + c]), g, s);
+        }
+        if (mesh && e > 0.f) atomicAdd(&deta[q], s / e);
+    }
+}
+
+// Weight-network backward: phi = w2 . tanh(W1 D + b1) + b2, eta = exp(-phi^2)
+__global__ void phi_bwd_kernel(const float *__restrict__ deta, const float *__restrict__ eta,
+                               const float *__restrict__ phi, const float *__restrict__ D, int HW,
+                               const float *__restrict__ W1, const float *__restrict__ b1, const float *__restrict__ w2,
+                               int hid, float *__restrict__ gW1, float *__restrict__ gb1, float *__restrict__ gw2,
+                               float *__restrict__ gb2)
+{
+    extern __shared__ float red[];   // 6*hid + 1
+    for (int k = threadIdx.x; k < 6 * hid + 1; k += blockDim.x) red[k] = 0.f;
+    __syncthreads();
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < HW; q += gridDim.x * blockDim.x) {
+        float dphi = deta[q] * eta[q] * (-2.f * phi[q]);
+        if (dphi == 0.f) continue;
+        float d[4] = {D[q], D[HW + q], D[2 * HW + q], D[3 * HW + q]};
+        atomicAdd(&red[6 * hid], dphi);
+        for (int k = 0; k < hid; ++k) {
+            float z = b1[k] + W1[4 * k] * d[0] + W1[4 * k + 1] * d[1] + W1[4 * k + 2] * d[2] + W1[4 * k + 3] * d[3];
+            float h = tanhf(z);
+            atomicAdd(&red[k], dphi * h);                       // w2
+            float dz = dphi * w2[k] * (1.f - h * h);
+            atomicAdd(&red[hid + k], dz);                       // b1
+            for (int c = 0; c < 4; ++c) atomicAdd(&red[2 * hid + 4 * k + c], dz * d[c]);   // W1
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < 6 * hid + 1; k += blockDim.x) {
+        float v = red[k];
+        if (v == 0.f) continue;
+        if (k < hid) atomicAdd(&gw2[k], v);
+        else if (k < 2 * hid) atomicAdd(&gb1[k - hid], v);
+        else if (k < 6 * hid) atomicAdd(&gW1[k - 2 * hid], v);
+        else atomicAdd(gb2, v);
+    }
+}
+
+// dst[p][dco + c] += src[p][sco + c], c < nc
+__global__ void add_slice_kernel(float *__restrict__ dst, int dcs, int dco, const float *__restrict__ src, int scs,
+                                 int sco, int nc, size_t P)
+{
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < P * nc; k += (size_t)gridDim.x * blockDim.x) {
+        size_t p = k / nc;
+        int c = k % nc;
+        dst[p * dcs + dco + c] += src[p * scs + sco + c];
+    }
+}
+
+// coarse[b][y][x][c] += sum of the 4 fine children (fine: [B][2H][2W][C])
+__global__ void up2_bwd_kernel(const float *__restrict__ fine, float *__restrict__ coarse, int B, int H, int W, int C)
+{
+    size_t n = (size_t)B * H * W * C;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+        int c = k % C;
+        size_t pix = k / C;
+        int x = pix % W, y = (pix / W) % H, b = pix / ((size_t)W * H);
+        float s = 0.f;
+        for (int t = 0; t < 4; ++t)
+            s += fine[((((size_t)b * 2 * H) + 2 * y + (t >> 1)) * 2 * W + 2 * x + (t & 1)) * C + c];
+        coarse[k] += s;
+    }
+}
+
+// fine[b][y][x][c] += 0.25 coarse[b][y/2][x/2][c]   (fine: [B][H][W][C])
+__global__ void pool2_bwd_kernel(const float *__restrict__ coarse, float *__restrict__ fine, int B, int H, int W, int C)
+{
+    size_t n = (size_t)B * H * W * C;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+        int c = k % C;
+        size_t pix = k / C;
+        int x = pix % W, y = (pix / W) % H, b = pix / ((size_t)W * H);
+        fine[k] += 0.25f * coarse[((((size_t)b * (H / 2)) + y / 2) * (W / 2) + x / 2) * C + c];
+    }
+}
+
+// dz = dt * (1 - t^2)
+__global__ void tanh_bwd_kernel(const float *__restrict__ dt, const float *__restrict__ t, float *__restrict__ dz,
+                                size_t n)
+{
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+        dz[k] = dt[k] * (1.f - t[k] * t[k]);
+}
+
+__global__ void fill_kernel(float *p, size_t n, float v)
+{
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) p[k] = v;
+}
+
+__global__ void sumsq_kernel(const float *__restrict__ g, size_t n, double *acc)
+{
+    double s = 0.0;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+        s += (double)g[k] * g[k];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    __shared__ double ws[32];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+        atomicAdd(acc, t);
+    }
+}
+
+// P' = P + rho g / ||g||  (||g||^2 read from the device)
+__global__ void perturb_kernel(const float *__restrict__ P, const float *__restrict__ g, float *__restrict__ Pp,
+                               size_t n, double rho, const double *gsq)
+{
+    const float s = (float)(rho / (sqrt(*gsq) + 1e-12));
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+        Pp[k] = P[k] + s * g[k];
+}
+
+__global__ void adam_kernel(float *__restrict__ P, const float *__restrict__ g, float *__restrict__ m,
+                            float *__restrict__ v, size_t n, float lr, float b1, float b2, float eps, float bc1,
+                            float bc2)
+{
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+        float gk = g[k];
+        float mk = b1 * m[k] + (1.f - b1) * gk;
+        float vk = b2 * v[k] + (1.f - b2) * gk * gk;
+        m[k] = mk;
+        v[k] = vk;
+        P[k] -= lr * (mk / bc1) / (sqrtf(vk / bc2) + eps);
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// workspace
+// ---------------------------------------------------------------------------
+
+struct TrainWs {
+    int capB = 0;
+    std::vector<size_t> G;        // per-layer dL/dY offsets (FP32 elements)
+    float *g = nullptr;           // all dL/dY buffers
+    size_t g_elems = 0;
+    float *dXb = nullptr, *dX = nullptr, *deta = nullptr;
+    bf16 *dZ = nullptr;
+    float *e = nullptr, *Ae = nullptr, *res = nullptr, *de = nullptr;
+    float *dU0 = nullptr, *dweff = nullptr, *dceff = nullptr;
+    float *dt3 = nullptr, *dt2 = nullptr, *dt1 = nullptr, *dz = nullptr, *ones = nullptr;
+    double *acc = nullptr;        // [0] loss sum, [1] grad sumsq
+};
+
+static void free_ws(TrainWs *w)
+{
+    if (!w) return;
+    cudaFree(w->g); cudaFree(w->dXb); cudaFree(w->dX); cudaFree(w->deta); cudaFree(w->dZ);
+    cudaFree(w->e); cudaFree(w->Ae); cudaFree(w->res); cudaFree(w->de); cudaFree(w->dU0);
+    cudaFree(w->dweff); cudaFree(w->dceff); cudaFree(w->dt3); cudaFree(w->dt2); cudaFree(w->dt1);
+    cudaFree(w->dz); cudaFree(w->ones); cudaFree(w->acc);
+    delete w;
+}
+
+void net_free_train(NetCache *c)
+{
+    free_ws((TrainWs *)c->train);
+    c->train = nullptr;
+}
+
+static ppe_status ensure_ws(ppe_net *n, NetCache *c, int B)
+{
+    TrainWs *w = (TrainWs *)c->train;
+    if (w && w->capB >= B) return PPE_OK;
+    free_ws(w);
+    w = new TrainWs();
+    c->train = w;
+    w->capB = B;
+    size_t off = 0, maxin = 0, maxout = 0;
+    w->G.resize(n->layers.size());
+    for (size_t i = 0; i < n->layers.size(); ++i) {
+        const ConvLayer &l = n->layers[i];
+        size_t px = (size_t)B * c->Hk[l.level] * c->Wk[l.level];
+        w->G[i] = off;
+        off += px * l.cout;
+        maxin = std::max(maxin, px * l.cin);
+        maxout = std::max(maxout, px * l.cout);
+    }
+    w->g_elems = off;
+    const size_t P = (size_t)c->H * c->W, N = (size_t)c->nx * c->ny;
+    const ppe_net_config &cf = n->cfg;
+    PPE_CUDA_TRY(cudaMalloc(&w->g, off * 4));
+    PPE_CUDA_TRY(cudaMalloc(&w->dXb, maxin * 4));
+    PPE_CUDA_TRY(cudaMalloc(&w->dX, maxin * 4));
+    PPE_CUDA_TRY(cudaMalloc(&w->dZ, maxout * 2));
+    PPE_CUDA_TRY(cudaMalloc(&w->deta, P * 4));
+    PPE_CUDA_TRY(cudaMalloc(&w->e, N * B * 4));
+    PPE_CUDA_TRY(cudaMalloc(&w->Ae, N * B * 4));
+    PPE_CUDA_TRY(cudaMalloc(&w->res, N * B * 4));
+    PPE_CUDA_TRY(cudaMalloc(&w->de, N * B * 4));
+    PPE_CUDA_TRY(cudaMalloc(&w->dU0, (size_t)B * P * cf.widths[0] * 4));
+    PPE_CUDA_TRY(cudaMalloc(&w->dweff, P * cf.widths[0] * 4));
+    PPE_CUDA_TRY(cudaMalloc(&w->dceff, P * 4));
+    PPE_CUDA_TRY(cudaMalloc(&w->dt3, P * cf.c_last * 4));
+    PPE_CUDA_TRY(cudaMalloc(&w->dt2, P * cf.trunk_hidden[1] * 4));
+    PPE_CUDA_TRY(cudaMalloc(&w->dt1, P * cf.trunk_hidden[0] * 4));
+    PPE_CUDA_TRY(cudaMalloc(&w->dz, P * std::max(cf.trunk_hidden[0], cf.trunk_hidden[1]) * 4));
+    PPE_CUDA_TRY(cudaMalloc(&w->ones, P * 4));
+    PPE_CUDA_TRY(cudaMalloc(&w->acc, 2 * sizeof(double)));
+    fill_kernel<<<g1d(P), 256>>>(w->ones, P, 1.f);
+    PPE_CUDA_TRY(cudaGetLastError());
+    return PPE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// loss, backward
+// ---------------------------------------------------------------------------
+
+// L = mean (R - A e)^2 and de = -(2/(B N)) A (R - A e).  Loss sum lands in w->acc[0].
+static ppe_status loss_de(ppe_grid *g, TrainWs *w, int B, const float *R, cudaStream_t s)
+{
+    const size_t N = (size_t)g->nx * g->ny;
+    apply_f32_kernel<<<g1d(N * B), 256, 0, s>>>(w->e, w->Ae, g->nx, g->ny, B, g->dx32, g->dy32, g->fx32, g->fy32, 1.f);
+    residual_kernel<<<g1d(N * B), 256, 0, s>>>(R, w->Ae, w->res, N * B, w->acc);
+    apply_f32_kernel<<<g1d(N * B), 256, 0, s>>>(w->res, w->de, g->nx, g->ny, B, g->dx32, g->dy32, g->fx32, g->fy32,
+                                                 (float)(-2.0 / ((double)B * N)));
+    PPE_CUDA_TRY(cudaGetLastError());
+    return PPE_OK;
+}
+
+static ppe_status conv_backward(ppe_net *n, NetCache *c, TrainWs *w, int li, const bf16 *Xb, const float *P,
+                                float *grads, int B, cudaStream_t s)
+{
+    const ConvLayer &l = n->layers[li];
+    const int k = l.level, H = c->Hk[k], W = c->Wk[k];
+    const size_t px = (size_t)B * H * W;
+    const float *dY = w->g + w->G[li];
+    const bf16 *Z = c->act + c->plan.Z[li];
+    act_bwd_kernel<<<g1d(px * l.cout), 256, 0, s>>>(dY, Z, w->dZ, px * l.cout, l.cout, grads + l.off_b);
+    // weight gradient
+    {
+        const int tiles = B * ((W + WG_W - 1) / WG_W) * ((H + WG_H - 1) / WG_H);
+        dim3 grid((l.cout + 31) / 32, (l.cin + 31) / 32, 1);
+        int blocks_xy = grid.x * grid.y;
+        int split = std::max(1, std::min(tiles, 592 / std::max(1, blocks_xy)));
+        int per = (tiles + split - 1) / split;
+        grid.z = (tiles + per - 1) / per;
+        wgrad_kernel<<<grid, 256, 0, s>>>(w->dZ, Xb, B, H, W, l.cin, l.cout, grads + l.off_w, per);
+    }
+    // data gradient: forward convolution of dZ with the transposed, flipped kernel
+    ConvArgs a;
+    a.in = w->dZ; a.w = n->wt + l.off_wt; a.bias = nullptr;
+    a.B = B; a.H = H; a.W = W; a.cin = l.cout; a.cout = l.cin;
+    a.epi.zf_out = w->dXb; a.epi.act = 0;
+    PPE_TRY(run_conv(n, a, s));
+    PPE_CUDA_TRY(cudaMemsetAsync(w->deta, 0, (size_t)H * W * 4, s));
+    const float *eta = c->eta + c->eoff[li];
+    eta_bwd_kernel<<<g1d(px), 256, 0, s>>>(w->dXb, Xb, eta, px, H * W, l.cin, w->dX, w->deta, n->cfg.mesh_conv);
+    if (n->cfg.mesh_conv) {
+        int hid = n->cfg.phi_hidden;
+        phi_bwd_kernel<<<std::min(256u, g1d((size_t)H * W)), 256, (6 * hid + 1) * 4, s>>>(
+            w->deta, eta, c->phi + c->eoff[li], c->delta + c->doff[k], H * W, P + l.off_p1w, P + l.off_p1b,
+            P + l.off_p2w, hid, grads + l.off_p1w, grads + l.off_p1b, grads + l.off_p2w, grads + l.off_p2b);
+    }
+    PPE_CUDA_TRY(cudaGetLastError());
+    return PPE_OK;
+}
+
+// Full backward: gradients of sum(de * e) into `grads` (zeroed here).
+static ppe_status net_backward(ppe_net *n, NetCache *c, TrainWs *w, ppe_grid *g, int B, const float *R,
+                               const float *P, float *grads, cudaStream_t s)
+{
+    const ppe_net_config &cf = n->cfg;
+    const int L = c->L;
+    const ActPlan &pl = c->plan;
+    const int Pn = c->H * c->W;
+    const int C0 = cf.widths[0];
+    PPE_CUDA_TRY(cudaMemsetAsync(grads, 0, n->nparams * 4, s));
+    PPE_CUDA_TRY(cudaMemsetAsync(w->g, 0, w->g_elems * 4, s));
+    auto G = [&](const std::string &name) { return w->g + w->G[layer_index(n, name)]; };
+
+    // DeepONet fold: e = sum_c U0_c weff_c + ceff
+    float *gdec0b = G("dec0b");
+    fold_bwd_kernel<<<g1d(Pn), 256, 0, s>>>(w->de, c->act + pl.U[0], c->weff, B, c->H, c->W, C0, g->nx, g->ny, gdec0b,
+                                            w->dweff, w->dceff);
+    // head + trunk: weff = head.w^T t3, ceff = head.b . t3 + out.b, t3 = T2 t2 + b2, t2 = tanh(T1 t1 + b1), ...
+    float *t1 = c->trunk, *t2 = t1 + (size_t)cf.trunk_hidden[0] * Pn, *t3 = t2 + (size_t)cf.trunk_hidden[1] * Pn;
+    const int h0 = cf.trunk_hidden[0], h1 = cf.trunk_hidden[1], cl = cf.c_last;
+    PPE_TRY(sgemm(cl, C0, Pn, t3, Pn, false, w->dweff, Pn, true, grads + n->off_head_w, C0, nullptr, 0, false, s));
+    PPE_TRY(sgemm(cl, 1, Pn, t3, Pn, false, w->dceff, 1, false, grads + n->off_head_b, 1, nullptr, 0, false, s));
+    PPE_TRY(sgemm(1, 1, Pn, w->dceff, Pn, false, w->ones, 1, false, grads + n->off_out_b, 1, nullptr, 0, false, s));
+    PPE_TRY(sgemm(cl, Pn, C0, P + n->off_head_w, C0, false, w->dweff, Pn, false, w->dt3, Pn, nullptr, 0, false, s));
+    PPE_TRY(sgemm(cl, Pn, 1, P + n->off_head_b, 1, false, w->dceff, Pn, false, w->dt3, Pn, nullptr, 0, true, s));
+    PPE_TRY(sgemm(cl, h1, Pn, w->dt3, Pn, false, t2, Pn, true, grads + n->off_tw[2], h1, nullptr, 0, false, s));
+    PPE_TRY(sgemm(cl, 1, Pn, w->dt3, Pn, false, w->ones, 1, false, grads + n->off_tb[2], 1, nullptr, 0, false, s));
+    PPE_TRY(sgemm(h1, Pn, cl, P + n->off_tw[2], h1, true, w->dt3, Pn, false, w->dt2, Pn, nullptr, 0, false, s));
+    tanh_bwd_kernel<<<g1d((size_t)h1 * Pn), 256, 0, s>>>(w->dt2, t2, w->dz, (size_t)h1 * Pn);
+    PPE_TRY(sgemm(h1, h0, Pn, w->dz, Pn, false, t1, Pn, true, grads + n->off_tw[1], h0, nullptr, 0, false, s));
+    PPE_TRY(sgemm(h1, 1, Pn, w->dz, Pn, false, w->ones, 1, false, grads + n->off_tb[1], 1, nullptr, 0, false, s));
+    PPE_TRY(sgemm(h0, Pn, h1, P + n->off_tw[1], h0, true, w->dz, Pn, false, w->dt1, Pn, nullptr, 0, false, s));
+    tanh_bwd_kernel<<<g1d((size_t)h0 * Pn), 256, 0, s>>>(w->dt1, t1, w->dz, (size_t)h0 * Pn);
+    PPE_TRY(sgemm(h0, 2, Pn, w->dz, Pn, false, c->xy, Pn, true, grads + n->off_tw[0], 2, nullptr, 0, false, s));
+    PPE_TRY(sgemm(h0, 1, Pn, w->dz, Pn, false, w->ones, 1, false, grads + n->off_tb[0], 1, nullptr, 0, false, s));
+
+    // decoder, level 0 upward
+    for (int k = 0; k <= L - 2; ++k) {
+        const std::string ks = std::to_string(k);
+        const int Ck = cf.widths[k];
+        const size_t px = (size_t)B * c->Hk[k] * c->Wk[k];
+        PPE_TRY(conv_backward(n, c, w, layer_index(n, "dec" + ks + "b"), c->act + pl.D[k], P, grads, B, s));
+        add_slice_kernel<<<g1d(px * Ck), 256, 0, s>>>(G("dec" + ks + "a"), Ck, 0, w->dX, Ck, 0, Ck, px);
+        PPE_TRY(conv_backward(n, c, w, layer_index(n, "dec" + ks + "a"), c->act + pl.CAT[k], P, grads, B, s));
+        add_slice_kernel<<<g1d(px * Ck), 256, 0, s>>>(G("up" + ks), Ck, 0, w->dX, 2 * Ck, 0, Ck, px);
+        add_slice_kernel<<<g1d(px * Ck), 256, 0, s>>>(G("enc" + ks + "b"), Ck, 0, w->dX, 2 * Ck, Ck, Ck, px);
+        PPE_TRY(conv_backward(n, c, w, layer_index(n, "up" + ks), c->act + pl.UP[k], P, grads, B, s));
+        const std::string next = (k + 1 == L - 1) ? "enc" + std::to_string(k + 1) + "b" : "dec" + std::to_string(k + 1) + "b";
+        const int C1 = cf.widths[k + 1];
+        up2_bwd_kernel<<<g1d((size_t)B * c->Hk[k + 1] * c->Wk[k + 1] * C1), 256, 0, s>>>(w->dX, G(next), B, c->Hk[k + 1],
+                                                                                        c->Wk[k + 1], C1);
+    }
+    // encoder, deepest level downward
+    for (int k = L - 1; k >= 0; --k) {
+        const std::string ks = std::to_string(k);
+        const int Ck = cf.widths[k];
+        const size_t px = (size_t)B * c->Hk[k] * c->Wk[k];
+        PPE_TRY(conv_backward(n, c, w, layer_index(n, "enc" + ks + "b"), c->act + pl.A[k], P, grads, B, s));
+        add_slice_kernel<<<g1d(px * Ck), 256, 0, s>>>(G("enc" + ks + "a"), Ck, 0, w->dX, Ck, 0, Ck, px);
+        if (k > 0) {
+            PPE_TRY(conv_backward(n, c, w, layer_index(n, "enc" + ks + "a"), c->act + pl.IN[k], P, grads, B, s));
+            const int Cp = cf.widths[k - 1];
+            pool2_bwd_kernel<<<g1d((size_t)B * c->Hk[k - 1] * c->Wk[k - 1] * Cp), 256, 0, s>>>(
+                w->dX, G("enc" + std::to_string(k - 1) + "b"), B, c->Hk[k - 1], c->Wk[k - 1], Cp);
+        }
+    }
+    // first layer (one input channel)
+    {
+        const int li = layer_index(n, "enc0a");
+        const ConvLayer &l = n->layers[li];
+        const size_t px = (size_t)B * c->H * c->W;
+        act_bwd_kernel<<<g1d(px * l.cout), 256, 0, s>>>(G("enc0a"), c->act + pl.Z[li], w->dZ, px * l.cout, l.cout,
+                                                       grads + l.off_b);
+        const float *eta = c->eta + c->eoff[li];
+        wgrad_in_kernel<<<1024, l.cout, 0, s>>>(w->dZ, R, eta, B, c->H, c->W, l.cout, g->nx, g->ny, grads + l.off_w);
+        if (cf.mesh_conv) {
+            PPE_CUDA_TRY(cudaMemsetAsync(w->deta, 0, (size_t)c->H * c->W * 4, s));
+            dgrad_in_kernel<<<g1d(px), 256, 0, s>>>(w->dZ, P + l.off_w, R, B, c->H, c->W, l.cout, g->nx, g->ny, w->deta);
+            int hid = cf.phi_hidden;
+            phi_bwd_kernel<<<std::min(256u, g1d((size_t)c->H * c->W)), 256, (6 * hid + 1) * 4, s>>>(
+                w->deta, eta, c->phi + c->eoff[li], c->delta + c->doff[0], c->H * c->W, P + l.off_p1w, P + l.off_p1b,
+                P + l.off_p2w, hid, grads + l.off_p1w, grads + l.off_p1b, grads + l.off_p2w, grads + l.off_p2b);
+        }
+    }
+    PPE_CUDA_TRY(cudaGetLastError());
+    return PPE_OK;
+}
+
+// forward + loss + backward at parameters P; gradient into grads, loss sum into w->acc[0]
+static ppe_status loss_and_grad(ppe_net *n, NetCache *c, TrainWs *w, ppe_grid *g, int B, const float *R, const float *P,
+                                float *grads, cudaStream_t s)
+{
+    InputSrc src;
+    src.r = R; src.pitch = g->nx; src.bstride = (size_t)g->nx * g->ny; src.nx = g->nx; src.ny = g->ny;
+    PPE_TRY(net_forward(n, c, B, src, P, w->e, g->nx, (size_t)g->nx * g->ny, true, s));
+    PPE_TRY(loss_de(g, w, B, R, s));
+    return net_backward(n, c, w, g, B, R, P, grads, s);
+}
+
+}  // namespace ppe
+
+using namespace ppe;
+
+extern "C" {
+
+void net_default_hparams(ppe_train_hparams *hp)
+{
+    if (!hp) return;
+    std::memset(hp, 0, sizeof(*hp));
+    hp->lr0 = 2e-4;
+    hp->total_steps = 1000000;
+    hp->rho = 2e-4;
+    hp->beta1 = 0.9;
+    hp->beta2 = 0.999;
+    hp->eps = 1e-8;
+}
+
+ppe_status net_get_step(const ppe_net *n, int64_t *step)
+{
+    if (!n || !step) { set_error("net_get_step: NULL argument"); return PPE_ERR_ARG; }
+    *step = n->step;
+    return PPE_OK;
+}
+
+static ppe_status train_prep(ppe_net *n, ppe_grid *g, int batch, const float *R, NetCache **cout, TrainWs **wout)
+{
+    if (!n || !g || !R || batch < 1) { set_error("net training: bad arguments"); return PPE_ERR_ARG; }
+    PPE_TRY(net_check_grid(n, g));
+    NetCache *c = (NetCache *)g->net_cache;
+    PPE_TRY(ensure_acts(n, c, batch));
+    PPE_TRY(ensure_ws(n, c, batch));
+    *cout = c;
+    *wout = (TrainWs *)c->train;
+    return PPE_OK;
+}
+
+ppe_status net_loss_grad(ppe_net *n, ppe_grid *g, int batch, const float *R, void *stream, double *loss_out,
+                         float *grad_host)
+{
+    clear_error();
+    NetCache *c;
+    TrainWs *w;
+    PPE_TRY(train_prep(n, g, batch, R, &c, &w));
+    cudaStream_t s = (cudaStream_t)stream;
+    PPE_CUDA_TRY(cudaMemsetAsync(w->acc, 0, 2 * sizeof(double), s));
+    PPE_TRY(loss_and_grad(n, c, w, g, batch, R, n->params, n->grads, s));
+    double acc[2];
+    PPE_CUDA_TRY(cudaMemcpyAsync(acc, w->acc, sizeof acc, cudaMemcpyDeviceToHost, s));
+    if (grad_host) PPE_CUDA_TRY(cudaMemcpyAsync(grad_host, n->grads, n->nparams * 4, cudaMemcpyDeviceToHost, s));
+    PPE_CUDA_TRY(cudaStreamSynchronize(s));
+    if (loss_out) *loss_out = acc[0] / ((double)batch * g->nx * g->ny);
+    return PPE_OK;
+}
+
+ppe_status net_train_step(ppe_net *n, ppe_grid *g, int batch, const float *R, const ppe_train_hparams *hp,
+                          void *stream, double *loss_out)
+{
+    clear_error();
+    if (!hp || !(hp->lr0 >= 0.0) || hp->total_steps < 1 || !(hp->rho >= 0.0)) {
+        set_error("net_train_step: bad hyper-parameters");
+        return PPE_ERR_ARG;
+    }
+    NetCache *c;
+    TrainWs *w;
+    PPE_TRY(train_prep(n, g, batch, R, &c, &w));
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t np = n->nparams;
+    PPE_CUDA_TRY(cudaMemsetAsync(w->acc, 0, 2 * sizeof(double), s));
+    PPE_TRY(loss_and_grad(n, c, w, g, batch, R, n->params, n->grads, s));
+    double loss_sum = 0.0;
+    PPE_CUDA_TRY(cudaMemcpyAsync(&loss_sum, w->acc, sizeof(double), cudaMemcpyDeviceToHost, s));
+    const float *gfinal = n->grads;
+    if (hp->rho > 0.0) {
+        sumsq_kernel<<<g1d(np), 256, 0, s>>>(n->grads, np, w->acc + 1);
+        perturb_kernel<<<g1d(np), 256, 0, s>>>(n->params, n->grads, n->params_pert, np, hp->rho, w->acc + 1);
+        PPE_TRY(loss_and_grad(n, c, w, g, batch, R, n->params_pert, n->grads2, s));
+        gfinal = n->grads2;
+    }
+    const double t = (double)n->step;
+    const double lr = 0.5 * hp->lr0 * (1.0 + std::cos(3.141592653589793 * std::min(t, (double)hp->total_steps) / hp->total_steps));
+    const double bc1 = 1.0 - std::pow(hp->beta1, t + 1.0), bc2 = 1.0 - std::pow(hp->beta2, t + 1.0);
+    adam_kernel<<<g1d(np), 256, 0, s>>>(n->params, gfinal, n->adam_m, n->adam_v, np, (float)lr, (float)hp->beta1,
+                                       (float)hp->beta2, (float)hp->eps, (float)bc1, (float)bc2);
+    PPE_CUDA_TRY(cudaGetLastError());
+    PPE_CUDA_TRY(cudaStreamSynchronize(s));
+    n->step++;
+    n->version++;          // caches (packed weights, eta, trunk) follow the new parameters
+    if (loss_out) *loss_out = loss_sum / ((double)batch * g->nx * g->ny);
+    return PPE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,108 @@
+"""The network's training path on the GPU against the FP64 network oracle.
+
+Loss (Eq. 18) and gradients come from the hand-written forward/backward
+kernels with BF16 activations and weights (relative rounding 2^-9 per
+layer) and FP32 accumulation, so the bars are those of a BF16 network: loss
+within 2e-2 relative, whole-gradient relative L2 error within 5e-2 and
+cosine >= 0.995, and the direction of every parameter tensor with a
+non-negligible gradient within cosine 0.98.  One SAM + Adam step moves every
+parameter whose gradient is large in the same direction as the oracle's step.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from oracle import net_oracle as N  # noqa: E402
+from paper_2604_01800_gb300 import inputs as I  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_01800_gb300 import api as A
+    return A
+
+
+TINY = I.NetConfig(widths=(16, 32), c_last=8, trunk=(16, 24), phi_hidden=4)
+
+
+def _setup(api, cfg, nx, ny, B, seed):
+    P = I.net_params(cfg, seed, phi_scale=0.5)
+    g = I.rng(seed + 1)
+    for k in P:
+        if k.endswith(".b"):
+            P[k] = (0.05 * g.standard_normal(P[k].shape)).astype(np.float32)
+    c = api.net_default_config(widths=list(cfg.widths), c_last=cfg.c_last, trunk_hidden=list(cfg.trunk),
+                               phi_hidden=cfg.phi_hidden, mesh_conv=int(cfg.mesh_conv))
+    net = api.net_create(c, 1)
+    net.set_params(api.flatten_params(P, cfg))
+    dx, dy = I.random_spacing(nx, g), I.random_spacing(ny, g)
+    R = np.stack([I.training_rhs(dx, dy, g) for _ in range(B)])
+    R = -R * np.outer(dy, dx)[None]                       # scaled right-hand sides b = -V S
+    R /= np.linalg.norm(R.reshape(B, -1), axis=1)[:, None, None]   # unit norm (Eq. 14)
+    R = R.astype(np.float32)
+    grid = api.ppe_create_grid(dx, dy)
+    net.attach(grid)
+    return net, P, grid, dx, dy, R
+
+
+def _oracle_loss_grad(P, cfg, dx, dy, R):
+    geo = N.Geometry(dx, dy, cfg.levels)
+    A = oracle.CSR(dx, dy)
+    return N.loss_and_grads(P, geo, A, R.astype(np.float64), cfg.widths, cfg.mesh_conv, len(cfg.trunk) + 1)
+
+
+@pytest.mark.parametrize("cfgname,nx,ny,B", [("tiny", 29, 21, 2), ("tiny", 32, 32, 1), ("full", 32, 48, 1)])
+def test_loss_and_gradient_match_oracle(api, cfgname, nx, ny, B):
+    cfg = TINY if cfgname == "tiny" else I.NetConfig()
+    net, P, grid, dx, dy, R = _setup(api, cfg, nx, ny, B, 7)
+    loss, g = net.loss_grad(grid, torch.tensor(R, dtype=torch.float32, device="cuda"))
+    Lo, go = _oracle_loss_grad(P, cfg, dx, dy, R)
+    assert abs(loss - Lo) <= 2e-2 * abs(Lo), (loss, Lo)
+    G = api.unflatten_params(g, cfg)
+    flat_o = np.concatenate([go[k].reshape(-1) for k in I.net_param_shapes(cfg)])
+    rel = np.linalg.norm(g - flat_o) / np.linalg.norm(flat_o)
+    cos = g @ flat_o / np.linalg.norm(g) / np.linalg.norm(flat_o)
+    assert rel <= 5e-2 and cos >= 0.995, (rel, cos)
+    big = np.linalg.norm(flat_o) * 1e-3
+    for k in I.net_param_shapes(cfg):
+        a, b = G[k].reshape(-1).astype(np.float64), go[k].reshape(-1)
+        if np.linalg.norm(b) > big and b.size > 1:
+            c = a @ b / (np.linalg.norm(a) * np.linalg.norm(b) + 1e-300)
+            assert c >= 0.98, (k, c)
+
+
+def test_train_step_matches_oracle_direction(api):
+    cfg = TINY
+    net, P, grid, dx, dy, R = _setup(api, cfg, 32, 24, 2, 11)
+    hp = dict(lr0=1e-3, total=100, rho=2e-4, beta1=0.9, beta2=0.999, eps=1e-8)
+    before = net.get_params()
+    loss = net.train_step(grid, torch.tensor(R, dtype=torch.float32, device="cuda"),
+                          lr0=hp["lr0"], total_steps=hp["total"], rho=hp["rho"])
+    after = net.get_params()
+    assert net.step == 1
+    geo = N.Geometry(dx, dy, cfg.levels)
+    A = oracle.CSR(dx, dy)
+    L0, Pn, st = N.sam_adam_step(P, N.adam_init(P), geo, A, R.astype(np.float64), cfg.widths, hp, True,
+                                 len(cfg.trunk) + 1)
+    assert abs(loss - L0) <= 2e-2 * abs(L0)
+    d_gpu = after - before
+    d_or = np.concatenate([(Pn[k] - P[k].astype(np.float64)).reshape(-1) for k in I.net_param_shapes(cfg)])
+    m = np.concatenate([st["m"][k].reshape(-1) for k in I.net_param_shapes(cfg)])
+    big = np.abs(m) >= 1e-2 * np.abs(m).max()         # entries the step is sure about
+    agree = np.mean(np.sign(d_gpu[big]) == np.sign(d_or[big]))
+    assert agree >= 0.99, agree
+    assert np.allclose(np.abs(d_gpu[big]), hp["lr0"], rtol=0.05)   # first Adam step: |delta| ~ lr
+
+
+def test_training_reduces_loss(api):
+    net, P, grid, dx, dy, R = _setup(api, TINY, 32, 32, 4, 13)
+    Rt = torch.tensor(R, dtype=torch.float32, device="cuda")
+    losses = [net.train_step(grid, Rt, lr0=2e-3, total_steps=60, rho=2e-4) for _ in range(60)]
+    assert losses[-1] < 0.5 * losses[0], (losses[0], losses[-1])
+    assert all(np.isfinite(losses))
