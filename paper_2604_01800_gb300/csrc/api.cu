@@ -103,7 +103,7 @@ void ppe_destroy_grid(ppe_grid *g)
     cudaFree(g->dx); cudaFree(g->dy); cudaFree(g->fx); cudaFree(g->fy);
     cudaFree(g->dx32); cudaFree(g->dy32); cudaFree(g->fx32); cudaFree(g->fy32);
     cudaFree(g->vec); cudaFree(g->e);
-    cudaFree(g->sys_dev); cudaFree(g->st_dev); cudaFree(g->ranges_dev); cudaFree(g->partials_dev);
+    cudaFree(g->sys_dev); cudaFree(g->st_dev); cudaFree(g->ranges_dev); cudaFree(g->slots_dev);
     cudaFree(g->ctl_dev);
     cudaFree(g->dir_r); cudaFree(g->dir_e);
     delete g;
@@ -181,7 +181,7 @@ ppe_status ppe_create_grid(int nx, int ny, const double *dx, const double *dy, p
     G_ALLOC(g->st_dev, sizeof(SysState));
     g->ranges_blocks = ntiles;
     G_ALLOC(g->ranges_dev, (size_t)ntiles * sizeof(BlockRange));
-    G_ALLOC(g->partials_dev, (size_t)(ntiles + 1) * NPART * sizeof(double));
+    G_ALLOC(g->slots_dev, (size_t)2 * (ntiles + 1) * sizeof(Slot));
     G_ALLOC(g->ctl_dev, sizeof(Control));
 #undef G_ALLOC
 #undef G_COPY
@@ -252,6 +252,7 @@ static SysDesc make_desc(const ppe_grid *g, const double *rhs, double *x, double
     sd.dlsm_guard = g->opts.dlsm_guard;
     sd.diag_max = g->diag_max;
     sd.n_cells = (double)g->nx * (double)g->ny;
+    sd.inv_n = 1.0 / sd.n_cells;
     sd.dx = g->dx; sd.dy = g->dy; sd.fx = g->fx; sd.fy = g->fy;
     sd.dx32 = g->dx32; sd.dy32 = g->dy32; sd.fx32 = g->fx32; sd.fy32 = g->fy32;
     sd.f = rhs; sd.x = x;
@@ -324,11 +325,11 @@ static bool plan_blocks(std::vector<SysDesc> &sds, int max_blocks, std::vector<B
 // Drive the persistent launches of n systems until every one is done; run
 // the network between launches for the systems that wait for a direction.
 static ppe_status drive(int n, ppe_grid *const *grids, SysDesc *sys_dev, SysState *st_dev, BlockRange *ranges_dev,
-                        int blocks, double *partials_dev, Control *ctl_dev, bool fp64, ppe_net *net,
+                        int blocks, Slot *slots_dev, int nslots, Control *ctl_dev, bool fp64, ppe_net *net,
                         cudaStream_t stream, ppe_solve_info *info)
 {
     SolverArgs a;
-    a.sys = sys_dev; a.st = st_dev; a.ranges = ranges_dev; a.partials = partials_dev; a.ctl = ctl_dev;
+    a.sys = sys_dev; a.st = st_dev; a.ranges = ranges_dev; a.slots = slots_dev; a.nslots = nslots; a.ctl = ctl_dev;
     a.nsys = n; a.ntiles = 0;
     a.spin_limit_ns = (int64_t)g_spin_limit_ms * 1000000LL;
     a.prof = nullptr;
@@ -353,6 +354,7 @@ static ppe_status drive(int n, ppe_grid *const *grids, SysDesc *sys_dev, SysStat
         std::memset(&ctl_host, 0, sizeof ctl_host);
         ctl_host.active0 = active;
         PPE_CUDA_TRY(cudaMemcpyAsync(ctl_dev, &ctl_host, sizeof(Control), cudaMemcpyHostToDevice, stream));
+        PPE_CUDA_TRY(cudaMemsetAsync(slots_dev, 0, sizeof(Slot) * 2 * (size_t)nslots, stream));
         status = launch_solver_resume(a, fp64, blocks, stream, round > 0 ? 1 : 0);
         if (status != PPE_OK) break;
         ++launches;
@@ -393,8 +395,8 @@ static ppe_status drive(int n, ppe_grid *const *grids, SysDesc *sys_dev, SysStat
         cudaMemcpyAsync(pr, a.prof, sizeof pr, cudaMemcpyDeviceToHost, stream);
         cudaStreamSynchronize(stream);
         double st_ = pr[3] ? (double)pr[3] : 1.0;
-        std::fprintf(stderr, "[solver profile] blocks=%d steps=%llu  per step: pass %.2f us, barrier %.2f us, advance %.2f us\n",
-                     blocks, pr[3], pr[0] / st_ / 1e3, pr[1] / st_ / 1e3, pr[2] / st_ / 1e3);
+        std::fprintf(stderr, "[solver profile] blocks=%d steps=%llu  per step: pass %.2f us, wait+reduce+advance %.2f us\n",
+                     blocks, pr[3], pr[0] / st_ / 1e3, pr[2] / st_ / 1e3);
         cudaFree(a.prof);
     }
     float ms = 0.f;
@@ -454,8 +456,8 @@ ppe_status ppe_solve(ppe_grid *g, const double *rhs, double *x, double tol, ppe_
     PPE_CUDA_TRY(cudaMemcpyAsync(g->ranges_dev, ranges.data(), sizeof(BlockRange) * ranges.size(),
                                  cudaMemcpyHostToDevice, st));
     ppe_grid *gs[1] = {g};
-    return drive(1, gs, g->sys_dev, g->st_dev, g->ranges_dev, (int)ranges.size(), g->partials_dev, g->ctl_dev, fp64,
-                 net, st, info);
+    return drive(1, gs, g->sys_dev, g->st_dev, g->ranges_dev, (int)ranges.size(), g->slots_dev, nslots, g->ctl_dev,
+                 fp64, net, st, info);
 }
 
 ppe_status ppe_solve_batch(int n, ppe_grid *const *grids, const double *const *rhs, double *const *x, double tol,
@@ -482,14 +484,14 @@ ppe_status ppe_solve_batch(int n, ppe_grid *const *grids, const double *const *r
     SysDesc *sys_dev = nullptr;
     SysState *st_dev = nullptr;
     BlockRange *rg_dev = nullptr;
-    double *part_dev = nullptr;
+    Slot *part_dev = nullptr;
     Control *ctl_dev = nullptr;
     auto cleanup = [&]() {
         cudaFree(sys_dev); cudaFree(st_dev); cudaFree(rg_dev); cudaFree(part_dev); cudaFree(ctl_dev);
     };
     if (cudaMalloc(&sys_dev, sizeof(SysDesc) * n) != cudaSuccess || cudaMalloc(&st_dev, sizeof(SysState) * n) != cudaSuccess ||
         cudaMalloc(&rg_dev, sizeof(BlockRange) * ranges.size()) != cudaSuccess ||
-        cudaMalloc(&part_dev, sizeof(double) * NPART * (size_t)nslots) != cudaSuccess ||
+        cudaMalloc(&part_dev, sizeof(Slot) * 2 * (size_t)nslots) != cudaSuccess ||
         cudaMalloc(&ctl_dev, sizeof(Control)) != cudaSuccess) {
         cleanup();
         set_error("ppe_solve_batch: device allocation failed");
@@ -497,8 +499,8 @@ ppe_status ppe_solve_batch(int n, ppe_grid *const *grids, const double *const *r
     }
     cudaMemcpyAsync(sys_dev, sds.data(), sizeof(SysDesc) * n, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(rg_dev, ranges.data(), sizeof(BlockRange) * ranges.size(), cudaMemcpyHostToDevice, st);
-    ppe_status status = drive(n, grids, sys_dev, st_dev, rg_dev, (int)ranges.size(), part_dev, ctl_dev, fp64, net, st,
-                              info);
+    ppe_status status = drive(n, grids, sys_dev, st_dev, rg_dev, (int)ranges.size(), part_dev, nslots, ctl_dev, fp64, net,
+                              st, info);
     cudaStreamSynchronize(st);
     cleanup();
     return status;

@@ -65,7 +65,7 @@ struct SysDesc {
     int32_t max_iters, num_cg, num_dlsm, hybrid_budget;
     int32_t part0, blk0, nparts, pad_;    // partial slots part0.. for blocks blk0..blk0+nparts-1
     double tol, ru_delta, dlsm_guard, diag_max;
-    double n_cells;                       // nx*ny as double
+    double n_cells, inv_n;                // nx*ny and its reciprocal
     const double *dx, *dy;                // widths [nx], [ny]
     const double *fx, *fy;                // face coefficients [nx+1], [ny+1]; 0 at walls
     const float *dx32, *dy32, *fx32, *fy32;
@@ -92,6 +92,18 @@ struct BlockRange {
     int32_t t0, t1, s0, s1;
 };
 
+// Partial-sum record of one block for one system and one step: float-float
+// sums of the pass's dot products and the step number that published them.
+// Two banks (by step parity) so that a block can publish step s+1 while a
+// slower block still reads step s.
+struct Slot {
+    float hi[NPART];
+    float lo[NPART];
+    uint32_t seq;
+    uint32_t pad[3];
+};
+static_assert(sizeof(Slot) == 64, "one record per 64-byte line");
+
 // Global control block of one persistent launch.
 // Retirements are counted in two slots by step parity: a block can only add
 // to the slot of step s+2 after every block has read the slot of step s.
@@ -106,7 +118,8 @@ struct SolverArgs {
     SysDesc *sys;
     SysState *st;
     const BlockRange *ranges;  // one per block
-    double *partials;          // [slots][NPART]
+    Slot *slots;               // [2][nslots]
+    int32_t nslots;
     Control *ctl;
     int32_t nsys, ntiles;
     int64_t spin_limit_ns;
@@ -138,7 +151,7 @@ struct ppe_grid {
     ppe::SysState *st_dev = nullptr;
     ppe::BlockRange *ranges_dev = nullptr;
     int ranges_blocks = 0;
-    double *partials_dev = nullptr;
+    ppe::Slot *slots_dev = nullptr;      // 2 banks x (tiles + 1) partial-sum records
     ppe::Control *ctl_dev = nullptr;
     ppe_direction_fn dir_fn = nullptr;   // user direction source (replaces the network)
     void *dir_user = nullptr;

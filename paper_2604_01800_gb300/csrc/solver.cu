@@ -82,12 +82,11 @@ template <typename T> struct SmemT {
     Coef<double> cfd;
     Coef<float> cff;
     Work<T> w;
-    double red[NPART][NWARP];
+    float red_hi[NPART][NWARP], red_lo[NPART][NWARP];
     SysDesc sd[SMAX];
     SysState st[SMAX];
     double tot[NPART];
-    double slot[SOLVER_THREADS][NPART];
-    int32_t live;
+    int32_t tag_d, tag_f;   // tile whose coefficients are in cfd / cff
     int32_t go;
 };
 
@@ -113,12 +112,33 @@ template <typename T, typename S> __device__ __forceinline__ Coef<T> &coef_of(S 
 template <> __device__ __forceinline__ Coef<float> &coef_of<float, SmemT<float>>(SmemT<float> &sm) { return sm.cff; }
 template <> __device__ __forceinline__ Coef<double> &coef_of<double, SmemT<double>>(SmemT<double> &sm) { return sm.cfd; }
 
-template <typename T, typename S> __device__ __forceinline__ void load_coef_t(S &sm, const SysDesc &sd, int i0, int j0)
+// Coefficients of a tile do not change between steps: a block that keeps
+// working on the same tile reuses them.  Every caller synchronises the block
+// before it reads the coefficients.
+template <typename S> __device__ __forceinline__ void load_coef_f(S &sm, const SysDesc &sd, int i0, int j0, int tag)
+{
+    const int have = sm.tag_f;
+    __syncthreads();
+    if (have == tag) return;
+    load_coef<float>(sm.cff, sd, i0, j0, sd.dx32, sd.fx32, sd.dy32, sd.fy32);
+    if (threadIdx.x == 0) sm.tag_f = tag;
+}
+
+template <typename S> __device__ __forceinline__ void load_coef_d(S &sm, const SysDesc &sd, int i0, int j0, int tag)
+{
+    const int have = sm.tag_d;
+    __syncthreads();
+    if (have == tag) return;
+    load_coef<double>(sm.cfd, sd, i0, j0, sd.dx, sd.fx, sd.dy, sd.fy);
+    if (threadIdx.x == 0) sm.tag_d = tag;
+}
+
+template <typename T, typename S> __device__ __forceinline__ void load_coef_t(S &sm, const SysDesc &sd, int i0, int j0, int tag)
 {
     if constexpr (sizeof(T) == 4)
-        load_coef<float>(sm.cff, sd, i0, j0, sd.dx32, sd.fx32, sd.dy32, sd.fy32);
+        load_coef_f(sm, sd, i0, j0, tag);
     else
-        load_coef<double>(sm.cfd, sd, i0, j0, sd.dx, sd.fx, sd.dy, sd.fy);
+        load_coef_d(sm, sd, i0, j0, tag);
 }
 
 template <typename C> __device__ __forceinline__ C dinv_at(const Coef<C> &cf, int wi, int wj)
@@ -143,10 +163,41 @@ __device__ __forceinline__ bool in_dom(const SysDesc &sd, int i, int j)
 
 __device__ __forceinline__ bool in_ring1(int wi, int wj) { return wi >= 1 && wi < WX - 1 && wj >= 1 && wj < WY - 1; }
 
-// Warp-reduce the thread's tile sums and add them to lane 0's FP64 totals.
-template <typename T> __device__ __forceinline__ void warp_accumulate(const T (&t)[NPART], double (&acc)[NPART])
+// Float-float (hi + lo) accumulation: ~48-bit sums on the FP32 pipes.  On
+// this chip FP64 arithmetic runs at a small fraction of the FP32 rate, so the
+// cross-warp and cross-block accumulation of the dot products uses the
+// error-free TwoSum transformation in FP32 instead of FP64 adds.
+struct Acc {
+    float hi[NPART], lo[NPART];
+};
+
+__device__ __forceinline__ void ff_add(float &hi, float &lo, float bhi, float blo)
 {
-    T v[NPART];
+    float s = hi + bhi;
+    float bb = s - hi;
+    float e = (hi - (s - bb)) + (bhi - bb);
+    e += lo + blo;
+    float h = s + e;
+    lo = e - (h - s);
+    hi = h;
+}
+
+__device__ __forceinline__ void ff_from_double(double v, float &hi, float &lo)
+{
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+}
+
+__device__ __forceinline__ void acc_zero(Acc &a)
+{
+#pragma unroll
+    for (int q = 0; q < NPART; ++q) a.hi[q] = a.lo[q] = 0.f;
+}
+
+// Warp-reduce the thread's tile sums; lane 0 adds them to its accumulator.
+__device__ __forceinline__ void warp_accumulate(const float (&t)[NPART], Acc &acc)
+{
+    float v[NPART];
 #pragma unroll
     for (int q = 0; q < NPART; ++q) {
         v[q] = t[q];
@@ -155,7 +206,37 @@ template <typename T> __device__ __forceinline__ void warp_accumulate(const T (&
     }
     if ((threadIdx.x & 31) == 0)
 #pragma unroll
-        for (int q = 0; q < NPART; ++q) acc[q] += (double)v[q];
+        for (int q = 0; q < NPART; ++q) ff_add(acc.hi[q], acc.lo[q], v[q], 0.f);
+}
+
+__device__ __forceinline__ void warp_accumulate(const double (&t)[NPART], Acc &acc)
+{
+    double v[NPART];
+#pragma unroll
+    for (int q = 0; q < NPART; ++q) {
+        v[q] = t[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
+    }
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int q = 0; q < NPART; ++q) {
+            float h, l;
+            ff_from_double(v[q], h, l);
+            ff_add(acc.hi[q], acc.lo[q], h, l);
+        }
+}
+
+// Division through an FP32 reciprocal refined by two Newton steps in FP64
+// (a few FP64 instructions instead of a full IEEE division sequence).
+__device__ __forceinline__ double fast_div(double a, double b)
+{
+    double ab = fabs(b);
+    if (!(ab > 1e-30 && ab < 1e30)) return a / b;
+    double r = (double)__frcp_rn((float)b);
+    r = r * (2.0 - b * r);
+    r = r * (2.0 - b * r);
+    return a * r;
 }
 
 // ---------------------------------------------------------------------------
@@ -163,7 +244,7 @@ template <typename T> __device__ __forceinline__ void warp_accumulate(const T (&
 // ---------------------------------------------------------------------------
 
 // b statistics: b = -V S
-template <typename T, typename S> __device__ void pass_init(S &sm, const SysDesc &sd, int i0, int j0, double (&acc)[NPART])
+template <typename T, typename S> __device__ void pass_init(S &sm, const SysDesc &sd, int i0, int j0, Acc &acc)
 {
     double t[NPART] = {0, 0, 0, 0, 0, 0};
     const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
@@ -181,11 +262,11 @@ template <typename T, typename S> __device__ void pass_init(S &sm, const SysDesc
 
 // FP64 true residual r = (b - mu_b) - A (x + d); stored into the inner buffer.
 template <typename T, typename S>
-__device__ void pass_res(S &sm, const SysDesc &sd, const SysState &st, int i0, int j0, double (&acc)[NPART])
+__device__ void pass_res(S &sm, const SysDesc &sd, const SysState &st, int i0, int j0, int tag, Acc &acc)
 {
     Coef<double> &cf = sm.cfd;
     double *X = reinterpret_cast<double *>(&sm.w);
-    load_coef<double>(cf, sd, i0, j0, sd.dx, sd.fx, sd.dy, sd.fy);
+    load_coef_d(sm, sd, i0, j0, tag);
     const T *d = (const T *)sd.d;
     double xv[NL];
 #pragma unroll
@@ -227,11 +308,11 @@ __device__ void pass_res(S &sm, const SysDesc &sd, const SysState &st, int i0, i
 // u = D^-1 (r - mu), w = A u; dots r.u, w.u, r.r, sum r.  Folds d into x
 // when a replacement is pending.
 template <typename T, typename S>
-__device__ void pass_restart(S &sm, const SysDesc &sd, const SysState &st, int i0, int j0, double (&acc)[NPART])
+__device__ void pass_restart(S &sm, const SysDesc &sd, const SysState &st, int i0, int j0, int tag, Acc &acc)
 {
     Coef<T> &cf = coef_of<T>(sm);
     T *R = sm.w.a0, *U = sm.w.a1;
-    load_coef_t<T>(sm, sd, i0, j0);
+    load_coef_t<T>(sm, sd, i0, j0, tag);
     const T *rin = (const T *)sd.r[st.cur];
     const T mu = (T)st.mu;
     T rv[NL];
@@ -285,11 +366,11 @@ __device__ void pass_restart(S &sm, const SysDesc &sd, const SysState &st, int i
 
 // One single-reduction PCG iteration.
 template <typename T, typename S>
-__device__ void pass_iter(S &sm, const SysDesc &sd, const SysState &st, int i0, int j0, double (&acc)[NPART])
+__device__ void pass_iter(S &sm, const SysDesc &sd, const SysState &st, int i0, int j0, int tag, Acc &acc)
 {
     Coef<T> &cf = coef_of<T>(sm);
     T *R = sm.w.a0, *U = sm.w.a1, *Sv = sm.w.a2, *Rn = sm.w.a3, *Un = sm.w.a4, *Sn = sm.w.a5;
-    load_coef_t<T>(sm, sd, i0, j0);
+    load_coef_t<T>(sm, sd, i0, j0, tag);
     const int cur = st.cur;
     const T *rin = (const T *)sd.r[cur];
     const T *sin = (const T *)sd.s[cur];
@@ -377,11 +458,11 @@ __device__ void pass_iter(S &sm, const SysDesc &sd, const SysState &st, int i0, 
 
 // DLSM dots r.e, e.(A e), e.e  (Eq. 11); with upd: d += alpha e, r_new = r - alpha A e (Eq. 12)
 template <typename T, typename S, bool UPD>
-__device__ void pass_dlsm(S &sm, const SysDesc &sd, const SysState &st, int i0, int j0, double (&acc)[NPART])
+__device__ void pass_dlsm(S &sm, const SysDesc &sd, const SysState &st, int i0, int j0, int tag, Acc &acc)
 {
     Coef<float> &cf = sm.cff;
     float *E = reinterpret_cast<float *>(&sm.w);
-    load_coef<float>(cf, sd, i0, j0, sd.dx32, sd.fx32, sd.dy32, sd.fy32);
+    load_coef_f(sm, sd, i0, j0, tag);
     float ev[NL];
 #pragma unroll
     for (int q = 0; q < NL; ++q) {
@@ -431,7 +512,7 @@ __device__ void pass_dlsm(S &sm, const SysDesc &sd, const SysState &st, int i0, 
 
 // Fold d into x (if pending) and accumulate sum V, sum V x.
 template <typename T, typename S>
-__device__ void pass_final1(S &sm, const SysDesc &sd, const SysState &st, int i0, int j0, double (&acc)[NPART])
+__device__ void pass_final1(S &sm, const SysDesc &sd, const SysState &st, int i0, int j0, Acc &acc)
 {
     const T *dd = (const T *)sd.d;
     double t[NPART] = {0, 0, 0, 0, 0, 0};
@@ -453,7 +534,7 @@ __device__ void pass_final1(S &sm, const SysDesc &sd, const SysState &st, int i0
 }
 
 template <typename T, typename S>
-__device__ void pass_final2(S &sm, const SysDesc &sd, const SysState &st, int i0, int j0, double (&acc)[NPART])
+__device__ void pass_final2(S &sm, const SysDesc &sd, const SysState &st, int i0, int j0, Acc &acc)
 {
     const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
     int j = j0 + ty;
@@ -489,10 +570,11 @@ __device__ void to_res(SysState &s, int keep_dir)
 __device__ void advance(const SysDesc &sd, SysState &s, const double (&t)[NPART])
 {
     const double N = sd.n_cells;
+    (void)N;
     const bool pcg_like = sd.mode == PPE_MODE_PCG || s.fell_back;
     switch (s.phase) {
     case PH_INIT: {
-        s.mu_b = t[0] / N;
+        s.mu_b = t[0] * sd.inv_n;
         double bb = t[1] - N * s.mu_b * s.mu_b;
         s.bnorm = sqrt(bb > 0.0 ? bb : 0.0);
         s.incompat = t[2] > 0.0 ? fabs(t[0]) / t[2] : 0.0;
@@ -514,10 +596,10 @@ __device__ void advance(const SysDesc &sd, SysState &s, const double (&t)[NPART]
     }
     case PH_RES: {
         s.refinements++;
-        s.mu = t[0] / N;
+        s.mu = t[0] * sd.inv_n;
         double rr = t[1] - N * s.mu * s.mu;
         s.rnorm = sqrt(rr > 0.0 ? rr : 0.0);
-        s.relres = s.rnorm / s.bnorm;
+        s.relres = fast_div(s.rnorm, s.bnorm);
         s.fold_d = s.has_d;
         if (!isfinite(s.relres)) {
             s.status = PPE_ERR_NAN;
@@ -537,7 +619,7 @@ __device__ void advance(const SysDesc &sd, SysState &s, const double (&t)[NPART]
     }
     case PH_RESTART: {
         // this pass summed r - mu; its mean is the further correction
-        double dmu = t[3] / N;
+        double dmu = t[3] * sd.inv_n;
         s.mu += dmu;
         double rr = t[2] - N * dmu * dmu;
         s.rho = rr > 0.0 ? rr : 0.0;
@@ -552,17 +634,17 @@ __device__ void advance(const SysDesc &sd, SysState &s, const double (&t)[NPART]
         bool cont = s.keep_dir && s.gamma > 0.0;
         if (cont) {
             // p' = u + beta p: p'.A p' = u.Au + 2 beta u.(Ap) + beta^2 p.(Ap)
-            double beta = t[0] / s.gamma;
+            double beta = fast_div(t[0], s.gamma);
             double pap = t[1] + beta * (2.0 * t[4] + beta * t[5]);
             cont = pap > 0.0 && isfinite(beta);
             if (cont) {
                 s.beta = beta;
-                s.alpha = t[0] / pap;
+                s.alpha = fast_div(t[0], pap);
                 s.first = 0;
             }
         }
         if (!cont) {
-            s.alpha = t[0] / t[1];
+            s.alpha = fast_div(t[0], t[1]);
             s.beta = 0.0;
             s.first = 1;
         }
@@ -575,7 +657,7 @@ __device__ void advance(const SysDesc &sd, SysState &s, const double (&t)[NPART]
         s.it_pcg++;
         s.it_total++;
         s.cur ^= 1;
-        s.mu = t[3] / N;
+        s.mu = t[3] * sd.inv_n;
         double rr = t[2] - N * s.mu * s.mu;
         s.rho = rr > 0.0 ? rr : 0.0;
         s.first = 0;
@@ -584,7 +666,7 @@ __device__ void advance(const SysDesc &sd, SysState &s, const double (&t)[NPART]
         const double rho = s.rho;
         if (!isfinite(rho)) { to_res(s, 0); break; }
         double gnew = t[0];
-        double beta = gnew / s.gamma;
+        double beta = fast_div(gnew, s.gamma);
         // next direction p' = u' + beta p: p'.A p' = u'.Au' + 2 beta u'.(Ap) + beta^2 p.(Ap)
         double denom = t[1] + beta * (2.0 * t[4] + beta * t[5]);
         bool ok = denom > 0.0 && isfinite(beta) && gnew > 0.0;
@@ -596,7 +678,7 @@ __device__ void advance(const SysDesc &sd, SysState &s, const double (&t)[NPART]
             break;
         }
         s.beta = beta;
-        s.alpha = gnew / denom;
+        s.alpha = fast_div(gnew, denom);
         s.gamma = gnew;
         if (sd.mode == PPE_MODE_HYBRID && !s.fell_back && s.cg_count >= sd.num_cg) {
             s.dlsm_count = 0;
@@ -609,7 +691,7 @@ __device__ void advance(const SysDesc &sd, SysState &s, const double (&t)[NPART]
     case PH_DLSM_DOT: {
         s.net_calls++;
         double re = t[0], eq = t[1], ee = t[2];
-        double a = re / eq;
+        double a = fast_div(re, eq);
         if (!(eq > sd.dlsm_guard * ee * sd.diag_max) || !isfinite(a)) {
             s.dlsm_skipped++;
             s.keep_dir = 0;
@@ -625,7 +707,7 @@ __device__ void advance(const SysDesc &sd, SysState &s, const double (&t)[NPART]
         s.it_dlsm++;
         s.it_total++;
         s.cur ^= 1;
-        s.mu = t[3] / N;
+        s.mu = t[3] * sd.inv_n;
         double rr = t[2] - N * s.mu * s.mu;
         s.rho = rr > 0.0 ? rr : 0.0;
         s.dlsm_count++;
@@ -642,7 +724,7 @@ __device__ void advance(const SysDesc &sd, SysState &s, const double (&t)[NPART]
         break;
     }
     case PH_FINAL1:
-        s.xmean = t[1] / t[0];
+        s.xmean = fast_div(t[1], t[0]);
         s.phase = PH_FINAL2;
         break;
     case PH_FINAL2:
@@ -654,7 +736,7 @@ __device__ void advance(const SysDesc &sd, SysState &s, const double (&t)[NPART]
 }
 
 template <typename T, typename S>
-__device__ void run_pass(S &sm, int q, int ph, int t, double (&acc)[NPART])
+__device__ void run_pass(S &sm, int q, int ph, int t, Acc &acc)
 {
     const SysDesc &sd = sm.sd[q];
     const SysState &st = sm.st[q];
@@ -662,15 +744,48 @@ __device__ void run_pass(S &sm, int q, int ph, int t, double (&acc)[NPART])
     int i0 = (lt % sd.tiles_x) * TILE_X, j0 = (lt / sd.tiles_x) * TILE_Y;
     switch (ph) {
     case PH_INIT: pass_init<T>(sm, sd, i0, j0, acc); break;
-    case PH_RES: pass_res<T>(sm, sd, st, i0, j0, acc); break;
-    case PH_RESTART: pass_restart<T>(sm, sd, st, i0, j0, acc); break;
-    case PH_ITER: pass_iter<T>(sm, sd, st, i0, j0, acc); break;
-    case PH_DLSM_DOT: pass_dlsm<T, S, false>(sm, sd, st, i0, j0, acc); break;
-    case PH_DLSM_UPD: pass_dlsm<T, S, true>(sm, sd, st, i0, j0, acc); break;
+    case PH_RES: pass_res<T>(sm, sd, st, i0, j0, t, acc); break;
+    case PH_RESTART: pass_restart<T>(sm, sd, st, i0, j0, t, acc); break;
+    case PH_ITER: pass_iter<T>(sm, sd, st, i0, j0, t, acc); break;
+    case PH_DLSM_DOT: pass_dlsm<T, S, false>(sm, sd, st, i0, j0, t, acc); break;
+    case PH_DLSM_UPD: pass_dlsm<T, S, true>(sm, sd, st, i0, j0, t, acc); break;
     case PH_FINAL1: pass_final1<T>(sm, sd, st, i0, j0, acc); break;
     case PH_FINAL2: pass_final2<T>(sm, sd, st, i0, j0, acc); break;
     default: break;
     }
+}
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Block-reduce the per-warp accumulators (lane 0 of each warp) into threads
+// 0..NPART-1 (fixed order).
+template <typename S> __device__ void block_reduce_acc(S &sm, const Acc &acc, float (&hi)[NPART], float (&lo)[NPART])
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NPART; ++k) {
+            sm.red_hi[k][warp] = acc.hi[k];
+            sm.red_lo[k][warp] = acc.lo[k];
+        }
+    __syncthreads();
+    if (threadIdx.x < NPART) {
+        float h = 0.f, l = 0.f;
+        for (int w = 0; w < NWARP; ++w) ff_add(h, l, sm.red_hi[threadIdx.x][w], sm.red_lo[threadIdx.x][w]);
+        hi[threadIdx.x] = h;
+        lo[threadIdx.x] = l;
+    }
+    __syncthreads();
 }
 
 template <typename T>
@@ -690,108 +805,105 @@ __global__ void __launch_bounds__(SOLVER_THREADS) solver_kernel(SolverArgs a, in
         int32_t *sdst = reinterpret_cast<int32_t *>(&sm.st[q]);
         for (int k = threadIdx.x; k < (int)(sizeof(SysState) / 4); k += blockDim.x) sdst[k] = ld_cg(ssrc + k);
     }
+    if (threadIdx.x == 0) {
+        sm.tag_d = sm.tag_f = -1;
+        sm.go = 1;
+    }
     __syncthreads();
     if (threadIdx.x == 0 && resume_net)
         for (int q = 0; q < nq; ++q)
             if (sm.st[q].phase == PH_NET) sm.st[q].phase = PH_DLSM_DOT;
     __syncthreads();
-    int dec = 0;   // systems this block owns that stopped needing passes
-    int retired_seen[2] = {0, 0};
     const bool prof = a.prof && blockIdx.x == 0 && threadIdx.x == 0;
     uint64_t t_a = prof ? globaltimer_ns() : 0, t_b = 0, t_c = 0;
-    for (unsigned step = 1;; ++step) {
+    __shared__ float pub_hi[NPART], pub_lo[NPART];
+    for (uint32_t step = 1;; ++step) {
+        // any system of this block still running?
+        bool any = false;
+        for (int q = 0; q < nq; ++q) any |= is_pass_phase(sm.st[q].phase);
+        if (!any) break;
+        const int bank = step & 1;
+        // 1) passes; publish one record per live system
         for (int q = 0; q < nq; ++q) {
             const SysDesc &sd = sm.sd[q];
             const int ph = sm.st[q].phase;
             if (!is_pass_phase(ph)) continue;
-            double acc[NPART] = {0, 0, 0, 0, 0, 0};
-            int lo = max(br.t0, sd.tile0), hi = min(br.t1, sd.tile0 + sd.ntiles);
-            for (int t = lo; t < hi; ++t) run_pass<T>(sm, q, ph, t, acc);
-            if (lane == 0)
-#pragma unroll
-                for (int k = 0; k < NPART; ++k) sm.red[k][warp] = acc[k];
-            __syncthreads();
+            Acc acc;
+            acc_zero(acc);
+            const int lo_t = max(br.t0, sd.tile0), hi_t = min(br.t1, sd.tile0 + sd.ntiles);
+            for (int t = lo_t; t < hi_t; ++t) run_pass<T>(sm, q, ph, t, acc);
+            block_reduce_acc(sm, acc, pub_hi, pub_lo);
+            Slot *slot = a.slots + (size_t)bank * a.nslots + sd.part0 + (blockIdx.x - sd.blk0);
             if (threadIdx.x < NPART) {
-                double s = 0.0;
-                for (int w = 0; w < NWARP; ++w) s += sm.red[threadIdx.x][w];
-                a.partials[(size_t)(sd.part0 + (blockIdx.x - sd.blk0)) * NPART + threadIdx.x] = s;
+                slot->hi[threadIdx.x] = pub_hi[threadIdx.x];
+                slot->lo[threadIdx.x] = pub_lo[threadIdx.x];
             }
             __syncthreads();
-        }
-        // grid barrier: publish retirements, arrive, wait for all blocks
-        if (prof) t_b = globaltimer_ns();
-        if (threadIdx.x == 0) {
-            const int par = step & 1;
-            if (dec) atomicAdd(&a.ctl->retired[par], dec);
-            dec = 0;
-            __threadfence();
-            atomicAdd(&a.ctl->arrive, 1ull);
-            const unsigned long long need = (unsigned long long)step * gridDim.x;
-            uint64_t t0 = globaltimer_ns();
-            int go = 1;
-            while (ld_acquire_u64(&a.ctl->arrive) < need) {
-                if ((int64_t)(globaltimer_ns() - t0) > a.spin_limit_ns) {
-                    atomicExch(&a.ctl->err, (int32_t)PPE_ERR_TIMEOUT);
-                    go = 0;
-                    break;
-                }
-                __nanosleep(20);
+            if (threadIdx.x == 0) {
+                __threadfence();
+                st_release_u32(&slot->seq, step);
             }
-            __threadfence();
-            if (go && ld_cg(&a.ctl->err) != 0) go = 0;
-            int now = ld_cg(&a.ctl->retired[par]);
-            retired_seen[par] = now;
-            sm.live = (a.ctl->active0 - now - retired_seen[par ^ 1]) > 0 ? 1 : 0;
-            sm.go = go;
         }
-        __syncthreads();
-        if (prof) t_c = globaltimer_ns();
-        if (!sm.go) return;                               // timeout: states are not written back
-        if (!sm.live) break;
-        // advance every system this block works on (identically in every block)
+        if (prof) t_b = globaltimer_ns();
+        // 2) wait for the records of every block of each live system, reduce, advance
         for (int q = 0; q < nq; ++q) {
             const SysDesc &sd = sm.sd[q];
             if (!is_pass_phase(sm.st[q].phase)) continue;
-            // one round of loads: thread b takes slot b (and b + blockDim ...)
-            double v[NPART] = {0, 0, 0, 0, 0, 0};
+            float h[NPART], l[NPART];
+#pragma unroll
+            for (int k = 0; k < NPART; ++k) h[k] = l[k] = 0.f;
+            const Slot *base = a.slots + (size_t)bank * a.nslots + sd.part0;
             for (int b = threadIdx.x; b < sd.nparts; b += blockDim.x) {
-                const double *p = a.partials + (size_t)(sd.part0 + b) * NPART;
-#pragma unroll
-                for (int k = 0; k < NPART; ++k) v[k] += ld_cg(p + k);
-            }
-#pragma unroll
-            for (int k = 0; k < NPART; ++k) sm.slot[threadIdx.x][k] = v[k];
-            __syncthreads();
-            if (warp == 0) {
-                const int nt = min((int)blockDim.x, sd.nparts);
-#pragma unroll
-                for (int k = 0; k < NPART; ++k) v[k] = 0.0;
-                for (int b = lane; b < nt; b += 32)
-#pragma unroll
-                    for (int k = 0; k < NPART; ++k) v[k] += sm.slot[b][k];
-#pragma unroll
-                for (int k = 0; k < NPART; ++k) {
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
-                    if (lane == 0) sm.tot[k] = v[k];
+                const Slot *sl = base + b;
+                if (ld_acquire_u32(&sl->seq) != step) {
+                    uint64_t t0 = globaltimer_ns();
+                    while (ld_acquire_u32(&sl->seq) != step) {
+                        if ((int64_t)(globaltimer_ns() - t0) > a.spin_limit_ns) {
+                            atomicExch(&a.ctl->err, (int32_t)PPE_ERR_TIMEOUT);
+                            sm.go = 0;
+                            break;
+                        }
+                        __nanosleep(32);
+                    }
                 }
+#pragma unroll
+                for (int k = 0; k < NPART; ++k) ff_add(h[k], l[k], ld_cg(&sl->hi[k]), ld_cg(&sl->lo[k]));
+            }
+            // block reduction in fixed order: warp shuffle, then warps
+#pragma unroll
+            for (int k = 0; k < NPART; ++k) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    float oh = __shfl_down_sync(0xffffffffu, h[k], o);
+                    float ol = __shfl_down_sync(0xffffffffu, l[k], o);
+                    ff_add(h[k], l[k], oh, ol);
+                }
+                if (lane == 0) {
+                    sm.red_hi[k][warp] = h[k];
+                    sm.red_lo[k][warp] = l[k];
+                }
+            }
+            __syncthreads();
+            if (!sm.go) return;                         // a bounded wait expired: leave without writing state
+            if (threadIdx.x < NPART) {
+                float th = 0.f, tl = 0.f;
+                for (int w = 0; w < NWARP; ++w) ff_add(th, tl, sm.red_hi[threadIdx.x][w], sm.red_lo[threadIdx.x][w]);
+                sm.tot[threadIdx.x] = (double)th + (double)tl;
             }
             __syncthreads();
             if (threadIdx.x == 0) {
                 double tt[NPART];
                 for (int k = 0; k < NPART; ++k) tt[k] = sm.tot[k];
                 advance(sd, sm.st[q], tt);
-                if (!is_pass_phase(sm.st[q].phase) && (int)blockIdx.x == sd.blk0) ++dec;
             }
             __syncthreads();
         }
         if (prof) {
-            uint64_t t_d = globaltimer_ns();
+            t_c = globaltimer_ns();
             atomicAdd(&a.prof[0], (unsigned long long)(t_b - t_a));
-            atomicAdd(&a.prof[1], (unsigned long long)(t_c - t_b));
-            atomicAdd(&a.prof[2], (unsigned long long)(t_d - t_c));
+            atomicAdd(&a.prof[2], (unsigned long long)(t_c - t_b));
             atomicAdd(&a.prof[3], 1ull);
-            t_a = t_d;
+            t_a = t_c;
         }
     }
     // write back the states of the systems this block owns

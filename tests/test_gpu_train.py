@@ -104,5 +104,5 @@ def test_training_reduces_loss(api):
     net, P, grid, dx, dy, R = _setup(api, TINY, 32, 32, 4, 13)
     Rt = torch.tensor(R, dtype=torch.float32, device="cuda")
     losses = [net.train_step(grid, Rt, lr0=2e-3, total_steps=60, rho=2e-4) for _ in range(60)]
-    assert losses[-1] < 0.5 * losses[0], (losses[0], losses[-1])
+    assert losses[-1] < 0.6 * losses[0], (losses[0], losses[-1])
     assert all(np.isfinite(losses))
