@@ -207,9 +207,13 @@ PPE_API ppe_status net_get_config(const ppe_net *net, ppe_net_config *cfg);
 /* Copy parameters in/out (host FP32 arrays of net_param_count entries). */
 PPE_API ppe_status net_set_params(ppe_net *net, const float *params, int64_t count);
 PPE_API ppe_status net_get_params(const ppe_net *net, float *params, int64_t count);
-/* Binary weights file: magic "PPENET01", config, step, parameters, Adam
- * moments, CRC32.  net_load returns PPE_ERR_FORMAT for a malformed file. */
+/* Binary weights file: magic "PPENET01", version, flags (bit 0: Adam moments
+ * present), config, parameter count, step, parameters, [Adam m, v], CRC32.
+ * net_save writes the moments (to resume training), net_save_params only the
+ * parameters (for inference).  net_load reads either and returns
+ * PPE_ERR_FORMAT for a malformed or corrupted file. */
 PPE_API ppe_status net_save(const ppe_net *net, const char *path);
+PPE_API ppe_status net_save_params(const ppe_net *net, const char *path);
 PPE_API ppe_status net_load(const char *path, ppe_net **out);
 /* Build the per-grid caches (distance maps, eta per layer, trunk features)
  * for this grid; required before net_infer / hybrid solves on it. */

@@ -83,6 +83,7 @@ _SIGS = [
     ("net_set_params", ctypes.c_int, [_P, _P, ctypes.c_int64]),
     ("net_get_params", ctypes.c_int, [_P, _P, ctypes.c_int64]),
     ("net_save", ctypes.c_int, [_P, ctypes.c_char_p]),
+    ("net_save_params", ctypes.c_int, [_P, ctypes.c_char_p]),
     ("net_load", ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(_P)]),
     ("net_attach", ctypes.c_int, [_P, _P]),
     ("net_infer", ctypes.c_int, [_P, _P, _P, _P, _P]),

@@ -214,8 +214,9 @@ class Net:
         check(_lib.load().net_get_params(self.handle, out.ctypes.data_as(ctypes.c_void_p), out.size), "net_get_params")
         return out
 
-    def save(self, path: str):
-        check(_lib.load().net_save(self.handle, path.encode()), "net_save")
+    def save(self, path: str, with_moments: bool = True):
+        fn = _lib.load().net_save if with_moments else _lib.load().net_save_params
+        check(fn(self.handle, path.encode()), "net_save")
 
     def attach(self, grid: Grid):
         check(_lib.load().net_attach(self.handle, grid.handle), "net_attach")

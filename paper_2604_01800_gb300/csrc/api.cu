@@ -330,6 +330,8 @@ static ppe_status drive(int n, ppe_grid *const *grids, SysDesc *sys_dev, SysStat
 {
     SolverArgs a;
     a.sys = sys_dev; a.st = st_dev; a.ranges = ranges_dev; a.slots = slots_dev; a.nslots = nslots; a.ctl = ctl_dev;
+    a.arrive = nullptr;
+    PPE_CUDA_TRY(cudaMallocAsync((void **)&a.arrive, sizeof(uint32_t) * n, stream));
     a.nsys = n; a.ntiles = 0;
     a.spin_limit_ns = (int64_t)g_spin_limit_ms * 1000000LL;
     a.prof = nullptr;
@@ -354,7 +356,7 @@ static ppe_status drive(int n, ppe_grid *const *grids, SysDesc *sys_dev, SysStat
         std::memset(&ctl_host, 0, sizeof ctl_host);
         ctl_host.active0 = active;
         PPE_CUDA_TRY(cudaMemcpyAsync(ctl_dev, &ctl_host, sizeof(Control), cudaMemcpyHostToDevice, stream));
-        PPE_CUDA_TRY(cudaMemsetAsync(slots_dev, 0, sizeof(Slot) * 2 * (size_t)nslots, stream));
+        PPE_CUDA_TRY(cudaMemsetAsync(a.arrive, 0, sizeof(uint32_t) * n, stream));
         status = launch_solver_resume(a, fp64, blocks, stream, round > 0 ? 1 : 0);
         if (status != PPE_OK) break;
         ++launches;
@@ -399,6 +401,7 @@ static ppe_status drive(int n, ppe_grid *const *grids, SysDesc *sys_dev, SysStat
                      blocks, pr[3], pr[0] / st_ / 1e3, pr[2] / st_ / 1e3);
         cudaFree(a.prof);
     }
+    cudaFreeAsync(a.arrive, stream);
     float ms = 0.f;
     cudaEventRecord(ev1, stream);
     cudaEventSynchronize(ev1);

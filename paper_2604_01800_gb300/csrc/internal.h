@@ -35,7 +35,7 @@ ppe_status cuda_status(cudaError_t e, const char *what);
 // tiling of the persistent solver kernel
 // ---------------------------------------------------------------------------
 constexpr int TILE_X = 128;                 // cells per tile row (4 per lane)
-constexpr int TILE_Y = 8;                   // rows per tile (one warp each)
+constexpr int TILE_Y = 16;                  // rows per tile (one warp each)
 constexpr int SOLVER_THREADS = 32 * TILE_Y;
 constexpr int NPART = 6;                    // FP64 partial sums per tile
 constexpr int PITCH_ALIGN = 32;             // inner-vector row pitch (elements)
@@ -99,8 +99,7 @@ struct BlockRange {
 struct Slot {
     float hi[NPART];
     float lo[NPART];
-    uint32_t seq;
-    uint32_t pad[3];
+    uint32_t pad[4];
 };
 static_assert(sizeof(Slot) == 64, "one record per 64-byte line");
 
@@ -120,6 +119,7 @@ struct SolverArgs {
     const BlockRange *ranges;  // one per block
     Slot *slots;               // [2][nslots]
     int32_t nslots;
+    uint32_t *arrive;          // per system: cumulative count of published records
     Control *ctl;
     int32_t nsys, ntiles;
     int64_t spin_limit_ns;

@@ -555,7 +555,7 @@ ppe_status net_get_params(const ppe_net *n, float *params, int64_t count)
     return PPE_OK;
 }
 
-ppe_status net_save(const ppe_net *n, const char *path)
+static ppe_status save_impl(const ppe_net *n, const char *path, bool with_moments)
 {
     clear_error();
     if (!n || !path) { set_error("net_save: NULL argument"); return PPE_ERR_ARG; }
@@ -566,12 +566,14 @@ ppe_status net_save(const ppe_net *n, const char *path)
         buf.insert(buf.end(), c, c + k);
     };
     const char magic[8] = {'P', 'P', 'E', 'N', 'E', 'T', '0', '1'};
-    uint32_t version = 1;
-    put(magic, 8); put(&version, 4); put(&n->cfg, sizeof(ppe_net_config));
+    uint32_t version = 1, flags = with_moments ? 1u : 0u;
+    put(magic, 8); put(&version, 4); put(&flags, 4); put(&n->cfg, sizeof(ppe_net_config));
     int64_t np = n->nparams, step = n->step;
     put(&np, 8); put(&step, 8);
     std::vector<float> tmp(np);
-    for (float *src : {n->params, n->adam_m, n->adam_v}) {
+    std::vector<float *> arrays = {n->params};
+    if (with_moments) { arrays.push_back(n->adam_m); arrays.push_back(n->adam_v); }
+    for (float *src : arrays) {
         PPE_CUDA_TRY(cudaMemcpy(tmp.data(), src, np * 4, cudaMemcpyDeviceToHost));
         put(tmp.data(), np * 4);
     }
@@ -585,6 +587,9 @@ ppe_status net_save(const ppe_net *n, const char *path)
     return PPE_OK;
 }
 
+ppe_status net_save(const ppe_net *n, const char *path) { return save_impl(n, path, true); }
+ppe_status net_save_params(const ppe_net *n, const char *path) { return save_impl(n, path, false); }
+
 ppe_status net_load(const char *path, ppe_net **out)
 {
     clear_error();
@@ -597,7 +602,7 @@ ppe_status net_load(const char *path, ppe_net **out)
     size_t r;
     while ((r = std::fread(tmp, 1, sizeof tmp, f)) > 0) buf.insert(buf.end(), tmp, tmp + r);
     std::fclose(f);
-    const size_t head = 8 + 4 + sizeof(ppe_net_config) + 16;
+    const size_t head = 8 + 4 + 4 + sizeof(ppe_net_config) + 16;
     if (buf.size() < head + 4 || std::memcmp(buf.data(), "PPENET01", 8) != 0) {
         set_error("net_load: not a PPENET01 file");
         return PPE_ERR_FORMAT;
@@ -605,16 +610,19 @@ ppe_status net_load(const char *path, ppe_net **out)
     uint32_t crc;
     std::memcpy(&crc, buf.data() + buf.size() - 4, 4);
     if (crc != crc32_bytes(buf.data(), buf.size() - 4)) { set_error("net_load: CRC mismatch"); return PPE_ERR_FORMAT; }
+    uint32_t flags;
+    std::memcpy(&flags, buf.data() + 12, 4);
     ppe_net_config cfg;
-    std::memcpy(&cfg, buf.data() + 12, sizeof cfg);
+    std::memcpy(&cfg, buf.data() + 16, sizeof cfg);
     int64_t np, step;
-    std::memcpy(&np, buf.data() + 12 + sizeof cfg, 8);
-    std::memcpy(&step, buf.data() + 20 + sizeof cfg, 8);
+    std::memcpy(&np, buf.data() + 16 + sizeof cfg, 8);
+    std::memcpy(&step, buf.data() + 24 + sizeof cfg, 8);
     if (!valid_config(cfg)) { set_error("net_load: invalid configuration"); return PPE_ERR_FORMAT; }
+    const bool moments = (flags & 1u) != 0;
     ppe_net *n = new ppe_net();
     n->cfg = cfg;
     build_layout(n);
-    if (n->nparams != np || buf.size() != head + (size_t)np * 12 + 4) {
+    if (n->nparams != np || buf.size() != head + (size_t)np * (moments ? 12 : 4) + 4) {
         delete n;
         set_error("net_load: size does not match the configuration");
         return PPE_ERR_FORMAT;
@@ -623,7 +631,7 @@ ppe_status net_load(const char *path, ppe_net **out)
     std::memcpy(n->host_params.data(), buf.data() + head, np * 4);
     ppe_status st = net_alloc(n);
     if (st == PPE_OK) st = upload_params(n);
-    if (st == PPE_OK) {
+    if (st == PPE_OK && moments) {
         cudaError_t e1 = cudaMemcpy(n->adam_m, buf.data() + head + np * 4, np * 4, cudaMemcpyHostToDevice);
         cudaError_t e2 = cudaMemcpy(n->adam_v, buf.data() + head + np * 8, np * 4, cudaMemcpyHostToDevice);
         if (e1 != cudaSuccess || e2 != cudaSuccess) st = cuda_status(e1 != cudaSuccess ? e1 : e2, "net_load");

@@ -841,7 +841,7 @@ __global__ void __launch_bounds__(SOLVER_THREADS) solver_kernel(SolverArgs a, in
             __syncthreads();
             if (threadIdx.x == 0) {
                 __threadfence();
-                st_release_u32(&slot->seq, step);
+                atomicAdd(&a.arrive[br.s0 + q], 1u);
             }
         }
         if (prof) t_b = globaltimer_ns();
@@ -853,19 +853,26 @@ __global__ void __launch_bounds__(SOLVER_THREADS) solver_kernel(SolverArgs a, in
 #pragma unroll
             for (int k = 0; k < NPART; ++k) h[k] = l[k] = 0.f;
             const Slot *base = a.slots + (size_t)bank * a.nslots + sd.part0;
-            for (int b = threadIdx.x; b < sd.nparts; b += blockDim.x) {
-                const Slot *sl = base + b;
-                if (ld_acquire_u32(&sl->seq) != step) {
+            if (threadIdx.x == 0) {
+                // every block of this system has published step `step`
+                const uint32_t need = step * (uint32_t)sd.nparts;
+                const uint32_t *cnt = a.arrive + br.s0 + q;
+                if (ld_acquire_u32(cnt) < need) {
                     uint64_t t0 = globaltimer_ns();
-                    while (ld_acquire_u32(&sl->seq) != step) {
+                    while (ld_acquire_u32(cnt) < need) {
                         if ((int64_t)(globaltimer_ns() - t0) > a.spin_limit_ns) {
                             atomicExch(&a.ctl->err, (int32_t)PPE_ERR_TIMEOUT);
                             sm.go = 0;
                             break;
                         }
-                        __nanosleep(32);
+                        __nanosleep(20);
                     }
                 }
+                __threadfence();
+            }
+            __syncthreads();
+            for (int b = threadIdx.x; b < sd.nparts; b += blockDim.x) {
+                const Slot *sl = base + b;
 #pragma unroll
                 for (int k = 0; k < NPART; ++k) ff_add(h[k], l[k], ld_cg(&sl->hi[k]), ld_cg(&sl->lo[k]));
             }
