@@ -168,6 +168,30 @@ PPE_API ppe_status ppe_solve_batch(int n, ppe_grid *const *grids, const double *
 typedef void (*ppe_direction_fn)(void *user, const float *r_hat_dev, float *e_dev, int nx, int ny, void *stream);
 PPE_API ppe_status ppe_set_direction_source(ppe_grid *grid, ppe_direction_fn fn, void *user);
 
+/*
+ * Allocation-free plain-PCG solve.  The paper has no counterpart: this entry
+ * point serves callers that cannot allocate device memory -- a host whose
+ * device memory is reserved up front by its own pool allocator, a loop that
+ * must not allocate after initialisation, a plugin whose host forbids device
+ * allocations.  It runs the same persistent solver kernel as ppe_solve but
+ * takes all scratch from one fixed-size __device__ array inside the library
+ * (about 3.5 MB, held by every GPU that loads the library until exit), and
+ * calls no cudaMalloc, cudaFree or other allocating routine.
+ *   nx, ny    1 <= nx, ny <= 4096 and nx*ny <= 65536; larger grids return
+ *             PPE_ERR_ARG with a message naming the limit.
+ *   dx, dy    host arrays of the cell widths (copied into the array).
+ *   rhs_dev, x_dev, tol_rel, precision, stream, info: as in ppe_solve
+ *             (mode is PPE_MODE_PCG).
+ * Every call shares the array and it keeps the last call's contents; each
+ * call clears what must start at zero.  Calls whose work overlaps on the GPU
+ * (different streams, or different host threads) race: serialise them.  The
+ * first call on a device looks the array's address up with that device
+ * current; make it before any stream capture.  The call synchronises stream.
+ */
+PPE_API ppe_status ppe_solve_noalloc(int nx, int ny, const double *dx, const double *dy, const double *rhs_dev,
+                                     double *x_dev, double tol_rel, ppe_precision precision, void *stream,
+                                     ppe_solve_info *info);
+
 /* Message describing the last failure on the calling thread ("" if none). */
 PPE_API const char *ppe_last_error(void);
 /* Library build identification, e.g. "ppe-gb300 sm_103a". */

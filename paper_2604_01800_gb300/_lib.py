@@ -96,6 +96,8 @@ _SIGS = [
                                       ctypes.POINTER(ctypes.c_double)]),
     ("net_loss_grad", ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P, ctypes.POINTER(ctypes.c_double), _P]),
     ("net_get_step", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
+    ("ppe_solve_noalloc", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, ctypes.c_double, ctypes.c_int,
+                                         _P, ctypes.POINTER(ppe_solve_info)]),
     ("ppe_last_error", ctypes.c_char_p, []),
     ("ppe_version", ctypes.c_char_p, []),
 ]
