@@ -209,7 +209,7 @@ typedef struct {
     int32_t widths[PPE_NET_MAX_LEVELS];      /* channels per level (multiples of 16)        */
     int32_t c_last;                          /* branch / trunk feature count                 */
     int32_t trunk_hidden[2];                 /* trunk MLP hidden widths (2 -> h0 -> h1 -> c_last) */
-    int32_t phi_hidden;                      /* hidden width of each Mesh-Conv weight network */
+    int32_t phi_hidden;                      /* hidden width of each Mesh-Conv weight network (1..16) */
     int32_t mesh_conv;                       /* 1: Mesh-Conv; 0: standard convolution (eta = 1) */
     int32_t reserved[4];
 } ppe_net_config;

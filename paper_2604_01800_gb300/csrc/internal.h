@@ -85,6 +85,8 @@ struct SysState {
     int32_t has_d, fold_d, reset_d, first, cur, zero_x, keep_dir;
     double alpha, beta, gamma, mu, mu_b, bnorm, target, rnorm, relres, incompat;
     double alpha_d, xmean, rho, rho_ref;
+    float alpha_f, beta_f, mu_f, alpha_d_f;   // FP32 copies for the FP32 passes
+    int32_t dlsm_useless, pad2_;
 };
 
 // Tiles [t0, t1) of a block; they belong to systems s0..s1.

@@ -77,7 +77,7 @@ static bool valid_config(const ppe_net_config &c)
     if (c.levels < 2 || c.levels > PPE_NET_MAX_LEVELS) return false;
     for (int k = 0; k < c.levels; ++k)
         if (c.widths[k] < 16 || c.widths[k] % 16 || c.widths[k] > 256) return false;
-    if (c.c_last < 1 || c.c_last > 1024 || c.phi_hidden < 1 || c.phi_hidden > 256) return false;
+    if (c.c_last < 1 || c.c_last > 1024 || c.phi_hidden < 1 || c.phi_hidden > 16) return false;
     if (c.trunk_hidden[0] < 1 || c.trunk_hidden[1] < 1 || c.trunk_hidden[0] > 4096 || c.trunk_hidden[1] > 4096)
         return false;
     return true;

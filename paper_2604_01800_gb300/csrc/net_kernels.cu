@@ -4,6 +4,8 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "net_kernels.cuh"
 #include "net_ops.h"
 
@@ -200,21 +202,24 @@ constexpr int GT = 64, GK = 16;
 __global__ void __launch_bounds__(256) sgemm_kernel(int M, int N, int K, const float *__restrict__ A, int lda,
                                                     int transA, const float *__restrict__ Bm, int ldb, int transB,
                                                     float *__restrict__ C, int ldc, const float *__restrict__ bias,
-                                                    int act, int accumulate)
+                                                    int act, int accumulate, int kchunk)
 {
     __shared__ float As[GK][GT + 1];
     __shared__ float Bs[GK][GT + 1];
     const int tid = threadIdx.x, tr = tid / 16, tc = tid % 16;
     const int m0 = blockIdx.y * GT, n0 = blockIdx.x * GT;
+    // split-K: block z sums k in [kb, ke) and adds its share atomically
+    const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
+    const bool split = gridDim.z > 1;
     float acc[4][4] = {};
-    for (int k0 = 0; k0 < K; k0 += GK) {
+    for (int k0 = kb; k0 < ke; k0 += GK) {
         for (int t = tid; t < GT * GK; t += 256) {
             int mm = t % GT, kk = t / GT;
             int m = m0 + mm, k = k0 + kk;
-            As[kk][mm] = (m < M && k < K) ? (transA ? A[(size_t)k * lda + m] : A[(size_t)m * lda + k]) : 0.f;
+            As[kk][mm] = (m < M && k < ke) ? (transA ? A[(size_t)k * lda + m] : A[(size_t)m * lda + k]) : 0.f;
             int nn = t % GT;
             int n = n0 + nn;
-            Bs[kk][nn] = (n < N && k < K) ? (transB ? Bm[(size_t)n * ldb + k] : Bm[(size_t)k * ldb + n]) : 0.f;
+            Bs[kk][nn] = (n < N && k < ke) ? (transB ? Bm[(size_t)n * ldb + k] : Bm[(size_t)k * ldb + n]) : 0.f;
         }
         __syncthreads();
 #pragma unroll
@@ -239,9 +244,13 @@ __global__ void __launch_bounds__(256) sgemm_kernel(int M, int N, int K, const f
         for (int j = 0; j < 4; ++j) {
             int n = n0 + tc * 4 + j;
             if (n >= N) continue;
+            float *c = C + (size_t)m * ldc + n;
+            if (split) {                       // identity epilogue, C accumulated
+                atomicAdd(c, acc[i][j] + ((bias && blockIdx.z == 0) ? bias[m] : 0.f));
+                continue;
+            }
             float v = acc[i][j] + (bias ? bias[m] : 0.f);
             if (act == 1) v = tanhf(v);
-            float *c = C + (size_t)m * ldc + n;
             *c = accumulate ? *c + v : v;
         }
     }
@@ -341,8 +350,23 @@ ppe_status eta_layer(const float *delta, int HW, const float *w1, const float *b
 ppe_status sgemm(int M, int N, int K, const float *A, int lda, bool transA, const float *B, int ldb, bool transB,
                  float *C, int ldc, const float *bias, int act, bool accumulate, cudaStream_t s)
 {
-    dim3 grid((N + GT - 1) / GT, (M + GT - 1) / GT);
-    sgemm_kernel<<<grid, 256, 0, s>>>(M, N, K, A, lda, transA, B, ldb, transB, C, ldc, bias, act, accumulate);
+    dim3 grid((N + GT - 1) / GT, (M + GT - 1) / GT, 1);
+    int kchunk = K;
+    const int tiles = grid.x * grid.y;
+    if (act == 0 && K >= 4096 && tiles < 296) {
+        // long reductions over pixels with a small output: split K across blocks
+        int splits = std::min((K + 1023) / 1024, std::max(1, 592 / tiles));
+        kchunk = (K + splits - 1) / splits;
+        kchunk = (kchunk + GK - 1) / GK * GK;
+        grid.z = (K + kchunk - 1) / kchunk;
+        if (grid.z > 1 && !accumulate) {      // the blocks add their shares into a cleared C
+            cudaError_t e = ldc == N ? cudaMemsetAsync(C, 0, (size_t)M * N * sizeof(float), s)
+                                     : cudaMemset2DAsync(C, (size_t)ldc * sizeof(float), 0, (size_t)N * sizeof(float),
+                                                         M, s);
+            if (e != cudaSuccess) return cuda_status(e, "sgemm split-K clear");
+        }
+    }
+    sgemm_kernel<<<grid, 256, 0, s>>>(M, N, K, A, lda, transA, B, ldb, transB, C, ldc, bias, act, accumulate, kchunk);
     PPE_CUDA_TRY(cudaGetLastError());
     return PPE_OK;
 }

@@ -240,38 +240,59 @@ __global__ void eta_bwd_kernel(const float *__restrict__ dXb, const bf16 *__rest
     }
 }
 
-// Weight-network backward: phi = w2 . tanh(W1 D + b1) + b2, eta = exp(-phi^2)
-__global__ void phi_bwd_kernel(const float *__restrict__ deta, const float *__restrict__ eta,
+// Weight-network backward: phi = w2 . tanh(W1 D + b1) + b2, eta = exp(-phi^2).
+// Each thread accumulates its pixels' contributions in registers (hid <= 16),
+// then the block reduces them with warp shuffles and one atomic per value.
+constexpr int PHI_MAXH = 16;
+__global__ void __launch_bounds__(256) phi_bwd_kernel(const float *__restrict__ deta, const float *__restrict__ eta,
                                const float *__restrict__ phi, const float *__restrict__ D, int HW,
                                const float *__restrict__ W1, const float *__restrict__ b1, const float *__restrict__ w2,
                                int hid, float *__restrict__ gW1, float *__restrict__ gb1, float *__restrict__ gw2,
                                float *__restrict__ gb2)
 {
-    extern __shared__ float red[];   // 6*hid + 1
-    for (int k = threadIdx.x; k < 6 * hid + 1; k += blockDim.x) red[k] = 0.f;
-    __syncthreads();
+    float a_w2[PHI_MAXH], a_b1[PHI_MAXH], a_W1[PHI_MAXH][4], a_b2 = 0.f;
+#pragma unroll
+    for (int k = 0; k < PHI_MAXH; ++k) {
+        a_w2[k] = a_b1[k] = 0.f;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) a_W1[k][c] = 0.f;
+    }
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < HW; q += gridDim.x * blockDim.x) {
         float dphi = deta[q] * eta[q] * (-2.f * phi[q]);
-        if (dphi == 0.f) continue;
         float d[4] = {D[q], D[HW + q], D[2 * HW + q], D[3 * HW + q]};
-        atomicAdd(&red[6 * hid], dphi);
-        for (int k = 0; k < hid; ++k) {
+        a_b2 += dphi;
+#pragma unroll
+        for (int k = 0; k < PHI_MAXH; ++k) {
+            if (k >= hid) break;
             float z = b1[k] + W1[4 * k] * d[0] + W1[4 * k + 1] * d[1] + W1[4 * k + 2] * d[2] + W1[4 * k + 3] * d[3];
             float h = tanhf(z);
-            atomicAdd(&red[k], dphi * h);                       // w2
+            a_w2[k] += dphi * h;
             float dz = dphi * w2[k] * (1.f - h * h);
-            atomicAdd(&red[hid + k], dz);                       // b1
-            for (int c = 0; c < 4; ++c) atomicAdd(&red[2 * hid + 4 * k + c], dz * d[c]);   // W1
+            a_b1[k] += dz;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) a_W1[k][c] += dz * d[c];
         }
     }
-    __syncthreads();
-    for (int k = threadIdx.x; k < 6 * hid + 1; k += blockDim.x) {
-        float v = red[k];
-        if (v == 0.f) continue;
-        if (k < hid) atomicAdd(&gw2[k], v);
-        else if (k < 2 * hid) atomicAdd(&gb1[k - hid], v);
-        else if (k < 6 * hid) atomicAdd(&gW1[k - 2 * hid], v);
-        else atomicAdd(gb2, v);
+    auto wsum = [](float v) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        return v;
+    };
+    const bool lead = (threadIdx.x & 31) == 0;
+    float v = wsum(a_b2);
+    if (lead && v != 0.f) atomicAdd(gb2, v);
+#pragma unroll
+    for (int k = 0; k < PHI_MAXH; ++k) {
+        if (k >= hid) break;
+        v = wsum(a_w2[k]);
+        if (lead && v != 0.f) atomicAdd(&gw2[k], v);
+        v = wsum(a_b1[k]);
+        if (lead && v != 0.f) atomicAdd(&gb1[k], v);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            v = wsum(a_W1[k][c]);
+            if (lead && v != 0.f) atomicAdd(&gW1[4 * k + c], v);
+        }
     }
 }
 
@@ -490,7 +511,7 @@ static ppe_status conv_backward(ppe_net *n, NetCache *c, TrainWs *w, int li, con
     eta_bwd_kernel<<<g1d(px), 256, 0, s>>>(w->dXb, Xb, eta, px, H * W, l.cin, w->dX, w->deta, n->cfg.mesh_conv);
     if (n->cfg.mesh_conv) {
         int hid = n->cfg.phi_hidden;
-        phi_bwd_kernel<<<std::min(256u, g1d((size_t)H * W)), 256, (6 * hid + 1) * 4, s>>>(
+        phi_bwd_kernel<<<std::min(256u, g1d((size_t)H * W)), 256, 0, s>>>(
             w->deta, eta, c->phi + c->eoff[li], c->delta + c->doff[k], H * W, P + l.off_p1w, P + l.off_p1b,
             P + l.off_p2w, hid, grads + l.off_p1w, grads + l.off_p1b, grads + l.off_p2w, grads + l.off_p2b);
     }
@@ -577,7 +598,7 @@ static ppe_status net_backward(ppe_net *n, NetCache *c, TrainWs *w, ppe_grid *g,
             PPE_CUDA_TRY(cudaMemsetAsync(w->deta, 0, (size_t)c->H * c->W * 4, s));
             dgrad_in_kernel<<<g1d(px), 256, 0, s>>>(w->dZ, P + l.off_w, R, B, c->H, c->W, l.cout, g->nx, g->ny, w->deta);
             int hid = cf.phi_hidden;
-            phi_bwd_kernel<<<std::min(256u, g1d((size_t)c->H * c->W)), 256, (6 * hid + 1) * 4, s>>>(
+            phi_bwd_kernel<<<std::min(256u, g1d((size_t)c->H * c->W)), 256, 0, s>>>(
                 w->deta, eta, c->phi + c->eoff[li], c->delta + c->doff[0], c->H * c->W, P + l.off_p1w, P + l.off_p1b,
                 P + l.off_p2w, hid, grads + l.off_p1w, grads + l.off_p1b, grads + l.off_p2w, grads + l.off_p2b);
         }

@@ -156,6 +156,21 @@ template <typename C> __device__ __forceinline__ C stencil(const Coef<C> &cf, co
     return cf.dy[wj] * ax + cf.dx[wi] * ay;
 }
 
+// Scalars of the current pass in the pass's arithmetic type (FP32 copies are
+// made once per step by the state transition, not by every thread).
+template <typename T> __device__ __forceinline__ T sc_alpha(const SysState &s);
+template <typename T> __device__ __forceinline__ T sc_beta(const SysState &s);
+template <typename T> __device__ __forceinline__ T sc_mu(const SysState &s);
+template <typename T> __device__ __forceinline__ T sc_alpha_d(const SysState &s);
+template <> __device__ __forceinline__ float sc_alpha<float>(const SysState &s) { return s.alpha_f; }
+template <> __device__ __forceinline__ float sc_beta<float>(const SysState &s) { return s.beta_f; }
+template <> __device__ __forceinline__ float sc_mu<float>(const SysState &s) { return s.mu_f; }
+template <> __device__ __forceinline__ float sc_alpha_d<float>(const SysState &s) { return s.alpha_d_f; }
+template <> __device__ __forceinline__ double sc_alpha<double>(const SysState &s) { return s.alpha; }
+template <> __device__ __forceinline__ double sc_beta<double>(const SysState &s) { return s.beta; }
+template <> __device__ __forceinline__ double sc_mu<double>(const SysState &s) { return s.mu; }
+template <> __device__ __forceinline__ double sc_alpha_d<double>(const SysState &s) { return s.alpha_d; }
+
 __device__ __forceinline__ bool in_dom(const SysDesc &sd, int i, int j)
 {
     return i >= 0 && j >= 0 && i < sd.nx && j < sd.ny;
@@ -314,7 +329,7 @@ __device__ void pass_restart(S &sm, const SysDesc &sd, const SysState &st, int i
     T *R = sm.w.a0, *U = sm.w.a1;
     load_coef_t<T>(sm, sd, i0, j0, tag);
     const T *rin = (const T *)sd.r[st.cur];
-    const T mu = (T)st.mu;
+    const T mu = sc_mu<T>(st);
     T rv[NL];
 #pragma unroll
     for (int q = 0; q < NL; ++q) {
@@ -378,7 +393,7 @@ __device__ void pass_iter(S &sm, const SysDesc &sd, const SysState &st, int i0, 
     T *sout = (T *)sd.s[cur ^ 1];
     T *pv = (T *)sd.p;
     T *dv = (T *)sd.d;
-    const T mu = (T)st.mu, alpha = (T)st.alpha, beta = (T)st.beta;
+    const T mu = sc_mu<T>(st), alpha = sc_alpha<T>(st), beta = sc_beta<T>(st);
     const bool first = st.first != 0;
     const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
     const int j = j0 + ty, wj0 = ty + 2;
@@ -483,7 +498,7 @@ __device__ void pass_dlsm(S &sm, const SysDesc &sd, const SysState &st, int i0, 
     const T *rin = (const T *)sd.r[cur];
     T *rout = (T *)sd.r[cur ^ 1];
     T *dv = (T *)sd.d;
-    const T mu = (T)st.mu, alpha = (T)st.alpha_d;
+    const T mu = sc_mu<T>(st), alpha = sc_alpha_d<T>(st);
     T t[NPART] = {0, 0, 0, 0, 0, 0};
     const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
     int j = j0 + ty, wj = ty + 2;
@@ -709,7 +724,12 @@ __device__ void advance(const SysDesc &sd, SysState &s, const double (&t)[NPART]
         s.cur ^= 1;
         s.mu = t[3] * sd.inv_n;
         double rr = t[2] - N * s.mu * s.mu;
+        const double rho_before = s.rho;
         s.rho = rr > 0.0 ? rr : 0.0;
+        // a direction that removes less than 10% of the residual norm is not
+        // worth its inference; after several in a row continue as plain PCG
+        s.dlsm_useless = s.rho > 0.81 * rho_before ? s.dlsm_useless + 1 : 0;
+        if (s.dlsm_useless >= 6) s.fell_back = 1;
         s.dlsm_count++;
         if (sd.mode == PPE_MODE_HYBRID && !s.fell_back && s.it_total >= sd.hybrid_budget) s.fell_back = 1;
         if (s.rho <= s.target * s.target || s.it_total >= iter_cap(sd) || !isfinite(s.rho)) {
@@ -733,6 +753,10 @@ __device__ void advance(const SysDesc &sd, SysState &s, const double (&t)[NPART]
     default:
         break;
     }
+    s.alpha_f = (float)s.alpha;
+    s.beta_f = (float)s.beta;
+    s.mu_f = (float)s.mu;
+    s.alpha_d_f = (float)s.alpha_d;
 }
 
 template <typename T, typename S>
