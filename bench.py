@@ -28,6 +28,7 @@ sys.path.insert(0, ROOT)
 from paper_2604_01800_gb300 import inputs as I  # noqa: E402
 
 METRIC = "PPE solves/s at rel-res 1e-8 (512x512 refined-box grid, mixed FP32/FP64 PCG)"
+WEIGHTS = os.path.join(ROOT, "paper_2604_01800_gb300", "weights", "hydea_mconv.ppenet")
 TOL = 1e-8
 L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2
 
@@ -257,12 +258,50 @@ def run_native(args):
 
     if not args.no_sweep and rank == 0:
         line["stencil_sweep"] = stencil_sweep(api, dev, peaks)
+    if rank == 0:
+        line["hybrid_vs_plain"] = hybrid_vs_plain(api, dev, flush)
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_oracle_baseline(w)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def hybrid_vs_plain(api, dev, flush, reps=5):
+    """HyDEA (Jacobi PCG + DLSM with the trained network) against plain PCG on
+    the 256x256 cylinder-refined grid with a masked-divergence source, both
+    mixed precision, to rel-res 1e-8 (median of `reps` solves each)."""
+    import torch
+    if not os.path.exists(WEIGHTS):
+        return {"available": False, "reason": "no trained weights file"}
+    net = api.net_load(WEIGHTS)
+    out = {"workload": "cyl256_mask (256x256, cylinder D=0.1, box-refined, growth 1.05)"}
+    for name, seeds in (("cyl256", range(reps)),):
+        rows = {"pcg": [], "hybrid": []}
+        for i in seeds:
+            w = I.config3(i)
+            g = api.ppe_create_grid(w.dx, w.dy, w.mask)
+            net.attach(g)
+            rhs = torch.tensor(w.f, dtype=torch.float64, device=dev)
+            for mode, key in ((api.PPE_MODE_PCG, "pcg"), (api.PPE_MODE_HYBRID, "hybrid")):
+                x = torch.zeros_like(rhs)
+                api.ppe_solve(g, rhs, x, TOL, mode, api.PPE_PREC_MIXED, net=net)     # warm (graph capture)
+                flush.fill_(1.0)
+                x.zero_()
+                info = api.ppe_solve(g, rhs, x, TOL, mode, api.PPE_PREC_MIXED, net=net)
+                rows[key].append(info)
+            g.close()
+        for key, infos in rows.items():
+            ms = float(np.median([i["ms_total"] for i in infos]))
+            out[key] = {"solves_per_s": 1e3 / ms, "ms_median": ms,
+                        "iters_median": float(np.median([i["iters_pcg"] + i["iters_dlsm"] for i in infos])),
+                        "dlsm_steps_median": float(np.median([i["iters_dlsm"] for i in infos])),
+                        "fell_back": int(sum(i["fell_back"] for i in infos)),
+                        "max_rel_res": float(max(i["rel_res_true"] for i in infos))}
+        out["speedup"] = out["hybrid"]["solves_per_s"] / out["pcg"]["solves_per_s"]
+    net.close()
+    return out
 
 
 def stencil_sweep(api, dev, peaks, n=8192, iters=60):

@@ -38,6 +38,7 @@ constexpr long long TC_WAIT_NS = 1000000000LL;   // 1 s bound on every wait
 
 struct TcArgs {
     int B, H, W, cin, cout, n_tile, tw, th, tiles_x, tiles_y, kblocks, stages, tmem_cols;
+    uint32_t bar_off;       // byte offset of the barriers: past both the pipeline and the epilogue staging
     const float *bias;
     Epi epi;
     int *err;
@@ -170,7 +171,7 @@ __global__ void __launch_bounds__(128, 1)
     const uint32_t b_bytes = (uint32_t)a.n_tile * BK * 2;
     const uint32_t tx_bytes = A_BYTES + b_bytes;                      // bytes landed per stage
     const uint32_t stage_bytes = (tx_bytes + 1023u) & ~1023u;         // 1024-aligned stage stride
-    const uint32_t bar0 = base + stage_bytes * a.stages;      // full[8], empty[8], acc
+    const uint32_t bar0 = base + a.bar_off;                    // full[8], empty[8], acc
     const uint32_t full0 = bar0, empty0 = bar0 + 8 * TC_MAX_STAGES, accb = bar0 + 16 * TC_MAX_STAGES;
     const uint32_t tslot = accb + 8;
     unsigned char *gbase = smem_raw + (base - raw);
@@ -244,25 +245,73 @@ __global__ void __launch_bounds__(128, 1)
         mma_commit(accb);     // arrives once every MMA issued above has completed
     }
     __syncwarp();
-    // epilogue: thread (warp w, lane l) owns TMEM lane / output pixel 32 w + l
-    bool ok = mbar_wait(accb, 0, a.err);
+    // epilogue: thread (warp w, lane l) owns TMEM lane / output pixel m = 32 w + l.
+    // Each output is staged as [128 pixels][n_tile] in the (now idle) pipeline
+    // shared memory and written back in 16-byte chunks, consecutive threads
+    // taking consecutive chunks of a pixel's channel run.
+    int ok = mbar_wait(accb, 0, a.err) ? 1 : 0;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    ok = __syncthreads_and(ok && *((volatile int *)a.err) == 0);
     const int m = threadIdx.x;
     const int px = x0 + m % a.tw, py = y0 + m / a.tw;
-    const bool valid = ok && px < a.W && py < a.H && *((volatile int *)a.err) == 0;
-    const size_t p = ((size_t)img * a.H + py) * a.W + px;
+    const bool inside = px < a.W && py < a.H;
     const int q = py * a.W + px;
-    for (int c = 0; c < a.n_tile; c += 16) {
-        float v[16];
-        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
-        if (valid) {
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+    unsigned char *stage = gbase;
+    for (int o = 0; o < 4; ++o) {
+        void *dst = nullptr;
+        int cs = a.cout, co = 0, es = 2;
+        float scale = 1.f;
+        bool act = false;
+        if (o == 0) { dst = a.epi.zf_out; es = 4; }
+        else if (o == 1) { dst = a.epi.z_out; }
+        else if (o == 2) {
+            dst = a.epi.out1; cs = a.epi.cs1; co = a.epi.co1; act = a.epi.act != 0;
+            scale = (a.epi.eta1 && inside) ? a.epi.eta1[q] : 1.f;
+        } else {
+            dst = a.epi.out2; cs = a.epi.cs2; co = a.epi.co2; act = a.epi.act != 0;
+            scale = (a.epi.eta2 && inside) ? a.epi.eta2[q] : 1.f;
+        }
+        if (!dst || !ok) continue;
+        const int rowb = a.n_tile * es + 16;        // padded staging row (bytes)
+        for (int c = 0; c < a.n_tile; c += 16) {
+            float v[16];
+            tmem_ld16(trow + (uint32_t)c, v);
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
-                int co = n0 + c + i;
-                float z = v[i] + (a.bias ? a.bias[co] : 0.f);
-                epi_store(a.epi, z, p, q, co, a.cout);
+                float z = v[i] + (a.bias ? a.bias[n0 + c + i] : 0.f);
+                v[i] = (act ? gelu_f(z) : z) * scale;
+            }
+            unsigned char *row = stage + (size_t)m * rowb + (size_t)c * es;
+            if (es == 4) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    *reinterpret_cast<float4 *>(row + 16 * i) = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+            } else {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    uint4 pk;
+                    uint32_t *w = reinterpret_cast<uint32_t *>(&pk);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        __nv_bfloat162 b2 = __floats2bfloat162_rn(v[8 * h + 2 * i], v[8 * h + 2 * i + 1]);
+                        w[i] = *reinterpret_cast<uint32_t *>(&b2);
+                    }
+                    *reinterpret_cast<uint4 *>(row + 16 * h) = pk;
+                }
             }
         }
+        __syncthreads();
+        const int cpr = a.n_tile * es / 16;         // 16-byte chunks per pixel
+        for (int k = threadIdx.x; k < TC_M * cpr; k += blockDim.x) {
+            const int mm = k / cpr, off = k % cpr;
+            const int qx = x0 + mm % a.tw, qy = y0 + mm / a.tw;
+            if (qx >= a.W || qy >= a.H) continue;
+            const size_t pp = ((size_t)img * a.H + qy) * a.W + qx;
+            const uint4 val = *reinterpret_cast<const uint4 *>(stage + (size_t)mm * rowb + 16 * off);
+            *reinterpret_cast<uint4 *>(reinterpret_cast<unsigned char *>(dst) + (pp * cs + co + n0) * es + 16 * off) = val;
+        }
+        __syncthreads();
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -330,8 +379,11 @@ ppe_status conv3x3_tc(const ConvArgs &a, cudaStream_t s)
     while (tmem_cols < n_tile) tmem_cols *= 2;
     const int stage_bytes = ((TC_M + n_tile) * bk * 2 + 1023) / 1024 * 1024;
     int stages = std::min(TC_MAX_STAGES, (200 * 1024) / stage_bytes);
+    stages = std::min(stages, 9 * (a.cin / bk));        // no deeper than the K loop
     if (stages < 2) stages = 2;
-    const size_t smem = (size_t)stage_bytes * stages + 1024 + 16 * TC_MAX_STAGES + 64;
+    const size_t staging = (size_t)TC_M * (n_tile * 4 + 16);      // widest epilogue staging (FP32 rows)
+    const size_t bar_off = (std::max((size_t)stage_bytes * stages, staging) + 127) / 128 * 128;
+    const size_t smem = bar_off + 1024 + 16 * TC_MAX_STAGES + 64;
 
     CUtensorMap mA, mB;
     CUtensorMapSwizzle sw = bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B
@@ -370,21 +422,26 @@ ppe_status conv3x3_tc(const ConvArgs &a, cudaStream_t s)
     t.kblocks = 9 * (a.cin / bk);
     t.stages = stages;
     t.tmem_cols = tmem_cols;
+    t.bar_off = (uint32_t)bar_off;
     t.bias = a.bias;
     t.epi = a.epi;
     t.err = err;
     dim3 grid(t.tiles_x * t.tiles_y * a.B, a.cout / n_tile);
     cudaError_t e;
-    if (bk == 64) {
-        cudaFuncSetAttribute(conv_tc_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // the shared-memory opt-in is a per-function attribute: set it once to the maximum
+    static std::once_flag attr_once;
+    std::call_once(attr_once, [] {
+        const int cap = 227 * 1024;
+        cudaFuncSetAttribute(conv_tc_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+        cudaFuncSetAttribute(conv_tc_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+        cudaFuncSetAttribute(conv_tc_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+    });
+    if (bk == 64)
         conv_tc_kernel<64><<<grid, 128, smem, s>>>(mA, mB, t);
-    } else if (bk == 32) {
-        cudaFuncSetAttribute(conv_tc_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    else if (bk == 32)
         conv_tc_kernel<32><<<grid, 128, smem, s>>>(mA, mB, t);
-    } else {
-        cudaFuncSetAttribute(conv_tc_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    else
         conv_tc_kernel<16><<<grid, 128, smem, s>>>(mA, mB, t);
-    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_status(e, "conv_tc_kernel launch");
     return PPE_OK;

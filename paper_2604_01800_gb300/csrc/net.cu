@@ -163,6 +163,8 @@ static void free_cache(NetCache *c)
 {
     if (!c) return;
     net_free_train(c);
+    if (c->dir_exec) cudaGraphExecDestroy(c->dir_exec);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     cudaFree(c->delta); cudaFree(c->eta); cudaFree(c->phi); cudaFree(c->xy); cudaFree(c->trunk);
     cudaFree(c->weff); cudaFree(c->ceff); cudaFree(c->act); cudaFree(c->grad_act); cudaFree(c->efull);
     cudaFree(c->red);
@@ -454,15 +456,47 @@ ppe_status net_forward(ppe_net *n, NetCache *c, int B, const InputSrc &src, cons
                     s);
 }
 
+// The DLSM direction of a solver system: the forward pass on its normalised
+// residual.  The sequence of launches is the same on every call, so it is
+// captured once into a CUDA graph (per grid and parameter version) and
+// replayed with a single launch afterwards.
 ppe_status net_direction(ppe_net *net, ppe_grid *g, const SysDesc *sd_dev, const SysState *st_dev, bool,
                          cudaStream_t stream, float *ms)
 {
     PPE_TRY(net_check_grid(net, g));
     NetCache *c = (NetCache *)g->net_cache;
-    InputSrc src;
-    src.sd = sd_dev; src.st = st_dev; src.nx = g->nx; src.ny = g->ny;
     if (ms) *ms = 0.f;
-    return net_forward(net, c, 1, src, net->params, g->e, g->pitch, 0, false, stream);
+    PPE_TRY(ensure_packed(net, net->params, stream));
+    PPE_TRY(refresh_cache(net, c, net->params, stream));
+    PPE_TRY(ensure_acts(net, c, 1));
+    if (!(c->dir_exec && c->dir_version == net->version && c->dir_key == (const void *)sd_dev)) {
+        if (c->dir_exec) {
+            cudaGraphExecDestroy(c->dir_exec);
+            c->dir_exec = nullptr;
+        }
+        if (!c->cap_stream) PPE_CUDA_TRY(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+        InputSrc src;
+        src.sd = sd_dev; src.st = st_dev; src.nx = g->nx; src.ny = g->ny;
+        cudaGraph_t graph = nullptr;
+        PPE_CUDA_TRY(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+        ppe_status fs = net_forward(net, c, 1, src, net->params, g->e, g->pitch, 0, false, c->cap_stream);
+        cudaError_t ce = cudaStreamEndCapture(c->cap_stream, &graph);
+        if (fs != PPE_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return fs;
+        }
+        if (ce != cudaSuccess) return cuda_status(ce, "cudaStreamEndCapture(direction)");
+        ce = cudaGraphInstantiate(&c->dir_exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) {
+            c->dir_exec = nullptr;
+            return cuda_status(ce, "cudaGraphInstantiate(direction)");
+        }
+        c->dir_version = net->version;
+        c->dir_key = sd_dev;
+    }
+    PPE_CUDA_TRY(cudaGraphLaunch(c->dir_exec, stream));
+    return PPE_OK;
 }
 
 }  // namespace ppe

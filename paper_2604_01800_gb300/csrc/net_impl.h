@@ -44,6 +44,11 @@ struct NetCache {
     size_t efull_elems = 0;
     double *red = nullptr;
     void *train = nullptr;                  // training workspace (net_train.cu)
+    // CUDA graph of the DLSM-direction forward (input: the solver state)
+    cudaGraphExec_t dir_exec = nullptr;
+    uint64_t dir_version = 0;
+    const void *dir_key = nullptr;
+    cudaStream_t cap_stream = nullptr;
 };
 
 void net_free_train(NetCache *c);

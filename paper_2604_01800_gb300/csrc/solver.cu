@@ -35,6 +35,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <mutex>
 
 #include "internal.h"
 
@@ -946,6 +947,18 @@ __global__ void __launch_bounds__(SOLVER_THREADS) solver_kernel(SolverArgs a, in
     }
 }
 
+// The dynamic shared-memory opt-in is a per-function attribute: set it once.
+void set_solver_attributes()
+{
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaFuncSetAttribute(solver_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(SmemT<double>));
+        cudaFuncSetAttribute(solver_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(SmemT<float>));
+    });
+}
+
 }  // namespace
 
 int solver_max_blocks(bool fp64, int blocks_per_sm_req)
@@ -954,13 +967,11 @@ int solver_max_blocks(bool fp64, int blocks_per_sm_req)
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     size_t smem = fp64 ? sizeof(SmemT<double>) : sizeof(SmemT<float>);
-    if (fp64) {
-        cudaFuncSetAttribute(solver_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    set_solver_attributes();
+    if (fp64)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solver_kernel<double>, SOLVER_THREADS, smem);
-    } else {
-        cudaFuncSetAttribute(solver_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    else
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solver_kernel<float>, SOLVER_THREADS, smem);
-    }
     if (blocks_per_sm_req > 0 && blocks_per_sm_req < per_sm) per_sm = blocks_per_sm_req;
     return per_sm * sms;
 }
@@ -972,15 +983,13 @@ ppe_status launch_solver_resume(const SolverArgs &a, bool fp64, int grid_blocks,
     int res = resume;
     void *params[] = {&args, &res};
     cudaError_t e;
-    if (fp64) {
-        cudaFuncSetAttribute(solver_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    set_solver_attributes();
+    if (fp64)
         e = cudaLaunchCooperativeKernel((const void *)solver_kernel<double>, dim3(grid_blocks),
                                         dim3(SOLVER_THREADS), params, smem, stream);
-    } else {
-        cudaFuncSetAttribute(solver_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    else
         e = cudaLaunchCooperativeKernel((const void *)solver_kernel<float>, dim3(grid_blocks),
                                         dim3(SOLVER_THREADS), params, smem, stream);
-    }
     if (e != cudaSuccess) return cuda_status(e, "cudaLaunchCooperativeKernel(solver)");
     return PPE_OK;
 }
