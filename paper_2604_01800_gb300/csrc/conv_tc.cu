@@ -351,6 +351,25 @@ int pick_bk(int cin) { return cin % 64 == 0 ? 64 : (cin % 32 == 0 ? 32 : 16); }
 
 }  // namespace
 
+// One-time set-up (driver entry point, error flag, kernel attributes); must
+// run outside any stream capture.
+ppe_status conv3x3_tc_prepare()
+{
+    if (!encode_fn()) {
+        set_error("cuTensorMapEncodeTiled unavailable");
+        return PPE_ERR_CUDA;
+    }
+    if (!err_flag()) return cuda_status(cudaErrorMemoryAllocation, "conv3x3_tc error flag");
+    static std::once_flag attr_once;
+    std::call_once(attr_once, [] {
+        const int cap = 227 * 1024;
+        cudaFuncSetAttribute(conv_tc_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+        cudaFuncSetAttribute(conv_tc_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+        cudaFuncSetAttribute(conv_tc_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+    });
+    return PPE_OK;
+}
+
 bool conv3x3_tc_supported(const ConvArgs &a)
 {
     return a.cin % 16 == 0 && a.cout % 16 == 0 && a.cin >= 16 && a.cout >= 16 && a.H >= 1 && a.W >= 1 &&
@@ -363,9 +382,9 @@ ppe_status conv3x3_tc(const ConvArgs &a, cudaStream_t s)
         set_error("conv3x3_tc: unsupported shape");
         return PPE_ERR_ARG;
     }
+    PPE_TRY(conv3x3_tc_prepare());
     auto encode = encode_fn();
     int *err = err_flag();
-    if (!err) return cuda_status(cudaErrorMemoryAllocation, "conv3x3_tc error flag");
     const int bk = pick_bk(a.cin);
     // output patch of 128 pixels: TW x TH with TW a power of two <= 128
     int tw = 8;
@@ -375,6 +394,12 @@ ppe_status conv3x3_tc(const ConvArgs &a, cudaStream_t s)
     int n_tile = a.cout;
     while (n_tile > 256) n_tile /= 2;
     if (a.cout % n_tile) n_tile = 16;
+    {
+        // few output patches (deep U-Net levels): split the output channels so
+        // that enough CTAs run; each slice re-reads the activations (L2-resident)
+        const long mtiles = (long)((a.W + tw - 1) / tw) * ((a.H + th - 1) / th) * a.B;
+        while (mtiles * (a.cout / n_tile) < 128 && n_tile > 32 && a.cout % (n_tile / 2) == 0) n_tile /= 2;
+    }
     int tmem_cols = 32;
     while (tmem_cols < n_tile) tmem_cols *= 2;
     const int stage_bytes = ((TC_M + n_tile) * bk * 2 + 1023) / 1024 * 1024;
@@ -428,14 +453,6 @@ ppe_status conv3x3_tc(const ConvArgs &a, cudaStream_t s)
     t.err = err;
     dim3 grid(t.tiles_x * t.tiles_y * a.B, a.cout / n_tile);
     cudaError_t e;
-    // the shared-memory opt-in is a per-function attribute: set it once to the maximum
-    static std::once_flag attr_once;
-    std::call_once(attr_once, [] {
-        const int cap = 227 * 1024;
-        cudaFuncSetAttribute(conv_tc_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-        cudaFuncSetAttribute(conv_tc_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-        cudaFuncSetAttribute(conv_tc_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-    });
     if (bk == 64)
         conv_tc_kernel<64><<<grid, 128, smem, s>>>(mA, mB, t);
     else if (bk == 32)

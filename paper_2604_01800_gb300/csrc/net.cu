@@ -475,6 +475,7 @@ ppe_status net_direction(ppe_net *net, ppe_grid *g, const SysDesc *sd_dev, const
             c->dir_exec = nullptr;
         }
         if (!c->cap_stream) PPE_CUDA_TRY(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+        if (net->use_tc) PPE_TRY(conv3x3_tc_prepare());     // one-time set-up cannot run inside a capture
         InputSrc src;
         src.sd = sd_dev; src.st = st_dev; src.nx = g->nx; src.ny = g->ny;
         cudaGraph_t graph = nullptr;

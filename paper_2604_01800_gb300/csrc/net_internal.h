@@ -54,5 +54,6 @@ ppe_status conv3x3_simt(const ConvArgs &a, cudaStream_t s);
 // shape is outside what the kernel supports.
 ppe_status conv3x3_tc(const ConvArgs &a, cudaStream_t s);
 bool conv3x3_tc_supported(const ConvArgs &a);
+ppe_status conv3x3_tc_prepare();
 
 }  // namespace ppe
