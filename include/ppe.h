@@ -97,7 +97,9 @@ typedef struct {
                                replacement (0.1)                                              */
     double dlsm_guard;      /* skip a DLSM step if e.Ae <= guard * e.e * max(diag A) (1e-10)   */
     int32_t blocks_per_sm;  /* persistent-kernel CTAs per SM (2; 0 = as many as fit)          */
-    int32_t reserved[7];
+    int32_t keep_dir_after_dlsm; /* 0: every CG-type phase restarts with p = z (Sec. 2.2 workflow,
+                               as a fresh KSPSolve); 1: CG directions continue across DLSM steps */
+    int32_t reserved[6];
 } ppe_solve_opts;
 
 PPE_API void ppe_default_options(ppe_solve_opts *opts);
@@ -125,6 +127,10 @@ PPE_API ppe_status ppe_set_options(ppe_grid *grid, const ppe_solve_opts *opts);
  * by -V to make it symmetric), FP64.  x, y: device [ny][nx]; may not alias.
  */
 PPE_API ppe_status ppe_apply(ppe_grid *grid, const double *x_dev, double *y_dev, void *stream);
+/* r = -V*S - A x (FP64, no projection): the residual of the scaled system for
+ * source S and iterate x.  All device [ny][nx]; r may not alias S or x. */
+PPE_API ppe_status ppe_residual(ppe_grid *grid, const double *S_dev, const double *x_dev, double *r_dev,
+                                void *stream);
 
 /*
  * Solve M x = S (Eq. 10) to ||P(b - A x)|| <= tol_rel * ||P b||.

@@ -36,7 +36,8 @@ class ppe_solve_info(ctypes.Structure):
 class ppe_solve_opts(ctypes.Structure):
     _fields_ = [("max_iters", ctypes.c_int32), ("num_cg", ctypes.c_int32), ("num_dlsm", ctypes.c_int32),
                 ("hybrid_budget", ctypes.c_int32), ("inner_rtol", ctypes.c_double), ("dlsm_guard", ctypes.c_double),
-                ("blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("blocks_per_sm", ctypes.c_int32), ("keep_dir_after_dlsm", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
 
 
 class ppe_net_config(ctypes.Structure):
@@ -71,6 +72,7 @@ _SIGS = [
     ("ppe_grid_shape", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     ("ppe_set_options", ctypes.c_int, [_P, ctypes.POINTER(ppe_solve_opts)]),
     ("ppe_apply", ctypes.c_int, [_P, _P, _P, _P]),
+    ("ppe_residual", ctypes.c_int, [_P, _P, _P, _P, _P]),
     ("ppe_solve", ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.c_int, ctypes.c_int, _P, _P,
                                  ctypes.POINTER(ppe_solve_info)]),
     ("ppe_solve_batch", ctypes.c_int, [ctypes.c_int, _P, _P, _P, ctypes.c_double, ctypes.c_int, ctypes.c_int, _P,

@@ -17,7 +17,7 @@ from ._lib import (PPE_MODE_HYBRID, PPE_MODE_PCG, PPE_PREC_FP64, PPE_PREC_MIXED,
                    ppe_solve_info, ppe_solve_opts)
 
 __all__ = ["Net", "net_create", "net_load", "net_default_config", "Grid", "ppe_create_grid", "ppe_destroy_grid", "ppe_apply", "ppe_solve", "ppe_solve_batch",
-           "ppe_set_options", "ppe_default_options", "ppe_set_direction_source", "PPE_MODE_PCG", "PPE_MODE_HYBRID", "PPE_PREC_FP64",
+           "ppe_set_options", "ppe_default_options", "ppe_set_direction_source", "ppe_residual", "PPE_MODE_PCG", "PPE_MODE_HYBRID", "PPE_PREC_FP64",
            "PPE_PREC_MIXED", "PPEError"]
 
 
@@ -125,6 +125,14 @@ def ppe_apply(grid: Grid, x: torch.Tensor, y: torch.Tensor, stream=None):
     n = grid.nx * grid.ny
     check(_lib.load().ppe_apply(grid.handle, _dptr(x, numel=n), _dptr(y, numel=n), _stream(stream)), "ppe_apply")
     return y
+
+
+def ppe_residual(grid: Grid, S: torch.Tensor, x: torch.Tensor, r: torch.Tensor, stream=None):
+    """r = -V S - A x (FP64 device tensors [ny, nx])."""
+    n = grid.nx * grid.ny
+    check(_lib.load().ppe_residual(grid.handle, _dptr(S, numel=n), _dptr(x, numel=n), _dptr(r, numel=n),
+                                   _stream(stream)), "ppe_residual")
+    return r
 
 
 def ppe_solve(grid: Grid, rhs: torch.Tensor, x: torch.Tensor, tol_rel: float = 1e-8, mode: int = PPE_MODE_PCG,

@@ -52,6 +52,23 @@ __global__ void apply_kernel(int nx, int ny, const double *__restrict__ dx, cons
 
 static int g_spin_limit_ms = 2000;
 
+// r = -V S - A x in FP64 (no projection).
+__global__ void residual_kernel(int nx, int ny, const double *__restrict__ dx, const double *__restrict__ dy,
+                                const double *__restrict__ fx, const double *__restrict__ fy,
+                                const double *__restrict__ S, const double *__restrict__ x, double *__restrict__ r)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= nx || j >= ny) return;
+    size_t k = (size_t)j * nx + i;
+    double c = x[k];
+    double xe = i + 1 < nx ? x[k + 1] : 0.0, xw = i > 0 ? x[k - 1] : 0.0;
+    double xn = j + 1 < ny ? x[k + nx] : 0.0, xs = j > 0 ? x[k - nx] : 0.0;
+    double ax = fx[i + 1] * (c - xe) + fx[i] * (c - xw);
+    double ay = fy[j + 1] * (c - xn) + fy[j] * (c - xs);
+    r[k] = -dx[i] * dy[j] * S[k] - (dy[j] * ax + dx[i] * ay);
+}
+
 // r_hat = (r - mu) / sqrt(rho) of a system's current residual, unpitched FP32.
 __global__ void rhat_kernel(const SysDesc *sd, const SysState *st, float *out)
 {
@@ -208,6 +225,17 @@ ppe_status ppe_set_options(ppe_grid *g, const ppe_solve_opts *o)
     return PPE_OK;
 }
 
+ppe_status ppe_residual(ppe_grid *g, const double *S, const double *x, double *r, void *stream)
+{
+    clear_error();
+    if (!g || !S || !x || !r) return arg_error("ppe_residual: NULL argument");
+    if (r == x || r == S) return arg_error("ppe_residual: r may not alias S or x");
+    dim3 blk(32, 8), grd((g->nx + 31) / 32, (g->ny + 7) / 8);
+    residual_kernel<<<grd, blk, 0, (cudaStream_t)stream>>>(g->nx, g->ny, g->dx, g->dy, g->fx, g->fy, S, x, r);
+    PPE_CUDA_TRY(cudaGetLastError());
+    return PPE_OK;
+}
+
 ppe_status ppe_set_direction_source(ppe_grid *g, ppe_direction_fn fn, void *user)
 {
     clear_error();
@@ -247,6 +275,7 @@ static SysDesc make_desc(const ppe_grid *g, const double *rhs, double *x, double
     sd.mode = mode; sd.precision = prec;
     sd.max_iters = g->opts.max_iters; sd.num_cg = g->opts.num_cg; sd.num_dlsm = g->opts.num_dlsm;
     sd.hybrid_budget = g->opts.hybrid_budget;
+    sd.keep_dir_after_dlsm = g->opts.keep_dir_after_dlsm ? 1 : 0;
     sd.tol = tol;
     sd.ru_delta = prec == PPE_PREC_MIXED ? g->opts.inner_rtol : 0.0;
     sd.dlsm_guard = g->opts.dlsm_guard;

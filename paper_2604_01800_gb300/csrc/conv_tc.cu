@@ -398,7 +398,8 @@ ppe_status conv3x3_tc(const ConvArgs &a, cudaStream_t s)
         // few output patches (deep U-Net levels): split the output channels so
         // that enough CTAs run; each slice re-reads the activations (L2-resident)
         const long mtiles = (long)((a.W + tw - 1) / tw) * ((a.H + th - 1) / th) * a.B;
-        while (mtiles * (a.cout / n_tile) < 128 && n_tile > 32 && a.cout % (n_tile / 2) == 0) n_tile /= 2;
+        while (mtiles * (a.cout / n_tile) < 128 && n_tile % 32 == 0 && n_tile > 32 && a.cout % (n_tile / 2) == 0)
+            n_tile /= 2;                                      // stays a multiple of 16
     }
     int tmem_cols = 32;
     while (tmem_cols < n_tile) tmem_cols *= 2;

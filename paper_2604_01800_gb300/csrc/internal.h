@@ -63,7 +63,8 @@ struct SysDesc {
     int32_t nx, ny, pitch, tiles_x, tile0, ntiles;
     int32_t mode, precision;              // ppe_mode, ppe_precision
     int32_t max_iters, num_cg, num_dlsm, hybrid_budget;
-    int32_t part0, blk0, nparts, pad_;    // partial slots part0.. for blocks blk0..blk0+nparts-1
+    int32_t part0, blk0, nparts;          // partial slots part0.. for blocks blk0..blk0+nparts-1
+    int32_t keep_dir_after_dlsm;          // 1: CG directions continue across DLSM steps
     double tol, ru_delta, dlsm_guard, diag_max;
     double n_cells, inv_n;                // nx*ny and its reciprocal
     const double *dx, *dy;                // widths [nx], [ny]

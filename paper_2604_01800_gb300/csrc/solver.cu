@@ -710,7 +710,7 @@ __device__ void advance(const SysDesc &sd, SysState &s, const double (&t)[NPART]
         double a = fast_div(re, eq);
         if (!(eq > sd.dlsm_guard * ee * sd.diag_max) || !isfinite(a)) {
             s.dlsm_skipped++;
-            s.keep_dir = 0;
+            s.keep_dir = sd.keep_dir_after_dlsm;
             s.reset_d = 0;
             s.phase = PH_RESTART;
         } else {
@@ -738,7 +738,7 @@ __device__ void advance(const SysDesc &sd, SysState &s, const double (&t)[NPART]
         } else if (s.dlsm_count < sd.num_dlsm && !s.fell_back) {
             s.phase = PH_NET;
         } else {
-            s.keep_dir = 0;
+            s.keep_dir = sd.keep_dir_after_dlsm;
             s.reset_d = 0;
             s.phase = PH_RESTART;
         }

@@ -368,22 +368,42 @@ def config5_grid(nx: int = 2048, ny: int = 1024):
     return dx, dy, [Body(0.5, 0.5, 0.05, 0.05)]
 
 
+def _masked_indicator(bodies, xs, ys, hfun, reach=0.05):
+    """chi on the tensor grid xs (columns) x ys (rows), evaluated only inside
+    each body's bounding box widened by `reach` (zero elsewhere)."""
+    chi = np.zeros((ys.size, xs.size))
+    for bd in bodies:
+        r = max(bd.a, bd.b) + reach
+        i0, i1 = np.searchsorted(xs, bd.cx - r), np.searchsorted(xs, bd.cx + r)
+        j0, j1 = np.searchsorted(ys, bd.cy - r), np.searchsorted(ys, bd.cy + r)
+        if i1 <= i0 or j1 <= j0:
+            continue
+        X, Y = np.meshgrid(xs[i0:i1], ys[j0:j1])
+        h = hfun(slice(j0, j1), slice(i0, i1))
+        chi[j0:j1, i0:i1] = np.maximum(chi[j0:j1, i0:i1],
+                                       0.5 * (1.0 - np.tanh(bd.level(X, Y) / (0.75 * h))))
+    return chi
+
+
 def config5_rhs(t: int, dx, dy, bodies, strouhal: float = 0.165,
                 dt: float = 0.05) -> np.ndarray:
     """Time-sequence stand-in for the flow solver's PPE source at step ``t``:
     masked divergence of a uniform stream carrying a row of alternating
-    Gaussian vortices advected downstream with Strouhal number 0.165."""
+    Gaussian vortices advected downstream with Strouhal number 0.165, plus a
+    small seeded perturbation (seed 5000 + t)."""
     g = rng(5000 + t)
-    lx, ly = dx.sum(), dy.sum()
+    lx = dx.sum()
     xf = np.concatenate([[0.0], np.cumsum(dx)])
     yf = np.concatenate([[0.0], np.cumsum(dy)])
     xc, yc = centres(dx), centres(dy)
     period = 0.1 / strouhal                  # D / (St U), U = 1
     time = t * dt
+    sig = 0.03
 
-    def vortex_u(X, Y):
-        u = np.zeros_like(X)
-        v = np.zeros_like(X)
+    def vortex_uv(xs, ys):
+        # separable Gaussians: u = -(y - py) e, v = (x - px) e, e = gam gx(x) gy(y)
+        u = np.zeros((ys.size, xs.size))
+        v = np.zeros((ys.size, xs.size))
         for k in range(12):
             age = (time + k * period / 2) % (6 * period)
             px = 0.6 + age
@@ -391,20 +411,18 @@ def config5_rhs(t: int, dx, dy, bodies, strouhal: float = 0.165,
                 continue
             py = 0.5 + (0.04 if k % 2 else -0.04)
             gam = 0.3 * (1 if k % 2 else -1)
-            r2 = (X - px) ** 2 + (Y - py) ** 2
-            e = gam * np.exp(-r2 / (2 * 0.03 ** 2))
-            u += -(Y - py) * e
-            v += (X - px) * e
+            gx = np.exp(-((xs - px) ** 2) / (2 * sig * sig))
+            gy = np.exp(-((ys - py) ** 2) / (2 * sig * sig))
+            u -= gam * np.outer(gy * (ys - py), gx)
+            v += gam * np.outer(gy, gx * (xs - px))
         return u, v
 
-    XU, YU = np.meshgrid(xf, yc)
-    XV, YV = np.meshgrid(xc, yf)
-    u = 1.0 + vortex_u(XU, YU)[0] + 0.02 * g.standard_normal(XU.shape)
-    v = vortex_u(XV, YV)[1] + 0.02 * g.standard_normal(XV.shape)
-    hu = np.sqrt(np.outer(dy, np.concatenate([[dx[0]], 0.5 * (dx[:-1] + dx[1:]), [dx[-1]]])))
-    hv = np.sqrt(np.outer(np.concatenate([[dy[0]], 0.5 * (dy[:-1] + dy[1:]), [dy[-1]]]), dx))
-    u *= 1.0 - _smoothed_indicator(bodies, XU, YU, hu)
-    v *= 1.0 - _smoothed_indicator(bodies, XV, YV, hv)
+    u = 1.0 + vortex_uv(xf, yc)[0] + 0.02 * g.standard_normal((yc.size, xf.size))
+    v = vortex_uv(xc, yf)[1] + 0.02 * g.standard_normal((yf.size, xc.size))
+    wx = np.concatenate([[dx[0]], 0.5 * (dx[:-1] + dx[1:]), [dx[-1]]])
+    wy = np.concatenate([[dy[0]], 0.5 * (dy[:-1] + dy[1:]), [dy[-1]]])
+    u *= 1.0 - _masked_indicator(bodies, xf, yc, lambda J, I_: np.sqrt(np.outer(dy[J], wx[I_])))
+    v *= 1.0 - _masked_indicator(bodies, xc, yf, lambda J, I_: np.sqrt(np.outer(wy[J], dx[I_])))
     div = (u[:, 1:] - u[:, :-1]) / dx[None, :] + (v[1:, :] - v[:-1, :]) / dy[:, None]
     return _zero_volume_mean(div, dx, dy)
 

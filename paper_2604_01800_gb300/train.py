@@ -4,8 +4,11 @@ forward/backward kernels (Sec. 2.4).
 The training set is fabricated by the method itself: random stretched grids
 (tanh or refined-box families, plus the cylinder-refined box family) and
 unit-norm right-hand sides b = -V S whose sources S are Gaussian sums or
-1/|k|^2 Fourier fields.  A step draws one grid and `batch` of its samples,
-so the batch shares the grid's geometry caches.  Every `eval_every` steps
+1/|k|^2 Fourier fields.  A fraction of the samples is replaced by the
+residual that plain PCG leaves on that system after k iterations (k
+log-uniform), i.e. by the kind of residual a DLSM step receives in the
+middle of a solve.  A step draws one grid and `batch` of its samples, so the
+batch shares the grid's geometry caches.  Every `eval_every` steps
 the hybrid solver is run on a held-out cylinder-grid system and its
 iteration count is logged next to plain PCG's.
 
@@ -63,6 +66,31 @@ def build_dataset(n_grids: int, per_grid: int, sizes, seed: int = 7000, workers:
     return grids, data
 
 
+def pcg_residuals(api, grid, dx, dy, R, gen, frac, kmax, dev):
+    """Replace a fraction of the unit-norm samples R (in place) by the
+    normalised residual of k plain-PCG iterations on A x = R."""
+    import torch
+    V = np.outer(dy, dx)
+    S = torch.empty(R.shape[1:], dtype=torch.float64, device=dev)
+    x = torch.empty_like(S)
+    r = torch.empty_like(S)
+    for i in range(R.shape[0]):
+        if gen.uniform() >= frac:
+            continue
+        k = int(np.exp(gen.uniform(0.0, np.log(kmax))))
+        S.copy_(torch.from_numpy(-R[i].astype(np.float64) / V))
+        x.zero_()
+        api.ppe_set_options(grid, max_iters=max(1, k))
+        api.ppe_solve(grid, S, x, 1e-14, api.PPE_MODE_PCG, api.PPE_PREC_MIXED, raise_on_error=False)
+        api.ppe_residual(grid, S, x, r)
+        rn = r.cpu().numpy()
+        rn -= rn.mean()
+        nrm = np.linalg.norm(rn)
+        if nrm > 0:
+            R[i] = (rn / nrm).astype(np.float32)
+    api.ppe_set_options(grid)
+
+
 def main(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--steps", type=int, default=4000)
@@ -77,6 +105,9 @@ def main(argv=None):
     p.add_argument("--out", default="hydea_mconv.ppenet")
     p.add_argument("--log", default=None)
     p.add_argument("--mesh-conv", type=int, default=1)
+    p.add_argument("--pcg-frac", type=float, default=0.7)
+    p.add_argument("--pcg-kmax", type=int, default=2000)
+    p.add_argument("--init", default=None, help="start from this weights file")
     a = p.parse_args(argv)
 
     sizes = [int(s) for s in a.sizes.split(",")]
@@ -88,13 +119,18 @@ def main(argv=None):
 
     from . import api
     dev = torch.device("cuda")
-    net = api.net_create(api.net_default_config(mesh_conv=a.mesh_conv), a.seed)
+    net = api.net_load(a.init) if a.init else api.net_create(api.net_default_config(mesh_conv=a.mesh_conv), a.seed)
     handles, pools = [], []
+    rgen = np.random.default_rng(a.seed + 17)
+    t_pcg = time.time()
     for (dx, dy), R in zip(grids, data):
         gh = api.ppe_create_grid(dx, dy)
+        if a.pcg_frac > 0:
+            pcg_residuals(api, gh, dx, dy, R, rgen, a.pcg_frac, a.pcg_kmax, dev)
         net.attach(gh)
         handles.append(gh)
         pools.append(torch.tensor(R, device=dev))
+    t_data += time.time() - t_pcg
     # held-out evaluation: the cylinder grid with a masked-divergence source
     w = I.config3(0)
     eg = api.ppe_create_grid(w.dx, w.dy, w.mask)
@@ -102,12 +138,17 @@ def main(argv=None):
     erhs = torch.tensor(w.f, dtype=torch.float64, device=dev)
 
     def evaluate():
+        out = {}
+        for keep in (0, 1):
+            api.ppe_set_options(eg, keep_dir_after_dlsm=keep)
+            x = torch.zeros_like(erhs)
+            hyb = api.ppe_solve(eg, erhs, x, 1e-8, api.PPE_MODE_HYBRID, api.PPE_PREC_MIXED, net=net)
+            out[f"hybrid{keep}"] = [hyb["iters_pcg"] + hyb["iters_dlsm"], hyb["iters_dlsm"], round(hyb["ms_total"], 2),
+                                    hyb["fell_back"]]
         x = torch.zeros_like(erhs)
-        hyb = api.ppe_solve(eg, erhs, x, 1e-8, api.PPE_MODE_HYBRID, api.PPE_PREC_MIXED, net=net)
-        x.zero_()
         pcg = api.ppe_solve(eg, erhs, x, 1e-8, api.PPE_MODE_PCG, api.PPE_PREC_MIXED)
-        return {"hybrid_iters": hyb["iters_pcg"] + hyb["iters_dlsm"], "hybrid_dlsm": hyb["iters_dlsm"],
-                "hybrid_ms": hyb["ms_total"], "pcg_iters": pcg["iters_pcg"], "pcg_ms": pcg["ms_total"]}
+        out["pcg"] = [pcg["iters_pcg"], round(pcg["ms_total"], 2)]
+        return out
 
     hp = api.net_default_hparams(lr0=a.lr, total_steps=a.steps, rho=a.rho)
     gen = np.random.default_rng(a.seed)
