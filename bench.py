@@ -353,35 +353,52 @@ def batch_vs_sequential(api, dev, flush, peaks, count=64):
             "effective_gbs": alg / tb / 1e9, "frac_of_hbm": alg / tb / 1e9 / peaks["hbm_gbs"]}
 
 
-def stencil_sweep(api, dev, peaks, n=8192, iters=60):
-    """Per-iteration cost of the persistent PCG kernel on an 8192^2 grid
-    (working set ~2 GB, far above L2): fixed iteration count, no refinement
-    convergence (the cap stops it)."""
+def stencil_sweep(api, dev, peaks, sizes=(4096, 8192, 16384), short=20, long=120):
+    """Per-iteration cost of the FP32 PCG iteration pass on grids far above L2:
+    two solves capped at `short` and `long` iterations (no residual
+    replacement in between), timed with CUDA events; the difference divided by
+    the extra iterations is the cost of one iteration pass over the grid."""
     import torch
-    dx = I.box_spacing(n, 0.4, 0.6, 1.01)
-    g = api.ppe_create_grid(dx, dx)
-    api.ppe_set_options(g, max_iters=iters)
-    rhs = torch.tensor(I.gaussian_rhs(dx, dx, I.rng(99)), dtype=torch.float64, device=dev)
+    out = []
+    for n in sizes:
+        dx = I.box_spacing(n, 0.4, 0.6, 1.01)
+        g = api.ppe_create_grid(dx, dx)
+        xc = np.cumsum(dx) - 0.5 * dx
+        gx = np.cos(np.pi * xc) + 0.3 * np.cos(3 * np.pi * xc)
+        gx -= np.dot(dx, gx) / dx.sum()         # volume-weighted zero mean: a compatible source
+        rhs = torch.outer(torch.tensor(gx, device=dev), torch.tensor(gx, device=dev)).contiguous()
+        for iter_pass in (1, 2):
+            out.append(_sweep_one(api, g, rhs, n, iter_pass, short, long, peaks))
+        g.close()
+        del rhs
+    return {"alg_bytes_per_cell_iter": 24, "method": f"(t[{long} its] - t[{short} its]) / extra iterations",
+            "grids": out}
+
+
+def _sweep_one(api, g, rhs, n, iter_pass, short, long, peaks):
+    import torch
     x = torch.zeros_like(rhs)
-    api.ppe_solve(g, rhs, x, 1e-14, api.PPE_MODE_PCG, api.PPE_PREC_MIXED, raise_on_error=False)
-    torch.cuda.synchronize()
-    times = []
-    for _ in range(3):
-        x.zero_()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        info = api.ppe_solve(g, rhs, x, 1e-14, api.PPE_MODE_PCG, api.PPE_PREC_MIXED, raise_on_error=False)
-        b.record()
-        torch.cuda.synchronize()
-        times.append(a.elapsed_time(b) / 1e3)
-    t = min(times)
-    N = n * n
-    # passes: INIT(8B) + RES(FP64: x, f, write r: 20B) + RESTART(4B) + iters*ITER(24B alg) + RES + FINAL
-    alg = N * (24.0 * info["iters_pcg"]) + N * (8 + 20) * info["refinements"] + N * 8 * 3
-    g.close()
-    return {"grid": f"{n}x{n}", "iters": info["iters_pcg"], "seconds": t,
-            "achieved_gbs": alg / t / 1e9, "frac_of_hbm": alg / t / 1e9 / peaks["hbm_gbs"],
-            "alg_bytes_per_cell_iter": 24}
+    t, info = {}, {}
+    for cap in (short, long):
+        api.ppe_set_options(g, max_iters=cap, inner_rtol=1e-12, iter_pass=iter_pass)
+        api.ppe_solve(g, rhs, x, 1e-14, api.PPE_MODE_PCG, api.PPE_PREC_MIXED, raise_on_error=False)
+        times = []
+        for _ in range(3):
+            x.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            info[cap] = api.ppe_solve(g, rhs, x, 1e-14, api.PPE_MODE_PCG, api.PPE_PREC_MIXED, raise_on_error=False)
+            b.record()
+            torch.cuda.synchronize()
+            times.append(a.elapsed_time(b) / 1e3)
+        t[cap] = min(times)
+    d_it = info[long]["iters_pcg"] - info[short]["iters_pcg"]
+    same_ref = info[long]["refinements"] == info[short]["refinements"]
+    t_it = (t[long] - t[short]) / max(d_it, 1)
+    gbs = 24.0 * n * n / t_it / 1e9
+    return {"grid": f"{n}x{n}", "iter_pass": ["", "tile", "stream"][iter_pass], "us_per_iter": 1e6 * t_it,
+            "achieved_gbs": gbs, "frac_of_hbm": gbs / peaks["hbm_gbs"], "extra_iters": d_it,
+            "same_refinements": same_ref}
 
 
 def main():

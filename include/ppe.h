@@ -99,7 +99,12 @@ typedef struct {
     int32_t blocks_per_sm;  /* persistent-kernel CTAs per SM (2; 0 = as many as fit)          */
     int32_t keep_dir_after_dlsm; /* 0: every CG-type phase restarts with p = z (Sec. 2.2 workflow,
                                as a fresh KSPSolve); 1: CG directions continue across DLSM steps */
-    int32_t reserved[6];
+    int32_t iter_pass;      /* MIXED precision only: 0 = choose by size (default), 1 = tiles of
+                               16x128 cells shared by a whole CTA, 2 = streaming (each warp
+                               marches down a 128-wide strip; for grids far larger than the
+                               number of CTAs).  Same arithmetic, same results up to rounding
+                               order.                                                          */
+    int32_t reserved[5];
 } ppe_solve_opts;
 
 PPE_API void ppe_default_options(ppe_solve_opts *opts);

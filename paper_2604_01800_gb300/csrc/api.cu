@@ -91,6 +91,55 @@ __global__ void pitch_copy_kernel(const float *src, float *dst, int nx, int ny, 
         dst[(k / nx) * pitch + k % nx] = src[k];
 }
 
+// Mean removal of a DLSM direction (A annihilates constants, so the loss of
+// Eq. 18 leaves the constant part of NN(r) free; removing it keeps the FP32
+// correction d from carrying a large constant).  Two kernels: per-block
+// partial sums, then every block forms the mean from the partials and
+// subtracts it.
+constexpr int DIR_PART_BLOCKS = 152;
+
+__global__ void __launch_bounds__(512) dir_partial_kernel(const float *e, int nx, int ny, int pitch, double *part)
+{
+    __shared__ double wsum[16];
+    const size_t n = (size_t)nx * ny;
+    float s = 0.f;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+        s += e[(k / nx) * pitch + k % nx];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = (double)s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wsum[w];
+        part[blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(512) dir_center_kernel(float *e, int nx, int ny, int pitch, const double *part,
+                                                         int nparts)
+{
+    __shared__ float mean;
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int b = 0; b < nparts; ++b) t += part[b];
+        mean = (float)(t / ((double)nx * ny));
+    }
+    __syncthreads();
+    const float m = mean;
+    const size_t n = (size_t)nx * ny;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+        e[(k / nx) * pitch + k % nx] -= m;
+}
+
+ppe_status center_direction(ppe_grid *g, cudaStream_t stream)
+{
+    dir_partial_kernel<<<DIR_PART_BLOCKS, 512, 0, stream>>>(g->e, g->nx, g->ny, g->pitch, g->dir_part);
+    const int nb = (int)std::min<size_t>(4 * DIR_PART_BLOCKS, ((size_t)g->nx * g->ny + 511) / 512);
+    dir_center_kernel<<<nb, 512, 0, stream>>>(g->e, g->nx, g->ny, g->pitch, g->dir_part, DIR_PART_BLOCKS);
+    PPE_CUDA_TRY(cudaGetLastError());
+    return PPE_OK;
+}
+
 }  // namespace ppe
 
 using namespace ppe;
@@ -119,7 +168,7 @@ void ppe_destroy_grid(ppe_grid *g)
     net_release_grid(g);
     cudaFree(g->dx); cudaFree(g->dy); cudaFree(g->fx); cudaFree(g->fy);
     cudaFree(g->dx32); cudaFree(g->dy32); cudaFree(g->fx32); cudaFree(g->fy32);
-    cudaFree(g->vec); cudaFree(g->e);
+    cudaFree(g->vec); cudaFree(g->e); cudaFree(g->tmaps_dev); cudaFree(g->dir_part);
     cudaFree(g->sys_dev); cudaFree(g->st_dev); cudaFree(g->ranges_dev); cudaFree(g->slots_dev);
     cudaFree(g->ctl_dev);
     cudaFree(g->dir_r); cudaFree(g->dir_e);
@@ -184,16 +233,27 @@ ppe_status ppe_create_grid(int nx, int ny, const double *dx, const double *dy, p
     G_ALLOC(g->fx32, (nx + 1) * 4); G_COPY(g->fx32, fx32.data(), (nx + 1) * 4);
     G_ALLOC(g->fy32, (ny + 1) * 4); G_COPY(g->fy32, fy32.data(), (ny + 1) * 4);
     size_t vbytes = (size_t)g->pitch * ny * 8;
-    G_ALLOC(g->vec, vbytes * 6);
+    G_ALLOC(g->vec, vbytes * 5);
     char *base = (char *)g->vec;
-    g->r[0] = base; g->r[1] = base + vbytes; g->s[0] = base + 2 * vbytes; g->s[1] = base + 3 * vbytes;
-    g->p = base + 4 * vbytes; g->d = base + 5 * vbytes;
+    g->r[0] = base; g->r[1] = base + vbytes; g->p[0] = base + 2 * vbytes; g->p[1] = base + 3 * vbytes;
+    g->d = base + 4 * vbytes;
+    {
+        CUtensorMap maps[3 * NMAPS];     // one set per kernel variant, in SolverVariant order
+        ppe_status ms = PPE_OK;
+        for (int v = 0; v < 3 && ms == PPE_OK; ++v)
+            ms = encode_solver_maps(g->r, g->p, g->d, nx, ny, g->pitch, (SolverVariant)v, maps + v * NMAPS);
+        if (ms != PPE_OK) return fail(ms);
+        G_ALLOC(g->tmaps_dev, sizeof maps);
+        G_COPY(g->tmaps_dev, maps, sizeof maps);
+    }
     G_ALLOC(g->e, (size_t)g->pitch * ny * 4);
+    G_ALLOC(g->dir_part, DIR_PART_BLOCKS * sizeof(double));
     {
         cudaError_t _e = cudaMemset(g->e, 0, (size_t)g->pitch * ny * 4);
         if (_e != cudaSuccess) return fail(cuda_status(_e, "cudaMemset(e)"));
     }
-    int ntiles = g->tiles_x * g->tiles_y;
+    // tile counts of the two tile widths; workspaces are sized for the larger
+    int ntiles = std::max(g->tiles_x, (nx + TILE_X_STREAM - 1) / TILE_X_STREAM) * g->tiles_y;
     G_ALLOC(g->sys_dev, sizeof(SysDesc));
     G_ALLOC(g->st_dev, sizeof(SysState));
     g->ranges_blocks = ntiles;
@@ -219,7 +279,8 @@ ppe_status ppe_set_options(ppe_grid *g, const ppe_solve_opts *o)
     clear_error();
     if (!g || !o) return arg_error("ppe_set_options: NULL argument");
     if (o->max_iters < 1 || o->num_cg < 1 || o->num_dlsm < 1 || o->hybrid_budget < 0 ||
-        !(o->inner_rtol > 0.0 && o->inner_rtol < 1.0) || !(o->dlsm_guard >= 0.0) || o->blocks_per_sm < 0)
+        !(o->inner_rtol > 0.0 && o->inner_rtol < 1.0) || !(o->dlsm_guard >= 0.0) || o->blocks_per_sm < 0 ||
+        o->iter_pass < 0 || o->iter_pass > 2)
         return arg_error("ppe_set_options: option out of range");
     g->opts = *o;
     return PPE_OK;
@@ -266,12 +327,14 @@ ppe_status ppe_apply(ppe_grid *g, const double *x, double *y, void *stream)
 namespace ppe {
 
 static SysDesc make_desc(const ppe_grid *g, const double *rhs, double *x, double tol, ppe_mode mode,
-                         ppe_precision prec, int tile0)
+                         ppe_precision prec, int tile0, SolverVariant v)
 {
     SysDesc sd;
     std::memset(&sd, 0, sizeof(sd));
-    sd.nx = g->nx; sd.ny = g->ny; sd.pitch = g->pitch; sd.tiles_x = g->tiles_x;
-    sd.tile0 = tile0; sd.ntiles = g->tiles_x * g->tiles_y;
+    const int tw = v == SV_FP32_STREAM ? TILE_X_STREAM : TILE_X;
+    sd.nx = g->nx; sd.ny = g->ny; sd.pitch = g->pitch;
+    sd.tiles_x = (g->nx + tw - 1) / tw; sd.tiles_y = g->tiles_y;
+    sd.tile0 = tile0; sd.ntiles = sd.tiles_x * sd.tiles_y;
     sd.mode = mode; sd.precision = prec;
     sd.max_iters = g->opts.max_iters; sd.num_cg = g->opts.num_cg; sd.num_dlsm = g->opts.num_dlsm;
     sd.hybrid_budget = g->opts.hybrid_budget;
@@ -285,8 +348,9 @@ static SysDesc make_desc(const ppe_grid *g, const double *rhs, double *x, double
     sd.dx = g->dx; sd.dy = g->dy; sd.fx = g->fx; sd.fy = g->fy;
     sd.dx32 = g->dx32; sd.dy32 = g->dy32; sd.fx32 = g->fx32; sd.fy32 = g->fy32;
     sd.f = rhs; sd.x = x;
-    sd.r[0] = g->r[0]; sd.r[1] = g->r[1]; sd.s[0] = g->s[0]; sd.s[1] = g->s[1];
-    sd.p = g->p; sd.d = g->d; sd.e = g->e;
+    sd.r[0] = g->r[0]; sd.r[1] = g->r[1]; sd.p[0] = g->p[0]; sd.p[1] = g->p[1];
+    sd.d = g->d; sd.e = g->e;
+    sd.tmaps = g->tmaps_dev + (int)v * NMAPS;
     return sd;
 }
 
@@ -354,9 +418,10 @@ static bool plan_blocks(std::vector<SysDesc> &sds, int max_blocks, std::vector<B
 // Drive the persistent launches of n systems until every one is done; run
 // the network between launches for the systems that wait for a direction.
 static ppe_status drive(int n, ppe_grid *const *grids, SysDesc *sys_dev, SysState *st_dev, BlockRange *ranges_dev,
-                        int blocks, Slot *slots_dev, int nslots, Control *ctl_dev, bool fp64, ppe_net *net,
-                        cudaStream_t stream, ppe_solve_info *info)
+                        int blocks, Slot *slots_dev, int nslots, Control *ctl_dev, SolverVariant variant,
+                        ppe_net *net, cudaStream_t stream, ppe_solve_info *info)
 {
+    const bool fp64 = variant == SV_FP64;
     SolverArgs a;
     a.sys = sys_dev; a.st = st_dev; a.ranges = ranges_dev; a.slots = slots_dev; a.nslots = nslots; a.ctl = ctl_dev;
     a.arrive = nullptr;
@@ -366,8 +431,8 @@ static ppe_status drive(int n, ppe_grid *const *grids, SysDesc *sys_dev, SysStat
     a.prof = nullptr;
     static const bool want_prof = std::getenv("PPE_SOLVER_PROFILE") != nullptr;
     if (want_prof) {
-        PPE_CUDA_TRY(cudaMalloc(&a.prof, 4 * sizeof(unsigned long long)));
-        PPE_CUDA_TRY(cudaMemsetAsync(a.prof, 0, 4 * sizeof(unsigned long long), stream));
+        PPE_CUDA_TRY(cudaMalloc(&a.prof, 8 * sizeof(unsigned long long)));
+        PPE_CUDA_TRY(cudaMemsetAsync(a.prof, 0, 8 * sizeof(unsigned long long), stream));
     }
 
     cudaEvent_t ev0, ev1;
@@ -386,7 +451,7 @@ static ppe_status drive(int n, ppe_grid *const *grids, SysDesc *sys_dev, SysStat
         ctl_host.active0 = active;
         PPE_CUDA_TRY(cudaMemcpyAsync(ctl_dev, &ctl_host, sizeof(Control), cudaMemcpyHostToDevice, stream));
         PPE_CUDA_TRY(cudaMemsetAsync(a.arrive, 0, sizeof(uint32_t) * n, stream));
-        status = launch_solver_resume(a, fp64, blocks, stream, round > 0 ? 1 : 0);
+        status = launch_solver_resume(a, variant, blocks, stream, round > 0 ? 1 : 0);
         if (status != PPE_OK) break;
         ++launches;
         PPE_CUDA_TRY(cudaMemcpyAsync(st.data(), st_dev, sizeof(SysState) * n, cudaMemcpyDeviceToHost, stream));
@@ -411,6 +476,8 @@ static ppe_status drive(int n, ppe_grid *const *grids, SysDesc *sys_dev, SysStat
                 pitch_copy_kernel<<<nb, 256, 0, stream>>>(g->dir_e, g->e, g->nx, g->ny, g->pitch);
                 cudaError_t ce = cudaGetLastError();
                 if (ce != cudaSuccess) { status = cuda_status(ce, "direction source"); break; }
+                status = center_direction(g, stream);
+                if (status != PPE_OK) break;
                 continue;
             }
             if (!net) { set_error("hybrid solve without a network or direction source"); status = PPE_ERR_NO_NET; break; }
@@ -422,12 +489,13 @@ static ppe_status drive(int n, ppe_grid *const *grids, SysDesc *sys_dev, SysStat
         if (launches > 10000000) { status = PPE_ERR_NOT_CONVERGED; break; }
     }
     if (a.prof) {
-        unsigned long long pr[4] = {0, 0, 0, 0};
+        unsigned long long pr[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         cudaMemcpyAsync(pr, a.prof, sizeof pr, cudaMemcpyDeviceToHost, stream);
         cudaStreamSynchronize(stream);
-        double st_ = pr[3] ? (double)pr[3] : 1.0;
-        std::fprintf(stderr, "[solver profile] blocks=%d steps=%llu  per step: pass %.2f us, wait+reduce+advance %.2f us\n",
-                     blocks, pr[3], pr[0] / st_ / 1e3, pr[2] / st_ / 1e3);
+        double st_ = pr[7] ? (double)pr[7] * 1e3 : 1.0;
+        std::fprintf(stderr, "[solver profile] blocks=%d steps=%llu  per step (us): pass %.2f, reduce+publish %.2f, "
+                     "wait %.2f, gather %.2f, advance %.2f\n", blocks, pr[7], pr[0] / st_, pr[1] / st_, pr[2] / st_,
+                     pr[3] / st_, pr[4] / st_);
         cudaFree(a.prof);
     }
     cudaFreeAsync(a.arrive, stream);
@@ -449,6 +517,18 @@ static ppe_status drive(int n, ppe_grid *const *grids, SysDesc *sys_dev, SysStat
         set_error(buf);
     }
     return worst;
+}
+
+// Kernel variant of a launch.  FP64 has one; in mixed precision the
+// streaming iteration pass pays off once every warp of the grid has at least
+// one tile (the tile-cooperative pass has lower latency on smaller grids).
+static SolverVariant pick_variant(ppe_precision prec, int iter_pass, int ntiles)
+{
+    if (prec == PPE_PREC_FP64) return SV_FP64;
+    if (iter_pass == 1) return SV_FP32_TILE;
+    if (iter_pass == 2) return SV_FP32_STREAM;
+    const int warps = solver_max_blocks(SV_FP32_STREAM, 0) * (SOLVER_THREADS / 32);
+    return ntiles >= warps ? SV_FP32_STREAM : SV_FP32_TILE;
 }
 
 static ppe_status check_solve_args(ppe_grid *g, const double *rhs, double *x, double tol, ppe_mode mode,
@@ -477,9 +557,9 @@ ppe_status ppe_solve(ppe_grid *g, const double *rhs, double *x, double tol, ppe_
     clear_error();
     PPE_TRY(check_solve_args(g, rhs, x, tol, mode, prec, net));
     cudaStream_t st = (cudaStream_t)stream;
-    std::vector<SysDesc> sds(1, make_desc(g, rhs, x, tol, mode, prec, 0));
-    bool fp64 = prec == PPE_PREC_FP64;
-    int maxb = std::min(solver_max_blocks(fp64, g->opts.blocks_per_sm), g->ranges_blocks);
+    const SolverVariant v = pick_variant(prec, g->opts.iter_pass, g->tiles_x * g->tiles_y);
+    std::vector<SysDesc> sds(1, make_desc(g, rhs, x, tol, mode, prec, 0, v));
+    int maxb = std::min(solver_max_blocks(v, g->opts.blocks_per_sm), sds[0].ntiles);
     if (maxb < 1) return cuda_status(cudaErrorInvalidConfiguration, "solver occupancy");
     std::vector<BlockRange> ranges;
     int nslots = 0;
@@ -489,7 +569,7 @@ ppe_status ppe_solve(ppe_grid *g, const double *rhs, double *x, double tol, ppe_
                                  cudaMemcpyHostToDevice, st));
     ppe_grid *gs[1] = {g};
     return drive(1, gs, g->sys_dev, g->st_dev, g->ranges_dev, (int)ranges.size(), g->slots_dev, nslots, g->ctl_dev,
-                 fp64, net, st, info);
+                 v, net, st, info);
 }
 
 ppe_status ppe_solve_batch(int n, ppe_grid *const *grids, const double *const *rhs, double *const *x, double tol,
@@ -504,12 +584,14 @@ ppe_status ppe_solve_batch(int n, ppe_grid *const *grids, const double *const *r
     cudaStream_t st = (cudaStream_t)stream;
     std::vector<SysDesc> sds(n);
     int ntiles = 0;
+    for (int i = 0; i < n; ++i) ntiles += grids[i]->tiles_x * grids[i]->tiles_y;
+    const SolverVariant v = pick_variant(prec, grids[0]->opts.iter_pass, ntiles);
+    ntiles = 0;
     for (int i = 0; i < n; ++i) {
-        sds[i] = make_desc(grids[i], rhs[i], x[i], tol, mode, prec, ntiles);
+        sds[i] = make_desc(grids[i], rhs[i], x[i], tol, mode, prec, ntiles, v);
         ntiles += sds[i].ntiles;
     }
-    bool fp64 = prec == PPE_PREC_FP64;
-    int maxb = std::min(solver_max_blocks(fp64, grids[0]->opts.blocks_per_sm), ntiles);
+    int maxb = std::min(solver_max_blocks(v, grids[0]->opts.blocks_per_sm), ntiles);
     std::vector<BlockRange> ranges;
     int nslots = 0;
     if (maxb < 1 || !plan_blocks(sds, maxb, ranges, nslots)) return arg_error("ppe_solve_batch: cannot partition");
@@ -531,7 +613,7 @@ ppe_status ppe_solve_batch(int n, ppe_grid *const *grids, const double *const *r
     }
     cudaMemcpyAsync(sys_dev, sds.data(), sizeof(SysDesc) * n, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(rg_dev, ranges.data(), sizeof(BlockRange) * ranges.size(), cudaMemcpyHostToDevice, st);
-    ppe_status status = drive(n, grids, sys_dev, st_dev, rg_dev, (int)ranges.size(), part_dev, nslots, ctl_dev, fp64, net,
+    ppe_status status = drive(n, grids, sys_dev, st_dev, rg_dev, (int)ranges.size(), part_dev, nslots, ctl_dev, v, net,
                               st, info);
     cudaStreamSynchronize(st);
     cleanup();

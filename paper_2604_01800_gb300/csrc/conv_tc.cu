@@ -27,6 +27,7 @@
 
 #include "net_internal.h"
 #include "net_kernels.cuh"
+#include "tma.cuh"
 
 namespace ppe {
 
@@ -44,70 +45,12 @@ struct TcArgs {
     int *err;
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ uint64_t gtimer()
-{
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
 // Bounded wait; returns false (and raises the error flag) on expiry.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err)
 {
-    if (mbar_try(bar, parity)) return true;
-    uint64_t t0 = gtimer();
-    while (!mbar_try(bar, parity)) {
-        if ((long long)(gtimer() - t0) > TC_WAIT_NS) {
-            atomicExch(err, 1);
-            return false;
-        }
-    }
-    return true;
-}
-
-__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, uint32_t bar, int c0, int c1, int c2,
-                                            int c3)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6}], "
-        "[%2];" ::"r"(dst),
-        "l"((uint64_t)map), "r"(bar), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
-        : "memory");
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, uint32_t bar, int c0, int c1)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
-            dst),
-        "l"((uint64_t)map), "r"(bar), "r"(c0), "r"(c1)
-        : "memory");
+    if (mbar_wait_bounded(bar, parity, TC_WAIT_NS)) return true;
+    atomicExch(err, 1);
+    return false;
 }
 
 // Shared-memory matrix descriptor of a K-major operand in the swizzled
@@ -189,7 +132,7 @@ __global__ void __launch_bounds__(128, 1)
             mbar_init(empty0 + 8 * s, 1);
         }
         mbar_init(accb, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        mbar_init_fence();
         asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
     }
@@ -323,20 +266,6 @@ __global__ void __launch_bounds__(128, 1)
 // host side
 // ---------------------------------------------------------------------------
 
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
-{
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        cudaDriverEntryPointQueryResult q;
-        void *p = nullptr;
-        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-    });
-    return fn;
-}
-
 int *err_flag()
 {
     static int *flag = nullptr;
@@ -355,7 +284,7 @@ int pick_bk(int cin) { return cin % 64 == 0 ? 64 : (cin % 32 == 0 ? 32 : 16); }
 // run outside any stream capture.
 ppe_status conv3x3_tc_prepare()
 {
-    if (!encode_fn()) {
+    if (!tensor_map_encoder()) {
         set_error("cuTensorMapEncodeTiled unavailable");
         return PPE_ERR_CUDA;
     }
@@ -373,7 +302,7 @@ ppe_status conv3x3_tc_prepare()
 bool conv3x3_tc_supported(const ConvArgs &a)
 {
     return a.cin % 16 == 0 && a.cout % 16 == 0 && a.cin >= 16 && a.cout >= 16 && a.H >= 1 && a.W >= 1 &&
-           a.B >= 1 && encode_fn() != nullptr;
+           a.B >= 1 && tensor_map_encoder() != nullptr;
 }
 
 ppe_status conv3x3_tc(const ConvArgs &a, cudaStream_t s)
@@ -383,7 +312,7 @@ ppe_status conv3x3_tc(const ConvArgs &a, cudaStream_t s)
         return PPE_ERR_ARG;
     }
     PPE_TRY(conv3x3_tc_prepare());
-    auto encode = encode_fn();
+    auto encode = tensor_map_encoder();
     int *err = err_flag();
     const int bk = pick_bk(a.cin);
     // output patch of 128 pixels: TW x TH with TW a power of two <= 128

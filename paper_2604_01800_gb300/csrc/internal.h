@@ -1,6 +1,7 @@
 // Internal declarations shared by the library's translation units.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -35,10 +36,20 @@ ppe_status cuda_status(cudaError_t e, const char *what);
 // tiling of the persistent solver kernel
 // ---------------------------------------------------------------------------
 constexpr int TILE_X = 128;                 // cells per tile row (4 per lane)
+constexpr int TILE_X_STREAM = 124;          // tile width of the streaming kernel: a warp row of
+                                            // 128 cells covers it plus a two-cell halo per side
 constexpr int TILE_Y = 16;                  // rows per tile (one warp each)
 constexpr int SOLVER_THREADS = 32 * TILE_Y;
 constexpr int NPART = 6;                    // FP64 partial sums per tile
 constexpr int PITCH_ALIGN = 32;             // inner-vector row pitch (elements)
+// A pass reads its tile with a halo: two cells in y and, so that the window
+// starts on a 16-byte boundary for the TMA unit, four cells in x.
+constexpr int WIN_OX = 4, WIN_OY = 2;
+constexpr int WIN_X = TILE_X + 2 * WIN_OX;  // 136 (window of a tile-cooperative tile)
+constexpr int WIN_Y = TILE_Y + 2 * WIN_OY;  // 20
+// Tensor maps of one system's inner vectors (per precision): the two residual
+// buffers and the two direction buffers (window boxes), and d (tile box).
+enum SolverMap : int { MAP_R0 = 0, MAP_R1 = 1, MAP_P0 = 2, MAP_P1 = 3, MAP_D = 4, NMAPS = 5 };
 
 inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
 
@@ -60,7 +71,7 @@ constexpr int SMAX = 8;   // systems one block may span
 
 // Static description of one system (device memory, written by the host).
 struct SysDesc {
-    int32_t nx, ny, pitch, tiles_x, tile0, ntiles;
+    int32_t nx, ny, pitch, tiles_x, tiles_y, tile0, ntiles;   // tiles numbered column by column
     int32_t mode, precision;              // ppe_mode, ppe_precision
     int32_t max_iters, num_cg, num_dlsm, hybrid_budget;
     int32_t part0, blk0, nparts;          // partial slots part0.. for blocks blk0..blk0+nparts-1
@@ -72,8 +83,9 @@ struct SysDesc {
     const float *dx32, *dy32, *fx32, *fy32;
     const double *f;                      // source S [ny][nx] (caller)
     double *x;                            // solution [ny][nx] (caller)
-    void *r[2], *s[2], *p, *d;            // inner vectors [ny][pitch], FP32 or FP64
+    void *r[2], *p[2], *d;                // inner vectors [ny][pitch], FP32 or FP64 (r, p double-buffered)
     float *e;                             // DLSM direction [ny][pitch]
+    const CUtensorMap *tmaps;             // NMAPS maps of r[0], r[1], p[0], p[1], d (device memory)
 };
 
 // Mutable per-system state.  Every block that works on a system keeps an
@@ -87,7 +99,7 @@ struct SysState {
     double alpha, beta, gamma, mu, mu_b, bnorm, target, rnorm, relres, incompat;
     double alpha_d, xmean, rho, rho_ref;
     float alpha_f, beta_f, mu_f, alpha_d_f;   // FP32 copies for the FP32 passes
-    int32_t dlsm_useless, pad2_;
+    int32_t dlsm_useless, pcur;           // pcur: which p buffer holds the current direction
 };
 
 // Tiles [t0, t1) of a block; they belong to systems s0..s1.
@@ -126,12 +138,27 @@ struct SolverArgs {
     Control *ctl;
     int32_t nsys, ntiles;
     int64_t spin_limit_ns;
-    unsigned long long *prof;  // nullable: block 0 accumulates ns in pass / barrier / advance, and steps
+    unsigned long long *prof;  // nullable: block 0 accumulates ns per step part [0..4] and the step count [7]
 };
 
-ppe_status launch_solver_resume(const SolverArgs &a, bool fp64, int grid_blocks, cudaStream_t stream,
+// Solver kernel variants: FP64, FP32 with the tile-cooperative iteration
+// pass, FP32 with the streaming iteration pass.
+enum SolverVariant : int { SV_FP64 = 0, SV_FP32_TILE = 1, SV_FP32_STREAM = 2 };
+
+ppe_status launch_solver_resume(const SolverArgs &a, SolverVariant v, int grid_blocks, cudaStream_t stream,
                                 int resume);
-int solver_max_blocks(bool fp64, int blocks_per_sm_req);
+int solver_max_blocks(SolverVariant v, int blocks_per_sm_req);
+
+// Encode the NMAPS tensor maps of one system's inner vectors for a kernel
+// variant (element type FP32 or FP64, box shapes of the variant's tiles; row
+// pitch `pitch` elements, a multiple of 4; every buffer 16-byte aligned).
+// Cells outside [0,nx) x [0,ny) read as zero.
+ppe_status encode_solver_maps(void *const r[2], void *const p[2], void *d, int nx, int ny, int pitch,
+                              SolverVariant v, CUtensorMap out[NMAPS]);
+
+// Remove the mean of the grid's DLSM direction e (two kernels on `stream`;
+// no allocation, so it may run inside a stream capture).
+ppe_status center_direction(ppe_grid *g, cudaStream_t stream);
 
 }  // namespace ppe
 
@@ -146,9 +173,11 @@ struct ppe_grid {
     // device copies
     double *dx = nullptr, *dy = nullptr, *fx = nullptr, *fy = nullptr;
     float *dx32 = nullptr, *dy32 = nullptr, *fx32 = nullptr, *fy32 = nullptr;
-    void *vec = nullptr;                 // 6 inner vectors, 8 bytes per element
+    void *vec = nullptr;                 // 5 inner vectors, 8 bytes per element
     float *e = nullptr;                  // DLSM direction
-    void *r[2] = {nullptr, nullptr}, *s[2] = {nullptr, nullptr}, *p = nullptr, *d = nullptr;
+    double *dir_part = nullptr;          // partial sums of the direction's mean removal
+    void *r[2] = {nullptr, nullptr}, *p[2] = {nullptr, nullptr}, *d = nullptr;
+    CUtensorMap *tmaps_dev = nullptr;    // [FP32 maps | FP64 maps] of the inner vectors
     // single-system launch resources
     ppe::SysDesc *sys_dev = nullptr;
     ppe::SysState *st_dev = nullptr;

@@ -457,7 +457,7 @@ ppe_status net_forward(ppe_net *n, NetCache *c, int B, const InputSrc &src, cons
 }
 
 // The DLSM direction of a solver system: the forward pass on its normalised
-// residual.  The sequence of launches is the same on every call, so it is
+// residual, with its mean removed.  The sequence of launches is the same on every call, so it is
 // captured once into a CUDA graph (per grid and parameter version) and
 // replayed with a single launch afterwards.
 ppe_status net_direction(ppe_net *net, ppe_grid *g, const SysDesc *sd_dev, const SysState *st_dev, bool,
@@ -481,6 +481,7 @@ ppe_status net_direction(ppe_net *net, ppe_grid *g, const SysDesc *sd_dev, const
         cudaGraph_t graph = nullptr;
         PPE_CUDA_TRY(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
         ppe_status fs = net_forward(net, c, 1, src, net->params, g->e, g->pitch, 0, false, c->cap_stream);
+        if (fs == PPE_OK) fs = center_direction(g, c->cap_stream);
         cudaError_t ce = cudaStreamEndCapture(c->cap_stream, &graph);
         if (fs != PPE_OK) {
             if (graph) cudaGraphDestroy(graph);

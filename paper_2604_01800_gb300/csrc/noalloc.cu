@@ -12,7 +12,7 @@
 // only the grid widths, the source and the solution buffer.
 //
 // Limits: nx, ny <= 4096 and nx*ny <= 65536 cells, plain PCG.  Every GPU that
-// loads the library holds the array (about 3.5 MB) until the process exits.
+// loads the library holds the array (about 3.3 MB) until the process exits.
 // All calls share the array and it keeps the last call's contents: each call
 // clears what must start at zero, and calls whose work overlaps on the GPU
 // race with each other.  The first call on a device looks the array's device
@@ -34,6 +34,10 @@ namespace {
 constexpr int NA_MAX_CELLS = 65536;
 constexpr int NA_MAX_DIM = 4096;
 constexpr int NA_MAX_BLOCKS = 1024;
+// Rows are padded to a multiple of 4 elements (16 bytes in FP32, as the TMA
+// unit requires); the padded vectors hold at most this many elements.
+constexpr int NA_PITCH_ALIGN = 4;
+constexpr size_t NA_MAX_PADDED = (size_t)NA_MAX_CELLS + (size_t)(NA_PITCH_ALIGN - 1) * NA_MAX_DIM;
 
 // byte layout of the scratch array (every part 256-byte aligned)
 constexpr size_t al(size_t x) { return (x + 255) / 256 * 256; }
@@ -51,9 +55,10 @@ constexpr size_t OFF_DX32 = OFF_FY + al(8 * (NA_MAX_DIM + 1));
 constexpr size_t OFF_DY32 = OFF_DX32 + al(4 * NA_MAX_DIM);
 constexpr size_t OFF_FX32 = OFF_DY32 + al(4 * NA_MAX_DIM);
 constexpr size_t OFF_FY32 = OFF_FX32 + al(4 * (NA_MAX_DIM + 1));
-constexpr size_t OFF_VEC = OFF_FY32 + al(4 * (NA_MAX_DIM + 1));
-constexpr size_t VEC_BYTES = al(8 * (size_t)NA_MAX_CELLS);
-constexpr size_t SCRATCH_BYTES = OFF_VEC + 6 * VEC_BYTES;
+constexpr size_t OFF_MAPS = OFF_FY32 + al(4 * (NA_MAX_DIM + 1));
+constexpr size_t OFF_VEC = OFF_MAPS + al(sizeof(CUtensorMap) * NMAPS);
+constexpr size_t VEC_BYTES = al(8 * NA_MAX_PADDED);
+constexpr size_t SCRATCH_BYTES = OFF_VEC + 5 * VEC_BYTES;
 
 // The scratch.  In host code this name is only a stand-in symbol, never a
 // device address: host code must use the address cudaGetSymbolAddress returns.
@@ -144,7 +149,8 @@ extern "C" ppe_status ppe_solve_noalloc(int nx, int ny, const double *dx, const 
     const bool fp64 = precision == PPE_PREC_FP64;
     const int tiles_x = (nx + TILE_X - 1) / TILE_X, tiles_y = (ny + TILE_Y - 1) / TILE_Y;
     const int ntiles = tiles_x * tiles_y;
-    int maxb = solver_max_blocks(fp64, 1);
+    const SolverVariant v = fp64 ? SV_FP64 : SV_FP32_TILE;
+    int maxb = solver_max_blocks(v, 1);
     if (maxb < 1) return cuda_status(cudaErrorInvalidConfiguration, "solver occupancy");
     if (maxb > NA_MAX_BLOCKS) maxb = NA_MAX_BLOCKS;
     const int chunk = (ntiles + maxb - 1) / maxb;
@@ -160,7 +166,9 @@ extern "C" ppe_status ppe_solve_noalloc(int nx, int ny, const double *dx, const 
     ppe_default_options(&opts);
     SysDesc sd;
     std::memset(&sd, 0, sizeof sd);
-    sd.nx = nx; sd.ny = ny; sd.pitch = nx; sd.tiles_x = tiles_x; sd.tile0 = 0; sd.ntiles = ntiles;
+    const int pitch = round_up(nx, NA_PITCH_ALIGN);
+    sd.nx = nx; sd.ny = ny; sd.pitch = pitch; sd.tiles_x = tiles_x; sd.tiles_y = tiles_y; sd.tile0 = 0;
+    sd.ntiles = ntiles;
     sd.mode = PPE_MODE_PCG; sd.precision = precision;
     sd.max_iters = opts.max_iters; sd.num_cg = opts.num_cg; sd.num_dlsm = opts.num_dlsm;
     sd.hybrid_budget = opts.hybrid_budget;
@@ -175,8 +183,12 @@ extern "C" ppe_status ppe_solve_noalloc(int nx, int ny, const double *dx, const 
     sd.dx32 = d_dx32; sd.dy32 = d_dy32; sd.fx32 = d_fx32; sd.fy32 = d_fy32;
     sd.f = rhs_dev; sd.x = x_dev;
     unsigned char *vec = base + OFF_VEC;
-    sd.r[0] = vec; sd.r[1] = vec + VEC_BYTES; sd.s[0] = vec + 2 * VEC_BYTES; sd.s[1] = vec + 3 * VEC_BYTES;
-    sd.p = vec + 4 * VEC_BYTES; sd.d = vec + 5 * VEC_BYTES; sd.e = nullptr;
+    sd.r[0] = vec; sd.r[1] = vec + VEC_BYTES; sd.p[0] = vec + 2 * VEC_BYTES; sd.p[1] = vec + 3 * VEC_BYTES;
+    sd.d = vec + 4 * VEC_BYTES; sd.e = nullptr;
+    CUtensorMap maps[NMAPS];
+    PPE_TRY(encode_solver_maps(sd.r, sd.p, sd.d, nx, ny, pitch, v, maps));
+    CUtensorMap *d_maps = (CUtensorMap *)(base + OFF_MAPS);
+    sd.tmaps = d_maps;
 
     SysDesc *d_sd = (SysDesc *)(base + OFF_DESC);
     SysState *d_st = (SysState *)(base + OFF_STATE);
@@ -185,6 +197,7 @@ extern "C" ppe_status ppe_solve_noalloc(int nx, int ny, const double *dx, const 
     BlockRange *d_ranges = (BlockRange *)(base + OFF_RANGES);
     Slot *d_slots = (Slot *)(base + OFF_SLOTS);
     PPE_CUDA_TRY(cudaMemcpyAsync(d_sd, &sd, sizeof sd, cudaMemcpyHostToDevice, st));
+    PPE_CUDA_TRY(cudaMemcpyAsync(d_maps, maps, sizeof maps, cudaMemcpyHostToDevice, st));
     PPE_CUDA_TRY(cudaMemcpyAsync(d_ranges, ranges, sizeof(BlockRange) * blocks, cudaMemcpyHostToDevice, st));
     // what must start at zero: state (phase INIT), control block, arrival counter
     PPE_CUDA_TRY(cudaMemsetAsync(d_st, 0, sizeof(SysState), st));
@@ -195,7 +208,7 @@ extern "C" ppe_status ppe_solve_noalloc(int nx, int ny, const double *dx, const 
     std::memset(&a, 0, sizeof a);
     a.sys = d_sd; a.st = d_st; a.ranges = d_ranges; a.slots = d_slots; a.nslots = blocks; a.ctl = d_ctl;
     a.arrive = d_arrive; a.nsys = 1; a.ntiles = ntiles; a.spin_limit_ns = 2000000000LL; a.prof = nullptr;
-    PPE_TRY(launch_solver_resume(a, fp64, blocks, st, 0));
+    PPE_TRY(launch_solver_resume(a, v, blocks, st, 0));
 
     SysState s;
     Control c;

@@ -5,9 +5,9 @@
 // One cooperative launch runs the per-system state machine of every system of
 // a batch.  Each block owns a contiguous range of tiles (of one or a few
 // systems).  A step: every block runs the current pass of each of its systems
-// over its tiles and writes one FP64 partial-sum record per system, then
-// arrives at a grid-wide counter barrier.  After the barrier each block reads
-// the partial records of its systems (fixed order, so every block obtains the
+// over its tiles and writes one partial-sum record per system, then arrives
+// at a per-system counter barrier.  After the barrier each block reads the
+// partial records of its systems (fixed order, so every block obtains the
 // same sums bit for bit) and advances its own copy of each system's state.
 // There is no serial finisher: a step costs one barrier plus one read of the
 // partial records.  The kernel returns when no system has a pass left (all
@@ -19,12 +19,20 @@
 // with face coefficients f = 2 / (width_left + width_right) and 0 at walls.
 //
 // PCG variant: Chronopoulos-Gear single-reduction CG with Jacobi
-// preconditioning.  Per iteration, with u = D^-1 r and w = A u:
-//   p = u + beta p,  s = w + beta s  (s = A p),  x += alpha p,  r -= alpha s,
-//   gamma' = r.u, delta' = (A u).u, beta' = gamma'/gamma,
-//   alpha' = gamma' / (delta' - beta' gamma' / alpha).
-// Each block recomputes the new residual on a one-cell ring around its tile
-// (reading r two cells out) so that A u' is available in the same pass.
+// preconditioning.  Per iteration, with u = D^-1 r:
+//   p = u + beta p,  x += alpha p,  r -= alpha A p,
+//   gamma' = r.u, delta' = (A u).u on the new residual, beta' = gamma'/gamma,
+//   alpha' = gamma' / p'.A p'  with  p'.A p' = delta' + 2 beta' u'.(A p) + beta'^2 p.(A p).
+// A p is not stored: each block rebuilds p on its tile plus a two-cell halo
+// (from r and the previous p, both read two cells out), applies A on a
+// one-cell ring, forms the new residual and u there, and applies A once more
+// on the tile.  Stored per iteration: r, p (double-buffered) and the
+// correction d, i.e. 12 bytes read and 12 written per cell in FP32.
+//
+// The iteration pass streams a block's tiles through two shared-memory
+// stages: while one tile is computed, the TMA unit loads the next tile's r
+// and p windows and its d tile (zero-filled outside the grid, which is the
+// Neumann stencil's zero padding).
 //
 // Mixed precision: the FP32 recursive residual is replaced by the FP64 true
 // residual b - A(x + d) whenever it has dropped by a factor ru_delta since
@@ -38,30 +46,25 @@
 #include <mutex>
 
 #include "internal.h"
+#include "tma.cuh"
 
 namespace ppe {
 
 namespace {
 
-constexpr int WX = TILE_X + 4;     // tile window with a two-cell halo
-constexpr int WY = TILE_Y + 4;
-constexpr int WN = WX * WY;
+// Geometry of a tile of width TW (128 for the tile-cooperative kernels, 124
+// for the streaming kernel) and 16 rows, with its window (halo 4 in x so that
+// the window starts on a 16-byte boundary, halo 2 in y) and one-cell ring.
+template <int TW> struct Geo {
+    static constexpr int TX = TW;
+    static constexpr int OX = WIN_OX, OY = WIN_OY;
+    static constexpr int WX = TW + 2 * WIN_OX, WY = TILE_Y + 2 * WIN_OY, WN = WX * WY;
+    static constexpr int WN_PAD = (WN + 31) / 32 * 32;     // window buffers padded to 128 bytes (FP32)
+    static constexpr int RX = TW + 2, RY = TILE_Y + 2, RN = RX * RY;
+    static constexpr int TN = TW * TILE_Y;
+    static constexpr int NRL = (RN + SOLVER_THREADS - 1) / SOLVER_THREADS;   // ring loads per thread
+};
 constexpr int NWARP = SOLVER_THREADS / 32;
-constexpr int NL = (WN + SOLVER_THREADS - 1) / SOLVER_THREADS;   // window loads per thread
-
-__device__ __forceinline__ uint64_t globaltimer_ns()
-{
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p)
-{
-    unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
 
 template <typename T> __device__ __forceinline__ T ld_cg(const T *p) { return __ldcg(p); }
 
@@ -69,49 +72,102 @@ template <typename T> __device__ __forceinline__ T recip(T v);
 template <> __device__ __forceinline__ float recip<float>(float v) { return v > 0.f ? __frcp_rn(v) : 0.f; }
 template <> __device__ __forceinline__ double recip<double>(double v) { return v > 0.0 ? 1.0 / v : 0.0; }
 
-// Coefficients of the tile window, in the arithmetic type C.
-template <typename C> struct Coef {
-    C dx[WX], fw[WX], fe[WX], sx[WX];
-    C dy[WY], fs[WY], fn[WY], sy[WY];
+// Coefficients over the tile window, in the arithmetic type C.
+template <typename C, int TW> struct Coef {
+    C dx[Geo<TW>::WX], fw[Geo<TW>::WX], fe[Geo<TW>::WX], sx[Geo<TW>::WX];
+    C dy[Geo<TW>::WY], fs[Geo<TW>::WY], fn[Geo<TW>::WY], sy[Geo<TW>::WY];
 };
 
-template <typename C> struct Work {
-    C a0[WN], a1[WN], a2[WN], a3[WN], a4[WN], a5[WN];
+// TMA destinations of one tile: r and p windows, d tile (sizes are multiples
+// of 128 bytes, so every part stays 128-byte aligned).
+template <typename T, int TW> struct Stage {
+    T r[Geo<TW>::WN_PAD];
+    T p[Geo<TW>::WN_PAD];
+    T d[Geo<TW>::TN];
+};
+static_assert((Geo<TILE_X>::WN_PAD * 4) % 128 == 0 && (Geo<TILE_X>::TN * 4) % 128 == 0,
+              "TMA destinations must stay 128-byte aligned");
+
+template <typename T, int TW> struct IterBufs {
+    Stage<T, TW> st[2];
+    T un[Geo<TW>::WN_PAD];    // new u on the one-cell ring
+    T q[Geo<TW>::WN_PAD];     // A p on the one-cell ring
 };
 
-template <typename T> struct SmemT {
-    Coef<double> cfd;
-    Coef<float> cff;
-    Work<T> w;
+// Scratch windows of the other passes.
+template <typename T, int TW> struct Work {
+    T a0[Geo<TW>::WN_PAD], a1[Geo<TW>::WN_PAD], a2[Geo<TW>::WN_PAD];
+};
+
+// Per-warp TMA chunks of the streaming pass: two buffers of four rows of the
+// r and p windows (132 wide) and of d (124 wide), each part padded to 128 bytes.
+constexpr int SRB = 4;
+constexpr int S_WX = TILE_X_STREAM + 2 * WIN_OX;
+constexpr int S_RBYTES = S_WX * SRB * 4, S_RPAD = (S_RBYTES + 127) / 128 * 128;
+constexpr int S_DBYTES = TILE_X_STREAM * SRB * 4, S_DPAD = (S_DBYTES + 127) / 128 * 128;
+constexpr int S_CHUNK = 2 * S_RPAD + S_DPAD;
+struct StreamBufs {
+    unsigned char buf[SOLVER_THREADS / 32][2][S_CHUNK];
+};
+
+template <typename T, int TW> union PassBufs {
+    IterBufs<T, TW> it;
+    Work<T, TW> w;
+};
+template <typename T> union PassBufs<T, TILE_X_STREAM> {
+    Work<T, TILE_X_STREAM> w;
+    StreamBufs sb;
+};
+
+template <typename T, int TW_> struct SmemT {
+    static constexpr int TW = TW_;
+    PassBufs<T, TW_> u;                  // first member: 128-byte aligned
+    unsigned long long bar[2];           // TMA completion barriers of the two stages
+    unsigned long long sbar[NWARP][2];   // streaming pass: per-warp chunk barriers
+    uint32_t sfills[NWARP];              // streaming pass: chunks issued per warp (buffer = fill & 1)
+    Coef<double, TW_> cfd;
+    Coef<float, TW_> cff;
     float red_hi[NPART][NWARP], red_lo[NPART][NWARP];
+    float pub_hi[NPART], pub_lo[NPART];
     SysDesc sd[SMAX];
     SysState st[SMAX];
-    double tot[NPART];
     int32_t tag_d, tag_f;   // tile whose coefficients are in cfd / cff
     int32_t go;
+    uint32_t fills;         // TMA stage fills issued so far (stage = fill & 1)
 };
 
-template <typename C>
-__device__ void load_coef(Coef<C> &cf, const SysDesc &sd, int i0, int j0, const C *DX, const C *FX,
+// Dynamic shared memory of a block (plus 128 bytes of alignment slack): two
+// FP32 blocks per SM, one FP64 block.
+static_assert(2 * (sizeof(SmemT<float, TILE_X>) + 128 + 1024) <= 228 * 1024, "FP32 solver: two blocks per SM");
+static_assert(sizeof(SmemT<double, TILE_X>) + 128 <= 227 * 1024, "FP64 solver: one block per SM");
+static_assert(sizeof(SmemT<float, TILE_X_STREAM>) + 128 <= 227 * 1024, "streaming solver: one block per SM");
+
+template <typename C, int TW>
+__device__ void load_coef(Coef<C, TW> &cf, const SysDesc &sd, int i0, int j0, const C *DX, const C *FX,
                           const C *DY, const C *FY)
 {
+    constexpr int WX = Geo<TW>::WX, WY = Geo<TW>::WY, OX = Geo<TW>::OX, OY = Geo<TW>::OY;
     for (int k = threadIdx.x; k < WX; k += blockDim.x) {
-        int i = i0 - 2 + k;
+        int i = i0 - OX + k;
         bool in = i >= 0 && i < sd.nx;
         C w = in ? DX[i] : C(0), a = in ? FX[i] : C(0), b = in ? FX[i + 1] : C(0);
         cf.dx[k] = w; cf.fw[k] = a; cf.fe[k] = b; cf.sx[k] = a + b;
     }
     for (int k = threadIdx.x; k < WY; k += blockDim.x) {
-        int j = j0 - 2 + k;
+        int j = j0 - OY + k;
         bool in = j >= 0 && j < sd.ny;
         C w = in ? DY[j] : C(0), a = in ? FY[j] : C(0), b = in ? FY[j + 1] : C(0);
         cf.dy[k] = w; cf.fs[k] = a; cf.fn[k] = b; cf.sy[k] = a + b;
     }
 }
 
-template <typename T, typename S> __device__ __forceinline__ Coef<T> &coef_of(S &sm);
-template <> __device__ __forceinline__ Coef<float> &coef_of<float, SmemT<float>>(SmemT<float> &sm) { return sm.cff; }
-template <> __device__ __forceinline__ Coef<double> &coef_of<double, SmemT<double>>(SmemT<double> &sm) { return sm.cfd; }
+template <typename T, typename S> __device__ __forceinline__ Coef<T, S::TW> &coef_of(S &sm)
+{
+    if constexpr (sizeof(T) == 4)
+        return sm.cff;
+    else
+        return sm.cfd;
+}
 
 // Coefficients of a tile do not change between steps: a block that keeps
 // working on the same tile reuses them.  Every caller synchronises the block
@@ -142,14 +198,15 @@ template <typename T, typename S> __device__ __forceinline__ void load_coef_t(S 
         load_coef_d(sm, sd, i0, j0, tag);
 }
 
-template <typename C> __device__ __forceinline__ C dinv_at(const Coef<C> &cf, int wi, int wj)
+template <typename C, int TW> __device__ __forceinline__ C dinv_at(const Coef<C, TW> &cf, int wi, int wj)
 {
     return recip<C>(cf.dy[wj] * cf.sx[wi] + cf.dx[wi] * cf.sy[wj]);
 }
 
 // (A U) at window point (wi, wj); U holds the window, zero outside the domain.
-template <typename C> __device__ __forceinline__ C stencil(const Coef<C> &cf, const C *U, int wi, int wj)
+template <typename C, int TW> __device__ __forceinline__ C stencil(const Coef<C, TW> &cf, const C *U, int wi, int wj)
 {
+    constexpr int WX = Geo<TW>::WX;
     int k = wj * WX + wi;
     C c = U[k];
     C ax = cf.fe[wi] * (c - U[k + 1]) + cf.fw[wi] * (c - U[k - 1]);
@@ -174,10 +231,25 @@ template <> __device__ __forceinline__ double sc_alpha_d<double>(const SysState 
 
 __device__ __forceinline__ bool in_dom(const SysDesc &sd, int i, int j)
 {
-    return i >= 0 && j >= 0 && i < sd.nx && j < sd.ny;
+    return (unsigned)i < (unsigned)sd.nx && (unsigned)j < (unsigned)sd.ny;
 }
 
-__device__ __forceinline__ bool in_ring1(int wi, int wj) { return wi >= 1 && wi < WX - 1 && wj >= 1 && wj < WY - 1; }
+// k-th point of the one-cell ring around the tile, as window coordinates
+template <int TW> __device__ __forceinline__ void ring_point(int k, int &wi, int &wj)
+{
+    wi = Geo<TW>::OX - 1 + k % Geo<TW>::RX;
+    wj = Geo<TW>::OY - 1 + k / Geo<TW>::RX;
+}
+
+// Tiles are numbered column by column (a strip of tiles stacked in y), so a
+// contiguous range of tiles is mostly a vertical strip: the streaming
+// iteration pass marches down it.
+template <int TW> __device__ __forceinline__ void tile_origin(const SysDesc &sd, int t, int &i0, int &j0)
+{
+    int lt = t - sd.tile0;
+    i0 = (lt / sd.tiles_y) * TW;
+    j0 = (lt % sd.tiles_y) * TILE_Y;
+}
 
 // Float-float (hi + lo) accumulation: ~48-bit sums on the FP32 pipes.  On
 // this chip FP64 arithmetic runs at a small fraction of the FP32 rate, so the
@@ -262,13 +334,17 @@ __device__ __forceinline__ double fast_div(double a, double b)
 // b statistics: b = -V S
 template <typename T, typename S> __device__ void pass_init(S &sm, const SysDesc &sd, int i0, int j0, Acc &acc)
 {
+    using G = Geo<S::TW>;
+    constexpr int WX = G::WX, WN = G::WN, OX = G::OX, OY = G::OY, RN = G::RN, NRL = G::NRL, TILE_X = G::TX;
+    constexpr int TILE_N = G::TN;
+    (void)WX; (void)WN; (void)OX; (void)OY; (void)RN; (void)NRL; (void)TILE_X; (void)TILE_N;
     double t[NPART] = {0, 0, 0, 0, 0, 0};
     const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
     int j = j0 + ty;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
         int i = i0 + tx + 32 * c;
-        if (i < sd.nx && j < sd.ny) {
+        if (tx + 32 * c < TILE_X && i < sd.nx && j < sd.ny) {
             double b = -sd.dx[i] * sd.dy[j] * sd.f[(size_t)j * sd.nx + i];
             t[0] += b; t[1] += b * b; t[2] += fabs(b);
         }
@@ -280,37 +356,41 @@ template <typename T, typename S> __device__ void pass_init(S &sm, const SysDesc
 template <typename T, typename S>
 __device__ void pass_res(S &sm, const SysDesc &sd, const SysState &st, int i0, int j0, int tag, Acc &acc)
 {
-    Coef<double> &cf = sm.cfd;
-    double *X = reinterpret_cast<double *>(&sm.w);
+    using G = Geo<S::TW>;
+    constexpr int WX = G::WX, WN = G::WN, OX = G::OX, OY = G::OY, RN = G::RN, NRL = G::NRL, TILE_X = G::TX;
+    constexpr int TILE_N = G::TN;
+    (void)WX; (void)WN; (void)OX; (void)OY; (void)RN; (void)NRL; (void)TILE_X; (void)TILE_N;
+    auto &cf = sm.cfd;
+    double *X = reinterpret_cast<double *>(&sm.u.w);
     load_coef_d(sm, sd, i0, j0, tag);
     const T *d = (const T *)sd.d;
-    double xv[NL];
+    double xv[NRL];
 #pragma unroll
-    for (int q = 0; q < NL; ++q) {
-        int k = threadIdx.x + q * SOLVER_THREADS;
+    for (int q = 0; q < NRL; ++q) {
+        int k = threadIdx.x + q * SOLVER_THREADS, wi, wj;
+        ring_point<S::TW>(k, wi, wj);
+        int i = i0 - OX + wi, j = j0 - OY + wj;
         xv[q] = 0.0;
-        if (k < WN) {
-            int wi = k % WX, wj = k / WX, i = i0 - 2 + wi, j = j0 - 2 + wj;
-            if (in_ring1(wi, wj) && in_dom(sd, i, j)) {
-                xv[q] = ld_cg(sd.x + (size_t)j * sd.nx + i);
-                if (st.has_d) xv[q] += (double)ld_cg(d + (size_t)j * sd.pitch + i);
-            }
+        if (k < RN && in_dom(sd, i, j)) {
+            xv[q] = ld_cg(sd.x + (size_t)j * sd.nx + i);
+            if (st.has_d) xv[q] += (double)ld_cg(d + (size_t)j * sd.pitch + i);
         }
     }
 #pragma unroll
-    for (int q = 0; q < NL; ++q) {
-        int k = threadIdx.x + q * SOLVER_THREADS;
-        if (k < WN) X[k] = xv[q];
+    for (int q = 0; q < NRL; ++q) {
+        int k = threadIdx.x + q * SOLVER_THREADS, wi, wj;
+        ring_point<S::TW>(k, wi, wj);
+        if (k < RN) X[wj * WX + wi] = xv[q];
     }
     __syncthreads();
     double t[NPART] = {0, 0, 0, 0, 0, 0};
     const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
-    int j = j0 + ty, wj = ty + 2;
+    int j = j0 + ty, wj = ty + OY;
     T *r = (T *)sd.r[st.cur];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-        int i = i0 + tx + 32 * c, wi = tx + 32 * c + 2;
-        if (i < sd.nx && j < sd.ny) {
+        int i = i0 + tx + 32 * c, wi = tx + 32 * c + OX;
+        if (tx + 32 * c < TILE_X && i < sd.nx && j < sd.ny) {
             double b = -sd.dx[i] * sd.dy[j] * ld_cg(sd.f + (size_t)j * sd.nx + i) - st.mu_b;
             double rv = b - stencil<double>(cf, X, wi, wj);
             r[(size_t)j * sd.pitch + i] = (T)rv;
@@ -321,53 +401,63 @@ __device__ void pass_res(S &sm, const SysDesc &sd, const SysState &st, int i0, i
     __syncthreads();
 }
 
-// u = D^-1 (r - mu), w = A u; dots r.u, w.u, r.r, sum r.  Folds d into x
-// when a replacement is pending.
+// u = D^-1 (r - mu), w = A u; dots r.u, w.u, r.r, sum r.  When the direction
+// is kept (continuation), also u.(A p) and p.(A p) of the current p.  Folds d
+// into x when a replacement is pending.
 template <typename T, typename S>
 __device__ void pass_restart(S &sm, const SysDesc &sd, const SysState &st, int i0, int j0, int tag, Acc &acc)
 {
-    Coef<T> &cf = coef_of<T>(sm);
-    T *R = sm.w.a0, *U = sm.w.a1;
+    using G = Geo<S::TW>;
+    constexpr int WX = G::WX, WN = G::WN, OX = G::OX, OY = G::OY, RN = G::RN, NRL = G::NRL, TILE_X = G::TX;
+    constexpr int TILE_N = G::TN;
+    (void)WX; (void)WN; (void)OX; (void)OY; (void)RN; (void)NRL; (void)TILE_X; (void)TILE_N;
+    auto &cf = coef_of<T>(sm);
+    T *R = sm.u.w.a0, *U = sm.u.w.a1, *P = sm.u.w.a2;
     load_coef_t<T>(sm, sd, i0, j0, tag);
     const T *rin = (const T *)sd.r[st.cur];
+    const T *pin = (const T *)sd.p[st.pcur];
+    const bool keep = st.keep_dir != 0;
     const T mu = sc_mu<T>(st);
-    T rv[NL];
+    T rv[NRL], pv[NRL];
 #pragma unroll
-    for (int q = 0; q < NL; ++q) {
-        int k = threadIdx.x + q * SOLVER_THREADS;
-        rv[q] = 0;
-        if (k < WN) {
-            int wi = k % WX, wj = k / WX, i = i0 - 2 + wi, j = j0 - 2 + wj;
-            if (in_ring1(wi, wj) && in_dom(sd, i, j)) rv[q] = ld_cg(rin + (size_t)j * sd.pitch + i) - mu;
+    for (int q = 0; q < NRL; ++q) {
+        int k = threadIdx.x + q * SOLVER_THREADS, wi, wj;
+        ring_point<S::TW>(k, wi, wj);
+        int i = i0 - OX + wi, j = j0 - OY + wj;
+        rv[q] = 0; pv[q] = 0;
+        if (k < RN && in_dom(sd, i, j)) {
+            size_t gi = (size_t)j * sd.pitch + i;
+            rv[q] = ld_cg(rin + gi) - mu;
+            if (keep) pv[q] = ld_cg(pin + gi);
         }
     }
-    __syncthreads();
+    __syncthreads();   // coefficients visible
 #pragma unroll
-    for (int q = 0; q < NL; ++q) {
-        int k = threadIdx.x + q * SOLVER_THREADS;
-        if (k < WN) {
-            R[k] = rv[q];
-            U[k] = rv[q] * dinv_at<T>(cf, k % WX, k / WX);
+    for (int q = 0; q < NRL; ++q) {
+        int k = threadIdx.x + q * SOLVER_THREADS, wi, wj;
+        ring_point<S::TW>(k, wi, wj);
+        if (k < RN) {
+            int w = wj * WX + wi;
+            R[w] = rv[q];
+            U[w] = rv[q] * dinv_at<T>(cf, wi, wj);
+            P[w] = pv[q];
         }
     }
     __syncthreads();
     T t[NPART] = {0, 0, 0, 0, 0, 0};
     const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
-    int j = j0 + ty, wj = ty + 2;
+    int j = j0 + ty, wj = ty + OY;
     T *dd = (T *)sd.d;
-    const T *pv = (const T *)sd.p;
-    const T *sv = (const T *)sd.s[st.cur];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-        int i = i0 + tx + 32 * c, wi = tx + 32 * c + 2;
-        if (i < sd.nx && j < sd.ny) {
+        int i = i0 + tx + 32 * c, wi = tx + 32 * c + OX;
+        if (tx + 32 * c < TILE_X && i < sd.nx && j < sd.ny) {
             int k = wj * WX + wi;
             T w = stencil<T>(cf, U, wi, wj);
             t[0] += R[k] * U[k]; t[1] += w * U[k]; t[2] += R[k] * R[k]; t[3] += R[k];
-            if (st.keep_dir) {   // continuation after a residual replacement: u.s and p.s of the kept direction
-                size_t gi = (size_t)j * sd.pitch + i;
-                T so = ld_cg(sv + gi);
-                t[4] += U[k] * so; t[5] += ld_cg(pv + gi) * so;
+            if (keep) {   // continuation: u.(A p) and p.(A p) of the kept direction
+                T ap = stencil<T>(cf, P, wi, wj);
+                t[4] += U[k] * ap; t[5] += P[k] * ap;
             }
             if (st.reset_d) {
                 size_t gi = (size_t)j * sd.pitch + i;
@@ -380,119 +470,387 @@ __device__ void pass_restart(S &sm, const SysDesc &sd, const SysState &st, int i
     __syncthreads();
 }
 
-// One single-reduction PCG iteration.
+// Issue the TMA loads of tile t into stage `fill & 1` (one thread).
 template <typename T, typename S>
-__device__ void pass_iter(S &sm, const SysDesc &sd, const SysState &st, int i0, int j0, int tag, Acc &acc)
+__device__ __forceinline__ void iter_issue(S &sm, const SysDesc &sd, const SysState &st, int t, uint32_t fill)
 {
-    Coef<T> &cf = coef_of<T>(sm);
-    T *R = sm.w.a0, *U = sm.w.a1, *Sv = sm.w.a2, *Rn = sm.w.a3, *Un = sm.w.a4, *Sn = sm.w.a5;
-    load_coef_t<T>(sm, sd, i0, j0, tag);
-    const int cur = st.cur;
-    const T *rin = (const T *)sd.r[cur];
-    const T *sin = (const T *)sd.s[cur];
-    T *rout = (T *)sd.r[cur ^ 1];
-    T *sout = (T *)sd.s[cur ^ 1];
-    T *pv = (T *)sd.p;
+    using G = Geo<S::TW>;
+    constexpr int WX = G::WX, WN = G::WN, OX = G::OX, OY = G::OY, RN = G::RN, NRL = G::NRL, TILE_X = G::TX;
+    constexpr int TILE_N = G::TN;
+    (void)WX; (void)WN; (void)OX; (void)OY; (void)RN; (void)NRL; (void)TILE_X; (void)TILE_N;
+    int i0, j0;
+    tile_origin<S::TW>(sd, t, i0, j0);
+    const int s = fill & 1;
+    const bool first = st.first != 0;
+    Stage<T, S::TW> &stg = sm.u.it.st[s];
+    const uint32_t bar = smem_u32(&sm.bar[s]);
+    const uint32_t bytes = (uint32_t)(((first ? 1 : 2) * WN + TILE_N) * sizeof(T));
+    // earlier generic accesses (this block's reads of the stage, and the
+    // grid's writes of the vectors ordered by the step barrier) before the
+    // async-proxy copies
+    fence_proxy_async();
+    mbar_expect_tx(bar, bytes);
+    tma_load_2d(smem_u32(stg.r), sd.tmaps + MAP_R0 + st.cur, bar, i0 - OX, j0 - OY);
+    if (!first) tma_load_2d(smem_u32(stg.p), sd.tmaps + MAP_P0 + st.pcur, bar, i0 - OX, j0 - OY);
+    tma_load_2d(smem_u32(stg.d), sd.tmaps + MAP_D, bar, i0, j0);
+}
+
+// One single-reduction PCG iteration over the tiles [t_lo, t_hi) of system q,
+// two-stage TMA pipeline (the next tile loads while this one is computed).
+template <typename T, typename S>
+__device__ void pass_iter(S &sm, int q, int t_lo, int t_hi, Acc &acc, const SolverArgs &a)
+{
+    using G = Geo<S::TW>;
+    constexpr int WX = G::WX, WN = G::WN, OX = G::OX, OY = G::OY, RN = G::RN, NRL = G::NRL, TILE_X = G::TX;
+    constexpr int TILE_N = G::TN;
+    (void)WX; (void)WN; (void)OX; (void)OY; (void)RN; (void)NRL; (void)TILE_X; (void)TILE_N;
+    const SysDesc &sd = sm.sd[q];
+    const SysState &st = sm.st[q];
+    auto &cf = coef_of<T>(sm);
+    IterBufs<T, S::TW> &ib = sm.u.it;
+    T *Un = ib.un, *Q = ib.q;
+    const int n = t_hi - t_lo;
+    if (n <= 0) return;
+    const uint32_t fill0 = sm.fills;
+    if (threadIdx.x == 0) iter_issue<T>(sm, sd, st, t_lo, fill0);
+    T *rout = (T *)sd.r[st.cur ^ 1];
+    T *pout = (T *)sd.p[st.pcur ^ 1];
     T *dv = (T *)sd.d;
     const T mu = sc_mu<T>(st), alpha = sc_alpha<T>(st), beta = sc_beta<T>(st);
     const bool first = st.first != 0;
     const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
-    const int j = j0 + ty, wj0 = ty + 2;
-    // issue every global load of this tile before using any of them
-    T rv[NL], sv[NL], pold[4], dold[4];
+    for (int k = 0; k < n; ++k) {
+        const int t = t_lo + k;
+        const uint32_t fill = fill0 + k;
+        if (threadIdx.x == 0 && k + 1 < n) iter_issue<T>(sm, sd, st, t + 1, fill + 1);
+        int i0, j0;
+        tile_origin<S::TW>(sd, t, i0, j0);
+        load_coef_t<T>(sm, sd, i0, j0, t);
+        Stage<T, S::TW> &stg = ib.st[fill & 1];
+        if (!mbar_wait_bounded(smem_u32(&sm.bar[fill & 1]), (fill >> 1) & 1, a.spin_limit_ns)) {
+            if (threadIdx.x == 0) atomicExch(&a.ctl->err, (int32_t)PPE_ERR_TIMEOUT);
+            sm.go = 0;
+        }
+        __syncthreads();   // coefficients visible
+        // window: r - mu and the new direction p = u + beta p (zero outside the domain)
+        T *Rw = stg.r, *Pw = stg.p;
+        for (int w = threadIdx.x; w < WN; w += SOLVER_THREADS) {
+            int wi = w % WX, wj = w / WX;
+            bool in = in_dom(sd, i0 - OX + wi, j0 - OY + wj);
+            T r = in ? Rw[w] - mu : T(0);
+            T u = r * dinv_at<T>(cf, wi, wj);
+            Rw[w] = r;
+            Pw[w] = first ? u : u + beta * Pw[w];
+        }
+        __syncthreads();
+        // one-cell ring: q = A p, r' = r - alpha q, u' = D^-1 r'
+        for (int w = threadIdx.x; w < RN; w += SOLVER_THREADS) {
+            int wi, wj;
+            ring_point<S::TW>(w, wi, wj);
+            int kk = wj * WX + wi;
+            T qv = stencil<T>(cf, Pw, wi, wj);
+            T rn = Rw[kk] - alpha * qv;
+            Rw[kk] = rn;
+            Un[kk] = rn * dinv_at<T>(cf, wi, wj);
+            Q[kk] = qv;
+        }
+        __syncthreads();
+        // tile: store p, d, r'; dots r'.u', (A u').u', r'.r', sum r', u'.(A p), p.(A p)
+        T tt[NPART] = {0, 0, 0, 0, 0, 0};
+        const int j = j0 + ty, wj = ty + OY;
 #pragma unroll
-    for (int q = 0; q < NL; ++q) {
-        int k = threadIdx.x + q * SOLVER_THREADS;
-        rv[q] = 0; sv[q] = 0;
-        if (k < WN) {
-            int wi = k % WX, wj = k / WX, i = i0 - 2 + wi, jj = j0 - 2 + wj;
-            if (in_dom(sd, i, jj)) {
-                size_t gi = (size_t)jj * sd.pitch + i;
-                rv[q] = ld_cg(rin + gi);
-                if (!first && in_ring1(wi, wj)) sv[q] = ld_cg(sin + gi);
+        for (int c = 0; c < 4; ++c) {
+            int i = i0 + tx + 32 * c, wi = tx + 32 * c + OX;
+            if (tx + 32 * c < TILE_X && i < sd.nx && j < sd.ny) {
+                int kk = wj * WX + wi;
+                size_t gi = (size_t)j * sd.pitch + i;
+                T pn = Pw[kk], rn = Rw[kk], un = Un[kk], qv = Q[kk];
+                pout[gi] = pn;
+                dv[gi] = stg.d[ty * TILE_X + tx + 32 * c] + alpha * pn;
+                rout[gi] = rn;
+                T wn = stencil<T>(cf, Un, wi, wj);
+                tt[0] += rn * un; tt[1] += wn * un; tt[2] += rn * rn; tt[3] += rn;
+                tt[4] += un * qv; tt[5] += pn * qv;
             }
         }
+        warp_accumulate(tt, acc);
+        __syncthreads();   // stage and ring buffers free for the next tile
     }
+    if (threadIdx.x == 0) sm.fills = fill0 + n;
+}
+
+// ---------------------------------------------------------------------------
+// Streaming iteration pass (FP32, for grids far larger than the block
+// count): the arithmetic of pass_iter organised for HBM bandwidth.  Each warp
+// takes a contiguous run of the block's tiles (a vertical strip, the tiles
+// being numbered column by column) and marches down it one row at a time.
+// The warp covers the 128 columns i0 - 2 .. i0 + 125, i.e. the 124 tile
+// columns and a two-cell halo on each side; lane l holds columns
+// i0 - 2 + 4l .. i0 + 1 + 4l.  The TMA unit streams the strip into shared
+// memory in chunks of four rows (r and p windows 132 wide from i0 - 4, d
+// 124 wide from i0; zero outside the grid), two chunks in flight per warp.
+// For a new window row s:
+//   row s:      P = D^-1 (r - mu) + beta p_old               (halo 2)
+//   row s - 1:  Q = A P, r' = (r - mu) - alpha Q, u' = D^-1 r'   (halo 1);
+//               on a tile row store p, r', d + alpha p and add r'.u', r'.r',
+//               sum r', u'.Q, p.Q
+//   row s - 2:  add (A u').u'
+// Three rows of P and u' and one row of r - mu stay in registers; east and
+// west neighbours come from the adjacent lane by shuffle.  Values the lane
+// computes at strip columns that a stage does not need (the outermost
+// column for Q, the two outermost for w') are never used.  No block barrier
+// is involved.
+// ---------------------------------------------------------------------------
+
+struct XCoef {
+    float dx[4], fw[4], fe[4];
+};
+
+// A at one row on the lane's four columns, from the rows below (S), at (C)
+// and above (N).
+__device__ __forceinline__ void stencil_row(const XCoef &xc, float dyj, float fsj, float fnj, const float (&S)[4],
+                                            const float (&C)[4], const float (&N)[4], float (&out)[4])
+{
+    const float w0 = __shfl_up_sync(0xffffffffu, C[3], 1);
+    const float e3 = __shfl_down_sync(0xffffffffu, C[0], 1);
+    const float W[4] = {w0, C[0], C[1], C[2]};
+    const float E[4] = {C[1], C[2], C[3], e3};
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-        int i = i0 + tx + 32 * c;
-        pold[c] = 0; dold[c] = 0;
-        if (i < sd.nx && j < sd.ny) {
-            size_t gi = (size_t)j * sd.pitch + i;
-            if (!first) pold[c] = ld_cg(pv + gi);
-            dold[c] = ld_cg(dv + gi);
-        }
+        const float cc = C[c];
+        const float ax = xc.fe[c] * (cc - E[c]) + xc.fw[c] * (cc - W[c]);
+        const float ay = fnj * (cc - N[c]) + fsj * (cc - S[c]);
+        out[c] = dyj * ax + xc.dx[c] * ay;
     }
-    __syncthreads();   // coefficients visible
+}
+
+__device__ __forceinline__ float dinv_f(const XCoef &xc, int c, float dyj, float syj)
+{
+    const float dg = dyj * (xc.fw[c] + xc.fe[c]) + xc.dx[c] * syj;
+    return dg > 0.f ? __frcp_rn(dg) : 0.f;
+}
+
+// Issue the TMA loads of chunk k of a run (window rows jb - 2 + 4k .. +3 of r
+// and p, rows jb - 3 + 4k .. +3 of d, i.e. the ring rows of those window
+// rows) into the warp's buffer g & 1.
+template <typename S>
+__device__ __forceinline__ void stream_issue(S &sm, const SysDesc &sd, const SysState &st, int warp, uint32_t g,
+                                             int i0, int jb, int k)
+{
+    unsigned char *buf = sm.u.sb.buf[warp][g & 1];
+    const uint32_t bar = smem_u32(&sm.sbar[warp][g & 1]);
+    const bool first = st.first != 0;
+    const uint32_t bytes = (first ? 1 : 2) * S_RBYTES + S_DBYTES;
+    fence_proxy_async();
+    mbar_expect_tx(bar, bytes);
+    tma_load_2d(smem_u32(buf), sd.tmaps + MAP_R0 + st.cur, bar, i0 - WIN_OX, jb - 2 + SRB * k);
+    if (!first) tma_load_2d(smem_u32(buf + S_RPAD), sd.tmaps + MAP_P0 + st.pcur, bar, i0 - WIN_OX, jb - 2 + SRB * k);
+    tma_load_2d(smem_u32(buf + 2 * S_RPAD), sd.tmaps + MAP_D, bar, i0, jb - 3 + SRB * k);
+}
+
+// Not inlined: it gets its own register allocation (the kernel saves its
+// live registers once per call instead of spilling inside the row loop).
+template <typename S>
+__device__ __noinline__ void pass_iter_stream(S &sm, int q, int t_lo, int t_hi, Acc &acc, const SolverArgs &a)
+{
+    const SysDesc &sd = sm.sd[q];
+    const SysState &st = sm.st[q];
+    StreamBufs &sb = sm.u.sb;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n = t_hi - t_lo;
+    const int c0 = t_lo + (int)((long long)n * warp / NWARP);
+    const int c1 = t_lo + (int)((long long)n * (warp + 1) / NWARP);
+    float *rout = (float *)sd.r[st.cur ^ 1];
+    float *pout = (float *)sd.p[st.pcur ^ 1];
+    float *dv = (float *)sd.d;
+    const float mu = st.mu_f, alpha = st.alpha_f, beta = st.beta_f;
+    const bool first = st.first != 0;
+    const int nx = sd.nx, ny = sd.ny;
+    const size_t pitch = (size_t)sd.pitch;
+    float tt[NPART] = {0, 0, 0, 0, 0, 0};
+    uint32_t gnext = sm.sfills[warp];      // global index of this warp's next chunk
+    bool ok = true;
+
+    for (int t = c0; t < c1;) {
+        // the run of tiles t .. t_end - 1 in one tile column
+        const int lt = t - sd.tile0;
+        const int col = lt / sd.tiles_y, trow = lt % sd.tiles_y;
+        const int t_end = min(c1, t + (sd.tiles_y - trow));
+        const int i0 = col * TILE_X_STREAM;
+        const int jb = trow * TILE_Y, je = min(ny, (trow + (t_end - t)) * TILE_Y);
+        t = t_end;
+        const int nchunks = (je - jb + 4 + SRB - 1) / SRB;
+        const uint32_t gb = gnext;
+        gnext += nchunks;
+        if (lane == 0) {
+            stream_issue(sm, sd, st, warp, gb, i0, jb, 0);
+            if (nchunks > 1) stream_issue(sm, sd, st, warp, gb + 1, i0, jb, 1);
+        }
+
+        const int x0 = i0 - 2 + 4 * lane;          // first column of the lane
+        XCoef xc;
+        bool vx[4], outc[4];
 #pragma unroll
-    for (int q = 0; q < NL; ++q) {
-        int k = threadIdx.x + q * SOLVER_THREADS;
-        if (k < WN) {
-            int wi = k % WX, wj = k / WX;
-            bool in = in_dom(sd, i0 - 2 + wi, j0 - 2 + wj);
-            T r = in ? rv[q] - mu : T(0);
-            R[k] = r;
-            U[k] = r * dinv_at<T>(cf, wi, wj);
-            Sv[k] = sv[q];
+        for (int c = 0; c < 4; ++c) {
+            const int x = x0 + c, pos = 4 * lane + c;   // pos: column within the 128-wide strip
+            vx[c] = x >= 0 && x < nx;
+            outc[c] = vx[c] && pos >= 2 && pos < TILE_X_STREAM + 2;
+            xc.dx[c] = vx[c] ? sd.dx32[x] : 0.f;
+            xc.fw[c] = vx[c] ? sd.fx32[x] : 0.f;
+            xc.fe[c] = vx[c] ? sd.fx32[x + 1] : 0.f;
         }
-    }
-    __syncthreads();
-    // new residual on the tile and its one-cell ring
-    for (int k = threadIdx.x; k < WN; k += blockDim.x) {
-        int wi = k % WX, wj = k / WX, i = i0 - 2 + wi, jj = j0 - 2 + wj;
-        T rn = 0, un = 0, sn = 0;
-        if (in_ring1(wi, wj) && in_dom(sd, i, jj)) {
-            T w = stencil<T>(cf, U, wi, wj);
-            sn = w + beta * Sv[k];
-            rn = R[k] - alpha * sn;
-            un = rn * dinv_at<T>(cf, wi, wj);
-        }
-        Rn[k] = rn; Un[k] = un; Sn[k] = sn;
-    }
-    __syncthreads();
-    T t[NPART] = {0, 0, 0, 0, 0, 0};
+        const bool out01 = outc[0] && outc[1], out23 = outc[2] && outc[3];
+
+        float P0[4], P1[4], P2[4];   // P of rows s-2, s-1, s
+        float R1[4];                 // r - mu of row s-1
+        float U0[4], U1[4], U2[4];   // u' of rows s-3, s-2, s-1
+        float ydy0 = 0.f, yfs0 = 0.f, yfn0 = 0.f, ydy1 = 0.f, yfs1 = 0.f, yfn1 = 0.f;   // rows s-2, s-1
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        int i = i0 + tx + 32 * c, wi = tx + 32 * c + 2;
-        if (i < sd.nx && j < sd.ny) {
-            int k = wj0 * WX + wi;
-            size_t gi = (size_t)j * sd.pitch + i;
-            T pn = U[k] + beta * pold[c];
-            pv[gi] = pn;
-            dv[gi] = dold[c] + alpha * pn;
-            sout[gi] = Sn[k];
-            T rn = Rn[k], un = Un[k];
-            rout[gi] = rn;
-            T wn = stencil<T>(cf, Un, wi, wj0);
-            t[0] += rn * un; t[1] += wn * un; t[2] += rn * rn; t[3] += rn;
-            t[4] += un * Sn[k]; t[5] += pn * Sn[k];
+        for (int c = 0; c < 4; ++c) P0[c] = P1[c] = P2[c] = R1[c] = U0[c] = U1[c] = U2[c] = 0.f;
+
+        for (int s = jb - 2; s <= je + 1; ++s) {
+            const int rel = s - (jb - 2), k = rel / SRB, rr = rel % SRB;
+            const uint32_t g = gb + k;
+            if (rr == 0) {
+                if (!mbar_wait_bounded(smem_u32(&sm.sbar[warp][g & 1]), (g >> 1) & 1, a.spin_limit_ns)) {
+                    if (ok && lane == 0) atomicExch(&a.ctl->err, (int32_t)PPE_ERR_TIMEOUT);
+                    ok = false;
+                    sm.go = 0;
+                }
+                // chunk k - 1 is consumed: its buffer takes chunk k + 1
+                __syncwarp();
+                if (lane == 0 && k >= 1 && k + 1 < nchunks) stream_issue(sm, sd, st, warp, g + 1, i0, jb, k + 1);
+            }
+            const unsigned char *buf = sm.u.sb.buf[warp][g & 1];
+            const float *rrow = reinterpret_cast<const float *>(buf) + rr * S_WX + 2 + 4 * lane;
+            const float *prow = reinterpret_cast<const float *>(buf + S_RPAD) + rr * S_WX + 2 + 4 * lane;
+            const float *drow = reinterpret_cast<const float *>(buf + 2 * S_RPAD) + rr * TILE_X_STREAM + 4 * lane - 2;
+            float lr[4], lp[4] = {0.f, 0.f, 0.f, 0.f};
+            {
+                const float2 a0 = *reinterpret_cast<const float2 *>(rrow);
+                const float2 a1 = *reinterpret_cast<const float2 *>(rrow + 2);
+                lr[0] = a0.x; lr[1] = a0.y; lr[2] = a1.x; lr[3] = a1.y;
+                if (!first) {
+                    const float2 b0 = *reinterpret_cast<const float2 *>(prow);
+                    const float2 b1 = *reinterpret_cast<const float2 *>(prow + 2);
+                    lp[0] = b0.x; lp[1] = b0.y; lp[2] = b1.x; lp[3] = b1.y;
+                }
+            }
+            const bool vy = s >= 0 && s < ny;
+            const float dy = vy ? sd.dy32[s] : 0.f, fs = vy ? sd.fy32[s] : 0.f, fn = vy ? sd.fy32[s + 1] : 0.f;
+            // row s: r - mu and P
+            float R2[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                P0[c] = P1[c];
+                P1[c] = P2[c];
+                const bool in = vy && vx[c];
+                const float r = in ? lr[c] - mu : 0.f;
+                const float di = dinv_f(xc, c, dy, fs + fn);
+                R2[c] = r;
+                P2[c] = first ? r * di : r * di + beta * (in ? lp[c] : 0.f);
+            }
+            if (s >= jb) {
+                // ring row s-1: Q = A P, r', u'; on a tile row also the stores of
+                // p, r', d + alpha p and the dots that need no neighbour of u'
+                float qv[4], rn1[4];
+                stencil_row(xc, ydy1, yfs1, yfn1, P0, P1, P2, qv);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    U0[c] = U1[c];
+                    U1[c] = U2[c];
+                    rn1[c] = R1[c] - alpha * qv[c];
+                    U2[c] = rn1[c] * dinv_f(xc, c, ydy1, yfs1 + yfn1);
+                }
+                const int jr = s - 1;
+                if (jr >= jb && jr < je) {
+                    float dd[4] = {0.f, 0.f, 0.f, 0.f};
+                    if (out01) {
+                        const float2 d0 = *reinterpret_cast<const float2 *>(drow);
+                        dd[0] = d0.x; dd[1] = d0.y;
+                    } else if (outc[0]) {
+                        dd[0] = drow[0];
+                    }
+                    if (out23) {
+                        const float2 d1 = *reinterpret_cast<const float2 *>(drow + 2);
+                        dd[2] = d1.x; dd[3] = d1.y;
+                    } else if (outc[2]) {
+                        dd[2] = drow[2];
+                    }
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        dd[c] += alpha * P1[c];
+                        if (outc[c]) {
+                            const float un = U2[c], rn = rn1[c], qq = qv[c];
+                            tt[0] += rn * un; tt[2] += rn * rn; tt[3] += rn;
+                            tt[4] += un * qq; tt[5] += P1[c] * qq;
+                        }
+                    }
+                    // a lane's column pairs are either both tile columns or neither
+                    // (x is even), except where the grid ends inside a pair
+                    const size_t o = (size_t)jr * pitch + x0;
+                    if (out01) {
+                        *reinterpret_cast<float2 *>(pout + o) = make_float2(P1[0], P1[1]);
+                        *reinterpret_cast<float2 *>(rout + o) = make_float2(rn1[0], rn1[1]);
+                        *reinterpret_cast<float2 *>(dv + o) = make_float2(dd[0], dd[1]);
+                    } else if (outc[0]) {
+                        pout[o] = P1[0]; rout[o] = rn1[0]; dv[o] = dd[0];
+                    }
+                    if (out23) {
+                        *reinterpret_cast<float2 *>(pout + o + 2) = make_float2(P1[2], P1[3]);
+                        *reinterpret_cast<float2 *>(rout + o + 2) = make_float2(rn1[2], rn1[3]);
+                        *reinterpret_cast<float2 *>(dv + o + 2) = make_float2(dd[2], dd[3]);
+                    } else if (outc[2]) {
+                        pout[o + 2] = P1[2]; rout[o + 2] = rn1[2]; dv[o + 2] = dd[2];
+                    }
+                }
+                if (s >= jb + 2) {
+                    // row s-2: (A u').u'
+                    float wv[4];
+                    stencil_row(xc, ydy0, yfs0, yfn0, U0, U1, U2, wv);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        if (outc[c]) tt[1] += wv[c] * U1[c];
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) R1[c] = R2[c];
+            ydy0 = ydy1; yfs0 = yfs1; yfn0 = yfn1;
+            ydy1 = dy; yfs1 = fs; yfn1 = fn;
         }
+        __syncwarp();   // this run's buffers are read before the next run's loads reuse them
     }
-    warp_accumulate(t, acc);
-    __syncthreads();
+    if (lane == 0) sm.sfills[warp] = gnext;
+    warp_accumulate(tt, acc);
 }
 
 // DLSM dots r.e, e.(A e), e.e  (Eq. 11); with upd: d += alpha e, r_new = r - alpha A e (Eq. 12)
 template <typename T, typename S, bool UPD>
 __device__ void pass_dlsm(S &sm, const SysDesc &sd, const SysState &st, int i0, int j0, int tag, Acc &acc)
 {
-    Coef<float> &cf = sm.cff;
-    float *E = reinterpret_cast<float *>(&sm.w);
-    load_coef_f(sm, sd, i0, j0, tag);
-    float ev[NL];
+    using G = Geo<S::TW>;
+    constexpr int WX = G::WX, WN = G::WN, OX = G::OX, OY = G::OY, RN = G::RN, NRL = G::NRL, TILE_X = G::TX;
+    constexpr int TILE_N = G::TN;
+    (void)WX; (void)WN; (void)OX; (void)OY; (void)RN; (void)NRL; (void)TILE_X; (void)TILE_N;
+    // A e in the pass's precision: in FP64 mode the FP32 direction is applied
+    // with the FP64 operator, as the FP64 iteration applies A to p
+    auto &cf = coef_of<T>(sm);
+    T *E = sm.u.w.a0;
+    load_coef_t<T>(sm, sd, i0, j0, tag);
+    float ev[NRL];
 #pragma unroll
-    for (int q = 0; q < NL; ++q) {
-        int k = threadIdx.x + q * SOLVER_THREADS;
+    for (int q = 0; q < NRL; ++q) {
+        int k = threadIdx.x + q * SOLVER_THREADS, wi, wj;
+        ring_point<S::TW>(k, wi, wj);
+        int i = i0 - OX + wi, j = j0 - OY + wj;
         ev[q] = 0.f;
-        if (k < WN) {
-            int wi = k % WX, wj = k / WX, i = i0 - 2 + wi, j = j0 - 2 + wj;
-            if (in_ring1(wi, wj) && in_dom(sd, i, j)) ev[q] = ld_cg(sd.e + (size_t)j * sd.pitch + i);
-        }
+        if (k < RN && in_dom(sd, i, j)) ev[q] = ld_cg(sd.e + (size_t)j * sd.pitch + i);
     }
 #pragma unroll
-    for (int q = 0; q < NL; ++q) {
-        int k = threadIdx.x + q * SOLVER_THREADS;
-        if (k < WN) E[k] = ev[q];
+    for (int q = 0; q < NRL; ++q) {
+        int k = threadIdx.x + q * SOLVER_THREADS, wi, wj;
+        ring_point<S::TW>(k, wi, wj);
+        if (k < RN) E[wj * WX + wi] = ev[q];
     }
     __syncthreads();
     const int cur = st.cur;
@@ -502,15 +860,15 @@ __device__ void pass_dlsm(S &sm, const SysDesc &sd, const SysState &st, int i0, 
     const T mu = sc_mu<T>(st), alpha = sc_alpha_d<T>(st);
     T t[NPART] = {0, 0, 0, 0, 0, 0};
     const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
-    int j = j0 + ty, wj = ty + 2;
+    int j = j0 + ty, wj = ty + OY;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-        int i = i0 + tx + 32 * c, wi = tx + 32 * c + 2;
-        if (i < sd.nx && j < sd.ny) {
+        int i = i0 + tx + 32 * c, wi = tx + 32 * c + OX;
+        if (tx + 32 * c < TILE_X && i < sd.nx && j < sd.ny) {
             int k = wj * WX + wi;
             size_t gi = (size_t)j * sd.pitch + i;
-            T e = (T)E[k];
-            T q = (T)stencil<float>(cf, E, wi, wj);
+            T e = E[k];
+            T q = stencil(cf, E, wi, wj);
             T r = ld_cg(rin + gi) - mu;
             if (UPD) {
                 T rn = r - alpha * q;
@@ -530,6 +888,10 @@ __device__ void pass_dlsm(S &sm, const SysDesc &sd, const SysState &st, int i0, 
 template <typename T, typename S>
 __device__ void pass_final1(S &sm, const SysDesc &sd, const SysState &st, int i0, int j0, Acc &acc)
 {
+    using G = Geo<S::TW>;
+    constexpr int WX = G::WX, WN = G::WN, OX = G::OX, OY = G::OY, RN = G::RN, NRL = G::NRL, TILE_X = G::TX;
+    constexpr int TILE_N = G::TN;
+    (void)WX; (void)WN; (void)OX; (void)OY; (void)RN; (void)NRL; (void)TILE_X; (void)TILE_N;
     const T *dd = (const T *)sd.d;
     double t[NPART] = {0, 0, 0, 0, 0, 0};
     const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
@@ -537,7 +899,7 @@ __device__ void pass_final1(S &sm, const SysDesc &sd, const SysState &st, int i0
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
         int i = i0 + tx + 32 * c;
-        if (i < sd.nx && j < sd.ny) {
+        if (tx + 32 * c < TILE_X && i < sd.nx && j < sd.ny) {
             size_t gx = (size_t)j * sd.nx + i;
             double x = st.zero_x ? 0.0 : ld_cg(sd.x + gx);
             if (st.fold_d && !st.zero_x) x += (double)ld_cg(dd + (size_t)j * sd.pitch + i);
@@ -552,12 +914,16 @@ __device__ void pass_final1(S &sm, const SysDesc &sd, const SysState &st, int i0
 template <typename T, typename S>
 __device__ void pass_final2(S &sm, const SysDesc &sd, const SysState &st, int i0, int j0, Acc &acc)
 {
+    using G = Geo<S::TW>;
+    constexpr int WX = G::WX, WN = G::WN, OX = G::OX, OY = G::OY, RN = G::RN, NRL = G::NRL, TILE_X = G::TX;
+    constexpr int TILE_N = G::TN;
+    (void)WX; (void)WN; (void)OX; (void)OY; (void)RN; (void)NRL; (void)TILE_X; (void)TILE_N;
     const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
     int j = j0 + ty;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
         int i = i0 + tx + 32 * c;
-        if (i < sd.nx && j < sd.ny) {
+        if (tx + 32 * c < TILE_X && i < sd.nx && j < sd.ny) {
             size_t gx = (size_t)j * sd.nx + i;
             sd.x[gx] = ld_cg(sd.x + gx) - st.xmean;
         }
@@ -587,7 +953,6 @@ __device__ void advance(const SysDesc &sd, SysState &s, const double (&t)[NPART]
 {
     const double N = sd.n_cells;
     (void)N;
-    const bool pcg_like = sd.mode == PPE_MODE_PCG || s.fell_back;
     switch (s.phase) {
     case PH_INIT: {
         s.mu_b = t[0] * sd.inv_n;
@@ -595,6 +960,7 @@ __device__ void advance(const SysDesc &sd, SysState &s, const double (&t)[NPART]
         s.bnorm = sqrt(bb > 0.0 ? bb : 0.0);
         s.incompat = t[2] > 0.0 ? fabs(t[0]) / t[2] : 0.0;
         s.cur = 0;
+        s.pcur = 0;
         if (!(s.incompat <= 1e-6)) {
             s.status = PPE_ERR_INCOMPATIBLE_RHS;
             s.phase = PH_DONE;
@@ -673,6 +1039,7 @@ __device__ void advance(const SysDesc &sd, SysState &s, const double (&t)[NPART]
         s.it_pcg++;
         s.it_total++;
         s.cur ^= 1;
+        s.pcur ^= 1;
         s.mu = t[3] * sd.inv_n;
         double rr = t[2] - N * s.mu * s.mu;
         s.rho = rr > 0.0 ? rr : 0.0;
@@ -687,10 +1054,10 @@ __device__ void advance(const SysDesc &sd, SysState &s, const double (&t)[NPART]
         double denom = t[1] + beta * (2.0 * t[4] + beta * t[5]);
         bool ok = denom > 0.0 && isfinite(beta) && gnew > 0.0;
         const double ru = sd.ru_delta * s.rho_ref;
-        if (rho <= s.target * s.target || s.it_total >= iter_cap(sd) || !ok || (pcg_like && rho <= ru * ru)) {
+        if (rho <= s.target * s.target || s.it_total >= iter_cap(sd) || !ok || rho <= ru * ru) {
             // gamma and alpha of the direction in use stay the reference for the
             // continuation after the residual replacement
-            to_res(s, pcg_like && ok ? 1 : 0);
+            to_res(s, ok ? 1 : 0);
             break;
         }
         s.beta = beta;
@@ -733,8 +1100,11 @@ __device__ void advance(const SysDesc &sd, SysState &s, const double (&t)[NPART]
         if (s.dlsm_useless >= 6) s.fell_back = 1;
         s.dlsm_count++;
         if (sd.mode == PPE_MODE_HYBRID && !s.fell_back && s.it_total >= sd.hybrid_budget) s.fell_back = 1;
+        const double ru = sd.ru_delta * s.rho_ref;
         if (s.rho <= s.target * s.target || s.it_total >= iter_cap(sd) || !isfinite(s.rho)) {
             to_res(s, 0);
+        } else if (s.rho <= ru * ru) {
+            to_res(s, sd.keep_dir_after_dlsm);   // residual replacement (mixed precision)
         } else if (s.dlsm_count < sd.num_dlsm && !s.fell_back) {
             s.phase = PH_NET;
         } else {
@@ -760,18 +1130,18 @@ __device__ void advance(const SysDesc &sd, SysState &s, const double (&t)[NPART]
     s.alpha_d_f = (float)s.alpha_d;
 }
 
+
 template <typename T, typename S>
 __device__ void run_pass(S &sm, int q, int ph, int t, Acc &acc)
 {
     const SysDesc &sd = sm.sd[q];
     const SysState &st = sm.st[q];
-    int lt = t - sd.tile0;
-    int i0 = (lt % sd.tiles_x) * TILE_X, j0 = (lt / sd.tiles_x) * TILE_Y;
+    int i0, j0;
+    tile_origin<S::TW>(sd, t, i0, j0);
     switch (ph) {
     case PH_INIT: pass_init<T>(sm, sd, i0, j0, acc); break;
     case PH_RES: pass_res<T>(sm, sd, st, i0, j0, t, acc); break;
     case PH_RESTART: pass_restart<T>(sm, sd, st, i0, j0, t, acc); break;
-    case PH_ITER: pass_iter<T>(sm, sd, st, i0, j0, t, acc); break;
     case PH_DLSM_DOT: pass_dlsm<T, S, false>(sm, sd, st, i0, j0, t, acc); break;
     case PH_DLSM_UPD: pass_dlsm<T, S, true>(sm, sd, st, i0, j0, t, acc); break;
     case PH_FINAL1: pass_final1<T>(sm, sd, st, i0, j0, acc); break;
@@ -785,11 +1155,6 @@ __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p)
     uint32_t v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
-}
-
-__device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v)
-{
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 // Block-reduce the per-warp accumulators (lane 0 of each warp) into threads
@@ -813,11 +1178,17 @@ template <typename S> __device__ void block_reduce_acc(S &sm, const Acc &acc, fl
     __syncthreads();
 }
 
-template <typename T>
-__global__ void __launch_bounds__(SOLVER_THREADS) solver_kernel(SolverArgs a, int resume_net)
+// STREAM (FP32 only) selects the streaming iteration pass; its register
+// needs allow one block per SM.
+template <typename T, bool STREAM>
+__global__ void __launch_bounds__(SOLVER_THREADS, (sizeof(T) == 4 && !STREAM) ? 2 : 1)
+    solver_kernel(SolverArgs a, int resume_net)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    SmemT<T> &sm = *reinterpret_cast<SmemT<T> *>(smem_raw);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // TMA destinations need 128-byte alignment: round the base up (the launch
+    // reserves 128 extra bytes)
+    using Sm = SmemT<T, STREAM ? TILE_X_STREAM : TILE_X>;
+    Sm &sm = *reinterpret_cast<Sm *>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
     const BlockRange br = a.ranges[blockIdx.x];
     const int nq = br.s1 - br.s0 + 1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -833,6 +1204,17 @@ __global__ void __launch_bounds__(SOLVER_THREADS) solver_kernel(SolverArgs a, in
     if (threadIdx.x == 0) {
         sm.tag_d = sm.tag_f = -1;
         sm.go = 1;
+        sm.fills = 0;
+        mbar_init(smem_u32(&sm.bar[0]), 1);
+        mbar_init(smem_u32(&sm.bar[1]), 1);
+        if constexpr (STREAM) {
+            for (int w = 0; w < NWARP; ++w) {
+                mbar_init(smem_u32(&sm.sbar[w][0]), 1);
+                mbar_init(smem_u32(&sm.sbar[w][1]), 1);
+                sm.sfills[w] = 0;
+            }
+        }
+        mbar_init_fence();
     }
     __syncthreads();
     if (threadIdx.x == 0 && resume_net)
@@ -840,8 +1222,9 @@ __global__ void __launch_bounds__(SOLVER_THREADS) solver_kernel(SolverArgs a, in
             if (sm.st[q].phase == PH_NET) sm.st[q].phase = PH_DLSM_DOT;
     __syncthreads();
     const bool prof = a.prof && blockIdx.x == 0 && threadIdx.x == 0;
-    uint64_t t_a = prof ? globaltimer_ns() : 0, t_b = 0, t_c = 0;
-    __shared__ float pub_hi[NPART], pub_lo[NPART];
+    // profile split of one step (block 0): pass, block reduce + publish,
+    // wait for the other blocks, reduction of their records, state advance
+    uint64_t t_a = prof ? gtimer() : 0, t_p = 0, t_b = 0, t_w = 0, t_r = 0, t_c = 0;
     for (uint32_t step = 1;; ++step) {
         // any system of this block still running?
         bool any = false;
@@ -856,12 +1239,19 @@ __global__ void __launch_bounds__(SOLVER_THREADS) solver_kernel(SolverArgs a, in
             Acc acc;
             acc_zero(acc);
             const int lo_t = max(br.t0, sd.tile0), hi_t = min(br.t1, sd.tile0 + sd.ntiles);
-            for (int t = lo_t; t < hi_t; ++t) run_pass<T>(sm, q, ph, t, acc);
-            block_reduce_acc(sm, acc, pub_hi, pub_lo);
+            if (ph == PH_ITER) {
+                if constexpr (STREAM)
+                    pass_iter_stream(sm, q, lo_t, hi_t, acc, a);
+                else
+                    pass_iter<T>(sm, q, lo_t, hi_t, acc, a);
+            } else
+                for (int t = lo_t; t < hi_t; ++t) run_pass<T>(sm, q, ph, t, acc);
+            if (prof && q == 0) t_p = gtimer();
+            block_reduce_acc(sm, acc, sm.pub_hi, sm.pub_lo);
             Slot *slot = a.slots + (size_t)bank * a.nslots + sd.part0 + (blockIdx.x - sd.blk0);
             if (threadIdx.x < NPART) {
-                slot->hi[threadIdx.x] = pub_hi[threadIdx.x];
-                slot->lo[threadIdx.x] = pub_lo[threadIdx.x];
+                slot->hi[threadIdx.x] = sm.pub_hi[threadIdx.x];
+                slot->lo[threadIdx.x] = sm.pub_lo[threadIdx.x];
             }
             __syncthreads();
             if (threadIdx.x == 0) {
@@ -869,72 +1259,79 @@ __global__ void __launch_bounds__(SOLVER_THREADS) solver_kernel(SolverArgs a, in
                 atomicAdd(&a.arrive[br.s0 + q], 1u);
             }
         }
-        if (prof) t_b = globaltimer_ns();
-        // 2) wait for the records of every block of each live system, reduce, advance
+        if (prof) t_b = gtimer();
+        // 2) wait for the records of every block of each live system, reduce,
+        //    advance: all in warp 0 (one block barrier per system and step)
         for (int q = 0; q < nq; ++q) {
             const SysDesc &sd = sm.sd[q];
             if (!is_pass_phase(sm.st[q].phase)) continue;
-            float h[NPART], l[NPART];
-#pragma unroll
-            for (int k = 0; k < NPART; ++k) h[k] = l[k] = 0.f;
-            const Slot *base = a.slots + (size_t)bank * a.nslots + sd.part0;
-            if (threadIdx.x == 0) {
-                // every block of this system has published step `step`
-                const uint32_t need = step * (uint32_t)sd.nparts;
-                const uint32_t *cnt = a.arrive + br.s0 + q;
-                if (ld_acquire_u32(cnt) < need) {
-                    uint64_t t0 = globaltimer_ns();
-                    while (ld_acquire_u32(cnt) < need) {
-                        if ((int64_t)(globaltimer_ns() - t0) > a.spin_limit_ns) {
-                            atomicExch(&a.ctl->err, (int32_t)PPE_ERR_TIMEOUT);
-                            sm.go = 0;
-                            break;
+            if (warp == 0) {
+                if (lane == 0) {
+                    // every block of this system has published step `step`
+                    const uint32_t need = step * (uint32_t)sd.nparts;
+                    const uint32_t *cnt = a.arrive + br.s0 + q;
+                    if (ld_acquire_u32(cnt) < need) {
+                        uint64_t t0 = gtimer();
+                        while (ld_acquire_u32(cnt) < need) {
+                            if ((int64_t)(gtimer() - t0) > a.spin_limit_ns) {
+                                atomicExch(&a.ctl->err, (int32_t)PPE_ERR_TIMEOUT);
+                                sm.go = 0;
+                                break;
+                            }
+                            __nanosleep(20);
                         }
-                        __nanosleep(20);
+                    }
+                    __threadfence();
+                    if (prof && q == 0) t_w = gtimer();
+                }
+                __syncwarp();
+                // lane l adds records l, l + 32, ... in order, then a fixed shuffle
+                // tree: every block obtains the same sums bit for bit
+                float h[NPART], l[NPART];
+#pragma unroll
+                for (int k = 0; k < NPART; ++k) h[k] = l[k] = 0.f;
+                const Slot *base = a.slots + (size_t)bank * a.nslots + sd.part0;
+                for (int b = lane; b < sd.nparts; b += 32) {
+                    const float4 *sl = reinterpret_cast<const float4 *>(base + b);
+                    const float4 v0 = __ldcg(sl), v1 = __ldcg(sl + 1), v2 = __ldcg(sl + 2);
+                    ff_add(h[0], l[0], v0.x, v1.z);
+                    ff_add(h[1], l[1], v0.y, v1.w);
+                    ff_add(h[2], l[2], v0.z, v2.x);
+                    ff_add(h[3], l[3], v0.w, v2.y);
+                    ff_add(h[4], l[4], v1.x, v2.z);
+                    ff_add(h[5], l[5], v1.y, v2.w);
+                }
+#pragma unroll
+                for (int k = 0; k < NPART; ++k) {
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        float oh = __shfl_down_sync(0xffffffffu, h[k], o);
+                        float ol = __shfl_down_sync(0xffffffffu, l[k], o);
+                        ff_add(h[k], l[k], oh, ol);
                     }
                 }
-                __threadfence();
-            }
-            __syncthreads();
-            for (int b = threadIdx.x; b < sd.nparts; b += blockDim.x) {
-                const Slot *sl = base + b;
+                if (lane == 0 && sm.go) {
+                    if (prof && q == 0) t_r = gtimer();
+                    double tt[NPART];
 #pragma unroll
-                for (int k = 0; k < NPART; ++k) ff_add(h[k], l[k], ld_cg(&sl->hi[k]), ld_cg(&sl->lo[k]));
-            }
-            // block reduction in fixed order: warp shuffle, then warps
-#pragma unroll
-            for (int k = 0; k < NPART; ++k) {
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    float oh = __shfl_down_sync(0xffffffffu, h[k], o);
-                    float ol = __shfl_down_sync(0xffffffffu, l[k], o);
-                    ff_add(h[k], l[k], oh, ol);
-                }
-                if (lane == 0) {
-                    sm.red_hi[k][warp] = h[k];
-                    sm.red_lo[k][warp] = l[k];
+                    for (int k = 0; k < NPART; ++k) tt[k] = (double)h[k] + (double)l[k];
+                    advance(sd, sm.st[q], tt);
                 }
             }
             __syncthreads();
             if (!sm.go) return;                         // a bounded wait expired: leave without writing state
-            if (threadIdx.x < NPART) {
-                float th = 0.f, tl = 0.f;
-                for (int w = 0; w < NWARP; ++w) ff_add(th, tl, sm.red_hi[threadIdx.x][w], sm.red_lo[threadIdx.x][w]);
-                sm.tot[threadIdx.x] = (double)th + (double)tl;
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                double tt[NPART];
-                for (int k = 0; k < NPART; ++k) tt[k] = sm.tot[k];
-                advance(sd, sm.st[q], tt);
-            }
-            __syncthreads();
         }
         if (prof) {
-            t_c = globaltimer_ns();
-            atomicAdd(&a.prof[0], (unsigned long long)(t_b - t_a));
-            atomicAdd(&a.prof[2], (unsigned long long)(t_c - t_b));
-            atomicAdd(&a.prof[3], 1ull);
+            t_c = gtimer();
+            if (t_p && t_w && t_r) {
+                a.prof[0] += t_p - t_a;
+                a.prof[1] += t_b - t_p;
+                a.prof[2] += t_w - t_b;
+                a.prof[3] += t_r - t_w;
+                a.prof[4] += t_c - t_r;
+                a.prof[7] += 1;
+            }
+            t_p = t_w = t_r = 0;
             t_a = t_c;
         }
     }
@@ -947,50 +1344,102 @@ __global__ void __launch_bounds__(SOLVER_THREADS) solver_kernel(SolverArgs a, in
     }
 }
 
+size_t solver_smem(SolverVariant v)
+{
+    switch (v) {
+    case SV_FP64: return sizeof(SmemT<double, TILE_X>) + 128;
+    case SV_FP32_STREAM: return sizeof(SmemT<float, TILE_X_STREAM>) + 128;
+    default: return sizeof(SmemT<float, TILE_X>) + 128;
+    }
+}
+
 // The dynamic shared-memory opt-in is a per-function attribute: set it once.
 void set_solver_attributes()
 {
     static std::once_flag once;
     std::call_once(once, [] {
-        cudaFuncSetAttribute(solver_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(SmemT<double>));
-        cudaFuncSetAttribute(solver_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(SmemT<float>));
+        cudaFuncSetAttribute(solver_kernel<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)solver_smem(SV_FP64));
+        cudaFuncSetAttribute(solver_kernel<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)solver_smem(SV_FP32_TILE));
+        cudaFuncSetAttribute(solver_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)solver_smem(SV_FP32_STREAM));
     });
 }
 
+const void *solver_fn(SolverVariant v)
+{
+    switch (v) {
+    case SV_FP64: return (const void *)solver_kernel<double, false>;
+    case SV_FP32_STREAM: return (const void *)solver_kernel<float, true>;
+    default: return (const void *)solver_kernel<float, false>;
+    }
+}
+
+
 }  // namespace
 
-int solver_max_blocks(bool fp64, int blocks_per_sm_req)
+int solver_max_blocks(SolverVariant v, int blocks_per_sm_req)
 {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    size_t smem = fp64 ? sizeof(SmemT<double>) : sizeof(SmemT<float>);
     set_solver_attributes();
-    if (fp64)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solver_kernel<double>, SOLVER_THREADS, smem);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solver_kernel<float>, SOLVER_THREADS, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solver_fn(v), SOLVER_THREADS, solver_smem(v));
     if (blocks_per_sm_req > 0 && blocks_per_sm_req < per_sm) per_sm = blocks_per_sm_req;
     return per_sm * sms;
 }
 
-ppe_status launch_solver_resume(const SolverArgs &a, bool fp64, int grid_blocks, cudaStream_t stream, int resume)
+ppe_status launch_solver_resume(const SolverArgs &a, SolverVariant v, int grid_blocks, cudaStream_t stream, int resume)
 {
-    size_t smem = fp64 ? sizeof(SmemT<double>) : sizeof(SmemT<float>);
     SolverArgs args = a;
     int res = resume;
     void *params[] = {&args, &res};
-    cudaError_t e;
     set_solver_attributes();
-    if (fp64)
-        e = cudaLaunchCooperativeKernel((const void *)solver_kernel<double>, dim3(grid_blocks),
-                                        dim3(SOLVER_THREADS), params, smem, stream);
-    else
-        e = cudaLaunchCooperativeKernel((const void *)solver_kernel<float>, dim3(grid_blocks),
-                                        dim3(SOLVER_THREADS), params, smem, stream);
+    cudaError_t e = cudaLaunchCooperativeKernel(solver_fn(v), dim3(grid_blocks), dim3(SOLVER_THREADS), params,
+                                                solver_smem(v), stream);
     if (e != cudaSuccess) return cuda_status(e, "cudaLaunchCooperativeKernel(solver)");
+    return PPE_OK;
+}
+
+ppe_status encode_solver_maps(void *const r[2], void *const p[2], void *d, int nx, int ny, int pitch,
+                              SolverVariant v, CUtensorMap out[NMAPS])
+{
+    const bool fp64 = v == SV_FP64, stream = v == SV_FP32_STREAM;
+    // tile-cooperative kernels: one tile window (136 x 20) and one tile (128 x 16);
+    // streaming kernel: chunks of SRB rows of a 132-wide window and of a 124-wide tile
+    const cuuint32_t win_w = stream ? S_WX : WIN_X, win_h = stream ? SRB : WIN_Y;
+    const cuuint32_t tile_w = stream ? TILE_X_STREAM : TILE_X, tile_h = stream ? SRB : TILE_Y;
+    auto encode = tensor_map_encoder();
+    if (!encode) {
+        set_error("cuTensorMapEncodeTiled unavailable");
+        return PPE_ERR_CUDA;
+    }
+    const size_t es = fp64 ? 8 : 4;
+    if (pitch % 4 != 0 || pitch < nx) {
+        set_error("encode_solver_maps: pitch must be a multiple of 4 and at least nx");
+        return PPE_ERR_ARG;
+    }
+    void *const bufs[NMAPS] = {r[0], r[1], p[0], p[1], d};
+    for (int m = 0; m < NMAPS; ++m) {
+        if ((uintptr_t)bufs[m] % 16 != 0) {
+            set_error("encode_solver_maps: vector not 16-byte aligned");
+            return PPE_ERR_ARG;
+        }
+        const bool win = m != MAP_D;
+        cuuint64_t dims[2] = {(cuuint64_t)nx, (cuuint64_t)ny};
+        cuuint64_t strides[1] = {(cuuint64_t)pitch * es};
+        cuuint32_t box[2] = {win ? win_w : tile_w, win ? win_h : tile_h};
+        cuuint32_t estr[2] = {1, 1};
+        CUresult cr = encode(&out[m], fp64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                             bufs[m], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (cr != CUDA_SUCCESS) {
+            set_error("cuTensorMapEncodeTiled(solver vectors) failed");
+            return PPE_ERR_CUDA;
+        }
+    }
     return PPE_OK;
 }
 

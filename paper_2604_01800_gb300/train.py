@@ -142,9 +142,10 @@ def main(argv=None):
         for keep in (0, 1):
             api.ppe_set_options(eg, keep_dir_after_dlsm=keep)
             x = torch.zeros_like(erhs)
-            hyb = api.ppe_solve(eg, erhs, x, 1e-8, api.PPE_MODE_HYBRID, api.PPE_PREC_MIXED, net=net)
+            hyb = api.ppe_solve(eg, erhs, x, 1e-8, api.PPE_MODE_HYBRID, api.PPE_PREC_MIXED, net=net,
+                                raise_on_error=False)
             out[f"hybrid{keep}"] = [hyb["iters_pcg"] + hyb["iters_dlsm"], hyb["iters_dlsm"], round(hyb["ms_total"], 2),
-                                    hyb["fell_back"]]
+                                    hyb["fell_back"], hyb["status"]]
         x = torch.zeros_like(erhs)
         pcg = api.ppe_solve(eg, erhs, x, 1e-8, api.PPE_MODE_PCG, api.PPE_PREC_MIXED)
         out["pcg"] = [pcg["iters_pcg"], round(pcg["ms_total"], 2)]
@@ -168,6 +169,7 @@ def main(argv=None):
             rec.update(evaluate())
             log.append(rec)
             print(json.dumps(rec), flush=True)
+            net.save(a.out, with_moments=False)     # checkpoint
     net.save(a.out, with_moments=False)
     summary = {"steps": a.steps, "batch": a.batch, "grids": a.grids, "per_grid": a.per_grid, "sizes": sizes,
                "data_seconds": t_data, "train_seconds": time.time() - t1, "log": log}

@@ -178,3 +178,50 @@ def test_repeatable_bitwise(api):
         api.ppe_solve(grid, _dev(w.f), x, RES_TOL, api.PPE_MODE_PCG, api.PPE_PREC_MIXED)
         outs.append(x.cpu().numpy())
     assert np.array_equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("iter_pass", [1, 2])
+@pytest.mark.parametrize("key", ["c1", "r37x300", "r129x131", "r260x9", "r1x50"])
+def test_iteration_pass_variants(api, key, iter_pass):
+    """The tile-cooperative (1) and streaming (2) FP32 iteration passes both
+    meet the parity bars on ragged grids."""
+    _check(api, key, api.PPE_PREC_MIXED, iter_pass=iter_pass)
+
+
+def test_streaming_pass_runs_across_tile_columns(api):
+    """620 x 1000 cells: 5 tile columns of 63 tiles over at most one block per
+    SM, so the tile runs of some warps end in one column and continue in the
+    next.  Both passes reach the tolerance (checked by the oracle) and agree."""
+    g = I.rng(77)
+    dx, dy = I.random_spacing(620, g), I.random_spacing(1000, g)
+    f = I.gaussian_rhs(dx, dy, g, 6)
+    grid = api.ppe_create_grid(dx, dy)
+    xs = []
+    for iter_pass in (1, 2):
+        api.ppe_set_options(grid, iter_pass=iter_pass)
+        x = torch.zeros(len(dy), len(dx), dtype=torch.float64, device="cuda")
+        info = api.ppe_solve(grid, _dev(f), x, RES_TOL, api.PPE_MODE_PCG, api.PPE_PREC_MIXED)
+        assert info["status"] == 0
+        xg = x.cpu().numpy()
+        assert oracle.true_relres(dx, dy, f, xg) <= RES_TOL * 1.05
+        xs.append(xg)
+    assert np.linalg.norm(xs[0] - xs[1]) <= 1e-6 * np.linalg.norm(xs[0])
+
+
+def test_batch_streaming_pass(api):
+    keys = ["c1", "r37x300", "r129x131", "r260x9"]
+    grids, rhs, xs, refs = [], [], [], []
+    for k in keys:
+        w, xo = _ref(k)
+        grids.append(api.ppe_create_grid(w.dx, w.dy))
+        api.ppe_set_options(grids[-1], iter_pass=2)
+        rhs.append(_dev(w.f))
+        xs.append(torch.zeros_like(rhs[-1]))
+        refs.append((w, xo))
+    infos, st = api.ppe_solve_batch(grids, rhs, xs, RES_TOL, api.PPE_MODE_PCG, api.PPE_PREC_MIXED)
+    assert st == 0
+    for (w, xo), x, info in zip(refs, xs, infos):
+        xg = x.cpu().numpy()
+        assert info["status"] == 0
+        assert oracle.true_relres(w.dx, w.dy, w.f, xg) <= RES_TOL * 1.05
+        assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= SOL_TOL
