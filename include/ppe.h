@@ -99,11 +99,11 @@ typedef struct {
     int32_t blocks_per_sm;  /* persistent-kernel CTAs per SM (2; 0 = as many as fit)          */
     int32_t keep_dir_after_dlsm; /* 0: every CG-type phase restarts with p = z (Sec. 2.2 workflow,
                                as a fresh KSPSolve); 1: CG directions continue across DLSM steps */
-    int32_t iter_pass;      /* MIXED precision only: 0 = choose by size (default), 1 = tiles of
-                               16x128 cells shared by a whole CTA, 2 = streaming (each warp
-                               marches down a 128-wide strip; for grids far larger than the
-                               number of CTAs).  Same arithmetic, same results up to rounding
-                               order.                                                          */
+    int32_t iter_pass;      /* MIXED precision only: 0 = the autotuned choice if there is one
+                               (ppe_autotune), else by size (default); 1 = tiles of 16x128
+                               cells shared by a whole CTA; 2 = streaming (each warp marches
+                               down a 124-wide strip; for grids far larger than the number of
+                               CTAs).  Same arithmetic, same results up to rounding order.     */
     int32_t reserved[5];
 } ppe_solve_opts;
 
@@ -202,6 +202,27 @@ PPE_API ppe_status ppe_set_direction_source(ppe_grid *grid, ppe_direction_fn fn,
 PPE_API ppe_status ppe_solve_noalloc(int nx, int ny, const double *dx, const double *dy, const double *rhs_dev,
                                      double *x_dev, double tol_rel, ppe_precision precision, void *stream,
                                      ppe_solve_info *info);
+
+/*
+ * Autotuner of the persistent kernel's launch configuration (the paper has no
+ * counterpart).  In MIXED precision it times, on this grid, the iteration-pass
+ * variants of ppe_solve_opts.iter_pass (tile-cooperative with 1 and with 2
+ * CTAs per SM, and streaming) by capped solves of a smooth synthetic source,
+ * and keeps the fastest: on the grid (used by ppe_solve when
+ * opts.iter_pass is 0) and in a process-wide table keyed by (nx, ny) that
+ * later grids of the same shape use.  If the environment variable
+ * PPE_TUNE_CACHE names a file, the table is read from it on first use and
+ * each new entry is appended (one JSON object per line).  The call allocates
+ * two temporary device fields of nx*ny doubles, runs about twenty solves of
+ * at most 40 iterations and synchronises `stream`.
+ */
+typedef struct {
+    int32_t iter_pass;       /* chosen variant: 1 tile-cooperative, 2 streaming          */
+    int32_t blocks_per_sm;   /* chosen CTAs per SM (0: as many as fit)                    */
+    double us_per_iter[3];   /* measured: tile x1 CTA/SM, tile x2 CTAs/SM, streaming      */
+    int32_t reserved[4];
+} ppe_tune_report;
+PPE_API ppe_status ppe_autotune(ppe_grid *grid, void *stream, ppe_tune_report *report);
 
 /* Message describing the last failure on the calling thread ("" if none). */
 PPE_API const char *ppe_last_error(void);

@@ -40,6 +40,11 @@ class ppe_solve_opts(ctypes.Structure):
                 ("iter_pass", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
+class ppe_tune_report(ctypes.Structure):
+    _fields_ = [("iter_pass", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("us_per_iter", ctypes.c_double * 3), ("reserved", ctypes.c_int32 * 4)]
+
+
 class ppe_net_config(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int32), ("widths", ctypes.c_int32 * 6), ("c_last", ctypes.c_int32),
                 ("trunk_hidden", ctypes.c_int32 * 2), ("phi_hidden", ctypes.c_int32), ("mesh_conv", ctypes.c_int32),
@@ -100,6 +105,7 @@ _SIGS = [
     ("net_get_step", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
     ("ppe_solve_noalloc", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, ctypes.c_double, ctypes.c_int,
                                          _P, ctypes.POINTER(ppe_solve_info)]),
+    ("ppe_autotune", ctypes.c_int, [_P, _P, ctypes.POINTER(ppe_tune_report)]),
     ("ppe_last_error", ctypes.c_char_p, []),
     ("ppe_version", ctypes.c_char_p, []),
 ]

@@ -93,6 +93,16 @@ def ppe_set_options(grid: Grid, opts: ppe_solve_opts | None = None, **kw):
     return o
 
 
+def ppe_autotune(grid: Grid, stream=None) -> dict:
+    """Time the iteration-pass variants on this grid (mixed precision) and keep
+    the fastest for later solves of this grid shape; returns the report."""
+    rep = _lib.ppe_tune_report()
+    check(_lib.load().ppe_autotune(grid.handle, _stream(stream), ctypes.byref(rep)), "ppe_autotune")
+    return {"iter_pass": rep.iter_pass, "blocks_per_sm": rep.blocks_per_sm,
+            "us_per_iter": {"tile_1cta": rep.us_per_iter[0], "tile_2cta": rep.us_per_iter[1],
+                            "stream": rep.us_per_iter[2]}}
+
+
 def ppe_set_direction_source(grid: Grid, fn):
     """Install ``fn(r_hat, e, stream)`` (torch CUDA float32 tensors [ny, nx]
     viewing the library's staging buffers) as the DLSM direction source of

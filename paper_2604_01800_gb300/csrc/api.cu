@@ -169,6 +169,7 @@ void ppe_destroy_grid(ppe_grid *g)
     cudaFree(g->dx); cudaFree(g->dy); cudaFree(g->fx); cudaFree(g->fy);
     cudaFree(g->dx32); cudaFree(g->dy32); cudaFree(g->fx32); cudaFree(g->fy32);
     cudaFree(g->vec); cudaFree(g->e); cudaFree(g->tmaps_dev); cudaFree(g->dir_part);
+    cudaFree(g->ycoef);
     cudaFree(g->sys_dev); cudaFree(g->st_dev); cudaFree(g->ranges_dev); cudaFree(g->slots_dev);
     cudaFree(g->ctl_dev);
     cudaFree(g->dir_r); cudaFree(g->dir_e);
@@ -238,10 +239,19 @@ ppe_status ppe_create_grid(int nx, int ny, const double *dx, const double *dy, p
     g->r[0] = base; g->r[1] = base + vbytes; g->p[0] = base + 2 * vbytes; g->p[1] = base + 3 * vbytes;
     g->d = base + 4 * vbytes;
     {
+        std::vector<float> yc((size_t)4 * ny);
+        for (int j = 0; j < ny; ++j) {
+            yc[4 * j] = (float)dy[j];
+            yc[4 * j + 1] = (float)fy[j];
+            yc[4 * j + 2] = (float)fy[j + 1];
+            yc[4 * j + 3] = 0.f;
+        }
+        G_ALLOC(g->ycoef, yc.size() * sizeof(float));
+        G_COPY(g->ycoef, yc.data(), yc.size() * sizeof(float));
         CUtensorMap maps[3 * NMAPS];     // one set per kernel variant, in SolverVariant order
         ppe_status ms = PPE_OK;
         for (int v = 0; v < 3 && ms == PPE_OK; ++v)
-            ms = encode_solver_maps(g->r, g->p, g->d, nx, ny, g->pitch, (SolverVariant)v, maps + v * NMAPS);
+            ms = encode_solver_maps(g->r, g->p, g->d, g->ycoef, nx, ny, g->pitch, (SolverVariant)v, maps + v * NMAPS);
         if (ms != PPE_OK) return fail(ms);
         G_ALLOC(g->tmaps_dev, sizeof maps);
         G_COPY(g->tmaps_dev, maps, sizeof maps);
@@ -557,9 +567,18 @@ ppe_status ppe_solve(ppe_grid *g, const double *rhs, double *x, double tol, ppe_
     clear_error();
     PPE_TRY(check_solve_args(g, rhs, x, tol, mode, prec, net));
     cudaStream_t st = (cudaStream_t)stream;
-    const SolverVariant v = pick_variant(prec, g->opts.iter_pass, g->tiles_x * g->tiles_y);
+    int pass = g->opts.iter_pass, bps = g->opts.blocks_per_sm;
+    if (prec == PPE_PREC_MIXED && pass == 0) {
+        if (g->tuned_pass) {
+            pass = g->tuned_pass;
+            bps = g->tuned_bps;
+        } else {
+            tune_lookup(g->nx, g->ny, &pass, &bps);
+        }
+    }
+    const SolverVariant v = pick_variant(prec, pass, g->tiles_x * g->tiles_y);
     std::vector<SysDesc> sds(1, make_desc(g, rhs, x, tol, mode, prec, 0, v));
-    int maxb = std::min(solver_max_blocks(v, g->opts.blocks_per_sm), sds[0].ntiles);
+    int maxb = std::min(solver_max_blocks(v, bps), sds[0].ntiles);
     if (maxb < 1) return cuda_status(cudaErrorInvalidConfiguration, "solver occupancy");
     std::vector<BlockRange> ranges;
     int nslots = 0;

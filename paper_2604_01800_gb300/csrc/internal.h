@@ -49,7 +49,9 @@ constexpr int WIN_X = TILE_X + 2 * WIN_OX;  // 136 (window of a tile-cooperative
 constexpr int WIN_Y = TILE_Y + 2 * WIN_OY;  // 20
 // Tensor maps of one system's inner vectors (per precision): the two residual
 // buffers and the two direction buffers (window boxes), and d (tile box).
-enum SolverMap : int { MAP_R0 = 0, MAP_R1 = 1, MAP_P0 = 2, MAP_P1 = 3, MAP_D = 4, NMAPS = 5 };
+// MAP_Y: the per-row y coefficients (dy, fy[j], fy[j+1], 0) as an FP32 [ny][4]
+// array, read by the streaming kernel.
+enum SolverMap : int { MAP_R0 = 0, MAP_R1 = 1, MAP_P0 = 2, MAP_P1 = 3, MAP_D = 4, MAP_Y = 5, NMAPS = 6 };
 
 inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
 
@@ -85,7 +87,7 @@ struct SysDesc {
     double *x;                            // solution [ny][nx] (caller)
     void *r[2], *p[2], *d;                // inner vectors [ny][pitch], FP32 or FP64 (r, p double-buffered)
     float *e;                             // DLSM direction [ny][pitch]
-    const CUtensorMap *tmaps;             // NMAPS maps of r[0], r[1], p[0], p[1], d (device memory)
+    const CUtensorMap *tmaps;             // NMAPS maps of r[0], r[1], p[0], p[1], d, y coefficients
 };
 
 // Mutable per-system state.  Every block that works on a system keeps an
@@ -152,9 +154,14 @@ int solver_max_blocks(SolverVariant v, int blocks_per_sm_req);
 // Encode the NMAPS tensor maps of one system's inner vectors for a kernel
 // variant (element type FP32 or FP64, box shapes of the variant's tiles; row
 // pitch `pitch` elements, a multiple of 4; every buffer 16-byte aligned).
-// Cells outside [0,nx) x [0,ny) read as zero.
-ppe_status encode_solver_maps(void *const r[2], void *const p[2], void *d, int nx, int ny, int pitch,
-                              SolverVariant v, CUtensorMap out[NMAPS]);
+// Cells outside [0,nx) x [0,ny) read as zero.  ycoef (nullable: the map is
+// then left zero) is the FP32 [ny][4] row-coefficient array.
+ppe_status encode_solver_maps(void *const r[2], void *const p[2], void *d, const float *ycoef, int nx, int ny,
+                              int pitch, SolverVariant v, CUtensorMap out[NMAPS]);
+
+// Autotuned launch configuration of a grid shape, if ppe_autotune measured
+// one in this process (or the tuning cache file holds one).
+bool tune_lookup(int nx, int ny, int *iter_pass, int *blocks_per_sm);
 
 // Remove the mean of the grid's DLSM direction e (two kernels on `stream`;
 // no allocation, so it may run inside a stream capture).
@@ -176,8 +183,10 @@ struct ppe_grid {
     void *vec = nullptr;                 // 5 inner vectors, 8 bytes per element
     float *e = nullptr;                  // DLSM direction
     double *dir_part = nullptr;          // partial sums of the direction's mean removal
+    float *ycoef = nullptr;              // [ny][4] FP32: dy, fy[j], fy[j+1], 0 (streaming kernel)
     void *r[2] = {nullptr, nullptr}, *p[2] = {nullptr, nullptr}, *d = nullptr;
-    CUtensorMap *tmaps_dev = nullptr;    // [FP32 maps | FP64 maps] of the inner vectors
+    CUtensorMap *tmaps_dev = nullptr;    // tensor maps of the inner vectors, one set per kernel variant
+    int tuned_pass = 0, tuned_bps = 0;   // ppe_autotune's choice (0: none)
     // single-system launch resources
     ppe::SysDesc *sys_dev = nullptr;
     ppe::SysState *st_dev = nullptr;

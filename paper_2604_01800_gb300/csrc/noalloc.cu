@@ -186,7 +186,7 @@ extern "C" ppe_status ppe_solve_noalloc(int nx, int ny, const double *dx, const 
     sd.r[0] = vec; sd.r[1] = vec + VEC_BYTES; sd.p[0] = vec + 2 * VEC_BYTES; sd.p[1] = vec + 3 * VEC_BYTES;
     sd.d = vec + 4 * VEC_BYTES; sd.e = nullptr;
     CUtensorMap maps[NMAPS];
-    PPE_TRY(encode_solver_maps(sd.r, sd.p, sd.d, nx, ny, pitch, v, maps));
+    PPE_TRY(encode_solver_maps(sd.r, sd.p, sd.d, nullptr, nx, ny, pitch, v, maps));
     CUtensorMap *d_maps = (CUtensorMap *)(base + OFF_MAPS);
     sd.tmaps = d_maps;
 

@@ -43,6 +43,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <cstring>
 #include <mutex>
 
 #include "internal.h"
@@ -105,7 +106,8 @@ constexpr int SRB = 4;
 constexpr int S_WX = TILE_X_STREAM + 2 * WIN_OX;
 constexpr int S_RBYTES = S_WX * SRB * 4, S_RPAD = (S_RBYTES + 127) / 128 * 128;
 constexpr int S_DBYTES = TILE_X_STREAM * SRB * 4, S_DPAD = (S_DBYTES + 127) / 128 * 128;
-constexpr int S_CHUNK = 2 * S_RPAD + S_DPAD;
+constexpr int S_YBYTES = 4 * SRB * 4;                    // dy, fy[j], fy[j+1], 0 of each row
+constexpr int S_CHUNK = 2 * S_RPAD + S_DPAD + 128;
 struct StreamBufs {
     unsigned char buf[SOLVER_THREADS / 32][2][S_CHUNK];
 };
@@ -588,7 +590,8 @@ __device__ void pass_iter(S &sm, int q, int t_lo, int t_hi, Acc &acc, const Solv
 // columns and a two-cell halo on each side; lane l holds columns
 // i0 - 2 + 4l .. i0 + 1 + 4l.  The TMA unit streams the strip into shared
 // memory in chunks of four rows (r and p windows 132 wide from i0 - 4, d
-// 124 wide from i0; zero outside the grid), two chunks in flight per warp.
+// 124 wide from i0, and the rows' y coefficients; zero outside the grid), two
+// chunks in flight per warp.
 // For a new window row s:
 //   row s:      P = D^-1 (r - mu) + beta p_old               (halo 2)
 //   row s - 1:  Q = A P, r' = (r - mu) - alpha Q, u' = D^-1 r'   (halo 1);
@@ -640,12 +643,13 @@ __device__ __forceinline__ void stream_issue(S &sm, const SysDesc &sd, const Sys
     unsigned char *buf = sm.u.sb.buf[warp][g & 1];
     const uint32_t bar = smem_u32(&sm.sbar[warp][g & 1]);
     const bool first = st.first != 0;
-    const uint32_t bytes = (first ? 1 : 2) * S_RBYTES + S_DBYTES;
+    const uint32_t bytes = (first ? 1 : 2) * S_RBYTES + S_DBYTES + S_YBYTES;
     fence_proxy_async();
     mbar_expect_tx(bar, bytes);
     tma_load_2d(smem_u32(buf), sd.tmaps + MAP_R0 + st.cur, bar, i0 - WIN_OX, jb - 2 + SRB * k);
     if (!first) tma_load_2d(smem_u32(buf + S_RPAD), sd.tmaps + MAP_P0 + st.pcur, bar, i0 - WIN_OX, jb - 2 + SRB * k);
     tma_load_2d(smem_u32(buf + 2 * S_RPAD), sd.tmaps + MAP_D, bar, i0, jb - 3 + SRB * k);
+    tma_load_2d(smem_u32(buf + 2 * S_RPAD + S_DPAD), sd.tmaps + MAP_Y, bar, 0, jb - 2 + SRB * k);
 }
 
 // Not inlined: it gets its own register allocation (the kernel saves its
@@ -702,57 +706,61 @@ __device__ __noinline__ void pass_iter_stream(S &sm, int q, int t_lo, int t_hi, 
         const bool out01 = outc[0] && outc[1], out23 = outc[2] && outc[3];
 
         float P0[4], P1[4], P2[4];   // P of rows s-2, s-1, s
-        float R1[4];                 // r - mu of row s-1
+        float R1[4], D1[4];          // r - mu and D^-1 of row s-1
         float U0[4], U1[4], U2[4];   // u' of rows s-3, s-2, s-1
-        float ydy0 = 0.f, yfs0 = 0.f, yfn0 = 0.f, ydy1 = 0.f, yfs1 = 0.f, yfn1 = 0.f;   // rows s-2, s-1
+        float ydy1 = 0.f, yfs1 = 0.f, yfn1 = 0.f;   // y coefficients of row s-1
+        float ydy0 = 0.f, yfs0 = 0.f, yfn0 = 0.f;   // and of row s-2
 #pragma unroll
-        for (int c = 0; c < 4; ++c) P0[c] = P1[c] = P2[c] = R1[c] = U0[c] = U1[c] = U2[c] = 0.f;
+        for (int c = 0; c < 4; ++c) P0[c] = P1[c] = P2[c] = R1[c] = D1[c] = U0[c] = U1[c] = U2[c] = 0.f;
 
-        for (int s = jb - 2; s <= je + 1; ++s) {
-            const int rel = s - (jb - 2), k = rel / SRB, rr = rel % SRB;
+        // One chunk (SRB window rows) per outer iteration; the rows of a chunk
+        // are unrolled, so the row windows rotate by renaming.  Rows before the
+        // run (s < jb) and after it (s > je + 1) are computed on zeros or on
+        // neighbouring data and never stored or summed.
+        for (int k = 0; k < nchunks; ++k) {
             const uint32_t g = gb + k;
-            if (rr == 0) {
-                if (!mbar_wait_bounded(smem_u32(&sm.sbar[warp][g & 1]), (g >> 1) & 1, a.spin_limit_ns)) {
-                    if (ok && lane == 0) atomicExch(&a.ctl->err, (int32_t)PPE_ERR_TIMEOUT);
-                    ok = false;
-                    sm.go = 0;
-                }
-                // chunk k - 1 is consumed: its buffer takes chunk k + 1
-                __syncwarp();
-                if (lane == 0 && k >= 1 && k + 1 < nchunks) stream_issue(sm, sd, st, warp, g + 1, i0, jb, k + 1);
+            if (!mbar_wait_bounded(smem_u32(&sm.sbar[warp][g & 1]), (g >> 1) & 1, a.spin_limit_ns)) {
+                if (ok && lane == 0) atomicExch(&a.ctl->err, (int32_t)PPE_ERR_TIMEOUT);
+                ok = false;
+                sm.go = 0;
             }
-            const unsigned char *buf = sm.u.sb.buf[warp][g & 1];
-            const float *rrow = reinterpret_cast<const float *>(buf) + rr * S_WX + 2 + 4 * lane;
-            const float *prow = reinterpret_cast<const float *>(buf + S_RPAD) + rr * S_WX + 2 + 4 * lane;
-            const float *drow = reinterpret_cast<const float *>(buf + 2 * S_RPAD) + rr * TILE_X_STREAM + 4 * lane - 2;
-            float lr[4], lp[4] = {0.f, 0.f, 0.f, 0.f};
-            {
-                const float2 a0 = *reinterpret_cast<const float2 *>(rrow);
-                const float2 a1 = *reinterpret_cast<const float2 *>(rrow + 2);
-                lr[0] = a0.x; lr[1] = a0.y; lr[2] = a1.x; lr[3] = a1.y;
-                if (!first) {
-                    const float2 b0 = *reinterpret_cast<const float2 *>(prow);
-                    const float2 b1 = *reinterpret_cast<const float2 *>(prow + 2);
-                    lp[0] = b0.x; lp[1] = b0.y; lp[2] = b1.x; lp[3] = b1.y;
-                }
-            }
-            const bool vy = s >= 0 && s < ny;
-            const float dy = vy ? sd.dy32[s] : 0.f, fs = vy ? sd.fy32[s] : 0.f, fn = vy ? sd.fy32[s + 1] : 0.f;
-            // row s: r - mu and P
-            float R2[4];
+            // chunk k - 1 is consumed: its buffer takes chunk k + 1
+            __syncwarp();
+            if (lane == 0 && k >= 1 && k + 1 < nchunks) stream_issue(sm, sd, st, warp, g + 1, i0, jb, k + 1);
+            const float *rbuf = reinterpret_cast<const float *>(sb.buf[warp][g & 1]) + 2 + 4 * lane;
+            const float *pbuf = reinterpret_cast<const float *>(sb.buf[warp][g & 1] + S_RPAD) + 2 + 4 * lane;
+            const float *dbuf = reinterpret_cast<const float *>(sb.buf[warp][g & 1] + 2 * S_RPAD) + 4 * lane - 2;
+            const float4 *ybuf = reinterpret_cast<const float4 *>(sb.buf[warp][g & 1] + 2 * S_RPAD + S_DPAD);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                P0[c] = P1[c];
-                P1[c] = P2[c];
-                const bool in = vy && vx[c];
-                const float r = in ? lr[c] - mu : 0.f;
-                const float di = dinv_f(xc, c, dy, fs + fn);
-                R2[c] = r;
-                P2[c] = first ? r * di : r * di + beta * (in ? lp[c] : 0.f);
-            }
-            if (s >= jb) {
-                // ring row s-1: Q = A P, r', u'; on a tile row also the stores of
-                // p, r', d + alpha p and the dots that need no neighbour of u'
+            for (int rr = 0; rr < SRB; ++rr) {
+                const int s = jb - 2 + SRB * k + rr;
+                float lr[4], lp[4] = {0.f, 0.f, 0.f, 0.f};
+                {
+                    const float2 a0 = *reinterpret_cast<const float2 *>(rbuf + rr * S_WX);
+                    const float2 a1 = *reinterpret_cast<const float2 *>(rbuf + rr * S_WX + 2);
+                    lr[0] = a0.x; lr[1] = a0.y; lr[2] = a1.x; lr[3] = a1.y;
+                    if (!first) {
+                        const float2 b0 = *reinterpret_cast<const float2 *>(pbuf + rr * S_WX);
+                        const float2 b1 = *reinterpret_cast<const float2 *>(pbuf + rr * S_WX + 2);
+                        lp[0] = b0.x; lp[1] = b0.y; lp[2] = b1.x; lp[3] = b1.y;
+                    }
+                }
+                const bool vy = s >= 0 && s < ny;
+                const float4 yc = ybuf[rr];          // zero outside the grid
+                const float dy = yc.x, fs = yc.y, fn = yc.z;
+                // row s: r - mu, D^-1, P
+                float R2[4], D2[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    P0[c] = P1[c];
+                    P1[c] = P2[c];
+                    const bool in = vy && vx[c];
+                    const float r = in ? lr[c] - mu : 0.f;
+                    D2[c] = dinv_f(xc, c, dy, fs + fn);
+                    R2[c] = r;
+                    P2[c] = first ? r * D2[c] : r * D2[c] + beta * (in ? lp[c] : 0.f);
+                }
+                // ring row s - 1: Q = A P, r', u'
                 float qv[4], rn1[4];
                 stencil_row(xc, ydy1, yfs1, yfn1, P0, P1, P2, qv);
 #pragma unroll
@@ -760,63 +768,52 @@ __device__ __noinline__ void pass_iter_stream(S &sm, int q, int t_lo, int t_hi, 
                     U0[c] = U1[c];
                     U1[c] = U2[c];
                     rn1[c] = R1[c] - alpha * qv[c];
-                    U2[c] = rn1[c] * dinv_f(xc, c, ydy1, yfs1 + yfn1);
+                    U2[c] = rn1[c] * D1[c];
                 }
-                const int jr = s - 1;
-                if (jr >= jb && jr < je) {
-                    float dd[4] = {0.f, 0.f, 0.f, 0.f};
+                // row s - 2: (A u').u'
+                float wv[4];
+                stencil_row(xc, ydy0, yfs0, yfn0, U0, U1, U2, wv);
+                const int jr = s - 1, jo = s - 2;
+                const bool ring_out = jr >= jb && jr < je, w_out = jo >= jb && jo < je;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const float m1 = (ring_out && outc[c]) ? 1.f : 0.f, m0 = (w_out && outc[c]) ? 1.f : 0.f;
+                    const float un = U2[c], rn = rn1[c], qq = qv[c];
+                    tt[0] += m1 * (rn * un); tt[2] += m1 * (rn * rn); tt[3] += m1 * rn;
+                    tt[4] += m1 * (un * qq); tt[5] += m1 * (P1[c] * qq);
+                    tt[1] += m0 * (wv[c] * U1[c]);
+                }
+                if (ring_out) {
+                    // store p, r', d + alpha p of ring row s - 1 (a tile row).  A lane's
+                    // column pairs are both tile columns or neither (x is even),
+                    // except where the grid ends inside a pair
+                    const float *drow = dbuf + rr * TILE_X_STREAM;
+                    const size_t o = (size_t)jr * pitch + x0;
                     if (out01) {
                         const float2 d0 = *reinterpret_cast<const float2 *>(drow);
-                        dd[0] = d0.x; dd[1] = d0.y;
+                        *reinterpret_cast<float2 *>(pout + o) = make_float2(P1[0], P1[1]);
+                        *reinterpret_cast<float2 *>(rout + o) = make_float2(rn1[0], rn1[1]);
+                        *reinterpret_cast<float2 *>(dv + o) = make_float2(d0.x + alpha * P1[0], d0.y + alpha * P1[1]);
                     } else if (outc[0]) {
-                        dd[0] = drow[0];
+                        pout[o] = P1[0]; rout[o] = rn1[0]; dv[o] = drow[0] + alpha * P1[0];
                     }
                     if (out23) {
                         const float2 d1 = *reinterpret_cast<const float2 *>(drow + 2);
-                        dd[2] = d1.x; dd[3] = d1.y;
-                    } else if (outc[2]) {
-                        dd[2] = drow[2];
-                    }
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        dd[c] += alpha * P1[c];
-                        if (outc[c]) {
-                            const float un = U2[c], rn = rn1[c], qq = qv[c];
-                            tt[0] += rn * un; tt[2] += rn * rn; tt[3] += rn;
-                            tt[4] += un * qq; tt[5] += P1[c] * qq;
-                        }
-                    }
-                    // a lane's column pairs are either both tile columns or neither
-                    // (x is even), except where the grid ends inside a pair
-                    const size_t o = (size_t)jr * pitch + x0;
-                    if (out01) {
-                        *reinterpret_cast<float2 *>(pout + o) = make_float2(P1[0], P1[1]);
-                        *reinterpret_cast<float2 *>(rout + o) = make_float2(rn1[0], rn1[1]);
-                        *reinterpret_cast<float2 *>(dv + o) = make_float2(dd[0], dd[1]);
-                    } else if (outc[0]) {
-                        pout[o] = P1[0]; rout[o] = rn1[0]; dv[o] = dd[0];
-                    }
-                    if (out23) {
                         *reinterpret_cast<float2 *>(pout + o + 2) = make_float2(P1[2], P1[3]);
                         *reinterpret_cast<float2 *>(rout + o + 2) = make_float2(rn1[2], rn1[3]);
-                        *reinterpret_cast<float2 *>(dv + o + 2) = make_float2(dd[2], dd[3]);
+                        *reinterpret_cast<float2 *>(dv + o + 2) = make_float2(d1.x + alpha * P1[2], d1.y + alpha * P1[3]);
                     } else if (outc[2]) {
-                        pout[o + 2] = P1[2]; rout[o + 2] = rn1[2]; dv[o + 2] = dd[2];
+                        pout[o + 2] = P1[2]; rout[o + 2] = rn1[2]; dv[o + 2] = drow[2] + alpha * P1[2];
                     }
                 }
-                if (s >= jb + 2) {
-                    // row s-2: (A u').u'
-                    float wv[4];
-                    stencil_row(xc, ydy0, yfs0, yfn0, U0, U1, U2, wv);
 #pragma unroll
-                    for (int c = 0; c < 4; ++c)
-                        if (outc[c]) tt[1] += wv[c] * U1[c];
+                for (int c = 0; c < 4; ++c) {
+                    R1[c] = R2[c];
+                    D1[c] = D2[c];
                 }
+                ydy0 = ydy1; yfs0 = yfs1; yfn0 = yfn1;
+                ydy1 = dy; yfs1 = fs; yfn1 = fn;
             }
-#pragma unroll
-            for (int c = 0; c < 4; ++c) R1[c] = R2[c];
-            ydy0 = ydy1; yfs0 = yfs1; yfn0 = yfn1;
-            ydy1 = dy; yfs1 = fs; yfn1 = fn;
         }
         __syncwarp();   // this run's buffers are read before the next run's loads reuse them
     }
@@ -1402,8 +1399,8 @@ ppe_status launch_solver_resume(const SolverArgs &a, SolverVariant v, int grid_b
     return PPE_OK;
 }
 
-ppe_status encode_solver_maps(void *const r[2], void *const p[2], void *d, int nx, int ny, int pitch,
-                              SolverVariant v, CUtensorMap out[NMAPS])
+ppe_status encode_solver_maps(void *const r[2], void *const p[2], void *d, const float *ycoef, int nx, int ny,
+                              int pitch, SolverVariant v, CUtensorMap out[NMAPS])
 {
     const bool fp64 = v == SV_FP64, stream = v == SV_FP32_STREAM;
     // tile-cooperative kernels: one tile window (136 x 20) and one tile (128 x 16);
@@ -1420,8 +1417,26 @@ ppe_status encode_solver_maps(void *const r[2], void *const p[2], void *d, int n
         set_error("encode_solver_maps: pitch must be a multiple of 4 and at least nx");
         return PPE_ERR_ARG;
     }
-    void *const bufs[NMAPS] = {r[0], r[1], p[0], p[1], d};
-    for (int m = 0; m < NMAPS; ++m) {
+    void *const bufs[MAP_Y] = {r[0], r[1], p[0], p[1], d};
+    std::memset(&out[MAP_Y], 0, sizeof(CUtensorMap));
+    if (ycoef) {
+        if ((uintptr_t)ycoef % 16 != 0) {
+            set_error("encode_solver_maps: row coefficients not 16-byte aligned");
+            return PPE_ERR_ARG;
+        }
+        cuuint64_t dims[2] = {4, (cuuint64_t)ny};
+        cuuint64_t strides[1] = {16};
+        cuuint32_t box[2] = {4, (cuuint32_t)(stream ? SRB : 1)};
+        cuuint32_t estr[2] = {1, 1};
+        CUresult cr = encode(&out[MAP_Y], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)ycoef, dims, strides, box, estr,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (cr != CUDA_SUCCESS) {
+            set_error("cuTensorMapEncodeTiled(row coefficients) failed");
+            return PPE_ERR_CUDA;
+        }
+    }
+    for (int m = 0; m < MAP_Y; ++m) {
         if ((uintptr_t)bufs[m] % 16 != 0) {
             set_error("encode_solver_maps: vector not 16-byte aligned");
             return PPE_ERR_ARG;

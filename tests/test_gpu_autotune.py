@@ -1,0 +1,47 @@
+"""The autotuner times the iteration-pass variants on a grid and the solves
+that follow use its choice; results stay within the parity bars."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from paper_2604_01800_gb300 import inputs as I  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_01800_gb300 import api as A
+    return A
+
+
+def test_autotune_then_solve(api, tmp_path):
+    cache = tmp_path / "tune.jsonl"
+    os.environ["PPE_TUNE_CACHE"] = str(cache)
+    try:
+        g = I.rng(31)
+        dx, dy = I.random_spacing(700, g), I.random_spacing(500, g)
+        f = I.gaussian_rhs(dx, dy, g, 6)
+        grid = api.ppe_create_grid(dx, dy)
+        rep = api.ppe_autotune(grid)
+        assert rep["iter_pass"] in (1, 2)
+        assert all(v > 0 for v in rep["us_per_iter"].values()), rep
+        best = min(rep["us_per_iter"].values())
+        chosen = {(1, 1): "tile_1cta", (1, 2): "tile_2cta", (2, 0): "stream"}[(rep["iter_pass"], rep["blocks_per_sm"])]
+        assert rep["us_per_iter"][chosen] == best
+        line = json.loads(cache.read_text().strip().splitlines()[-1])
+        assert (line["nx"], line["ny"], line["iter_pass"]) == (700, 500, rep["iter_pass"])
+        # a solve with the default options now runs the tuned variant
+        x = torch.zeros(500, 700, dtype=torch.float64, device="cuda")
+        info = api.ppe_solve(grid, torch.tensor(f, device="cuda"), x, 1e-8, api.PPE_MODE_PCG, api.PPE_PREC_MIXED)
+        assert info["status"] == 0
+        assert oracle.true_relres(dx, dy, f, x.cpu().numpy()) <= 1.05e-8
+    finally:
+        os.environ.pop("PPE_TUNE_CACHE", None)
