@@ -102,7 +102,7 @@ typedef struct {
     int32_t iter_pass;      /* MIXED precision only: 0 = the autotuned choice if there is one
                                (ppe_autotune), else by size (default); 1 = tiles of 16x128
                                cells shared by a whole CTA; 2 = streaming (each warp marches
-                               down a 124-wide strip; for grids far larger than the number of
+                               down a 120-wide strip; for grids far larger than the number of
                                CTAs).  Same arithmetic, same results up to rounding order.     */
     int32_t reserved[5];
 } ppe_solve_opts;

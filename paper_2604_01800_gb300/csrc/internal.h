@@ -36,8 +36,8 @@ ppe_status cuda_status(cudaError_t e, const char *what);
 // tiling of the persistent solver kernel
 // ---------------------------------------------------------------------------
 constexpr int TILE_X = 128;                 // cells per tile row (4 per lane)
-constexpr int TILE_X_STREAM = 124;          // tile width of the streaming kernel: a warp row of
-                                            // 128 cells covers it plus a two-cell halo per side
+constexpr int TILE_X_STREAM = 120;          // tile width of the streaming kernel: a warp row of
+                                            // 128 cells covers it plus a four-cell halo per side
 constexpr int TILE_Y = 16;                  // rows per tile (one warp each)
 constexpr int SOLVER_THREADS = 32 * TILE_Y;
 constexpr int NPART = 6;                    // FP64 partial sums per tile

@@ -100,10 +100,11 @@ template <typename T, int TW> struct Work {
     T a0[Geo<TW>::WN_PAD], a1[Geo<TW>::WN_PAD], a2[Geo<TW>::WN_PAD];
 };
 
-// Per-warp TMA chunks of the streaming pass: two buffers of four rows of the
-// r and p windows (132 wide) and of d (124 wide), each part padded to 128 bytes.
+// Per-warp TMA chunks of the streaming pass: two buffers of SRB rows of r and
+// p (128 wide from i0 - 4), of d (120 wide from i0) and of the rows' y
+// coefficients, each part padded to 128 bytes.
 constexpr int SRB = 4;
-constexpr int S_WX = TILE_X_STREAM + 2 * WIN_OX;
+constexpr int S_WX = TILE_X_STREAM + 8;
 constexpr int S_RBYTES = S_WX * SRB * 4, S_RPAD = (S_RBYTES + 127) / 128 * 128;
 constexpr int S_DBYTES = TILE_X_STREAM * SRB * 4, S_DPAD = (S_DBYTES + 127) / 128 * 128;
 constexpr int S_YBYTES = 4 * SRB * 4;                    // dy, fy[j], fy[j+1], 0 of each row
@@ -586,23 +587,23 @@ __device__ void pass_iter(S &sm, int q, int t_lo, int t_hi, Acc &acc, const Solv
 // count): the arithmetic of pass_iter organised for HBM bandwidth.  Each warp
 // takes a contiguous run of the block's tiles (a vertical strip, the tiles
 // being numbered column by column) and marches down it one row at a time.
-// The warp covers the 128 columns i0 - 2 .. i0 + 125, i.e. the 124 tile
-// columns and a two-cell halo on each side; lane l holds columns
-// i0 - 2 + 4l .. i0 + 1 + 4l.  The TMA unit streams the strip into shared
-// memory in chunks of four rows (r and p windows 132 wide from i0 - 4, d
-// 124 wide from i0, and the rows' y coefficients; zero outside the grid), two
-// chunks in flight per warp.
-// For a new window row s:
+// The warp covers the 128 columns i0 - 4 .. i0 + 123: the 120 tile columns
+// and a four-cell halo on each side (two are needed; four keep every lane's
+// columns on a 16-byte boundary).  Lane l holds columns i0 - 4 + 4l ..
+// i0 - 1 + 4l: one 16-byte shared-memory load per vector and row, one
+// 16-byte store per vector and row.  The TMA unit streams the strip into
+// shared memory in chunks of four rows (r and p 128 wide from i0 - 4, d 120
+// wide from i0, and the rows' y coefficients; zero outside the grid), two
+// chunks in flight per warp.  For a new window row s:
 //   row s:      P = D^-1 (r - mu) + beta p_old               (halo 2)
 //   row s - 1:  Q = A P, r' = (r - mu) - alpha Q, u' = D^-1 r'   (halo 1);
 //               on a tile row store p, r', d + alpha p and add r'.u', r'.r',
 //               sum r', u'.Q, p.Q
 //   row s - 2:  add (A u').u'
-// Three rows of P and u' and one row of r - mu stay in registers; east and
-// west neighbours come from the adjacent lane by shuffle.  Values the lane
-// computes at strip columns that a stage does not need (the outermost
-// column for Q, the two outermost for w') are never used.  No block barrier
-// is involved.
+// Three rows of P and u' and one row of r - mu and D^-1 stay in registers;
+// east and west neighbours come from the adjacent lane by shuffle.  Lanes 0
+// and 31 hold only halo columns: their values feed their neighbours'
+// stencils and are never stored or summed.  No block barrier is involved.
 // ---------------------------------------------------------------------------
 
 struct XCoef {
@@ -627,15 +628,9 @@ __device__ __forceinline__ void stencil_row(const XCoef &xc, float dyj, float fs
     }
 }
 
-__device__ __forceinline__ float dinv_f(const XCoef &xc, int c, float dyj, float syj)
-{
-    const float dg = dyj * (xc.fw[c] + xc.fe[c]) + xc.dx[c] * syj;
-    return dg > 0.f ? __frcp_rn(dg) : 0.f;
-}
-
-// Issue the TMA loads of chunk k of a run (window rows jb - 2 + 4k .. +3 of r
-// and p, rows jb - 3 + 4k .. +3 of d, i.e. the ring rows of those window
-// rows) into the warp's buffer g & 1.
+// Issue the TMA loads of chunk k of a run (window rows jb - 2 + 4k .. +3 of r,
+// p and the y coefficients, rows jb - 3 + 4k .. +3 of d, i.e. the ring rows
+// of those window rows) into the warp's buffer g & 1.
 template <typename S>
 __device__ __forceinline__ void stream_issue(S &sm, const SysDesc &sd, const SysState &st, int warp, uint32_t g,
                                              int i0, int jb, int k)
@@ -669,7 +664,7 @@ __device__ __noinline__ void pass_iter_stream(S &sm, int q, int t_lo, int t_hi, 
     float *dv = (float *)sd.d;
     const float mu = st.mu_f, alpha = st.alpha_f, beta = st.beta_f;
     const bool first = st.first != 0;
-    const int nx = sd.nx, ny = sd.ny;
+    const int nx = sd.nx;
     const size_t pitch = (size_t)sd.pitch;
     float tt[NPART] = {0, 0, 0, 0, 0, 0};
     uint32_t gnext = sm.sfills[warp];      // global index of this warp's next chunk
@@ -681,7 +676,7 @@ __device__ __noinline__ void pass_iter_stream(S &sm, int q, int t_lo, int t_hi, 
         const int col = lt / sd.tiles_y, trow = lt % sd.tiles_y;
         const int t_end = min(c1, t + (sd.tiles_y - trow));
         const int i0 = col * TILE_X_STREAM;
-        const int jb = trow * TILE_Y, je = min(ny, (trow + (t_end - t)) * TILE_Y);
+        const int jb = trow * TILE_Y, je = min(sd.ny, (trow + (t_end - t)) * TILE_Y);
         t = t_end;
         const int nchunks = (je - jb + 4 + SRB - 1) / SRB;
         const uint32_t gb = gnext;
@@ -691,19 +686,18 @@ __device__ __noinline__ void pass_iter_stream(S &sm, int q, int t_lo, int t_hi, 
             if (nchunks > 1) stream_issue(sm, sd, st, warp, gb + 1, i0, jb, 1);
         }
 
-        const int x0 = i0 - 2 + 4 * lane;          // first column of the lane
-        XCoef xc;
-        bool vx[4], outc[4];
+        const int x0 = i0 - 4 + 4 * lane;          // first column of the lane (16-byte aligned)
+        XCoef xc;                                  // dx > 0 exactly on grid columns
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            const int x = x0 + c, pos = 4 * lane + c;   // pos: column within the 128-wide strip
-            vx[c] = x >= 0 && x < nx;
-            outc[c] = vx[c] && pos >= 2 && pos < TILE_X_STREAM + 2;
-            xc.dx[c] = vx[c] ? sd.dx32[x] : 0.f;
-            xc.fw[c] = vx[c] ? sd.fx32[x] : 0.f;
-            xc.fe[c] = vx[c] ? sd.fx32[x + 1] : 0.f;
+            const int x = x0 + c;
+            const bool v = x >= 0 && x < nx;
+            xc.dx[c] = v ? sd.dx32[x] : 0.f;
+            xc.fw[c] = v ? sd.fx32[x] : 0.f;
+            xc.fe[c] = v ? sd.fx32[x + 1] : 0.f;
         }
-        const bool out01 = outc[0] && outc[1], out23 = outc[2] && outc[3];
+        // lanes 1..30 hold the tile columns; the float4 lies inside the row's pitch
+        const bool own = lane >= 1 && lane <= 30 && x0 < nx;
 
         float P0[4], P1[4], P2[4];   // P of rows s-2, s-1, s
         float R1[4], D1[4];          // r - mu and D^-1 of row s-1
@@ -727,38 +721,34 @@ __device__ __noinline__ void pass_iter_stream(S &sm, int q, int t_lo, int t_hi, 
             // chunk k - 1 is consumed: its buffer takes chunk k + 1
             __syncwarp();
             if (lane == 0 && k >= 1 && k + 1 < nchunks) stream_issue(sm, sd, st, warp, g + 1, i0, jb, k + 1);
-            const float *rbuf = reinterpret_cast<const float *>(sb.buf[warp][g & 1]) + 2 + 4 * lane;
-            const float *pbuf = reinterpret_cast<const float *>(sb.buf[warp][g & 1] + S_RPAD) + 2 + 4 * lane;
-            const float *dbuf = reinterpret_cast<const float *>(sb.buf[warp][g & 1] + 2 * S_RPAD) + 4 * lane - 2;
-            const float4 *ybuf = reinterpret_cast<const float4 *>(sb.buf[warp][g & 1] + 2 * S_RPAD + S_DPAD);
+            const unsigned char *cb = sb.buf[warp][g & 1];
+            const float4 *rbuf = reinterpret_cast<const float4 *>(cb) + lane;
+            const float4 *pbuf = reinterpret_cast<const float4 *>(cb + S_RPAD) + lane;
+            // d rows hold the 120 tile columns; lane l >= 1 reads its four at 4l - 4
+            const float4 *dbuf = reinterpret_cast<const float4 *>(cb + 2 * S_RPAD) + (lane >= 1 ? lane - 1 : 0);
+            const float4 *ybuf = reinterpret_cast<const float4 *>(cb + 2 * S_RPAD + S_DPAD);
 #pragma unroll
             for (int rr = 0; rr < SRB; ++rr) {
                 const int s = jb - 2 + SRB * k + rr;
-                float lr[4], lp[4] = {0.f, 0.f, 0.f, 0.f};
-                {
-                    const float2 a0 = *reinterpret_cast<const float2 *>(rbuf + rr * S_WX);
-                    const float2 a1 = *reinterpret_cast<const float2 *>(rbuf + rr * S_WX + 2);
-                    lr[0] = a0.x; lr[1] = a0.y; lr[2] = a1.x; lr[3] = a1.y;
-                    if (!first) {
-                        const float2 b0 = *reinterpret_cast<const float2 *>(pbuf + rr * S_WX);
-                        const float2 b1 = *reinterpret_cast<const float2 *>(pbuf + rr * S_WX + 2);
-                        lp[0] = b0.x; lp[1] = b0.y; lp[2] = b1.x; lp[3] = b1.y;
-                    }
-                }
-                const bool vy = s >= 0 && s < ny;
+                const float4 a4 = rbuf[rr * (S_WX / 4)];
+                float4 b4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (!first) b4 = pbuf[rr * (S_WX / 4)];
+                const float lr[4] = {a4.x, a4.y, a4.z, a4.w}, lp[4] = {b4.x, b4.y, b4.z, b4.w};
                 const float4 yc = ybuf[rr];          // zero outside the grid
-                const float dy = yc.x, fs = yc.y, fn = yc.z;
-                // row s: r - mu, D^-1, P
+                const float dy = yc.x, fs = yc.y, fn = yc.z, sy = fs + fn;
+                const float vy = dy > 0.f ? 1.f : 0.f;   // row inside the grid
+                // row s: r - mu, D^-1, P (zero outside the grid)
                 float R2[4], D2[4];
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
                     P0[c] = P1[c];
                     P1[c] = P2[c];
-                    const bool in = vy && vx[c];
-                    const float r = in ? lr[c] - mu : 0.f;
-                    D2[c] = dinv_f(xc, c, dy, fs + fn);
+                    const float in = xc.dx[c] > 0.f ? vy : 0.f;
+                    const float r = in * (lr[c] - mu);
+                    const float dg = dy * (xc.fw[c] + xc.fe[c]) + xc.dx[c] * sy;
+                    D2[c] = dg > 0.f ? __frcp_rn(dg) : 0.f;
                     R2[c] = r;
-                    P2[c] = first ? r * D2[c] : r * D2[c] + beta * (in ? lp[c] : 0.f);
+                    P2[c] = first ? r * D2[c] : r * D2[c] + beta * (in * lp[c]);
                 }
                 // ring row s - 1: Q = A P, r', u'
                 float qv[4], rn1[4];
@@ -775,36 +765,23 @@ __device__ __noinline__ void pass_iter_stream(S &sm, int q, int t_lo, int t_hi, 
                 stencil_row(xc, ydy0, yfs0, yfn0, U0, U1, U2, wv);
                 const int jr = s - 1, jo = s - 2;
                 const bool ring_out = jr >= jb && jr < je, w_out = jo >= jb && jo < je;
+                const float m1 = ring_out && own ? 1.f : 0.f, m0 = w_out && own ? 1.f : 0.f;
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
-                    const float m1 = (ring_out && outc[c]) ? 1.f : 0.f, m0 = (w_out && outc[c]) ? 1.f : 0.f;
-                    const float un = U2[c], rn = rn1[c], qq = qv[c];
-                    tt[0] += m1 * (rn * un); tt[2] += m1 * (rn * rn); tt[3] += m1 * rn;
-                    tt[4] += m1 * (un * qq); tt[5] += m1 * (P1[c] * qq);
-                    tt[1] += m0 * (wv[c] * U1[c]);
+                    const float oc = xc.dx[c] > 0.f ? 1.f : 0.f;       // tile column inside the grid
+                    const float rm = (m1 * oc) * rn1[c], qm = (m1 * oc) * qv[c];
+                    tt[0] += rm * U2[c]; tt[2] += rm * rn1[c]; tt[3] += rm;
+                    tt[4] += U2[c] * qm; tt[5] += P1[c] * qm;
+                    tt[1] += (m0 * oc) * wv[c] * U1[c];
                 }
-                if (ring_out) {
-                    // store p, r', d + alpha p of ring row s - 1 (a tile row).  A lane's
-                    // column pairs are both tile columns or neither (x is even),
-                    // except where the grid ends inside a pair
-                    const float *drow = dbuf + rr * TILE_X_STREAM;
+                if (ring_out && own) {
+                    // store p, r', d + alpha p of ring row s - 1 (a tile row)
+                    const float4 d4 = dbuf[rr * (TILE_X_STREAM / 4)];
                     const size_t o = (size_t)jr * pitch + x0;
-                    if (out01) {
-                        const float2 d0 = *reinterpret_cast<const float2 *>(drow);
-                        *reinterpret_cast<float2 *>(pout + o) = make_float2(P1[0], P1[1]);
-                        *reinterpret_cast<float2 *>(rout + o) = make_float2(rn1[0], rn1[1]);
-                        *reinterpret_cast<float2 *>(dv + o) = make_float2(d0.x + alpha * P1[0], d0.y + alpha * P1[1]);
-                    } else if (outc[0]) {
-                        pout[o] = P1[0]; rout[o] = rn1[0]; dv[o] = drow[0] + alpha * P1[0];
-                    }
-                    if (out23) {
-                        const float2 d1 = *reinterpret_cast<const float2 *>(drow + 2);
-                        *reinterpret_cast<float2 *>(pout + o + 2) = make_float2(P1[2], P1[3]);
-                        *reinterpret_cast<float2 *>(rout + o + 2) = make_float2(rn1[2], rn1[3]);
-                        *reinterpret_cast<float2 *>(dv + o + 2) = make_float2(d1.x + alpha * P1[2], d1.y + alpha * P1[3]);
-                    } else if (outc[2]) {
-                        pout[o + 2] = P1[2]; rout[o + 2] = rn1[2]; dv[o + 2] = drow[2] + alpha * P1[2];
-                    }
+                    *reinterpret_cast<float4 *>(pout + o) = make_float4(P1[0], P1[1], P1[2], P1[3]);
+                    *reinterpret_cast<float4 *>(rout + o) = make_float4(rn1[0], rn1[1], rn1[2], rn1[3]);
+                    *reinterpret_cast<float4 *>(dv + o) = make_float4(d4.x + alpha * P1[0], d4.y + alpha * P1[1],
+                                                                      d4.z + alpha * P1[2], d4.w + alpha * P1[3]);
                 }
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
