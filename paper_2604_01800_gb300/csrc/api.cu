@@ -355,6 +355,8 @@ static SysDesc make_desc(const ppe_grid *g, const double *rhs, double *x, double
     sd.diag_max = g->diag_max;
     sd.n_cells = (double)g->nx * (double)g->ny;
     sd.inv_n = 1.0 / sd.n_cells;
+    sd.n_cells_f = (float)sd.n_cells;
+    sd.inv_n_f = (float)sd.inv_n;
     sd.dx = g->dx; sd.dy = g->dy; sd.fx = g->fx; sd.fy = g->fy;
     sd.dx32 = g->dx32; sd.dy32 = g->dy32; sd.fx32 = g->fx32; sd.fy32 = g->fy32;
     sd.f = rhs; sd.x = x;
@@ -427,13 +429,30 @@ static bool plan_blocks(std::vector<SysDesc> &sds, int max_blocks, std::vector<B
 
 // Drive the persistent launches of n systems until every one is done; run
 // the network between launches for the systems that wait for a direction.
+// Rebalancing of a batch: launches end every max_steps steps; when the tiles
+// of the systems still running have dropped below a fraction of the planned
+// ones, the host spreads them over all blocks again (finished systems get no
+// tiles).  Systems of very different iteration counts otherwise leave most
+// SMs idle at the end of a batch.
+struct Replan {
+    std::vector<SysDesc> *sds;      // host copy of the descriptions (updated in place)
+    std::vector<int> full_tiles;    // tiles of each system
+    int max_blocks = 0, slot_cap = 0, max_steps = 0;
+    double fraction = 0.75;
+};
+
 static ppe_status drive(int n, ppe_grid *const *grids, SysDesc *sys_dev, SysState *st_dev, BlockRange *ranges_dev,
                         int blocks, Slot *slots_dev, int nslots, Control *ctl_dev, SolverVariant variant,
-                        ppe_net *net, cudaStream_t stream, ppe_solve_info *info)
+                        ppe_net *net, cudaStream_t stream, ppe_solve_info *info, Replan *rp = nullptr)
 {
     const bool fp64 = variant == SV_FP64;
     SolverArgs a;
     a.sys = sys_dev; a.st = st_dev; a.ranges = ranges_dev; a.slots = slots_dev; a.nslots = nslots; a.ctl = ctl_dev;
+    a.max_steps = rp ? rp->max_steps : 0;
+    a.pad_ = 0;
+    int planned_tiles = 0;
+    if (rp)
+        for (int s = 0; s < n; ++s) planned_tiles += (*rp->sds)[s].ntiles;
     a.arrive = nullptr;
     PPE_CUDA_TRY(cudaMallocAsync((void **)&a.arrive, sizeof(uint32_t) * n, stream));
     a.nsys = n; a.ntiles = 0;
@@ -473,8 +492,39 @@ static ppe_status drive(int n, ppe_grid *const *grids, SysDesc *sys_dev, SysStat
             break;
         }
         active = 0;
-        for (int s = 0; s < n; ++s) active += st[s].phase == PH_NET;
-        if (!active) break;
+        int live = 0, live_tiles = 0;
+        for (int s = 0; s < n; ++s) {
+            active += st[s].phase == PH_NET;
+            if (st[s].phase != PH_DONE) {
+                ++live;
+                if (rp) live_tiles += rp->full_tiles[s];
+            }
+        }
+        if (!live) break;
+        if (!active) {
+            // the launch ended on its step budget
+            if (!rp) { status = PPE_ERR_CUDA; set_error("solver kernel left with systems running"); break; }
+            if (live_tiles < rp->fraction * planned_tiles) {
+                std::vector<SysDesc> &sds = *rp->sds;
+                int t0 = 0;
+                for (int s = 0; s < n; ++s) {
+                    sds[s].ntiles = st[s].phase != PH_DONE ? rp->full_tiles[s] : 0;
+                    sds[s].tile0 = t0;
+                    t0 += sds[s].ntiles;
+                }
+                std::vector<BlockRange> ranges;
+                int ns = 0;
+                if (plan_blocks(sds, std::min(rp->max_blocks, t0), ranges, ns) && ns <= rp->slot_cap) {
+                    PPE_CUDA_TRY(cudaMemcpyAsync(sys_dev, sds.data(), sizeof(SysDesc) * n, cudaMemcpyHostToDevice,
+                                                 stream));
+                    PPE_CUDA_TRY(cudaMemcpyAsync(ranges_dev, ranges.data(), sizeof(BlockRange) * ranges.size(),
+                                                 cudaMemcpyHostToDevice, stream));
+                    blocks = (int)ranges.size();     // a.nslots (the bank stride) stays the capacity
+                    planned_tiles = t0;
+                }
+            }
+            continue;
+        }
         float t = 0.f;
         for (int s = 0; s < n; ++s) {
             if (st[s].phase != PH_NET) continue;
@@ -504,8 +554,8 @@ static ppe_status drive(int n, ppe_grid *const *grids, SysDesc *sys_dev, SysStat
         cudaStreamSynchronize(stream);
         double st_ = pr[7] ? (double)pr[7] * 1e3 : 1.0;
         std::fprintf(stderr, "[solver profile] blocks=%d steps=%llu  per step (us): pass %.2f, reduce+publish %.2f, "
-                     "wait %.2f, gather %.2f, advance %.2f\n", blocks, pr[7], pr[0] / st_, pr[1] / st_, pr[2] / st_,
-                     pr[3] / st_, pr[4] / st_);
+                     "wait %.2f, gather %.2f, advance %.2f (state machine %.2f)\n", blocks, pr[7], pr[0] / st_,
+                     pr[1] / st_, pr[2] / st_, pr[3] / st_, pr[4] / st_, pr[5] / st_);
         cudaFree(a.prof);
     }
     cudaFreeAsync(a.arrive, stream);
@@ -606,14 +656,22 @@ ppe_status ppe_solve_batch(int n, ppe_grid *const *grids, const double *const *r
     for (int i = 0; i < n; ++i) ntiles += grids[i]->tiles_x * grids[i]->tiles_y;
     const SolverVariant v = pick_variant(prec, grids[0]->opts.iter_pass, ntiles);
     ntiles = 0;
+    Replan rp;
+    rp.sds = &sds;
     for (int i = 0; i < n; ++i) {
         sds[i] = make_desc(grids[i], rhs[i], x[i], tol, mode, prec, ntiles, v);
         ntiles += sds[i].ntiles;
+        rp.full_tiles.push_back(sds[i].ntiles);
     }
-    int maxb = std::min(solver_max_blocks(v, grids[0]->opts.blocks_per_sm), ntiles);
+    const int maxb_all = solver_max_blocks(v, grids[0]->opts.blocks_per_sm);
+    int maxb = std::min(maxb_all, ntiles);
     std::vector<BlockRange> ranges;
     int nslots = 0;
     if (maxb < 1 || !plan_blocks(sds, maxb, ranges, nslots)) return arg_error("ppe_solve_batch: cannot partition");
+    rp.max_blocks = maxb_all;
+    rp.slot_cap = maxb_all + n + 1;          // parts of any plan: at most one per block plus one per system
+    rp.max_steps = n > 1 ? 400 : 0;
+    nslots = std::max(nslots, rp.slot_cap);
     SysDesc *sys_dev = nullptr;
     SysState *st_dev = nullptr;
     BlockRange *rg_dev = nullptr;
@@ -623,7 +681,7 @@ ppe_status ppe_solve_batch(int n, ppe_grid *const *grids, const double *const *r
         cudaFree(sys_dev); cudaFree(st_dev); cudaFree(rg_dev); cudaFree(part_dev); cudaFree(ctl_dev);
     };
     if (cudaMalloc(&sys_dev, sizeof(SysDesc) * n) != cudaSuccess || cudaMalloc(&st_dev, sizeof(SysState) * n) != cudaSuccess ||
-        cudaMalloc(&rg_dev, sizeof(BlockRange) * ranges.size()) != cudaSuccess ||
+        cudaMalloc(&rg_dev, sizeof(BlockRange) * std::max<size_t>(ranges.size(), (size_t)maxb_all)) != cudaSuccess ||
         cudaMalloc(&part_dev, sizeof(Slot) * 2 * (size_t)nslots) != cudaSuccess ||
         cudaMalloc(&ctl_dev, sizeof(Control)) != cudaSuccess) {
         cleanup();
@@ -633,7 +691,7 @@ ppe_status ppe_solve_batch(int n, ppe_grid *const *grids, const double *const *r
     cudaMemcpyAsync(sys_dev, sds.data(), sizeof(SysDesc) * n, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(rg_dev, ranges.data(), sizeof(BlockRange) * ranges.size(), cudaMemcpyHostToDevice, st);
     ppe_status status = drive(n, grids, sys_dev, st_dev, rg_dev, (int)ranges.size(), part_dev, nslots, ctl_dev, v, net,
-                              st, info);
+                              st, info, rp.max_steps > 0 ? &rp : nullptr);
     cudaStreamSynchronize(st);
     cleanup();
     return status;

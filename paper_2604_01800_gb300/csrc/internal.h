@@ -80,6 +80,7 @@ struct SysDesc {
     int32_t keep_dir_after_dlsm;          // 1: CG directions continue across DLSM steps
     double tol, ru_delta, dlsm_guard, diag_max;
     double n_cells, inv_n;                // nx*ny and its reciprocal
+    float n_cells_f, inv_n_f;             // the same in FP32
     const double *dx, *dy;                // widths [nx], [ny]
     const double *fx, *fy;                // face coefficients [nx+1], [ny+1]; 0 at walls
     const float *dx32, *dy32, *fx32, *fy32;
@@ -102,6 +103,7 @@ struct SysState {
     double alpha_d, xmean, rho, rho_ref;
     float alpha_f, beta_f, mu_f, alpha_d_f;   // FP32 copies for the FP32 passes
     int32_t dlsm_useless, pcur;           // pcur: which p buffer holds the current direction
+    float gamma_f, target_sq_f, ru_sq_f, rho_f;   // FP32 state of the FP32 iteration's transition
 };
 
 // Tiles [t0, t1) of a block; they belong to systems s0..s1.
@@ -140,7 +142,9 @@ struct SolverArgs {
     Control *ctl;
     int32_t nsys, ntiles;
     int64_t spin_limit_ns;
-    unsigned long long *prof;  // nullable: block 0 accumulates ns per step part [0..4] and the step count [7]
+    int32_t max_steps;         // > 0: every block leaves after this many steps (the host may re-plan)
+    int32_t pad_;
+    unsigned long long *prof;  // nullable: block 0 accumulates ns per step part [0..5] and the step count [7]
 };
 
 // Solver kernel variants: FP64, FP32 with the tile-cooperative iteration

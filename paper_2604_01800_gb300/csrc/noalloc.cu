@@ -179,6 +179,8 @@ extern "C" ppe_status ppe_solve_noalloc(int nx, int ny, const double *dx, const 
     sd.diag_max = 0.0;
     sd.n_cells = (double)nx * ny;
     sd.inv_n = 1.0 / sd.n_cells;
+    sd.n_cells_f = (float)sd.n_cells;
+    sd.inv_n_f = (float)sd.inv_n;
     sd.dx = d_dx; sd.dy = d_dy; sd.fx = d_fx; sd.fy = d_fy;
     sd.dx32 = d_dx32; sd.dy32 = d_dy32; sd.fx32 = d_fx32; sd.fy32 = d_fy32;
     sd.f = rhs_dev; sd.x = x_dev;

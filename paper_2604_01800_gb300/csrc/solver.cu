@@ -475,7 +475,8 @@ __device__ void pass_restart(S &sm, const SysDesc &sd, const SysState &st, int i
 
 // Issue the TMA loads of tile t into stage `fill & 1` (one thread).
 template <typename T, typename S>
-__device__ __forceinline__ void iter_issue(S &sm, const SysDesc &sd, const SysState &st, int t, uint32_t fill)
+__device__ __forceinline__ void iter_issue_at(S &sm, const SysDesc &sd, int cur, int pcur, bool first, int t,
+                                              uint32_t fill)
 {
     using G = Geo<S::TW>;
     constexpr int WX = G::WX, WN = G::WN, OX = G::OX, OY = G::OY, RN = G::RN, NRL = G::NRL, TILE_X = G::TX;
@@ -484,7 +485,6 @@ __device__ __forceinline__ void iter_issue(S &sm, const SysDesc &sd, const SysSt
     int i0, j0;
     tile_origin<S::TW>(sd, t, i0, j0);
     const int s = fill & 1;
-    const bool first = st.first != 0;
     Stage<T, S::TW> &stg = sm.u.it.st[s];
     const uint32_t bar = smem_u32(&sm.bar[s]);
     const uint32_t bytes = (uint32_t)(((first ? 1 : 2) * WN + TILE_N) * sizeof(T));
@@ -493,9 +493,15 @@ __device__ __forceinline__ void iter_issue(S &sm, const SysDesc &sd, const SysSt
     // async-proxy copies
     fence_proxy_async();
     mbar_expect_tx(bar, bytes);
-    tma_load_2d(smem_u32(stg.r), sd.tmaps + MAP_R0 + st.cur, bar, i0 - OX, j0 - OY);
-    if (!first) tma_load_2d(smem_u32(stg.p), sd.tmaps + MAP_P0 + st.pcur, bar, i0 - OX, j0 - OY);
+    tma_load_2d(smem_u32(stg.r), sd.tmaps + MAP_R0 + cur, bar, i0 - OX, j0 - OY);
+    if (!first) tma_load_2d(smem_u32(stg.p), sd.tmaps + MAP_P0 + pcur, bar, i0 - OX, j0 - OY);
     tma_load_2d(smem_u32(stg.d), sd.tmaps + MAP_D, bar, i0, j0);
+}
+
+template <typename T, typename S>
+__device__ __forceinline__ void iter_issue(S &sm, const SysDesc &sd, const SysState &st, int t, uint32_t fill)
+{
+    iter_issue_at<T>(sm, sd, st.cur, st.pcur, st.first != 0, t, fill);
 }
 
 // One single-reduction PCG iteration over the tiles [t_lo, t_hi) of system q,
@@ -1098,12 +1104,83 @@ __device__ void advance(const SysDesc &sd, SysState &s, const double (&t)[NPART]
     default:
         break;
     }
+    s.gamma_f = (float)s.gamma;
+    s.rho_f = (float)s.rho;
+    s.target_sq_f = (float)(s.target * s.target);
+    s.ru_sq_f = (float)(sd.ru_delta * s.rho_ref * sd.ru_delta * s.rho_ref);
     s.alpha_f = (float)s.alpha;
     s.beta_f = (float)s.beta;
     s.mu_f = (float)s.mu;
     s.alpha_d_f = (float)s.alpha_d;
 }
 
+
+// float-float product with an FP32 factor: (h + l) * b
+__device__ __forceinline__ void ff_mul(float &h, float &l, float b)
+{
+    const float p = h * b;
+    float e = fmaf(h, b, -p);
+    e = fmaf(l, b, e);
+    h = p + e;
+    l = e - (h - p);
+}
+
+// The transition after an iteration pass of the FP32 kernels, in FP32 and
+// float-float arithmetic: GB300's FP64 pipe has a long latency, and this
+// transition is on the critical path of every iteration.  It computes what
+// the PH_ITER case of advance() computes (the denominator p'.A p', where
+// two terms nearly cancel, in float-float from the float-float dot
+// products) and keeps the FP64 state fields in step for the other phases.
+__device__ void advance_iter_f32(const SysDesc &sd, SysState &s, const float (&h)[NPART], const float (&l)[NPART])
+{
+    s.it_pcg++;
+    s.it_total++;
+    s.cur ^= 1;
+    s.pcur ^= 1;
+    s.first = 0;
+    s.cg_count++;
+    const float mu = (h[3] + l[3]) * sd.inv_n_f;
+    const float rr = (h[2] + l[2]) - sd.n_cells_f * mu * mu;
+    const float rho = rr > 0.f ? rr : 0.f;
+    s.mu_f = mu;
+    s.rho_f = rho;
+    s.mu = (double)mu;
+    s.rho = (double)rho;
+    if (sd.mode == PPE_MODE_HYBRID && !s.fell_back && s.it_total >= sd.hybrid_budget) s.fell_back = 1;
+    if (!isfinite(rho)) {
+        to_res(s, 0);
+        return;
+    }
+    const float gnew = h[0] + l[0];
+    const float beta = __fdiv_rn(gnew, s.gamma_f);
+    // p'.A p' = u'.Au' + beta (2 u'.(Ap) + beta p.(Ap)), in float-float
+    float wh = h[5], wl = l[5];
+    ff_mul(wh, wl, beta);
+    ff_add(wh, wl, 2.f * h[4], 2.f * l[4]);
+    ff_mul(wh, wl, beta);
+    ff_add(wh, wl, h[1], l[1]);
+    const float denom = wh + wl;
+    const bool ok = denom > 0.f && isfinite(beta) && gnew > 0.f;
+    if (rho <= s.target_sq_f || s.it_total >= iter_cap(sd) || !ok || rho <= s.ru_sq_f) {
+        // gamma and alpha of the direction in use stay the reference for the
+        // continuation after the residual replacement
+        to_res(s, ok ? 1 : 0);
+        return;
+    }
+    const float alpha = __fdiv_rn(gnew, denom);
+    s.beta_f = beta;
+    s.alpha_f = alpha;
+    s.gamma_f = gnew;
+    s.beta = (double)beta;
+    s.alpha = (double)alpha;
+    s.gamma = (double)gnew;
+    if (sd.mode == PPE_MODE_HYBRID && !s.fell_back && s.cg_count >= sd.num_cg) {
+        s.dlsm_count = 0;
+        s.phase = PH_NET;
+    } else {
+        s.phase = PH_ITER;
+    }
+}
 
 template <typename T, typename S>
 __device__ void run_pass(S &sm, int q, int ph, int t, Acc &acc)
@@ -1198,8 +1275,11 @@ __global__ void __launch_bounds__(SOLVER_THREADS, (sizeof(T) == 4 && !STREAM) ? 
     const bool prof = a.prof && blockIdx.x == 0 && threadIdx.x == 0;
     // profile split of one step (block 0): pass, block reduce + publish,
     // wait for the other blocks, reduction of their records, state advance
-    uint64_t t_a = prof ? gtimer() : 0, t_p = 0, t_b = 0, t_w = 0, t_r = 0, t_c = 0;
+    uint64_t t_a = prof ? gtimer() : 0, t_p = 0, t_b = 0, t_w = 0, t_r = 0, t_x = 0, t_c = 0;
     for (uint32_t step = 1;; ++step) {
+        // a step budget ends the launch at the same step in every block, so each
+        // system stops between two of its steps
+        if (a.max_steps > 0 && step > (uint32_t)a.max_steps) break;
         // any system of this block still running?
         bool any = false;
         for (int q = 0; q < nq; ++q) any |= is_pass_phase(sm.st[q].phase);
@@ -1265,15 +1345,29 @@ __global__ void __launch_bounds__(SOLVER_THREADS, (sizeof(T) == 4 && !STREAM) ? 
 #pragma unroll
                 for (int k = 0; k < NPART; ++k) h[k] = l[k] = 0.f;
                 const Slot *base = a.slots + (size_t)bank * a.nslots + sd.part0;
-                for (int b = lane; b < sd.nparts; b += 32) {
-                    const float4 *sl = reinterpret_cast<const float4 *>(base + b);
-                    const float4 v0 = __ldcg(sl), v1 = __ldcg(sl + 1), v2 = __ldcg(sl + 2);
+                auto add_slot = [&](const float4 &v0, const float4 &v1, const float4 &v2) {
                     ff_add(h[0], l[0], v0.x, v1.z);
                     ff_add(h[1], l[1], v0.y, v1.w);
                     ff_add(h[2], l[2], v0.z, v2.x);
                     ff_add(h[3], l[3], v0.w, v2.y);
                     ff_add(h[4], l[4], v1.x, v2.z);
                     ff_add(h[5], l[5], v1.y, v2.w);
+                };
+                int b = lane;
+                // two records per lane with their loads in flight together
+                for (; b + 32 < sd.nparts; b += 64) {
+                    float4 v[2][3];
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        const float4 *sl = reinterpret_cast<const float4 *>(base + b + 32 * u);
+                        v[u][0] = __ldcg(sl); v[u][1] = __ldcg(sl + 1); v[u][2] = __ldcg(sl + 2);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) add_slot(v[u][0], v[u][1], v[u][2]);
+                }
+                for (; b < sd.nparts; b += 32) {
+                    const float4 *sl = reinterpret_cast<const float4 *>(base + b);
+                    add_slot(__ldcg(sl), __ldcg(sl + 1), __ldcg(sl + 2));
                 }
 #pragma unroll
                 for (int k = 0; k < NPART; ++k) {
@@ -1286,10 +1380,15 @@ __global__ void __launch_bounds__(SOLVER_THREADS, (sizeof(T) == 4 && !STREAM) ? 
                 }
                 if (lane == 0 && sm.go) {
                     if (prof && q == 0) t_r = gtimer();
-                    double tt[NPART];
+                    if (sizeof(T) == 4 && sm.st[q].phase == PH_ITER) {
+                        advance_iter_f32(sd, sm.st[q], h, l);
+                    } else {
+                        double tt[NPART];
 #pragma unroll
-                    for (int k = 0; k < NPART; ++k) tt[k] = (double)h[k] + (double)l[k];
-                    advance(sd, sm.st[q], tt);
+                        for (int k = 0; k < NPART; ++k) tt[k] = (double)h[k] + (double)l[k];
+                        advance(sd, sm.st[q], tt);
+                    }
+                    if (prof && q == 0) t_x = gtimer();
                 }
             }
             __syncthreads();
@@ -1303,6 +1402,7 @@ __global__ void __launch_bounds__(SOLVER_THREADS, (sizeof(T) == 4 && !STREAM) ? 
                 a.prof[2] += t_w - t_b;
                 a.prof[3] += t_r - t_w;
                 a.prof[4] += t_c - t_r;
+                a.prof[5] += t_x - t_r;
                 a.prof[7] += 1;
             }
             t_p = t_w = t_r = 0;

@@ -1,0 +1,76 @@
+"""Small, self-contained workloads for profiling one kernel at a time.
+
+    python -m paper_2604_01800_gb300.workloads c2            # 512x512 refined box, mixed PCG to 1e-8
+    python -m paper_2604_01800_gb300.workloads capped N ITS  # N x N box grid, mixed PCG capped at ITS iterations
+    python -m paper_2604_01800_gb300.workloads infer         # network inference on the 256x256 cylinder grid
+
+Each runs its solve (or inference) twice or more: the first launch warms up,
+so a profiler can skip it (``-s 1``).  Synthetic inputs only.
+"""
+from __future__ import annotations
+
+import sys
+
+import numpy as np
+
+
+def c2():
+    import torch
+    from . import api, inputs as I
+    w = I.config2(0)
+    g = api.ppe_create_grid(w.dx, w.dy)
+    rhs = torch.tensor(w.f, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        x = torch.zeros_like(rhs)
+        info = api.ppe_solve(g, rhs, x, 1e-8, api.PPE_MODE_PCG, api.PPE_PREC_MIXED)
+    torch.cuda.synchronize()
+    print(f"c2: {info['iters_pcg']} iterations, {info['ms_total']:.2f} ms")
+
+
+def capped(n: int, its: int):
+    import torch
+    from . import api, inputs as I
+    dx = I.box_spacing(n, 0.4, 0.6, 1.01)
+    xc = np.cumsum(dx) - 0.5 * dx
+    gx = np.cos(np.pi * xc) + 0.3 * np.cos(3 * np.pi * xc)
+    gx -= np.dot(dx, gx) / dx.sum()
+    g = api.ppe_create_grid(dx, dx)
+    rhs = torch.outer(torch.tensor(gx, device="cuda"), torch.tensor(gx, device="cuda")).contiguous()
+    x = torch.zeros_like(rhs)
+    api.ppe_set_options(g, max_iters=its, inner_rtol=1e-12)
+    for _ in range(2):
+        x.zero_()
+        info = api.ppe_solve(g, rhs, x, 1e-14, api.PPE_MODE_PCG, api.PPE_PREC_MIXED, raise_on_error=False)
+    torch.cuda.synchronize()
+    print(f"capped {n}x{n}: {info['iters_pcg']} iterations, {info['ms_total']:.2f} ms")
+
+
+def infer():
+    import torch
+    from . import api, inputs as I
+    w = I.config3(0)
+    g = api.ppe_create_grid(w.dx, w.dy, w.mask)
+    net = api.net_create(api.net_default_config(), 1)
+    net.attach(g)
+    r = torch.randn(w.ny, w.nx, device="cuda", dtype=torch.float32)
+    e = torch.empty_like(r)
+    for _ in range(3):
+        net.infer(g, r, e)
+    torch.cuda.synchronize()
+    print(f"infer 256x256: |e| = {float(e.abs().mean()):.3e}")
+
+
+def main(argv=None):
+    a = sys.argv[1:] if argv is None else argv
+    if not a or a[0] == "c2":
+        c2()
+    elif a[0] == "capped":
+        capped(int(a[1]), int(a[2]))
+    elif a[0] == "infer":
+        infer()
+    else:
+        raise SystemExit(__doc__)
+
+
+if __name__ == "__main__":
+    main()
