@@ -96,7 +96,8 @@ typedef struct {
     double inner_rtol;      /* MIXED: FP32 residual drop that triggers an FP64 residual
                                replacement (0.1)                                              */
     double dlsm_guard;      /* skip a DLSM step if e.Ae <= guard * e.e * max(diag A) (1e-10)   */
-    int32_t blocks_per_sm;  /* persistent-kernel CTAs per SM (2; 0 = as many as fit)          */
+    int32_t blocks_per_sm;  /* cap on persistent-kernel CTAs per SM (2; 0 = as many as fit;
+                               the solver kernels fit one)                                    */
     int32_t keep_dir_after_dlsm; /* 0: every CG-type phase restarts with p = z (Sec. 2.2 workflow,
                                as a fresh KSPSolve); 1: CG directions continue across DLSM steps */
     int32_t iter_pass;      /* MIXED precision only: 0 = the autotuned choice if there is one
@@ -206,8 +207,8 @@ PPE_API ppe_status ppe_solve_noalloc(int nx, int ny, const double *dx, const dou
 /*
  * Autotuner of the persistent kernel's launch configuration (the paper has no
  * counterpart).  In MIXED precision it times, on this grid, the iteration-pass
- * variants of ppe_solve_opts.iter_pass (tile-cooperative with 1 and with 2
- * CTAs per SM, and streaming) by capped solves of a smooth synthetic source,
+ * variants of ppe_solve_opts.iter_pass (tile-cooperative and streaming) by
+ * capped solves of a smooth synthetic source,
  * and keeps the fastest: on the grid (used by ppe_solve when
  * opts.iter_pass is 0) and in a process-wide table keyed by (nx, ny) that
  * later grids of the same shape use.  If the environment variable
@@ -219,7 +220,7 @@ PPE_API ppe_status ppe_solve_noalloc(int nx, int ny, const double *dx, const dou
 typedef struct {
     int32_t iter_pass;       /* chosen variant: 1 tile-cooperative, 2 streaming          */
     int32_t blocks_per_sm;   /* chosen CTAs per SM (0: as many as fit)                    */
-    double us_per_iter[3];   /* measured: tile x1 CTA/SM, tile x2 CTAs/SM, streaming      */
+    double us_per_iter[3];   /* measured: tile-cooperative, (unused), streaming           */
     int32_t reserved[4];
 } ppe_tune_report;
 PPE_API ppe_status ppe_autotune(ppe_grid *grid, void *stream, ppe_tune_report *report);

@@ -99,8 +99,7 @@ def ppe_autotune(grid: Grid, stream=None) -> dict:
     rep = _lib.ppe_tune_report()
     check(_lib.load().ppe_autotune(grid.handle, _stream(stream), ctypes.byref(rep)), "ppe_autotune")
     return {"iter_pass": rep.iter_pass, "blocks_per_sm": rep.blocks_per_sm,
-            "us_per_iter": {"tile_1cta": rep.us_per_iter[0], "tile_2cta": rep.us_per_iter[1],
-                            "stream": rep.us_per_iter[2]}}
+            "us_per_iter": {"tile": rep.us_per_iter[0], "stream": rep.us_per_iter[2]}}
 
 
 def ppe_set_direction_source(grid: Grid, fn):

@@ -580,15 +580,16 @@ static ppe_status drive(int n, ppe_grid *const *grids, SysDesc *sys_dev, SysStat
 }
 
 // Kernel variant of a launch.  FP64 has one; in mixed precision the
-// streaming iteration pass pays off once every warp of the grid has at least
-// one tile (the tile-cooperative pass has lower latency on smaller grids).
+// streaming iteration pass pays off once the grid has a few tiles per block
+// (measured on GB300: 2048 x 1024 = 1024 tiles, 30 us per iteration against
+// 39 us; the tile-cooperative pass has the lower latency on grids of a few
+// hundred tiles).  ppe_autotune measures instead of guessing.
 static SolverVariant pick_variant(ppe_precision prec, int iter_pass, int ntiles)
 {
     if (prec == PPE_PREC_FP64) return SV_FP64;
     if (iter_pass == 1) return SV_FP32_TILE;
     if (iter_pass == 2) return SV_FP32_STREAM;
-    const int warps = solver_max_blocks(SV_FP32_STREAM, 0) * (SOLVER_THREADS / 32);
-    return ntiles >= warps ? SV_FP32_STREAM : SV_FP32_TILE;
+    return ntiles >= 1024 ? SV_FP32_STREAM : SV_FP32_TILE;
 }
 
 static ppe_status check_solve_args(ppe_grid *g, const double *rhs, double *x, double tol, ppe_mode mode,

@@ -2,8 +2,8 @@
 // paper has no counterpart).  In mixed precision two iteration passes do the
 // same arithmetic: the tile-cooperative pass (a whole CTA on one 16 x 128
 // tile, lowest latency) and the streaming pass (each warp marches down a
-// strip, highest bandwidth), and the tile-cooperative kernel can run one or
-// two CTAs per SM.  Which is fastest depends on the grid's size and shape, so
+// strip, highest bandwidth).  Which is faster depends on the grid's size and
+// shape, so
 // ppe_autotune times each candidate on the grid itself: capped solves of a
 // smooth synthetic source at two iteration caps, whose time difference is
 // the cost of the extra iterations.  The choice is recorded on the grid and
@@ -155,13 +155,14 @@ extern "C" ppe_status ppe_autotune(ppe_grid *g, void *stream, ppe_tune_report *r
     }
     ppe_status status = check_cuda(cudaMemcpyAsync(rhs, S.data(), bytes, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync");
 
-    // candidates: tile pass with 1 or 2 CTAs per SM, streaming pass
-    struct Cand { int pass, bps; };
-    const Cand cands[3] = {{1, 1}, {1, 2}, {2, 0}};
+    // candidates: the tile-cooperative and the streaming pass (slot 1 of the
+    // report is unused: both kernels run one CTA per SM)
+    struct Cand { int slot, pass, bps; };
+    const Cand cands[2] = {{0, 1, 0}, {2, 2, 0}};
     const int short_cap = 8, long_cap = 40;
     TuneEntry e;
     double best = 1e30;
-    for (int c = 0; c < 3 && status == PPE_OK; ++c) {
+    for (int c = 0; c < 2 && status == PPE_OK; ++c) {
         ppe_solve_opts o = g->opts;
         o.iter_pass = cands[c].pass;
         o.blocks_per_sm = cands[c].bps;
@@ -174,7 +175,7 @@ extern "C" ppe_status ppe_autotune(ppe_grid *g, void *stream, ppe_tune_report *r
         status = time_capped(g, o, rhs, x, st, &t1);
         if (status != PPE_OK) break;
         const double us = 1e6 * std::max(t1 - t0, 0.0) / (long_cap - short_cap);
-        e.us[c] = us;
+        e.us[cands[c].slot] = us;
         if (us < best) {
             best = us;
             e.iter_pass = cands[c].pass;

@@ -130,8 +130,7 @@ template <typename T, int TW_> struct SmemT {
     uint32_t sfills[NWARP];              // streaming pass: chunks issued per warp (buffer = fill & 1)
     Coef<double, TW_> cfd;
     Coef<float, TW_> cff;
-    float red_hi[NPART][NWARP], red_lo[NPART][NWARP];
-    float pub_hi[NPART], pub_lo[NPART];
+    float red_hi[2][NPART][NWARP], red_lo[2][NPART][NWARP];   // per-warp partials, two buffers
     SysDesc sd[SMAX];
     SysState st[SMAX];
     int32_t tag_d, tag_f;   // tile whose coefficients are in cfd / cff
@@ -1210,29 +1209,52 @@ __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p)
 
 // Block-reduce the per-warp accumulators (lane 0 of each warp) into threads
 // 0..NPART-1 (fixed order).
-template <typename S> __device__ void block_reduce_acc(S &sm, const Acc &acc, float (&hi)[NPART], float (&lo)[NPART])
+// Block sums of the pass's partials (fixed order: warp shuffles, then a
+// shuffle tree over the warps in warp 0), written as the block's record for
+// this step; lane 0 of warp 0 then bumps the system's arrival counter.  The
+// per-warp scratch alternates between two buffers, so a warp that runs ahead
+// into the next system's pass cannot overwrite what warp 0 still reads.
+template <typename S>
+__device__ void block_publish(S &sm, const Acc &acc, Slot *slot, uint32_t *counter, int par)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0)
 #pragma unroll
         for (int k = 0; k < NPART; ++k) {
-            sm.red_hi[k][warp] = acc.hi[k];
-            sm.red_lo[k][warp] = acc.lo[k];
+            sm.red_hi[par][k][warp] = acc.hi[k];
+            sm.red_lo[par][k][warp] = acc.lo[k];
         }
     __syncthreads();
-    if (threadIdx.x < NPART) {
-        float h = 0.f, l = 0.f;
-        for (int w = 0; w < NWARP; ++w) ff_add(h, l, sm.red_hi[threadIdx.x][w], sm.red_lo[threadIdx.x][w]);
-        hi[threadIdx.x] = h;
-        lo[threadIdx.x] = l;
+    if (warp == 0) {
+        float h[NPART], l[NPART];
+#pragma unroll
+        for (int k = 0; k < NPART; ++k) {
+            h[k] = lane < NWARP ? sm.red_hi[par][k][lane] : 0.f;
+            l[k] = lane < NWARP ? sm.red_lo[par][k][lane] : 0.f;
+        }
+#pragma unroll
+        for (int o = NWARP / 2; o > 0; o >>= 1)
+#pragma unroll
+            for (int k = 0; k < NPART; ++k) {
+                const float oh = __shfl_down_sync(0xffffffffu, h[k], o);
+                const float ol = __shfl_down_sync(0xffffffffu, l[k], o);
+                ff_add(h[k], l[k], oh, ol);
+            }
+        if (lane == 0) {
+            float4 *dst = reinterpret_cast<float4 *>(slot);
+            dst[0] = make_float4(h[0], h[1], h[2], h[3]);
+            dst[1] = make_float4(h[4], h[5], l[0], l[1]);
+            dst[2] = make_float4(l[2], l[3], l[4], l[5]);
+            __threadfence();
+            atomicAdd(counter, 1u);
+        }
     }
-    __syncthreads();
 }
 
 // STREAM (FP32 only) selects the streaming iteration pass; its register
 // needs allow one block per SM.
 template <typename T, bool STREAM>
-__global__ void __launch_bounds__(SOLVER_THREADS, (sizeof(T) == 4 && !STREAM) ? 2 : 1)
+__global__ void __launch_bounds__(SOLVER_THREADS, 1)
     solver_kernel(SolverArgs a, int resume_net)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -1276,6 +1298,7 @@ __global__ void __launch_bounds__(SOLVER_THREADS, (sizeof(T) == 4 && !STREAM) ? 
     // profile split of one step (block 0): pass, block reduce + publish,
     // wait for the other blocks, reduction of their records, state advance
     uint64_t t_a = prof ? gtimer() : 0, t_p = 0, t_b = 0, t_w = 0, t_r = 0, t_x = 0, t_c = 0;
+    int red_par = 0;
     for (uint32_t step = 1;; ++step) {
         // a step budget ends the launch at the same step in every block, so each
         // system stops between two of its steps
@@ -1301,17 +1324,9 @@ __global__ void __launch_bounds__(SOLVER_THREADS, (sizeof(T) == 4 && !STREAM) ? 
             } else
                 for (int t = lo_t; t < hi_t; ++t) run_pass<T>(sm, q, ph, t, acc);
             if (prof && q == 0) t_p = gtimer();
-            block_reduce_acc(sm, acc, sm.pub_hi, sm.pub_lo);
             Slot *slot = a.slots + (size_t)bank * a.nslots + sd.part0 + (blockIdx.x - sd.blk0);
-            if (threadIdx.x < NPART) {
-                slot->hi[threadIdx.x] = sm.pub_hi[threadIdx.x];
-                slot->lo[threadIdx.x] = sm.pub_lo[threadIdx.x];
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                __threadfence();
-                atomicAdd(&a.arrive[br.s0 + q], 1u);
-            }
+            block_publish(sm, acc, slot, a.arrive + br.s0 + q, red_par);
+            red_par ^= 1;
         }
         if (prof) t_b = gtimer();
         // 2) wait for the records of every block of each live system, reduce,

@@ -3,6 +3,7 @@
     python -m paper_2604_01800_gb300.workloads c2            # 512x512 refined box, mixed PCG to 1e-8
     python -m paper_2604_01800_gb300.workloads capped N ITS  # N x N box grid, mixed PCG capped at ITS iterations
     python -m paper_2604_01800_gb300.workloads infer         # network inference on the 256x256 cylinder grid
+    python -m paper_2604_01800_gb300.workloads train N STEPS # training steps, batch 8 on an N x N stretched grid
 
 Each runs its solve (or inference) twice or more: the first launch warms up,
 so a profiler can skip it (``-s 1``).  Synthetic inputs only.
@@ -60,6 +61,28 @@ def infer():
     print(f"infer 256x256: |e| = {float(e.abs().mean()):.3e}")
 
 
+def train(n: int, steps: int):
+    import time
+
+    import torch
+    from . import api, inputs as I
+    net = api.net_create(api.net_default_config(), 1)
+    g = I.rng(3)
+    dx, dy = I.random_spacing(n, g), I.random_spacing(n, g)
+    grid = api.ppe_create_grid(dx, dy)
+    net.attach(grid)
+    R = np.stack([I.training_rhs(dx, dy, g) for _ in range(8)]).astype(np.float32)
+    R /= np.linalg.norm(R.reshape(8, -1), axis=1)[:, None, None]
+    Rt = torch.tensor(R, device="cuda")
+    hp = api.net_default_hparams(lr0=1e-3, total_steps=max(steps, 1))
+    for i in range(steps):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        loss = net.train_step(grid, Rt, hp)
+        torch.cuda.synchronize()
+        print(f"train {n}x{n} step {i}: loss {loss:.4e}, {1e3 * (time.perf_counter() - t):.1f} ms")
+
+
 def main(argv=None):
     a = sys.argv[1:] if argv is None else argv
     if not a or a[0] == "c2":
@@ -68,6 +91,8 @@ def main(argv=None):
         capped(int(a[1]), int(a[2]))
     elif a[0] == "infer":
         infer()
+    elif a[0] == "train":
+        train(int(a[1]), int(a[2]))
     else:
         raise SystemExit(__doc__)
 

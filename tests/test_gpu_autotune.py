@@ -34,7 +34,7 @@ def test_autotune_then_solve(api, tmp_path):
         assert rep["iter_pass"] in (1, 2)
         assert all(v > 0 for v in rep["us_per_iter"].values()), rep
         best = min(rep["us_per_iter"].values())
-        chosen = {(1, 1): "tile_1cta", (1, 2): "tile_2cta", (2, 0): "stream"}[(rep["iter_pass"], rep["blocks_per_sm"])]
+        chosen = {1: "tile", 2: "stream"}[rep["iter_pass"]]
         assert rep["us_per_iter"][chosen] == best
         line = json.loads(cache.read_text().strip().splitlines()[-1])
         assert (line["nx"], line["ny"], line["iter_pass"]) == (700, 500, rep["iter_pass"])
