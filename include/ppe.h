@@ -187,7 +187,7 @@ PPE_API ppe_status ppe_set_direction_source(ppe_grid *grid, ppe_direction_fn fn,
  * must not allocate after initialisation, a plugin whose host forbids device
  * allocations.  It runs the same persistent solver kernel as ppe_solve but
  * takes all scratch from one fixed-size __device__ array inside the library
- * (about 3.5 MB, held by every GPU that loads the library until exit), and
+ * (about 3.3 MB, held by every GPU that loads the library until exit), and
  * calls no cudaMalloc, cudaFree or other allocating routine.
  *   nx, ny    1 <= nx, ny <= 4096 and nx*ny <= 65536; larger grids return
  *             PPE_ERR_ARG with a message naming the limit.

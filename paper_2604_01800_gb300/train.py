@@ -91,6 +91,55 @@ def pcg_residuals(api, grid, dx, dy, R, gen, frac, kmax, dev):
     api.ppe_set_options(grid)
 
 
+def ritz_vectors(api, grid, n_cells: int, m: int, seed: int, dev):
+    """Ritz vectors of the grid's operator A from m Lanczos steps with full
+    reorthogonalisation (Sec. 2.3, Eq. 13: T_m = V_m^T A V_m, Q_m = V_m U_m),
+    ordered by increasing Ritz value; the constant null space is projected
+    out.  Returns (Q [m, N] FP32 on the device, Ritz values)."""
+    import torch
+    gen = torch.Generator(device=dev).manual_seed(seed)
+    V = torch.zeros(m, n_cells, dtype=torch.float64, device=dev)
+    v = torch.randn(n_cells, dtype=torch.float64, device=dev, generator=gen)
+    v -= v.mean()
+    v /= v.norm()
+    w = torch.empty_like(v)
+    alpha = np.zeros(m)
+    beta = np.zeros(m)
+    ny, nx = grid.ny, grid.nx
+    k_used = m
+    for k in range(m):
+        V[k] = v
+        api.ppe_apply(grid, v.view(ny, nx), w.view(ny, nx))
+        alpha[k] = float(w @ v)
+        w -= alpha[k] * v
+        if k > 0:
+            w -= beta[k - 1] * V[k - 1]
+        for _ in range(2):                      # full reorthogonalisation, twice
+            w -= V[:k + 1].t() @ (V[:k + 1] @ w)
+        w -= w.mean()
+        beta[k] = float(w.norm())
+        if beta[k] < 1e-12 * abs(alpha[k]):
+            k_used = k + 1
+            break
+        v = w / beta[k]
+    T = np.diag(alpha[:k_used]) + np.diag(beta[:k_used - 1], 1) + np.diag(beta[:k_used - 1], -1)
+    theta, U = np.linalg.eigh(T)
+    Q = torch.tensor(U.T, device=dev) @ V[:k_used]
+    return Q.float(), theta
+
+
+def ritz_samples(Q, count: int, b: float, gen):
+    """Samples of Eqs. 14-15: R = sum_j c_j q_j / ||.||, c_j = 9 N(0,1) for the
+    lowest b*m Ritz vectors and N(0,1) for the others."""
+    import torch
+    m = Q.shape[0]
+    c = torch.tensor(gen.standard_normal((count, m)), dtype=torch.float32, device=Q.device)
+    c[:, :int(b * m)] *= 9.0
+    R = c @ Q
+    R -= R.mean(dim=1, keepdim=True)
+    return R / R.norm(dim=1, keepdim=True)
+
+
 def main(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--steps", type=int, default=4000)
@@ -108,11 +157,18 @@ def main(argv=None):
     p.add_argument("--pcg-frac", type=float, default=0.7)
     p.add_argument("--pcg-kmax", type=int, default=2000)
     p.add_argument("--init", default=None, help="start from this weights file")
+    p.add_argument("--ritz-c3", type=int, default=0,
+                   help="fine-tune on the 256x256 cylinder grid with Ritz-vector samples (Eqs. 13-15) "
+                        "from this many Lanczos steps instead of the random-grid dataset")
+    p.add_argument("--ritz-b", type=float, default=0.6)
     a = p.parse_args(argv)
 
     sizes = [int(s) for s in a.sizes.split(",")]
     t0 = time.time()
-    grids, data = build_dataset(a.grids, a.per_grid, sizes)
+    if a.ritz_c3:
+        grids, data = [], []
+    else:
+        grids, data = build_dataset(a.grids, a.per_grid, sizes)
     t_data = time.time() - t0
 
     import torch
@@ -136,6 +192,13 @@ def main(argv=None):
     eg = api.ppe_create_grid(w.dx, w.dy, w.mask)
     net.attach(eg)
     erhs = torch.tensor(w.f, dtype=torch.float64, device=dev)
+    ritz_Q = None
+    if a.ritz_c3:
+        t_r = time.time()
+        ritz_Q, theta = ritz_vectors(api, eg, w.nx * w.ny, a.ritz_c3, a.seed + 5, dev)
+        t_data += time.time() - t_r
+        print(json.dumps({"ritz_steps": a.ritz_c3, "ritz_min": float(theta[0]), "ritz_max": float(theta[-1]),
+                          "seconds": time.time() - t_r}), flush=True)
 
     def evaluate():
         out = {}
@@ -157,10 +220,15 @@ def main(argv=None):
     t1 = time.time()
     ema = None
     for step in range(a.steps):
-        gi = int(gen.integers(0, len(handles)))
-        idx = torch.tensor(gen.choice(pools[gi].shape[0], a.batch, replace=False), device=dev)
-        R = pools[gi].index_select(0, idx).contiguous()
-        loss = net.train_step(handles[gi], R, hp)
+        if ritz_Q is not None:
+            gh = eg
+            R = ritz_samples(ritz_Q, a.batch, a.ritz_b, gen).view(a.batch, w.ny, w.nx).contiguous()
+        else:
+            gi = int(gen.integers(0, len(handles)))
+            idx = torch.tensor(gen.choice(pools[gi].shape[0], a.batch, replace=False), device=dev)
+            R = pools[gi].index_select(0, idx).contiguous()
+            gh = handles[gi]
+        loss = net.train_step(gh, R, hp)
         # loss relative to that of the zero network (mean R^2 = 1/N for unit-norm R)
         rel = loss * R[0].numel()
         ema = rel if ema is None else 0.98 * ema + 0.02 * rel
