@@ -268,7 +268,9 @@ PPE_API ppe_status net_get_params(const ppe_net *net, float *params, int64_t cou
  * present), config, parameter count, step, parameters, [Adam m, v], CRC32.
  * net_save writes the moments (to resume training), net_save_params only the
  * parameters (for inference).  net_load reads either and returns
- * PPE_ERR_FORMAT for a malformed or corrupted file. */
+ * PPE_ERR_FORMAT for a malformed or corrupted file.  A file with moments
+ * resumes at its saved step; one without them starts a fresh optimiser at
+ * step 0 (zero moments, the cosine schedule from lr0). */
 PPE_API ppe_status net_save(const ppe_net *net, const char *path);
 PPE_API ppe_status net_save_params(const ppe_net *net, const char *path);
 PPE_API ppe_status net_load(const char *path, ppe_net **out);

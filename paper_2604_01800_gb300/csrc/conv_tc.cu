@@ -9,9 +9,11 @@
 // zero padding.  The B tile is a TMA box load of the packed weights
 // [Cout][9*Cin] (K-major).  Both land in shared memory in the swizzled
 // K-major layout the tensor cores read; one elected thread issues
-// tcgen05.mma (BF16 x BF16 -> FP32) into a TMEM accumulator, and the four
-// warps read it back with tcgen05.ld for the fused epilogue (bias, GELU,
-// per-pixel Mesh-Conv weight of the consumer layer, BF16 stores).
+// tcgen05.mma (BF16 x BF16 -> FP32) into a TMEM accumulator, and all
+// sixteen warps read it back with tcgen05.ld for the fused epilogue (bias,
+// GELU, per-pixel Mesh-Conv weight of the consumer layer, BF16 stores): the
+// epilogue's SIMT work, not the MMAs, sets the time of these small GEMMs, so
+// it gets four warps per TMEM lane quarter.
 //
 // The input tensor arrives already multiplied by this layer's eta (the
 // producing kernel applies it), so the A operand is loaded as is.
@@ -36,6 +38,9 @@ namespace {
 constexpr int TC_M = 128;
 constexpr int TC_MAX_STAGES = 8;
 constexpr long long TC_WAIT_NS = 1000000000LL;   // 1 s bound on every wait
+constexpr int TC_THREADS = 512;                  // 16 warps: 2 issue roles, all 16 in the epilogue
+constexpr int TC_GROUPS = TC_THREADS / 128;      // epilogue column groups
+constexpr uint32_t TC_BAR_BYTES = 256;           // barriers and the TMEM slot, before the bias
 
 struct TcArgs {
     int B, H, W, cin, cout, n_tile, tw, th, tiles_x, tiles_y, kblocks, stages, tmem_cols;
@@ -103,7 +108,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
 }
 
 template <int BK>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(TC_THREADS, 2)
     conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs a)
 {
     constexpr int SW = BK * 2;                 // swizzle span = row bytes
@@ -114,11 +119,12 @@ __global__ void __launch_bounds__(128, 1)
     const uint32_t b_bytes = (uint32_t)a.n_tile * BK * 2;
     const uint32_t tx_bytes = A_BYTES + b_bytes;                      // bytes landed per stage
     const uint32_t stage_bytes = (tx_bytes + 1023u) & ~1023u;         // 1024-aligned stage stride
-    const uint32_t bar0 = base + a.bar_off;                    // full[8], empty[8], acc
+    const uint32_t bar0 = base + a.bar_off;                    // full[8], empty[8], acc, TMEM slot, bias
     const uint32_t full0 = bar0, empty0 = bar0 + 8 * TC_MAX_STAGES, accb = bar0 + 16 * TC_MAX_STAGES;
     const uint32_t tslot = accb + 8;
     unsigned char *gbase = smem_raw + (base - raw);
     uint32_t *tslot_ptr = reinterpret_cast<uint32_t *>(gbase + (tslot - base));
+    float *bias_s = reinterpret_cast<float *>(gbase + a.bar_off + TC_BAR_BYTES);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tile = blockIdx.x % (a.tiles_x * a.tiles_y), img = blockIdx.x / (a.tiles_x * a.tiles_y);
@@ -126,6 +132,7 @@ __global__ void __launch_bounds__(128, 1)
     const int n0 = blockIdx.y * a.n_tile;
     const int cblocks = a.cin / BK;
 
+    for (int i = threadIdx.x; i < a.n_tile; i += TC_THREADS) bias_s[i] = a.bias ? a.bias[n0 + i] : 0.f;
     if (threadIdx.x == 0) {
         for (int s = 0; s < a.stages; ++s) {
             mbar_init(full0 + 8 * s, 1);
@@ -188,71 +195,90 @@ __global__ void __launch_bounds__(128, 1)
         mma_commit(accb);     // arrives once every MMA issued above has completed
     }
     __syncwarp();
-    // epilogue: thread (warp w, lane l) owns TMEM lane / output pixel m = 32 w + l.
-    // Each output is staged as [128 pixels][n_tile] in the (now idle) pipeline
+    // epilogue: warp w reads TMEM lane quarter w % 4 (output pixels
+    // m = 32 (w % 4) + lane) and the 16-column chunks g, g + G, g + 2G, ... of
+    // the accumulator, g = w / 4 and G = TC_THREADS / 128 column groups.  The
+    // outputs are staged [128 pixels][n_tile] in the (now idle) pipeline
     // shared memory and written back in 16-byte chunks, consecutive threads
-    // taking consecutive chunks of a pixel's channel run.
+    // taking consecutive chunks of a pixel's channel run.  Pass 0 writes the
+    // FP32 pre-activation, pass 1 the BF16 pre-activation, pass 2 the
+    // activation (computed once) into out1 and out2 with their per-pixel
+    // Mesh-Conv weights.
     int ok = mbar_wait(accb, 0, a.err) ? 1 : 0;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     ok = __syncthreads_and(ok && *((volatile int *)a.err) == 0);
-    const int m = threadIdx.x;
+    const int quarter = warp & 3, group = warp >> 2;
+    const int m = quarter * 32 + lane;
     const int px = x0 + m % a.tw, py = y0 + m / a.tw;
     const bool inside = px < a.W && py < a.H;
     const int q = py * a.W + px;
-    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
     unsigned char *stage = gbase;
-    for (int o = 0; o < 4; ++o) {
-        void *dst = nullptr;
-        int cs = a.cout, co = 0, es = 2;
-        float scale = 1.f;
-        bool act = false;
-        if (o == 0) { dst = a.epi.zf_out; es = 4; }
-        else if (o == 1) { dst = a.epi.z_out; }
-        else if (o == 2) {
-            dst = a.epi.out1; cs = a.epi.cs1; co = a.epi.co1; act = a.epi.act != 0;
-            scale = (a.epi.eta1 && inside) ? a.epi.eta1[q] : 1.f;
+    for (int pass = 0; pass < 3 && ok; ++pass) {
+        void *dst0 = nullptr, *dst1 = nullptr;
+        int cs0 = a.cout, co0 = 0, cs1 = a.cout, co1 = 0;
+        float sc0 = 1.f, sc1 = 1.f;
+        const int es = pass == 0 ? 4 : 2;
+        if (pass == 0) {
+            dst0 = a.epi.zf_out;
+        } else if (pass == 1) {
+            dst0 = a.epi.z_out;
         } else {
-            dst = a.epi.out2; cs = a.epi.cs2; co = a.epi.co2; act = a.epi.act != 0;
-            scale = (a.epi.eta2 && inside) ? a.epi.eta2[q] : 1.f;
+            // out1 and out2 share one staging layout; out2 alone moves into slot 0
+            dst0 = a.epi.out1; cs0 = a.epi.cs1; co0 = a.epi.co1;
+            sc0 = (a.epi.eta1 && inside) ? a.epi.eta1[q] : 1.f;
+            dst1 = a.epi.out2; cs1 = a.epi.cs2; co1 = a.epi.co2;
+            sc1 = (a.epi.eta2 && inside) ? a.epi.eta2[q] : 1.f;
+            if (!dst0) { dst0 = dst1; cs0 = cs1; co0 = co1; sc0 = sc1; dst1 = nullptr; }
         }
-        if (!dst || !ok) continue;
-        const int rowb = a.n_tile * es + 16;        // padded staging row (bytes)
-        for (int c = 0; c < a.n_tile; c += 16) {
+        if (!dst0) continue;                          // uniform across the block
+        const int nout = dst1 ? 2 : 1;
+        const bool act = pass == 2 && a.epi.act != 0;
+        const int rowb = a.n_tile * es + 16;          // padded staging row (bytes)
+        const int plane = TC_M * rowb;                // one output's staging
+        for (int c = 16 * group; c < a.n_tile; c += 16 * TC_GROUPS) {
             float v[16];
             tmem_ld16(trow + (uint32_t)c, v);
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
-                float z = v[i] + (a.bias ? a.bias[n0 + c + i] : 0.f);
-                v[i] = (act ? gelu_f(z) : z) * scale;
+                const float z = v[i] + bias_s[c + i];
+                v[i] = act ? gelu_f(z) : z;
             }
-            unsigned char *row = stage + (size_t)m * rowb + (size_t)c * es;
-            if (es == 4) {
+            for (int o = 0; o < nout; ++o) {
+                const float sc = o == 0 ? sc0 : sc1;
+                unsigned char *row = stage + (size_t)o * plane + (size_t)m * rowb + (size_t)c * es;
+                if (es == 4) {
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    *reinterpret_cast<float4 *>(row + 16 * i) = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-            } else {
+                    for (int i = 0; i < 4; ++i)
+                        *reinterpret_cast<float4 *>(row + 16 * i) =
+                            make_float4(v[4 * i] * sc, v[4 * i + 1] * sc, v[4 * i + 2] * sc, v[4 * i + 3] * sc);
+                } else {
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    uint4 pk;
-                    uint32_t *w = reinterpret_cast<uint32_t *>(&pk);
+                    for (int h = 0; h < 2; ++h) {
+                        uint4 pk;
+                        uint32_t *w = reinterpret_cast<uint32_t *>(&pk);
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        __nv_bfloat162 b2 = __floats2bfloat162_rn(v[8 * h + 2 * i], v[8 * h + 2 * i + 1]);
-                        w[i] = *reinterpret_cast<uint32_t *>(&b2);
+                        for (int i = 0; i < 4; ++i) {
+                            __nv_bfloat162 b2 = __floats2bfloat162_rn(v[8 * h + 2 * i] * sc, v[8 * h + 2 * i + 1] * sc);
+                            w[i] = *reinterpret_cast<uint32_t *>(&b2);
+                        }
+                        *reinterpret_cast<uint4 *>(row + 16 * h) = pk;
                     }
-                    *reinterpret_cast<uint4 *>(row + 16 * h) = pk;
                 }
             }
         }
         __syncthreads();
-        const int cpr = a.n_tile * es / 16;         // 16-byte chunks per pixel
-        for (int k = threadIdx.x; k < TC_M * cpr; k += blockDim.x) {
-            const int mm = k / cpr, off = k % cpr;
+        const int cpr = a.n_tile * es / 16;           // 16-byte chunks per pixel
+        for (int k = threadIdx.x; k < nout * TC_M * cpr; k += TC_THREADS) {
+            const int o = k / (TC_M * cpr), rem = k - o * (TC_M * cpr);
+            const int mm = rem / cpr, off = rem - mm * cpr;
             const int qx = x0 + mm % a.tw, qy = y0 + mm / a.tw;
             if (qx >= a.W || qy >= a.H) continue;
             const size_t pp = ((size_t)img * a.H + qy) * a.W + qx;
-            const uint4 val = *reinterpret_cast<const uint4 *>(stage + (size_t)mm * rowb + 16 * off);
-            *reinterpret_cast<uint4 *>(reinterpret_cast<unsigned char *>(dst) + (pp * cs + co + n0) * es + 16 * off) = val;
+            const int cs = o == 0 ? cs0 : cs1, co = o == 0 ? co0 : co1;
+            unsigned char *dst = reinterpret_cast<unsigned char *>(o == 0 ? dst0 : dst1);
+            const uint4 val = *reinterpret_cast<const uint4 *>(stage + (size_t)o * plane + (size_t)mm * rowb + 16 * off);
+            *reinterpret_cast<uint4 *>(dst + (pp * cs + co + n0) * es + 16 * off) = val;
         }
         __syncthreads();
     }
@@ -336,9 +362,10 @@ ppe_status conv3x3_tc(const ConvArgs &a, cudaStream_t s)
     int stages = std::min(TC_MAX_STAGES, (200 * 1024) / stage_bytes);
     stages = std::min(stages, 9 * (a.cin / bk));        // no deeper than the K loop
     if (stages < 2) stages = 2;
-    const size_t staging = (size_t)TC_M * (n_tile * 4 + 16);      // widest epilogue staging (FP32 rows)
+    // widest epilogue staging: one FP32 output, or two BF16 outputs
+    const size_t staging = std::max((size_t)TC_M * (n_tile * 4 + 16), (size_t)2 * TC_M * (n_tile * 2 + 16));
     const size_t bar_off = (std::max((size_t)stage_bytes * stages, staging) + 127) / 128 * 128;
-    const size_t smem = bar_off + 1024 + 16 * TC_MAX_STAGES + 64;
+    const size_t smem = bar_off + TC_BAR_BYTES + (size_t)n_tile * 4 + 1024;   // + alignment slack
 
     CUtensorMap mA, mB;
     CUtensorMapSwizzle sw = bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B
@@ -384,11 +411,11 @@ ppe_status conv3x3_tc(const ConvArgs &a, cudaStream_t s)
     dim3 grid(t.tiles_x * t.tiles_y * a.B, a.cout / n_tile);
     cudaError_t e;
     if (bk == 64)
-        conv_tc_kernel<64><<<grid, 128, smem, s>>>(mA, mB, t);
+        conv_tc_kernel<64><<<grid, TC_THREADS, smem, s>>>(mA, mB, t);
     else if (bk == 32)
-        conv_tc_kernel<32><<<grid, 128, smem, s>>>(mA, mB, t);
+        conv_tc_kernel<32><<<grid, TC_THREADS, smem, s>>>(mA, mB, t);
     else
-        conv_tc_kernel<16><<<grid, 128, smem, s>>>(mA, mB, t);
+        conv_tc_kernel<16><<<grid, TC_THREADS, smem, s>>>(mA, mB, t);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_status(e, "conv_tc_kernel launch");
     return PPE_OK;

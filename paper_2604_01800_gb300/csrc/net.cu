@@ -673,7 +673,9 @@ ppe_status net_load(const char *path, ppe_net **out)
         if (e1 != cudaSuccess || e2 != cudaSuccess) st = cuda_status(e1 != cudaSuccess ? e1 : e2, "net_load");
     }
     if (st != PPE_OK) { net_destroy(n); return st; }
-    n->step = step;
+    // Without its moments the optimiser restarts: Adam's bias correction and
+    // the cosine schedule count from zero again (a fine-tuning run).
+    n->step = moments ? step : 0;
     *out = n;
     return PPE_OK;
 }

@@ -75,8 +75,13 @@ template <> __device__ __forceinline__ double recip<double>(double v) { return v
 
 // Coefficients over the tile window, in the arithmetic type C.
 template <typename C, int TW> struct Coef {
+    // the tile-cooperative geometry also keeps the window's Jacobi weights
+    // D^-1 (computed once per tile, read every pass); the streaming pass
+    // forms them from the 1-D arrays
+    static constexpr bool KEEP_DINV = TW == TILE_X;
     C dx[Geo<TW>::WX], fw[Geo<TW>::WX], fe[Geo<TW>::WX], sx[Geo<TW>::WX];
     C dy[Geo<TW>::WY], fs[Geo<TW>::WY], fn[Geo<TW>::WY], sy[Geo<TW>::WY];
+    C dinv[KEEP_DINV ? Geo<TW>::WN : 1];
 };
 
 // TMA destinations of one tile: r and p windows, d tile (sizes are multiples
@@ -138,9 +143,9 @@ template <typename T, int TW_> struct SmemT {
     uint32_t fills;         // TMA stage fills issued so far (stage = fill & 1)
 };
 
-// Dynamic shared memory of a block (plus 128 bytes of alignment slack): two
-// FP32 blocks per SM, one FP64 block.
-static_assert(2 * (sizeof(SmemT<float, TILE_X>) + 128 + 1024) <= 228 * 1024, "FP32 solver: two blocks per SM");
+// Dynamic shared memory of a block (plus 128 bytes of alignment slack): one
+// block per SM in every variant.
+static_assert(sizeof(SmemT<float, TILE_X>) + 128 <= 227 * 1024, "FP32 solver: one block per SM");
 static_assert(sizeof(SmemT<double, TILE_X>) + 128 <= 227 * 1024, "FP64 solver: one block per SM");
 static_assert(sizeof(SmemT<float, TILE_X_STREAM>) + 128 <= 227 * 1024, "streaming solver: one block per SM");
 
@@ -160,6 +165,13 @@ __device__ void load_coef(Coef<C, TW> &cf, const SysDesc &sd, int i0, int j0, co
         bool in = j >= 0 && j < sd.ny;
         C w = in ? DY[j] : C(0), a = in ? FY[j] : C(0), b = in ? FY[j + 1] : C(0);
         cf.dy[k] = w; cf.fs[k] = a; cf.fn[k] = b; cf.sy[k] = a + b;
+    }
+    if constexpr (Coef<C, TW>::KEEP_DINV) {
+        __syncthreads();
+        for (int k = threadIdx.x; k < Geo<TW>::WN; k += blockDim.x) {
+            const int wi = k % WX, wj = k / WX;
+            cf.dinv[k] = recip<C>(cf.dy[wj] * cf.sx[wi] + cf.dx[wi] * cf.sy[wj]);
+        }
     }
 }
 
@@ -202,7 +214,10 @@ template <typename T, typename S> __device__ __forceinline__ void load_coef_t(S 
 
 template <typename C, int TW> __device__ __forceinline__ C dinv_at(const Coef<C, TW> &cf, int wi, int wj)
 {
-    return recip<C>(cf.dy[wj] * cf.sx[wi] + cf.dx[wi] * cf.sy[wj]);
+    if constexpr (Coef<C, TW>::KEEP_DINV)
+        return cf.dinv[wj * Geo<TW>::WX + wi];
+    else
+        return recip<C>(cf.dy[wj] * cf.sx[wi] + cf.dx[wi] * cf.sy[wj]);
 }
 
 // (A U) at window point (wi, wj); U holds the window, zero outside the domain.

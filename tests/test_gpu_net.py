@@ -115,6 +115,7 @@ def test_weights_file_roundtrip(api, tmp_path):
     net.save(path)
     net2 = api.net_load(path)
     assert np.array_equal(net2.get_params(), net.get_params())
+    assert net2.step == net.step
     raw = bytearray(open(path, "rb").read())
     raw[100] ^= 0xFF
     bad = tmp_path / "bad.ppenet"

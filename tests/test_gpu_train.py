@@ -106,3 +106,25 @@ def test_training_reduces_loss(api):
     losses = [net.train_step(grid, Rt, lr0=2e-3, total_steps=60, rho=2e-4) for _ in range(60)]
     assert losses[-1] < 0.6 * losses[0], (losses[0], losses[-1])
     assert all(np.isfinite(losses))
+
+
+def test_params_only_file_restarts_the_optimiser(api, tmp_path):
+    """A weights file without Adam moments starts a fresh optimiser (step 0),
+    so fine-tuning from it takes real steps even when the saved run had
+    exhausted its own cosine schedule; a file with moments resumes its step."""
+    net, P, grid, dx, dy, R = _setup(api, TINY, 32, 24, 2, 17)
+    Rt = torch.tensor(R, dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        net.train_step(grid, Rt, lr0=1e-3, total_steps=3, rho=0.0)
+    assert net.step == 3
+    full, params = str(tmp_path / "full.ppenet"), str(tmp_path / "params.ppenet")
+    net.save(full, with_moments=True)
+    net.save(params, with_moments=False)
+    assert api.net_load(full).step == 3
+    ft = api.net_load(params)
+    assert ft.step == 0
+    ft.attach(grid)
+    before = ft.get_params()
+    ft.train_step(grid, Rt, lr0=1e-3, total_steps=3, rho=0.0)
+    moved = np.abs(ft.get_params() - before)
+    assert moved.max() > 0.5e-3                        # a first Adam step moves by about lr0
