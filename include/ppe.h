@@ -105,7 +105,11 @@ typedef struct {
                                cells shared by a whole CTA; 2 = streaming (each warp marches
                                down a 120-wide strip; for grids far larger than the number of
                                CTAs).  Same arithmetic, same results up to rounding order.     */
-    int32_t reserved[5];
+    int32_t dlsm_stall_limit; /* hybrid: continue as plain PCG after this many DLSM steps in a
+                               row that each leave more than 90% of the residual norm
+                               (6; 0 = never).  Not in the paper: a guard against a network
+                               that does not fit the grid.                                    */
+    int32_t reserved[4];
 } ppe_solve_opts;
 
 PPE_API void ppe_default_options(ppe_solve_opts *opts);

@@ -1,19 +1,24 @@
 // tcgen05 implicit-GEMM 3x3 convolution for sm_103a (the Mesh-Convs of the
 // DeepONet branch, Sec. 2.4).
 //
-// GEMM view of one CTA: M = 128 output pixels (a TW x TH patch of one image),
-// N = a slice of the output channels, K = 9 taps x Cin input channels.
+// GEMM view of one tile: M = 128 output pixels (a TW x TH patch of one
+// image), N = a slice of the output channels, K = 9 taps x Cin input channels.
 // For every (tap, channel block) the A tile is a TMA box load of the NHWC
 // activation tensor at the tap's shifted coordinates; coordinates outside the
 // image are zero-filled by the TMA unit, which is exactly the convolution's
 // zero padding.  The B tile is a TMA box load of the packed weights
 // [Cout][9*Cin] (K-major).  Both land in shared memory in the swizzled
 // K-major layout the tensor cores read; one elected thread issues
-// tcgen05.mma (BF16 x BF16 -> FP32) into a TMEM accumulator, and all
-// sixteen warps read it back with tcgen05.ld for the fused epilogue (bias,
-// GELU, per-pixel Mesh-Conv weight of the consumer layer, BF16 stores): the
-// epilogue's SIMT work, not the MMAs, sets the time of these small GEMMs, so
-// it gets four warps per TMEM lane quarter.
+// tcgen05.mma (BF16 x BF16 -> FP32) into a TMEM accumulator, and twelve
+// epilogue warps read it back with tcgen05.ld for the fused epilogue (bias,
+// GELU, per-pixel Mesh-Conv weight of the consumer layer, BF16 stores).
+//
+// The layers are small GEMMs (M <= 65,536 pixels, N <= 256, K <= 2,304), so a
+// CTA per tile would spend most of its life filling its pipeline and draining
+// its accumulator.  The kernel is therefore persistent: one or two CTAs per
+// SM walk the tiles; the TMA stage ring runs on from one tile to the next,
+// and two TMEM accumulators let the epilogue of a tile overlap the MMAs of
+// the following one.
 //
 // The input tensor arrives already multiplied by this layer's eta (the
 // producing kernel applies it), so the A operand is loaded as is.
@@ -38,13 +43,16 @@ namespace {
 constexpr int TC_M = 128;
 constexpr int TC_MAX_STAGES = 8;
 constexpr long long TC_WAIT_NS = 1000000000LL;   // 1 s bound on every wait
-constexpr int TC_THREADS = 512;                  // 16 warps: 2 issue roles, all 16 in the epilogue
-constexpr int TC_GROUPS = TC_THREADS / 128;      // epilogue column groups
-constexpr uint32_t TC_BAR_BYTES = 256;           // barriers and the TMEM slot, before the bias
+constexpr int TC_THREADS = 512;                  // warp 0: TMA producer, warp 1: MMA issuer, warps 4-15: epilogue
+constexpr int TC_EPI_WARP0 = 4;
+constexpr int TC_EPI_WARPS = TC_THREADS / 32 - TC_EPI_WARP0;   // three per TMEM lane quarter
+constexpr int TC_GROUPS = TC_EPI_WARPS / 4;                      // epilogue column groups
+constexpr uint32_t TC_BAR_BYTES = 256;           // barriers and the TMEM slot
 
 struct TcArgs {
     int B, H, W, cin, cout, n_tile, tw, th, tiles_x, tiles_y, kblocks, stages, tmem_cols;
-    uint32_t bar_off;       // byte offset of the barriers: past both the pipeline and the epilogue staging
+    int nslices, ntiles;    // output-channel slices; tiles = (image patches) x slices
+    uint32_t bar_off;       // byte offset of the barriers, past the pipeline stages
     const float *bias;
     Epi epi;
     int *err;
@@ -93,6 +101,27 @@ __device__ __forceinline__ void mma_commit(uint32_t bar)
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(bar) : "memory");
+}
+
+// 16 consecutive BF16 channels (32 bytes, 16-byte aligned), each scaled by sc.
+__device__ __forceinline__ void store_bf16x16(bf16 *dst, const float (&v)[16], float sc)
+{
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        uint4 pk;
+        uint32_t *w = reinterpret_cast<uint32_t *>(&pk);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            __nv_bfloat162 b2 = __floats2bfloat162_rn(v[8 * h + 2 * i] * sc, v[8 * h + 2 * i + 1] * sc);
+            w[i] = *reinterpret_cast<uint32_t *>(&b2);
+        }
+        reinterpret_cast<uint4 *>(dst)[h] = pk;
+    }
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
 {
     uint32_t r[16];
@@ -119,26 +148,26 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
     const uint32_t b_bytes = (uint32_t)a.n_tile * BK * 2;
     const uint32_t tx_bytes = A_BYTES + b_bytes;                      // bytes landed per stage
     const uint32_t stage_bytes = (tx_bytes + 1023u) & ~1023u;         // 1024-aligned stage stride
-    const uint32_t bar0 = base + a.bar_off;                    // full[8], empty[8], acc, TMEM slot, bias
-    const uint32_t full0 = bar0, empty0 = bar0 + 8 * TC_MAX_STAGES, accb = bar0 + 16 * TC_MAX_STAGES;
-    const uint32_t tslot = accb + 8;
-    unsigned char *gbase = smem_raw + (base - raw);
-    uint32_t *tslot_ptr = reinterpret_cast<uint32_t *>(gbase + (tslot - base));
-    float *bias_s = reinterpret_cast<float *>(gbase + a.bar_off + TC_BAR_BYTES);
+    // barriers: full[8], empty[8] of the stages; acc_full[2], acc_empty[2] of
+    // the two TMEM accumulators; then the TMEM address slot
+    const uint32_t bar0 = base + a.bar_off;
+    const uint32_t full0 = bar0, empty0 = bar0 + 8 * TC_MAX_STAGES;
+    const uint32_t accf0 = bar0 + 16 * TC_MAX_STAGES, acce0 = accf0 + 16, tslot = acce0 + 16;
+    uint32_t *tslot_ptr = reinterpret_cast<uint32_t *>(smem_raw + (tslot - raw));
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tile = blockIdx.x % (a.tiles_x * a.tiles_y), img = blockIdx.x / (a.tiles_x * a.tiles_y);
-    const int x0 = (tile % a.tiles_x) * a.tw, y0 = (tile / a.tiles_x) * a.th;
-    const int n0 = blockIdx.y * a.n_tile;
     const int cblocks = a.cin / BK;
+    const int tiles_xy = a.tiles_x * a.tiles_y;
 
-    for (int i = threadIdx.x; i < a.n_tile; i += TC_THREADS) bias_s[i] = a.bias ? a.bias[n0 + i] : 0.f;
     if (threadIdx.x == 0) {
         for (int s = 0; s < a.stages; ++s) {
             mbar_init(full0 + 8 * s, 1);
             mbar_init(empty0 + 8 * s, 1);
         }
-        mbar_init(accb, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(accf0 + 8 * b, 1);
+            mbar_init(acce0 + 8 * b, TC_EPI_WARPS);
+        }
         mbar_init_fence();
         asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
@@ -154,134 +183,121 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tslot_ptr;
 
-    if (warp == 0 && lane == 0) {
-        // producer: TMA loads of the A (activation) and B (weight) tiles
-        bool ok = true;
-        int armed = 0;
-        for (int kb = 0; kb < a.kblocks && ok; ++kb) {
-            int s = kb % a.stages;
-            uint32_t ph = (kb / a.stages) & 1;
-            ok = mbar_wait(empty0 + 8 * s, ph ^ 1, a.err);
-            if (!ok) break;
-            int tap = kb / cblocks, c0 = (kb % cblocks) * BK;
-            int ky = tap / 3, kx = tap % 3;
-            uint32_t sa = base + stage_bytes * s, sb = sa + A_BYTES;
-            mbar_expect_tx(full0 + 8 * s, tx_bytes);
-            tma_load_4d(sa, &tmA, full0 + 8 * s, c0, x0 + kx - 1, y0 + ky - 1, img);
-            tma_load_2d(sb, &tmB, full0 + 8 * s, tap * a.cin + c0, n0);
-            armed = kb + 1;
-        }
-        if (!ok) {
-            // let copies already in flight land before the CTA leaves
-            for (int kb = (armed > a.stages ? armed - a.stages : 0); kb < armed; ++kb)
-                mbar_wait(full0 + 8 * (kb % a.stages), (kb / a.stages) & 1, a.err);
-        }
-    } else if (warp == 1 && lane == 0) {
-        // MMA issuer
-        const uint32_t idesc = instr_desc(a.n_tile);
-        bool ok = true;
-        for (int kb = 0; kb < a.kblocks; ++kb) {
-            int s = kb % a.stages;
-            uint32_t ph = (kb / a.stages) & 1;
-            ok = mbar_wait(full0 + 8 * s, ph, a.err);
-            if (!ok) break;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            uint32_t sa = base + stage_bytes * s, sb = sa + A_BYTES;
-#pragma unroll
-            for (int k = 0; k < BK / 16; ++k)
-                mma_bf16(tmem, smem_desc<SW>(sa + 32 * k), smem_desc<SW>(sb + 32 * k), idesc, (kb | k) != 0);
-            mma_commit(empty0 + 8 * s);
-        }
-        mma_commit(accb);     // arrives once every MMA issued above has completed
-    }
-    __syncwarp();
-    // epilogue: warp w reads TMEM lane quarter w % 4 (output pixels
-    // m = 32 (w % 4) + lane) and the 16-column chunks g, g + G, g + 2G, ... of
-    // the accumulator, g = w / 4 and G = TC_THREADS / 128 column groups.  The
-    // outputs are staged [128 pixels][n_tile] in the (now idle) pipeline
-    // shared memory and written back in 16-byte chunks, consecutive threads
-    // taking consecutive chunks of a pixel's channel run.  Pass 0 writes the
-    // FP32 pre-activation, pass 1 the BF16 pre-activation, pass 2 the
-    // activation (computed once) into out1 and out2 with their per-pixel
-    // Mesh-Conv weights.
-    int ok = mbar_wait(accb, 0, a.err) ? 1 : 0;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    ok = __syncthreads_and(ok && *((volatile int *)a.err) == 0);
-    const int quarter = warp & 3, group = warp >> 2;
-    const int m = quarter * 32 + lane;
-    const int px = x0 + m % a.tw, py = y0 + m / a.tw;
-    const bool inside = px < a.W && py < a.H;
-    const int q = py * a.W + px;
-    const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
-    unsigned char *stage = gbase;
-    for (int pass = 0; pass < 3 && ok; ++pass) {
-        void *dst0 = nullptr, *dst1 = nullptr;
-        int cs0 = a.cout, co0 = 0, cs1 = a.cout, co1 = 0;
-        float sc0 = 1.f, sc1 = 1.f;
-        const int es = pass == 0 ? 4 : 2;
-        if (pass == 0) {
-            dst0 = a.epi.zf_out;
-        } else if (pass == 1) {
-            dst0 = a.epi.z_out;
-        } else {
-            // out1 and out2 share one staging layout; out2 alone moves into slot 0
-            dst0 = a.epi.out1; cs0 = a.epi.cs1; co0 = a.epi.co1;
-            sc0 = (a.epi.eta1 && inside) ? a.epi.eta1[q] : 1.f;
-            dst1 = a.epi.out2; cs1 = a.epi.cs2; co1 = a.epi.co2;
-            sc1 = (a.epi.eta2 && inside) ? a.epi.eta2[q] : 1.f;
-            if (!dst0) { dst0 = dst1; cs0 = cs1; co0 = co1; sc0 = sc1; dst1 = nullptr; }
-        }
-        if (!dst0) continue;                          // uniform across the block
-        const int nout = dst1 ? 2 : 1;
-        const bool act = pass == 2 && a.epi.act != 0;
-        const int rowb = a.n_tile * es + 16;          // padded staging row (bytes)
-        const int plane = TC_M * rowb;                // one output's staging
-        for (int c = 16 * group; c < a.n_tile; c += 16 * TC_GROUPS) {
-            float v[16];
-            tmem_ld16(trow + (uint32_t)c, v);
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const float z = v[i] + bias_s[c + i];
-                v[i] = act ? gelu_f(z) : z;
-            }
-            for (int o = 0; o < nout; ++o) {
-                const float sc = o == 0 ? sc0 : sc1;
-                unsigned char *row = stage + (size_t)o * plane + (size_t)m * rowb + (size_t)c * es;
-                if (es == 4) {
-#pragma unroll
-                    for (int i = 0; i < 4; ++i)
-                        *reinterpret_cast<float4 *>(row + 16 * i) =
-                            make_float4(v[4 * i] * sc, v[4 * i + 1] * sc, v[4 * i + 2] * sc, v[4 * i + 3] * sc);
-                } else {
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        uint4 pk;
-                        uint32_t *w = reinterpret_cast<uint32_t *>(&pk);
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            __nv_bfloat162 b2 = __floats2bfloat162_rn(v[8 * h + 2 * i] * sc, v[8 * h + 2 * i + 1] * sc);
-                            w[i] = *reinterpret_cast<uint32_t *>(&b2);
-                        }
-                        *reinterpret_cast<uint4 *>(row + 16 * h) = pk;
-                    }
+    // The CTA walks the tiles blockIdx.x, blockIdx.x + gridDim.x, ...; tile t
+    // is output patch t / nslices and channel slice t % nslices.  The stage
+    // ring and its phases run on across tiles; the accumulator alternates
+    // between two TMEM buffers, so the epilogue of one tile overlaps the MMAs
+    // of the next.
+    if (warp == 0) {
+        if (lane == 0) {
+            // producer: TMA loads of the A (activation) and B (weight) tiles
+            bool ok = true;
+            int it = 0, armed = 0;
+            for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
+                const int mt = t / a.nslices, ns = t - mt * a.nslices;
+                const int img = mt / tiles_xy, tile = mt - img * tiles_xy;
+                const int x0 = (tile % a.tiles_x) * a.tw, y0 = (tile / a.tiles_x) * a.th, n0 = ns * a.n_tile;
+                for (int kb = 0; kb < a.kblocks; ++kb, ++it) {
+                    const int s = it % a.stages;
+                    const uint32_t ph = (it / a.stages) & 1;
+                    ok = mbar_wait(empty0 + 8 * s, ph ^ 1, a.err);
+                    if (!ok) break;
+                    const int tap = kb / cblocks, c0 = (kb % cblocks) * BK;
+                    const int ky = tap / 3, kx = tap % 3;
+                    const uint32_t sa = base + stage_bytes * s, sb = sa + A_BYTES;
+                    mbar_expect_tx(full0 + 8 * s, tx_bytes);
+                    tma_load_4d(sa, &tmA, full0 + 8 * s, c0, x0 + kx - 1, y0 + ky - 1, img);
+                    tma_load_2d(sb, &tmB, full0 + 8 * s, tap * a.cin + c0, n0);
+                    armed = it + 1;
                 }
             }
+            if (!ok) {
+                // let copies already in flight land before the CTA leaves
+                for (int k = (armed > a.stages ? armed - a.stages : 0); k < armed; ++k)
+                    mbar_wait(full0 + 8 * (k % a.stages), (k / a.stages) & 1, a.err);
+            }
         }
-        __syncthreads();
-        const int cpr = a.n_tile * es / 16;           // 16-byte chunks per pixel
-        for (int k = threadIdx.x; k < nout * TC_M * cpr; k += TC_THREADS) {
-            const int o = k / (TC_M * cpr), rem = k - o * (TC_M * cpr);
-            const int mm = rem / cpr, off = rem - mm * cpr;
-            const int qx = x0 + mm % a.tw, qy = y0 + mm / a.tw;
-            if (qx >= a.W || qy >= a.H) continue;
-            const size_t pp = ((size_t)img * a.H + qy) * a.W + qx;
-            const int cs = o == 0 ? cs0 : cs1, co = o == 0 ? co0 : co1;
-            unsigned char *dst = reinterpret_cast<unsigned char *>(o == 0 ? dst0 : dst1);
-            const uint4 val = *reinterpret_cast<const uint4 *>(stage + (size_t)o * plane + (size_t)mm * rowb + 16 * off);
-            *reinterpret_cast<uint4 *>(dst + (pp * cs + co + n0) * es + 16 * off) = val;
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // MMA issuer
+            const uint32_t idesc = instr_desc(a.n_tile);
+            bool ok = true;
+            int it = 0;
+            for (int t = blockIdx.x, i = 0; t < a.ntiles && ok; t += gridDim.x, ++i) {
+                const int b = i & 1;
+                ok = mbar_wait(acce0 + 8 * b, ((i >> 1) & 1) ^ 1, a.err);   // epilogue drained buffer b
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t acc = tmem + (uint32_t)(b * a.n_tile);
+                for (int kb = 0; kb < a.kblocks; ++kb, ++it) {
+                    const int s = it % a.stages;
+                    ok = mbar_wait(full0 + 8 * s, (it / a.stages) & 1, a.err);
+                    if (!ok) break;
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t sa = base + stage_bytes * s, sb = sa + A_BYTES;
+#pragma unroll
+                    for (int k = 0; k < BK / 16; ++k)
+                        mma_bf16(acc, smem_desc<SW>(sa + 32 * k), smem_desc<SW>(sb + 32 * k), idesc, (kb | k) != 0);
+                    mma_commit(empty0 + 8 * s);
+                }
+                if (!ok) break;
+                mma_commit(accf0 + 8 * b);      // arrives once every MMA of this tile has completed
+            }
         }
-        __syncthreads();
+    } else if (warp >= TC_EPI_WARP0) {
+        // epilogue: warp w reads TMEM lane quarter w % 4 (output pixels
+        // m = 32 (w % 4) + lane) and the 16-column chunks g, g + G, ... of the
+        // accumulator, g its column group.  Each thread stores its pixel's
+        // channel runs directly (32- or 64-byte pieces): bias, the FP32 and
+        // BF16 pre-activations when asked for, and the activation (computed
+        // once) into out1 and out2 with their per-pixel Mesh-Conv weights.
+        const int quarter = warp & 3, group = (warp - TC_EPI_WARP0) >> 2;
+        const int m = quarter * 32 + lane;
+        const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+        const Epi &e = a.epi;
+        for (int t = blockIdx.x, i = 0; t < a.ntiles; t += gridDim.x, ++i) {
+            const int b = i & 1;
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(accf0 + 8 * b, (i >> 1) & 1, a.err));
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int mt = t / a.nslices, ns = t - mt * a.nslices;
+            const int img = mt / tiles_xy, tile = mt - img * tiles_xy;
+            const int px = (tile % a.tiles_x) * a.tw + m % a.tw, py = (tile / a.tiles_x) * a.th + m / a.tw;
+            const int n0 = ns * a.n_tile;
+            const bool inside = px < a.W && py < a.H;
+            const int q = py * a.W + px;
+            const size_t pp = ((size_t)img * a.H + py) * a.W + px;
+            const float sc1 = (e.eta1 && inside) ? e.eta1[q] : 1.f;
+            const float sc2 = (e.eta2 && inside) ? e.eta2[q] : 1.f;
+            const bool act = e.act != 0;
+            for (int c = 16 * group; c < a.n_tile; c += 16 * TC_GROUPS) {
+                float v[16];
+                tmem_ld16(tmem + (uint32_t)(b * a.n_tile + c) + lane_off, v);
+                if (!inside) continue;
+                const int ch = n0 + c;
+#pragma unroll
+                for (int k = 0; k < 16; ++k) v[k] += a.bias ? __ldg(a.bias + ch + k) : 0.f;
+                if (e.zf_out) {
+                    float4 *d = reinterpret_cast<float4 *>(e.zf_out + pp * a.cout + ch);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) d[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+                }
+                if (e.z_out) store_bf16x16(e.z_out + pp * a.cout + ch, v, 1.f);
+                if (e.out1 || e.out2) {
+                    if (act) {
+#pragma unroll
+                        for (int k = 0; k < 16; ++k) v[k] = gelu_f(v[k]);
+                    }
+                    if (e.out1) store_bf16x16(e.out1 + pp * e.cs1 + e.co1 + ch, v, sc1);
+                    if (e.out2) store_bf16x16(e.out2 + pp * e.cs2 + e.co2 + ch, v, sc2);
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acce0 + 8 * b);     // buffer b may be overwritten
+        }
     }
+    __syncwarp();
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
@@ -300,6 +316,19 @@ int *err_flag()
         if (cudaMalloc(&flag, sizeof(int)) == cudaSuccess) cudaMemset(flag, 0, sizeof(int));
     });
     return flag;
+}
+
+int sm_count()
+{
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+    if (!cache[dev]) {
+        int n = 0;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        cache[dev] = n > 0 ? n : 1;
+    }
+    return cache[dev];
 }
 
 int pick_bk(int cin) { return cin % 64 == 0 ? 64 : (cin % 32 == 0 ? 32 : 16); }
@@ -349,23 +378,31 @@ ppe_status conv3x3_tc(const ConvArgs &a, cudaStream_t s)
     int n_tile = a.cout;
     while (n_tile > 256) n_tile /= 2;
     if (a.cout % n_tile) n_tile = 16;
-    {
-        // few output patches (deep U-Net levels): split the output channels so
-        // that enough CTAs run; each slice re-reads the activations (L2-resident)
-        const long mtiles = (long)((a.W + tw - 1) / tw) * ((a.H + th - 1) / th) * a.B;
-        while (mtiles * (a.cout / n_tile) < 128 && n_tile % 32 == 0 && n_tile > 32 && a.cout % (n_tile / 2) == 0)
-            n_tile /= 2;                                      // stays a multiple of 16
-    }
-    int tmem_cols = 32;
-    while (tmem_cols < n_tile) tmem_cols *= 2;
+    const int nsm = sm_count();
+    const long mtiles = (long)((a.W + tw - 1) / tw) * ((a.H + th - 1) / th) * a.B;
+    // few output patches (deep U-Net levels): split the output channels until
+    // every SM has a tile; each slice re-reads the activations (L2-resident)
+    while (mtiles * (a.cout / n_tile) < nsm && n_tile % 32 == 0 && n_tile > 16 && a.cout % (n_tile / 2) == 0)
+        n_tile /= 2;                                          // stays a multiple of 16
+    const int nslices = a.cout / n_tile;
+    const long ntiles = mtiles * nslices;
+    int tmem_cols = 32;                                       // two accumulators of n_tile columns
+    while (tmem_cols < 2 * n_tile) tmem_cols *= 2;
     const int stage_bytes = ((TC_M + n_tile) * bk * 2 + 1023) / 1024 * 1024;
-    int stages = std::min(TC_MAX_STAGES, (200 * 1024) / stage_bytes);
-    stages = std::min(stages, 9 * (a.cin / bk));        // no deeper than the K loop
+    // two CTAs per SM when a pipeline of three or more stages fits in half the
+    // shared memory and both CTAs' accumulators fit the 512 TMEM columns
+    int ctas_per_sm = 2;
+    int stages = std::min(TC_MAX_STAGES, (110 * 1024) / stage_bytes);
+    if (stages < 3 || tmem_cols > 256) {
+        ctas_per_sm = 1;
+        stages = std::min(TC_MAX_STAGES, (200 * 1024) / stage_bytes);
+    }
     if (stages < 2) stages = 2;
-    // widest epilogue staging: one FP32 output, or two BF16 outputs
-    const size_t staging = std::max((size_t)TC_M * (n_tile * 4 + 16), (size_t)2 * TC_M * (n_tile * 2 + 16));
-    const size_t bar_off = (std::max((size_t)stage_bytes * stages, staging) + 127) / 128 * 128;
-    const size_t smem = bar_off + TC_BAR_BYTES + (size_t)n_tile * 4 + 1024;   // + alignment slack
+    const size_t bar_off = (size_t)stage_bytes * stages;
+    size_t smem = bar_off + TC_BAR_BYTES + 1024;             // + alignment slack
+    // one CTA per SM: claim more than half the shared memory, so that no second
+    // CTA lands on the SM and waits for the first one's TMEM
+    if (ctas_per_sm == 1) smem = std::max(smem, (size_t)116 * 1024);
 
     CUtensorMap mA, mB;
     CUtensorMapSwizzle sw = bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B
@@ -401,6 +438,8 @@ ppe_status conv3x3_tc(const ConvArgs &a, cudaStream_t s)
     t.tw = tw; t.th = th;
     t.tiles_x = (a.W + tw - 1) / tw;
     t.tiles_y = (a.H + th - 1) / th;
+    t.nslices = nslices;
+    t.ntiles = (int)ntiles;
     t.kblocks = 9 * (a.cin / bk);
     t.stages = stages;
     t.tmem_cols = tmem_cols;
@@ -408,7 +447,8 @@ ppe_status conv3x3_tc(const ConvArgs &a, cudaStream_t s)
     t.bias = a.bias;
     t.epi = a.epi;
     t.err = err;
-    dim3 grid(t.tiles_x * t.tiles_y * a.B, a.cout / n_tile);
+    // persistent: one or two CTAs per SM, each walking its share of the tiles
+    dim3 grid((unsigned)std::min<long>(ntiles, (long)nsm * ctas_per_sm));
     cudaError_t e;
     if (bk == 64)
         conv_tc_kernel<64><<<grid, TC_THREADS, smem, s>>>(mA, mB, t);

@@ -78,6 +78,7 @@ struct SysDesc {
     int32_t max_iters, num_cg, num_dlsm, hybrid_budget;
     int32_t part0, blk0, nparts;          // partial slots part0.. for blocks blk0..blk0+nparts-1
     int32_t keep_dir_after_dlsm;          // 1: CG directions continue across DLSM steps
+    int32_t dlsm_stall_limit;             // DLSM steps in a row that barely reduce r before plain PCG (0: never)
     double tol, ru_delta, dlsm_guard, diag_max;
     double n_cells, inv_n;                // nx*ny and its reciprocal
     float n_cells_f, inv_n_f;             // the same in FP32

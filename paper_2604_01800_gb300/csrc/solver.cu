@@ -1091,7 +1091,7 @@ __device__ void advance(const SysDesc &sd, SysState &s, const double (&t)[NPART]
         // a direction that removes less than 10% of the residual norm is not
         // worth its inference; after several in a row continue as plain PCG
         s.dlsm_useless = s.rho > 0.81 * rho_before ? s.dlsm_useless + 1 : 0;
-        if (s.dlsm_useless >= 6) s.fell_back = 1;
+        if (sd.dlsm_stall_limit > 0 && s.dlsm_useless >= sd.dlsm_stall_limit) s.fell_back = 1;
         s.dlsm_count++;
         if (sd.mode == PPE_MODE_HYBRID && !s.fell_back && s.it_total >= sd.hybrid_budget) s.fell_back = 1;
         const double ru = sd.ru_delta * s.rho_ref;
