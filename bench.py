@@ -29,6 +29,9 @@ from paper_2604_01800_gb300 import inputs as I  # noqa: E402
 
 METRIC = "PPE solves/s at rel-res 1e-8 (512x512 refined-box grid, mixed FP32/FP64 PCG)"
 WEIGHTS = os.path.join(ROOT, "paper_2604_01800_gb300", "weights", "hydea_mconv.ppenet")
+# DRAM bytes of one launch of the solver kernel on the 512x512 workload (one
+# whole mixed-precision solve), from an ncu capture of the current kernel
+SOLVER_C2_DRAM_BYTES = 4.441856e6 + 0.09344e6
 TOL = 1e-8
 L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2
 
@@ -242,7 +245,9 @@ def run_native(args):
     alg_bytes = n * (24.0 * it + 24.0 * ref)       # FP32 iterations + FP64 residual passes
     achieved = alg_bytes / (t_total / args.steps) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+            "frac": achieved / peaks["hbm_gbs"], "traffic": SOLVER_C2_DRAM_BYTES,
+            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch (one solve), "
+                              "profiles/solver_kernel_tile_c2.md",
             "kernel": "solver_kernel<float>", "peak_source": f"hbm_gbs ({peak_src})",
             "note": "working set (~10 MB) is L2-resident: latency/barrier-bound, not HBM-bound"}
 
@@ -270,38 +275,41 @@ def run_native(args):
 
 
 def hybrid_vs_plain(api, dev, flush, reps=5):
-    """HyDEA (Jacobi PCG + DLSM with the trained network) against plain PCG on
-    the 256x256 cylinder-refined grid with a masked-divergence source, both
-    mixed precision, to rel-res 1e-8 (median of `reps` solves each)."""
+    """HyDEA (Jacobi PCG + DLSM with a trained network) against plain PCG on
+    the 256x256 cylinder-refined grid with masked-divergence sources, all in
+    mixed precision, to rel-res 1e-8 (median of `reps` sources each), with
+    the network trained on random stretched grids."""
     import torch
     if not os.path.exists(WEIGHTS):
         return {"available": False, "reason": "no trained weights file"}
-    net = api.net_load(WEIGHTS)
+    nets = {"hybrid": api.net_load(WEIGHTS)}
     out = {"workload": "cyl256_mask (256x256, cylinder D=0.1, box-refined, growth 1.05)"}
-    for name, seeds in (("cyl256", range(reps)),):
-        rows = {"pcg": [], "hybrid": []}
-        for i in seeds:
-            w = I.config3(i)
-            g = api.ppe_create_grid(w.dx, w.dy, w.mask)
-            net.attach(g)
-            rhs = torch.tensor(w.f, dtype=torch.float64, device=dev)
-            for mode, key in ((api.PPE_MODE_PCG, "pcg"), (api.PPE_MODE_HYBRID, "hybrid")):
-                x = torch.zeros_like(rhs)
-                api.ppe_solve(g, rhs, x, TOL, mode, api.PPE_PREC_MIXED, net=net)     # warm (graph capture)
-                flush.fill_(1.0)
-                x.zero_()
-                info = api.ppe_solve(g, rhs, x, TOL, mode, api.PPE_PREC_MIXED, net=net)
-                rows[key].append(info)
-            g.close()
-        for key, infos in rows.items():
-            ms = float(np.median([i["ms_total"] for i in infos]))
-            out[key] = {"solves_per_s": 1e3 / ms, "ms_median": ms,
-                        "iters_median": float(np.median([i["iters_pcg"] + i["iters_dlsm"] for i in infos])),
-                        "dlsm_steps_median": float(np.median([i["iters_dlsm"] for i in infos])),
-                        "fell_back": int(sum(i["fell_back"] for i in infos)),
-                        "max_rel_res": float(max(i["rel_res_true"] for i in infos))}
-        out["speedup"] = out["hybrid"]["solves_per_s"] / out["pcg"]["solves_per_s"]
-    net.close()
+    rows = {k: [] for k in ["pcg", *nets]}
+    for i in range(reps):
+        w = I.config3(i)
+        g = api.ppe_create_grid(w.dx, w.dy, w.mask)
+        rhs = torch.tensor(w.f, dtype=torch.float64, device=dev)
+        for key in rows:
+            net = nets.get(key)
+            mode = api.PPE_MODE_PCG if net is None else api.PPE_MODE_HYBRID
+            if net is not None:
+                net.attach(g)
+            x = torch.zeros_like(rhs)
+            api.ppe_solve(g, rhs, x, TOL, mode, api.PPE_PREC_MIXED, net=net)     # warm (graph capture)
+            flush.fill_(1.0)
+            x.zero_()
+            rows[key].append(api.ppe_solve(g, rhs, x, TOL, mode, api.PPE_PREC_MIXED, net=net))
+        g.close()
+    for key, infos in rows.items():
+        ms = float(np.median([i["ms_total"] for i in infos]))
+        out[key] = {"solves_per_s": 1e3 / ms, "ms_median": ms,
+                    "iters_median": float(np.median([i["iters_pcg"] + i["iters_dlsm"] for i in infos])),
+                    "dlsm_steps_median": float(np.median([i["iters_dlsm"] for i in infos])),
+                    "fell_back": int(sum(i["fell_back"] for i in infos)),
+                    "max_rel_res": float(max(i["rel_res_true"] for i in infos))}
+    out["speedup"] = out["hybrid"]["solves_per_s"] / out["pcg"]["solves_per_s"]
+    for net in nets.values():
+        net.close()
     return out
 
 

@@ -1215,6 +1215,11 @@ __device__ void run_pass(S &sm, int q, int ph, int t, Acc &acc)
     }
 }
 
+__device__ __forceinline__ void red_release_add_u32(uint32_t *p, uint32_t v)
+{
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p)
 {
     uint32_t v;
@@ -1260,8 +1265,8 @@ __device__ void block_publish(S &sm, const Acc &acc, Slot *slot, uint32_t *count
             dst[0] = make_float4(h[0], h[1], h[2], h[3]);
             dst[1] = make_float4(h[4], h[5], l[0], l[1]);
             dst[2] = make_float4(l[2], l[3], l[4], l[5]);
-            __threadfence();
-            atomicAdd(counter, 1u);
+            // release: the record's stores are visible before the count is
+            red_release_add_u32(counter, 1u);
         }
     }
 }
@@ -1384,7 +1389,18 @@ __global__ void __launch_bounds__(SOLVER_THREADS, 1)
                     ff_add(h[5], l[5], v1.y, v2.w);
                 };
                 int b = lane;
-                // two records per lane with their loads in flight together
+                // four, then two records per lane with their loads in flight
+                // together (the order of the additions stays l, l + 32, ...)
+                for (; b + 96 < sd.nparts; b += 128) {
+                    float4 v[4][3];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const float4 *sl = reinterpret_cast<const float4 *>(base + b + 32 * u);
+                        v[u][0] = __ldcg(sl); v[u][1] = __ldcg(sl + 1); v[u][2] = __ldcg(sl + 2);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) add_slot(v[u][0], v[u][1], v[u][2]);
+                }
                 for (; b + 32 < sd.nparts; b += 64) {
                     float4 v[2][3];
 #pragma unroll
