@@ -266,6 +266,7 @@ def run_native(args):
     if rank == 0:
         line["hybrid_vs_plain"] = hybrid_vs_plain(api, dev, flush)
         line["batch_vs_sequential"] = batch_vs_sequential(api, dev, flush, peaks)
+        line["sequence_c5"] = sequence_c5(api, dev, flush)
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_oracle_baseline(w)
     if rank == 0:
@@ -310,6 +311,49 @@ def hybrid_vs_plain(api, dev, flush, reps=5):
     out["speedup"] = out["hybrid"]["solves_per_s"] / out["pcg"]["solves_per_s"]
     for net in nets.values():
         net.close()
+    return out
+
+
+def sequence_c5(api, dev, flush, steps=16):
+    """The projection loop's use of the solver on the 2048x1024 wake-refined
+    cylinder grid: one solve per time step to rel-res 1e-8, warm-started from
+    the previous step's solution, plain mixed PCG and the hybrid each on its
+    own chain.  The first `steps` of the 500-step sequence (sources built on
+    the host before timing); solve times are device-timed."""
+    import torch
+    dx, dy, bodies = I.config5_grid()
+    grid = api.ppe_create_grid(dx, dy)
+    srcs = [I.config5_rhs(t, dx, dy, bodies) for t in range(steps)]
+    arms = {"pcg": None}
+    if os.path.exists(WEIGHTS):
+        arms["hybrid"] = api.net_load(WEIGHTS)
+    out = {"workload": f"cyl2048x1024 wake-refined (spacing ratio {I.spacing_ratio(dx, dy):.1f}), "
+                       f"first {steps} of 500 steps, warm starts", "cells": int(dx.size * dy.size)}
+    for key, net in arms.items():
+        if net is not None:
+            net.attach(grid)
+        mode = api.PPE_MODE_PCG if net is None else api.PPE_MODE_HYBRID
+        x = torch.zeros(dy.size, dx.size, dtype=torch.float64, device=dev)
+        rhs = torch.empty_like(x)
+        rhs.copy_(torch.from_numpy(srcs[0]))
+        api.ppe_solve(grid, rhs, torch.zeros_like(x), TOL, mode, api.PPE_PREC_MIXED, net=net)   # warm-up
+        infos = []
+        for f in srcs:
+            rhs.copy_(torch.from_numpy(f))
+            flush.fill_(2.0)
+            infos.append(api.ppe_solve(grid, rhs, x, TOL, mode, api.PPE_PREC_MIXED, net=net))
+        ms = [i["ms_total"] for i in infos]
+        out[key] = {"total_ms": float(sum(ms)), "ms_per_step": float(np.mean(ms)),
+                    "iters_per_step": float(np.mean([i["iters_pcg"] + i["iters_dlsm"] for i in infos])),
+                    "dlsm_steps": int(sum(i["iters_dlsm"] for i in infos)),
+                    "fell_back": int(sum(i["fell_back"] for i in infos)),
+                    "max_rel_res": float(max(i["rel_res_true"] for i in infos)),
+                    "all_ok": bool(all(i["status"] == 0 for i in infos))}
+        if net is not None:
+            net.close()
+    if "hybrid" in out:
+        out["speedup"] = out["pcg"]["total_ms"] / out["hybrid"]["total_ms"]
+    grid.close()
     return out
 
 

@@ -117,6 +117,32 @@ def test_hybrid_budget_falls_back_to_pcg(api, case):
     _check_solution(w, x, xo)
 
 
+@pytest.mark.parametrize("limit", [6, 0])
+def test_stall_limit_hands_useless_directions_to_pcg(api, case, limit):
+    """A fixed random field as the direction barely moves the residual.  With
+    dlsm_stall_limit = 6 the solve gives up on DLSM after such steps and
+    finishes as plain PCG; with 0 it keeps alternating until the iteration
+    budget.  Both reach the plain solution."""
+    w, xo = case
+    grid = api.ppe_create_grid(w.dx, w.dy)
+    api.ppe_set_options(grid, dlsm_stall_limit=limit, hybrid_budget=60)
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    fixed = torch.randn(w.ny, w.nx, generator=gen, device="cuda")
+
+    def same(r, e, stream):
+        e.copy_(fixed)
+
+    api.ppe_set_direction_source(grid, same)
+    x = torch.zeros(w.ny, w.nx, dtype=torch.float64, device="cuda")
+    info = api.ppe_solve(grid, _dev(w.f), x, RES_TOL, api.PPE_MODE_HYBRID, api.PPE_PREC_MIXED)
+    assert info["status"] == 0 and info["fell_back"] == 1
+    if limit:
+        assert limit <= info["iters_dlsm"] <= 2 * limit, info
+    else:
+        assert info["iters_dlsm"] >= 20, info            # 60 iterations of CG^3 DLSM^2 cycles
+    _check_solution(w, x, xo)
+
+
 def test_hybrid_without_source_is_an_error(api, case):
     w, _ = case
     grid = api.ppe_create_grid(w.dx, w.dy)

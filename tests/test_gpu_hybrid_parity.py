@@ -61,7 +61,7 @@ def test_fp64_hybrid_follows_the_oracle(api, case, num_cg, num_dlsm, theta):
         e.copy_((Mg @ r.double().reshape(-1)).reshape(ny, nx).float())
 
     grid = api.ppe_create_grid(dx, dy)
-    api.ppe_set_options(grid, num_cg=num_cg, num_dlsm=num_dlsm)
+    api.ppe_set_options(grid, num_cg=num_cg, num_dlsm=num_dlsm, dlsm_stall_limit=0)   # the oracle has no give-up rule
     api.ppe_set_direction_source(grid, direction)
     x = torch.zeros(ny, nx, dtype=torch.float64, device="cuda")
     info = api.ppe_solve(grid, torch.tensor(S, device="cuda"), x, 1e-8, api.PPE_MODE_HYBRID, api.PPE_PREC_FP64)
