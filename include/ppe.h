@@ -105,11 +105,14 @@ typedef struct {
                                cells shared by a whole CTA; 2 = streaming (each warp marches
                                down a 120-wide strip; for grids far larger than the number of
                                CTAs).  Same arithmetic, same results up to rounding order.     */
-    int32_t dlsm_stall_limit; /* hybrid: continue as plain PCG after this many DLSM steps in a
-                               row that each leave more than 90% of the residual norm
-                               (6; 0 = never).  Not in the paper: a guard against a network
-                               that does not fit the grid.                                    */
-    int32_t reserved[4];
+    int32_t dlsm_stall_limit; /* hybrid: continue as plain PCG after this many unprofitable DLSM
+                               steps in a row (6; 0 = never).  A step is unprofitable when it
+                               removes less of the error's A-norm energy, (r.e)^2 / (e.Ae),
+                               than dlsm_cost_iters iterations of the CG phase before it
+                               remove at their mean (alpha r.u each).  Not in the paper: a
+                               guard against a network that does not pay for its inference. */
+    int32_t dlsm_cost_iters;  /* a DLSM step's cost in CG iterations for that test (16)        */
+    int32_t reserved[3];
 } ppe_solve_opts;
 
 PPE_API void ppe_default_options(ppe_solve_opts *opts);

@@ -38,7 +38,7 @@ class ppe_solve_opts(ctypes.Structure):
                 ("hybrid_budget", ctypes.c_int32), ("inner_rtol", ctypes.c_double), ("dlsm_guard", ctypes.c_double),
                 ("blocks_per_sm", ctypes.c_int32), ("keep_dir_after_dlsm", ctypes.c_int32),
                 ("iter_pass", ctypes.c_int32), ("dlsm_stall_limit", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("dlsm_cost_iters", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class ppe_tune_report(ctypes.Structure):

@@ -161,6 +161,7 @@ void ppe_default_options(ppe_solve_opts *o)
     o->dlsm_guard = 1e-10;
     o->blocks_per_sm = 2;
     o->dlsm_stall_limit = 6;
+    o->dlsm_cost_iters = 16;
 }
 
 void ppe_destroy_grid(ppe_grid *g)
@@ -291,7 +292,8 @@ ppe_status ppe_set_options(ppe_grid *g, const ppe_solve_opts *o)
     if (!g || !o) return arg_error("ppe_set_options: NULL argument");
     if (o->max_iters < 1 || o->num_cg < 1 || o->num_dlsm < 1 || o->hybrid_budget < 0 ||
         !(o->inner_rtol > 0.0 && o->inner_rtol < 1.0) || !(o->dlsm_guard >= 0.0) || o->blocks_per_sm < 0 ||
-        o->iter_pass < 0 || o->iter_pass > 2 || o->dlsm_stall_limit < 0)
+        o->iter_pass < 0 || o->iter_pass > 2 || o->dlsm_stall_limit < 0 ||
+        o->dlsm_cost_iters < 0)
         return arg_error("ppe_set_options: option out of range");
     g->opts = *o;
     return PPE_OK;
@@ -351,6 +353,7 @@ static SysDesc make_desc(const ppe_grid *g, const double *rhs, double *x, double
     sd.hybrid_budget = g->opts.hybrid_budget;
     sd.keep_dir_after_dlsm = g->opts.keep_dir_after_dlsm ? 1 : 0;
     sd.dlsm_stall_limit = g->opts.dlsm_stall_limit;
+    sd.dlsm_cost = g->opts.dlsm_cost_iters;
     sd.tol = tol;
     sd.ru_delta = prec == PPE_PREC_MIXED ? g->opts.inner_rtol : 0.0;
     sd.dlsm_guard = g->opts.dlsm_guard;

@@ -78,7 +78,8 @@ struct SysDesc {
     int32_t max_iters, num_cg, num_dlsm, hybrid_budget;
     int32_t part0, blk0, nparts;          // partial slots part0.. for blocks blk0..blk0+nparts-1
     int32_t keep_dir_after_dlsm;          // 1: CG directions continue across DLSM steps
-    int32_t dlsm_stall_limit;             // DLSM steps in a row that barely reduce r before plain PCG (0: never)
+    int32_t dlsm_stall_limit;             // unprofitable DLSM steps in a row before plain PCG (0: never)
+    int32_t dlsm_cost;                    // a DLSM step's cost in CG iterations (profitability threshold)
     double tol, ru_delta, dlsm_guard, diag_max;
     double n_cells, inv_n;                // nx*ny and its reciprocal
     float n_cells_f, inv_n_f;             // the same in FP32
@@ -104,6 +105,8 @@ struct SysState {
     double alpha_d, xmean, rho, rho_ref;
     float alpha_f, beta_f, mu_f, alpha_d_f;   // FP32 copies for the FP32 passes
     int32_t dlsm_useless, pcur;           // pcur: which p buffer holds the current direction
+    int32_t e_cg_n;                       // CG iterations of the current CG phase
+    float e_cg, e_dlsm;                   // error energy (A-norm^2) they removed; the last DLSM step's
     float gamma_f, target_sq_f, ru_sq_f, rho_f;   // FP32 state of the FP32 iteration's transition
 };
 

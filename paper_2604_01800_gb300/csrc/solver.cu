@@ -1003,6 +1003,8 @@ __device__ void advance(const SysDesc &sd, SysState &s, const double (&t)[NPART]
         s.fold_d = 0;
         s.has_d = 1;
         s.cg_count = 0;
+        s.e_cg = 0.f;
+        s.e_cg_n = 0;
         if (s.rho <= s.target * s.target || !(t[1] > 0.0) || !(t[0] > 0.0)) {
             to_res(s, 0);
             break;
@@ -1030,6 +1032,10 @@ __device__ void advance(const SysDesc &sd, SysState &s, const double (&t)[NPART]
         break;
     }
     case PH_ITER: {
+        // the pass stepped alpha along a direction with r.u = gamma: it removed
+        // alpha gamma of the error's A-norm energy
+        s.e_cg += (float)(s.alpha * s.gamma);
+        s.e_cg_n++;
         s.it_pcg++;
         s.it_total++;
         s.cur ^= 1;
@@ -1076,6 +1082,7 @@ __device__ void advance(const SysDesc &sd, SysState &s, const double (&t)[NPART]
             s.phase = PH_RESTART;
         } else {
             s.alpha_d = a;
+            s.e_dlsm = (float)(a * re);           // (r.e)^2 / (e.Ae): the energy this step removes
             s.phase = PH_DLSM_UPD;
         }
         break;
@@ -1086,11 +1093,12 @@ __device__ void advance(const SysDesc &sd, SysState &s, const double (&t)[NPART]
         s.cur ^= 1;
         s.mu = t[3] * sd.inv_n;
         double rr = t[2] - N * s.mu * s.mu;
-        const double rho_before = s.rho;
         s.rho = rr > 0.0 ? rr : 0.0;
-        // a direction that removes less than 10% of the residual norm is not
-        // worth its inference; after several in a row continue as plain PCG
-        s.dlsm_useless = s.rho > 0.81 * rho_before ? s.dlsm_useless + 1 : 0;
+        // the step is worth its inference if it removed at least as much error
+        // energy as dlsm_cost iterations of the CG phase before it (at their
+        // mean); after several unprofitable steps in a row continue as plain PCG
+        const bool useful = s.e_cg_n == 0 || s.e_dlsm >= (float)sd.dlsm_cost * (s.e_cg / (float)s.e_cg_n);
+        s.dlsm_useless = useful ? 0 : s.dlsm_useless + 1;
         if (sd.dlsm_stall_limit > 0 && s.dlsm_useless >= sd.dlsm_stall_limit) s.fell_back = 1;
         s.dlsm_count++;
         if (sd.mode == PPE_MODE_HYBRID && !s.fell_back && s.it_total >= sd.hybrid_budget) s.fell_back = 1;
@@ -1147,6 +1155,8 @@ __device__ __forceinline__ void ff_mul(float &h, float &l, float b)
 // products) and keeps the FP64 state fields in step for the other phases.
 __device__ void advance_iter_f32(const SysDesc &sd, SysState &s, const float (&h)[NPART], const float (&l)[NPART])
 {
+    s.e_cg += s.alpha_f * s.gamma_f;        // energy removed by the step the pass took (see PH_ITER)
+    s.e_cg_n++;
     s.it_pcg++;
     s.it_total++;
     s.cur ^= 1;
