@@ -26,6 +26,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 from paper_2604_01800_gb300 import inputs as I  # noqa: E402
+from paper_2604_01800_gb300 import shard  # noqa: E402
 
 METRIC = "PPE solves/s at rel-res 1e-8 (512x512 refined-box grid, mixed FP32/FP64 PCG)"
 WEIGHTS = os.path.join(ROOT, "paper_2604_01800_gb300", "weights", "hydea_mconv.ppenet")
@@ -140,20 +141,26 @@ def run_reference(args):
     w = I.config2(0)
     import oracle
     oracle.build()
+    # one full solve gives the iteration count of the workload; each step is
+    # then a bounded sample (a quarter of the iterations, a few seconds on one
+    # host thread), scaled to solves/s by the fraction of a solve it covers
+    _, full, _ = oracle.solve(w.dx, w.dy, w.f, tol_rel=TOL)
+    cap = max(1, full["iters"] // 4)
     for _ in range(args.warmup):
-        oracle.solve(w.dx, w.dy, w.f, tol_rel=TOL)
+        oracle.solve(w.dx, w.dy, w.f, tol_rel=1e-30, maxit=cap)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        x, info, st = oracle.solve(w.dx, w.dy, w.f, tol_rel=TOL)
+        x, info, st = oracle.solve(w.dx, w.dy, w.f, tol_rel=1e-30, maxit=cap)
     dt = time.perf_counter() - t0
-    v = args.steps / dt
+    v = args.steps * (cap / full["iters"]) / dt
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "tol_rel": TOL,
                                              "solver": "CPU FP64 Jacobi PCG (oracle)"},
             "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} full solves, one host thread"},
+                             "sample": f"{args.steps} x {cap} of the {full['iters']} iterations of a full "
+                                       f"solve, one host thread, scaled to solves/s"},
             "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -206,11 +213,7 @@ def run_native(args):
     if world > 1:
         dist.barrier()
     ms = [a.elapsed_time(b) for a, b in ev]
-    t_total = sum(ms) / 1e3
-    if world > 1:
-        t = torch.tensor([t_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_total = float(t.item())
+    t_total = shard.max_over_ranks(sum(ms) / 1e3, dev)
     value = world * args.steps / t_total
     for info in infos:
         assert info["status"] == 0 and info["rel_res_true"] <= TOL, info
@@ -233,9 +236,7 @@ def run_native(args):
     e2e = {"value": world * e2e_steps / e2e_dt if world == 1 else None, "unit": "solves/s",
            "h2d_bytes_per_step": int(h_rhs.numel() * 8), "d2h_bytes_per_step": int(h_x.numel() * 8)}
     if world > 1:
-        t = torch.tensor([e2e_dt], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e["value"] = world * e2e_steps / float(t.item())
+        e2e["value"] = world * e2e_steps / shard.max_over_ranks(e2e_dt, dev)
 
     # ---- roofline of the dominant kernel (the persistent solver kernel)
     peaks, peak_src = _peaks()
@@ -265,7 +266,9 @@ def run_native(args):
         line["stencil_sweep"] = stencil_sweep(api, dev, peaks)
     if rank == 0:
         line["hybrid_vs_plain"] = hybrid_vs_plain(api, dev, flush)
-        line["batch_vs_sequential"] = batch_vs_sequential(api, dev, flush, peaks)
+    batch = batch_vs_sequential(api, dev, flush, peaks, rank, world)      # every rank: its share
+    if rank == 0:
+        line["batch_vs_sequential"] = batch
         line["sequence_c5"] = sequence_c5(api, dev, flush)
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_oracle_baseline(w)
@@ -357,12 +360,16 @@ def sequence_c5(api, dev, flush, steps=16):
     return out
 
 
-def batch_vs_sequential(api, dev, flush, peaks, count=64):
+def batch_vs_sequential(api, dev, flush, peaks, rank=0, world=1, count=64):
     """64 independent systems (n ~ U{128..768}, random stretching, 0-3
     obstacles, masked-divergence sources) in one persistent launch against 64
-    sequential ppe_solve calls; mixed precision, rel-res 1e-8."""
+    sequential ppe_solve calls; mixed precision, rel-res 1e-8.  With several
+    ranks each solves its share (greedy balance on estimated cost) and the
+    slowest rank's time counts."""
     import torch
-    ws = I.config4(count)
+    ws_all = I.config4(count)
+    mine = shard.partition([shard.system_cost(w.nx, w.ny) for w in ws_all], world)[rank]
+    ws = [ws_all[i] for i in mine]
     grids = [api.ppe_create_grid(w.dx, w.dy, w.mask) for w in ws]
     rhs = [torch.tensor(w.f, dtype=torch.float64, device=dev) for w in ws]
     xs = [torch.zeros_like(r) for r in rhs]
@@ -393,16 +400,24 @@ def batch_vs_sequential(api, dev, flush, peaks, count=64):
     batch()
     tb, ib = min((batch() for _ in range(2)), key=lambda t: t[0])
     ts, iseq = sequential()
-    ok = all(i["status"] == 0 and i["rel_res_true"] <= TOL for i in ib)
-    # algorithmic bytes of the batch: 24 B per cell per FP32 iteration, 24 B per FP64 residual pass
-    alg = sum(w.nx * w.ny * 24.0 * (i["iters_pcg"] + i["refinements"]) for w, i in zip(ws, ib))
     for g in grids:
         g.close()
-    return {"systems": count, "cells": cells, "all_converged": ok,
+    # algorithmic bytes of the batch: 24 B per cell per FP32 iteration, 24 B per FP64 residual pass
+    mine_rep = {"ok": all(i["status"] == 0 and i["rel_res_true"] <= TOL for i in ib), "cells": cells,
+                "iters": [i["iters_pcg"] for i in ib],
+                "alg": sum(w.nx * w.ny * 24.0 * (i["iters_pcg"] + i["refinements"]) for w, i in zip(ws, ib))}
+    tb, ts = shard.max_over_ranks(tb, dev), shard.max_over_ranks(ts, dev)
+    reps = shard.gather_to_rank0(mine_rep)
+    if rank != 0:
+        return None
+    iters = [k for r in reps for k in r["iters"]]
+    alg = sum(r["alg"] for r in reps)
+    return {"systems": count, "ranks": world, "cells": sum(r["cells"] for r in reps),
+            "all_converged": all(r["ok"] for r in reps),
             "batch_seconds": tb, "batch_systems_per_s": count / tb,
             "sequential_seconds": ts, "sequential_systems_per_s": count / ts, "speedup": ts / tb,
-            "max_iters": max(i["iters_pcg"] for i in ib), "mean_iters": float(np.mean([i["iters_pcg"] for i in ib])),
-            "effective_gbs": alg / tb / 1e9, "frac_of_hbm": alg / tb / 1e9 / peaks["hbm_gbs"]}
+            "max_iters": max(iters), "mean_iters": float(np.mean(iters)),
+            "effective_gbs": alg / tb / 1e9, "frac_of_hbm": alg / tb / 1e9 / peaks["hbm_gbs"] / world}
 
 
 def stencil_sweep(api, dev, peaks, sizes=(4096, 8192, 16384), short=20, long=120):
