@@ -74,7 +74,7 @@ template <> __device__ __forceinline__ float recip<float>(float v) { return v > 
 template <> __device__ __forceinline__ double recip<double>(double v) { return v > 0.0 ? 1.0 / v : 0.0; }
 
 // Coefficients over the tile window, in the arithmetic type C.
-template <typename C, int TW> struct Coef {
+template <typename C, int TW> struct alignas(16) Coef {
     // the tile-cooperative geometry also keeps the window's Jacobi weights
     // D^-1 (computed once per tile, read every pass); the streaming pass
     // forms them from the 1-D arrays
@@ -488,6 +488,51 @@ __device__ void pass_restart(S &sm, const SysDesc &sd, const SysState &st, int i
 }
 
 // Issue the TMA loads of tile t into stage `fill & 1` (one thread).
+// Four consecutive values (16-byte aligned): one 16-byte access in FP32, two
+// in FP64.
+__device__ __forceinline__ void ld4(const float *p, float (&v)[4])
+{
+    const float4 a = *reinterpret_cast<const float4 *>(p);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+}
+__device__ __forceinline__ void ld4(const double *p, double (&v)[4])
+{
+    const double2 a = reinterpret_cast<const double2 *>(p)[0], b = reinterpret_cast<const double2 *>(p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void st4(float *p, const float (&v)[4])
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4(double *p, const double (&v)[4])
+{
+    reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
+}
+
+// (A U) at the four window points w .. w + 3 of row wj (columns wc .. wc + 3).
+template <typename C, int TW>
+__device__ __forceinline__ void stencil4(const Coef<C, TW> &cf, const C *U, int w, int wc, int wj, C (&out)[4])
+{
+    constexpr int WX = Geo<TW>::WX;
+    C c[4], n[4], sv[4], fe[4], fw[4], dx[4];
+    ld4(U + w, c);
+    ld4(U + w + WX, n);
+    ld4(U + w - WX, sv);
+    ld4(cf.fe + wc, fe);
+    ld4(cf.fw + wc, fw);
+    ld4(cf.dx + wc, dx);
+    const C left = U[w - 1], right = U[w + 4];
+    const C fn = cf.fn[wj], fs = cf.fs[wj], dy = cf.dy[wj];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const C e = k < 3 ? c[k + 1] : right, west = k > 0 ? c[k - 1] : left;
+        const C ax = fe[k] * (c[k] - e) + fw[k] * (c[k] - west);
+        const C ay = fn * (c[k] - n[k]) + fs * (c[k] - sv[k]);
+        out[k] = dy * ax + dx[k] * ay;
+    }
+}
+
 template <typename T, typename S>
 __device__ __forceinline__ void iter_issue_at(S &sm, const SysDesc &sd, int cur, int pcur, bool first, int t,
                                               uint32_t fill)
@@ -541,7 +586,6 @@ __device__ void pass_iter(S &sm, int q, int t_lo, int t_hi, Acc &acc, const Solv
     T *dv = (T *)sd.d;
     const T mu = sc_mu<T>(st), alpha = sc_alpha<T>(st), beta = sc_beta<T>(st);
     const bool first = st.first != 0;
-    const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
     for (int k = 0; k < n; ++k) {
         const int t = t_lo + k;
         const uint32_t fill = fill0 + k;
@@ -555,45 +599,99 @@ __device__ void pass_iter(S &sm, int q, int t_lo, int t_hi, Acc &acc, const Solv
             sm.go = 0;
         }
         __syncthreads();   // coefficients visible
+        // Every stage works on groups of four consecutive cells (16-byte
+        // shared and global accesses); window rows (136), the tile's columns
+        // (from window column 4) and the grid pitch are multiples of four.
+        static_assert(Coef<T, S::TW>::KEEP_DINV && WX % 4 == 0 && OX % 4 == 0 && TILE_X % 4 == 0,
+                      "four-cell groups stay aligned");
+        constexpr int GX = WX / 4, TG = TILE_X / 4;
         // window: r - mu and the new direction p = u + beta p (zero outside the domain)
         T *Rw = stg.r, *Pw = stg.p;
-        for (int w = threadIdx.x; w < WN; w += SOLVER_THREADS) {
-            int wi = w % WX, wj = w / WX;
-            bool in = in_dom(sd, i0 - OX + wi, j0 - OY + wj);
-            T r = in ? Rw[w] - mu : T(0);
-            T u = r * dinv_at<T>(cf, wi, wj);
-            Rw[w] = r;
-            Pw[w] = first ? u : u + beta * Pw[w];
+        for (int g = threadIdx.x; g < G::WY * GX; g += SOLVER_THREADS) {
+            const int wj = g / GX, wc = (g - wj * GX) * 4, w = wj * WX + wc;
+            const int i = i0 - OX + wc;
+            const bool row_in = (unsigned)(j0 - OY + wj) < (unsigned)sd.ny;
+            T r[4], p[4], dinv[4];
+            ld4(Rw + w, r);
+            ld4(Pw + w, p);
+            ld4(cf.dinv + w, dinv);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const bool in = row_in && (unsigned)(i + k) < (unsigned)sd.nx;
+                const T rv = in ? r[k] - mu : T(0);
+                const T u = rv * dinv[k];
+                r[k] = rv;
+                p[k] = first ? u : u + beta * p[k];
+            }
+            st4(Rw + w, r);
+            st4(Pw + w, p);
         }
         __syncthreads();
-        // one-cell ring: q = A p, r' = r - alpha q, u' = D^-1 r'
-        for (int w = threadIdx.x; w < RN; w += SOLVER_THREADS) {
-            int wi, wj;
-            ring_point<S::TW>(w, wi, wj);
-            int kk = wj * WX + wi;
-            T qv = stencil<T>(cf, Pw, wi, wj);
-            T rn = Rw[kk] - alpha * qv;
-            Rw[kk] = rn;
-            Un[kk] = rn * dinv_at<T>(cf, wi, wj);
-            Q[kk] = qv;
+        // one-cell ring: q = A p, r' = r - alpha q, u' = D^-1 r'; the tile's
+        // columns in groups of four, the two edge columns one cell at a time
+        constexpr int NRV = (TILE_N / TILE_X + 2) * TG;
+        for (int g = threadIdx.x; g < NRV + 2 * (TILE_N / TILE_X + 2); g += SOLVER_THREADS) {
+            if (g < NRV) {
+                const int wj = OY - 1 + g / TG, wc = OX + (g % TG) * 4, w = wj * WX + wc;
+                T qv[4], r[4], dinv[4], un[4];
+                stencil4<T>(cf, Pw, w, wc, wj, qv);
+                ld4(Rw + w, r);
+                ld4(cf.dinv + w, dinv);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    r[k] -= alpha * qv[k];
+                    un[k] = r[k] * dinv[k];
+                }
+                st4(Rw + w, r);
+                st4(Un + w, un);
+                st4(Q + w, qv);
+            } else {
+                const int e = g - NRV;
+                const int wj = OY - 1 + (e >> 1), wi = (e & 1) ? OX + TILE_X : OX - 1;
+                const int kk = wj * WX + wi;
+                const T qv = stencil<T>(cf, Pw, wi, wj);
+                const T rn = Rw[kk] - alpha * qv;
+                Rw[kk] = rn;
+                Un[kk] = rn * cf.dinv[kk];
+                Q[kk] = qv;
+            }
         }
         __syncthreads();
         // tile: store p, d, r'; dots r'.u', (A u').u', r'.r', sum r', u'.(A p), p.(A p)
         T tt[NPART] = {0, 0, 0, 0, 0, 0};
-        const int j = j0 + ty, wj = ty + OY;
+        for (int g = threadIdx.x; g < TILE_N / 4; g += SOLVER_THREADS) {
+            const int ty = g / TG, cx = (g - ty * TG) * 4;
+            const int j = j0 + ty, i = i0 + cx;
+            if (j >= sd.ny || i >= sd.nx) continue;
+            const int wj = OY + ty, wc = OX + cx, w = wj * WX + wc;
+            T pn[4], rn[4], un[4], qv[4], dd[4], wn[4];
+            ld4(Pw + w, pn);
+            ld4(Rw + w, rn);
+            ld4(Un + w, un);
+            ld4(Q + w, qv);
+            ld4(stg.d + ty * TILE_X + cx, dd);
+            stencil4<T>(cf, Un, w, wc, wj, wn);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            int i = i0 + tx + 32 * c, wi = tx + 32 * c + OX;
-            if (tx + 32 * c < TILE_X && i < sd.nx && j < sd.ny) {
-                int kk = wj * WX + wi;
-                size_t gi = (size_t)j * sd.pitch + i;
-                T pn = Pw[kk], rn = Rw[kk], un = Un[kk], qv = Q[kk];
-                pout[gi] = pn;
-                dv[gi] = stg.d[ty * TILE_X + tx + 32 * c] + alpha * pn;
-                rout[gi] = rn;
-                T wn = stencil<T>(cf, Un, wi, wj);
-                tt[0] += rn * un; tt[1] += wn * un; tt[2] += rn * rn; tt[3] += rn;
-                tt[4] += un * qv; tt[5] += pn * qv;
+            for (int k = 0; k < 4; ++k) dd[k] += alpha * pn[k];
+            const size_t gi = (size_t)j * sd.pitch + i;
+            if (i + 3 < sd.nx) {
+                st4(pout + gi, pn);
+                st4(dv + gi, dd);
+                st4(rout + gi, rn);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (i + k < sd.nx) {
+                        pout[gi + k] = pn[k];
+                        dv[gi + k] = dd[k];
+                        rout[gi + k] = rn[k];
+                    }
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (i + k >= sd.nx) continue;
+                tt[0] += rn[k] * un[k]; tt[1] += wn[k] * un[k]; tt[2] += rn[k] * rn[k]; tt[3] += rn[k];
+                tt[4] += un[k] * qv[k]; tt[5] += pn[k] * qv[k];
             }
         }
         warp_accumulate(tt, acc);
