@@ -146,6 +146,7 @@ template <typename T, int TW_> struct SmemT {
 // Dynamic shared memory of a block (plus 128 bytes of alignment slack): one
 // block per SM in every variant.
 static_assert(sizeof(SmemT<float, TILE_X>) + 128 <= 227 * 1024, "FP32 solver: one block per SM");
+static_assert(SMAX <= NWARP, "one warp per system of a block in the step's reduction");
 static_assert(sizeof(SmemT<double, TILE_X>) + 128 <= 227 * 1024, "FP64 solver: one block per SM");
 static_assert(sizeof(SmemT<float, TILE_X_STREAM>) + 128 <= 227 * 1024, "streaming solver: one block per SM");
 
@@ -1458,11 +1459,12 @@ __global__ void __launch_bounds__(SOLVER_THREADS, 1)
         }
         if (prof) t_b = gtimer();
         // 2) wait for the records of every block of each live system, reduce,
-        //    advance: all in warp 0 (one block barrier per system and step)
-        for (int q = 0; q < nq; ++q) {
+        //    advance: system q in warp q mod 16, so the systems a block spans
+        //    (at most SMAX) are served at once; one block barrier per step
+        for (int q = warp; q < nq; q += NWARP) {
             const SysDesc &sd = sm.sd[q];
             if (!is_pass_phase(sm.st[q].phase)) continue;
-            if (warp == 0) {
+            {
                 if (lane == 0) {
                     // every block of this system has published step `step`
                     const uint32_t need = step * (uint32_t)sd.nparts;
@@ -1545,9 +1547,9 @@ __global__ void __launch_bounds__(SOLVER_THREADS, 1)
                     if (prof && q == 0) t_x = gtimer();
                 }
             }
-            __syncthreads();
-            if (!sm.go) return;                         // a bounded wait expired: leave without writing state
         }
+        __syncthreads();
+        if (!sm.go) return;                             // a bounded wait expired: leave without writing state
         if (prof) {
             t_c = gtimer();
             if (t_p && t_w && t_r) {
