@@ -94,10 +94,17 @@ template <typename T, int TW> struct Stage {
 static_assert((Geo<TILE_X>::WN_PAD * 4) % 128 == 0 && (Geo<TILE_X>::TN * 4) % 128 == 0,
               "TMA destinations must stay 128-byte aligned");
 
+// The 1-D coefficient arrays of a tile's window as stored in global memory
+// (cell widths, face coefficients; zero outside the grid), staged by cp.async.
+template <typename T, int TW> struct CoefRaw {
+    T dx[Geo<TW>::WX], fx[Geo<TW>::WX + 1], dy[Geo<TW>::WY], fy[Geo<TW>::WY + 1];
+};
+
 template <typename T, int TW> struct IterBufs {
     Stage<T, TW> st[2];
     T un[Geo<TW>::WN_PAD];    // new u on the one-cell ring
     T q[Geo<TW>::WN_PAD];     // A p on the one-cell ring
+    CoefRaw<T, TW> raw[2];    // the next tile's coefficient arrays, in flight during this tile
 };
 
 // Scratch windows of the other passes.
@@ -211,6 +218,90 @@ template <typename T, typename S> __device__ __forceinline__ void load_coef_t(S 
         load_coef_f(sm, sd, i0, j0, tag);
     else
         load_coef_d(sm, sd, i0, j0, tag);
+}
+
+// Asynchronous 4- or 8-byte copy global -> shared; an invalid element is
+// zero-filled without reading global memory (src then points at element 0).
+__device__ __forceinline__ void cp_async_el(float *dst, const float *src, bool valid)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(valid ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_el(double *dst, const double *src, bool valid)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(valid ? 8 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Start copying the coefficient arrays of the tile at (i0, j0) into raw.
+template <typename T, int TW>
+__device__ __forceinline__ void issue_coef_raw(CoefRaw<T, TW> &raw, const SysDesc &sd, int i0, int j0)
+{
+    constexpr int WX = Geo<TW>::WX, WY = Geo<TW>::WY, OX = Geo<TW>::OX, OY = Geo<TW>::OY;
+    const T *DX, *FX, *DY, *FY;
+    if constexpr (sizeof(T) == 4) {
+        DX = sd.dx32; FX = sd.fx32; DY = sd.dy32; FY = sd.fy32;
+    } else {
+        DX = sd.dx; FX = sd.fx; DY = sd.dy; FY = sd.fy;
+    }
+    static_assert(WX + 1 <= 256 && 256 + WY + 1 <= SOLVER_THREADS, "one copy per thread");
+    const int k = threadIdx.x;
+    if (k <= WX) {
+        const int i = i0 - OX + k;
+        if (k < WX) {
+            const bool v = (unsigned)i < (unsigned)sd.nx;
+            cp_async_el(&raw.dx[k], DX + (v ? i : 0), v);
+        }
+        const bool vf = (unsigned)i <= (unsigned)sd.nx;       // faces 0 .. nx
+        cp_async_el(&raw.fx[k], FX + (vf ? i : 0), vf);
+    } else if (k >= 256 && k <= 256 + WY) {
+        const int kk = k - 256, j = j0 - OY + kk;
+        if (kk < WY) {
+            const bool v = (unsigned)j < (unsigned)sd.ny;
+            cp_async_el(&raw.dy[kk], DY + (v ? j : 0), v);
+        }
+        const bool vf = (unsigned)j <= (unsigned)sd.ny;
+        cp_async_el(&raw.fy[kk], FY + (vf ? j : 0), vf);
+    }
+    cp_async_commit();
+}
+
+// The tile's coefficients (and D^-1 window) from staged arrays, as load_coef
+// forms them from global memory; the caller has waited for the copies and
+// synchronised the block.
+template <typename C, int TW>
+__device__ void coef_from_raw(Coef<C, TW> &cf, const CoefRaw<C, TW> &raw, const SysDesc &sd, int i0, int j0)
+{
+    constexpr int WX = Geo<TW>::WX, WY = Geo<TW>::WY, OX = Geo<TW>::OX, OY = Geo<TW>::OY;
+    for (int k = threadIdx.x; k < WX; k += blockDim.x) {
+        const bool in = (unsigned)(i0 - OX + k) < (unsigned)sd.nx;
+        const C a = in ? raw.fx[k] : C(0), b = in ? raw.fx[k + 1] : C(0);
+        cf.dx[k] = raw.dx[k]; cf.fw[k] = a; cf.fe[k] = b; cf.sx[k] = a + b;
+    }
+    for (int k = threadIdx.x; k < WY; k += blockDim.x) {
+        const bool in = (unsigned)(j0 - OY + k) < (unsigned)sd.ny;
+        const C a = in ? raw.fy[k] : C(0), b = in ? raw.fy[k + 1] : C(0);
+        cf.dy[k] = raw.dy[k]; cf.fs[k] = a; cf.fn[k] = b; cf.sy[k] = a + b;
+    }
+    if constexpr (Coef<C, TW>::KEEP_DINV) {
+        __syncthreads();
+        for (int k = threadIdx.x; k < Geo<TW>::WN; k += blockDim.x) {
+            const int wi = k % WX, wj = k / WX;
+            cf.dinv[k] = recip<C>(cf.dy[wj] * cf.sx[wi] + cf.dx[wi] * cf.sy[wj]);
+        }
+    }
+}
+
+template <typename T, typename S> __device__ __forceinline__ void set_coef_tag(S &sm, int tag)
+{
+    if (threadIdx.x == 0) {
+        if constexpr (sizeof(T) == 4)
+            sm.tag_f = tag;
+        else
+            sm.tag_d = tag;
+    }
 }
 
 template <typename C, int TW> __device__ __forceinline__ C dinv_at(const Coef<C, TW> &cf, int wi, int wj)
@@ -536,7 +627,7 @@ __device__ __forceinline__ void stencil4(const Coef<C, TW> &cf, const C *U, int 
 
 template <typename T, typename S>
 __device__ __forceinline__ void iter_issue_at(S &sm, const SysDesc &sd, int cur, int pcur, bool first, int t,
-                                              uint32_t fill)
+                                              uint32_t fill, bool fence)
 {
     using G = Geo<S::TW>;
     constexpr int WX = G::WX, WN = G::WN, OX = G::OX, OY = G::OY, RN = G::RN, NRL = G::NRL, TILE_X = G::TX;
@@ -548,10 +639,11 @@ __device__ __forceinline__ void iter_issue_at(S &sm, const SysDesc &sd, int cur,
     Stage<T, S::TW> &stg = sm.u.it.st[s];
     const uint32_t bar = smem_u32(&sm.bar[s]);
     const uint32_t bytes = (uint32_t)(((first ? 1 : 2) * WN + TILE_N) * sizeof(T));
-    // earlier generic accesses (this block's reads of the stage, and the
-    // grid's writes of the vectors ordered by the step barrier) before the
-    // async-proxy copies
-    fence_proxy_async();
+    // the grid's writes of the vectors (ordered by the step barrier) before
+    // the async-proxy copies: needed once per pass; later tiles of the pass
+    // read the same buffers, which the pass itself does not write (it writes
+    // the other r and p buffers and other tiles' parts of d)
+    if (fence) fence_proxy_async();
     mbar_expect_tx(bar, bytes);
     tma_load_2d(smem_u32(stg.r), sd.tmaps + MAP_R0 + cur, bar, i0 - OX, j0 - OY);
     if (!first) tma_load_2d(smem_u32(stg.p), sd.tmaps + MAP_P0 + pcur, bar, i0 - OX, j0 - OY);
@@ -559,9 +651,10 @@ __device__ __forceinline__ void iter_issue_at(S &sm, const SysDesc &sd, int cur,
 }
 
 template <typename T, typename S>
-__device__ __forceinline__ void iter_issue(S &sm, const SysDesc &sd, const SysState &st, int t, uint32_t fill)
+__device__ __forceinline__ void iter_issue(S &sm, const SysDesc &sd, const SysState &st, int t, uint32_t fill,
+                                           bool fence)
 {
-    iter_issue_at<T>(sm, sd, st.cur, st.pcur, st.first != 0, t, fill);
+    iter_issue_at<T>(sm, sd, st.cur, st.pcur, st.first != 0, t, fill, fence);
 }
 
 // One single-reduction PCG iteration over the tiles [t_lo, t_hi) of system q,
@@ -581,7 +674,7 @@ __device__ void pass_iter(S &sm, int q, int t_lo, int t_hi, Acc &acc, const Solv
     const int n = t_hi - t_lo;
     if (n <= 0) return;
     const uint32_t fill0 = sm.fills;
-    if (threadIdx.x == 0) iter_issue<T>(sm, sd, st, t_lo, fill0);
+    if (threadIdx.x == 0) iter_issue<T>(sm, sd, st, t_lo, fill0, true);
     T *rout = (T *)sd.r[st.cur ^ 1];
     T *pout = (T *)sd.p[st.pcur ^ 1];
     T *dv = (T *)sd.d;
@@ -590,10 +683,23 @@ __device__ void pass_iter(S &sm, int q, int t_lo, int t_hi, Acc &acc, const Solv
     for (int k = 0; k < n; ++k) {
         const int t = t_lo + k;
         const uint32_t fill = fill0 + k;
-        if (threadIdx.x == 0 && k + 1 < n) iter_issue<T>(sm, sd, st, t + 1, fill + 1);
+        if (threadIdx.x == 0 && k + 1 < n) iter_issue<T>(sm, sd, st, t + 1, fill + 1, false);
         int i0, j0;
         tile_origin<S::TW>(sd, t, i0, j0);
-        load_coef_t<T>(sm, sd, i0, j0, t);
+        if (k == 0) {
+            load_coef_t<T>(sm, sd, i0, j0, t);
+        } else {
+            // this tile's arrays were copied while the previous tile was computed
+            cp_async_wait_all();
+            __syncthreads();
+            coef_from_raw<T>(cf, ib.raw[k & 1], sd, i0, j0);
+            set_coef_tag<T>(sm, t);
+        }
+        if (k + 1 < n) {
+            int i1, j1;
+            tile_origin<S::TW>(sd, t + 1, i1, j1);
+            issue_coef_raw<T>(ib.raw[(k + 1) & 1], sd, i1, j1);
+        }
         Stage<T, S::TW> &stg = ib.st[fill & 1];
         if (!mbar_wait_bounded(smem_u32(&sm.bar[fill & 1]), (fill >> 1) & 1, a.spin_limit_ns)) {
             if (threadIdx.x == 0) atomicExch(&a.ctl->err, (int32_t)PPE_ERR_TIMEOUT);
