@@ -585,16 +585,19 @@ static ppe_status drive(int n, ppe_grid *const *grids, SysDesc *sys_dev, SysStat
 }
 
 // Kernel variant of a launch.  FP64 has one; in mixed precision the
-// streaming iteration pass pays off once the grid has a few tiles per block
-// (measured on GB300: 2048 x 1024 = 1024 tiles, 30 us per iteration against
-// 39 us; the tile-cooperative pass has the lower latency on grids of a few
-// hundred tiles).  ppe_autotune measures instead of guessing.
+// streaming iteration pass pays off once the grid has a few tiles per block.
+// Measured on GB300 (per iteration, tile-cooperative / streaming): 896^2 =
+// 392 tiles 18.7 / 21.9 us, 1024^2 = 512 tiles 21.4 / 18.3 us, 2048 x 1024 =
+// 1024 tiles 33.1 / 22.0 us; on grids of a few hundred tiles or fewer the
+// tile-cooperative pass has the lower latency (512^2: 8.1 / 17.3 us).
+// ppe_autotune measures instead of guessing.
+constexpr int STREAM_MIN_TILES = 448;
 static SolverVariant pick_variant(ppe_precision prec, int iter_pass, int ntiles)
 {
     if (prec == PPE_PREC_FP64) return SV_FP64;
     if (iter_pass == 1) return SV_FP32_TILE;
     if (iter_pass == 2) return SV_FP32_STREAM;
-    return ntiles >= 1024 ? SV_FP32_STREAM : SV_FP32_TILE;
+    return ntiles >= STREAM_MIN_TILES ? SV_FP32_STREAM : SV_FP32_TILE;
 }
 
 static ppe_status check_solve_args(ppe_grid *g, const double *rhs, double *x, double tol, ppe_mode mode,

@@ -882,8 +882,13 @@ __device__ __noinline__ void pass_iter_stream(S &sm, int q, int t_lo, int t_hi, 
     StreamBufs &sb = sm.u.sb;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n = t_hi - t_lo;
-    const int c0 = t_lo + (int)((long long)n * warp / NWARP);
-    const int c1 = t_lo + (int)((long long)n * (warp + 1) / NWARP);
+    // The block's tiles are consecutive rows of one strip or a few (a tile is
+    // TILE_Y rows of a strip, tiles are numbered down the strips): split those
+    // rows evenly over the warps, so that a block with fewer tiles than warps
+    // still keeps every warp busy.
+    const int rows_per_col = sd.tiles_y * TILE_Y;
+    const int u_lo = (t_lo - sd.tile0) * TILE_Y, nu = n * TILE_Y;
+    const int u0 = u_lo + (int)((long long)nu * warp / NWARP), u1 = u_lo + (int)((long long)nu * (warp + 1) / NWARP);
     float *rout = (float *)sd.r[st.cur ^ 1];
     float *pout = (float *)sd.p[st.pcur ^ 1];
     float *dv = (float *)sd.d;
@@ -895,14 +900,14 @@ __device__ __noinline__ void pass_iter_stream(S &sm, int q, int t_lo, int t_hi, 
     uint32_t gnext = sm.sfills[warp];      // global index of this warp's next chunk
     bool ok = true;
 
-    for (int t = c0; t < c1;) {
-        // the run of tiles t .. t_end - 1 in one tile column
-        const int lt = t - sd.tile0;
-        const int col = lt / sd.tiles_y, trow = lt % sd.tiles_y;
-        const int t_end = min(c1, t + (sd.tiles_y - trow));
+    for (int u = u0; u < u1;) {
+        // the run of rows u .. u_end - 1 in one strip
+        const int col = u / rows_per_col, r = u - col * rows_per_col;
+        const int u_end = min(u1, u - r + rows_per_col);
         const int i0 = col * TILE_X_STREAM;
-        const int jb = trow * TILE_Y, je = min(sd.ny, (trow + (t_end - t)) * TILE_Y);
-        t = t_end;
+        const int jb = r, je = min(sd.ny, r + (u_end - u));
+        u = u_end;
+        if (jb >= je) continue;                    // rows of the strip's last tile below the grid
         const int nchunks = (je - jb + 4 + SRB - 1) / SRB;
         const uint32_t gb = gnext;
         gnext += nchunks;
