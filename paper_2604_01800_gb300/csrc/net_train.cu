@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(256) wgrad_kernel(const bf16 *__restrict__ dZ,
                                                     int tiles_per_block)
 {
     __shared__ float dzs[WG_P][33];
-    __shared__ float xs[(WG_H + 2) * (WG_W + 2)][32];
+    __shared__ __align__(16) float xs[(WG_H + 2) * (WG_W + 2)][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int co0 = blockIdx.x * 32, ci0 = blockIdx.y * 32;
     const int tw = (W + WG_W - 1) / WG_W, th = (H + WG_H - 1) / WG_H;
@@ -162,9 +162,12 @@ __global__ void __launch_bounds__(256) wgrad_kernel(const bf16 *__restrict__ dZ,
             int py = p / WG_W, px = p % WG_W;
 #pragma unroll
             for (int t = 0; t < 9; ++t) {
-                const float *xr = xs[(py + t / 3) * (WG_W + 2) + px + t % 3];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[j][t] = fmaf(d, xr[warp * 4 + j], acc[j][t]);
+                // the warp's four input channels in one 16-byte (broadcast) load
+                const float4 xv = *reinterpret_cast<const float4 *>(&xs[(py + t / 3) * (WG_W + 2) + px + t % 3][warp * 4]);
+                acc[0][t] = fmaf(d, xv.x, acc[0][t]);
+                acc[1][t] = fmaf(d, xv.y, acc[1][t]);
+                acc[2][t] = fmaf(d, xv.z, acc[2][t]);
+                acc[3][t] = fmaf(d, xv.w, acc[3][t]);
             }
         }
     }
