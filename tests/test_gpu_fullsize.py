@@ -1,0 +1,73 @@
+"""Full-size cases, in the launch configuration the bench times.
+
+At these sizes the oracle's full solve would take minutes, so the GPU's
+answers are checked through properties that hold at any size, evaluated by
+the oracle in FP64: the true relative residual ||P(b - A x)|| / ||P b|| at
+most the tolerance (5% slack for the evaluation's own rounding), and a zero
+volume-weighted mean.  A sample of the smallest systems is also compared
+with the oracle's own solution.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from paper_2604_01800_gb300 import inputs as I  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-8
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_01800_gb300 import api as A
+    return A
+
+
+def _dev(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def _check_properties(dx, dy, f, xg):
+    assert oracle.true_relres(dx, dy, f, xg) <= TOL * 1.05
+    V = np.outer(dy, dx)
+    assert abs((V * xg).sum()) <= 1e-10 * (V * np.abs(xg)).sum()
+
+
+def test_config5_2048x1024_warm_started_steps(api):
+    """Two steps of the projection loop on the wake-refined 2048 x 1024 grid
+    (streaming pass), the second warm-started from the first."""
+    dx, dy, bodies = I.config5_grid()
+    grid = api.ppe_create_grid(dx, dy)
+    x = torch.zeros(dy.size, dx.size, dtype=torch.float64, device="cuda")
+    for t in range(2):
+        f = I.config5_rhs(t, dx, dy, bodies)
+        info = api.ppe_solve(grid, _dev(f), x, TOL, api.PPE_MODE_PCG, api.PPE_PREC_MIXED)
+        assert info["status"] == 0, info
+        _check_properties(dx, dy, f, x.cpu().numpy())
+    grid.close()
+
+
+def test_config4_batch_of_64(api):
+    """The 64 uneven systems (128^2 - 768^2, obstacles) in one batched
+    persistent solve, as the bench runs them."""
+    ws = I.config4(64)
+    grids = [api.ppe_create_grid(w.dx, w.dy, w.mask) for w in ws]
+    rhs = [_dev(w.f) for w in ws]
+    xs = [torch.zeros_like(r) for r in rhs]
+    infos, st = api.ppe_solve_batch(grids, rhs, xs, TOL, api.PPE_MODE_PCG, api.PPE_PREC_MIXED)
+    assert st == 0
+    for w, x, info in zip(ws, xs, infos):
+        assert info["status"] == 0, (w.name, info)
+        _check_properties(w.dx, w.dy, w.f, x.cpu().numpy())
+    # the three smallest systems against the oracle's solution
+    for k in sorted(range(64), key=lambda i: ws[i].nx * ws[i].ny)[:3]:
+        w = ws[k]
+        xo, _, _ = oracle.solve(w.dx, w.dy, w.f, tol_rel=1e-11)
+        xg = xs[k].cpu().numpy()
+        assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-6, w.name
+    for g in grids:
+        g.close()
