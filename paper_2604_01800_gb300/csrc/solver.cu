@@ -32,7 +32,9 @@
 // The iteration pass streams a block's tiles through two shared-memory
 // stages: while one tile is computed, the TMA unit loads the next tile's r
 // and p windows and its d tile (zero-filled outside the grid, which is the
-// Neumann stencil's zero padding).
+// Neumann stencil's zero padding), and cp.async brings the next tile's 1-D
+// coefficient arrays.  For grids far larger than the block count a streaming
+// variant has each warp march down rows of 120-wide strips instead.
 //
 // Mixed precision: the FP32 recursive residual is replaced by the FP64 true
 // residual b - A(x + d) whenever it has dropped by a factor ru_delta since
