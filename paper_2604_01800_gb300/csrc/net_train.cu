@@ -119,13 +119,32 @@ __global__ void act_bwd_kernel(const float *__restrict__ dY, const bf16 *__restr
 }
 
 // dW[co][ci][tap] += sum_p dZ[p][co] * X[p + tap][ci]  (X: the layer's eta-weighted input)
-constexpr int WG_H = 8, WG_W = 16, WG_P = WG_H * WG_W;
+//
+// A block forms a 32 Cout x 32 Cin x 9-tap slab over its share of 8 x 16
+// pixel tiles.  The next tile's raw BF16 rows of dZ and X (16-byte pieces,
+// zero-filled outside the image) are copied by cp.async while the current
+// tile is computed, then widened to FP32 in shared memory.  Needs Cin and
+// Cout multiples of 8.
+constexpr int WG_H = 8, WG_W = 16, WG_P = WG_H * WG_W, WG_XP = (WG_H + 2) * (WG_W + 2);
+constexpr size_t WG_SMEM = sizeof(float) * WG_P * 33 + sizeof(float) * WG_XP * 32 + sizeof(bf16) * (WG_P + WG_XP) * 32;
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, bool valid)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+
 __global__ void __launch_bounds__(256) wgrad_kernel(const bf16 *__restrict__ dZ, const bf16 *__restrict__ X, int B,
                                                     int H, int W, int cin, int cout, float *__restrict__ dW,
                                                     int tiles_per_block)
 {
-    __shared__ float dzs[WG_P][33];
-    __shared__ __align__(16) float xs[(WG_H + 2) * (WG_W + 2)][32];
+    extern __shared__ __align__(16) unsigned char wg_smem[];
+    float(*xs)[32] = reinterpret_cast<float(*)[32]>(wg_smem);                                   // [WG_XP][32]
+    bf16(*xr)[32] = reinterpret_cast<bf16(*)[32]>(wg_smem + sizeof(float) * WG_XP * 32);      // [WG_XP][32]
+    bf16(*dzr)[32] = reinterpret_cast<bf16(*)[32]>(wg_smem + sizeof(float) * WG_XP * 32 + sizeof(bf16) * WG_XP * 32);
+    float(*dzs)[33] = reinterpret_cast<float(*)[33]>(wg_smem + sizeof(float) * WG_XP * 32 +
+                                                     sizeof(bf16) * (WG_XP + WG_P) * 32);       // [WG_P][33]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int co0 = blockIdx.x * 32, ci0 = blockIdx.y * 32;
     const int tw = (W + WG_W - 1) / WG_W, th = (H + WG_H - 1) / WG_H;
@@ -137,26 +156,46 @@ __global__ void __launch_bounds__(256) wgrad_kernel(const bf16 *__restrict__ dZ,
         for (int t = 0; t < 9; ++t) acc[j][t] = 0.f;
     const long t0 = (long)blockIdx.z * tiles_per_block;
     const long t1 = min(total, t0 + tiles_per_block);
+    auto issue = [&](long tile) {
+        const int b = tile / (tw * th), r = tile % (tw * th);
+        const int y0 = (r / tw) * WG_H, x0 = (r % tw) * WG_W;
+        for (int k = threadIdx.x; k < WG_P * 4; k += 256) {
+            const int q = k & 3, p = k >> 2;
+            const int y = y0 + p / WG_W, x = x0 + p % WG_W;
+            const bool v = y < H && x < W && co0 + 8 * q < cout;
+            cp_async16(&dzr[p][8 * q], v ? dZ + (((size_t)b * H + y) * W + x) * cout + co0 + 8 * q : dZ, v);
+        }
+        for (int k = threadIdx.x; k < WG_XP * 4; k += 256) {
+            const int q = k & 3, p = k >> 2;
+            const int y = y0 - 1 + p / (WG_W + 2), x = x0 - 1 + p % (WG_W + 2);
+            const bool v = y >= 0 && y < H && x >= 0 && x < W && ci0 + 8 * q < cin;
+            cp_async16(&xr[p][8 * q], v ? X + (((size_t)b * H + y) * W + x) * cin + ci0 + 8 * q : X, v);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    if (t0 < t1) issue(t0);
     for (long tile = t0; tile < t1; ++tile) {
-        int b = tile / (tw * th), r = tile % (tw * th);
-        int y0 = (r / tw) * WG_H, x0 = (r % tw) * WG_W;
-        __syncthreads();
-        for (int k = threadIdx.x; k < WG_P * 32; k += 256) {
-            int c = k % 32, p = k / 32;
-            int y = y0 + p / WG_W, x = x0 + p % WG_W;
-            float v = 0.f;
-            if (y < H && x < W && co0 + c < cout) v = __bfloat162float(dZ[(((size_t)b * H + y) * W + x) * cout + co0 + c]);
-            dzs[p][c] = v;
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        __syncthreads();          // this tile's rows from every thread; the previous tile's products done
+        for (int k = threadIdx.x; k < WG_P * 4; k += 256) {
+            const int q = k & 3, p = k >> 2;
+            const uint4 raw = *reinterpret_cast<const uint4 *>(&dzr[p][8 * q]);
+            const bf16 *h = reinterpret_cast<const bf16 *>(&raw);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) dzs[p][8 * q + i] = __bfloat162float(h[i]);
         }
-        for (int k = threadIdx.x; k < (WG_H + 2) * (WG_W + 2) * 32; k += 256) {
-            int c = k % 32, p = k / 32;
-            int y = y0 - 1 + p / (WG_W + 2), x = x0 - 1 + p % (WG_W + 2);
-            float v = 0.f;
-            if (y >= 0 && y < H && x >= 0 && x < W && ci0 + c < cin)
-                v = __bfloat162float(X[(((size_t)b * H + y) * W + x) * cin + ci0 + c]);
-            xs[p][c] = v;
+        for (int k = threadIdx.x; k < WG_XP * 4; k += 256) {
+            const int q = k & 3, p = k >> 2;
+            const uint4 raw = *reinterpret_cast<const uint4 *>(&xr[p][8 * q]);
+            const bf16 *h = reinterpret_cast<const bf16 *>(&raw);
+            float4 *dst = reinterpret_cast<float4 *>(&xs[p][8 * q]);
+            dst[0] = make_float4(__bfloat162float(h[0]), __bfloat162float(h[1]), __bfloat162float(h[2]),
+                                 __bfloat162float(h[3]));
+            dst[1] = make_float4(__bfloat162float(h[4]), __bfloat162float(h[5]), __bfloat162float(h[6]),
+                                 __bfloat162float(h[7]));
         }
-        __syncthreads();
+        __syncthreads();          // widened tiles visible; the raw buffers are free
+        if (tile + 1 < t1) issue(tile + 1);
         for (int p = 0; p < WG_P; ++p) {
             float d = dzs[p][lane];
             int py = p / WG_W, px = p % WG_W;
@@ -501,7 +540,16 @@ static ppe_status conv_backward(ppe_net *n, NetCache *c, TrainWs *w, int li, con
         int split = std::max(1, std::min(tiles, 592 / std::max(1, blocks_xy)));
         int per = (tiles + split - 1) / split;
         grid.z = (tiles + per - 1) / per;
-        wgrad_kernel<<<grid, 256, 0, s>>>(w->dZ, Xb, B, H, W, l.cin, l.cout, grads + l.off_w, per);
+        if (l.cin % 8 || l.cout % 8) {
+            set_error("weight gradient: channel counts must be multiples of 8");
+            return PPE_ERR_ARG;
+        }
+        static bool attr_set = false;
+        if (!attr_set) {
+            PPE_CUDA_TRY(cudaFuncSetAttribute(wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WG_SMEM));
+            attr_set = true;
+        }
+        wgrad_kernel<<<grid, 256, WG_SMEM, s>>>(w->dZ, Xb, B, H, W, l.cin, l.cout, grads + l.off_w, per);
     }
     // data gradient: forward convolution of dZ with the transposed, flipped kernel
     ConvArgs a;
