@@ -120,13 +120,18 @@ __global__ void act_bwd_kernel(const float *__restrict__ dY, const bf16 *__restr
 
 // dW[co][ci][tap] += sum_p dZ[p][co] * X[p + tap][ci]  (X: the layer's eta-weighted input)
 //
-// A block forms a 32 Cout x 32 Cin x 9-tap slab over its share of 8 x 16
-// pixel tiles.  The next tile's raw BF16 rows of dZ and X (16-byte pieces,
-// zero-filled outside the image) are copied by cp.async while the current
-// tile is computed, then widened to FP32 in shared memory.  Needs Cin and
-// Cout multiples of 8.
+// A block forms a (32 NCO) Cout x 32 Cin x 9-tap slab over its share of
+// 8 x 16 pixel tiles; a thread owns NCO output channels (lane, lane + 32, ...)
+// and four input channels, so every input value it loads feeds 9 NCO
+// products per tap group.  The next tile's raw BF16 rows of dZ and X (16-byte
+// pieces, zero-filled outside the image) are copied by cp.async while the
+// current tile is computed, then widened to FP32 in shared memory.  Needs Cin
+// and Cout multiples of 8.
 constexpr int WG_H = 8, WG_W = 16, WG_P = WG_H * WG_W, WG_XP = (WG_H + 2) * (WG_W + 2);
-constexpr size_t WG_SMEM = sizeof(float) * WG_P * 33 + sizeof(float) * WG_XP * 32 + sizeof(bf16) * (WG_P + WG_XP) * 32;
+template <int NCO> constexpr size_t wg_smem()
+{
+    return sizeof(float) * WG_P * (32 * NCO + 1) + sizeof(float) * WG_XP * 32 + sizeof(bf16) * (WG_P * 32 * NCO + WG_XP * 32);
+}
 
 __device__ __forceinline__ void cp_async16(void *dst, const void *src, bool valid)
 {
@@ -135,32 +140,36 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src, bool vali
                  : "memory");
 }
 
+template <int NCO>
 __global__ void __launch_bounds__(256) wgrad_kernel(const bf16 *__restrict__ dZ, const bf16 *__restrict__ X, int B,
                                                     int H, int W, int cin, int cout, float *__restrict__ dW,
                                                     int tiles_per_block)
 {
+    constexpr int NC = 32 * NCO;           // output channels of the block
     extern __shared__ __align__(16) unsigned char wg_smem[];
     float(*xs)[32] = reinterpret_cast<float(*)[32]>(wg_smem);                                   // [WG_XP][32]
     bf16(*xr)[32] = reinterpret_cast<bf16(*)[32]>(wg_smem + sizeof(float) * WG_XP * 32);      // [WG_XP][32]
-    bf16(*dzr)[32] = reinterpret_cast<bf16(*)[32]>(wg_smem + sizeof(float) * WG_XP * 32 + sizeof(bf16) * WG_XP * 32);
-    float(*dzs)[33] = reinterpret_cast<float(*)[33]>(wg_smem + sizeof(float) * WG_XP * 32 +
-                                                     sizeof(bf16) * (WG_XP + WG_P) * 32);       // [WG_P][33]
+    bf16(*dzr)[NC] = reinterpret_cast<bf16(*)[NC]>(wg_smem + sizeof(float) * WG_XP * 32 + sizeof(bf16) * WG_XP * 32);
+    float(*dzs)[NC + 1] = reinterpret_cast<float(*)[NC + 1]>(wg_smem + sizeof(float) * WG_XP * 32 +
+                                                             sizeof(bf16) * (WG_XP * 32 + WG_P * NC));   // [WG_P][NC+1]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int co0 = blockIdx.x * 32, ci0 = blockIdx.y * 32;
+    const int co0 = blockIdx.x * NC, ci0 = blockIdx.y * 32;
     const int tw = (W + WG_W - 1) / WG_W, th = (H + WG_H - 1) / WG_H;
     const long total = (long)B * tw * th;
-    float acc[4][9];
+    float acc[NCO][4][9];
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
+    for (int u = 0; u < NCO; ++u)
 #pragma unroll
-        for (int t = 0; t < 9; ++t) acc[j][t] = 0.f;
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int t = 0; t < 9; ++t) acc[u][j][t] = 0.f;
     const long t0 = (long)blockIdx.z * tiles_per_block;
     const long t1 = min(total, t0 + tiles_per_block);
     auto issue = [&](long tile) {
         const int b = tile / (tw * th), r = tile % (tw * th);
         const int y0 = (r / tw) * WG_H, x0 = (r % tw) * WG_W;
-        for (int k = threadIdx.x; k < WG_P * 4; k += 256) {
-            const int q = k & 3, p = k >> 2;
+        for (int k = threadIdx.x; k < WG_P * 4 * NCO; k += 256) {
+            const int q = k % (4 * NCO), p = k / (4 * NCO);
             const int y = y0 + p / WG_W, x = x0 + p % WG_W;
             const bool v = y < H && x < W && co0 + 8 * q < cout;
             cp_async16(&dzr[p][8 * q], v ? dZ + (((size_t)b * H + y) * W + x) * cout + co0 + 8 * q : dZ, v);
@@ -177,8 +186,8 @@ __global__ void __launch_bounds__(256) wgrad_kernel(const bf16 *__restrict__ dZ,
     for (long tile = t0; tile < t1; ++tile) {
         asm volatile("cp.async.wait_all;" ::: "memory");
         __syncthreads();          // this tile's rows from every thread; the previous tile's products done
-        for (int k = threadIdx.x; k < WG_P * 4; k += 256) {
-            const int q = k & 3, p = k >> 2;
+        for (int k = threadIdx.x; k < WG_P * 4 * NCO; k += 256) {
+            const int q = k % (4 * NCO), p = k / (4 * NCO);
             const uint4 raw = *reinterpret_cast<const uint4 *>(&dzr[p][8 * q]);
             const bf16 *h = reinterpret_cast<const bf16 *>(&raw);
 #pragma unroll
@@ -197,27 +206,35 @@ __global__ void __launch_bounds__(256) wgrad_kernel(const bf16 *__restrict__ dZ,
         __syncthreads();          // widened tiles visible; the raw buffers are free
         if (tile + 1 < t1) issue(tile + 1);
         for (int p = 0; p < WG_P; ++p) {
-            float d = dzs[p][lane];
+            float d[NCO];
+#pragma unroll
+            for (int u = 0; u < NCO; ++u) d[u] = dzs[p][lane + 32 * u];
             int py = p / WG_W, px = p % WG_W;
 #pragma unroll
             for (int t = 0; t < 9; ++t) {
                 // the warp's four input channels in one 16-byte (broadcast) load
                 const float4 xv = *reinterpret_cast<const float4 *>(&xs[(py + t / 3) * (WG_W + 2) + px + t % 3][warp * 4]);
-                acc[0][t] = fmaf(d, xv.x, acc[0][t]);
-                acc[1][t] = fmaf(d, xv.y, acc[1][t]);
-                acc[2][t] = fmaf(d, xv.z, acc[2][t]);
-                acc[3][t] = fmaf(d, xv.w, acc[3][t]);
+#pragma unroll
+                for (int u = 0; u < NCO; ++u) {
+                    acc[u][0][t] = fmaf(d[u], xv.x, acc[u][0][t]);
+                    acc[u][1][t] = fmaf(d[u], xv.y, acc[u][1][t]);
+                    acc[u][2][t] = fmaf(d[u], xv.z, acc[u][2][t]);
+                    acc[u][3][t] = fmaf(d[u], xv.w, acc[u][3][t]);
+                }
             }
         }
     }
-    int co = co0 + lane;
-    if (co >= cout) return;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        int ci = ci0 + warp * 4 + j;
-        if (ci >= cin) continue;
+    for (int u = 0; u < NCO; ++u) {
+        const int co = co0 + lane + 32 * u;
+        if (co >= cout) continue;
 #pragma unroll
-        for (int t = 0; t < 9; ++t) atomicAdd(&dW[((size_t)co * cin + ci) * 9 + t], acc[j][t]);
+        for (int j = 0; j < 4; ++j) {
+            const int ci = ci0 + warp * 4 + j;
+            if (ci >= cin) continue;
+#pragma unroll
+            for (int t = 0; t < 9; ++t) atomicAdd(&dW[((size_t)co * cin + ci) * 9 + t], acc[u][j][t]);
+        }
     }
 }
 
@@ -534,22 +551,31 @@ static ppe_status conv_backward(ppe_net *n, NetCache *c, TrainWs *w, int li, con
     act_bwd_kernel<<<g1d(px * l.cout), 256, 0, s>>>(dY, Z, w->dZ, px * l.cout, l.cout, grads + l.off_b);
     // weight gradient
     {
-        const int tiles = B * ((W + WG_W - 1) / WG_W) * ((H + WG_H - 1) / WG_H);
-        dim3 grid((l.cout + 31) / 32, (l.cin + 31) / 32, 1);
-        int blocks_xy = grid.x * grid.y;
-        int split = std::max(1, std::min(tiles, 592 / std::max(1, blocks_xy)));
-        int per = (tiles + split - 1) / split;
-        grid.z = (tiles + per - 1) / per;
         if (l.cin % 8 || l.cout % 8) {
             set_error("weight gradient: channel counts must be multiples of 8");
             return PPE_ERR_ARG;
         }
+        // two output channels per thread from 64 on (each loaded input value
+        // then feeds twice the products); one below
+        const int nco = l.cout >= 64 ? 2 : 1;
+        const int tiles = B * ((W + WG_W - 1) / WG_W) * ((H + WG_H - 1) / WG_H);
+        dim3 grid((l.cout + 32 * nco - 1) / (32 * nco), (l.cin + 31) / 32, 1);
+        int blocks_xy = grid.x * grid.y;
+        int split = std::max(1, std::min(tiles, 592 / std::max(1, blocks_xy)));
+        int per = (tiles + split - 1) / split;
+        grid.z = (tiles + per - 1) / per;
         static bool attr_set = false;
         if (!attr_set) {
-            PPE_CUDA_TRY(cudaFuncSetAttribute(wgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WG_SMEM));
+            PPE_CUDA_TRY(cudaFuncSetAttribute(wgrad_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)wg_smem<1>()));
+            PPE_CUDA_TRY(cudaFuncSetAttribute(wgrad_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)wg_smem<2>()));
             attr_set = true;
         }
-        wgrad_kernel<<<grid, 256, WG_SMEM, s>>>(w->dZ, Xb, B, H, W, l.cin, l.cout, grads + l.off_w, per);
+        if (nco == 2)
+            wgrad_kernel<2><<<grid, 256, wg_smem<2>(), s>>>(w->dZ, Xb, B, H, W, l.cin, l.cout, grads + l.off_w, per);
+        else
+            wgrad_kernel<1><<<grid, 256, wg_smem<1>(), s>>>(w->dZ, Xb, B, H, W, l.cin, l.cout, grads + l.off_w, per);
     }
     // data gradient: forward convolution of dZ with the transposed, flipped kernel
     ConvArgs a;
