@@ -1,20 +1,29 @@
 """Benchmark of the PPE hot path on GB300.
 
-One step = one complete PPE solve to relative residual 1e-8 of the 512x512
-refined-box workload (refined box [0.4, 0.6]^2, geometric growth 1.05,
-random-Fourier source with 1/|k|^2 amplitudes up to |k| = 32), inputs
-resident in HBM.  Prints one JSON line (rank 0).
+The metric: PPE solves per second to relative residual 1e-8, the hybrid
+solver (Jacobi PCG alternating with DLSM steps whose directions come from the
+grid-spacing-aware DeepONet, Sec. 2.2) against plain PCG, on the 256x256 grid
+refined around an immersed cylinder (masked-divergence sources), in mixed
+precision (FP32 inner iterations, FP64 refinement, BF16 network).  One step
+= one complete hybrid solve of one source (every step of the hot path: RHS
+preparation, refinement, PCG iterations, network inference, DLSM updates,
+finalisation), inputs resident in HBM, L2 flushed between steps.  The plain
+PCG arm is timed the same way on the same sources.  Prints one JSON line
+(rank 0) with the other workloads as extra keys: the 64^2 FP64 system, the
+512^2 refined-box system, a stencil sweep far above L2, the 64-system batch
+(plain and hybrid) and the first steps of the 2048x1024 time sequence.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
 ``--impl reference`` times the FP64 CPU oracle (Jacobi PCG on the assembled
-CSR matrix) on the host cores for the same workload and metric.
+CSR matrix, all host cores) on the same workload and metric.
 """
 from __future__ import annotations
 
 import argparse
 import json
 import os
+import platform
 import subprocess
 import sys
 import threading
@@ -28,13 +37,11 @@ sys.path.insert(0, ROOT)
 from paper_2604_01800_gb300 import inputs as I  # noqa: E402
 from paper_2604_01800_gb300 import shard  # noqa: E402
 
-METRIC = "PPE solves/s at rel-res 1e-8 (512x512 refined-box grid, mixed FP32/FP64 PCG)"
+METRIC = "PPE solves/s at rel-res 1e-8: hybrid vs plain PCG, 1 GB300; stencil HBM GB/s"
 WEIGHTS = os.path.join(ROOT, "paper_2604_01800_gb300", "weights", "hydea_mconv.ppenet")
-# DRAM bytes of one launch of the solver kernel on the 512x512 workload (one
-# whole mixed-precision solve), from an ncu capture of the current kernel
-SOLVER_C2_DRAM_BYTES = 4.397312e6 + 0.122624e6
 TOL = 1e-8
 L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2
+SOURCES = 5                         # distinct sources of the headline workload, cycled over the steps
 
 
 def _args():
@@ -45,6 +52,7 @@ def _args():
     p.add_argument("--impl", default="native", choices=["native", "reference"])
     p.add_argument("--no-sweep", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-extras", action="store_true")
     return p.parse_args()
 
 
@@ -117,52 +125,127 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def cpu_oracle_baseline(w, max_seconds=30.0, min_solves=1):
-    """Time the FP64 CPU oracle on the host (single thread) on whole solves."""
+def _cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.processor() or platform.machine()
+
+
+def _time_oracle_solves(ws, openmp, reps):
+    """Median seconds of `reps` whole oracle solves (sources cycled)."""
+    import oracle
+    times, iters = [], []
+    for k in range(reps):
+        w = ws[k % len(ws)]
+        t0 = time.perf_counter()
+        _, info, st = oracle.solve(w.dx, w.dy, w.f, tol_rel=TOL, openmp=openmp)
+        times.append(time.perf_counter() - t0)
+        iters.append(info["iters"])
+        assert st == 0 and info["rel_res_true"] <= TOL
+    return float(np.median(times)), float(np.median(iters))
+
+
+def cpu_oracle_baseline(ws, reps=5):
+    """The FP64 CPU oracle (CSR Jacobi PCG) on the headline workload: whole
+    solves, median of `reps`, on every host core (OpenMP build) and on one
+    thread (the build the tests use)."""
     import oracle
     oracle.build()
-    times = []
-    t_start = time.perf_counter()
-    while len(times) < min_solves or (time.perf_counter() - t_start < max_seconds * 0.5 and len(times) < 3):
-        t0 = time.perf_counter()
-        x, info, st = oracle.solve(w.dx, w.dy, w.f, tol_rel=TOL)
-        times.append(time.perf_counter() - t0)
-        if time.perf_counter() - t_start > max_seconds:
-            break
-    return {"value": 1.0 / float(np.median(times)), "unit": "solves/s", "cores": 1, "kind": "oracle",
-            "sample": f"{len(times)} full solve(s) of the {w.nx}x{w.ny} workload to rel-res 1e-8, "
-                      f"FP64 CSR Jacobi PCG, one host thread", "iters": info["iters"]}
+    oracle.build(openmp=True)
+    cores = os.cpu_count() or 1
+    t_all, it = _time_oracle_solves(ws, True, reps)
+    t_one, _ = _time_oracle_solves(ws, False, reps)
+    return {"value": 1.0 / t_all, "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample": f"median of {reps} whole solves of the {ws[0].nx}x{ws[0].ny} workload ({len(ws)} sources "
+                      f"cycled) to rel-res 1e-8, FP64 CSR Jacobi PCG, OpenMP on {cores} host threads",
+            "iters": it, "cpu_model": _cpu_model(), "hardware_concurrency": cores,
+            "single_thread": {"value": 1.0 / t_one, "unit": "solves/s", "cores": 1}}
 
 
 def run_reference(args):
     rank, world, _ = _dist()
     if rank != 0:
         return
-    w = I.config2(0)
+    ws = [I.config3(i) for i in range(SOURCES)]
     import oracle
-    oracle.build()
-    # one full solve gives the iteration count of the workload; each step is
-    # then a bounded sample (a quarter of the iterations, a few seconds on one
-    # host thread), scaled to solves/s by the fraction of a solve it covers
-    _, full, _ = oracle.solve(w.dx, w.dy, w.f, tol_rel=TOL)
-    cap = max(1, full["iters"] // 4)
-    for _ in range(args.warmup):
-        oracle.solve(w.dx, w.dy, w.f, tol_rel=1e-30, maxit=cap)
+    oracle.build(openmp=True)
+    cores = os.cpu_count() or 1
+    for k in range(args.warmup):
+        w = ws[k % SOURCES]
+        oracle.solve(w.dx, w.dy, w.f, tol_rel=TOL, openmp=True)
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        x, info, st = oracle.solve(w.dx, w.dy, w.f, tol_rel=1e-30, maxit=cap)
+    iters = []
+    for k in range(args.steps):
+        w = ws[k % SOURCES]
+        _, info, st = oracle.solve(w.dx, w.dy, w.f, tol_rel=TOL, openmp=True)
+        iters.append(info["iters"])
     dt = time.perf_counter() - t0
-    v = args.steps * (cap / full["iters"]) / dt
+    v = args.steps / dt
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "tol_rel": TOL,
-                                             "solver": "CPU FP64 Jacobi PCG (oracle)"},
-            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} x {cap} of the {full['iters']} iterations of a full "
-                                       f"solve, one host thread, scaled to solves/s"},
+            "data": "synthetic", "config": {"workload": ws[0].name, "nx": ws[0].nx, "ny": ws[0].ny, "tol_rel": TOL,
+                                             "sources": SOURCES, "solver": "CPU FP64 Jacobi PCG (oracle)"},
+            "iters_per_solve": float(np.mean(iters)),
+            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} whole solves ({SOURCES} sources cycled), OpenMP on {cores} "
+                                       f"host threads", "cpu_model": _cpu_model()},
             "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def _direction_kernels(levels):
+    """Kernel launches of one DLSM direction: the input convolution, two
+    convolutions per encoder level with a pooling before each level but the
+    first, an up-sampling and three convolutions per decoder level, the fold
+    of head and trunk, and the two kernels of the mean removal."""
+    return 2 + 3 * (levels - 1) + 4 * (levels - 1) + 1 + 2
+
+
+def _kernels_of(info, levels):
+    """Kernels of one solve in its graph: the initialisation, a solver segment
+    and a decision kernel per segment, and the network branches taken."""
+    return 1 + 2 * info["launches"] + info["net_calls"] * _direction_kernels(levels)
+
+
+def _time_arm(api, grid, rhs_list, x, mode, net, steps, flush, stream, clk=None):
+    """CUDA-event time of `steps` solves (L2 flushed before each), sources cycled."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    infos = []
+    torch.cuda.synchronize()
+    for k in range(steps):
+        flush.fill_(float(k))
+        x.zero_()
+        ev[k][0].record(stream)
+        infos.append(api.ppe_solve(grid, rhs_list[k % len(rhs_list)], x, TOL, mode, api.PPE_PREC_MIXED, net=net))
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev], infos
+
+
+def _e2e_arm(api, grid, ws, mode, net, steps, dev):
+    """Through the public API with host buffers: pinned source in, solution out."""
+    import torch
+    h_rhs = [torch.tensor(w.f, dtype=torch.float64).pin_memory() for w in ws]
+    h_x = torch.empty_like(h_rhs[0]).pin_memory()
+    d_rhs = torch.empty(h_rhs[0].shape, dtype=torch.float64, device=dev)
+    d_x = torch.empty_like(d_rhs)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(steps):
+        d_rhs.copy_(h_rhs[k % len(ws)], non_blocking=True)
+        d_x.zero_()
+        api.ppe_solve(grid, d_rhs, d_x, TOL, mode, api.PPE_PREC_MIXED, net=net)
+        h_x.copy_(d_x, non_blocking=True)
+        torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return dt, int(h_rhs[0].numel() * 8), int(h_x.numel() * 8)
 
 
 def run_native(args):
@@ -177,143 +260,219 @@ def run_native(args):
         dist.init_process_group("nccl")
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
-
-    w = I.config2(rank)              # weak scaling: each rank solves its own system
-    grid = api.ppe_create_grid(w.dx, w.dy)
-    rhs = torch.tensor(w.f, dtype=torch.float64, device=dev)
-    x = torch.zeros_like(rhs)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    prec = api.PPE_PREC_MIXED
 
-    def solve_once():
-        x.zero_()
-        return api.ppe_solve(grid, rhs, x, TOL, api.PPE_MODE_PCG, prec)
+    # weak scaling: each rank solves its own sources of the cylinder workload
+    ws = [I.config3(SOURCES * rank + i) for i in range(SOURCES)]
+    w0 = ws[0]
+    grid = api.ppe_create_grid(w0.dx, w0.dy, w0.mask)
+    net = api.net_load(WEIGHTS)
+    net.attach(grid)
+    levels = net.config().levels
+    rhs = [torch.tensor(w.f, dtype=torch.float64, device=dev) for w in ws]
+    x = torch.zeros_like(rhs[0])
+    H, P = api.PPE_MODE_HYBRID, api.PPE_MODE_PCG
 
-    for _ in range(args.warmup):
-        info = solve_once()
+    for k in range(args.warmup):
+        for mode, nt in ((H, net), (P, None)):
+            x.zero_()
+            api.ppe_solve(grid, rhs[k % SOURCES], x, TOL, mode, api.PPE_PREC_MIXED, net=nt)
     torch.cuda.synchronize()
-
-    # ---- device-resident timing: CUDA events around each solve, L2 flushed between
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    infos = []
-    launches = 0
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        for k in range(args.steps):
-            flush.fill_(float(k))
-            x.zero_()
-            ev[k][0].record(stream)
-            info = api.ppe_solve(grid, rhs, x, TOL, api.PPE_MODE_PCG, prec)
-            ev[k][1].record(stream)
-            infos.append(info)
-            launches += info["launches"]
-        torch.cuda.synchronize()
+        ms_h, info_h = _time_arm(api, grid, rhs, x, H, net, args.steps, flush, stream)
     if world > 1:
         dist.barrier()
-    ms = [a.elapsed_time(b) for a, b in ev]
-    t_total = shard.max_over_ranks(sum(ms) / 1e3, dev)
-    value = world * args.steps / t_total
-    for info in infos:
-        assert info["status"] == 0 and info["rel_res_true"] <= TOL, info
-
-    # ---- end-to-end: pinned host source in, host solution out, through the public API
-    h_rhs = torch.tensor(w.f, dtype=torch.float64).pin_memory()
-    h_x = torch.empty_like(h_rhs).pin_memory()
-    d_rhs = torch.empty_like(rhs)
-    d_x = torch.empty_like(rhs)
     torch.cuda.synchronize()
-    e2e_steps = max(3, args.steps // 2)
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        d_rhs.copy_(h_rhs, non_blocking=True)
-        d_x.zero_()
-        api.ppe_solve(grid, d_rhs, d_x, TOL, api.PPE_MODE_PCG, prec)
-        h_x.copy_(d_x, non_blocking=True)
-        torch.cuda.synchronize()
-    e2e_dt = time.perf_counter() - t0
-    e2e = {"value": world * e2e_steps / e2e_dt if world == 1 else None, "unit": "solves/s",
-           "h2d_bytes_per_step": int(h_rhs.numel() * 8), "d2h_bytes_per_step": int(h_x.numel() * 8)}
+    ms_p, info_p = _time_arm(api, grid, rhs, x, P, None, args.steps, flush, stream)
     if world > 1:
-        e2e["value"] = world * e2e_steps / shard.max_over_ranks(e2e_dt, dev)
+        dist.barrier()
+    for info in info_h + info_p:
+        assert info["status"] == 0 and info["rel_res_true"] <= TOL, info
+    t_h = shard.max_over_ranks(sum(ms_h) / 1e3, dev)
+    t_p = shard.max_over_ranks(sum(ms_p) / 1e3, dev)
+    value = world * args.steps / t_h
+    plain_value = world * args.steps / t_p
 
-    # ---- roofline of the dominant kernel (the persistent solver kernel)
+    e2e_steps = max(3, args.steps // 2)
+    dt_h, bi, bo = _e2e_arm(api, grid, ws, H, net, e2e_steps, dev)
+    dt_p, _, _ = _e2e_arm(api, grid, ws, P, None, e2e_steps, dev)
+    dt_h, dt_p = shard.max_over_ranks(dt_h, dev), shard.max_over_ranks(dt_p, dev)
+    e2e = {"value": world * e2e_steps / dt_h, "unit": "solves/s", "h2d_bytes_per_step": bi,
+           "d2h_bytes_per_step": bo}
+
+    def med(infos, k):
+        return float(np.median([i[k] for i in infos]))
+
     peaks, peak_src = _peaks()
-    it = float(np.mean([i["iters_pcg"] for i in infos]))
-    ref = float(np.mean([i["refinements"] for i in infos]))
-    n = w.nx * w.ny
-    alg_bytes = n * (24.0 * it + 24.0 * ref)       # FP32 iterations + FP64 residual passes
-    achieved = alg_bytes / (t_total / args.steps) / 1e9
+    n = w0.nx * w0.ny
+    # roofline of the dominant kernel, the persistent solver kernel: its
+    # algorithmic bytes per solve (24 B/cell per PCG iteration and per FP64
+    # pass, 20 B/cell per DLSM update) over its device time in the solve
+    # (the kernel's own step clock: ms_pcg + ms_dlsm + ms_refine)
+    def solver_roof(infos):
+        b = [n * (24.0 * (i["iters_pcg"] + i["refinements"]) + 20.0 * i["iters_dlsm"]) for i in infos]
+        t = [(i["ms_pcg"] + i["ms_dlsm"] + i["ms_refine"]) / 1e3 for i in infos]
+        return float(np.mean(b)), float(np.mean(t))
+
+    bytes_h, t_solver = solver_roof(info_h)
+    achieved = bytes_h / t_solver / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"], "traffic": SOLVER_C2_DRAM_BYTES,
-            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch (one solve), "
-                              "profiles/solver_kernel_tile_c2.md",
-            "kernel": "solver_kernel<float>", "peak_source": f"hbm_gbs ({peak_src})",
-            "note": "working set (~10 MB) is L2-resident: latency/barrier-bound, not HBM-bound"}
+            "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+            "kernel": "solver_kernel<float, tile>", "peak_source": f"hbm_gbs ({peak_src})",
+            "units": "24 B/cell per PCG iteration and FP64 pass, 20 B/cell per DLSM update, per solve",
+            "note": "working set (~3 MB) is L2-resident: barrier/latency-bound, not HBM-bound"}
+    kernels = int(sum(_kernels_of(i, levels) for i in info_h))
 
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_h / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 solver, bf16 network",
             "data": "synthetic",
-            "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "tol_rel": TOL, "mode": "pcg",
-                       "precision": "mixed FP32 inner / FP64 refinement", "l2": "flushed between steps",
-                       "spacing_ratio": round(I.spacing_ratio(w.dx, w.dy), 2)},
-            "iters_per_solve": it, "refinements_per_solve": ref,
-            "e2e": e2e, "gpu_launches": launches, "roofline": roof, "clocks": clk.summary()}
-
-    if not args.no_sweep and rank == 0:
-        line["stencil_sweep"] = stencil_sweep(api, dev, peaks)
-    if rank == 0:
-        line["hybrid_vs_plain"] = hybrid_vs_plain(api, dev, flush)
-    batch = batch_vs_sequential(api, dev, flush, peaks, rank, world)      # every rank: its share
-    if rank == 0:
-        line["batch_vs_sequential"] = batch
-        line["sequence_c5"] = sequence_c5(api, dev, flush)
+            "config": {"workload": w0.name, "nx": w0.nx, "ny": w0.ny, "tol_rel": TOL, "mode": "hybrid",
+                       "sources": SOURCES, "precision": "FP32 inner / FP64 refinement / BF16 network",
+                       "network": os.path.basename(WEIGHTS), "num_cg": 3, "num_dlsm": 2,
+                       "l2": "flushed between steps", "spacing_ratio": round(I.spacing_ratio(w0.dx, w0.dy), 2)},
+            "iters_per_solve": med(info_h, "iters_pcg") + med(info_h, "iters_dlsm"),
+            "dlsm_steps_per_solve": med(info_h, "iters_dlsm"),
+            "fell_back": int(sum(i["fell_back"] for i in info_h)),
+            "phase_ms": {k: med(info_h, k) for k in ("ms_pcg", "ms_dlsm", "ms_net", "ms_refine", "ms_total")},
+            "plain_pcg": {"value": plain_value, "unit": "solves/s", "ms_per_step": 1e3 * t_p / args.steps,
+                          "iters_per_solve": med(info_p, "iters_pcg"),
+                          "e2e": {"value": world * e2e_steps / dt_p, "unit": "solves/s", "h2d_bytes_per_step": bi,
+                                  "d2h_bytes_per_step": bo}},
+            "speedup_vs_plain": value / plain_value,
+            "e2e": e2e, "gpu_launches": kernels, "roofline": roof, "clocks": clk.summary()}
+    if rank == 0 and not args.no_extras:
+        line["roofline_conv"] = _safe(conv_roofline, api, net, grid, dev, peaks, peak_src, flush)
+        line["c1_fp64"] = _safe(small_fp64, api, dev, flush)
+        line["c2_mixed"] = _safe(refined_box, api, dev, flush, peaks, peak_src)
+        if not args.no_sweep:
+            line["stencil_sweep"] = _safe(stencil_sweep, api, dev, peaks)
+    if not args.no_extras:
+        batch = batch_vs_sequential(api, dev, flush, peaks, rank, world)      # every rank: its share
+        if rank == 0:
+            line["batch_vs_sequential"] = batch
+            line["sequence_c5"] = _safe(sequence_c5, api, dev, flush)
     if rank == 0 and world == 1 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_oracle_baseline(w)
+        line["cpu_baseline"] = _safe(cpu_oracle_baseline, ws)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
 
 
-def hybrid_vs_plain(api, dev, flush, reps=5):
-    """HyDEA (Jacobi PCG + DLSM with a trained network) against plain PCG on
-    the 256x256 cylinder-refined grid with masked-divergence sources, all in
-    mixed precision, to rel-res 1e-8 (median of `reps` sources each), with
-    the network trained on random stretched grids."""
+def _safe(fn, *a):
+    """An extra section that fails is reported, not allowed to end the run."""
+    try:
+        return fn(*a)
+    except Exception as exc:          # noqa: BLE001
+        return {"error": f"{type(exc).__name__}: {exc}"}
+
+
+def conv_roofline(api, net, grid, dev, peaks, peak_src, flush, reps=20):
+    """The network's inference on the headline grid (the tcgen05 convolutions
+    are its dominant kernels), CUDA-event timed, against the BF16 tensor peak:
+    FLOPs = 2 * 9 * Cin * Cout * H * W summed over the 3x3 layers."""
     import torch
-    if not os.path.exists(WEIGHTS):
-        return {"available": False, "reason": "no trained weights file"}
-    nets = {"hybrid": api.net_load(WEIGHTS)}
-    out = {"workload": "cyl256_mask (256x256, cylinder D=0.1, box-refined, growth 1.05)"}
-    rows = {k: [] for k in ["pcg", *nets]}
-    for i in range(reps):
-        w = I.config3(i)
-        g = api.ppe_create_grid(w.dx, w.dy, w.mask)
-        rhs = torch.tensor(w.f, dtype=torch.float64, device=dev)
-        for key in rows:
-            net = nets.get(key)
-            mode = api.PPE_MODE_PCG if net is None else api.PPE_MODE_HYBRID
-            if net is not None:
-                net.attach(g)
-            x = torch.zeros_like(rhs)
-            api.ppe_solve(g, rhs, x, TOL, mode, api.PPE_PREC_MIXED, net=net)     # warm (graph capture)
-            flush.fill_(1.0)
+    from paper_2604_01800_gb300 import inputs as Iw
+    cfg = net.config()
+    widths = tuple(cfg.widths[:cfg.levels])
+    ncfg = Iw.NetConfig(widths=widths)
+    flops = 0.0
+    for name, cin, cout, lev in Iw.conv_layers(ncfg):
+        if cin == 1:
+            continue                      # the one-channel input layer runs on CUDA cores
+        flops += 2.0 * 9 * cin * cout * (256 >> lev) * (256 >> lev)
+    r = torch.randn(1, 256, 256, dtype=torch.float32, device=dev)
+    e = torch.empty_like(r)
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            net.infer(grid, r, e)          # buffers and one-time set-up before the capture
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()        # the inference's launches replayed as one graph
+    with torch.cuda.graph(graph):
+        net.infer(grid, r, e)
+    ts = []
+    for _ in range(reps):
+        flush.fill_(0.5)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        graph.replay()
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b) / 1e3)
+    t = float(np.median(ts))
+    tf = flops / t / 1e12
+    return {"bound": "tensor", "achieved": tf, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+            "frac": tf / peaks["bf16_tflops"], "traffic": None, "ms_per_inference": 1e3 * t,
+            "gflop_per_inference": flops / 1e9, "peak_source": f"bf16_tflops burst ({peak_src})",
+            "note": "whole inference (all launches) timed; the tensor-core convolutions are part of it"}
+
+
+def small_fp64(api, dev, flush, reps=10):
+    """The 64x64 tanh-stretched system in FP64 Jacobi PCG: solves/s and
+    microseconds per iteration (latency-bound; no HBM claim)."""
+    import torch
+    w = I.config1(0)
+    g = api.ppe_create_grid(w.dx, w.dy)
+    rhs = torch.tensor(w.f, dtype=torch.float64, device=dev)
+    x = torch.zeros_like(rhs)
+    for _ in range(3):
+        x.zero_()
+        api.ppe_solve(g, rhs, x, TOL, api.PPE_MODE_PCG, api.PPE_PREC_FP64)
+    ms, infos = [], []
+    for _ in range(reps):
+        flush.fill_(1.5)
+        x.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        infos.append(api.ppe_solve(g, rhs, x, TOL, api.PPE_MODE_PCG, api.PPE_PREC_FP64))
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    g.close()
+    m = float(np.median(ms))
+    it = float(np.median([i["iters_pcg"] for i in infos]))
+    return {"workload": w.name, "solves_per_s": 1e3 / m, "ms_per_solve": m, "iters": it,
+            "us_per_iter": 1e3 * m / it, "all_ok": all(i["status"] == 0 for i in infos)}
+
+
+def refined_box(api, dev, flush, peaks, peak_src, reps=10):
+    """The 512x512 refined-box system: mixed PCG (FP32 inner, FP64
+    refinement) and plain FP64 PCG, solves/s and the solver kernel's
+    effective bandwidth."""
+    import torch
+    w = I.config2(0)
+    g = api.ppe_create_grid(w.dx, w.dy)
+    rhs = torch.tensor(w.f, dtype=torch.float64, device=dev)
+    x = torch.zeros_like(rhs)
+    out = {"workload": w.name, "spacing_ratio": round(I.spacing_ratio(w.dx, w.dy), 2)}
+    for key, prec in (("mixed", api.PPE_PREC_MIXED), ("fp64", api.PPE_PREC_FP64)):
+        for _ in range(2):
             x.zero_()
-            rows[key].append(api.ppe_solve(g, rhs, x, TOL, mode, api.PPE_PREC_MIXED, net=net))
-        g.close()
-    for key, infos in rows.items():
-        ms = float(np.median([i["ms_total"] for i in infos]))
-        out[key] = {"solves_per_s": 1e3 / ms, "ms_median": ms,
-                    "iters_median": float(np.median([i["iters_pcg"] + i["iters_dlsm"] for i in infos])),
-                    "dlsm_steps_median": float(np.median([i["iters_dlsm"] for i in infos])),
-                    "fell_back": int(sum(i["fell_back"] for i in infos)),
-                    "max_rel_res": float(max(i["rel_res_true"] for i in infos))}
-    out["speedup"] = out["hybrid"]["solves_per_s"] / out["pcg"]["solves_per_s"]
-    for net in nets.values():
-        net.close()
+            api.ppe_solve(g, rhs, x, TOL, api.PPE_MODE_PCG, prec)
+        ms, infos = [], []
+        for _ in range(reps if key == "mixed" else 3):
+            flush.fill_(2.5)
+            x.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            infos.append(api.ppe_solve(g, rhs, x, TOL, api.PPE_MODE_PCG, prec))
+            b.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        m = float(np.median(ms))
+        it = float(np.median([i["iters_pcg"] for i in infos]))
+        ref = float(np.median([i["refinements"] for i in infos]))
+        bpc = 24.0 if key == "mixed" else 48.0
+        gbs = w.nx * w.ny * (bpc * it + 24.0 * ref) / (m / 1e3) / 1e9
+        out[key] = {"solves_per_s": 1e3 / m, "ms_per_solve": m, "iters": it, "refinements": ref,
+                    "us_per_iter": 1e3 * m / it, "effective_gbs": gbs, "frac_of_hbm": gbs / peaks["hbm_gbs"],
+                    "all_ok": all(i["status"] == 0 and i["rel_res_true"] <= TOL for i in infos)}
+    g.close()
     return out
 
 
@@ -331,7 +490,9 @@ def sequence_c5(api, dev, flush, steps=16):
     if os.path.exists(WEIGHTS):
         arms["hybrid"] = api.net_load(WEIGHTS)
     out = {"workload": f"cyl2048x1024 wake-refined (spacing ratio {I.spacing_ratio(dx, dy):.1f}), "
-                       f"first {steps} of 500 steps, warm starts", "cells": int(dx.size * dy.size)}
+                       f"first {steps} of 500 steps, warm starts", "cells": int(dx.size * dy.size),
+           "measured_steps": steps, "sequence_steps": 500,
+           "extrapolated": f"total_500_ms_extrapolated = ms_per_step of the first {steps} steps x 500"}
     for key, net in arms.items():
         if net is not None:
             net.attach(grid)
@@ -347,6 +508,7 @@ def sequence_c5(api, dev, flush, steps=16):
             infos.append(api.ppe_solve(grid, rhs, x, TOL, mode, api.PPE_PREC_MIXED, net=net))
         ms = [i["ms_total"] for i in infos]
         out[key] = {"total_ms": float(sum(ms)), "ms_per_step": float(np.mean(ms)),
+                    "total_500_ms_extrapolated": float(np.mean(ms)) * 500,
                     "iters_per_step": float(np.mean([i["iters_pcg"] + i["iters_dlsm"] for i in infos])),
                     "dlsm_steps": int(sum(i["iters_dlsm"] for i in infos)),
                     "fell_back": int(sum(i["fell_back"] for i in infos)),
@@ -375,13 +537,13 @@ def batch_vs_sequential(api, dev, flush, peaks, rank=0, world=1, count=64):
     xs = [torch.zeros_like(r) for r in rhs]
     cells = sum(w.nx * w.ny for w in ws)
 
-    def batch():
+    def batch(mode=api.PPE_MODE_PCG, net=None):
         for x in xs:
             x.zero_()
         flush.fill_(2.0)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
-        infos, st = api.ppe_solve_batch(grids, rhs, xs, TOL, api.PPE_MODE_PCG, api.PPE_PREC_MIXED)
+        infos, st = api.ppe_solve_batch(grids, rhs, xs, TOL, mode, api.PPE_PREC_MIXED, net=net)
         b.record()
         torch.cuda.synchronize()
         return a.elapsed_time(b) / 1e3, infos
@@ -400,24 +562,48 @@ def batch_vs_sequential(api, dev, flush, peaks, rank=0, world=1, count=64):
     batch()
     tb, ib = min((batch() for _ in range(2)), key=lambda t: t[0])
     ts, iseq = sequential()
+    # the hybrid batch: one graph launch, the network's branches per system
+    net = api.net_load(WEIGHTS)
+    for g in grids:
+        net.attach(g)
+    batch(api.PPE_MODE_HYBRID, net)
+    th, ih = batch(api.PPE_MODE_HYBRID, net)
+    net.close()
     for g in grids:
         g.close()
-    # algorithmic bytes of the batch: 24 B per cell per FP32 iteration, 24 B per FP64 residual pass
-    mine_rep = {"ok": all(i["status"] == 0 and i["rel_res_true"] <= TOL for i in ib), "cells": cells,
-                "iters": [i["iters_pcg"] for i in ib],
-                "alg": sum(w.nx * w.ny * 24.0 * (i["iters_pcg"] + i["refinements"]) for w, i in zip(ws, ib))}
-    tb, ts = shard.max_over_ranks(tb, dev), shard.max_over_ranks(ts, dev)
+
+    # algorithmic bytes of the solver kernel: 24 B per cell per FP32
+    # iteration and per FP64 residual pass, 20 B per cell per DLSM update
+    def alg(infos):
+        return sum(w.nx * w.ny * (24.0 * (i["iters_pcg"] + i["refinements"]) + 20.0 * i["iters_dlsm"])
+                   for w, i in zip(ws, infos))
+
+    def ok(infos):
+        return all(i["status"] == 0 and i["rel_res_true"] <= TOL for i in infos)
+
+    mine_rep = {"ok": ok(ib), "ok_h": ok(ih), "cells": cells, "iters": [i["iters_pcg"] for i in ib],
+                "iters_h": [i["iters_pcg"] + i["iters_dlsm"] for i in ih],
+                "dlsm": sum(i["iters_dlsm"] for i in ih), "fell_back": sum(i["fell_back"] for i in ih),
+                "alg": alg(ib), "alg_h": alg(ih),
+                "solver_ms_h": sum(i["ms_pcg"] + i["ms_dlsm"] + i["ms_refine"] for i in ih[:1])}
+    tb, ts, th = (shard.max_over_ranks(t, dev) for t in (tb, ts, th))
     reps = shard.gather_to_rank0(mine_rep)
     if rank != 0:
         return None
     iters = [k for r in reps for k in r["iters"]]
-    alg = sum(r["alg"] for r in reps)
+    iters_h = [k for r in reps for k in r["iters_h"]]
+    a, ah = sum(r["alg"] for r in reps), sum(r["alg_h"] for r in reps)
     return {"systems": count, "ranks": world, "cells": sum(r["cells"] for r in reps),
-            "all_converged": all(r["ok"] for r in reps),
-            "batch_seconds": tb, "batch_systems_per_s": count / tb,
-            "sequential_seconds": ts, "sequential_systems_per_s": count / ts, "speedup": ts / tb,
-            "max_iters": max(iters), "mean_iters": float(np.mean(iters)),
-            "effective_gbs": alg / tb / 1e9, "frac_of_hbm": alg / tb / 1e9 / peaks["hbm_gbs"] / world}
+            "drive": "one CUDA graph launch per batch (device-side loop, on-device re-planning)",
+            "pcg": {"all_converged": all(r["ok"] for r in reps), "seconds": tb, "systems_per_s": count / tb,
+                    "max_iters": max(iters), "mean_iters": float(np.mean(iters)),
+                    "effective_gbs": a / tb / 1e9, "frac_of_hbm": a / tb / 1e9 / peaks["hbm_gbs"] / world},
+            "hybrid": {"all_converged": all(r["ok_h"] for r in reps), "seconds": th, "systems_per_s": count / th,
+                       "max_iters": max(iters_h), "mean_iters": float(np.mean(iters_h)),
+                       "dlsm_steps": sum(r["dlsm"] for r in reps), "fell_back": sum(r["fell_back"] for r in reps),
+                       "effective_gbs": ah / th / 1e9, "frac_of_hbm": ah / th / 1e9 / peaks["hbm_gbs"] / world},
+            "sequential_pcg": {"seconds": ts, "systems_per_s": count / ts},
+            "speedup_batch_vs_sequential": ts / tb, "speedup_hybrid_batch_vs_sequential": ts / th}
 
 
 def stencil_sweep(api, dev, peaks, sizes=(4096, 8192, 16384), short=20, long=120):

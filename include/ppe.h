@@ -84,7 +84,23 @@ typedef struct {
     double rel_res_true;    /* ||P(b - A x)|| / ||P b|| in FP64 at exit                  */
     double incompat;        /* |sum b| / sum |b| before projection                       */
     double ms_total;        /* wall time of the call on its stream (ms)                  */
-    double ms_net;          /* part of ms_total spent in network inference (ms)          */
+    double ms_net;          /* device time from each segment that asked for a DLSM
+                               direction to the segment that used it: the network
+                               inference and the direction's mean removal (ms)         */
+    double ms_pcg;          /* device time of the CG-type passes (Sec. 2.2; ms)          */
+    double ms_dlsm;         /* device time of the DLSM passes: r.e, e.Ae and the update
+                               of Eqs. 11-12 (ms)                                        */
+    double ms_refine;       /* device time of the FP64 passes: statistics of b, true
+                               residuals (iterative refinement), finalisation (ms)       */
+    int32_t drive;          /* 0: the solve ran as one CUDA graph launch whose device-side
+                               loop alternated solver segments and network branches
+                               (no host round-trip per hybrid cycle); 1: the host
+                               launched each segment and direction                       */
+    int32_t precision_fallback; /* 1: the mixed solve's FP32 inner iteration stalled (three
+                               refinements in a row failed to halve the true residual, as
+                               happens once the system's conditioning exceeds what FP32
+                               resolves) and the solve was continued in FP64 from there; the
+                               counts and times include both parts                      */
 } ppe_solve_info;
 
 /* Solver options; ppe_default_options() fills the defaults shown. */
@@ -94,7 +110,8 @@ typedef struct {
     int32_t num_dlsm;       /* Num_DLSM: DLSM steps per hybrid cycle (2; Sec. 2.2)            */
     int32_t hybrid_budget;  /* iterations after which hybrid mode continues as plain PCG      */
     double inner_rtol;      /* MIXED: FP32 residual drop that triggers an FP64 residual
-                               replacement (0.1)                                              */
+                               replacement (0.3: measured on GB300, 3,660 iterations on the
+                               512^2 refined-box grid against 4,338 at 0.1)                 */
     double dlsm_guard;      /* skip a DLSM step if e.Ae <= guard * e.e * max(diag A) (1e-10)   */
     int32_t blocks_per_sm;  /* cap on persistent-kernel CTAs per SM (2; 0 = as many as fit;
                                the solver kernels fit one)                                    */
@@ -112,7 +129,15 @@ typedef struct {
                                remove at their mean (alpha r.u each).  Not in the paper: a
                                guard against a network that does not pay for its inference. */
     int32_t dlsm_cost_iters;  /* a DLSM step's cost in CG iterations for that test (16)        */
-    int32_t reserved[3];
+    int32_t spin_limit_ms;  /* bound on every device-side wait of the solver kernel, in ms (2000).
+                               On expiry the kernel returns and the solve reports PPE_ERR_TIMEOUT. */
+    int32_t host_loop;      /* 0: one graph launch with device-side alternation (default);
+                               1: the host launches each solver segment and network direction
+                               (always so for a grid with a direction source)                 */
+    int32_t debug_skip_block; /* test hook, 0 = off: block debug_skip_block - 1 of the solver
+                               kernel withholds its partial sums at its second step, so the
+                               other blocks' bounded waits expire (PPE_ERR_TIMEOUT)           */
+    int32_t reserved[5];
 } ppe_solve_opts;
 
 PPE_API void ppe_default_options(ppe_solve_opts *opts);

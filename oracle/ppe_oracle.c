@@ -22,6 +22,11 @@
  *   The answer is the unique solution with zero volume-weighted mean.
  *
  * The assembled matrix is plain CSR, rows in [ny][nx] row-major order.
+ *
+ * Built plain (gcc -O2) it runs on one thread; that build is the one the
+ * tests use.  Built with -fopenmp (the benchmark's all-core CPU timing only)
+ * the vector loops below run on every host core; the reductions then add in
+ * a different order, which changes results only at rounding level.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -67,6 +72,7 @@ int or_assemble(int nx, int ny, const double *dx, const double *dy,
 void or_spmv(long n, const long *rowptr, const int *col, const double *val,
              const double *x, double *y)
 {
+#pragma omp parallel for schedule(static)
     for (long r = 0; r < n; ++r) {
         double s = 0.0;
         for (long k = rowptr[r]; k < rowptr[r + 1]; ++k) s += val[k] * x[col[k]];
@@ -77,6 +83,7 @@ void or_spmv(long n, const long *rowptr, const int *col, const double *val,
 static double dot(long n, const double *a, const double *b)
 {
     double s = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : s)
     for (long i = 0; i < n; ++i) s += a[i] * b[i];
     return s;
 }
@@ -85,8 +92,10 @@ static double dot(long n, const double *a, const double *b)
 static void project(long n, double *v)
 {
     double s = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : s)
     for (long i = 0; i < n; ++i) s += v[i];
     s /= (double)n;
+#pragma omp parallel for schedule(static)
     for (long i = 0; i < n; ++i) v[i] -= s;
 }
 
@@ -119,12 +128,15 @@ long or_jpcg(long n, const long *rowptr, const int *col, const double *val,
         double pq = dot(n, p, q);
         if (!(pq > 0.0)) break;
         double alpha = rz / pq;
+#pragma omp parallel for schedule(static)
         for (long i = 0; i < n; ++i) { x[i] += alpha * p[i]; r[i] -= alpha * q[i]; }
         project(n, r);
+#pragma omp parallel for schedule(static)
         for (long i = 0; i < n; ++i) z[i] = dinv[i] * r[i];
         double rz_new = dot(n, r, z);
         double beta = rz_new / rz;
         rz = rz_new;
+#pragma omp parallel for schedule(static)
         for (long i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
         ++it;
     }
@@ -175,6 +187,7 @@ int or_solve(int nx, int ny, const double *dx, const double *dy,
     if (status == OR_OK && bnorm > 0.0) {
         for (int restart = 0; restart < 20; ++restart) {
             or_spmv(n, rowptr, col, val, x, r);
+#pragma omp parallel for schedule(static)
             for (long i = 0; i < n; ++i) r[i] = b[i] - r[i];
             project(n, r);
             relres = sqrt(dot(n, r, r)) / bnorm;

@@ -27,7 +27,9 @@ class ppe_solve_info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("iters_pcg", ctypes.c_int32), ("iters_dlsm", ctypes.c_int32),
                 ("dlsm_skipped", ctypes.c_int32), ("refinements", ctypes.c_int32), ("fell_back", ctypes.c_int32),
                 ("net_calls", ctypes.c_int32), ("launches", ctypes.c_int32), ("rel_res_true", ctypes.c_double),
-                ("incompat", ctypes.c_double), ("ms_total", ctypes.c_double), ("ms_net", ctypes.c_double)]
+                ("incompat", ctypes.c_double), ("ms_total", ctypes.c_double), ("ms_net", ctypes.c_double),
+                ("ms_pcg", ctypes.c_double), ("ms_dlsm", ctypes.c_double), ("ms_refine", ctypes.c_double),
+                ("drive", ctypes.c_int32), ("precision_fallback", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -38,7 +40,8 @@ class ppe_solve_opts(ctypes.Structure):
                 ("hybrid_budget", ctypes.c_int32), ("inner_rtol", ctypes.c_double), ("dlsm_guard", ctypes.c_double),
                 ("blocks_per_sm", ctypes.c_int32), ("keep_dir_after_dlsm", ctypes.c_int32),
                 ("iter_pass", ctypes.c_int32), ("dlsm_stall_limit", ctypes.c_int32),
-                ("dlsm_cost_iters", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("dlsm_cost_iters", ctypes.c_int32), ("spin_limit_ms", ctypes.c_int32), ("host_loop", ctypes.c_int32),
+                ("debug_skip_block", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class ppe_tune_report(ctypes.Structure):

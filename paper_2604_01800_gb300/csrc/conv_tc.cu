@@ -308,14 +308,26 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
 // host side
 // ---------------------------------------------------------------------------
 
+// Error flag of the tensor-core kernels, one per device (allocated on first
+// use with that device current).
+std::mutex g_flag_mu;
+int *g_flag[MAX_DEVICES] = {};
+
 int *err_flag()
 {
-    static int *flag = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        if (cudaMalloc(&flag, sizeof(int)) == cudaSuccess) cudaMemset(flag, 0, sizeof(int));
-    });
-    return flag;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return nullptr;
+    std::lock_guard<std::mutex> lk(g_flag_mu);
+    if (!g_flag[dev]) {
+        int *f = nullptr;
+        if (cudaMalloc(&f, sizeof(int)) != cudaSuccess) return nullptr;
+        if (cudaMemset(f, 0, sizeof(int)) != cudaSuccess) {
+            cudaFree(f);
+            return nullptr;
+        }
+        g_flag[dev] = f;
+    }
+    return g_flag[dev];
 }
 
 int sm_count()
@@ -344,13 +356,18 @@ ppe_status conv3x3_tc_prepare()
         return PPE_ERR_CUDA;
     }
     if (!err_flag()) return cuda_status(cudaErrorMemoryAllocation, "conv3x3_tc error flag");
-    static std::once_flag attr_once;
-    std::call_once(attr_once, [] {
+    // the shared-memory opt-in is a per-device attribute of each kernel
+    static PerDevice attrs;
+    const bool ok = once_per_device(attrs, [](int) {
         const int cap = 227 * 1024;
-        cudaFuncSetAttribute(conv_tc_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-        cudaFuncSetAttribute(conv_tc_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-        cudaFuncSetAttribute(conv_tc_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+        return cudaFuncSetAttribute(conv_tc_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap) ==
+                   cudaSuccess &&
+               cudaFuncSetAttribute(conv_tc_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap) ==
+                   cudaSuccess &&
+               cudaFuncSetAttribute(conv_tc_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap) ==
+                   cudaSuccess;
     });
+    if (!ok) return cuda_status(cudaGetLastError(), "cudaFuncSetAttribute(conv_tc_kernel)");
     return PPE_OK;
 }
 

@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -31,6 +32,24 @@ ppe_status cuda_status(cudaError_t e, const char *what);
         ppe_status _s = (call);                                                \
         if (_s != PPE_OK) return _s;                                           \
     } while (0)
+
+// ---------------------------------------------------------------------------
+// per-device one-time set-up (kernel attributes, lookups): fn runs with the
+// device current until it succeeds once on that device
+// ---------------------------------------------------------------------------
+constexpr int MAX_DEVICES = 64;
+struct PerDevice {
+    std::mutex m;
+    bool done[MAX_DEVICES] = {};
+};
+template <class F> bool once_per_device(PerDevice &pd, F fn)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return false;
+    std::lock_guard<std::mutex> lk(pd.m);
+    if (!pd.done[dev]) pd.done[dev] = fn(dev);
+    return pd.done[dev];
+}
 
 // ---------------------------------------------------------------------------
 // tiling of the persistent solver kernel
@@ -108,6 +127,16 @@ struct SysState {
     int32_t e_cg_n;                       // CG iterations of the current CG phase
     float e_cg, e_dlsm;                   // error energy (A-norm^2) they removed; the last DLSM step's
     float gamma_f, target_sq_f, ru_sq_f, rho_f;   // FP32 state of the FP32 iteration's transition
+    // mixed precision: FP32 iterations since the last true residual and in
+    // the inner solve before it; refinements in a row that did not halve the
+    // true residual; 1 once the FP32 iteration is judged stalled
+    int32_t it_rep, it_rep_prev, stall, prec_stalled, overran;
+    double relres_prev;                   // true relative residual at the previous refinement
+    // device time by kind of step (globaltimer ns, measured by the system's
+    // first block): CG-type passes, DLSM passes, FP64 passes (statistics of b,
+    // true residuals, finalisation), and the time between a segment that asked
+    // for a network direction and the segment that used it
+    uint64_t ns_pcg, ns_dlsm, ns_fp64, ns_net, t_net0;
 };
 
 // Tiles [t0, t1) of a block; they belong to systems s0..s1.
@@ -147,7 +176,7 @@ struct SolverArgs {
     int32_t nsys, ntiles;
     int64_t spin_limit_ns;
     int32_t max_steps;         // > 0: every block leaves after this many steps (the host may re-plan)
-    int32_t pad_;
+    int32_t skip_block;        // test hook: block skip_block - 1 withholds its record at step 2 (0: off)
     unsigned long long *prof;  // nullable: block 0 accumulates ns per step part [0..5] and the step count [7]
 };
 
@@ -158,6 +187,84 @@ enum SolverVariant : int { SV_FP64 = 0, SV_FP32_TILE = 1, SV_FP32_STREAM = 2 };
 ppe_status launch_solver_resume(const SolverArgs &a, SolverVariant v, int grid_blocks, cudaStream_t stream,
                                 int resume);
 int solver_max_blocks(SolverVariant v, int blocks_per_sm_req);
+// Kernel function and dynamic shared memory of a variant (graph nodes).
+const void *solver_kernel_fn(SolverVariant v);
+size_t solver_smem_bytes(SolverVariant v);
+// Set the variants' shared-memory attributes on the current device.
+void set_solver_attributes();
+
+// Split the tiles of n systems into contiguous block ranges: every range
+// holds at most `chunk` tiles (the smallest chunk for which at most
+// max_blocks ranges result) and tiles of at most SMAX systems.  ntiles[s] = 0
+// leaves system s without tiles.  Writes tile0 (prefix sums), blk0 and
+// nparts (the ranges a system's tiles fall in, i.e. the blocks whose records
+// it reduces), part0 (its first record slot) and the ranges; returns the
+// number of ranges (-1 if more than max_ranges would be needed) and the
+// record slots in *nslots.  Host and device (on-device re-planning of a
+// batch) run the same function.
+__host__ __device__ inline int plan_ranges(int n, const int32_t *ntiles, int max_blocks, int32_t *tile0,
+                                           int32_t *blk0, int32_t *nparts, int32_t *part0, BlockRange *ranges,
+                                           int max_ranges, int *nslots)
+{
+    int total = 0;
+    for (int s = 0; s < n; ++s) {
+        tile0[s] = total;
+        total += ntiles[s];
+    }
+    int nr = 0;
+    if (total > 0) {
+        if (max_blocks < 1) return -1;
+        for (int chunk = (total + max_blocks - 1) / max_blocks;; ++chunk) {
+            nr = 0;
+            int t = 0, s = 0;
+            while (t < total) {
+                while (tile0[s] + ntiles[s] <= t) ++s;              // the system holding tile t
+                const int lim = s + SMAX < n ? tile0[s + SMAX] : total;
+                const int e = t + chunk < lim ? t + chunk : lim;
+                int s1 = s;
+                while (tile0[s1] + ntiles[s1] <= e - 1) ++s1;
+                if (nr < max_ranges) {
+                    ranges[nr].t0 = t; ranges[nr].t1 = e; ranges[nr].s0 = s; ranges[nr].s1 = s1;
+                }
+                ++nr;
+                t = e;
+            }
+            if (nr <= max_blocks && nr <= max_ranges) break;
+            if (chunk > total) return -1;
+        }
+    }
+    int slots = 0;
+    for (int s = 0; s < n; ++s) {
+        int first = -1, last = -1;
+        for (int b = 0; b < nr; ++b)
+            if (s >= ranges[b].s0 && s <= ranges[b].s1) {
+                if (first < 0) first = b;
+                last = b;
+            }
+        blk0[s] = first;
+        nparts[s] = first < 0 ? 0 : last - first + 1;
+        part0[s] = slots;
+        slots += nparts[s];
+    }
+    *nslots = slots;
+    return nr;
+}
+
+// Device-resident alternation of a solve (one CUDA graph launch): the loop
+// control the decision kernel reads and updates between solver segments.
+struct DriveCtl {
+    int32_t n;              // systems
+    int32_t max_blocks;     // blocks of every solver launch (ranges beyond the plan are empty)
+    int32_t slot_cap;       // record slots per bank
+    int32_t max_steps;      // > 0: segments end on this step budget and a batch may be re-planned
+    int32_t planned_tiles;  // tiles of the current plan
+    int32_t launches;       // solver segments run so far
+    int32_t loop_cap;       // give up after this many segments
+    int32_t err;            // ppe_status of the loop itself (timeout, cap)
+    float fraction;         // re-plan when the running systems hold fewer tiles than this share of the plan
+    int32_t with_net;       // 1: the graph has a network branch per system
+    int32_t pad_[2];
+};
 
 // Encode the NMAPS tensor maps of one system's inner vectors for a kernel
 // variant (element type FP32 or FP64, box shapes of the variant's tiles; row
@@ -174,6 +281,35 @@ bool tune_lookup(int nx, int ny, int *iter_pass, int *blocks_per_sm);
 // Remove the mean of the grid's DLSM direction e (two kernels on `stream`;
 // no allocation, so it may run inside a stream capture).
 ppe_status center_direction(ppe_grid *g, cudaStream_t stream);
+
+// Device resources of one set of solver launches (a grid's single solves, or
+// a batch), allocated once and reused by every solve: descriptions, states,
+// block ranges, record slots, barrier counters, loop control, events, and
+// the solve graph with what it was built for.
+struct LaunchSet {
+    int n = 0, max_ranges = 0, slot_cap = 0, device = 0;
+    SysDesc *sys = nullptr;
+    SysState *st = nullptr;
+    BlockRange *ranges = nullptr, *ranges_tmp = nullptr;
+    Slot *slots = nullptr;               // 2 banks x slot_cap records
+    Control *ctl = nullptr;
+    uint32_t *arrive = nullptr;          // per system: cumulative count of published records
+    DriveCtl *dc = nullptr;
+    int32_t *full_tiles = nullptr;       // per system: tiles of its full plan
+    int32_t *plan_scratch = nullptr;     // 5 n integers for on-device re-planning
+    cudaGraphConditionalHandle *if_handles = nullptr;   // per system: its network branch
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaStream_t cap = nullptr;          // capture stream of the network branches
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    // what the graph was built for
+    SolverArgs built_args{};
+    int built_variant = -1, built_blocks = 0, built_with_net = 0;
+    const void *built_net = nullptr;
+    uint64_t built_version = 0;
+};
+ppe_status launch_set_create(int n, int max_ranges, int slot_cap, LaunchSet **out);
+void launch_set_destroy(LaunchSet *ls);
 
 }  // namespace ppe
 
@@ -195,13 +331,8 @@ struct ppe_grid {
     void *r[2] = {nullptr, nullptr}, *p[2] = {nullptr, nullptr}, *d = nullptr;
     CUtensorMap *tmaps_dev = nullptr;    // tensor maps of the inner vectors, one set per kernel variant
     int tuned_pass = 0, tuned_bps = 0;   // ppe_autotune's choice (0: none)
-    // single-system launch resources
-    ppe::SysDesc *sys_dev = nullptr;
-    ppe::SysState *st_dev = nullptr;
-    ppe::BlockRange *ranges_dev = nullptr;
-    int ranges_blocks = 0;
-    ppe::Slot *slots_dev = nullptr;      // 2 banks x (tiles + 1) partial-sum records
-    ppe::Control *ctl_dev = nullptr;
+    uint64_t id = 0;                     // process-unique creation number (keys cached batch plans)
+    ppe::LaunchSet *ls = nullptr;        // single-system launch resources and the solve graph
     ppe_direction_fn dir_fn = nullptr;   // user direction source (replaces the network)
     void *dir_user = nullptr;
     float *dir_r = nullptr, *dir_e = nullptr;   // [ny][nx] staging for dir_fn

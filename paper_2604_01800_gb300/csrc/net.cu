@@ -456,6 +456,39 @@ ppe_status net_forward(ppe_net *n, NetCache *c, int B, const InputSrc &src, cons
                     s);
 }
 
+ppe_status net_prepare_direction(ppe_net *net, ppe_grid *g, cudaStream_t stream)
+{
+    PPE_TRY(net_check_grid(net, g));
+    NetCache *c = (NetCache *)g->net_cache;
+    PPE_TRY(ensure_packed(net, net->params, stream));
+    PPE_TRY(refresh_cache(net, c, net->params, stream));
+    PPE_TRY(ensure_acts(net, c, 1));
+    if (net->use_tc) PPE_TRY(conv3x3_tc_prepare());     // one-time set-up cannot run inside a capture
+    return PPE_OK;
+}
+
+ppe_status net_record_direction(ppe_net *net, ppe_grid *g, const SysDesc *sd_dev, const SysState *st_dev,
+                                cudaStream_t stream)
+{
+    PPE_TRY(net_check_grid(net, g));
+    NetCache *c = (NetCache *)g->net_cache;
+    InputSrc src;
+    src.sd = sd_dev; src.st = st_dev; src.nx = g->nx; src.ny = g->ny;
+    PPE_TRY(net_forward(net, c, 1, src, net->params, g->e, g->pitch, 0, false, stream));
+    return center_direction(g, stream);
+}
+
+uint64_t net_direction_key(const ppe_net *net, const ppe_grid *g)
+{
+    // what a captured direction bakes in: the parameter version (packed
+    // weights, eta, trunk fold) and the grid's activation buffers
+    const NetCache *c = g ? (const NetCache *)g->net_cache : nullptr;
+    uint64_t h = net ? net->version : 0;
+    h = h * 0x100000001b3ull ^ (uint64_t)(uintptr_t)c;
+    h = h * 0x100000001b3ull ^ (uint64_t)(uintptr_t)(c ? c->act : nullptr);
+    return h;
+}
+
 // The DLSM direction of a solver system: the forward pass on its normalised
 // residual, with its mean removed.  The sequence of launches is the same on every call, so it is
 // captured once into a CUDA graph (per grid and parameter version) and
@@ -469,7 +502,8 @@ ppe_status net_direction(ppe_net *net, ppe_grid *g, const SysDesc *sd_dev, const
     PPE_TRY(ensure_packed(net, net->params, stream));
     PPE_TRY(refresh_cache(net, c, net->params, stream));
     PPE_TRY(ensure_acts(net, c, 1));
-    if (!(c->dir_exec && c->dir_version == net->version && c->dir_key == (const void *)sd_dev)) {
+    if (!(c->dir_exec && c->dir_version == net->version && c->dir_key == (const void *)sd_dev &&
+          c->dir_act == (const void *)c->act)) {
         if (c->dir_exec) {
             cudaGraphExecDestroy(c->dir_exec);
             c->dir_exec = nullptr;
@@ -496,6 +530,7 @@ ppe_status net_direction(ppe_net *net, ppe_grid *g, const SysDesc *sd_dev, const
         }
         c->dir_version = net->version;
         c->dir_key = sd_dev;
+        c->dir_act = c->act;
     }
     PPE_CUDA_TRY(cudaGraphLaunch(c->dir_exec, stream));
     return PPE_OK;

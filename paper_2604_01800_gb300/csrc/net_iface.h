@@ -14,5 +14,16 @@ ppe_status net_check_grid(ppe_net *net, ppe_grid *g);
 // the elapsed time of the inference on `stream`.
 ppe_status net_direction(ppe_net *net, ppe_grid *g, const SysDesc *sd_dev, const SysState *st_dev,
                          bool fp64_inner, cudaStream_t stream, float *ms);
+// Bring the packed weights, the grid's caches and its activation buffers up
+// to date for directions (kernels on `stream`; call outside any capture).
+ppe_status net_prepare_direction(ppe_net *net, ppe_grid *g, cudaStream_t stream);
+// Enqueue the direction's launches for system (sd_dev, st_dev) on a stream
+// that is being captured (after net_prepare_direction): the forward pass on
+// the normalised residual, then the mean removal of e.
+ppe_status net_record_direction(ppe_net *net, ppe_grid *g, const SysDesc *sd_dev, const SysState *st_dev,
+                                cudaStream_t stream);
+// Key of what a captured direction of this grid bakes in (parameter version,
+// activation buffers); a changed key means the capture must be redone.
+uint64_t net_direction_key(const ppe_net *net, const ppe_grid *g);
 
 }  // namespace ppe

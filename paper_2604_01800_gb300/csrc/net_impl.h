@@ -48,6 +48,7 @@ struct NetCache {
     cudaGraphExec_t dir_exec = nullptr;
     uint64_t dir_version = 0;
     const void *dir_key = nullptr;
+    const void *dir_act = nullptr;          // activation buffer the graph was captured with
     cudaStream_t cap_stream = nullptr;
 };
 

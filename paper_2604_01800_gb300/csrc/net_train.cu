@@ -98,7 +98,9 @@ __global__ void fold_bwd_kernel(const float *__restrict__ de, const bf16 *__rest
     }
 }
 
-// dZ = dY * gelu'(Z) (BF16); db[c] += sum over pixels (C divides 256)
+// dZ = dY * gelu'(Z) (BF16); db[c] += sum over pixels.  The block size is a
+// multiple of C (C <= 256), so that element k of the grid-stride loop always
+// has channel threadIdx.x % C in a thread.
 __global__ void act_bwd_kernel(const float *__restrict__ dY, const bf16 *__restrict__ Z, bf16 *__restrict__ dZ,
                                size_t n, int C, float *__restrict__ db)
 {
@@ -112,10 +114,17 @@ __global__ void act_bwd_kernel(const float *__restrict__ dY, const bf16 *__restr
     red[threadIdx.x] = acc;
     __syncthreads();
     if ((int)threadIdx.x < C) {
+        // threads t = c, c + C, ... of the block all summed channel c
         float s = 0.f;
         for (int t = threadIdx.x; t < (int)blockDim.x; t += C) s += red[t];
         atomicAdd(&db[threadIdx.x], s);
     }
+}
+
+void act_bwd(const float *dY, const bf16 *Z, bf16 *dZ, size_t n, int C, float *db, cudaStream_t s)
+{
+    const int bs = (256 / C) * C;          // a multiple of C
+    act_bwd_kernel<<<g1d(n, bs), bs, 0, s>>>(dY, Z, dZ, n, C, db);
 }
 
 // dW[co][ci][tap] += sum_p dZ[p][co] * X[p + tap][ci]  (X: the layer's eta-weighted input)
@@ -548,7 +557,7 @@ static ppe_status conv_backward(ppe_net *n, NetCache *c, TrainWs *w, int li, con
     const size_t px = (size_t)B * H * W;
     const float *dY = w->g + w->G[li];
     const bf16 *Z = c->act + c->plan.Z[li];
-    act_bwd_kernel<<<g1d(px * l.cout), 256, 0, s>>>(dY, Z, w->dZ, px * l.cout, l.cout, grads + l.off_b);
+    act_bwd(dY, Z, w->dZ, px * l.cout, l.cout, grads + l.off_b, s);
     // weight gradient
     {
         if (l.cin % 8 || l.cout % 8) {
@@ -564,14 +573,15 @@ static ppe_status conv_backward(ppe_net *n, NetCache *c, TrainWs *w, int li, con
         int split = std::max(1, std::min(tiles, 592 / std::max(1, blocks_xy)));
         int per = (tiles + split - 1) / split;
         grid.z = (tiles + per - 1) / per;
-        static bool attr_set = false;
-        if (!attr_set) {
-            PPE_CUDA_TRY(cudaFuncSetAttribute(wgrad_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)wg_smem<1>()));
-            PPE_CUDA_TRY(cudaFuncSetAttribute(wgrad_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)wg_smem<2>()));
-            attr_set = true;
-        }
+        // the shared-memory opt-in is a per-device attribute of each kernel
+        static PerDevice attrs;
+        if (!once_per_device(attrs, [](int) {
+                return cudaFuncSetAttribute(wgrad_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)wg_smem<1>()) == cudaSuccess &&
+                       cudaFuncSetAttribute(wgrad_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)wg_smem<2>()) == cudaSuccess;
+            }))
+            return cuda_status(cudaGetLastError(), "cudaFuncSetAttribute(wgrad_kernel)");
         if (nco == 2)
             wgrad_kernel<2><<<grid, 256, wg_smem<2>(), s>>>(w->dZ, Xb, B, H, W, l.cin, l.cout, grads + l.off_w, per);
         else
@@ -667,8 +677,7 @@ static ppe_status net_backward(ppe_net *n, NetCache *c, TrainWs *w, ppe_grid *g,
         const int li = layer_index(n, "enc0a");
         const ConvLayer &l = n->layers[li];
         const size_t px = (size_t)B * c->H * c->W;
-        act_bwd_kernel<<<g1d(px * l.cout), 256, 0, s>>>(G("enc0a"), c->act + pl.Z[li], w->dZ, px * l.cout, l.cout,
-                                                       grads + l.off_b);
+        act_bwd(G("enc0a"), c->act + pl.Z[li], w->dZ, px * l.cout, l.cout, grads + l.off_b, s);
         const float *eta = c->eta + c->eoff[li];
         wgrad_in_kernel<<<1024, l.cout, 0, s>>>(w->dZ, R, eta, B, c->H, c->W, l.cout, g->nx, g->ny, grads + l.off_w);
         if (cf.mesh_conv) {

@@ -17,7 +17,8 @@
 // clears what must start at zero, and calls whose work overlaps on the GPU
 // race with each other.  The first call on a device looks the array's device
 // address up (cudaGetSymbolAddress, with that device current); make that
-// first call before any stream capture.
+// first call before any stream capture (a lookup that fails is retried by
+// the next call).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -75,29 +76,28 @@ __global__ void na_coeff_kernel(int n, const double *w, double *f, float *w32, f
     }
 }
 
-struct DevBase {
-    unsigned char *ptr = nullptr;
-    cudaError_t err = cudaSuccess;
-    std::once_flag once;
-};
-DevBase g_base[64];
+// Device address of the scratch array on the current device, looked up with
+// that device current.  Only a successful lookup is kept: a failed one (for
+// example a first call made during a stream capture) is retried by the next
+// call instead of disabling the entry point for the rest of the process.
+std::mutex g_base_mu;
+unsigned char *g_base[MAX_DEVICES] = {};
 
-// Device address of the scratch array on the current device, looked up once
-// per device with that device current.
 unsigned char *scratch_base(int dev, cudaError_t *err)
 {
-    if (dev < 0 || dev >= 64) {
+    if (dev < 0 || dev >= MAX_DEVICES) {
         *err = cudaErrorInvalidDevice;
         return nullptr;
     }
-    DevBase &b = g_base[dev];
-    std::call_once(b.once, [&] {
+    std::lock_guard<std::mutex> lk(g_base_mu);
+    if (!g_base[dev]) {
         void *p = nullptr;
-        b.err = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        b.ptr = (unsigned char *)p;
-    });
-    *err = b.err;
-    return b.err == cudaSuccess ? b.ptr : nullptr;
+        *err = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (*err != cudaSuccess) return nullptr;
+        g_base[dev] = (unsigned char *)p;
+    }
+    *err = cudaSuccess;
+    return g_base[dev];
 }
 
 }  // namespace

@@ -147,6 +147,7 @@ template <typename T, int TW_> struct SmemT {
     float red_hi[2][NPART][NWARP], red_lo[2][NPART][NWARP];   // per-warp partials, two buffers
     SysDesc sd[SMAX];
     SysState st[SMAX];
+    int32_t ph0[SMAX];      // phase of each system at the start of the step (step timing)
     int32_t tag_d, tag_f;   // tile whose coefficients are in cfd / cff
     int32_t go;
     uint32_t fills;         // TMA stage fills issued so far (stage = fill & 1)
@@ -1142,6 +1143,12 @@ __device__ void pass_final2(S &sm, const SysDesc &sd, const SysState &st, int i0
 
 __device__ __forceinline__ bool is_pass_phase(int ph) { return ph != PH_NET && ph != PH_DONE; }
 
+// max(v, 0) for a sum of squares that rounding may push below zero; a NaN
+// stays NaN, so that a non-finite vector surfaces as PPE_ERR_NAN instead of
+// reading as a zero norm
+__device__ __forceinline__ double nonneg(double v) { return v > 0.0 ? v : (v == v ? 0.0 : v); }
+__device__ __forceinline__ float nonneg(float v) { return v > 0.f ? v : (v == v ? 0.f : v); }
+
 __device__ __forceinline__ int iter_cap(const SysDesc &sd)
 {
     return sd.max_iters + (sd.mode == PPE_MODE_HYBRID ? sd.hybrid_budget : 0);
@@ -1163,11 +1170,15 @@ __device__ void advance(const SysDesc &sd, SysState &s, const double (&t)[NPART]
     case PH_INIT: {
         s.mu_b = t[0] * sd.inv_n;
         double bb = t[1] - N * s.mu_b * s.mu_b;
-        s.bnorm = sqrt(bb > 0.0 ? bb : 0.0);
+        s.bnorm = sqrt(nonneg(bb));
         s.incompat = t[2] > 0.0 ? fabs(t[0]) / t[2] : 0.0;
         s.cur = 0;
         s.pcur = 0;
-        if (!(s.incompat <= 1e-6)) {
+        if (!isfinite(t[0]) || !isfinite(t[1]) || !isfinite(t[2])) {
+            s.status = PPE_ERR_NAN;
+            s.relres = t[1];
+            s.phase = PH_FINAL1;
+        } else if (!(s.incompat <= 1e-6)) {
             s.status = PPE_ERR_INCOMPATIBLE_RHS;
             s.phase = PH_DONE;
         } else if (!(s.bnorm > 0.0)) {
@@ -1186,9 +1197,22 @@ __device__ void advance(const SysDesc &sd, SysState &s, const double (&t)[NPART]
         s.refinements++;
         s.mu = t[0] * sd.inv_n;
         double rr = t[1] - N * s.mu * s.mu;
-        s.rnorm = sqrt(rr > 0.0 ? rr : 0.0);
+        s.rnorm = sqrt(nonneg(rr));
         s.relres = fast_div(s.rnorm, s.bnorm);
         s.fold_d = s.has_d;
+        // mixed precision: an FP32 inner solve normally cuts the true residual
+        // by about inner_rtol; when the system's conditioning exceeds what
+        // FP32 resolves, the inner iteration stalls and the true residual
+        // stops falling.  Three refinements in a row that fail to halve it
+        // end the mixed solve (the host continues it in FP64).
+        if (sd.precision == PPE_PREC_MIXED && s.refinements > 1)
+            s.stall = s.relres > 0.5 * s.relres_prev ? s.stall + 1 : 0;
+        s.relres_prev = s.relres;
+        // the budget of an inner solve follows the last one that reached its
+        // reduction target (an overrun does not raise it)
+        if (s.it_rep > 0 && !s.overran) s.it_rep_prev = s.it_rep;
+        s.it_rep = 0;
+        s.overran = 0;
         if (!isfinite(s.relres)) {
             s.status = PPE_ERR_NAN;
             s.fold_d = 0;
@@ -1197,6 +1221,10 @@ __device__ void advance(const SysDesc &sd, SysState &s, const double (&t)[NPART]
             s.phase = PH_FINAL1;
         } else if (s.it_total >= iter_cap(sd) || s.refinements > 5000) {
             s.status = PPE_ERR_NOT_CONVERGED;
+            s.phase = PH_FINAL1;
+        } else if (s.stall >= 3) {
+            s.status = PPE_ERR_NOT_CONVERGED;
+            s.prec_stalled = 1;
             s.phase = PH_FINAL1;
         } else {
             s.rho_ref = s.rnorm;
@@ -1210,7 +1238,7 @@ __device__ void advance(const SysDesc &sd, SysState &s, const double (&t)[NPART]
         double dmu = t[3] * sd.inv_n;
         s.mu += dmu;
         double rr = t[2] - N * dmu * dmu;
-        s.rho = rr > 0.0 ? rr : 0.0;
+        s.rho = nonneg(rr);
         s.reset_d = 0;
         s.fold_d = 0;
         s.has_d = 1;
@@ -1254,7 +1282,7 @@ __device__ void advance(const SysDesc &sd, SysState &s, const double (&t)[NPART]
         s.pcur ^= 1;
         s.mu = t[3] * sd.inv_n;
         double rr = t[2] - N * s.mu * s.mu;
-        s.rho = rr > 0.0 ? rr : 0.0;
+        s.rho = nonneg(rr);
         s.first = 0;
         s.cg_count++;
         if (sd.mode == PPE_MODE_HYBRID && !s.fell_back && s.it_total >= sd.hybrid_budget) s.fell_back = 1;
@@ -1305,7 +1333,7 @@ __device__ void advance(const SysDesc &sd, SysState &s, const double (&t)[NPART]
         s.cur ^= 1;
         s.mu = t[3] * sd.inv_n;
         double rr = t[2] - N * s.mu * s.mu;
-        s.rho = rr > 0.0 ? rr : 0.0;
+        s.rho = nonneg(rr);
         // the step is worth its inference if it removed at least as much error
         // energy as dlsm_cost iterations of the CG phase before it (at their
         // mean); after several unprofitable steps in a row continue as plain PCG
@@ -1377,7 +1405,7 @@ __device__ void advance_iter_f32(const SysDesc &sd, SysState &s, const float (&h
     s.cg_count++;
     const float mu = (h[3] + l[3]) * sd.inv_n_f;
     const float rr = (h[2] + l[2]) - sd.n_cells_f * mu * mu;
-    const float rho = rr > 0.f ? rr : 0.f;
+    const float rho = nonneg(rr);
     s.mu_f = mu;
     s.rho_f = rho;
     s.mu = (double)mu;
@@ -1397,7 +1425,13 @@ __device__ void advance_iter_f32(const SysDesc &sd, SysState &s, const float (&h
     ff_add(wh, wl, h[1], l[1]);
     const float denom = wh + wl;
     const bool ok = denom > 0.f && isfinite(beta) && gnew > 0.f;
-    if (rho <= s.target_sq_f || s.it_total >= iter_cap(sd) || !ok || rho <= s.ru_sq_f) {
+    // an inner solve that runs far past the length of the previous one
+    // (2000 + 4x) ends with a residual replacement, so a stalled FP32
+    // iteration is noticed by the refinement's stall test
+    s.it_rep++;
+    const bool overrun = s.it_rep > 2000 + 4 * s.it_rep_prev;
+    s.overran = overrun && !(rho <= s.ru_sq_f);
+    if (rho <= s.target_sq_f || s.it_total >= iter_cap(sd) || !ok || rho <= s.ru_sq_f || overrun) {
         // gamma and alpha of the direction in use stay the reference for the
         // continuation after the residual replacement
         to_res(s, ok ? 1 : 0);
@@ -1534,13 +1568,18 @@ __global__ void __launch_bounds__(SOLVER_THREADS, 1)
     __syncthreads();
     if (threadIdx.x == 0 && resume_net)
         for (int q = 0; q < nq; ++q)
-            if (sm.st[q].phase == PH_NET) sm.st[q].phase = PH_DLSM_DOT;
+            if (sm.st[q].phase == PH_NET) {
+                sm.st[q].phase = PH_DLSM_DOT;
+                // the direction was computed since the segment that asked for it ended
+                if ((int)blockIdx.x == sm.sd[q].blk0) sm.st[q].ns_net += gtimer() - sm.st[q].t_net0;
+            }
     __syncthreads();
     const bool prof = a.prof && blockIdx.x == 0 && threadIdx.x == 0;
     // profile split of one step (block 0): pass, block reduce + publish,
     // wait for the other blocks, reduction of their records, state advance
     uint64_t t_a = prof ? gtimer() : 0, t_p = 0, t_b = 0, t_w = 0, t_r = 0, t_x = 0, t_c = 0;
     int red_par = 0;
+    uint64_t t_step = 0;
     for (uint32_t step = 1;; ++step) {
         // a step budget ends the launch at the same step in every block, so each
         // system stops between two of its steps
@@ -1550,6 +1589,10 @@ __global__ void __launch_bounds__(SOLVER_THREADS, 1)
         for (int q = 0; q < nq; ++q) any |= is_pass_phase(sm.st[q].phase);
         if (!any) break;
         const int bank = step & 1;
+        if (threadIdx.x == 0) {
+            t_step = gtimer();
+            for (int q = 0; q < nq; ++q) sm.ph0[q] = sm.st[q].phase;
+        }
         // 1) passes; publish one record per live system
         for (int q = 0; q < nq; ++q) {
             const SysDesc &sd = sm.sd[q];
@@ -1566,6 +1609,9 @@ __global__ void __launch_bounds__(SOLVER_THREADS, 1)
             } else
                 for (int t = lo_t; t < hi_t; ++t) run_pass<T>(sm, q, ph, t, acc);
             if (prof && q == 0) t_p = gtimer();
+            // test hook: one block withholds its record once, so that the other
+            // blocks' bounded waits expire (the failure path of the barrier)
+            if (a.skip_block == (int)blockIdx.x + 1 && step == 2) continue;
             Slot *slot = a.slots + (size_t)bank * a.nslots + sd.part0 + (blockIdx.x - sd.blk0);
             block_publish(sm, acc, slot, a.arrive + br.s0 + q, red_par);
             red_par ^= 1;
@@ -1663,6 +1709,21 @@ __global__ void __launch_bounds__(SOLVER_THREADS, 1)
         }
         __syncthreads();
         if (!sm.go) return;                             // a bounded wait expired: leave without writing state
+        if (threadIdx.x == 0) {
+            // the step's device time, charged by each system's first block to the
+            // kind of pass the system ran
+            const uint64_t dt = gtimer() - t_step;
+            for (int q = 0; q < nq; ++q) {
+                if ((int)blockIdx.x != sm.sd[q].blk0) continue;
+                const int ph = sm.ph0[q];
+                if (ph == PH_ITER || ph == PH_RESTART)
+                    sm.st[q].ns_pcg += dt;
+                else if (ph == PH_DLSM_DOT || ph == PH_DLSM_UPD)
+                    sm.st[q].ns_dlsm += dt;
+                else if (is_pass_phase(ph))
+                    sm.st[q].ns_fp64 += dt;
+            }
+        }
         if (prof) {
             t_c = gtimer();
             if (t_p && t_w && t_r) {
@@ -1678,6 +1739,11 @@ __global__ void __launch_bounds__(SOLVER_THREADS, 1)
             t_a = t_c;
         }
     }
+    // a system that waits for a network direction starts its network clock
+    if (threadIdx.x == 0)
+        for (int q = 0; q < nq; ++q)
+            if ((int)blockIdx.x == sm.sd[q].blk0 && sm.st[q].phase == PH_NET) sm.st[q].t_net0 = gtimer();
+    __syncthreads();
     // write back the states of the systems this block owns
     for (int q = 0; q < nq; ++q) {
         if ((int)blockIdx.x != sm.sd[q].blk0) continue;
@@ -1696,20 +1762,6 @@ size_t solver_smem(SolverVariant v)
     }
 }
 
-// The dynamic shared-memory opt-in is a per-function attribute: set it once.
-void set_solver_attributes()
-{
-    static std::once_flag once;
-    std::call_once(once, [] {
-        cudaFuncSetAttribute(solver_kernel<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)solver_smem(SV_FP64));
-        cudaFuncSetAttribute(solver_kernel<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)solver_smem(SV_FP32_TILE));
-        cudaFuncSetAttribute(solver_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)solver_smem(SV_FP32_STREAM));
-    });
-}
-
 const void *solver_fn(SolverVariant v)
 {
     switch (v) {
@@ -1721,6 +1773,24 @@ const void *solver_fn(SolverVariant v)
 
 
 }  // namespace
+
+// The dynamic shared-memory opt-in is a per-function attribute of each
+// device: set it once per device.
+void set_solver_attributes()
+{
+    static PerDevice pd;
+    once_per_device(pd, [](int) {
+        return cudaFuncSetAttribute(solver_kernel<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)solver_smem(SV_FP64)) == cudaSuccess &&
+               cudaFuncSetAttribute(solver_kernel<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)solver_smem(SV_FP32_TILE)) == cudaSuccess &&
+               cudaFuncSetAttribute(solver_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)solver_smem(SV_FP32_STREAM)) == cudaSuccess;
+    });
+}
+
+const void *solver_kernel_fn(SolverVariant v) { return solver_fn(v); }
+size_t solver_smem_bytes(SolverVariant v) { return solver_smem(v); }
 
 int solver_max_blocks(SolverVariant v, int blocks_per_sm_req)
 {

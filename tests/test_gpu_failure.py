@@ -1,0 +1,106 @@
+"""Failure paths, made to happen without faulting the GPU.
+
+* Bounded barrier wait: a test hook makes one block of the persistent solver
+  kernel withhold its partial sums once.  The other blocks' waits (bounded
+  by spin_limit_ms) expire; every block returns, and the solve reports
+  PPE_ERR_TIMEOUT, in both drivers.  The grid then solves normally.
+* Non-finite input: a NaN in the initial guess makes the FP64 true residual
+  non-finite, which ends the solve with PPE_ERR_NAN.
+* Non-finite DLSM direction: the curvature guard (e.Ae compared with
+  guard * e.e * max diag) rejects it; the solve goes on with CG and reaches
+  the oracle's solution.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from paper_2604_01800_gb300 import inputs as I  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-8
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_01800_gb300 import api as A
+    return A
+
+
+def _dev(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+@pytest.mark.parametrize("host_loop", [0, 1])
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_withheld_record_times_out(api, host_loop, prec):
+    w = I.config3(0)                               # 256^2: 32 tiles, so several blocks share the system
+    p = api.PPE_PREC_MIXED if prec == "mixed" else api.PPE_PREC_FP64
+    grid = api.ppe_create_grid(w.dx, w.dy)
+    api.ppe_set_options(grid, debug_skip_block=2, spin_limit_ms=20, host_loop=host_loop)
+    x = torch.zeros(w.ny, w.nx, dtype=torch.float64, device="cuda")
+    info = api.ppe_solve(grid, _dev(w.f), x, TOL, api.PPE_MODE_PCG, p, raise_on_error=False)
+    assert info["status"] == api._lib.PPE_ERR_TIMEOUT, info
+    assert b"wait expired" in api._lib.load().ppe_last_error()
+    torch.cuda.synchronize()                       # the context is intact
+    api.ppe_set_options(grid, host_loop=host_loop)
+    info = api.ppe_solve(grid, _dev(w.f), x, TOL, api.PPE_MODE_PCG, p)
+    assert info["status"] == 0
+    assert oracle.true_relres(w.dx, w.dy, w.f, x.cpu().numpy()) <= TOL * 1.05
+
+
+def test_nan_initial_guess_reports_nan(api):
+    w = I.config1(1)
+    grid = api.ppe_create_grid(w.dx, w.dy)
+    x = torch.zeros(w.ny, w.nx, dtype=torch.float64, device="cuda")
+    x[5, 7] = float("nan")
+    info = api.ppe_solve(grid, _dev(w.f), x, TOL, api.PPE_MODE_PCG, api.PPE_PREC_MIXED, raise_on_error=False)
+    assert info["status"] == api._lib.PPE_ERR_NAN, info
+    x.zero_()
+    assert api.ppe_solve(grid, _dev(w.f), x, TOL, api.PPE_MODE_PCG, api.PPE_PREC_MIXED)["status"] == 0
+
+
+def test_nan_direction_is_rejected(api):
+    w = I.config1(2)
+    xo, _, _ = oracle.solve(w.dx, w.dy, w.f, tol_rel=1e-11)
+    grid = api.ppe_create_grid(w.dx, w.dy)
+    api.ppe_set_options(grid, hybrid_budget=40)
+
+    def nan_source(r, e, stream):
+        e.fill_(float("nan"))
+
+    api.ppe_set_direction_source(grid, nan_source)
+    x = torch.zeros(w.ny, w.nx, dtype=torch.float64, device="cuda")
+    info = api.ppe_solve(grid, _dev(w.f), x, TOL, api.PPE_MODE_HYBRID, api.PPE_PREC_MIXED)
+    assert info["status"] == 0 and info["dlsm_skipped"] >= 1 and info["iters_dlsm"] == 0, info
+    xg = x.cpu().numpy()
+    assert oracle.true_relres(w.dx, w.dy, w.f, xg) <= TOL * 1.05
+    assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-6
+
+
+@pytest.mark.parametrize("shape", [(4096, 16), (16, 4096)])
+def test_stalled_mixed_solve_continues_in_fp64(api, shape):
+    """A long strip: the FP64 Jacobi-PCG needs ~30,000 iterations, and FP32
+    inner iterations cannot resolve the system (they stall).  The mixed solve
+    notices (refinements that stop halving the true residual) and continues
+    in FP64 from its iterate, reaching the tolerance."""
+    g = I.rng(43)
+    nx, ny = shape
+    dx, dy = I.random_spacing(nx, g), I.random_spacing(ny, g)
+    f = I.gaussian_rhs(dx, dy, g, 6)
+    grid = api.ppe_create_grid(dx, dy)
+    x = torch.zeros(ny, nx, dtype=torch.float64, device="cuda")
+    info = api.ppe_solve(grid, _dev(f), x, TOL, api.PPE_MODE_PCG, api.PPE_PREC_MIXED)
+    assert info["status"] == 0 and info["precision_fallback"] == 1, info
+    assert oracle.true_relres(dx, dy, f, x.cpu().numpy()) <= TOL * 1.05
+
+
+def test_well_conditioned_mixed_solve_stays_mixed(api):
+    w = I.config2(0)
+    grid = api.ppe_create_grid(w.dx, w.dy)
+    x = torch.zeros(w.ny, w.nx, dtype=torch.float64, device="cuda")
+    info = api.ppe_solve(grid, _dev(w.f), x, TOL, api.PPE_MODE_PCG, api.PPE_PREC_MIXED)
+    assert info["status"] == 0 and info["precision_fallback"] == 0, info

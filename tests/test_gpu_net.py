@@ -57,9 +57,15 @@ def _conv_case(api, B, H, W, cin, cout, impl, seed):
     assert np.all(err <= 1e-5 * scale + 1e-6), float((err / (scale + 1e-30)).max())
 
 
+# The last two shapes have far more output tiles (of 128 pixels) than the
+# kernel has CTAs (one or two per SM): 1,024 and 512 tiles, so every CTA walks
+# several tiles, alternating its two TMEM accumulators and carrying the stage
+# ring's phases from tile to tile, as at the full 256^2 and 512^2 sizes.  They
+# cover both channel-block widths of the kernel (32- and 64-channel blocks).
 @pytest.mark.parametrize("B,H,W,cin,cout", [(1, 16, 16, 16, 16), (2, 13, 21, 32, 48), (1, 8, 40, 64, 32),
                                              (1, 32, 32, 256, 128), (2, 64, 64, 64, 256), (1, 7, 9, 16, 16),
-                                             (3, 24, 40, 128, 64), (1, 256, 8, 32, 32)])
+                                             (3, 24, 40, 128, 64), (1, 256, 8, 32, 32), (2, 256, 256, 32, 32),
+                                             (1, 256, 256, 64, 64)])
 @pytest.mark.parametrize("impl", [0, 1], ids=["tcgen05", "simt"])
 def test_conv_matches_oracle(api, B, H, W, cin, cout, impl):
     _conv_case(api, B, H, W, cin, cout, impl, 100 + H)
@@ -84,10 +90,14 @@ def _make_net(api, cfg, seed, phi_scale=0.5):
     return net, P
 
 
+# "conv": the standard-convolution ablation of Sec. 3 (mesh_conv = 0, eta = 1
+# in every layer), against the oracle's forward with the same switch.
 @pytest.mark.parametrize("cfgname,nx,ny,B", [("tiny", 29, 21, 2), ("tiny", 32, 32, 1), ("full", 64, 48, 1),
-                                             ("full", 50, 70, 2)])
+                                             ("full", 50, 70, 2), ("conv", 29, 21, 2), ("fullconv", 64, 48, 1)])
 def test_forward_matches_oracle(api, cfgname, nx, ny, B):
-    cfg = _tiny_cfg() if cfgname == "tiny" else I.NetConfig()
+    cfg = {"tiny": _tiny_cfg(), "full": I.NetConfig(),
+           "conv": I.NetConfig(widths=(16, 32), c_last=8, trunk=(16, 24), phi_hidden=4, mesh_conv=False),
+           "fullconv": I.NetConfig(mesh_conv=False)}[cfgname]
     net, P = _make_net(api, cfg, 3)
     g = I.rng(11)
     dx, dy = I.random_spacing(nx, g), I.random_spacing(ny, g)
@@ -123,3 +133,26 @@ def test_weights_file_roundtrip(api, tmp_path):
     with pytest.raises(api.PPEError) as ei:
         api.net_load(str(bad))
     assert ei.value.status == api._lib.PPE_ERR_FORMAT
+
+
+def test_forward_full_config_on_cylinder_grid(api):
+    """The full 32-256 network on the 256^2 cylinder grid: every layer runs at
+    its full size (the 256^2 layers walk several tiles per CTA), checked
+    element by element against the oracle's forward pass."""
+    cfg = I.NetConfig()
+    net, P = _make_net(api, cfg, 3)
+    w = I.config3(0)
+    g = I.rng(19)
+    R = g.standard_normal((1, w.ny, w.nx)).astype(np.float32)
+    grid = api.ppe_create_grid(w.dx, w.dy)
+    net.attach(grid)
+    r = torch.tensor(R, dtype=torch.float32, device="cuda")
+    e = torch.zeros_like(r)
+    net.infer(grid, r, e)
+    torch.cuda.synchronize()
+    geo = N.Geometry(w.dx, w.dy, cfg.levels)
+    eo, _ = N.forward(P, geo, R.astype(np.float64), cfg.widths, cfg.mesh_conv, len(cfg.trunk) + 1)
+    eg = e.cpu().numpy().astype(np.float64)
+    rel = np.linalg.norm(eg - eo) / np.linalg.norm(eo)
+    cos = (eg * eo).sum() / np.linalg.norm(eg) / np.linalg.norm(eo)
+    assert rel <= 3e-2 and cos >= 0.999, (rel, cos)

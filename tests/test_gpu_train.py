@@ -3,9 +3,13 @@
 Loss (Eq. 18) and gradients come from the hand-written forward/backward
 kernels with BF16 activations and weights (relative rounding 2^-9 per
 layer) and FP32 accumulation, so the bars are those of a BF16 network: loss
-within 2e-2 relative, whole-gradient relative L2 error within 5e-2 and
+within 2e-2 relative, whole-gradient relative L2 error within 2e-2 and
 cosine >= 0.995, and the direction of every parameter tensor with a
-non-negligible gradient within cosine 0.98.  One SAM + Adam step moves every
+non-negligible gradient within cosine 0.98.  The gradient bar follows from
+the same ~2^-9 per-layer rounding compounded over the backward pass's
+depth, which sits at about 1.3e-2 for the full 32-256 network at 128^2.
+There is no FP32 network path to hold to a tighter bar: every contraction
+of the network runs with BF16 operands.  One SAM + Adam step moves every
 parameter whose gradient is large in the same direction as the oracle's step.
 """
 import numpy as np
@@ -57,9 +61,20 @@ def _oracle_loss_grad(P, cfg, dx, dy, R):
     return N.loss_and_grads(P, geo, A, R.astype(np.float64), cfg.widths, cfg.mesh_conv, len(cfg.trunk) + 1)
 
 
-@pytest.mark.parametrize("cfgname,nx,ny,B", [("tiny", 29, 21, 2), ("tiny", 32, 32, 1), ("full", 32, 48, 1)])
+# "wide96": widths (32, 96), so the weight gradient's 64-channel blocks of
+# output channels end in a partly filled block (zero-filled loads beyond
+# Cout, skipped stores), on an unpadded grid: on a padded one the loss
+# gradient A (R - A e) amplifies the BF16 error of e at the crop boundary
+# twice by A, which the wider layers' larger rounding makes visible; "full"
+# at 128^2 runs the data gradients through the tensor-core kernel with
+# several tiles per CTA.
+WIDE96 = I.NetConfig(widths=(32, 96), c_last=8, trunk=(16, 24), phi_hidden=4)
+
+
+@pytest.mark.parametrize("cfgname,nx,ny,B", [("tiny", 29, 21, 2), ("tiny", 32, 32, 1), ("full", 32, 48, 1),
+                                             ("wide96", 32, 32, 2), ("full", 128, 128, 1)])
 def test_loss_and_gradient_match_oracle(api, cfgname, nx, ny, B):
-    cfg = TINY if cfgname == "tiny" else I.NetConfig()
+    cfg = {"tiny": TINY, "wide96": WIDE96, "full": I.NetConfig()}[cfgname]
     net, P, grid, dx, dy, R = _setup(api, cfg, nx, ny, B, 7)
     loss, g = net.loss_grad(grid, torch.tensor(R, dtype=torch.float32, device="cuda"))
     Lo, go = _oracle_loss_grad(P, cfg, dx, dy, R)
@@ -68,7 +83,7 @@ def test_loss_and_gradient_match_oracle(api, cfgname, nx, ny, B):
     flat_o = np.concatenate([go[k].reshape(-1) for k in I.net_param_shapes(cfg)])
     rel = np.linalg.norm(g - flat_o) / np.linalg.norm(flat_o)
     cos = g @ flat_o / np.linalg.norm(g) / np.linalg.norm(flat_o)
-    assert rel <= 5e-2 and cos >= 0.995, (rel, cos)
+    assert rel <= 2e-2 and cos >= 0.995, (rel, cos)
     big = np.linalg.norm(flat_o) * 1e-3
     for k in I.net_param_shapes(cfg):
         a, b = G[k].reshape(-1).astype(np.float64), go[k].reshape(-1)
@@ -101,10 +116,13 @@ def test_train_step_matches_oracle_direction(api):
 
 
 def test_training_reduces_loss(api):
+    """150 steps on a fixed batch halve the loss (measured: 0.43 of the first
+    step's).  A 60-step schedule stops at 0.51: the cosine decay has the
+    learning rate near zero for its last third."""
     net, P, grid, dx, dy, R = _setup(api, TINY, 32, 32, 4, 13)
     Rt = torch.tensor(R, dtype=torch.float32, device="cuda")
-    losses = [net.train_step(grid, Rt, lr0=2e-3, total_steps=60, rho=2e-4) for _ in range(60)]
-    assert losses[-1] < 0.6 * losses[0], (losses[0], losses[-1])
+    losses = [net.train_step(grid, Rt, lr0=2e-3, total_steps=150, rho=2e-4) for _ in range(150)]
+    assert losses[-1] < 0.5 * losses[0], (losses[0], losses[-1])
     assert all(np.isfinite(losses))
 
 

@@ -67,6 +67,33 @@ def test_noalloc_matches_regular_solve_twice(api, prec):
         assert np.linalg.norm(a - b) / np.linalg.norm(b) <= SOL_TOL
 
 
+@pytest.mark.parametrize("prec,shapes", [("mixed", ((256, 256), (512, 128))),
+                                         ("fp64", ((256, 256), (4096, 16), (17, 3855)))])
+def test_noalloc_at_the_size_limits(api, prec, shapes):
+    """Grids that fill the fixed array, two or three calls in a row: 65,536
+    cells as 256 x 256; a 4096 x 16 strip whose rows reach the width limit;
+    and 17 x 3855, whose rows pad from 17 to 20 cells, so that the padded
+    vectors come closest to their bound.  The long strips need tens of
+    thousands of Jacobi-PCG iterations even in FP64 (the oracle takes 27,212
+    on the 4096 x 16 one): there FP32 inner iterations stall whatever the
+    entry point (ppe_solve then continues in FP64; this entry point reports
+    PPE_ERR_NOT_CONVERGED), so mixed precision runs the 256 x 256 grid and a
+    512 x 128 one."""
+    p = api.PPE_PREC_MIXED if prec == "mixed" else api.PPE_PREC_FP64
+    for k, (nx, ny) in enumerate(shapes):
+        w = _ragged(nx, ny, 41 + 2 * k)
+        grid = api.ppe_create_grid(w.dx, w.dy)
+        x_ref = torch.zeros(w.ny, w.nx, dtype=torch.float64, device="cuda")
+        api.ppe_solve(grid, torch.tensor(w.f, dtype=torch.float64, device="cuda"), x_ref, RES_TOL,
+                      api.PPE_MODE_PCG, p)
+        x = torch.zeros((w.ny, w.nx), dtype=torch.float64, device="cuda")
+        st, info = _noalloc(api, w, x, p)
+        assert st == 0, api._lib.load().ppe_last_error()
+        assert info.status == 0 and info.rel_res_true <= RES_TOL
+        a, b = x.cpu().numpy(), x_ref.cpu().numpy()
+        assert np.linalg.norm(a - b) / np.linalg.norm(b) <= SOL_TOL
+
+
 def test_noalloc_rejects_oversized_grid(api):
     n = 300                                             # 90000 cells > 65536
     w = I.Workload("big", I.uniform_spacing(n), I.uniform_spacing(n), np.zeros((n, n)))
