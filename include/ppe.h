@@ -137,7 +137,18 @@ typedef struct {
     int32_t debug_skip_block; /* test hook, 0 = off: block debug_skip_block - 1 of the solver
                                kernel withholds its partial sums at its second step, so the
                                other blocks' bounded waits expire (PPE_ERR_TIMEOUT)           */
-    int32_t reserved[5];
+    int32_t preconditioner; /* CG-type partner of PPE_MODE_PCG (Sec. 2.6): 0 = Jacobi (default);
+                               1 = multigrid (the paper's MGPCG analogue on the tensor grid): CG
+                               preconditioned by one V-cycle per iteration -- cells merged
+                               pairwise per axis, the operator re-discretised on every level,
+                               linear prolongation with restriction its transpose, damped
+                               alternating line-Jacobi smoothing, pseudo-inverse on a coarsest
+                               level of at most 256 cells.  Runs FP32 inner iterations with
+                               FP64 refinement (PPE_PREC_MIXED); single systems only
+                               (ppe_solve; PPE_ERR_ARG for hybrid mode, FP64 precision or a
+                               batch).  The hierarchy is built on the grid's first multigrid
+                               solve (allocates; later solves reuse it).                     */
+    int32_t reserved[4];
 } ppe_solve_opts;
 
 PPE_API void ppe_default_options(ppe_solve_opts *opts);
@@ -169,6 +180,27 @@ PPE_API ppe_status ppe_apply(ppe_grid *grid, const double *x_dev, double *y_dev,
  * source S and iterate x.  All device [ny][nx]; r may not alias S or x. */
 PPE_API ppe_status ppe_residual(ppe_grid *grid, const double *S_dev, const double *x_dev, double *r_dev,
                                 void *stream);
+
+/*
+ * The projection step around the PPE (Sec. 2.1 Eqs. 6-8) on the staggered
+ * grid: u device [ny][nx+1] (x faces; face i of row j lies between cells i-1
+ * and i), v device [ny+1][nx] (y faces), FP64.  The wall faces hold the
+ * prescribed normal velocity.
+ *   ppe_source:  S = (D u* - bc2) / dt, the PPE source of Eq. 6 (device
+ *                [ny][nx]): the whole divergence of u* over dt, the wall faces'
+ *                prescribed normal velocity (the bc2 part) included.  It is
+ *                compatible when the net flux through the walls vanishes.
+ *   ppe_project: u <- u - dt G dp, v <- v - dt G dp on the interior faces
+ *                (Eq. 7) and, if p is not NULL, p <- p + dp (Eq. 8).  The wall
+ *                faces are not changed.
+ * D G equals the operator M that ppe_solve inverts, so after ppe_solve on S
+ * and ppe_project the interior divergence of (u, v) vanishes to the solve's
+ * tolerance.  Kernels on `stream`; no synchronisation.  dt > 0.
+ */
+PPE_API ppe_status ppe_source(ppe_grid *grid, const double *u_dev, const double *v_dev, double dt, double *S_dev,
+                              void *stream);
+PPE_API ppe_status ppe_project(ppe_grid *grid, const double *dp_dev, double dt, double *u_dev, double *v_dev,
+                               double *p_dev, void *stream);
 
 /*
  * Solve M x = S (Eq. 10) to ||P(b - A x)|| <= tol_rel * ||P b||.
@@ -346,6 +378,11 @@ PPE_API ppe_status net_loss_grad(ppe_net *net, ppe_grid *grid, int batch, const 
                                  double *loss_out, float *grad_host);
 /* Number of optimiser steps taken (the t of the schedule). */
 PPE_API ppe_status net_get_step(const ppe_net *net, int64_t *step);
+
+/* Test hook: one V-cycle of the multigrid partner (see ppe_solve_opts.preconditioner)
+ * applied to r (device FP32 [ny][nx], zero sum); z (device FP32 [ny][nx]) receives it.
+ * Builds the grid's hierarchy on first use. */
+PPE_API ppe_status ppe_debug_mg_vcycle(ppe_grid *grid, const float *r_dev, float *z_dev, void *stream);
 
 /* Test hook: one 3x3 convolution (zero padding 1, no activation) of a BF16
  * NHWC input in_bf16 [B][H][W][cin] with packed BF16 weights

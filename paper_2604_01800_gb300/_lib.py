@@ -15,6 +15,7 @@ _lib = None
 PPE_OK, PPE_ERR_ARG, PPE_ERR_CUDA, PPE_ERR_NOMEM, PPE_ERR_INCOMPATIBLE_RHS = 0, 1, 2, 3, 4
 PPE_ERR_NOT_CONVERGED, PPE_ERR_TIMEOUT, PPE_ERR_NAN, PPE_ERR_NO_NET, PPE_ERR_FORMAT = 5, 6, 7, 8, 9
 PPE_MODE_PCG, PPE_MODE_HYBRID = 0, 1
+PPE_PRECOND_JACOBI, PPE_PRECOND_MG = 0, 1
 PPE_PREC_FP64, PPE_PREC_MIXED = 0, 1
 PPE_BC_NEUMANN = 0
 
@@ -41,7 +42,8 @@ class ppe_solve_opts(ctypes.Structure):
                 ("blocks_per_sm", ctypes.c_int32), ("keep_dir_after_dlsm", ctypes.c_int32),
                 ("iter_pass", ctypes.c_int32), ("dlsm_stall_limit", ctypes.c_int32),
                 ("dlsm_cost_iters", ctypes.c_int32), ("spin_limit_ms", ctypes.c_int32), ("host_loop", ctypes.c_int32),
-                ("debug_skip_block", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("debug_skip_block", ctypes.c_int32), ("preconditioner", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class ppe_tune_report(ctypes.Structure):
@@ -110,6 +112,9 @@ _SIGS = [
     ("ppe_solve_noalloc", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, ctypes.c_double, ctypes.c_int,
                                          _P, ctypes.POINTER(ppe_solve_info)]),
     ("ppe_autotune", ctypes.c_int, [_P, _P, ctypes.POINTER(ppe_tune_report)]),
+    ("ppe_debug_mg_vcycle", ctypes.c_int, [_P, _P, _P, _P]),
+    ("ppe_source", ctypes.c_int, [_P, _P, _P, ctypes.c_double, _P, _P]),
+    ("ppe_project", ctypes.c_int, [_P, _P, ctypes.c_double, _P, _P, _P, _P]),
     ("ppe_last_error", ctypes.c_char_p, []),
     ("ppe_version", ctypes.c_char_p, []),
 ]

@@ -144,6 +144,22 @@ def ppe_residual(grid: Grid, S: torch.Tensor, x: torch.Tensor, r: torch.Tensor, 
     return r
 
 
+def ppe_source(grid: Grid, u: torch.Tensor, v: torch.Tensor, dt: float, S: torch.Tensor, stream=None):
+    """S = (D u* - bc2) / dt from the staggered faces u [ny, nx+1], v [ny+1, nx] (Eq. 6)."""
+    nx, ny = grid.nx, grid.ny
+    check(_lib.load().ppe_source(grid.handle, _dptr(u, numel=ny * (nx + 1)), _dptr(v, numel=(ny + 1) * nx),
+                                 float(dt), _dptr(S, numel=nx * ny), _stream(stream)), "ppe_source")
+    return S
+
+
+def ppe_project(grid: Grid, dp: torch.Tensor, dt: float, u: torch.Tensor, v: torch.Tensor, p=None, stream=None):
+    """u, v <- u, v - dt G dp on the interior faces (Eq. 7); p <- p + dp (Eq. 8)."""
+    nx, ny = grid.nx, grid.ny
+    pp = None if p is None else _dptr(p, numel=nx * ny)
+    check(_lib.load().ppe_project(grid.handle, _dptr(dp, numel=nx * ny), float(dt), _dptr(u, numel=ny * (nx + 1)),
+                                  _dptr(v, numel=(ny + 1) * nx), pp, _stream(stream)), "ppe_project")
+
+
 def ppe_solve(grid: Grid, rhs: torch.Tensor, x: torch.Tensor, tol_rel: float = 1e-8, mode: int = PPE_MODE_PCG,
               precision: int = PPE_PREC_MIXED, net=None, stream=None, raise_on_error: bool = True) -> dict:
     """Solve M x = rhs in place of ``x``; returns the info report as a dict."""

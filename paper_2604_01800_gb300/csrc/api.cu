@@ -152,6 +152,7 @@ void ppe_destroy_grid(ppe_grid *g)
     cudaFree(g->vec); cudaFree(g->e); cudaFree(g->tmaps_dev); cudaFree(g->dir_part);
     cudaFree(g->ycoef);
     launch_set_destroy(g->ls);
+    mg_plan_destroy(g->mg);
     cudaFree(g->dir_r); cudaFree(g->dir_e);
     delete g;
 }
@@ -274,7 +275,7 @@ ppe_status ppe_set_options(ppe_grid *g, const ppe_solve_opts *o)
         !(o->inner_rtol > 0.0 && o->inner_rtol < 1.0) || !(o->dlsm_guard >= 0.0) || o->blocks_per_sm < 0 ||
         o->iter_pass < 0 || o->iter_pass > 2 || o->dlsm_stall_limit < 0 ||
         o->dlsm_cost_iters < 0 || o->spin_limit_ms < 0 || o->host_loop < 0 || o->host_loop > 1 ||
-        o->debug_skip_block < 0)
+        o->debug_skip_block < 0 || o->preconditioner < 0 || o->preconditioner > 1)
         return arg_error("ppe_set_options: option out of range");
     g->opts = *o;
     return PPE_OK;

@@ -747,6 +747,12 @@ ppe_status ppe_solve(ppe_grid *g, const double *rhs, double *x, double tol, ppe_
     clear_error();
     PPE_TRY(check_solve_args(g, rhs, x, tol, mode, prec, net));
     cudaStream_t st = (cudaStream_t)stream;
+    if (g->opts.preconditioner == 1) {
+        // the multigrid partner (plain PCG, FP32 inner with FP64 refinement)
+        if (mode != PPE_MODE_PCG || prec != PPE_PREC_MIXED)
+            return arg_error("ppe_solve: the multigrid partner runs PPE_MODE_PCG in PPE_PREC_MIXED");
+        return mg_solve(g, rhs, x, tol, st, info);
+    }
     ppe_solve_info a;
     std::memset(&a, 0, sizeof a);
     ppe_status status = solve_single(g, rhs, x, tol, mode, prec, net, st, &a);
@@ -772,6 +778,9 @@ ppe_status ppe_solve_batch(int n, ppe_grid *const *grids, const double *const *r
     for (int i = 0; i < n; ++i)
         for (int k = 0; k < i; ++k)
             if (grids[i] == grids[k]) return arg_error("ppe_solve_batch: a grid handle may appear only once");
+    for (int i = 0; i < n; ++i)
+        if (grids[i]->opts.preconditioner != 0)
+            return arg_error("ppe_solve_batch: batches run the Jacobi partner (preconditioner 0)");
     cudaStream_t st = (cudaStream_t)stream;
     int ntiles = 0;
     for (int i = 0; i < n; ++i) ntiles += grids[i]->tiles_x * grids[i]->tiles_y;

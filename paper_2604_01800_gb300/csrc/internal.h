@@ -311,6 +311,14 @@ struct LaunchSet {
 ppe_status launch_set_create(int n, int max_ranges, int slot_cap, LaunchSet **out);
 void launch_set_destroy(LaunchSet *ls);
 
+// The multigrid partner (mg.cu): hierarchy and buffers of a grid, built on
+// its first multigrid solve; the solve itself (FP32 inner MG-PCG, FP64
+// refinement).
+struct MgPlan;
+void mg_plan_destroy(MgPlan *m);
+ppe_status mg_solve(ppe_grid *g, const double *rhs, double *x, double tol, cudaStream_t stream,
+                    ppe_solve_info *info);
+
 }  // namespace ppe
 
 // The grid handle (opaque in the public header).
@@ -333,6 +341,7 @@ struct ppe_grid {
     int tuned_pass = 0, tuned_bps = 0;   // ppe_autotune's choice (0: none)
     uint64_t id = 0;                     // process-unique creation number (keys cached batch plans)
     ppe::LaunchSet *ls = nullptr;        // single-system launch resources and the solve graph
+    ppe::MgPlan *mg = nullptr;           // multigrid hierarchy (first multigrid solve)
     ppe_direction_fn dir_fn = nullptr;   // user direction source (replaces the network)
     void *dir_user = nullptr;
     float *dir_r = nullptr, *dir_e = nullptr;   // [ny][nx] staging for dir_fn

@@ -388,9 +388,20 @@ def _masked_indicator(bodies, xs, ys, hfun, reach=0.05):
 def config5_rhs(t: int, dx, dy, bodies, strouhal: float = 0.165,
                 dt: float = 0.05) -> np.ndarray:
     """Time-sequence stand-in for the flow solver's PPE source at step ``t``:
-    masked divergence of a uniform stream carrying a row of alternating
-    Gaussian vortices advected downstream with Strouhal number 0.165, plus a
-    small seeded perturbation (seed 5000 + t)."""
+    masked divergence of the intermediate velocity of ``config5_velocity``."""
+    u, v = config5_velocity(t, dx, dy, bodies, strouhal, dt)
+    div = (u[:, 1:] - u[:, :-1]) / dx[None, :] + (v[1:, :] - v[:-1, :]) / dy[:, None]
+    return _zero_volume_mean(div, dx, dy)
+
+
+def config5_velocity(t: int, dx, dy, bodies, strouhal: float = 0.165, dt: float = 0.05):
+    """Stand-in for the intermediate velocity u* of step ``t`` (the momentum
+    and immersed-boundary steps, Eqs. 3-5, are not part of this library): a
+    uniform stream carrying a row of alternating Gaussian vortices advected
+    downstream with Strouhal number 0.165, plus a small seeded perturbation
+    (seed 5000 + t), masked by the smoothed body indicator.  Staggered faces:
+    u [ny, nx+1], v [ny+1, nx]; the stream enters and leaves through the left
+    and right walls with equal fluxes."""
     g = rng(5000 + t)
     lx = dx.sum()
     xf = np.concatenate([[0.0], np.cumsum(dx)])
@@ -423,8 +434,9 @@ def config5_rhs(t: int, dx, dy, bodies, strouhal: float = 0.165,
     wy = np.concatenate([[dy[0]], 0.5 * (dy[:-1] + dy[1:]), [dy[-1]]])
     u *= 1.0 - _masked_indicator(bodies, xf, yc, lambda J, I_: np.sqrt(np.outer(dy[J], wx[I_])))
     v *= 1.0 - _masked_indicator(bodies, xc, yf, lambda J, I_: np.sqrt(np.outer(wy[J], dx[I_])))
-    div = (u[:, 1:] - u[:, :-1]) / dx[None, :] + (v[1:, :] - v[:-1, :]) / dy[:, None]
-    return _zero_volume_mean(div, dx, dy)
+    u[:, -1] = u[:, 0]                        # outflow = inflow: the walls' net flux vanishes
+    v[0, :] = v[-1, :] = 0.0
+    return u, v
 
 
 def training_rhs(dx, dy, g: np.random.Generator) -> np.ndarray:

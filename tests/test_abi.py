@@ -54,7 +54,7 @@ def test_struct_layouts_agree_with_the_header():
     assert (o.inner_rtol, o.dlsm_guard) == (0.3, 1e-10)
     assert (o.blocks_per_sm, o.keep_dir_after_dlsm, o.iter_pass) == (2, 0, 0)
     assert (o.dlsm_stall_limit, o.dlsm_cost_iters) == (6, 16)
-    assert (o.spin_limit_ms, o.host_loop, o.debug_skip_block) == (2000, 0, 0)
+    assert (o.spin_limit_ms, o.host_loop, o.debug_skip_block, o.preconditioner) == (2000, 0, 0, 0)
     assert list(o.reserved) == [0] * len(o.reserved)
     c = _lib.ppe_net_config()
     L.net_default_config(ctypes.byref(c))
