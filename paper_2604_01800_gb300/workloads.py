@@ -4,6 +4,8 @@
     python -m paper_2604_01800_gb300.workloads capped N ITS  # N x N box grid, mixed PCG capped at ITS iterations
     python -m paper_2604_01800_gb300.workloads infer         # network inference on the 256x256 cylinder grid
     python -m paper_2604_01800_gb300.workloads train N STEPS # training steps, batch 8 on an N x N stretched grid
+    python -m paper_2604_01800_gb300.workloads hybrid        # hybrid solve (shipped network) on the 256x256 cylinder grid
+    python -m paper_2604_01800_gb300.workloads mg NAME       # multigrid-partner solve: c1, c2, c3 or c5
 
 Each runs its solve (or inference) twice or more: the first launch warms up,
 so a profiler can skip it (``-s 1``).  Synthetic inputs only.
@@ -83,6 +85,42 @@ def train(n: int, steps: int):
         print(f"train {n}x{n} step {i}: loss {loss:.4e}, {1e3 * (time.perf_counter() - t):.1f} ms")
 
 
+def hybrid():
+    import os
+
+    import torch
+    from . import api, inputs as I
+    w = I.config3(0)
+    g = api.ppe_create_grid(w.dx, w.dy, w.mask)
+    net = api.net_load(os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "hydea_mconv.ppenet"))
+    net.attach(g)
+    rhs = torch.tensor(w.f, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        x = torch.zeros_like(rhs)
+        info = api.ppe_solve(g, rhs, x, 1e-8, api.PPE_MODE_HYBRID, api.PPE_PREC_MIXED, net=net)
+    torch.cuda.synchronize()
+    print(f"hybrid c3: {info['iters_pcg']} + {info['iters_dlsm']} iterations, {info['ms_total']:.2f} ms")
+
+
+def mg(name: str):
+    import torch
+    from . import api, inputs as I
+    if name == "c5":
+        dx, dy, bodies = I.config5_grid()
+        f = I.config5_rhs(0, dx, dy, bodies)
+    else:
+        w = {"c1": I.config1, "c2": I.config2, "c3": I.config3}[name](0)
+        dx, dy, f = w.dx, w.dy, w.f
+    g = api.ppe_create_grid(dx, dy)
+    api.ppe_set_options(g, preconditioner=1)
+    rhs = torch.tensor(f, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        x = torch.zeros_like(rhs)
+        info = api.ppe_solve(g, rhs, x, 1e-8, api.PPE_MODE_PCG, api.PPE_PREC_MIXED)
+    torch.cuda.synchronize()
+    print(f"multigrid {name}: {info['iters_pcg']} iterations, {info['ms_total']:.2f} ms")
+
+
 def main(argv=None):
     a = sys.argv[1:] if argv is None else argv
     if not a or a[0] == "c2":
@@ -93,6 +131,10 @@ def main(argv=None):
         infer()
     elif a[0] == "train":
         train(int(a[1]), int(a[2]))
+    elif a[0] == "hybrid":
+        hybrid()
+    elif a[0] == "mg":
+        mg(a[1] if len(a) > 1 else "c2")
     else:
         raise SystemExit(__doc__)
 

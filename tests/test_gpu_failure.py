@@ -82,11 +82,16 @@ def test_nan_direction_is_rejected(api):
 
 
 @pytest.mark.parametrize("shape", [(4096, 16), (16, 4096)])
-def test_stalled_mixed_solve_continues_in_fp64(api, shape):
-    """A long strip: the FP64 Jacobi-PCG needs ~30,000 iterations, and FP32
-    inner iterations cannot resolve the system (they stall).  The mixed solve
-    notices (refinements that stop halving the true residual) and continues
-    in FP64 from its iterate, reaching the tolerance."""
+def test_ill_conditioned_strip_mixed_solve_converges(api, shape):
+    """A long strip: the FP64 Jacobi-PCG needs ~30,000 iterations, and the
+    condition number is near the reciprocal of FP32's precision, so an FP32
+    inner solve loses its reduction target: its recursive residual stops
+    tracking the true one.  The inner solve's length budget (2000 + 4x the
+    last successful one) then forces residual replacements often enough for
+    the mixed solve to keep converging (measured: 2-3x FP64's iteration
+    count at a fifth to a tenth of its cost per iteration); should the true
+    residual stop halving for three refinements, the solve continues in
+    FP64 instead.  Either way it must reach the tolerance."""
     g = I.rng(43)
     nx, ny = shape
     dx, dy = I.random_spacing(nx, g), I.random_spacing(ny, g)
@@ -94,7 +99,8 @@ def test_stalled_mixed_solve_continues_in_fp64(api, shape):
     grid = api.ppe_create_grid(dx, dy)
     x = torch.zeros(ny, nx, dtype=torch.float64, device="cuda")
     info = api.ppe_solve(grid, _dev(f), x, TOL, api.PPE_MODE_PCG, api.PPE_PREC_MIXED)
-    assert info["status"] == 0 and info["precision_fallback"] == 1, info
+    assert info["status"] == 0, info
+    assert info["iters_pcg"] <= 150_000, info
     assert oracle.true_relres(dx, dy, f, x.cpu().numpy()) <= TOL * 1.05
 
 
