@@ -1,30 +1,42 @@
 // tcgen05 implicit-GEMM 3x3 convolution for sm_103a (the Mesh-Convs of the
 // DeepONet branch, Sec. 2.4).
 //
-// GEMM view of one tile: M = 128 output pixels (a TW x TH patch of one
+// GEMM view of one tile: M = 128 output pixels (an 8 x 16 patch of one
 // image), N = a slice of the output channels, K = 9 taps x Cin input channels.
-// For every (tap, channel block) the A tile is a TMA box load of the NHWC
-// activation tensor at the tap's shifted coordinates; coordinates outside the
-// image are zero-filled by the TMA unit, which is exactly the convolution's
-// zero padding.  The B tile is a TMA box load of the packed weights
-// [Cout][9*Cin] (K-major).  Both land in shared memory in the swizzled
-// K-major layout the tensor cores read; one elected thread issues
-// tcgen05.mma (BF16 x BF16 -> FP32) into a TMEM accumulator, and twelve
-// epilogue warps read it back with tcgen05.ld for the fused epilogue (bias,
-// GELU, per-pixel Mesh-Conv weight of the consumer layer, BF16 stores).
+// The activations come in as halo windows: for each channel block and each
+// horizontal tap offset kx, one TMA box load brings the 8 x 18 pixel window
+// at x0 + kx - 1, y0 - 1 of the NHWC tensor into shared memory, in the
+// swizzled K-major layout the tensor cores read (one 8-row atom per window
+// row).  The three vertical taps ky are the same window read from atom ky
+// on, so one load serves three taps: 432 pixel rows per channel block where
+// nine shifted tiles took 1,152.  Coordinates outside the image are
+// zero-filled by the TMA unit, which is exactly the convolution's zero
+// padding.  The B tiles are TMA box loads of the packed weights
+// [Cout][9*Cin] (K-major).  One elected thread issues tcgen05.mma
+// (BF16 x BF16 -> FP32) into a TMEM accumulator, and twelve epilogue warps
+// read it back with tcgen05.ld for the fused epilogue (bias, GELU, per-pixel
+// Mesh-Conv weight of the consumer layer, BF16 stores).
 //
-// The layers are small GEMMs (M <= 65,536 pixels, N <= 256, K <= 2,304), so a
-// CTA per tile would spend most of its life filling its pipeline and draining
-// its accumulator.  The kernel is therefore persistent: one or two CTAs per
-// SM walk the tiles; the TMA stage ring runs on from one tile to the next,
-// and two TMEM accumulators let the epilogue of a tile overlap the MMAs of
-// the following one.
+// The layers are small GEMMs (M <= 65,536 pixels, N <= 256, K <= 2,304)
+// whose time goes into moving operands from L2, so the kernel shares loads
+// across a thread-block cluster of cm x cn CTAs: the cn CTAs that compute
+// different output-channel slices of one patch receive its activation
+// windows from one multicast TMA load, and the cm CTAs that compute the same
+// slice of different patches receive its weight tiles from one multicast.
+// Every CTA of the cluster releases a stage to all of them (multicast MMA
+// commit), so a stage is refilled only when every CTA that received it has
+// consumed it.
+//
+// The kernel is persistent: one or two CTAs per SM walk the tiles, the stage
+// ring runs on from one tile to the next, and two TMEM accumulators let the
+// epilogue of a tile overlap the MMAs of the following one.
 //
 // The input tensor arrives already multiplied by this layer's eta (the
 // producing kernel applies it), so the A operand is loaded as is.
 //
 // Every wait is bounded: on expiry the CTA records an error flag, skips the
-// remaining work, frees its TMEM and returns.
+// remaining work, frees its TMEM and returns, after the cluster's CTAs have
+// all stopped issuing copies into one another.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -41,6 +53,8 @@ namespace ppe {
 namespace {
 
 constexpr int TC_M = 128;
+constexpr int TC_TW = 8, TC_TH = 16;             // output patch (pixels): one 8-row atom per patch row
+constexpr int TC_WIN = TC_TW * (TC_TH + 2);      // pixel rows of a halo window (8 x 18)
 constexpr int TC_MAX_STAGES = 8;
 constexpr long long TC_WAIT_NS = 1000000000LL;   // 1 s bound on every wait
 constexpr int TC_THREADS = 512;                  // warp 0: TMA producer, warp 1: MMA issuer, warps 4-15: epilogue
@@ -50,8 +64,10 @@ constexpr int TC_GROUPS = TC_EPI_WARPS / 4;                      // epilogue col
 constexpr uint32_t TC_BAR_BYTES = 256;           // barriers and the TMEM slot
 
 struct TcArgs {
-    int B, H, W, cin, cout, n_tile, tw, th, tiles_x, tiles_y, kblocks, stages, tmem_cols;
-    int nslices, ntiles;    // output-channel slices; tiles = (image patches) x slices
+    int B, H, W, cin, cout, n_tile, tiles_x, tiles_y, stages, tmem_cols;
+    int mtiles, nslices;    // image patches; output-channel slices
+    int cm, cn;             // cluster shape: cm patches x cn slices (cm * cn CTAs)
+    int units;              // cluster work units: ceil(mtiles / cm) x (nslices / cn)
     uint32_t bar_off;       // byte offset of the barriers, past the pipeline stages
     const float *bias;
     Epi epi;
@@ -101,6 +117,16 @@ __device__ __forceinline__ void mma_commit(uint32_t bar)
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
+// Arrive on the barrier at offset `bar` in every CTA of `mask` once the MMAs
+// issued so far have completed.
+__device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+        "h"(mask)
+        : "memory");
+}
+
 __device__ __forceinline__ void mbar_arrive(uint32_t bar)
 {
     asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(bar) : "memory");
@@ -140,13 +166,14 @@ template <int BK>
 __global__ void __launch_bounds__(TC_THREADS, 2)
     conv_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcArgs a)
 {
-    constexpr int SW = BK * 2;                 // swizzle span = row bytes
-    constexpr uint32_t A_BYTES = TC_M * BK * 2;
+    constexpr int RB = BK * 2;                 // bytes per K-major row = swizzle span
+    constexpr uint32_t A_BYTES = TC_WIN * RB;  // one halo window
+    constexpr uint32_t ATOM = 8 * RB;          // one 8-row swizzle atom = one window row
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
-    const uint32_t b_bytes = (uint32_t)a.n_tile * BK * 2;
-    const uint32_t tx_bytes = A_BYTES + b_bytes;                      // bytes landed per stage
+    const uint32_t b_bytes = (uint32_t)a.n_tile * RB;                 // one tap's weight tile
+    const uint32_t tx_bytes = A_BYTES + 3 * b_bytes;                  // bytes landed per stage
     const uint32_t stage_bytes = (tx_bytes + 1023u) & ~1023u;         // 1024-aligned stage stride
     // barriers: full[8], empty[8] of the stages; acc_full[2], acc_empty[2] of
     // the two TMEM accumulators; then the TMEM address slot
@@ -157,12 +184,24 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int cblocks = a.cin / BK;
+    const int kiters = 3 * cblocks;            // (channel block, kx) stages per tile
     const int tiles_xy = a.tiles_x * a.tiles_y;
+    const int cs = a.cm * a.cn;
+    const bool clustered = cs > 1;
+    const int rank = clustered ? (int)cluster_rank() : 0;
+    const int rm = rank / a.cn, rn = rank - rm * a.cn;
+    const int cluster = blockIdx.x / cs, nclusters = gridDim.x / cs;
+    const int sgroups = a.nslices / a.cn;
+    // multicast masks: the CTAs of this patch row (activations), of this slice column (weights), all
+    const uint16_t mask_a = (uint16_t)(((1u << a.cn) - 1u) << (rm * a.cn));
+    uint16_t mask_b = 0;
+    for (int i = 0; i < a.cm; ++i) mask_b |= (uint16_t)(1u << (i * a.cn + rn));
+    const uint16_t mask_all = (uint16_t)((1u << cs) - 1u);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < a.stages; ++s) {
             mbar_init(full0 + 8 * s, 1);
-            mbar_init(empty0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, cs);     // every CTA of the cluster releases every stage
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(accf0 + 8 * b, 1);
@@ -179,66 +218,93 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
+    // the cluster's barriers are initialised before any CTA sends it copies or arrivals
+    if (clustered)
+        cluster_sync();
+    else
+        __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tslot_ptr;
 
-    // The CTA walks the tiles blockIdx.x, blockIdx.x + gridDim.x, ...; tile t
-    // is output patch t / nslices and channel slice t % nslices.  The stage
-    // ring and its phases run on across tiles; the accumulator alternates
-    // between two TMEM buffers, so the epilogue of one tile overlaps the MMAs
-    // of the next.
+    // Cluster c walks the units c, c + nclusters, ...; unit u is patch group
+    // u / sgroups (patches cm * group + rm) and slice group u % sgroups
+    // (slices cn * group + rn).  A patch past the last one (ragged cluster
+    // row) is computed on zero-filled loads and not stored.
     if (warp == 0) {
         if (lane == 0) {
-            // producer: TMA loads of the A (activation) and B (weight) tiles
+            // producer: the halo windows (one CTA per patch row multicasts) and
+            // the weight tiles (one CTA per slice column multicasts)
             bool ok = true;
             int it = 0, armed = 0;
-            for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
-                const int mt = t / a.nslices, ns = t - mt * a.nslices;
+            for (int u = cluster; u < a.units && ok; u += nclusters) {
+                const int mt = (u / sgroups) * a.cm + rm, ns = (u % sgroups) * a.cn + rn;
                 const int img = mt / tiles_xy, tile = mt - img * tiles_xy;
-                const int x0 = (tile % a.tiles_x) * a.tw, y0 = (tile / a.tiles_x) * a.th, n0 = ns * a.n_tile;
-                for (int kb = 0; kb < a.kblocks; ++kb, ++it) {
+                const int x0 = (tile % a.tiles_x) * TC_TW, y0 = (tile / a.tiles_x) * TC_TH, n0 = ns * a.n_tile;
+                for (int kb = 0; kb < kiters; ++kb, ++it) {
                     const int s = it % a.stages;
                     const uint32_t ph = (it / a.stages) & 1;
                     ok = mbar_wait(empty0 + 8 * s, ph ^ 1, a.err);
                     if (!ok) break;
-                    const int tap = kb / cblocks, c0 = (kb % cblocks) * BK;
-                    const int ky = tap / 3, kx = tap % 3;
+                    const int c0 = (kb / 3) * BK, kx = kb % 3;
                     const uint32_t sa = base + stage_bytes * s, sb = sa + A_BYTES;
                     mbar_expect_tx(full0 + 8 * s, tx_bytes);
-                    tma_load_4d(sa, &tmA, full0 + 8 * s, c0, x0 + kx - 1, y0 + ky - 1, img);
-                    tma_load_2d(sb, &tmB, full0 + 8 * s, tap * a.cin + c0, n0);
+                    if (a.cn == 1)
+                        tma_load_4d(sa, &tmA, full0 + 8 * s, c0, x0 + kx - 1, y0 - 1, img);
+                    else if (rn == 0)
+                        tma_load_4d_mc(sa, &tmA, full0 + 8 * s, c0, x0 + kx - 1, y0 - 1, img, mask_a);
+                    if (a.cm == 1 || rm == 0) {
+#pragma unroll
+                        for (int ky = 0; ky < 3; ++ky) {
+                            const int k0 = (3 * ky + kx) * a.cin + c0;      // tap (ky, kx) of the packed weights
+                            if (a.cm == 1)
+                                tma_load_2d(sb + ky * b_bytes, &tmB, full0 + 8 * s, k0, n0);
+                            else
+                                tma_load_2d_mc(sb + ky * b_bytes, &tmB, full0 + 8 * s, k0, n0, mask_b);
+                        }
+                    }
                     armed = it + 1;
                 }
             }
             if (!ok) {
-                // let copies already in flight land before the CTA leaves
+                // let this CTA's own copies in flight land before it leaves
                 for (int k = (armed > a.stages ? armed - a.stages : 0); k < armed; ++k)
-                    mbar_wait(full0 + 8 * (k % a.stages), (k / a.stages) & 1, a.err);
+                    if (!mbar_wait_bounded(full0 + 8 * (k % a.stages), (k / a.stages) & 1, TC_WAIT_NS)) break;
+            }
+            if (clustered) {
+                // every CTA of the cluster has released the last stages: no
+                // arrival of theirs is still on its way to this CTA
+                for (int k = it; k < it + a.stages; ++k)
+                    if (!mbar_wait(empty0 + 8 * (k % a.stages), ((k / a.stages) & 1) ^ 1, a.err)) break;
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            // MMA issuer
+            // MMA issuer: per stage, the three vertical taps of the window
             const uint32_t idesc = instr_desc(a.n_tile);
             bool ok = true;
             int it = 0;
-            for (int t = blockIdx.x, i = 0; t < a.ntiles && ok; t += gridDim.x, ++i) {
+            for (int u = cluster, i = 0; u < a.units && ok; u += nclusters, ++i) {
                 const int b = i & 1;
                 ok = mbar_wait(acce0 + 8 * b, ((i >> 1) & 1) ^ 1, a.err);   // epilogue drained buffer b
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t acc = tmem + (uint32_t)(b * a.n_tile);
-                for (int kb = 0; kb < a.kblocks; ++kb, ++it) {
+                for (int kb = 0; kb < kiters; ++kb, ++it) {
                     const int s = it % a.stages;
                     ok = mbar_wait(full0 + 8 * s, (it / a.stages) & 1, a.err);
                     if (!ok) break;
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t sa = base + stage_bytes * s, sb = sa + A_BYTES;
 #pragma unroll
-                    for (int k = 0; k < BK / 16; ++k)
-                        mma_bf16(acc, smem_desc<SW>(sa + 32 * k), smem_desc<SW>(sb + 32 * k), idesc, (kb | k) != 0);
-                    mma_commit(empty0 + 8 * s);
+                    for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+                        for (int k = 0; k < BK / 16; ++k)
+                            mma_bf16(acc, smem_desc<RB>(sa + ky * ATOM + 32 * k),
+                                     smem_desc<RB>(sb + ky * b_bytes + 32 * k), idesc, (kb | ky | k) != 0);
+                    if (clustered)
+                        mma_commit_mc(empty0 + 8 * s, mask_all);
+                    else
+                        mma_commit(empty0 + 8 * s);
                 }
                 if (!ok) break;
                 mma_commit(accf0 + 8 * b);      // arrives once every MMA of this tile has completed
@@ -255,16 +321,16 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
         const int m = quarter * 32 + lane;
         const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
         const Epi &e = a.epi;
-        for (int t = blockIdx.x, i = 0; t < a.ntiles; t += gridDim.x, ++i) {
+        for (int u = cluster, i = 0; u < a.units; u += nclusters, ++i) {
             const int b = i & 1;
             const bool ok = __all_sync(0xffffffffu, mbar_wait(accf0 + 8 * b, (i >> 1) & 1, a.err));
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const int mt = t / a.nslices, ns = t - mt * a.nslices;
+            const int mt = (u / sgroups) * a.cm + rm, ns = (u % sgroups) * a.cn + rn;
             const int img = mt / tiles_xy, tile = mt - img * tiles_xy;
-            const int px = (tile % a.tiles_x) * a.tw + m % a.tw, py = (tile / a.tiles_x) * a.th + m / a.tw;
+            const int px = (tile % a.tiles_x) * TC_TW + m % TC_TW, py = (tile / a.tiles_x) * TC_TH + m / TC_TW;
             const int n0 = ns * a.n_tile;
-            const bool inside = px < a.W && py < a.H;
+            const bool inside = mt < a.mtiles && px < a.W && py < a.H;
             const int q = py * a.W + px;
             const size_t pp = ((size_t)img * a.H + py) * a.W + px;
             const float sc1 = (e.eta1 && inside) ? e.eta1[q] : 1.f;
@@ -302,6 +368,8 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
     __syncthreads();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols) : "memory");
+    // no CTA leaves while another of its cluster may still write into it
+    if (clustered) cluster_sync();
 }
 
 // ---------------------------------------------------------------------------
@@ -387,25 +455,33 @@ ppe_status conv3x3_tc(const ConvArgs &a, cudaStream_t s)
     auto encode = tensor_map_encoder();
     int *err = err_flag();
     const int bk = pick_bk(a.cin);
-    // output patch of 128 pixels: TW x TH with TW a power of two <= 128
-    int tw = 8;
-    while (tw < a.W && tw < TC_M) tw *= 2;
-    int th = TC_M / tw;
-    // output-channel slice: the whole of Cout when it fits one MMA (<= 256)
+    const int rb = 2 * bk;
+    // output-channel slice: the whole of Cout up to 128 (a stage holds three
+    // taps' weight tiles beside the halo window)
     int n_tile = a.cout;
-    while (n_tile > 256) n_tile /= 2;
-    if (a.cout % n_tile) n_tile = 16;
+    while (n_tile > 128) n_tile /= 2;
+    if (a.cout % n_tile || n_tile % 16) n_tile = 16;
     const int nsm = sm_count();
-    const long mtiles = (long)((a.W + tw - 1) / tw) * ((a.H + th - 1) / th) * a.B;
+    const int tiles_x = (a.W + TC_TW - 1) / TC_TW, tiles_y = (a.H + TC_TH - 1) / TC_TH;
+    const long mtiles = (long)tiles_x * tiles_y * a.B;
     // few output patches (deep U-Net levels): split the output channels until
-    // every SM has a tile; each slice re-reads the activations (L2-resident)
+    // every SM has a tile; the slices of a patch share its activation loads
     while (mtiles * (a.cout / n_tile) < nsm && n_tile % 32 == 0 && n_tile > 16 && a.cout % (n_tile / 2) == 0)
         n_tile /= 2;                                          // stays a multiple of 16
     const int nslices = a.cout / n_tile;
-    const long ntiles = mtiles * nslices;
+    // cluster: cn slices of one patch (multicast activations) x cm patches
+    // of one slice (multicast weights), at most 8 CTAs
+    int cn = 1;
+    for (int d = 8; d >= 2; --d)
+        if (nslices % d == 0) { cn = d; break; }
+    // pairs of patches share their weight loads when there are patches enough
+    // to keep every SM busy with pairs
+    const int cm = (cn <= 4 && mtiles >= nsm / 2) ? 2 : 1;
+    const int cs = cm * cn;
+    const long units = (mtiles + cm - 1) / cm * (nslices / cn);
     int tmem_cols = 32;                                       // two accumulators of n_tile columns
     while (tmem_cols < 2 * n_tile) tmem_cols *= 2;
-    const int stage_bytes = ((TC_M + n_tile) * bk * 2 + 1023) / 1024 * 1024;
+    const int stage_bytes = ((TC_WIN + 3 * n_tile) * rb + 1023) / 1024 * 1024;
     // two CTAs per SM when a pipeline of three or more stages fits in half the
     // shared memory and both CTAs' accumulators fit the 512 TMEM columns
     int ctas_per_sm = 2;
@@ -427,7 +503,7 @@ ppe_status conv3x3_tc(const ConvArgs &a, cudaStream_t s)
     {
         cuuint64_t dims[4] = {(cuuint64_t)a.cin, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)a.B};
         cuuint64_t strides[3] = {(cuuint64_t)a.cin * 2, (cuuint64_t)a.W * a.cin * 2, (cuuint64_t)a.H * a.W * a.cin * 2};
-        cuuint32_t box[4] = {(cuuint32_t)bk, (cuuint32_t)tw, (cuuint32_t)th, 1};
+        cuuint32_t box[4] = {(cuuint32_t)bk, (cuuint32_t)TC_TW, (cuuint32_t)(TC_TH + 2), 1};
         cuuint32_t es[4] = {1, 1, 1, 1};
         CUresult r = encode(&mA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void *)a.in, dims, strides, box, es,
                             CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -452,28 +528,42 @@ ppe_status conv3x3_tc(const ConvArgs &a, cudaStream_t s)
     }
     TcArgs t;
     t.B = a.B; t.H = a.H; t.W = a.W; t.cin = a.cin; t.cout = a.cout; t.n_tile = n_tile;
-    t.tw = tw; t.th = th;
-    t.tiles_x = (a.W + tw - 1) / tw;
-    t.tiles_y = (a.H + th - 1) / th;
-    t.nslices = nslices;
-    t.ntiles = (int)ntiles;
-    t.kblocks = 9 * (a.cin / bk);
+    t.tiles_x = tiles_x;
+    t.tiles_y = tiles_y;
     t.stages = stages;
     t.tmem_cols = tmem_cols;
+    t.mtiles = (int)mtiles;
+    t.nslices = nslices;
+    t.cm = cm;
+    t.cn = cn;
+    t.units = (int)units;
     t.bar_off = (uint32_t)bar_off;
     t.bias = a.bias;
     t.epi = a.epi;
     t.err = err;
-    // persistent: one or two CTAs per SM, each walking its share of the tiles
-    dim3 grid((unsigned)std::min<long>(ntiles, (long)nsm * ctas_per_sm));
+    // persistent: one or two CTAs per SM in clusters of cs, each cluster
+    // walking its share of the units
+    const long clusters = std::min<long>(units, std::max(1L, (long)nsm * ctas_per_sm / cs));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(clusters * cs));
+    cfg.blockDim = dim3(TC_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     cudaError_t e;
     if (bk == 64)
-        conv_tc_kernel<64><<<grid, TC_THREADS, smem, s>>>(mA, mB, t);
+        e = cudaLaunchKernelEx(&cfg, conv_tc_kernel<64>, mA, mB, t);
     else if (bk == 32)
-        conv_tc_kernel<32><<<grid, TC_THREADS, smem, s>>>(mA, mB, t);
+        e = cudaLaunchKernelEx(&cfg, conv_tc_kernel<32>, mA, mB, t);
     else
-        conv_tc_kernel<16><<<grid, TC_THREADS, smem, s>>>(mA, mB, t);
-    e = cudaGetLastError();
+        e = cudaLaunchKernelEx(&cfg, conv_tc_kernel<16>, mA, mB, t);
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_status(e, "conv_tc_kernel launch");
     return PPE_OK;
 }

@@ -71,3 +71,37 @@ def test_config4_batch_of_64(api):
         assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-6, w.name
     for g in grids:
         g.close()
+
+
+@pytest.mark.parametrize("delta,compatible", [(3e-7, True), (0.97e-6, True), (1.03e-6, False)])
+def test_cross_block_sums_at_two_million_cells(api, delta, compatible):
+    """Partial sums cross blocks as float-float (two FP32 words, a ~48-bit
+    significand), not FP64.  On the 2048 x 1024 grid the source is +-(1 + u)
+    on the two halves, so every block's FP64 partial sum of b is large and
+    the halves cancel across blocks; a constant shift leaves the imbalance
+    |sum b| / sum |b| at `delta`.  The device's imbalance must match the
+    exactly rounded FP64 sums (math.fsum) to 1e-3 relative -- 152 column-strip
+    block sums added in plain FP32 miss it by 0.6% to 20% on these sources --
+    and must fall on the right side of the 1e-6 compatibility bound."""
+    import math
+    dx, dy, _ = I.config5_grid()
+    nx, ny = dx.size, dy.size
+    g = I.rng(77)
+    sign = np.where(np.arange(nx) < nx // 2, 1.0, -1.0)[None, :]
+    S = sign * (1.0 + 0.5 * g.random((ny, nx)))
+    V = np.outer(dy, dx)
+    S -= math.fsum((V * S).ravel()) / math.fsum(V.ravel())
+    S -= delta * math.fsum(np.abs(V * S).ravel()) / math.fsum(V.ravel())
+    b = (-dx[None, :] * dy[:, None]) * S                  # the device's rounding order
+    exact = abs(math.fsum(b.ravel())) / math.fsum(np.abs(b).ravel())
+    assert abs(exact / delta - 1.0) < 0.01
+    grid = api.ppe_create_grid(dx, dy)
+    api.ppe_set_options(grid, max_iters=1)
+    x = torch.zeros(ny, nx, dtype=torch.float64, device="cuda")
+    info = api.ppe_solve(grid, _dev(S), x, TOL, api.PPE_MODE_PCG, api.PPE_PREC_MIXED, raise_on_error=False)
+    if compatible:
+        assert info["status"] == api._lib.PPE_ERR_NOT_CONVERGED, info     # one iteration allowed
+    else:
+        assert info["status"] == api._lib.PPE_ERR_INCOMPATIBLE_RHS, info
+    assert abs(info["incompat"] - exact) <= 1e-3 * exact, (info["incompat"], exact)
+    grid.close()
