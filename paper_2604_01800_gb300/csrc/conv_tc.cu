@@ -336,26 +336,51 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
             const float sc1 = (e.eta1 && inside) ? e.eta1[q] : 1.f;
             const float sc2 = (e.eta2 && inside) ? e.eta2[q] : 1.f;
             const bool act = e.act != 0;
+            // pooling sums 2x2 pixel groups across lanes (l, l^1, l^8, l^9 of a
+            // warp: two columns of two patch rows), so then every lane takes part
+            const bool pool = e.pool_out != nullptr;
             for (int c = 16 * group; c < a.n_tile; c += 16 * TC_GROUPS) {
                 float v[16];
                 tmem_ld16(tmem + (uint32_t)(b * a.n_tile + c) + lane_off, v);
-                if (!inside) continue;
+                if (!inside && !pool) continue;
                 const int ch = n0 + c;
 #pragma unroll
                 for (int k = 0; k < 16; ++k) v[k] += a.bias ? __ldg(a.bias + ch + k) : 0.f;
-                if (e.zf_out) {
+                if (inside && e.zf_out) {
                     float4 *d = reinterpret_cast<float4 *>(e.zf_out + pp * a.cout + ch);
 #pragma unroll
                     for (int k = 0; k < 4; ++k) d[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
                 }
-                if (e.z_out) store_bf16x16(e.z_out + pp * a.cout + ch, v, 1.f);
-                if (e.out1 || e.out2) {
+                if (inside && e.z_out) store_bf16x16(e.z_out + pp * a.cout + ch, v, 1.f);
+                if (e.out1 || e.out2 || pool || e.up_out) {
                     if (act) {
 #pragma unroll
                         for (int k = 0; k < 16; ++k) v[k] = gelu_f(v[k]);
                     }
-                    if (e.out1) store_bf16x16(e.out1 + pp * e.cs1 + e.co1 + ch, v, sc1);
-                    if (e.out2) store_bf16x16(e.out2 + pp * e.cs2 + e.co2 + ch, v, sc2);
+                    if (inside && e.out1) store_bf16x16(e.out1 + pp * e.cs1 + e.co1 + ch, v, sc1);
+                    if (inside && e.out2) store_bf16x16(e.out2 + pp * e.cs2 + e.co2 + ch, v, sc2);
+                    if (inside && e.up_out) {
+                        // nearest 2x: the pixel's four children on the fine grid
+                        const int Wf = 2 * a.W;
+#pragma unroll
+                        for (int d = 0; d < 4; ++d) {
+                            const int fx = 2 * px + (d & 1), fy = 2 * py + (d >> 1);
+                            const size_t pf = ((size_t)img * 2 * a.H + fy) * Wf + fx;
+                            store_bf16x16(e.up_out + pf * e.up_cs + ch, v, e.up_eta ? e.up_eta[fy * Wf + fx] : 1.f);
+                        }
+                    }
+                    if (pool) {
+#pragma unroll
+                        for (int k = 0; k < 16; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], 1);
+#pragma unroll
+                        for (int k = 0; k < 16; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], 8);
+                        if (inside && (lane & 9) == 0) {
+                            const int Wc = a.W >> 1, Hc = a.H >> 1, xc = px >> 1, yc = py >> 1;
+                            const size_t pc = ((size_t)img * Hc + yc) * Wc + xc;
+                            store_bf16x16(e.pool_out + pc * e.pool_cs + ch, v,
+                                          0.25f * (e.pool_eta ? e.pool_eta[yc * Wc + xc] : 1.f));
+                        }
+                    }
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -452,6 +477,10 @@ ppe_status conv3x3_tc(const ConvArgs &a, cudaStream_t s)
         return PPE_ERR_ARG;
     }
     PPE_TRY(conv3x3_tc_prepare());
+    if (a.epi.pool_out && (a.H % 2 || a.W % 2)) {
+        set_error("conv3x3_tc: a fused 2x2 pooling needs even H and W");
+        return PPE_ERR_ARG;
+    }
     auto encode = tensor_map_encoder();
     int *err = err_flag();
     const int bk = pick_bk(a.cin);

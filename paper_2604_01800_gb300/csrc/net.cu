@@ -400,7 +400,7 @@ ppe_status net_forward(ppe_net *n, NetCache *c, int B, const InputSrc &src, cons
     const ActPlan &pl = c->plan;
     auto eta = [&](const std::string &name) { return c->eta + c->eoff[layer_index(n, name)]; };
     auto zbuf = [&](int li) { return keep_z ? act + pl.Z[li] : (bf16 *)nullptr; };
-    auto conv = [&](const std::string &name, const bf16 *in, int k, const Epi &ep) -> ppe_status {
+    auto args = [&](const std::string &name, const bf16 *in, int k, const Epi &ep) {
         int li = layer_index(n, name);
         const ConvLayer &l = n->layers[li];
         ConvArgs a;
@@ -408,8 +408,18 @@ ppe_status net_forward(ppe_net *n, NetCache *c, int B, const InputSrc &src, cons
         a.B = B; a.H = c->Hk[k]; a.W = c->Wk[k]; a.cin = l.cin; a.cout = l.cout;
         a.epi = ep;
         a.epi.z_out = zbuf(li);
-        return run_conv(n, a, s);
+        return a;
     };
+    auto conv = [&](const std::string &name, const bf16 *in, int k, const Epi &ep) -> ppe_status {
+        return run_conv(n, args(name, in, k, ep), s);
+    };
+    // on the tensor-core path the 2x2 pooling and the nearest up-sampling
+    // run in the producing convolution's epilogue; otherwise the raw output
+    // goes to P[k] / U[k] and separate kernels pool or up-sample it
+    auto fused = [&](const std::string &name, const bf16 *in, int k) {
+        return n->use_tc && conv3x3_tc_supported(args(name, in, k, Epi()));
+    };
+    bool pooled[PPE_NET_MAX_LEVELS] = {}, upped[PPE_NET_MAX_LEVELS] = {};
     // enc0a: 1-channel input
     {
         int li = layer_index(n, "enc0a");
@@ -423,16 +433,26 @@ ppe_status net_forward(ppe_net *n, NetCache *c, int B, const InputSrc &src, cons
         const int Ck = cf.widths[k];
         std::string ks = std::to_string(k);
         if (k > 0) {
-            PPE_TRY(pool2(act + pl.P[k - 1], act + pl.IN[k], B, c->Hk[k], c->Wk[k], cf.widths[k - 1],
-                          eta("enc" + ks + "a"), s));
+            if (!pooled[k])
+                PPE_TRY(pool2(act + pl.P[k - 1], act + pl.IN[k], B, c->Hk[k], c->Wk[k], cf.widths[k - 1],
+                              eta("enc" + ks + "a"), s));
             Epi ep;
             ep.out1 = act + pl.A[k]; ep.cs1 = Ck; ep.eta1 = eta("enc" + ks + "b");
             PPE_TRY(conv("enc" + ks + "a", act + pl.IN[k], k, ep));
         }
         Epi ep;
+        const bool f = fused("enc" + ks + "b", act + pl.A[k], k);
         if (k < L - 1) {
             ep.out1 = act + pl.CAT[k]; ep.cs1 = 2 * Ck; ep.co1 = Ck; ep.eta1 = eta("dec" + ks + "a");
-            ep.out2 = act + pl.P[k]; ep.cs2 = Ck; ep.co2 = 0; ep.eta2 = nullptr;
+            if (f) {
+                ep.pool_out = act + pl.IN[k + 1]; ep.pool_cs = Ck; ep.pool_eta = eta("enc" + std::to_string(k + 1) + "a");
+                pooled[k + 1] = true;
+            } else {
+                ep.out2 = act + pl.P[k]; ep.cs2 = Ck; ep.co2 = 0; ep.eta2 = nullptr;
+            }
+        } else if (f && k > 0) {
+            ep.up_out = act + pl.UP[k - 1]; ep.up_cs = Ck; ep.up_eta = eta("up" + std::to_string(k - 1));
+            upped[k - 1] = true;
         } else {
             ep.out1 = act + pl.U[k]; ep.cs1 = Ck;
         }
@@ -441,7 +461,9 @@ ppe_status net_forward(ppe_net *n, NetCache *c, int B, const InputSrc &src, cons
     for (int k = L - 2; k >= 0; --k) {
         const int Ck = cf.widths[k];
         std::string ks = std::to_string(k);
-        PPE_TRY(up2(act + pl.U[k + 1], act + pl.UP[k], B, c->Hk[k], c->Wk[k], cf.widths[k + 1], eta("up" + ks), s));
+        if (!upped[k])
+            PPE_TRY(up2(act + pl.U[k + 1], act + pl.UP[k], B, c->Hk[k], c->Wk[k], cf.widths[k + 1], eta("up" + ks),
+                        s));
         Epi e1;
         e1.out1 = act + pl.CAT[k]; e1.cs1 = 2 * Ck; e1.co1 = 0; e1.eta1 = eta("dec" + ks + "a");
         PPE_TRY(conv("up" + ks, act + pl.UP[k], k, e1));
@@ -449,7 +471,12 @@ ppe_status net_forward(ppe_net *n, NetCache *c, int B, const InputSrc &src, cons
         e2.out1 = act + pl.D[k]; e2.cs1 = Ck; e2.eta1 = eta("dec" + ks + "b");
         PPE_TRY(conv("dec" + ks + "a", act + pl.CAT[k], k, e2));
         Epi e3;
-        e3.out1 = act + pl.U[k]; e3.cs1 = Ck;
+        if (k > 0 && fused("dec" + ks + "b", act + pl.D[k], k)) {
+            e3.up_out = act + pl.UP[k - 1]; e3.up_cs = Ck; e3.up_eta = eta("up" + std::to_string(k - 1));
+            upped[k - 1] = true;
+        } else {
+            e3.out1 = act + pl.U[k]; e3.cs1 = Ck;
+        }
         PPE_TRY(conv("dec" + ks + "b", act + pl.D[k], k, e3));
     }
     return fold_out(act + pl.U[0], c->weff, c->ceff, B, c->H, c->W, cf.widths[0], e, e_pitch, e_bstride, c->nx, c->ny,

@@ -37,6 +37,15 @@ struct Epi {
     int cs2 = 0, co2 = 0;
     const float *eta2 = nullptr;
     int act = 1;   // 1: GELU, 0: identity
+    // tensor-core path only: the activation 2x2-averaged (the next level's
+    // pooled input, times pool_eta at the coarse pixel; H and W even) and
+    // nearest-2x up-sampled (times up_eta at the fine pixel)
+    bf16 *pool_out = nullptr;
+    int pool_cs = 0;
+    const float *pool_eta = nullptr;
+    bf16 *up_out = nullptr;
+    int up_cs = 0;
+    const float *up_eta = nullptr;
 };
 
 // Convolution problem: NHWC BF16 input [B][H][W][cin] (already eta-weighted),

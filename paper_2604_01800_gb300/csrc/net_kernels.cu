@@ -96,6 +96,7 @@ __device__ __forceinline__ float input_at(const InputSrc &s, int b, int y, int x
 }
 
 // First layer (1 input channel): eta-weighted input, 3x3 conv, epilogue.
+// Scalar form, for widths or destinations the staged form does not take.
 __global__ void conv_in_kernel(InputSrc src, int B, int H, int W, const float *__restrict__ eta,
                                const bf16 *__restrict__ w, const float *__restrict__ bias, int C, Epi e)
 {
@@ -121,6 +122,92 @@ __global__ void conv_in_kernel(InputSrc src, int B, int H, int W, const float *_
 #pragma unroll
         for (int t = 0; t < 9; ++t) z = fmaf(__bfloat162float(w[co * 9 + t]), v[t], z);
         epi_store(e, z, pg, q, co, C);
+    }
+}
+
+// Staged form: a block computes CI_PX pixels of one row, 32 output channels
+// at a time into registers; each BF16 destination is written through a
+// shared-memory tile, so that consecutive lanes store consecutive 16-byte
+// pieces of the NHWC rows.
+constexpr int CI_PX = 128;
+constexpr int CI_CH = 32;
+
+__device__ __forceinline__ void ci_flush(const bf16 (*tile)[CI_CH + 8], bf16 *dst, int cs, int co, int np)
+{
+    // dst: pixel 0 of this block's run, channel 0 of the chunk; np valid pixels
+    for (int k = threadIdx.x; k < np * (CI_CH / 8); k += blockDim.x) {
+        const int px = k / (CI_CH / 8), part = k % (CI_CH / 8);
+        *reinterpret_cast<uint4 *>(dst + (size_t)px * cs + co + 8 * part) =
+            *reinterpret_cast<const uint4 *>(&tile[px][8 * part]);
+    }
+}
+
+__global__ void __launch_bounds__(CI_PX) conv_in_staged_kernel(InputSrc src, int B, int H, int W,
+                                                               const float *__restrict__ eta,
+                                                               const bf16 *__restrict__ w,
+                                                               const float *__restrict__ bias, int C, Epi e)
+{
+    __shared__ float ws[CI_CH][9];
+    __shared__ float bs[CI_CH];
+    __shared__ __align__(16) bf16 tile[CI_PX][CI_CH + 8];      // padded rows: conflict-free column writes
+    const int x0 = blockIdx.x * CI_PX, y = blockIdx.y, b = blockIdx.z;
+    const int x = x0 + threadIdx.x;
+    const int np = min(CI_PX, W - x0);
+    float v[9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+        int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
+        float s = 0.f;
+        if (x < W && yy >= 0 && yy < H && xx >= 0 && xx < W) {
+            s = input_at(src, b, yy, xx);
+            if (eta) s *= eta[yy * W + xx];
+        }
+        v[t] = s;
+    }
+    const size_t p0 = ((size_t)b * H + y) * W + x0;
+    const int q = y * W + min(x, W - 1);
+    const float s1 = (e.eta1 && x < W) ? e.eta1[q] : 1.f;
+    const float s2 = (e.eta2 && x < W) ? e.eta2[q] : 1.f;
+    for (int c0 = 0; c0 < C; c0 += CI_CH) {
+        __syncthreads();
+        for (int k = threadIdx.x; k < CI_CH * 9; k += blockDim.x)
+            ws[k / 9][k % 9] = __bfloat162float(w[(c0 + k / 9) * 9 + k % 9]);
+        if (threadIdx.x < CI_CH) bs[threadIdx.x] = bias ? bias[c0 + threadIdx.x] : 0.f;
+        __syncthreads();
+        float z[CI_CH];
+#pragma unroll
+        for (int c = 0; c < CI_CH; ++c) {
+            float a = bs[c];
+#pragma unroll
+            for (int t = 0; t < 9; ++t) a = fmaf(ws[c][t], v[t], a);
+            z[c] = a;
+        }
+        if (e.zf_out && x < W)
+            for (int c = 0; c < CI_CH; ++c) e.zf_out[(p0 + threadIdx.x) * C + c0 + c] = z[c];
+        if (e.z_out) {
+#pragma unroll
+            for (int c = 0; c < CI_CH; ++c) tile[threadIdx.x][c] = __float2bfloat16_rn(z[c]);
+            __syncthreads();
+            ci_flush(tile, e.z_out + p0 * C, C, c0, np);
+            __syncthreads();
+        }
+        if (e.act) {
+#pragma unroll
+            for (int c = 0; c < CI_CH; ++c) z[c] = gelu_f(z[c]);
+        }
+        if (e.out1) {
+#pragma unroll
+            for (int c = 0; c < CI_CH; ++c) tile[threadIdx.x][c] = __float2bfloat16_rn(z[c] * s1);
+            __syncthreads();
+            ci_flush(tile, e.out1 + p0 * e.cs1 + e.co1, e.cs1, c0, np);
+            __syncthreads();
+        }
+        if (e.out2) {
+#pragma unroll
+            for (int c = 0; c < CI_CH; ++c) tile[threadIdx.x][c] = __float2bfloat16_rn(z[c] * s2);
+            __syncthreads();
+            ci_flush(tile, e.out2 + p0 * e.cs2 + e.co2, e.cs2, c0, np);
+        }
     }
 }
 
@@ -268,7 +355,17 @@ __global__ void fold_kernel(const bf16 *__restrict__ Y, const float *__restrict_
     const bf16 *yp = Y + (((size_t)b * H + y) * W + x) * C;
     float s = ceff[q];
     size_t HW = (size_t)H * W;
-    for (int c = 0; c < C; ++c) s = fmaf(__bfloat162float(yp[c]), weff[c * HW + q], s);
+    if ((C & 7) == 0) {
+        // the pixel's channels as 16-byte pieces (rows are 16-byte aligned)
+        for (int c = 0; c < C; c += 8) {
+            const uint4 raw = *reinterpret_cast<const uint4 *>(yp + c);
+            const bf16 *h = reinterpret_cast<const bf16 *>(&raw);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) s = fmaf(__bfloat162float(h[i]), weff[(c + i) * HW + q], s);
+        }
+    } else {
+        for (int c = 0; c < C; ++c) s = fmaf(__bfloat162float(yp[c]), weff[c * HW + q], s);
+    }
     e[b * e_bstride + (size_t)y * e_pitch + x] = s;
 }
 
@@ -318,7 +415,17 @@ ppe_status conv_in(const InputSrc &src, int B, int H, int W, const float *eta, c
                    const Epi &e, cudaStream_t s)
 {
     dim3 grid((W + 127) / 128, H, B);
-    conv_in_kernel<<<grid, 128, 0, s>>>(src, B, H, W, eta, w, bias, C, e);
+    // the staged form needs whole 32-channel chunks and 16-byte aligned
+    // destination rows and offsets
+    auto aligned = [](const void *p, int cs, int co) {
+        return ((uintptr_t)p & 15) == 0 && cs % 8 == 0 && co % 8 == 0;
+    };
+    const bool staged = C % CI_CH == 0 && (!e.z_out || aligned(e.z_out, C, 0)) &&
+                        (!e.out1 || aligned(e.out1, e.cs1, e.co1)) && (!e.out2 || aligned(e.out2, e.cs2, e.co2));
+    if (staged)
+        conv_in_staged_kernel<<<grid, CI_PX, 0, s>>>(src, B, H, W, eta, w, bias, C, e);
+    else
+        conv_in_kernel<<<grid, 128, 0, s>>>(src, B, H, W, eta, w, bias, C, e);
     PPE_CUDA_TRY(cudaGetLastError());
     return PPE_OK;
 }
