@@ -39,6 +39,7 @@ from paper_2604_01800_gb300 import shard  # noqa: E402
 
 METRIC = "PPE solves/s at rel-res 1e-8: hybrid vs plain PCG, 1 GB300; stencil HBM GB/s"
 WEIGHTS = os.path.join(ROOT, "paper_2604_01800_gb300", "weights", "hydea_mconv.ppenet")
+CONV_WEIGHTS = os.path.join(ROOT, "paper_2604_01800_gb300", "weights", "hydea_conv.ppenet")
 TOL = 1e-8
 L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2
 SOURCES = 5                         # distinct sources of the headline workload, cycled over the steps
@@ -349,6 +350,7 @@ def run_native(args):
         line["c1_fp64"] = _safe(small_fp64, api, dev, flush)
         line["c2_mixed"] = _safe(refined_box, api, dev, flush, peaks, peak_src)
         line["multigrid_partner"] = _safe(mg_partner, api, dev, flush, peaks)
+        line["ablation_mesh_conv"] = _safe(conv_ablation, api, dev, flush, ws)
         if not args.no_sweep:
             line["stencil_sweep"] = _safe(stencil_sweep, api, dev, peaks)
     if not args.no_extras:
@@ -411,6 +413,71 @@ def conv_roofline(api, net, grid, dev, peaks, peak_src, flush, reps=20):
             "frac": tf / peaks["bf16_tflops"], "traffic": None, "ms_per_inference": 1e3 * t,
             "gflop_per_inference": flops / 1e9, "peak_source": f"bf16_tflops burst ({peak_src})",
             "note": "whole inference (all launches) timed; the tensor-core convolutions are part of it"}
+
+
+def conv_ablation(api, dev, flush, ws):
+    """Sec. 3.2's ablation: the network trained with standard convolutions
+    (eta = 1 in every layer) against the Mesh-Conv network, same recipe and
+    number of steps, on the cylinder grid.  Per network: the hybrid solve
+    (median over the sources) and the share of the exact error energy that
+    one DLSM step removes from a zero start, (b.e)^2 / (e.Ae) / (b.x*), with
+    x* from an FP64 solve to 1e-12 and A applied by ppe_apply."""
+    import torch
+    w0 = ws[0]
+    grid = api.ppe_create_grid(w0.dx, w0.dy, w0.mask)
+    V = torch.outer(torch.tensor(w0.dy), torch.tensor(w0.dx)).to(dev)
+    srcs, bs, xs = [], [], []
+    for w in ws:
+        S = torch.tensor(w.f, dtype=torch.float64, device=dev)
+        x = torch.zeros_like(S)
+        api.ppe_solve(grid, S, x, 1e-12, api.PPE_MODE_PCG, api.PPE_PREC_FP64)
+        b = -V * S
+        srcs.append(S)
+        bs.append(b - b.mean())
+        xs.append(x)
+    out = {"workload": w0.name, "sources": len(ws)}
+    for key, path in (("mesh_conv", WEIGHTS), ("standard_conv", CONV_WEIGHTS)):
+        if not os.path.exists(path):
+            out[key] = {"error": "weights missing"}
+            continue
+        net = api.net_load(path)
+        net.attach(grid)
+        shares = []
+        for b, xstar in zip(bs, xs):
+            rhat = (b / b.norm()).float().reshape(1, w0.ny, w0.nx).contiguous()
+            e = torch.empty_like(rhat)
+            net.infer(grid, rhat, e)
+            e = e[0].double()
+            e = e - e.mean()
+            Ae = torch.empty_like(e)
+            api.ppe_apply(grid, e.contiguous(), Ae)
+            shares.append(float((b * e).sum() ** 2 / (e * Ae).sum() / (b * xstar).sum()))
+        x = torch.zeros_like(srcs[0])
+        ms, infos = [], []
+        for S in srcs:
+            api.ppe_solve(grid, S, x.zero_(), TOL, api.PPE_MODE_HYBRID, api.PPE_PREC_MIXED, net=net)   # warm
+            flush.fill_(1.0)
+            x.zero_()
+            a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            infos.append(api.ppe_solve(grid, S, x, TOL, api.PPE_MODE_HYBRID, api.PPE_PREC_MIXED, net=net))
+            c.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(c))
+        log = os.path.splitext(path)[0] + ".train_log.json"
+        rel_loss = None
+        if os.path.exists(log):
+            with open(log) as f:
+                rel_loss = json.load(f)["log"][-1]["rel_loss_ema"]
+        out[key] = {"energy_share_first_dlsm_step": float(np.median(shares)),
+                    "hybrid_ms_per_solve": float(np.median(ms)),
+                    "hybrid_iters": float(np.median([i["iters_pcg"] + i["iters_dlsm"] for i in infos])),
+                    "dlsm_steps": float(np.median([i["iters_dlsm"] for i in infos])),
+                    "all_ok": bool(all(i["status"] == 0 for i in infos)),
+                    "train_rel_loss_final": rel_loss}
+        net.close()
+    grid.close()
+    return out
 
 
 def mg_partner(api, dev, flush, peaks, reps=10):

@@ -23,6 +23,10 @@
 // different output-channel slices of one patch receive its activation
 // windows from one multicast TMA load, and the cm CTAs that compute the same
 // slice of different patches receive its weight tiles from one multicast.
+// The issuing is spread over the cluster (the TMA unit's rate in rows is
+// what limits a stage): each CTA of a patch row loads one piece of the
+// window, and the three taps' weight tiles come from different CTAs of a
+// slice column.
 // Every CTA of the cluster releases a stage to all of them (multicast MMA
 // commit), so a stage is refilled only when every CTA that received it has
 // consumed it.
@@ -68,6 +72,7 @@ struct TcArgs {
     int mtiles, nslices;    // image patches; output-channel slices
     int cm, cn;             // cluster shape: cm patches x cn slices (cm * cn CTAs)
     int units;              // cluster work units: ceil(mtiles / cm) x (nslices / cn)
+    int qa, pa;             // a halo window is loaded as pa pieces of qa image rows, one per CTA of a patch row
     uint32_t bar_off;       // byte offset of the barriers, past the pipeline stages
     const float *bias;
     Epi epi;
@@ -173,7 +178,8 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     const uint32_t b_bytes = (uint32_t)a.n_tile * RB;                 // one tap's weight tile
-    const uint32_t tx_bytes = A_BYTES + 3 * b_bytes;                  // bytes landed per stage
+    const uint32_t piece_bytes = (uint32_t)(a.qa * TC_TW) * RB;       // qa window rows
+    const uint32_t tx_bytes = a.pa * piece_bytes + 3 * b_bytes;       // bytes landed per stage
     const uint32_t stage_bytes = (tx_bytes + 1023u) & ~1023u;         // 1024-aligned stage stride
     // barriers: full[8], empty[8] of the stages; acc_full[2], acc_empty[2] of
     // the two TMEM accumulators; then the TMEM address slot
@@ -248,19 +254,24 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
                     const int c0 = (kb / 3) * BK, kx = kb % 3;
                     const uint32_t sa = base + stage_bytes * s, sb = sa + A_BYTES;
                     mbar_expect_tx(full0 + 8 * s, tx_bytes);
-                    if (a.cn == 1)
-                        tma_load_4d(sa, &tmA, full0 + 8 * s, c0, x0 + kx - 1, y0 - 1, img);
-                    else if (rn == 0)
-                        tma_load_4d_mc(sa, &tmA, full0 + 8 * s, c0, x0 + kx - 1, y0 - 1, img, mask_a);
-                    if (a.cm == 1 || rm == 0) {
+                    // the window's piece rn (image rows rn*qa ..) to the CTAs of this patch row
+                    if (rn < a.pa) {
+                        const int r0 = rn * a.qa;
+                        if (a.cn == 1)
+                            tma_load_4d(sa, &tmA, full0 + 8 * s, c0, x0 + kx - 1, y0 - 1 + r0, img);
+                        else
+                            tma_load_4d_mc(sa + r0 * ATOM, &tmA, full0 + 8 * s, c0, x0 + kx - 1, y0 - 1 + r0, img,
+                                           mask_a);
+                    }
+                    // weight tile of tap (ky, kx) from the CTA ky % cm of this slice column
 #pragma unroll
-                        for (int ky = 0; ky < 3; ++ky) {
-                            const int k0 = (3 * ky + kx) * a.cin + c0;      // tap (ky, kx) of the packed weights
-                            if (a.cm == 1)
-                                tma_load_2d(sb + ky * b_bytes, &tmB, full0 + 8 * s, k0, n0);
-                            else
-                                tma_load_2d_mc(sb + ky * b_bytes, &tmB, full0 + 8 * s, k0, n0, mask_b);
-                        }
+                    for (int ky = 0; ky < 3; ++ky) {
+                        if (ky % a.cm != rm) continue;
+                        const int k0 = (3 * ky + kx) * a.cin + c0;
+                        if (a.cm == 1)
+                            tma_load_2d(sb + ky * b_bytes, &tmB, full0 + 8 * s, k0, n0);
+                        else
+                            tma_load_2d_mc(sb + ky * b_bytes, &tmB, full0 + 8 * s, k0, n0, mask_b);
                     }
                     armed = it + 1;
                 }
@@ -485,29 +496,48 @@ ppe_status conv3x3_tc(const ConvArgs &a, cudaStream_t s)
     int *err = err_flag();
     const int bk = pick_bk(a.cin);
     const int rb = 2 * bk;
-    // output-channel slice: the whole of Cout up to 128 (a stage holds three
-    // taps' weight tiles beside the halo window)
-    int n_tile = a.cout;
-    while (n_tile > 128) n_tile /= 2;
-    if (a.cout % n_tile || n_tile % 16) n_tile = 16;
+    // Output-channel slice.  A stage delivers a halo window (144 rows) and
+    // three weight tiles (3 n rows) into every CTA that uses it, and what
+    // bounds these layers is the bytes an SM takes in (about 30 per cycle,
+    // measured, multicast or not).  Per SM that is ceil(tiles / SMs) x stages
+    // per tile x the stage's rows: wide slices reuse a window over more output
+    // channels, narrow ones spread few patches over more SMs.  Take the width
+    // (a divisor of Cout, 16..128) that minimises it, the wider on ties.
     const int nsm = sm_count();
     const int tiles_x = (a.W + TC_TW - 1) / TC_TW, tiles_y = (a.H + TC_TH - 1) / TC_TH;
     const long mtiles = (long)tiles_x * tiles_y * a.B;
-    // few output patches (deep U-Net levels): split the output channels until
-    // every SM has a tile; the slices of a patch share its activation loads
-    while (mtiles * (a.cout / n_tile) < nsm && n_tile % 32 == 0 && n_tile > 16 && a.cout % (n_tile / 2) == 0)
-        n_tile /= 2;                                          // stays a multiple of 16
+    const int kiters = 3 * (a.cin / bk);
+    int n_tile = 0;
+    double best = 0.0;
+    for (int n = std::min(a.cout, 128); n >= 16; --n) {
+        if (a.cout % n || n % 16) continue;
+        const long tiles = mtiles * (a.cout / n);
+        const double per_sm = (double)((tiles + nsm - 1) / nsm) * kiters * (TC_WIN + 3 * n);
+        if (n_tile == 0 || per_sm < best) {
+            best = per_sm;
+            n_tile = n;
+        }
+    }
     const int nslices = a.cout / n_tile;
     // cluster: cn slices of one patch (multicast activations) x cm patches
-    // of one slice (multicast weights), at most 8 CTAs
+    // of one slice (multicast weights), at most 4 CTAs: clusters of 8 at one
+    // CTA per SM (about 190 KB of shared memory each) were measured to run
+    // in two waves where those of 4 ran in one
     int cn = 1;
-    for (int d = 8; d >= 2; --d)
+    for (int d = 4; d >= 2; --d)
         if (nslices % d == 0) { cn = d; break; }
     // pairs of patches share their weight loads when there are patches enough
     // to keep every SM busy with pairs
-    const int cm = (cn <= 4 && mtiles >= nsm / 2) ? 2 : 1;
+    const int cm = (cn <= 2 && mtiles >= nsm / 2) ? 2 : 1;
     const int cs = cm * cn;
     const long units = (mtiles + cm - 1) / cm * (nslices / cn);
+    // the cn CTAs of a patch row each load a piece of its halo windows: qa
+    // image rows, the smallest divisor of the window height that needs at
+    // most cn pieces
+    int qa = TC_TH + 2;
+    for (int d = 1; d <= TC_TH + 2; ++d)
+        if ((TC_TH + 2) % d == 0 && (TC_TH + 2) / d <= cn) { qa = d; break; }
+    const int pa = (TC_TH + 2) / qa;
     int tmem_cols = 32;                                       // two accumulators of n_tile columns
     while (tmem_cols < 2 * n_tile) tmem_cols *= 2;
     const int stage_bytes = ((TC_WIN + 3 * n_tile) * rb + 1023) / 1024 * 1024;
@@ -515,7 +545,7 @@ ppe_status conv3x3_tc(const ConvArgs &a, cudaStream_t s)
     // shared memory and both CTAs' accumulators fit the 512 TMEM columns
     int ctas_per_sm = 2;
     int stages = std::min(TC_MAX_STAGES, (110 * 1024) / stage_bytes);
-    if (stages < 3 || tmem_cols > 256) {
+    if (stages < 3 || tmem_cols > 256 || mtiles * nslices <= nsm) {
         ctas_per_sm = 1;
         stages = std::min(TC_MAX_STAGES, (200 * 1024) / stage_bytes);
     }
@@ -532,7 +562,7 @@ ppe_status conv3x3_tc(const ConvArgs &a, cudaStream_t s)
     {
         cuuint64_t dims[4] = {(cuuint64_t)a.cin, (cuuint64_t)a.W, (cuuint64_t)a.H, (cuuint64_t)a.B};
         cuuint64_t strides[3] = {(cuuint64_t)a.cin * 2, (cuuint64_t)a.W * a.cin * 2, (cuuint64_t)a.H * a.W * a.cin * 2};
-        cuuint32_t box[4] = {(cuuint32_t)bk, (cuuint32_t)TC_TW, (cuuint32_t)(TC_TH + 2), 1};
+        cuuint32_t box[4] = {(cuuint32_t)bk, (cuuint32_t)TC_TW, (cuuint32_t)qa, 1};
         cuuint32_t es[4] = {1, 1, 1, 1};
         CUresult r = encode(&mA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void *)a.in, dims, strides, box, es,
                             CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -566,6 +596,8 @@ ppe_status conv3x3_tc(const ConvArgs &a, cudaStream_t s)
     t.cm = cm;
     t.cn = cn;
     t.units = (int)units;
+    t.qa = qa;
+    t.pa = pa;
     t.bar_off = (uint32_t)bar_off;
     t.bias = a.bias;
     t.epi = a.epi;
