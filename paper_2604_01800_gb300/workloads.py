@@ -6,6 +6,11 @@
     python -m paper_2604_01800_gb300.workloads train N STEPS # training steps, batch 8 on an N x N stretched grid
     python -m paper_2604_01800_gb300.workloads hybrid        # hybrid solve (shipped network) on the 256x256 cylinder grid
     python -m paper_2604_01800_gb300.workloads mg NAME       # multigrid-partner solve: c1, c2, c3 or c5
+    python -m paper_2604_01800_gb300.workloads pcg NAME      # plain mixed Jacobi PCG: c1, c2, c3 or c5
+
+A trailing ``host`` (``hybrid host``, ``pcg c3 host``) runs the solves with
+the host-loop driver, which launches the same solver kernel directly instead
+of from the solve's CUDA graph (a profiler replays direct launches).
 
 Each runs its solve (or inference) twice or more: the first launch warms up,
 so a profiler can skip it (``-s 1``).  Synthetic inputs only.
@@ -85,7 +90,7 @@ def train(n: int, steps: int):
         print(f"train {n}x{n} step {i}: loss {loss:.4e}, {1e3 * (time.perf_counter() - t):.1f} ms")
 
 
-def hybrid():
+def hybrid(host: bool = False):
     import os
 
     import torch
@@ -94,6 +99,7 @@ def hybrid():
     g = api.ppe_create_grid(w.dx, w.dy, w.mask)
     net = api.net_load(os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "hydea_mconv.ppenet"))
     net.attach(g)
+    api.ppe_set_options(g, host_loop=int(host))
     rhs = torch.tensor(w.f, dtype=torch.float64, device="cuda")
     for _ in range(2):
         x = torch.zeros_like(rhs)
@@ -102,15 +108,19 @@ def hybrid():
     print(f"hybrid c3: {info['iters_pcg']} + {info['iters_dlsm']} iterations, {info['ms_total']:.2f} ms")
 
 
-def mg(name: str):
-    import torch
-    from . import api, inputs as I
+def _system(name: str):
+    from . import inputs as I
     if name == "c5":
         dx, dy, bodies = I.config5_grid()
-        f = I.config5_rhs(0, dx, dy, bodies)
-    else:
-        w = {"c1": I.config1, "c2": I.config2, "c3": I.config3}[name](0)
-        dx, dy, f = w.dx, w.dy, w.f
+        return dx, dy, I.config5_rhs(0, dx, dy, bodies)
+    w = {"c1": I.config1, "c2": I.config2, "c3": I.config3}[name](0)
+    return w.dx, w.dy, w.f
+
+
+def mg(name: str):
+    import torch
+    from . import api
+    dx, dy, f = _system(name)
     g = api.ppe_create_grid(dx, dy)
     api.ppe_set_options(g, preconditioner=1)
     rhs = torch.tensor(f, dtype=torch.float64, device="cuda")
@@ -119,6 +129,20 @@ def mg(name: str):
         info = api.ppe_solve(g, rhs, x, 1e-8, api.PPE_MODE_PCG, api.PPE_PREC_MIXED)
     torch.cuda.synchronize()
     print(f"multigrid {name}: {info['iters_pcg']} iterations, {info['ms_total']:.2f} ms")
+
+
+def pcg(name: str, host: bool = False):
+    import torch
+    from . import api
+    dx, dy, f = _system(name)
+    g = api.ppe_create_grid(dx, dy)
+    api.ppe_set_options(g, host_loop=int(host))
+    rhs = torch.tensor(f, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        x = torch.zeros_like(rhs)
+        info = api.ppe_solve(g, rhs, x, 1e-8, api.PPE_MODE_PCG, api.PPE_PREC_MIXED)
+    torch.cuda.synchronize()
+    print(f"pcg {name}: {info['iters_pcg']} iterations, {info['ms_total']:.2f} ms")
 
 
 def main(argv=None):
@@ -132,9 +156,11 @@ def main(argv=None):
     elif a[0] == "train":
         train(int(a[1]), int(a[2]))
     elif a[0] == "hybrid":
-        hybrid()
+        hybrid(a[-1] == "host")
     elif a[0] == "mg":
         mg(a[1] if len(a) > 1 else "c2")
+    elif a[0] == "pcg":
+        pcg(a[1] if len(a) > 1 and a[1] != "host" else "c3", a[-1] == "host")
     else:
         raise SystemExit(__doc__)
 
