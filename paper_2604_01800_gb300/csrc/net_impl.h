@@ -2,6 +2,7 @@
 // training module.
 #pragma once
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -64,6 +65,16 @@ ppe_status net_forward(ppe_net *n, NetCache *c, int B, const InputSrc &src, cons
 
 }  // namespace ppe
 
+// Parameter versions are unique across the process: a network's versions
+// start at a serial of its own (upper 32 bits), so a graph or cache keyed by
+// (pointer, version) never matches a later network that happens to reuse a
+// freed network's memory.
+inline uint64_t net_version_base()
+{
+    static std::atomic<uint64_t> serial{0};
+    return (serial.fetch_add(1) + 1) << 32;
+}
+
 struct ppe_net {
     ppe_net_config cfg{};
     std::vector<ppe::ConvLayer> layers;
@@ -74,7 +85,7 @@ struct ppe_net {
     float *adam_m = nullptr, *adam_v = nullptr;
     ppe::bf16 *wp = nullptr, *wt = nullptr;
     double *scratch = nullptr;
-    uint64_t version = 1, packed_version = 0;
+    uint64_t version = net_version_base() + 1, packed_version = 0;
     const float *packed_src = nullptr;
     int64_t step = 0;
     bool use_tc = true;

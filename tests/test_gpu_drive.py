@@ -127,3 +127,33 @@ def test_batch_graph_and_host_loop_agree(api, mode):
         assert oracle.true_relres(w.dx, w.dy, w.f, xa[k]) <= TOL * 1.05
     if mode == "hybrid":
         assert sum(i["net_calls"] for i in ia) >= len(ws)
+
+
+def test_replaced_network_is_not_replayed_from_a_stale_graph(api):
+    """A grid's solve graph holds the attached network's forward pass.  After
+    that network is destroyed, a new one attached to the same grid (whose
+    object and buffers may reuse the freed memory) must get graphs of its
+    own: its hybrid solve on the reused grid equals, bit for bit, the same
+    solve on a fresh grid."""
+    w = _ragged(64, 48, 21)
+    cfg = api.net_default_config(widths=[16, 32], c_last=8, trunk_hidden=[16, 24], phi_hidden=4)
+    opts = dict(dlsm_stall_limit=0, hybrid_budget=60)
+    grid = api.ppe_create_grid(w.dx, w.dy)
+    first = api.net_create(cfg, 11)
+    first.attach(grid)
+    _solve(api, grid, w, api.PPE_MODE_HYBRID, api.PPE_PREC_MIXED, 0, net=first, **opts)
+    first.close()
+    second = api.net_create(cfg, 12)
+    second.attach(grid)
+    xa, ia = _solve(api, grid, w, api.PPE_MODE_HYBRID, api.PPE_PREC_MIXED, 0, net=second, **opts)
+    second.close()
+    fresh = api.ppe_create_grid(w.dx, w.dy)
+    again = api.net_create(cfg, 12)
+    again.attach(fresh)
+    xb, ib = _solve(api, fresh, w, api.PPE_MODE_HYBRID, api.PPE_PREC_MIXED, 0, net=again, **opts)
+    assert ia["status"] == 0 and ib["status"] == 0 and ia["iters_dlsm"] >= 1
+    assert (ia["iters_pcg"], ia["iters_dlsm"]) == (ib["iters_pcg"], ib["iters_dlsm"])
+    assert np.array_equal(xa, xb)
+    again.close()
+    fresh.close()
+    grid.close()
