@@ -392,6 +392,16 @@ PPE_API ppe_status ppe_debug_mg_vcycle(ppe_grid *grid, const float *r_dev, float
 PPE_API ppe_status ppe_debug_conv3x3(const void *in_bf16, const void *w_bf16, const float *bias, int B, int H, int W,
                                      int cin, int cout, float *out, int impl, void *stream);
 
+/* Test hook: the weight gradient of one 3x3 convolution (Sec. 2.4, the
+ * training step's backward), added into dW [cout][cin][9] (FP32, tap =
+ * 3*ky + kx): dW[co][ci][t] += sum over pixels of dZ[p][co] * X[p + t][ci],
+ * X zero outside the image.  dZ_bf16 [B][H][W][cout] and X_bf16
+ * [B][H][W][cin] are BF16 NHWC.  impl 0: tensor-core (tcgen05) kernel
+ * (PPE_ERR_ARG for channel counts it does not take), 1: CUDA-core kernel.
+ * All pointers are device pointers. */
+PPE_API ppe_status ppe_debug_wgrad(const void *dZ_bf16, const void *X_bf16, int B, int H, int W, int cin, int cout,
+                                   float *dW, int impl, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

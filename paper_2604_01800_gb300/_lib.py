@@ -113,6 +113,8 @@ _SIGS = [
                                          _P, ctypes.POINTER(ppe_solve_info)]),
     ("ppe_autotune", ctypes.c_int, [_P, _P, ctypes.POINTER(ppe_tune_report)]),
     ("ppe_debug_mg_vcycle", ctypes.c_int, [_P, _P, _P, _P]),
+    ("ppe_debug_wgrad", ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P,
+                                       ctypes.c_int, _P]),
     ("ppe_source", ctypes.c_int, [_P, _P, _P, ctypes.c_double, _P, _P]),
     ("ppe_project", ctypes.c_int, [_P, _P, ctypes.c_double, _P, _P, _P, _P]),
     ("ppe_last_error", ctypes.c_char_p, []),

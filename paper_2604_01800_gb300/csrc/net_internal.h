@@ -64,5 +64,9 @@ ppe_status conv3x3_simt(const ConvArgs &a, cudaStream_t s);
 ppe_status conv3x3_tc(const ConvArgs &a, cudaStream_t s);
 bool conv3x3_tc_supported(const ConvArgs &a);
 ppe_status conv3x3_tc_prepare();
+// tcgen05 weight gradient dW[co][ci][9] += (dZ, X); PPE_ERR_ARG for channel
+// counts the kernel does not take (then the CUDA-core kernel runs)
+bool wgrad_tc_supported(int cin, int cout);
+ppe_status wgrad_tc(const bf16 *dZ, const bf16 *X, int B, int H, int W, int cin, int cout, float *dW, cudaStream_t s);
 
 }  // namespace ppe

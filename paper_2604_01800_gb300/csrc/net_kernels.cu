@@ -150,6 +150,21 @@ __global__ void __launch_bounds__(CI_PX) conv_in_staged_kernel(InputSrc src, int
     __shared__ float ws[CI_CH][9];
     __shared__ float bs[CI_CH];
     __shared__ __align__(16) bf16 tile[CI_PX][CI_CH + 8];      // padded rows: conflict-free column writes
+    // the solver state's residual, read once per block instead of per tap
+    __shared__ const void *sr;
+    __shared__ int sfp64, spitch;
+    __shared__ double smu;
+    __shared__ float sscale;
+    if (threadIdx.x == 0 && src.st) {
+        const SysState &st = *src.st;
+        const SysDesc &sd = *src.sd;
+        sr = sd.r[st.cur];
+        sfp64 = sd.precision == PPE_PREC_FP64;
+        spitch = sd.pitch;
+        smu = st.mu;
+        sscale = st.rho > 0.0 ? (float)(1.0 / sqrt(st.rho)) : 0.f;
+    }
+    __syncthreads();
     const int x0 = blockIdx.x * CI_PX, y = blockIdx.y, b = blockIdx.z;
     const int x = x0 + threadIdx.x;
     const int np = min(CI_PX, W - x0);
@@ -158,8 +173,14 @@ __global__ void __launch_bounds__(CI_PX) conv_in_staged_kernel(InputSrc src, int
     for (int t = 0; t < 9; ++t) {
         int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
         float s = 0.f;
-        if (x < W && yy >= 0 && yy < H && xx >= 0 && xx < W) {
-            s = input_at(src, b, yy, xx);
+        if (x < W && yy >= 0 && yy < H && xx >= 0 && xx < W && yy < src.ny && xx < src.nx) {
+            if (src.st) {
+                const size_t k = (size_t)yy * spitch + xx;
+                const double r = sfp64 ? ((const double *)sr)[k] : (double)((const float *)sr)[k];
+                s = (float)(r - smu) * sscale;
+            } else {
+                s = src.r[(size_t)b * src.bstride + (size_t)yy * src.pitch + xx] * src.scale;
+            }
             if (eta) s *= eta[yy * W + xx];
         }
         v[t] = s;

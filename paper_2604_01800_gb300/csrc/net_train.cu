@@ -549,6 +549,40 @@ static ppe_status loss_de(ppe_grid *g, TrainWs *w, int B, const float *R, cudaSt
     return PPE_OK;
 }
 
+// CUDA-core weight gradient dW[co][ci][9] += (dZ, X)
+static ppe_status wgrad_simt(const bf16 *dZ, const bf16 *Xb, int B, int H, int W, int cin, int cout, float *dW,
+                             cudaStream_t s)
+{
+    if (cin % 8 || cout % 8) {
+        set_error("weight gradient: channel counts must be multiples of 8");
+        return PPE_ERR_ARG;
+    }
+    // two output channels per thread from 64 on (each loaded input value
+    // then feeds twice the products); one below
+    const int nco = cout >= 64 ? 2 : 1;
+    const int tiles = B * ((W + WG_W - 1) / WG_W) * ((H + WG_H - 1) / WG_H);
+    dim3 grid((cout + 32 * nco - 1) / (32 * nco), (cin + 31) / 32, 1);
+    int blocks_xy = grid.x * grid.y;
+    int split = std::max(1, std::min(tiles, 592 / std::max(1, blocks_xy)));
+    int per = (tiles + split - 1) / split;
+    grid.z = (tiles + per - 1) / per;
+    // the shared-memory opt-in is a per-device attribute of each kernel
+    static PerDevice attrs;
+    if (!once_per_device(attrs, [](int) {
+            return cudaFuncSetAttribute(wgrad_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)wg_smem<1>()) == cudaSuccess &&
+                   cudaFuncSetAttribute(wgrad_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)wg_smem<2>()) == cudaSuccess;
+        }))
+        return cuda_status(cudaGetLastError(), "cudaFuncSetAttribute(wgrad_kernel)");
+    if (nco == 2)
+        wgrad_kernel<2><<<grid, 256, wg_smem<2>(), s>>>(dZ, Xb, B, H, W, cin, cout, dW, per);
+    else
+        wgrad_kernel<1><<<grid, 256, wg_smem<1>(), s>>>(dZ, Xb, B, H, W, cin, cout, dW, per);
+    PPE_CUDA_TRY(cudaGetLastError());
+    return PPE_OK;
+}
+
 static ppe_status conv_backward(ppe_net *n, NetCache *c, TrainWs *w, int li, const bf16 *Xb, const float *P,
                                 float *grads, int B, cudaStream_t s)
 {
@@ -558,35 +592,11 @@ static ppe_status conv_backward(ppe_net *n, NetCache *c, TrainWs *w, int li, con
     const float *dY = w->g + w->G[li];
     const bf16 *Z = c->act + c->plan.Z[li];
     act_bwd(dY, Z, w->dZ, px * l.cout, l.cout, grads + l.off_b, s);
-    // weight gradient
-    {
-        if (l.cin % 8 || l.cout % 8) {
-            set_error("weight gradient: channel counts must be multiples of 8");
-            return PPE_ERR_ARG;
-        }
-        // two output channels per thread from 64 on (each loaded input value
-        // then feeds twice the products); one below
-        const int nco = l.cout >= 64 ? 2 : 1;
-        const int tiles = B * ((W + WG_W - 1) / WG_W) * ((H + WG_H - 1) / WG_H);
-        dim3 grid((l.cout + 32 * nco - 1) / (32 * nco), (l.cin + 31) / 32, 1);
-        int blocks_xy = grid.x * grid.y;
-        int split = std::max(1, std::min(tiles, 592 / std::max(1, blocks_xy)));
-        int per = (tiles + split - 1) / split;
-        grid.z = (tiles + per - 1) / per;
-        // the shared-memory opt-in is a per-device attribute of each kernel
-        static PerDevice attrs;
-        if (!once_per_device(attrs, [](int) {
-                return cudaFuncSetAttribute(wgrad_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)wg_smem<1>()) == cudaSuccess &&
-                       cudaFuncSetAttribute(wgrad_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)wg_smem<2>()) == cudaSuccess;
-            }))
-            return cuda_status(cudaGetLastError(), "cudaFuncSetAttribute(wgrad_kernel)");
-        if (nco == 2)
-            wgrad_kernel<2><<<grid, 256, wg_smem<2>(), s>>>(w->dZ, Xb, B, H, W, l.cin, l.cout, grads + l.off_w, per);
-        else
-            wgrad_kernel<1><<<grid, 256, wg_smem<1>(), s>>>(w->dZ, Xb, B, H, W, l.cin, l.cout, grads + l.off_w, per);
-    }
+    // weight gradient: tensor cores where the kernel takes the channel counts
+    if (n->use_tc && wgrad_tc_supported(l.cin, l.cout))
+        PPE_TRY(wgrad_tc(w->dZ, Xb, B, H, W, l.cin, l.cout, grads + l.off_w, s));
+    else
+        PPE_TRY(wgrad_simt(w->dZ, Xb, B, H, W, l.cin, l.cout, grads + l.off_w, s));
     // data gradient: forward convolution of dZ with the transposed, flipped kernel
     ConvArgs a;
     a.in = w->dZ; a.w = n->wt + l.off_wt; a.bias = nullptr;
@@ -705,6 +715,20 @@ static ppe_status loss_and_grad(ppe_net *n, NetCache *c, TrainWs *w, ppe_grid *g
 }
 
 }  // namespace ppe
+
+extern "C" ppe_status ppe_debug_wgrad(const void *dZ, const void *X, int B, int H, int W, int cin, int cout, float *dW,
+                                      int impl, void *stream)
+{
+    ppe::clear_error();
+    if (!dZ || !X || !dW || B < 1 || H < 1 || W < 1 || cin < 1 || cout < 1) {
+        ppe::set_error("ppe_debug_wgrad: bad arguments");
+        return PPE_ERR_ARG;
+    }
+    const ppe::bf16 *z = (const ppe::bf16 *)dZ, *x = (const ppe::bf16 *)X;
+    if (impl == 0) return ppe::wgrad_tc(z, x, B, H, W, cin, cout, dW, (cudaStream_t)stream);
+    return ppe::wgrad_simt(z, x, B, H, W, cin, cout, dW, (cudaStream_t)stream);
+}
+
 
 using namespace ppe;
 

@@ -146,3 +146,48 @@ def test_params_only_file_restarts_the_optimiser(api, tmp_path):
     ft.train_step(grid, Rt, lr0=1e-3, total_steps=3, rho=0.0)
     moved = np.abs(ft.get_params() - before)
     assert moved.max() > 0.5e-3                        # a first Adam step moves by about lr0
+
+
+def _wgrad_fp64(dz, x):
+    """dW[co][ci][3 ky + kx] = sum over pixels of dZ[p][co] * X[p + (kx-1, ky-1)][ci],
+    X zero outside the image; FP64, one matrix product per tap."""
+    B, H, W, cout = dz.shape
+    cin = x.shape[3]
+    xp = np.zeros((B, H + 2, W + 2, cin))
+    xp[:, 1:-1, 1:-1] = x
+    out = np.zeros((cout, cin, 9))
+    Z = dz.reshape(-1, cout)
+    for ky in range(3):
+        for kx in range(3):
+            Xs = xp[:, ky:ky + H, kx:kx + W].reshape(-1, cin)
+            out[:, :, 3 * ky + kx] = Z.T @ Xs
+    return out
+
+
+# Every channel combination of the network (the stacked-tap form for Cin 32
+# and 64, one accumulator per tap for Cin >= 128, output channels split over
+# CTAs where the accumulators would not fit), ragged patches (H, W not
+# multiples of 16 and 8), and a batch whose CTAs walk many patches each.
+@pytest.mark.parametrize("B,H,W,cin,cout", [(2, 24, 20, 32, 32), (1, 19, 13, 32, 64), (2, 16, 24, 64, 32),
+                                             (1, 21, 17, 64, 64), (1, 16, 16, 64, 128), (1, 13, 22, 128, 64),
+                                             (1, 16, 8, 128, 128), (1, 8, 16, 128, 256), (1, 8, 8, 256, 128),
+                                             (1, 8, 8, 256, 256), (1, 16, 16, 32, 96), (2, 16, 16, 64, 96),
+                                             (8, 64, 64, 32, 32)])
+@pytest.mark.parametrize("impl", [0, 1], ids=["tcgen05", "simt"])
+def test_weight_gradient_matches_fp64(api, B, H, W, cin, cout, impl):
+    import ctypes
+    g = I.rng(500 + H + cin + cout)
+    bf = lambda a: torch.tensor(a, dtype=torch.float32).to(torch.bfloat16)   # noqa: E731
+    dz = bf(g.standard_normal((B, H, W, cout)))
+    x = bf(g.standard_normal((B, H, W, cin)))
+    ref = _wgrad_fp64(dz.float().numpy().astype(np.float64), x.float().numpy().astype(np.float64))
+    scale = _wgrad_fp64(np.abs(dz.float().numpy().astype(np.float64)), np.abs(x.float().numpy().astype(np.float64)))
+    dW = torch.zeros(cout, cin, 9, dtype=torch.float32, device="cuda")
+    L = api._lib.load()
+    dzd, xd = dz.cuda(), x.cuda()
+    st = L.ppe_debug_wgrad(ctypes.c_void_p(dzd.data_ptr()), ctypes.c_void_p(xd.data_ptr()), B, H, W, cin, cout,
+                           ctypes.c_void_p(dW.data_ptr()), impl, None)
+    api._lib.check(st, "ppe_debug_wgrad")
+    torch.cuda.synchronize()
+    err = np.abs(dW.cpu().numpy() - ref)
+    assert np.all(err <= 1e-5 * scale + 1e-5), float((err / (scale + 1e-30)).max())
