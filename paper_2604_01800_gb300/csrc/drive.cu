@@ -341,6 +341,11 @@ ppe_status drive_host(int n, ppe_grid *const *grids, LaunchSet &ls, int blocks, 
     }
     PPE_CUDA_TRY(cudaEventRecord(ls.ev0, stream));
     PPE_CUDA_TRY(cudaMemsetAsync(ls.st, 0, sizeof(SysState) * n, stream));
+    {
+        long max_cells = 0;
+        for (int s = 0; s < n; ++s) max_cells = std::max<long>(max_cells, (long)grids[s]->nx * grids[s]->ny);
+        PPE_TRY(launch_scale(ls.sys, ls.st, n, max_cells, stream));
+    }
     int launches = 0;
     ppe_status status = PPE_OK;
     Control ctl_host;
@@ -487,13 +492,28 @@ ppe_status build_graph(LaunchSet &ls, const SolverArgs &args_in, SolverVariant v
         if ((e = cudaGraphAddKernelNode(&init_node, g, nullptr, 0, &kp)) != cudaSuccess)
             return fail(e, "cudaGraphAddKernelNode(init)");
     }
+    // the power-of-two scale of every system (max |b|)
+    cudaGraphNode_t scale_node;
+    {
+        long max_cells = 0;
+        for (int s = 0; s < n; ++s) max_cells = std::max<long>(max_cells, (long)grids[s]->nx * grids[s]->ny);
+        int nn = n;
+        void *p[] = {&ls.sys, &ls.st, &nn};
+        cudaKernelNodeParams kp = {};
+        kp.func = const_cast<void *>(scale_kernel_fn());
+        kp.gridDim = scale_grid(n, max_cells);
+        kp.blockDim = dim3(256);
+        kp.kernelParams = p;
+        if ((e = cudaGraphAddKernelNode(&scale_node, g, &init_node, 1, &kp)) != cudaSuccess)
+            return fail(e, "cudaGraphAddKernelNode(scale)");
+    }
     // the loop
     cudaGraphNodeParams wp = {};
     wp.type = cudaGraphNodeTypeConditional;
     wp.conditional.handle = wh;
     wp.conditional.type = cudaGraphCondTypeWhile;
     wp.conditional.size = 1;
-    if ((e = cudaGraphAddNode(&while_node, g, &init_node, nullptr, 1, &wp)) != cudaSuccess)
+    if ((e = cudaGraphAddNode(&while_node, g, &scale_node, nullptr, 1, &wp)) != cudaSuccess)
         return fail(e, "cudaGraphAddNode(loop)");
     cudaGraph_t body = wp.conditional.phGraph_out[0];
     // solver segment: the cooperative persistent kernel, resuming systems that

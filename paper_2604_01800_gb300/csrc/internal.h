@@ -137,6 +137,10 @@ struct SysState {
     // true residuals, finalisation), and the time between a segment that asked
     // for a network direction and the segment that used it
     uint64_t ns_pcg, ns_dlsm, ns_fp64, ns_net, t_net0;
+    // bit pattern of max |b| over the system (set before the first segment by
+    // the scale kernel): the solver works on 2^-e b and 2^-e x, e its binary
+    // exponent, so that sums of squares stay inside the float-float range
+    uint64_t bmax_bits;
 };
 
 // Tiles [t0, t1) of a block; they belong to systems s0..s1.
@@ -188,6 +192,11 @@ ppe_status launch_solver_resume(const SolverArgs &a, SolverVariant v, int grid_b
                                 int resume);
 int solver_max_blocks(SolverVariant v, int blocks_per_sm_req);
 // Kernel function and dynamic shared memory of a variant (graph nodes).
+// max |b| of every system into its state (states zeroed before): the
+// power-of-two scale of the solve; one launch for n systems
+const void *scale_kernel_fn();
+dim3 scale_grid(int n, long max_cells);
+ppe_status launch_scale(const SysDesc *sys, SysState *st, int n, long max_cells, cudaStream_t s);
 const void *solver_kernel_fn(SolverVariant v);
 size_t solver_smem_bytes(SolverVariant v);
 // Set the variants' shared-memory attributes on the current device.

@@ -661,11 +661,13 @@ __device__ bool vcycle(const MgArgs &a, Sync &s, float mu0, double *dot)
 __device__ __forceinline__ double nonneg(double v) { return v > 0.0 ? v : (v == v ? 0.0 : v); }
 
 // (A u) in FP64 at fine cell (i, j), u = x + d
-__device__ __forceinline__ double apply64(const MgArgs &a, int i, int j)
+// A (x + d / sigma) at cell (i, j), FP64; unsig = 1 / sigma (d holds the
+// scaled FP32 correction of the current inner solve)
+__device__ __forceinline__ double apply64(const MgArgs &a, int i, int j, double unsig)
 {
     const int nx = a.nx;
     const size_t k = (size_t)j * nx + i;
-    auto u = [&](size_t q) { return a.x[q] + (double)a.d[q]; };
+    auto u = [&](size_t q) { return a.x[q] + (double)a.d[q] * unsig; };
     const double c = u(k);
     double ax = 0.0, ay = 0.0;
     if (i > 0) ax += a.fx[i] * (c - u(k - 1));
@@ -703,6 +705,10 @@ __global__ void __launch_bounds__(MG_THREADS, 1) mg_kernel(MgArgs a)
     const double incompat = st[2] > 0.0 ? fabs(st[0]) / st[2] : 0.0;
     int status = PPE_OK, iters = 0, refinements = 0, stall = 0, stalled = 0;
     double relres = 0.0, relres_prev = 0.0;
+    // the FP32 inner solve works on 2^-e r, e the binary exponent of the true
+    // residual's norm (exact scaling: the FP32 vectors stay in range whatever
+    // the scale of the source); d is folded back with the inverse
+    double sig = 1.0;
     if (!isfinite(st[0]) || !isfinite(st[1])) {
         status = PPE_ERR_NAN;
     } else if (!(incompat <= 1e-6)) {
@@ -711,12 +717,13 @@ __global__ void __launch_bounds__(MG_THREADS, 1) mg_kernel(MgArgs a)
         for (int k = dg.wid; k < n; k += dg.nw) a.x[k] = 0.0;
     } else {
         for (;;) {
-            // true residual of x + d in FP64
+            // true residual of x + d / sigma in FP64
+            const double unsig = 1.0 / sig;
             double rs[2] = {0.0, 0.0};
             for (int k = dg.wid; k < n; k += dg.nw) {
                 const int i = k % nx, j = k / nx;
                 const double b = -a.dx[i] * a.dy[j] * a.S[k] - mub;
-                const double rv = b - apply64(a, i, j);
+                const double rv = b - apply64(a, i, j, unsig);
                 a.r64[k] = rv;
                 rs[0] += rv;
                 rs[1] += rv * rv;
@@ -727,10 +734,15 @@ __global__ void __launch_bounds__(MG_THREADS, 1) mg_kernel(MgArgs a)
             relres = sqrt(rsq) / bnorm;
             ++refinements;
             // fold d into x; the FP32 residual of the next inner solve
+            if (rsq > 0.0 && isfinite(rsq)) {
+                int e = 0;
+                frexp(sqrt(rsq), &e);
+                sig = ldexp(1.0, -max(-1020, min(1020, e)));
+            }
             for (int k = dg.wid; k < n; k += dg.nw) {
-                a.x[k] += (double)a.d[k];
+                a.x[k] += (double)a.d[k] * unsig;
                 a.d[k] = 0.f;
-                r[k] = (float)(a.r64[k] - mu);
+                r[k] = (float)((a.r64[k] - mu) * sig);
             }
             if (!grid_bar(a, s)) return;
             if (!isfinite(relres)) { status = PPE_ERR_NAN; break; }
@@ -742,7 +754,7 @@ __global__ void __launch_bounds__(MG_THREADS, 1) mg_kernel(MgArgs a)
             relres_prev = relres;
             if (stall >= 3) { status = PPE_ERR_NOT_CONVERGED; stalled = 1; break; }
             const double target_sq = fmax((double)MG_INNER_RTOL * MG_INNER_RTOL * rsq,
-                                           0.25 * a.tol * a.tol * bnorm * bnorm);
+                                           0.25 * a.tol * a.tol * bnorm * bnorm) * sig * sig;
             // inner MG-PCG on A d = r (FP32 vectors, FP64 scalars)
             float mur = 0.f;                   // lagged mean of the FP32 residual
             double g[1] = {0.0};

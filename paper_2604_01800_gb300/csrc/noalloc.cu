@@ -205,6 +205,7 @@ extern "C" ppe_status ppe_solve_noalloc(int nx, int ny, const double *dx, const 
     PPE_CUDA_TRY(cudaMemsetAsync(d_st, 0, sizeof(SysState), st));
     PPE_CUDA_TRY(cudaMemsetAsync(d_ctl, 0, sizeof(Control), st));
     PPE_CUDA_TRY(cudaMemsetAsync(d_arrive, 0, sizeof(uint32_t), st));
+    PPE_TRY(launch_scale(d_sd, d_st, 1, (long)nx * ny, st));
 
     SolverArgs a;
     std::memset(&a, 0, sizeof a);

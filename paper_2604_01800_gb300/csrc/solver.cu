@@ -443,9 +443,33 @@ __device__ __forceinline__ double fast_div(double a, double b)
 // passes over one tile; thread sums go to acc (lane 0 of each warp)
 // ---------------------------------------------------------------------------
 
-// b statistics: b = -V S
-template <typename T, typename S> __device__ void pass_init(S &sm, const SysDesc &sd, int i0, int j0, Acc &acc)
+// The solve's power-of-two scale sigma = 2^-e, e the binary exponent of max |b|
+// (1 for a zero or non-finite b).  Multiplying by it is exact, so the scaled
+// solve is the unscaled one bit for bit wherever that one stays in range.
+__device__ __forceinline__ double sys_scale(const SysState &s)
 {
+    const uint64_t bits = s.bmax_bits;
+    if (bits == 0 || bits >= 0x7FF0000000000000ull) return 1.0;
+    int e = 0;
+    frexp(__longlong_as_double((long long)bits), &e);
+    return ldexp(1.0, -max(e, -1020));
+}
+
+// 1 / sys_scale(s), also exact
+__device__ __forceinline__ double sys_unscale(const SysState &s)
+{
+    const uint64_t bits = s.bmax_bits;
+    if (bits == 0 || bits >= 0x7FF0000000000000ull) return 1.0;
+    int e = 0;
+    frexp(__longlong_as_double((long long)bits), &e);
+    return ldexp(1.0, max(e, -1020));
+}
+
+// b statistics: b = -V S (scaled)
+template <typename T, typename S>
+__device__ void pass_init(S &sm, const SysDesc &sd, const SysState &st, int i0, int j0, Acc &acc)
+{
+    const double sg = sys_scale(st);
     using G = Geo<S::TW>;
     constexpr int WX = G::WX, WN = G::WN, OX = G::OX, OY = G::OY, RN = G::RN, NRL = G::NRL, TILE_X = G::TX;
     constexpr int TILE_N = G::TN;
@@ -457,7 +481,7 @@ template <typename T, typename S> __device__ void pass_init(S &sm, const SysDesc
     for (int c = 0; c < 4; ++c) {
         int i = i0 + tx + 32 * c;
         if (tx + 32 * c < TILE_X && i < sd.nx && j < sd.ny) {
-            double b = -sd.dx[i] * sd.dy[j] * sd.f[(size_t)j * sd.nx + i];
+            double b = -sd.dx[i] * sd.dy[j] * sd.f[(size_t)j * sd.nx + i] * sg;
             t[0] += b; t[1] += b * b; t[2] += fabs(b);
         }
     }
@@ -476,6 +500,7 @@ __device__ void pass_res(S &sm, const SysDesc &sd, const SysState &st, int i0, i
     double *X = reinterpret_cast<double *>(&sm.u.w);
     load_coef_d(sm, sd, i0, j0, tag);
     const T *d = (const T *)sd.d;
+    const double sg = sys_scale(st);
     double xv[NRL];
 #pragma unroll
     for (int q = 0; q < NRL; ++q) {
@@ -484,7 +509,7 @@ __device__ void pass_res(S &sm, const SysDesc &sd, const SysState &st, int i0, i
         int i = i0 - OX + wi, j = j0 - OY + wj;
         xv[q] = 0.0;
         if (k < RN && in_dom(sd, i, j)) {
-            xv[q] = ld_cg(sd.x + (size_t)j * sd.nx + i);
+            xv[q] = ld_cg(sd.x + (size_t)j * sd.nx + i) * sg;
             if (st.has_d) xv[q] += (double)ld_cg(d + (size_t)j * sd.pitch + i);
         }
     }
@@ -503,7 +528,7 @@ __device__ void pass_res(S &sm, const SysDesc &sd, const SysState &st, int i0, i
     for (int c = 0; c < 4; ++c) {
         int i = i0 + tx + 32 * c, wi = tx + 32 * c + OX;
         if (tx + 32 * c < TILE_X && i < sd.nx && j < sd.ny) {
-            double b = -sd.dx[i] * sd.dy[j] * ld_cg(sd.f + (size_t)j * sd.nx + i) - st.mu_b;
+            double b = -sd.dx[i] * sd.dy[j] * ld_cg(sd.f + (size_t)j * sd.nx + i) * sg - st.mu_b;
             double rv = b - stencil<double>(cf, X, wi, wj);
             r[(size_t)j * sd.pitch + i] = (T)rv;
             t[0] += rv; t[1] += rv * rv;
@@ -573,7 +598,7 @@ __device__ void pass_restart(S &sm, const SysDesc &sd, const SysState &st, int i
             }
             if (st.reset_d) {
                 size_t gi = (size_t)j * sd.pitch + i;
-                if (st.fold_d) sd.x[(size_t)j * sd.nx + i] += (double)ld_cg(dd + gi);
+                if (st.fold_d) sd.x[(size_t)j * sd.nx + i] += (double)ld_cg(dd + gi) * sys_unscale(st);
                 dd[gi] = T(0);
             }
         }
@@ -1100,6 +1125,7 @@ __device__ void pass_final1(S &sm, const SysDesc &sd, const SysState &st, int i0
     constexpr int TILE_N = G::TN;
     (void)WX; (void)WN; (void)OX; (void)OY; (void)RN; (void)NRL; (void)TILE_X; (void)TILE_N;
     const T *dd = (const T *)sd.d;
+    const double sg = sys_scale(st);
     double t[NPART] = {0, 0, 0, 0, 0, 0};
     const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
     int j = j0 + ty;
@@ -1109,10 +1135,10 @@ __device__ void pass_final1(S &sm, const SysDesc &sd, const SysState &st, int i0
         if (tx + 32 * c < TILE_X && i < sd.nx && j < sd.ny) {
             size_t gx = (size_t)j * sd.nx + i;
             double x = st.zero_x ? 0.0 : ld_cg(sd.x + gx);
-            if (st.fold_d && !st.zero_x) x += (double)ld_cg(dd + (size_t)j * sd.pitch + i);
+            if (st.fold_d && !st.zero_x) x += (double)ld_cg(dd + (size_t)j * sd.pitch + i) * sys_unscale(st);
             sd.x[gx] = x;
             double v = sd.dx[i] * sd.dy[j];
-            t[0] += v; t[1] += v * x;
+            t[0] += v; t[1] += v * (x * sg);
         }
     }
     warp_accumulate(t, acc);
@@ -1132,7 +1158,7 @@ __device__ void pass_final2(S &sm, const SysDesc &sd, const SysState &st, int i0
         int i = i0 + tx + 32 * c;
         if (tx + 32 * c < TILE_X && i < sd.nx && j < sd.ny) {
             size_t gx = (size_t)j * sd.nx + i;
-            sd.x[gx] = ld_cg(sd.x + gx) - st.xmean;
+            sd.x[gx] = ld_cg(sd.x + gx) - st.xmean * sys_unscale(st);
         }
     }
 }
@@ -1460,7 +1486,7 @@ __device__ void run_pass(S &sm, int q, int ph, int t, Acc &acc)
     int i0, j0;
     tile_origin<S::TW>(sd, t, i0, j0);
     switch (ph) {
-    case PH_INIT: pass_init<T>(sm, sd, i0, j0, acc); break;
+    case PH_INIT: pass_init<T>(sm, sd, st, i0, j0, acc); break;
     case PH_RES: pass_res<T>(sm, sd, st, i0, j0, t, acc); break;
     case PH_RESTART: pass_restart<T>(sm, sd, st, i0, j0, t, acc); break;
     case PH_DLSM_DOT: pass_dlsm<T, S, false>(sm, sd, st, i0, j0, t, acc); break;
@@ -1469,6 +1495,28 @@ __device__ void run_pass(S &sm, int q, int ph, int t, Acc &acc)
     case PH_FINAL2: pass_final2<T>(sm, sd, st, i0, j0, acc); break;
     default: break;
     }
+}
+
+// max |b| = max |V S| of each system into st[s].bmax_bits (states zeroed
+// before); blockIdx.y is the system.  A NaN in b gives NaN bits above every
+// finite value, which the scale ignores (the init pass then reports the NaN).
+__global__ void __launch_bounds__(256) scale_kernel(const SysDesc *sys, SysState *st, int n)
+{
+    const int s = blockIdx.y;
+    if (s >= n) return;
+    const SysDesc &sd = sys[s];
+    const size_t cells = (size_t)sd.nx * sd.ny;
+    double m = 0.0;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < cells; k += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(k % sd.nx), j = (int)(k / sd.nx);
+        const double b = fabs(sd.dx[i] * sd.dy[j] * sd.f[k]);
+        if (!(b <= m)) m = b;
+    }
+    // non-negative doubles order like their bit patterns
+    unsigned long long bits = (unsigned long long)__double_as_longlong(m);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) bits = max(bits, __shfl_xor_sync(0xffffffffu, bits, o));
+    if ((threadIdx.x & 31) == 0 && bits) atomicMax((unsigned long long *)&st[s].bmax_bits, bits);
 }
 
 __device__ __forceinline__ void red_release_add_u32(uint32_t *p, uint32_t v)
@@ -1791,6 +1839,21 @@ void set_solver_attributes()
 
 const void *solver_kernel_fn(SolverVariant v) { return solver_fn(v); }
 size_t solver_smem_bytes(SolverVariant v) { return solver_smem(v); }
+
+const void *scale_kernel_fn() { return (const void *)scale_kernel; }
+
+dim3 scale_grid(int n, long max_cells)
+{
+    const long gx = std::min<long>(64, std::max<long>(1, (max_cells + 255) / 256));
+    return dim3((unsigned)gx, (unsigned)n);
+}
+
+ppe_status launch_scale(const SysDesc *sys, SysState *st, int n, long max_cells, cudaStream_t s)
+{
+    scale_kernel<<<scale_grid(n, max_cells), 256, 0, s>>>(sys, st, n);
+    PPE_CUDA_TRY(cudaGetLastError());
+    return PPE_OK;
+}
 
 int solver_max_blocks(SolverVariant v, int blocks_per_sm_req)
 {

@@ -225,3 +225,31 @@ def test_batch_streaming_pass(api):
         assert info["status"] == 0
         assert oracle.true_relres(w.dx, w.dy, w.f, xg) <= RES_TOL * 1.05
         assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= SOL_TOL
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64", "multigrid"])
+def test_solution_scales_exactly_with_the_source(api, prec):
+    """Cross-block sums are float-float (FP32's exponent range) and the inner
+    vectors of the mixed and multigrid solves are FP32, so the solver works on
+    the system scaled by a power of two (the binary exponent of max |b|, or of
+    the residual norm for an inner solve); the scaling is exact.  A source
+    multiplied by 2^k must give the solution multiplied by 2^k bit for bit,
+    for k = +-110, where |b|^2 lies far outside FP32's range."""
+    w = I.config1(0)
+    grid = api.ppe_create_grid(w.dx, w.dy)
+    if prec == "multigrid":
+        api.ppe_set_options(grid, preconditioner=1)
+    p = api.PPE_PREC_FP64 if prec == "fp64" else api.PPE_PREC_MIXED
+    out = {}
+    for k in (0, -110, 110):
+        x = torch.zeros(w.ny, w.nx, dtype=torch.float64, device="cuda")
+        info = api.ppe_solve(grid, _dev(np.ldexp(w.f, k)), x, 1e-8, api.PPE_MODE_PCG, p)
+        assert info["status"] == 0 and info["rel_res_true"] <= 1e-8, (k, info)
+        out[k] = (x.cpu().numpy(), info["iters_pcg"])
+    x0, it0 = out[0]
+    assert np.abs(x0).max() > 0
+    for k in (-110, 110):
+        xk, itk = out[k]
+        assert itk == it0, (k, itk, it0)
+        assert np.array_equal(np.ldexp(xk, -k), x0), k
+    grid.close()
