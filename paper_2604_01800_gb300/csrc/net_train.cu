@@ -124,7 +124,9 @@ __global__ void act_bwd_kernel(const float *__restrict__ dY, const bf16 *__restr
 void act_bwd(const float *dY, const bf16 *Z, bf16 *dZ, size_t n, int C, float *db, cudaStream_t s)
 {
     const int bs = (256 / C) * C;          // a multiple of C
-    act_bwd_kernel<<<g1d(n, bs), bs, 0, s>>>(dY, Z, dZ, n, C, db);
+    // a grid-stride loop over at most 1024 blocks: each block adds its channel
+    // sums once, so the bias gradient's atomics stay few
+    act_bwd_kernel<<<std::min(1024u, g1d(n, bs)), bs, 0, s>>>(dY, Z, dZ, n, C, db);
 }
 
 // dW[co][ci][tap] += sum_p dZ[p][co] * X[p + tap][ci]  (X: the layer's eta-weighted input)
@@ -253,24 +255,54 @@ __device__ __forceinline__ float rin_at(const float *R, int b, int y, int x, int
     return (y >= 0 && x >= 0 && y < ny && x < nx) ? R[((size_t)b * ny + y) * nx + x] : 0.f;
 }
 
-__global__ void wgrad_in_kernel(const bf16 *__restrict__ dZ, const float *__restrict__ R, const float *__restrict__ eta,
-                                int B, int H, int W, int C, int nx, int ny, float *__restrict__ dW)
+// dW[co][tap] of the first layer: eight warps per block, each on its own
+// pixels (lane = output channel, up to four per lane), then the block's warps
+// are summed in shared memory and added once per (co, tap).
+constexpr int WI_WARPS = 8, WI_MAXU = 4;   // C <= 128
+__global__ void __launch_bounds__(32 * WI_WARPS) wgrad_in_kernel(const bf16 *__restrict__ dZ,
+                                                                const float *__restrict__ R,
+                                                                const float *__restrict__ eta, int B, int H, int W,
+                                                                int C, int nx, int ny, float *__restrict__ dW)
 {
-    const int co = threadIdx.x;   // blockDim.x == C
-    float acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    __shared__ float red[WI_WARPS][WI_MAXU * 32 * 9];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float acc[WI_MAXU][9];
+#pragma unroll
+    for (int u = 0; u < WI_MAXU; ++u)
+#pragma unroll
+        for (int t = 0; t < 9; ++t) acc[u][t] = 0.f;
     const size_t P = (size_t)B * H * W;
-    for (size_t p = blockIdx.x; p < P; p += gridDim.x) {
-        int x = p % W, y = (p / W) % H, b = p / ((size_t)W * H);
-        float d = __bfloat162float(dZ[p * C + co]);
+    for (size_t p = (size_t)blockIdx.x * WI_WARPS + warp; p < P; p += (size_t)gridDim.x * WI_WARPS) {
+        const int x = p % W, y = (p / W) % H, b = p / ((size_t)W * H);
+        float v[9];
 #pragma unroll
         for (int t = 0; t < 9; ++t) {
-            int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
-            float v = (yy >= 0 && xx >= 0 && yy < H && xx < W) ? rin_at(R, b, yy, xx, nx, ny) * eta[yy * W + xx] : 0.f;
-            acc[t] = fmaf(d, v, acc[t]);
+            const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
+            v[t] = (yy >= 0 && xx >= 0 && yy < H && xx < W) ? rin_at(R, b, yy, xx, nx, ny) * eta[yy * W + xx] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < WI_MAXU; ++u) {
+            const int co = lane + 32 * u;
+            if (co >= C) break;
+            const float d = __bfloat162float(dZ[p * C + co]);
+#pragma unroll
+            for (int t = 0; t < 9; ++t) acc[u][t] = fmaf(d, v[t], acc[u][t]);
         }
     }
 #pragma unroll
-    for (int t = 0; t < 9; ++t) atomicAdd(&dW[co * 9 + t], acc[t]);
+    for (int u = 0; u < WI_MAXU; ++u) {
+        const int co = lane + 32 * u;
+        if (co >= C) break;
+#pragma unroll
+        for (int t = 0; t < 9; ++t) red[warp][co * 9 + t] = acc[u][t];
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < C * 9; k += blockDim.x) {
+        float sum = 0.f;
+#pragma unroll
+        for (int w = 0; w < WI_WARPS; ++w) sum += red[w][k];
+        atomicAdd(&dW[k], sum);
+    }
 }
 
 __global__ void dgrad_in_kernel(const bf16 *__restrict__ dZ, const float *__restrict__ Wt /*[C][9] FP32 OIHW*/,
@@ -293,18 +325,39 @@ __global__ void dgrad_in_kernel(const bf16 *__restrict__ dZ, const float *__rest
 }
 
 // dX = eta d(eta X);  d eta += sum_c (eta X) d(eta X) / eta
-__global__ void eta_bwd_kernel(const float *__restrict__ dXb, const bf16 *__restrict__ Xb, const float *__restrict__ eta,
-                               size_t P, int HW, int C, float *__restrict__ dX, float *__restrict__ deta, int mesh)
+// A thread takes four channels of a pixel (16-byte loads and stores); the
+// pixel's C/4 threads are consecutive lanes, summed by shuffles when C/4
+// divides 32, and one of them adds to d eta.
+__global__ void eta_bwd_kernel(const float4 *__restrict__ dXb, const uint2 *__restrict__ Xb,
+                               const float *__restrict__ eta, size_t P, int HW, int C4, float4 *__restrict__ dX,
+                               float *__restrict__ deta, int mesh)
 {
-    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < P; p += (size_t)gridDim.x * blockDim.x) {
-        int q = p % HW;
-        float e = eta[q], s = 0.f;
-        for (int c = 0; c < C; ++c) {
-            float g = dXb[p * C + c];
-            dX[p * C + c] = e * g;
-            s = fmaf(__bfloat162float(Xb[p * C + c]), g, s);
+    const size_t n = P * C4;
+    const bool seg = C4 <= 32 && (32 % C4) == 0;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t base = (size_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+        const size_t k = base + threadIdx.x;
+        const bool ok = k < n;
+        float s = 0.f, e = 0.f;
+        int q = 0;
+        if (ok) {
+            const size_t p = k / C4;
+            q = (int)(p % HW);
+            e = eta[q];
+            const float4 g = dXb[k];
+            dX[k] = make_float4(e * g.x, e * g.y, e * g.z, e * g.w);
+            const uint2 raw = Xb[k];
+            const bf16 *h = reinterpret_cast<const bf16 *>(&raw);
+            s = __bfloat162float(h[0]) * g.x + __bfloat162float(h[1]) * g.y + __bfloat162float(h[2]) * g.z +
+                __bfloat162float(h[3]) * g.w;
         }
-        if (mesh && e > 0.f) atomicAdd(&deta[q], s / e);
+        if (!mesh) continue;
+        if (seg) {
+            for (int o = 1; o < C4; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (ok && (threadIdx.x % C4) == 0 && e > 0.f) atomicAdd(&deta[q], s / e);
+        } else if (ok && e > 0.f) {
+            atomicAdd(&deta[q], s / e);
+        }
     }
 }
 
@@ -605,7 +658,9 @@ static ppe_status conv_backward(ppe_net *n, NetCache *c, TrainWs *w, int li, con
     PPE_TRY(run_conv(n, a, s));
     PPE_CUDA_TRY(cudaMemsetAsync(w->deta, 0, (size_t)H * W * 4, s));
     const float *eta = c->eta + c->eoff[li];
-    eta_bwd_kernel<<<g1d(px), 256, 0, s>>>(w->dXb, Xb, eta, px, H * W, l.cin, w->dX, w->deta, n->cfg.mesh_conv);
+    eta_bwd_kernel<<<std::min(2048u, g1d(px * (l.cin / 4))), 256, 0, s>>>(
+        reinterpret_cast<const float4 *>(w->dXb), reinterpret_cast<const uint2 *>(Xb), eta, px, H * W, l.cin / 4,
+        reinterpret_cast<float4 *>(w->dX), w->deta, n->cfg.mesh_conv);
     if (n->cfg.mesh_conv) {
         int hid = n->cfg.phi_hidden;
         phi_bwd_kernel<<<std::min(256u, g1d((size_t)H * W)), 256, 0, s>>>(
@@ -689,7 +744,11 @@ static ppe_status net_backward(ppe_net *n, NetCache *c, TrainWs *w, ppe_grid *g,
         const size_t px = (size_t)B * c->H * c->W;
         act_bwd(G("enc0a"), c->act + pl.Z[li], w->dZ, px * l.cout, l.cout, grads + l.off_b, s);
         const float *eta = c->eta + c->eoff[li];
-        wgrad_in_kernel<<<1024, l.cout, 0, s>>>(w->dZ, R, eta, B, c->H, c->W, l.cout, g->nx, g->ny, grads + l.off_w);
+        if (l.cout > 32 * WI_MAXU) {
+            set_error("first-layer weight gradient: at most 128 channels");
+            return PPE_ERR_ARG;
+        }
+        wgrad_in_kernel<<<512, 32 * WI_WARPS, 0, s>>>(w->dZ, R, eta, B, c->H, c->W, l.cout, g->nx, g->ny, grads + l.off_w);
         if (cf.mesh_conv) {
             PPE_CUDA_TRY(cudaMemsetAsync(w->deta, 0, (size_t)c->H * c->W * 4, s));
             dgrad_in_kernel<<<g1d(px), 256, 0, s>>>(w->dZ, P + l.off_w, R, B, c->H, c->W, l.cout, g->nx, g->ny, w->deta);
