@@ -148,7 +148,12 @@ typedef struct {
                                (ppe_solve; PPE_ERR_ARG for hybrid mode, FP64 precision or a
                                batch).  The hierarchy is built on the grid's first multigrid
                                solve (allocates; later solves reuse it).                     */
-    int32_t reserved[4];
+    int32_t debug_force_stall; /* test hook, 0 = off: a mixed-precision solve counts every
+                               refinement after the first as one that failed to halve the
+                               true residual, so its stall rule ends the FP32 iteration and
+                               the solve continues in FP64 from the iterate
+                               (ppe_solve_info.precision_fallback = 1)                      */
+    int32_t reserved[3];
 } ppe_solve_opts;
 
 PPE_API void ppe_default_options(ppe_solve_opts *opts);

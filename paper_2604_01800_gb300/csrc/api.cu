@@ -275,7 +275,7 @@ ppe_status ppe_set_options(ppe_grid *g, const ppe_solve_opts *o)
         !(o->inner_rtol > 0.0 && o->inner_rtol < 1.0) || !(o->dlsm_guard >= 0.0) || o->blocks_per_sm < 0 ||
         o->iter_pass < 0 || o->iter_pass > 2 || o->dlsm_stall_limit < 0 ||
         o->dlsm_cost_iters < 0 || o->spin_limit_ms < 0 || o->host_loop < 0 || o->host_loop > 1 ||
-        o->debug_skip_block < 0 || o->preconditioner < 0 || o->preconditioner > 1)
+        o->debug_skip_block < 0 || o->preconditioner < 0 || o->preconditioner > 1 || o->debug_force_stall < 0)
         return arg_error("ppe_set_options: option out of range");
     g->opts = *o;
     return PPE_OK;

@@ -170,6 +170,7 @@ SysDesc make_desc(const ppe_grid *g, const double *rhs, double *x, double tol, p
     sd.keep_dir_after_dlsm = g->opts.keep_dir_after_dlsm ? 1 : 0;
     sd.dlsm_stall_limit = g->opts.dlsm_stall_limit;
     sd.dlsm_cost = g->opts.dlsm_cost_iters;
+    sd.force_stall = g->opts.debug_force_stall ? 1 : 0;
     sd.tol = tol;
     sd.ru_delta = prec == PPE_PREC_MIXED ? g->opts.inner_rtol : 0.0;
     sd.dlsm_guard = g->opts.dlsm_guard;

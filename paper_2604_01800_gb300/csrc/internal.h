@@ -99,6 +99,7 @@ struct SysDesc {
     int32_t keep_dir_after_dlsm;          // 1: CG directions continue across DLSM steps
     int32_t dlsm_stall_limit;             // unprofitable DLSM steps in a row before plain PCG (0: never)
     int32_t dlsm_cost;                    // a DLSM step's cost in CG iterations (profitability threshold)
+    int32_t force_stall;                  // test hook: every refinement after the first counts as stalled
     double tol, ru_delta, dlsm_guard, diag_max;
     double n_cells, inv_n;                // nx*ny and its reciprocal
     float n_cells_f, inv_n_f;             // the same in FP32

@@ -1229,10 +1229,12 @@ __device__ void advance(const SysDesc &sd, SysState &s, const double (&t)[NPART]
         // mixed precision: an FP32 inner solve normally cuts the true residual
         // by about inner_rtol; when the system's conditioning exceeds what
         // FP32 resolves, the inner iteration stalls and the true residual
-        // stops falling.  Three refinements in a row that fail to halve it
-        // end the mixed solve (the host continues it in FP64).
+        // stops falling.  Three refinements in a row that fail to cut it by
+        // max(1/2, sqrt(inner_rtol)) end the mixed solve (the host continues
+        // it in FP64); the square root keeps a planned reduction weaker than
+        // one half from counting as a stall.
         if (sd.precision == PPE_PREC_MIXED && s.refinements > 1)
-            s.stall = s.relres > 0.5 * s.relres_prev ? s.stall + 1 : 0;
+            s.stall = (s.relres > fmax(0.5, sqrt(sd.ru_delta)) * s.relres_prev || sd.force_stall) ? s.stall + 1 : 0;
         s.relres_prev = s.relres;
         // the budget of an inner solve follows the last one that reached its
         // reduction target (an overrun does not raise it)

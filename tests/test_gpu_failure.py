@@ -9,6 +9,8 @@
 * Non-finite DLSM direction: the curvature guard (e.Ae compared with
   guard * e.e * max diag) rejects it; the solve goes on with CG and reaches
   the oracle's solution.
+* Stalled FP32 inner iteration: a test hook makes the mixed solve's stall
+  rule fire; the solve continues in FP64 from its iterate, in both drivers.
 """
 import numpy as np
 import pytest
@@ -102,6 +104,28 @@ def test_ill_conditioned_strip_mixed_solve_converges(api, shape):
     assert info["status"] == 0, info
     assert info["iters_pcg"] <= 150_000, info
     assert oracle.true_relres(dx, dy, f, x.cpu().numpy()) <= TOL * 1.05
+
+
+@pytest.mark.parametrize("host_loop", [0, 1])
+def test_stalled_mixed_solve_continues_in_fp64(api, host_loop):
+    """The FP64 continuation: a test hook makes the mixed solve count every
+    refinement after the first as one that failed to halve the true residual
+    (no real system has been found on which FP32 inner iterations stall), so
+    the stall rule ends the FP32 iteration after three of them; the solve
+    then continues in FP64 from its iterate and reaches the oracle's
+    solution, with both phases' iterations in the report."""
+    w = I.config3(0)
+    grid = api.ppe_create_grid(w.dx, w.dy)
+    api.ppe_set_options(grid, debug_force_stall=1, host_loop=host_loop)
+    x = torch.zeros(w.ny, w.nx, dtype=torch.float64, device="cuda")
+    info = api.ppe_solve(grid, _dev(w.f), x, TOL, api.PPE_MODE_PCG, api.PPE_PREC_MIXED)
+    assert info["status"] == 0 and info["precision_fallback"] == 1, info
+    assert info["refinements"] >= 4, info
+    xg = x.cpu().numpy()
+    assert oracle.true_relres(w.dx, w.dy, w.f, xg) <= TOL * 1.05
+    xo, _, _ = oracle.solve(w.dx, w.dy, w.f, tol_rel=1e-11)
+    assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= 1e-6
+    grid.close()
 
 
 def test_well_conditioned_mixed_solve_stays_mixed(api):
