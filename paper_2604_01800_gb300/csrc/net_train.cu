@@ -394,25 +394,48 @@ __global__ void __launch_bounds__(256) phi_bwd_kernel(const float *__restrict__ 
             for (int c = 0; c < 4; ++c) a_W1[k][c] += dz * d[c];
         }
     }
+    // warp sums, then the block's warps summed in shared memory: one atomic
+    // per value and block (per warp, the ~100 values had drawn thousands of
+    // atomics each)
+    constexpr int NV = 1 + 6 * PHI_MAXH;
+    __shared__ float red[8][NV];
     auto wsum = [](float v) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         return v;
     };
-    const bool lead = (threadIdx.x & 31) == 0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float v = wsum(a_b2);
-    if (lead && v != 0.f) atomicAdd(gb2, v);
+    if (lane == 0) red[warp][0] = v;
 #pragma unroll
     for (int k = 0; k < PHI_MAXH; ++k) {
         if (k >= hid) break;
         v = wsum(a_w2[k]);
-        if (lead && v != 0.f) atomicAdd(&gw2[k], v);
+        if (lane == 0) red[warp][1 + 6 * k] = v;
         v = wsum(a_b1[k]);
-        if (lead && v != 0.f) atomicAdd(&gb1[k], v);
+        if (lane == 0) red[warp][2 + 6 * k] = v;
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             v = wsum(a_W1[k][c]);
-            if (lead && v != 0.f) atomicAdd(&gW1[4 * k + c], v);
+            if (lane == 0) red[warp][3 + 6 * k + c] = v;
+        }
+    }
+    __syncthreads();
+    const int nv = 1 + 6 * hid, nw = blockDim.x >> 5;
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+        float sum = 0.f;
+        for (int w = 0; w < nw; ++w) sum += red[w][i];
+        if (sum == 0.f) continue;
+        if (i == 0) {
+            atomicAdd(gb2, sum);
+        } else {
+            const int k = (i - 1) / 6, f = (i - 1) % 6;
+            if (f == 0)
+                atomicAdd(&gw2[k], sum);
+            else if (f == 1)
+                atomicAdd(&gb1[k], sum);
+            else
+                atomicAdd(&gW1[4 * k + (f - 2)], sum);
         }
     }
 }
@@ -663,7 +686,7 @@ static ppe_status conv_backward(ppe_net *n, NetCache *c, TrainWs *w, int li, con
         reinterpret_cast<float4 *>(w->dX), w->deta, n->cfg.mesh_conv);
     if (n->cfg.mesh_conv) {
         int hid = n->cfg.phi_hidden;
-        phi_bwd_kernel<<<std::min(256u, g1d((size_t)H * W)), 256, 0, s>>>(
+        phi_bwd_kernel<<<std::min(128u, g1d((size_t)H * W)), 256, 0, s>>>(
             w->deta, eta, c->phi + c->eoff[li], c->delta + c->doff[k], H * W, P + l.off_p1w, P + l.off_p1b,
             P + l.off_p2w, hid, grads + l.off_p1w, grads + l.off_p1b, grads + l.off_p2w, grads + l.off_p2b);
     }
@@ -753,7 +776,7 @@ static ppe_status net_backward(ppe_net *n, NetCache *c, TrainWs *w, ppe_grid *g,
             PPE_CUDA_TRY(cudaMemsetAsync(w->deta, 0, (size_t)c->H * c->W * 4, s));
             dgrad_in_kernel<<<g1d(px), 256, 0, s>>>(w->dZ, P + l.off_w, R, B, c->H, c->W, l.cout, g->nx, g->ny, w->deta);
             int hid = cf.phi_hidden;
-            phi_bwd_kernel<<<std::min(256u, g1d((size_t)c->H * c->W)), 256, 0, s>>>(
+            phi_bwd_kernel<<<std::min(128u, g1d((size_t)c->H * c->W)), 256, 0, s>>>(
                 w->deta, eta, c->phi + c->eoff[li], c->delta + c->doff[0], c->H * c->W, P + l.off_p1w, P + l.off_p1b,
                 P + l.off_p2w, hid, grads + l.off_p1w, grads + l.off_p1b, grads + l.off_p2w, grads + l.off_p2b);
         }
