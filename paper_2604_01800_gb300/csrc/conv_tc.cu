@@ -188,6 +188,10 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
     const uint32_t accf0 = bar0 + 16 * TC_MAX_STAGES, acce0 = accf0 + 16, tslot = acce0 + 16;
     uint32_t *tslot_ptr = reinterpret_cast<uint32_t *>(smem_raw + (tslot - raw));
 
+    // programmatic dependent launch: the next layer may start its set-up
+    // (barriers, TMEM, cluster) while this one runs; it reads nothing the
+    // previous kernel writes before griddepcontrol.wait below
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int cblocks = a.cin / BK;
     const int kiters = 3 * cblocks;            // (channel block, kx) stages per tile
@@ -231,6 +235,8 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
         __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tslot_ptr;
+    // the previous kernel (this layer's input) has completed and its writes are visible
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 
     // Cluster c walks the units c, c + nclusters, ...; unit u is patch group
     // u / sgroups (patches cm * group + rm) and slice group u % sgroups
@@ -610,13 +616,17 @@ ppe_status conv3x3_tc(const ConvArgs &a, cudaStream_t s)
     cfg.blockDim = dim3(TC_THREADS);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = (unsigned)cs;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    // the layer's set-up overlaps the previous kernel's tail (measured: a
+    // 256^2 inference 218 -> 196 us with L2 flushed)
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     cudaError_t e;
     if (bk == 64)
         e = cudaLaunchKernelEx(&cfg, conv_tc_kernel<64>, mA, mB, t);

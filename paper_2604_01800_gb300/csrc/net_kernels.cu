@@ -147,6 +147,9 @@ __global__ void __launch_bounds__(CI_PX) conv_in_staged_kernel(InputSrc src, int
                                                                const bf16 *__restrict__ w,
                                                                const float *__restrict__ bias, int C, Epi e)
 {
+    // the next kernel (a tensor-core convolution launched as a programmatic
+    // dependent) may start its set-up now; it waits for this grid's results
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     __shared__ float ws[CI_CH][9];
     __shared__ float bs[CI_CH];
     __shared__ __align__(16) bf16 tile[CI_PX][CI_CH + 8];      // padded rows: conflict-free column writes
