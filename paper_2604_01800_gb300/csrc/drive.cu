@@ -337,8 +337,8 @@ ppe_status drive_host(int n, ppe_grid *const *grids, LaunchSet &ls, int blocks, 
         for (int s = 0; s < n; ++s) planned_tiles += (*rp->sds)[s].ntiles;
     static const bool want_prof = std::getenv("PPE_SOLVER_PROFILE") != nullptr;
     if (want_prof) {
-        PPE_CUDA_TRY(cudaMalloc(&a.prof, 8 * sizeof(unsigned long long)));
-        PPE_CUDA_TRY(cudaMemsetAsync(a.prof, 0, 8 * sizeof(unsigned long long), stream));
+        PPE_CUDA_TRY(cudaMalloc(&a.prof, 16 * sizeof(unsigned long long)));
+        PPE_CUDA_TRY(cudaMemsetAsync(a.prof, 0, 16 * sizeof(unsigned long long), stream));
     }
     PPE_CUDA_TRY(cudaEventRecord(ls.ev0, stream));
     PPE_CUDA_TRY(cudaMemsetAsync(ls.st, 0, sizeof(SysState) * n, stream));
@@ -425,13 +425,16 @@ ppe_status drive_host(int n, ppe_grid *const *grids, LaunchSet &ls, int blocks, 
         if (launches > LOOP_CAP) { status = PPE_ERR_NOT_CONVERGED; break; }
     }
     if (a.prof) {
-        unsigned long long pr[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        unsigned long long pr[16] = {};
         cudaMemcpyAsync(pr, a.prof, sizeof pr, cudaMemcpyDeviceToHost, stream);
         cudaStreamSynchronize(stream);
-        double st_ = pr[7] ? (double)pr[7] * 1e3 : 1.0;
+        double st_ = pr[7] ? (double)pr[7] * 1e3 : 1.0, si_ = pr[13] ? (double)pr[13] * 1e3 : 1.0;
         std::fprintf(stderr, "[solver profile] blocks=%d steps=%llu  per step (us): pass %.2f, reduce+publish %.2f, "
                      "wait %.2f, gather %.2f, advance %.2f (state machine %.2f)\n", blocks, pr[7], pr[0] / st_,
                      pr[1] / st_, pr[2] / st_, pr[3] / st_, pr[4] / st_, pr[5] / st_);
+        std::fprintf(stderr, "[solver profile] iteration passes=%llu  per pass (us): to the data wait %.2f, data wait "
+                     "%.2f, window stage %.2f, ring stage %.2f, tile stage and sums %.2f\n", pr[13], pr[8] / si_,
+                     pr[9] / si_, pr[10] / si_, pr[11] / si_, pr[12] / si_);
         cudaFree(a.prof);
     }
     float ms = 0.f;

@@ -182,7 +182,7 @@ struct SolverArgs {
     int64_t spin_limit_ns;
     int32_t max_steps;         // > 0: every block leaves after this many steps (the host may re-plan)
     int32_t skip_block;        // test hook: block skip_block - 1 withholds its record at step 2 (0: off)
-    unsigned long long *prof;  // nullable: block 0 accumulates ns per step part [0..5] and the step count [7]
+    unsigned long long *prof;  // nullable, 16 words: block 0's ns per step part [0..5], step count [7], iteration-pass parts [8..12] and their count [13]
 };
 
 // Solver kernel variants: FP64, FP32 with the tile-cooperative iteration

@@ -128,7 +128,9 @@ __device__ bool grid_bar(const MgArgs &a, Sync &s)
                 __nanosleep(32);
             }
         }
-        __threadfence();
+        // no fence here: the last block's fence above acquires the others'
+        // arrivals, a waiter's acquire load the last block's release, and the
+        // block barrier below orders the block's later loads after either
         s.gen = target;
         ok_s = ok;
     }

@@ -151,6 +151,8 @@ template <typename T, int TW_> struct SmemT {
     int32_t tag_d, tag_f;   // tile whose coefficients are in cfd / cff
     int32_t go;
     uint32_t fills;         // TMA stage fills issued so far (stage = fill & 1)
+    uint64_t ptime[4];      // step profile (block 0): iteration pass before and after its data wait, after two stages
+    unsigned long long pacc[14];   // step profile (block 0): accumulated ns, written to SolverArgs::prof at the end
 };
 
 // Dynamic shared memory of a block (plus 128 bytes of alignment slack): one
@@ -729,11 +731,14 @@ __device__ void pass_iter(S &sm, int q, int t_lo, int t_hi, Acc &acc, const Solv
             issue_coef_raw<T>(ib.raw[(k + 1) & 1], sd, i1, j1);
         }
         Stage<T, S::TW> &stg = ib.st[fill & 1];
+        const bool prof = a.prof && blockIdx.x == 0 && threadIdx.x == 0 && q == 0;
+        if (prof) sm.ptime[0] = gtimer();
         if (!mbar_wait_bounded(smem_u32(&sm.bar[fill & 1]), (fill >> 1) & 1, a.spin_limit_ns)) {
             if (threadIdx.x == 0) atomicExch(&a.ctl->err, (int32_t)PPE_ERR_TIMEOUT);
             sm.go = 0;
         }
         __syncthreads();   // coefficients visible
+        if (prof) sm.ptime[1] = gtimer();
         // Every stage works on groups of four consecutive cells (16-byte
         // shared and global accesses); window rows (136), the tile's columns
         // (from window column 4) and the grid pitch are multiples of four.
@@ -762,6 +767,7 @@ __device__ void pass_iter(S &sm, int q, int t_lo, int t_hi, Acc &acc, const Solv
             st4(Pw + w, p);
         }
         __syncthreads();
+        if (prof) sm.ptime[2] = gtimer();
         // one-cell ring: q = A p, r' = r - alpha q, u' = D^-1 r'; the tile's
         // columns in groups of four, the two edge columns one cell at a time
         constexpr int NRV = (TILE_N / TILE_X + 2) * TG;
@@ -792,6 +798,7 @@ __device__ void pass_iter(S &sm, int q, int t_lo, int t_hi, Acc &acc, const Solv
             }
         }
         __syncthreads();
+        if (prof) sm.ptime[3] = gtimer();
         // tile: store p, d, r'; dots r'.u', (A u').u', r'.r', sum r', u'.(A p), p.(A p)
         T tt[NPART] = {0, 0, 0, 0, 0, 0};
         for (int g = threadIdx.x; g < TILE_N / 4; g += SOLVER_THREADS) {
@@ -1604,6 +1611,8 @@ __global__ void __launch_bounds__(SOLVER_THREADS, 1)
         sm.tag_d = sm.tag_f = -1;
         sm.go = 1;
         sm.fills = 0;
+        sm.ptime[0] = 0;
+        for (int k = 0; k < 14; ++k) sm.pacc[k] = 0;
         mbar_init(smem_u32(&sm.bar[0]), 1);
         mbar_init(smem_u32(&sm.bar[1]), 1);
         if constexpr (STREAM) {
@@ -1679,7 +1688,7 @@ __global__ void __launch_bounds__(SOLVER_THREADS, 1)
                     const uint32_t need = step * (uint32_t)sd.nparts;
                     const uint32_t *cnt = a.arrive + br.s0 + q;
                     if (ld_acquire_u32(cnt) < need) {
-                        uint64_t t0 = gtimer();
+                        const uint64_t t0 = gtimer();
                         while (ld_acquire_u32(cnt) < need) {
                             if ((int64_t)(gtimer() - t0) > a.spin_limit_ns) {
                                 atomicExch(&a.ctl->err, (int32_t)PPE_ERR_TIMEOUT);
@@ -1689,9 +1698,10 @@ __global__ void __launch_bounds__(SOLVER_THREADS, 1)
                             __nanosleep(20);
                         }
                     }
-                    __threadfence();
                     if (prof && q == 0) t_w = gtimer();
                 }
+                // the acquire of lane 0 and the warp barrier order every lane's
+                // record loads after the other blocks' releases
                 __syncwarp();
                 // lane l adds records l, l + 32, ... in order, then a fixed shuffle
                 // tree: every block obtains the same sums bit for bit
@@ -1777,18 +1787,31 @@ __global__ void __launch_bounds__(SOLVER_THREADS, 1)
         if (prof) {
             t_c = gtimer();
             if (t_p && t_w && t_r) {
-                a.prof[0] += t_p - t_a;
-                a.prof[1] += t_b - t_p;
-                a.prof[2] += t_w - t_b;
-                a.prof[3] += t_r - t_w;
-                a.prof[4] += t_c - t_r;
-                a.prof[5] += t_x - t_r;
-                a.prof[7] += 1;
+                unsigned long long *pa = sm.pacc;
+                pa[0] += t_p - t_a;
+                pa[1] += t_b - t_p;
+                pa[2] += t_w - t_b;
+                pa[3] += t_r - t_w;
+                pa[4] += t_c - t_r;
+                pa[5] += t_x - t_r;
+                pa[7] += 1;
+                // the iteration pass's parts (steps that ran one)
+                if (sm.ptime[0]) {
+                    pa[8] += sm.ptime[0] - t_a;
+                    pa[9] += sm.ptime[1] - sm.ptime[0];
+                    pa[10] += sm.ptime[2] - sm.ptime[1];
+                    pa[11] += sm.ptime[3] - sm.ptime[2];
+                    pa[12] += t_p - sm.ptime[3];
+                    pa[13] += 1;
+                }
             }
+            sm.ptime[0] = 0;
             t_p = t_w = t_r = 0;
             t_a = t_c;
         }
     }
+    if (prof)
+        for (int k = 0; k < 14; ++k) a.prof[k] += sm.pacc[k];
     // a system that waits for a network direction starts its network clock
     if (threadIdx.x == 0)
         for (int q = 0; q < nq; ++q)
