@@ -851,7 +851,10 @@ __device__ void pass_iter(S &sm, int q, int t_lo, int t_hi, Acc &acc, const Solv
             }
         }
         warp_accumulate(tt, acc);
-        __syncthreads();   // stage and ring buffers free for the next tile
+        // stage and ring buffers free for the next tile; after the last tile
+        // the step's publish barrier (or the next pass's barriers, which all
+        // come before any thread writes these buffers again) does it
+        if (k + 1 < n) __syncthreads();
     }
     if (threadIdx.x == 0) sm.fills = fill0 + n;
 }
