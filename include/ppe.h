@@ -118,8 +118,8 @@ typedef struct {
     int32_t keep_dir_after_dlsm; /* 0: every CG-type phase restarts with p = z (Sec. 2.2 workflow,
                                as a fresh KSPSolve); 1: CG directions continue across DLSM steps */
     int32_t iter_pass;      /* MIXED precision only: 0 = the autotuned choice if there is one
-                               (ppe_autotune), else by size (default); 1 = tiles of 16x128
-                               cells shared by a whole CTA; 2 = streaming (each warp marches
+                               (ppe_autotune), else by size (default); 1 = tiles of 128 cells
+                               by 16 or 8 rows (tile_rows) shared by a whole CTA; 2 = streaming (each warp marches
                                down a 120-wide strip; for grids far larger than the number of
                                CTAs).  Same arithmetic, same results up to rounding order.     */
     int32_t dlsm_stall_limit; /* hybrid: continue as plain PCG after this many unprofitable DLSM
@@ -153,7 +153,12 @@ typedef struct {
                                true residual, so its stall rule ends the FP32 iteration and
                                the solve continues in FP64 from the iterate
                                (ppe_solve_info.precision_fallback = 1)                      */
-    int32_t reserved[3];
+    int32_t tile_rows;      /* rows of a tile-cooperative tile: 0 = by size (default: 8 when
+                               twice the grid's count of 16-row tiles fits on the SMs, so that
+                               a small grid spreads over twice the CTAs, else 16); 8 or 16 to
+                               choose.  Any precision; same arithmetic, same results up to
+                               rounding order.  Ignored by the streaming pass (16).          */
+    int32_t reserved[2];
 } ppe_solve_opts;
 
 PPE_API void ppe_default_options(ppe_solve_opts *opts);

@@ -43,7 +43,8 @@ class ppe_solve_opts(ctypes.Structure):
                 ("iter_pass", ctypes.c_int32), ("dlsm_stall_limit", ctypes.c_int32),
                 ("dlsm_cost_iters", ctypes.c_int32), ("spin_limit_ms", ctypes.c_int32), ("host_loop", ctypes.c_int32),
                 ("debug_skip_block", ctypes.c_int32), ("preconditioner", ctypes.c_int32),
-                ("debug_force_stall", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("debug_force_stall", ctypes.c_int32), ("tile_rows", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class ppe_tune_report(ctypes.Structure):

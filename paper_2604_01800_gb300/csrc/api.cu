@@ -229,9 +229,9 @@ ppe_status ppe_create_grid(int nx, int ny, const double *dx, const double *dy, p
         }
         G_ALLOC(g->ycoef, yc.size() * sizeof(float));
         G_COPY(g->ycoef, yc.data(), yc.size() * sizeof(float));
-        CUtensorMap maps[3 * NMAPS];     // one set per kernel variant, in SolverVariant order
+        CUtensorMap maps[SV_COUNT * NMAPS];   // one set per kernel variant, in SolverVariant order
         ppe_status ms = PPE_OK;
-        for (int v = 0; v < 3 && ms == PPE_OK; ++v)
+        for (int v = 0; v < SV_COUNT && ms == PPE_OK; ++v)
             ms = encode_solver_maps(g->r, g->p, g->d, g->ycoef, nx, ny, g->pitch, (SolverVariant)v, maps + v * NMAPS);
         if (ms != PPE_OK) return fail(ms);
         G_ALLOC(g->tmaps_dev, sizeof maps);
@@ -243,8 +243,9 @@ ppe_status ppe_create_grid(int nx, int ny, const double *dx, const double *dy, p
         cudaError_t _e = cudaMemset(g->e, 0, (size_t)g->pitch * ny * 4);
         if (_e != cudaSuccess) return fail(cuda_status(_e, "cudaMemset(e)"));
     }
-    // tile counts of the two tile widths; workspaces are sized for the larger
-    int ntiles = std::max(g->tiles_x, (nx + TILE_X_STREAM - 1) / TILE_X_STREAM) * g->tiles_y;
+    // tile counts of the tile shapes; workspaces are sized for the largest
+    int ntiles = std::max(g->tiles_x, (nx + TILE_X_STREAM - 1) / TILE_X_STREAM) *
+                 ((ny + TILE_Y_SHORT - 1) / TILE_Y_SHORT);
     {
         ppe_status ls = launch_set_create(1, ntiles, ntiles + 1, &g->ls);
         if (ls != PPE_OK) return fail(ls);
@@ -275,7 +276,8 @@ ppe_status ppe_set_options(ppe_grid *g, const ppe_solve_opts *o)
         !(o->inner_rtol > 0.0 && o->inner_rtol < 1.0) || !(o->dlsm_guard >= 0.0) || o->blocks_per_sm < 0 ||
         o->iter_pass < 0 || o->iter_pass > 2 || o->dlsm_stall_limit < 0 ||
         o->dlsm_cost_iters < 0 || o->spin_limit_ms < 0 || o->host_loop < 0 || o->host_loop > 1 ||
-        o->debug_skip_block < 0 || o->preconditioner < 0 || o->preconditioner > 1 || o->debug_force_stall < 0)
+        o->debug_skip_block < 0 || o->preconditioner < 0 || o->preconditioner > 1 || o->debug_force_stall < 0 ||
+        (o->tile_rows != 0 && o->tile_rows != TILE_Y && o->tile_rows != TILE_Y_SHORT))
         return arg_error("ppe_set_options: option out of range");
     g->opts = *o;
     return PPE_OK;

@@ -160,9 +160,9 @@ SysDesc make_desc(const ppe_grid *g, const double *rhs, double *x, double tol, p
 {
     SysDesc sd;
     std::memset(&sd, 0, sizeof(sd));
-    const int tw = v == SV_FP32_STREAM ? TILE_X_STREAM : TILE_X;
+    const int tw = solver_tile_w(v), th = solver_tile_h(v);
     sd.nx = g->nx; sd.ny = g->ny; sd.pitch = g->pitch;
-    sd.tiles_x = (g->nx + tw - 1) / tw; sd.tiles_y = g->tiles_y;
+    sd.tiles_x = (g->nx + tw - 1) / tw; sd.tiles_y = (g->ny + th - 1) / th;
     sd.tile0 = tile0; sd.ntiles = sd.tiles_x * sd.tiles_y;
     sd.mode = mode; sd.precision = prec;
     sd.max_iters = g->opts.max_iters; sd.num_cg = g->opts.num_cg; sd.num_dlsm = g->opts.num_dlsm;
@@ -238,13 +238,25 @@ void merge_fallback(ppe_solve_info &fp64, const ppe_solve_info &mixed)
 // 1024 tiles 33.1 / 22.0 us; on grids of a few hundred tiles or fewer the
 // tile-cooperative pass has the lower latency (512^2: 8.1 / 17.3 us).
 // ppe_autotune measures instead of guessing.
+//
+// ntiles counts 128x16 tiles.  When twice that many fit on the SMs, the
+// 128x8 tiles of the short-tile variants put one half-size tile on each of
+// twice the blocks: the per-block work of a step halves while the step's
+// synchronisation stays, which shortens an iteration on small grids.
 constexpr int STREAM_MIN_TILES = 448;
-SolverVariant pick_variant(ppe_precision prec, int iter_pass, int ntiles)
+SolverVariant pick_variant(ppe_precision prec, int iter_pass, int ntiles, int tile_rows)
 {
-    if (prec == PPE_PREC_FP64) return SV_FP64;
-    if (iter_pass == 1) return SV_FP32_TILE;
+    static const int sms = [] {
+        int dev = 0, n = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        return n;
+    }();
+    const bool short_tiles = tile_rows ? tile_rows == TILE_Y_SHORT : 2 * ntiles <= sms;
+    if (prec == PPE_PREC_FP64) return short_tiles ? SV_FP64_SHORT : SV_FP64;
     if (iter_pass == 2) return SV_FP32_STREAM;
-    return ntiles >= STREAM_MIN_TILES ? SV_FP32_STREAM : SV_FP32_TILE;
+    if (iter_pass == 1 || ntiles < STREAM_MIN_TILES) return short_tiles ? SV_FP32_SHORT : SV_FP32_TILE;
+    return SV_FP32_STREAM;
 }
 
 ppe_status check_solve_args(ppe_grid *g, const double *rhs, double *x, double tol, ppe_mode mode,
@@ -323,7 +335,7 @@ ppe_status drive_host(int n, ppe_grid *const *grids, LaunchSet &ls, int blocks, 
                       ppe_net *net, const ppe_solve_opts &opts, cudaStream_t stream, ppe_solve_info *info,
                       Replan *rp)
 {
-    const bool fp64 = variant == SV_FP64;
+    const bool fp64 = solver_variant_fp64(variant);
     SolverArgs a;
     std::memset(&a, 0, sizeof a);
     a.sys = ls.sys; a.st = ls.st; a.ranges = ls.ranges; a.slots = ls.slots; a.nslots = nslots; a.ctl = ls.ctl;
@@ -737,7 +749,7 @@ ppe_status solve_single(ppe_grid *g, const double *rhs, double *x, double tol, p
             tune_lookup(g->nx, g->ny, &pass, &bps);
         }
     }
-    const SolverVariant v = pick_variant(prec, pass, g->tiles_x * g->tiles_y);
+    const SolverVariant v = pick_variant(prec, pass, g->tiles_x * g->tiles_y, g->opts.tile_rows);
     std::vector<SysDesc> sds(1, make_desc(g, rhs, x, tol, mode, prec, 0, v));
     const int maxb = std::min(solver_max_blocks(v, bps), sds[0].ntiles);
     if (maxb < 1) return cuda_status(cudaErrorInvalidConfiguration, "solver occupancy");
@@ -808,7 +820,7 @@ ppe_status ppe_solve_batch(int n, ppe_grid *const *grids, const double *const *r
     cudaStream_t st = (cudaStream_t)stream;
     int ntiles = 0;
     for (int i = 0; i < n; ++i) ntiles += grids[i]->tiles_x * grids[i]->tiles_y;
-    const SolverVariant v = pick_variant(prec, grids[0]->opts.iter_pass, ntiles);
+    const SolverVariant v = pick_variant(prec, grids[0]->opts.iter_pass, ntiles, grids[0]->opts.tile_rows);
     std::vector<SysDesc> sds(n);
     std::vector<int32_t> full(n);
     for (int i = 0; i < n; ++i) {

@@ -55,17 +55,25 @@ namespace ppe {
 
 namespace {
 
-// Geometry of a tile of width TW (128 for the tile-cooperative kernels, 124
-// for the streaming kernel) and 16 rows, with its window (halo 4 in x so that
-// the window starts on a 16-byte boundary, halo 2 in y) and one-cell ring.
-template <int TW> struct Geo {
-    static constexpr int TX = TW;
+// Geometry of a tile: TX columns (128 for the tile-cooperative kernels, 124
+// for the streaming kernel) and TY rows (16, or 8 for the short-tile kernels
+// that spread a small grid over twice the blocks), with its window (halo 4
+// in x so that the window starts on a 16-byte boundary, halo 2 in y) and
+// one-cell ring.  The template key GK packs both: TX * 32 + TY.
+constexpr int geo_key(int tx, int ty) { return tx * 32 + ty; }
+constexpr int GEO_TILE = geo_key(TILE_X, TILE_Y), GEO_SHORT = geo_key(TILE_X, TILE_Y_SHORT),
+              GEO_STREAM = geo_key(TILE_X_STREAM, TILE_Y);
+template <int GK> struct Geo {
+    static constexpr int TX = GK / 32, TY = GK % 32;
     static constexpr int OX = WIN_OX, OY = WIN_OY;
-    static constexpr int WX = TW + 2 * WIN_OX, WY = TILE_Y + 2 * WIN_OY, WN = WX * WY;
+    static constexpr int WX = TX + 2 * WIN_OX, WY = TY + 2 * WIN_OY, WN = WX * WY;
     static constexpr int WN_PAD = (WN + 31) / 32 * 32;     // window buffers padded to 128 bytes (FP32)
-    static constexpr int RX = TW + 2, RY = TILE_Y + 2, RN = RX * RY;
-    static constexpr int TN = TW * TILE_Y;
+    static constexpr int RX = TX + 2, RY = TY + 2, RN = RX * RY;
+    static constexpr int TN = TX * TY;
     static constexpr int NRL = (RN + SOLVER_THREADS - 1) / SOLVER_THREADS;   // ring loads per thread
+    // the passes that work row by row: SOLVER_THREADS / TY threads per row,
+    // up to CPT columns each
+    static constexpr int TPR = SOLVER_THREADS / TY, CPT = (TX + TPR - 1) / TPR;
 };
 constexpr int NWARP = SOLVER_THREADS / 32;
 
@@ -76,42 +84,43 @@ template <> __device__ __forceinline__ float recip<float>(float v) { return v > 
 template <> __device__ __forceinline__ double recip<double>(double v) { return v > 0.0 ? 1.0 / v : 0.0; }
 
 // Coefficients over the tile window, in the arithmetic type C.
-template <typename C, int TW> struct alignas(16) Coef {
+template <typename C, int GK> struct alignas(16) Coef {
     // the tile-cooperative geometry also keeps the window's Jacobi weights
     // D^-1 (computed once per tile, read every pass); the streaming pass
     // forms them from the 1-D arrays
-    static constexpr bool KEEP_DINV = TW == TILE_X;
-    C dx[Geo<TW>::WX], fw[Geo<TW>::WX], fe[Geo<TW>::WX], sx[Geo<TW>::WX];
-    C dy[Geo<TW>::WY], fs[Geo<TW>::WY], fn[Geo<TW>::WY], sy[Geo<TW>::WY];
-    C dinv[KEEP_DINV ? Geo<TW>::WN : 1];
+    static constexpr bool KEEP_DINV = Geo<GK>::TX == TILE_X;
+    C dx[Geo<GK>::WX], fw[Geo<GK>::WX], fe[Geo<GK>::WX], sx[Geo<GK>::WX];
+    C dy[Geo<GK>::WY], fs[Geo<GK>::WY], fn[Geo<GK>::WY], sy[Geo<GK>::WY];
+    C dinv[KEEP_DINV ? Geo<GK>::WN : 1];
 };
 
 // TMA destinations of one tile: r and p windows, d tile (sizes are multiples
 // of 128 bytes, so every part stays 128-byte aligned).
-template <typename T, int TW> struct Stage {
-    T r[Geo<TW>::WN_PAD];
-    T p[Geo<TW>::WN_PAD];
-    T d[Geo<TW>::TN];
+template <typename T, int GK> struct Stage {
+    T r[Geo<GK>::WN_PAD];
+    T p[Geo<GK>::WN_PAD];
+    T d[Geo<GK>::TN];
 };
-static_assert((Geo<TILE_X>::WN_PAD * 4) % 128 == 0 && (Geo<TILE_X>::TN * 4) % 128 == 0,
+static_assert((Geo<GEO_TILE>::WN_PAD * 4) % 128 == 0 && (Geo<GEO_TILE>::TN * 4) % 128 == 0 &&
+                  (Geo<GEO_SHORT>::WN_PAD * 4) % 128 == 0 && (Geo<GEO_SHORT>::TN * 4) % 128 == 0,
               "TMA destinations must stay 128-byte aligned");
 
 // The 1-D coefficient arrays of a tile's window as stored in global memory
 // (cell widths, face coefficients; zero outside the grid), staged by cp.async.
-template <typename T, int TW> struct CoefRaw {
-    T dx[Geo<TW>::WX], fx[Geo<TW>::WX + 1], dy[Geo<TW>::WY], fy[Geo<TW>::WY + 1];
+template <typename T, int GK> struct CoefRaw {
+    T dx[Geo<GK>::WX], fx[Geo<GK>::WX + 1], dy[Geo<GK>::WY], fy[Geo<GK>::WY + 1];
 };
 
-template <typename T, int TW> struct IterBufs {
-    Stage<T, TW> st[2];
-    T un[Geo<TW>::WN_PAD];    // new u on the one-cell ring
-    T q[Geo<TW>::WN_PAD];     // A p on the one-cell ring
-    CoefRaw<T, TW> raw[2];    // the next tile's coefficient arrays, in flight during this tile
+template <typename T, int GK> struct IterBufs {
+    Stage<T, GK> st[2];
+    T un[Geo<GK>::WN_PAD];    // new u on the one-cell ring
+    T q[Geo<GK>::WN_PAD];     // A p on the one-cell ring
+    CoefRaw<T, GK> raw[2];    // the next tile's coefficient arrays, in flight during this tile
 };
 
 // Scratch windows of the other passes.
-template <typename T, int TW> struct Work {
-    T a0[Geo<TW>::WN_PAD], a1[Geo<TW>::WN_PAD], a2[Geo<TW>::WN_PAD];
+template <typename T, int GK> struct Work {
+    T a0[Geo<GK>::WN_PAD], a1[Geo<GK>::WN_PAD], a2[Geo<GK>::WN_PAD];
 };
 
 // Per-warp TMA chunks of the streaming pass: two buffers of SRB rows of r and
@@ -127,23 +136,23 @@ struct StreamBufs {
     unsigned char buf[SOLVER_THREADS / 32][2][S_CHUNK];
 };
 
-template <typename T, int TW> union PassBufs {
-    IterBufs<T, TW> it;
-    Work<T, TW> w;
+template <typename T, int GK> union PassBufs {
+    IterBufs<T, GK> it;
+    Work<T, GK> w;
 };
-template <typename T> union PassBufs<T, TILE_X_STREAM> {
-    Work<T, TILE_X_STREAM> w;
+template <typename T> union PassBufs<T, GEO_STREAM> {
+    Work<T, GEO_STREAM> w;
     StreamBufs sb;
 };
 
-template <typename T, int TW_> struct SmemT {
-    static constexpr int TW = TW_;
-    PassBufs<T, TW_> u;                  // first member: 128-byte aligned
+template <typename T, int GK_> struct SmemT {
+    static constexpr int GK = GK_;
+    PassBufs<T, GK_> u;                  // first member: 128-byte aligned
     unsigned long long bar[2];           // TMA completion barriers of the two stages
     unsigned long long sbar[NWARP][2];   // streaming pass: per-warp chunk barriers
     uint32_t sfills[NWARP];              // streaming pass: chunks issued per warp (buffer = fill & 1)
-    Coef<double, TW_> cfd;
-    Coef<float, TW_> cff;
+    Coef<double, GK_> cfd;
+    Coef<float, GK_> cff;
     float red_hi[2][NPART][NWARP], red_lo[2][NPART][NWARP];   // per-warp partials, two buffers
     SysDesc sd[SMAX];
     SysState st[SMAX];
@@ -160,16 +169,16 @@ template <typename T, int TW_> struct SmemT {
 
 // Dynamic shared memory of a block (plus 128 bytes of alignment slack): one
 // block per SM in every variant.
-static_assert(sizeof(SmemT<float, TILE_X>) + 128 <= 227 * 1024, "FP32 solver: one block per SM");
+static_assert(sizeof(SmemT<float, GEO_TILE>) + 128 <= 227 * 1024, "FP32 solver: one block per SM");
 static_assert(SMAX <= NWARP, "one warp per system of a block in the step's reduction");
-static_assert(sizeof(SmemT<double, TILE_X>) + 128 <= 227 * 1024, "FP64 solver: one block per SM");
-static_assert(sizeof(SmemT<float, TILE_X_STREAM>) + 128 <= 227 * 1024, "streaming solver: one block per SM");
+static_assert(sizeof(SmemT<double, GEO_TILE>) + 128 <= 227 * 1024, "FP64 solver: one block per SM");
+static_assert(sizeof(SmemT<float, GEO_STREAM>) + 128 <= 227 * 1024, "streaming solver: one block per SM");
 
-template <typename C, int TW>
-__device__ void load_coef(Coef<C, TW> &cf, const SysDesc &sd, int i0, int j0, const C *DX, const C *FX,
+template <typename C, int GK>
+__device__ void load_coef(Coef<C, GK> &cf, const SysDesc &sd, int i0, int j0, const C *DX, const C *FX,
                           const C *DY, const C *FY)
 {
-    constexpr int WX = Geo<TW>::WX, WY = Geo<TW>::WY, OX = Geo<TW>::OX, OY = Geo<TW>::OY;
+    constexpr int WX = Geo<GK>::WX, WY = Geo<GK>::WY, OX = Geo<GK>::OX, OY = Geo<GK>::OY;
     for (int k = threadIdx.x; k < WX; k += blockDim.x) {
         int i = i0 - OX + k;
         bool in = i >= 0 && i < sd.nx;
@@ -182,16 +191,16 @@ __device__ void load_coef(Coef<C, TW> &cf, const SysDesc &sd, int i0, int j0, co
         C w = in ? DY[j] : C(0), a = in ? FY[j] : C(0), b = in ? FY[j + 1] : C(0);
         cf.dy[k] = w; cf.fs[k] = a; cf.fn[k] = b; cf.sy[k] = a + b;
     }
-    if constexpr (Coef<C, TW>::KEEP_DINV) {
+    if constexpr (Coef<C, GK>::KEEP_DINV) {
         __syncthreads();
-        for (int k = threadIdx.x; k < Geo<TW>::WN; k += blockDim.x) {
+        for (int k = threadIdx.x; k < Geo<GK>::WN; k += blockDim.x) {
             const int wi = k % WX, wj = k / WX;
             cf.dinv[k] = recip<C>(cf.dy[wj] * cf.sx[wi] + cf.dx[wi] * cf.sy[wj]);
         }
     }
 }
 
-template <typename T, typename S> __device__ __forceinline__ Coef<T, S::TW> &coef_of(S &sm)
+template <typename T, typename S> __device__ __forceinline__ Coef<T, S::GK> &coef_of(S &sm)
 {
     if constexpr (sizeof(T) == 4)
         return sm.cff;
@@ -244,10 +253,10 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Start copying the coefficient arrays of the tile at (i0, j0) into raw.
-template <typename T, int TW>
-__device__ __forceinline__ void issue_coef_raw(CoefRaw<T, TW> &raw, const SysDesc &sd, int i0, int j0)
+template <typename T, int GK>
+__device__ __forceinline__ void issue_coef_raw(CoefRaw<T, GK> &raw, const SysDesc &sd, int i0, int j0)
 {
-    constexpr int WX = Geo<TW>::WX, WY = Geo<TW>::WY, OX = Geo<TW>::OX, OY = Geo<TW>::OY;
+    constexpr int WX = Geo<GK>::WX, WY = Geo<GK>::WY, OX = Geo<GK>::OX, OY = Geo<GK>::OY;
     const T *DX, *FX, *DY, *FY;
     if constexpr (sizeof(T) == 4) {
         DX = sd.dx32; FX = sd.fx32; DY = sd.dy32; FY = sd.fy32;
@@ -279,10 +288,10 @@ __device__ __forceinline__ void issue_coef_raw(CoefRaw<T, TW> &raw, const SysDes
 // The tile's coefficients (and D^-1 window) from staged arrays, as load_coef
 // forms them from global memory; the caller has waited for the copies and
 // synchronised the block.
-template <typename C, int TW>
-__device__ void coef_from_raw(Coef<C, TW> &cf, const CoefRaw<C, TW> &raw, const SysDesc &sd, int i0, int j0)
+template <typename C, int GK>
+__device__ void coef_from_raw(Coef<C, GK> &cf, const CoefRaw<C, GK> &raw, const SysDesc &sd, int i0, int j0)
 {
-    constexpr int WX = Geo<TW>::WX, WY = Geo<TW>::WY, OX = Geo<TW>::OX, OY = Geo<TW>::OY;
+    constexpr int WX = Geo<GK>::WX, WY = Geo<GK>::WY, OX = Geo<GK>::OX, OY = Geo<GK>::OY;
     for (int k = threadIdx.x; k < WX; k += blockDim.x) {
         const bool in = (unsigned)(i0 - OX + k) < (unsigned)sd.nx;
         const C a = in ? raw.fx[k] : C(0), b = in ? raw.fx[k + 1] : C(0);
@@ -293,9 +302,9 @@ __device__ void coef_from_raw(Coef<C, TW> &cf, const CoefRaw<C, TW> &raw, const 
         const C a = in ? raw.fy[k] : C(0), b = in ? raw.fy[k + 1] : C(0);
         cf.dy[k] = raw.dy[k]; cf.fs[k] = a; cf.fn[k] = b; cf.sy[k] = a + b;
     }
-    if constexpr (Coef<C, TW>::KEEP_DINV) {
+    if constexpr (Coef<C, GK>::KEEP_DINV) {
         __syncthreads();
-        for (int k = threadIdx.x; k < Geo<TW>::WN; k += blockDim.x) {
+        for (int k = threadIdx.x; k < Geo<GK>::WN; k += blockDim.x) {
             const int wi = k % WX, wj = k / WX;
             cf.dinv[k] = recip<C>(cf.dy[wj] * cf.sx[wi] + cf.dx[wi] * cf.sy[wj]);
         }
@@ -312,18 +321,18 @@ template <typename T, typename S> __device__ __forceinline__ void set_coef_tag(S
     }
 }
 
-template <typename C, int TW> __device__ __forceinline__ C dinv_at(const Coef<C, TW> &cf, int wi, int wj)
+template <typename C, int GK> __device__ __forceinline__ C dinv_at(const Coef<C, GK> &cf, int wi, int wj)
 {
-    if constexpr (Coef<C, TW>::KEEP_DINV)
-        return cf.dinv[wj * Geo<TW>::WX + wi];
+    if constexpr (Coef<C, GK>::KEEP_DINV)
+        return cf.dinv[wj * Geo<GK>::WX + wi];
     else
         return recip<C>(cf.dy[wj] * cf.sx[wi] + cf.dx[wi] * cf.sy[wj]);
 }
 
 // (A U) at window point (wi, wj); U holds the window, zero outside the domain.
-template <typename C, int TW> __device__ __forceinline__ C stencil(const Coef<C, TW> &cf, const C *U, int wi, int wj)
+template <typename C, int GK> __device__ __forceinline__ C stencil(const Coef<C, GK> &cf, const C *U, int wi, int wj)
 {
-    constexpr int WX = Geo<TW>::WX;
+    constexpr int WX = Geo<GK>::WX;
     int k = wj * WX + wi;
     C c = U[k];
     C ax = cf.fe[wi] * (c - U[k + 1]) + cf.fw[wi] * (c - U[k - 1]);
@@ -352,20 +361,20 @@ __device__ __forceinline__ bool in_dom(const SysDesc &sd, int i, int j)
 }
 
 // k-th point of the one-cell ring around the tile, as window coordinates
-template <int TW> __device__ __forceinline__ void ring_point(int k, int &wi, int &wj)
+template <int GK> __device__ __forceinline__ void ring_point(int k, int &wi, int &wj)
 {
-    wi = Geo<TW>::OX - 1 + k % Geo<TW>::RX;
-    wj = Geo<TW>::OY - 1 + k / Geo<TW>::RX;
+    wi = Geo<GK>::OX - 1 + k % Geo<GK>::RX;
+    wj = Geo<GK>::OY - 1 + k / Geo<GK>::RX;
 }
 
 // Tiles are numbered column by column (a strip of tiles stacked in y), so a
 // contiguous range of tiles is mostly a vertical strip: the streaming
 // iteration pass marches down it.
-template <int TW> __device__ __forceinline__ void tile_origin(const SysDesc &sd, int t, int &i0, int &j0)
+template <int GK> __device__ __forceinline__ void tile_origin(const SysDesc &sd, int t, int &i0, int &j0)
 {
     int lt = t - sd.tile0;
-    i0 = (lt / sd.tiles_y) * TW;
-    j0 = (lt % sd.tiles_y) * TILE_Y;
+    i0 = (lt / sd.tiles_y) * Geo<GK>::TX;
+    j0 = (lt % sd.tiles_y) * Geo<GK>::TY;
 }
 
 // Float-float (hi + lo) accumulation: ~48-bit sums on the FP32 pipes.  On
@@ -475,17 +484,17 @@ template <typename T, typename S>
 __device__ void pass_init(S &sm, const SysDesc &sd, const SysState &st, int i0, int j0, Acc &acc)
 {
     const double sg = sys_scale(st);
-    using G = Geo<S::TW>;
+    using G = Geo<S::GK>;
     constexpr int WX = G::WX, WN = G::WN, OX = G::OX, OY = G::OY, RN = G::RN, NRL = G::NRL, TILE_X = G::TX;
     constexpr int TILE_N = G::TN;
     (void)WX; (void)WN; (void)OX; (void)OY; (void)RN; (void)NRL; (void)TILE_X; (void)TILE_N;
     double t[NPART] = {0, 0, 0, 0, 0, 0};
-    const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
+    const int ty = threadIdx.x / G::TPR, tx = threadIdx.x % G::TPR;
     int j = j0 + ty;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        int i = i0 + tx + 32 * c;
-        if (tx + 32 * c < TILE_X && i < sd.nx && j < sd.ny) {
+    for (int c = 0; c < G::CPT; ++c) {
+        int i = i0 + tx + G::TPR * c;
+        if (tx + G::TPR * c < TILE_X && i < sd.nx && j < sd.ny) {
             double b = -sd.dx[i] * sd.dy[j] * sd.f[(size_t)j * sd.nx + i] * sg;
             t[0] += b; t[1] += b * b; t[2] += fabs(b);
         }
@@ -497,7 +506,7 @@ __device__ void pass_init(S &sm, const SysDesc &sd, const SysState &st, int i0, 
 template <typename T, typename S>
 __device__ void pass_res(S &sm, const SysDesc &sd, const SysState &st, int i0, int j0, int tag, Acc &acc)
 {
-    using G = Geo<S::TW>;
+    using G = Geo<S::GK>;
     constexpr int WX = G::WX, WN = G::WN, OX = G::OX, OY = G::OY, RN = G::RN, NRL = G::NRL, TILE_X = G::TX;
     constexpr int TILE_N = G::TN;
     (void)WX; (void)WN; (void)OX; (void)OY; (void)RN; (void)NRL; (void)TILE_X; (void)TILE_N;
@@ -510,7 +519,7 @@ __device__ void pass_res(S &sm, const SysDesc &sd, const SysState &st, int i0, i
 #pragma unroll
     for (int q = 0; q < NRL; ++q) {
         int k = threadIdx.x + q * SOLVER_THREADS, wi, wj;
-        ring_point<S::TW>(k, wi, wj);
+        ring_point<S::GK>(k, wi, wj);
         int i = i0 - OX + wi, j = j0 - OY + wj;
         xv[q] = 0.0;
         if (k < RN && in_dom(sd, i, j)) {
@@ -521,18 +530,18 @@ __device__ void pass_res(S &sm, const SysDesc &sd, const SysState &st, int i0, i
 #pragma unroll
     for (int q = 0; q < NRL; ++q) {
         int k = threadIdx.x + q * SOLVER_THREADS, wi, wj;
-        ring_point<S::TW>(k, wi, wj);
+        ring_point<S::GK>(k, wi, wj);
         if (k < RN) X[wj * WX + wi] = xv[q];
     }
     __syncthreads();
     double t[NPART] = {0, 0, 0, 0, 0, 0};
-    const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
+    const int ty = threadIdx.x / G::TPR, tx = threadIdx.x % G::TPR;
     int j = j0 + ty, wj = ty + OY;
     T *r = (T *)sd.r[st.cur];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        int i = i0 + tx + 32 * c, wi = tx + 32 * c + OX;
-        if (tx + 32 * c < TILE_X && i < sd.nx && j < sd.ny) {
+    for (int c = 0; c < G::CPT; ++c) {
+        int i = i0 + tx + G::TPR * c, wi = tx + G::TPR * c + OX;
+        if (tx + G::TPR * c < TILE_X && i < sd.nx && j < sd.ny) {
             double b = -sd.dx[i] * sd.dy[j] * ld_cg(sd.f + (size_t)j * sd.nx + i) * sg - st.mu_b;
             double rv = b - stencil<double>(cf, X, wi, wj);
             r[(size_t)j * sd.pitch + i] = (T)rv;
@@ -549,7 +558,7 @@ __device__ void pass_res(S &sm, const SysDesc &sd, const SysState &st, int i0, i
 template <typename T, typename S>
 __device__ void pass_restart(S &sm, const SysDesc &sd, const SysState &st, int i0, int j0, int tag, Acc &acc)
 {
-    using G = Geo<S::TW>;
+    using G = Geo<S::GK>;
     constexpr int WX = G::WX, WN = G::WN, OX = G::OX, OY = G::OY, RN = G::RN, NRL = G::NRL, TILE_X = G::TX;
     constexpr int TILE_N = G::TN;
     (void)WX; (void)WN; (void)OX; (void)OY; (void)RN; (void)NRL; (void)TILE_X; (void)TILE_N;
@@ -564,7 +573,7 @@ __device__ void pass_restart(S &sm, const SysDesc &sd, const SysState &st, int i
 #pragma unroll
     for (int q = 0; q < NRL; ++q) {
         int k = threadIdx.x + q * SOLVER_THREADS, wi, wj;
-        ring_point<S::TW>(k, wi, wj);
+        ring_point<S::GK>(k, wi, wj);
         int i = i0 - OX + wi, j = j0 - OY + wj;
         rv[q] = 0; pv[q] = 0;
         if (k < RN && in_dom(sd, i, j)) {
@@ -577,7 +586,7 @@ __device__ void pass_restart(S &sm, const SysDesc &sd, const SysState &st, int i
 #pragma unroll
     for (int q = 0; q < NRL; ++q) {
         int k = threadIdx.x + q * SOLVER_THREADS, wi, wj;
-        ring_point<S::TW>(k, wi, wj);
+        ring_point<S::GK>(k, wi, wj);
         if (k < RN) {
             int w = wj * WX + wi;
             R[w] = rv[q];
@@ -587,13 +596,13 @@ __device__ void pass_restart(S &sm, const SysDesc &sd, const SysState &st, int i
     }
     __syncthreads();
     T t[NPART] = {0, 0, 0, 0, 0, 0};
-    const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
+    const int ty = threadIdx.x / G::TPR, tx = threadIdx.x % G::TPR;
     int j = j0 + ty, wj = ty + OY;
     T *dd = (T *)sd.d;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        int i = i0 + tx + 32 * c, wi = tx + 32 * c + OX;
-        if (tx + 32 * c < TILE_X && i < sd.nx && j < sd.ny) {
+    for (int c = 0; c < G::CPT; ++c) {
+        int i = i0 + tx + G::TPR * c, wi = tx + G::TPR * c + OX;
+        if (tx + G::TPR * c < TILE_X && i < sd.nx && j < sd.ny) {
             int k = wj * WX + wi;
             T w = stencil<T>(cf, U, wi, wj);
             t[0] += R[k] * U[k]; t[1] += w * U[k]; t[2] += R[k] * R[k]; t[3] += R[k];
@@ -636,10 +645,10 @@ __device__ __forceinline__ void st4(double *p, const double (&v)[4])
 }
 
 // (A U) at the four window points w .. w + 3 of row wj (columns wc .. wc + 3).
-template <typename C, int TW>
-__device__ __forceinline__ void stencil4(const Coef<C, TW> &cf, const C *U, int w, int wc, int wj, C (&out)[4])
+template <typename C, int GK>
+__device__ __forceinline__ void stencil4(const Coef<C, GK> &cf, const C *U, int w, int wc, int wj, C (&out)[4])
 {
-    constexpr int WX = Geo<TW>::WX;
+    constexpr int WX = Geo<GK>::WX;
     C c[4], n[4], sv[4], fe[4], fw[4], dx[4];
     ld4(U + w, c);
     ld4(U + w + WX, n);
@@ -662,14 +671,14 @@ template <typename T, typename S>
 __device__ __forceinline__ void iter_issue_at(S &sm, const SysDesc &sd, int cur, int pcur, bool first, int t,
                                               uint32_t fill, bool fence)
 {
-    using G = Geo<S::TW>;
+    using G = Geo<S::GK>;
     constexpr int WX = G::WX, WN = G::WN, OX = G::OX, OY = G::OY, RN = G::RN, NRL = G::NRL, TILE_X = G::TX;
     constexpr int TILE_N = G::TN;
     (void)WX; (void)WN; (void)OX; (void)OY; (void)RN; (void)NRL; (void)TILE_X; (void)TILE_N;
     int i0, j0;
-    tile_origin<S::TW>(sd, t, i0, j0);
+    tile_origin<S::GK>(sd, t, i0, j0);
     const int s = fill & 1;
-    Stage<T, S::TW> &stg = sm.u.it.st[s];
+    Stage<T, S::GK> &stg = sm.u.it.st[s];
     const uint32_t bar = smem_u32(&sm.bar[s]);
     const uint32_t bytes = (uint32_t)(((first ? 1 : 2) * WN + TILE_N) * sizeof(T));
     // The grid's writes of the vectors (ordered by the step barrier) before
@@ -706,14 +715,14 @@ __device__ __forceinline__ void iter_issue(S &sm, const SysDesc &sd, const SysSt
 template <typename T, typename S>
 __device__ void pass_iter(S &sm, int q, int t_lo, int t_hi, Acc &acc, const SolverArgs &a)
 {
-    using G = Geo<S::TW>;
+    using G = Geo<S::GK>;
     constexpr int WX = G::WX, WN = G::WN, OX = G::OX, OY = G::OY, RN = G::RN, NRL = G::NRL, TILE_X = G::TX;
     constexpr int TILE_N = G::TN;
     (void)WX; (void)WN; (void)OX; (void)OY; (void)RN; (void)NRL; (void)TILE_X; (void)TILE_N;
     const SysDesc &sd = sm.sd[q];
     const SysState &st = sm.st[q];
     auto &cf = coef_of<T>(sm);
-    IterBufs<T, S::TW> &ib = sm.u.it;
+    IterBufs<T, S::GK> &ib = sm.u.it;
     T *Un = ib.un, *Q = ib.q;
     const int n = t_hi - t_lo;
     if (n <= 0) return;
@@ -729,7 +738,7 @@ __device__ void pass_iter(S &sm, int q, int t_lo, int t_hi, Acc &acc, const Solv
         const uint32_t fill = fill0 + k;
         if (threadIdx.x == 0 && k + 1 < n) iter_issue<T>(sm, sd, st, t + 1, fill + 1, false);
         int i0, j0;
-        tile_origin<S::TW>(sd, t, i0, j0);
+        tile_origin<S::GK>(sd, t, i0, j0);
         if (k == 0) {
             load_coef_t<T>(sm, sd, i0, j0, t);
         } else {
@@ -741,10 +750,10 @@ __device__ void pass_iter(S &sm, int q, int t_lo, int t_hi, Acc &acc, const Solv
         }
         if (k + 1 < n) {
             int i1, j1;
-            tile_origin<S::TW>(sd, t + 1, i1, j1);
+            tile_origin<S::GK>(sd, t + 1, i1, j1);
             issue_coef_raw<T>(ib.raw[(k + 1) & 1], sd, i1, j1);
         }
-        Stage<T, S::TW> &stg = ib.st[fill & 1];
+        Stage<T, S::GK> &stg = ib.st[fill & 1];
         const bool prof = a.prof && blockIdx.x == 0 && threadIdx.x == 0 && q == 0;
         if (prof) sm.ptime[0] = gtimer();
         if (!mbar_wait_bounded(smem_u32(&sm.bar[fill & 1]), (fill >> 1) & 1, a.spin_limit_ns)) {
@@ -756,7 +765,7 @@ __device__ void pass_iter(S &sm, int q, int t_lo, int t_hi, Acc &acc, const Solv
         // Every stage works on groups of four consecutive cells (16-byte
         // shared and global accesses); window rows (136), the tile's columns
         // (from window column 4) and the grid pitch are multiples of four.
-        static_assert(Coef<T, S::TW>::KEEP_DINV && WX % 4 == 0 && OX % 4 == 0 && TILE_X % 4 == 0,
+        static_assert(Coef<T, S::GK>::KEEP_DINV && WX % 4 == 0 && OX % 4 == 0 && TILE_X % 4 == 0,
                       "four-cell groups stay aligned");
         constexpr int GX = WX / 4, TG = TILE_X / 4;
         // window: r - mu and the new direction p = u + beta p (zero outside the domain)
@@ -1087,7 +1096,7 @@ __device__ __noinline__ void pass_iter_stream(S &sm, int q, int t_lo, int t_hi, 
 template <typename T, typename S, bool UPD>
 __device__ void pass_dlsm(S &sm, const SysDesc &sd, const SysState &st, int i0, int j0, int tag, Acc &acc)
 {
-    using G = Geo<S::TW>;
+    using G = Geo<S::GK>;
     constexpr int WX = G::WX, WN = G::WN, OX = G::OX, OY = G::OY, RN = G::RN, NRL = G::NRL, TILE_X = G::TX;
     constexpr int TILE_N = G::TN;
     (void)WX; (void)WN; (void)OX; (void)OY; (void)RN; (void)NRL; (void)TILE_X; (void)TILE_N;
@@ -1100,7 +1109,7 @@ __device__ void pass_dlsm(S &sm, const SysDesc &sd, const SysState &st, int i0, 
 #pragma unroll
     for (int q = 0; q < NRL; ++q) {
         int k = threadIdx.x + q * SOLVER_THREADS, wi, wj;
-        ring_point<S::TW>(k, wi, wj);
+        ring_point<S::GK>(k, wi, wj);
         int i = i0 - OX + wi, j = j0 - OY + wj;
         ev[q] = 0.f;
         if (k < RN && in_dom(sd, i, j)) ev[q] = ld_cg(sd.e + (size_t)j * sd.pitch + i);
@@ -1108,7 +1117,7 @@ __device__ void pass_dlsm(S &sm, const SysDesc &sd, const SysState &st, int i0, 
 #pragma unroll
     for (int q = 0; q < NRL; ++q) {
         int k = threadIdx.x + q * SOLVER_THREADS, wi, wj;
-        ring_point<S::TW>(k, wi, wj);
+        ring_point<S::GK>(k, wi, wj);
         if (k < RN) E[wj * WX + wi] = ev[q];
     }
     __syncthreads();
@@ -1118,12 +1127,12 @@ __device__ void pass_dlsm(S &sm, const SysDesc &sd, const SysState &st, int i0, 
     T *dv = (T *)sd.d;
     const T mu = sc_mu<T>(st), alpha = sc_alpha_d<T>(st);
     T t[NPART] = {0, 0, 0, 0, 0, 0};
-    const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
+    const int ty = threadIdx.x / G::TPR, tx = threadIdx.x % G::TPR;
     int j = j0 + ty, wj = ty + OY;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        int i = i0 + tx + 32 * c, wi = tx + 32 * c + OX;
-        if (tx + 32 * c < TILE_X && i < sd.nx && j < sd.ny) {
+    for (int c = 0; c < G::CPT; ++c) {
+        int i = i0 + tx + G::TPR * c, wi = tx + G::TPR * c + OX;
+        if (tx + G::TPR * c < TILE_X && i < sd.nx && j < sd.ny) {
             int k = wj * WX + wi;
             size_t gi = (size_t)j * sd.pitch + i;
             T e = E[k];
@@ -1147,19 +1156,19 @@ __device__ void pass_dlsm(S &sm, const SysDesc &sd, const SysState &st, int i0, 
 template <typename T, typename S>
 __device__ void pass_final1(S &sm, const SysDesc &sd, const SysState &st, int i0, int j0, Acc &acc)
 {
-    using G = Geo<S::TW>;
+    using G = Geo<S::GK>;
     constexpr int WX = G::WX, WN = G::WN, OX = G::OX, OY = G::OY, RN = G::RN, NRL = G::NRL, TILE_X = G::TX;
     constexpr int TILE_N = G::TN;
     (void)WX; (void)WN; (void)OX; (void)OY; (void)RN; (void)NRL; (void)TILE_X; (void)TILE_N;
     const T *dd = (const T *)sd.d;
     const double sg = sys_scale(st);
     double t[NPART] = {0, 0, 0, 0, 0, 0};
-    const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
+    const int ty = threadIdx.x / G::TPR, tx = threadIdx.x % G::TPR;
     int j = j0 + ty;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        int i = i0 + tx + 32 * c;
-        if (tx + 32 * c < TILE_X && i < sd.nx && j < sd.ny) {
+    for (int c = 0; c < G::CPT; ++c) {
+        int i = i0 + tx + G::TPR * c;
+        if (tx + G::TPR * c < TILE_X && i < sd.nx && j < sd.ny) {
             size_t gx = (size_t)j * sd.nx + i;
             double x = st.zero_x ? 0.0 : ld_cg(sd.x + gx);
             if (st.fold_d && !st.zero_x) x += (double)ld_cg(dd + (size_t)j * sd.pitch + i) * sys_unscale(st);
@@ -1174,16 +1183,16 @@ __device__ void pass_final1(S &sm, const SysDesc &sd, const SysState &st, int i0
 template <typename T, typename S>
 __device__ void pass_final2(S &sm, const SysDesc &sd, const SysState &st, int i0, int j0, Acc &acc)
 {
-    using G = Geo<S::TW>;
+    using G = Geo<S::GK>;
     constexpr int WX = G::WX, WN = G::WN, OX = G::OX, OY = G::OY, RN = G::RN, NRL = G::NRL, TILE_X = G::TX;
     constexpr int TILE_N = G::TN;
     (void)WX; (void)WN; (void)OX; (void)OY; (void)RN; (void)NRL; (void)TILE_X; (void)TILE_N;
-    const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
+    const int ty = threadIdx.x / G::TPR, tx = threadIdx.x % G::TPR;
     int j = j0 + ty;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        int i = i0 + tx + 32 * c;
-        if (tx + 32 * c < TILE_X && i < sd.nx && j < sd.ny) {
+    for (int c = 0; c < G::CPT; ++c) {
+        int i = i0 + tx + G::TPR * c;
+        if (tx + G::TPR * c < TILE_X && i < sd.nx && j < sd.ny) {
             size_t gx = (size_t)j * sd.nx + i;
             sd.x[gx] = ld_cg(sd.x + gx) - st.xmean * sys_unscale(st);
         }
@@ -1513,7 +1522,7 @@ __device__ void run_pass(S &sm, int q, int ph, int t, Acc &acc)
     const SysDesc &sd = sm.sd[q];
     const SysState &st = sm.st[q];
     int i0, j0;
-    tile_origin<S::TW>(sd, t, i0, j0);
+    tile_origin<S::GK>(sd, t, i0, j0);
     switch (ph) {
     case PH_INIT: pass_init<T>(sm, sd, st, i0, j0, acc); break;
     case PH_RES: pass_res<T>(sm, sd, st, i0, j0, t, acc); break;
@@ -1604,16 +1613,19 @@ __device__ void block_publish(S &sm, const Acc &acc, Slot *slot, uint32_t *count
     }
 }
 
-// STREAM (FP32 only) selects the streaming iteration pass; its register
-// needs allow one block per SM.
-template <typename T, bool STREAM>
+// GK selects the tile geometry: GEO_TILE and GEO_SHORT run the
+// tile-cooperative iteration pass on 128x16 or 128x8 tiles, GEO_STREAM
+// (FP32 only) the streaming pass; their register needs allow one block per
+// SM.
+template <typename T, int GK_>
 __global__ void __launch_bounds__(SOLVER_THREADS, 1)
     solver_kernel(SolverArgs a, int resume_net)
 {
+    constexpr bool STREAM = GK_ == GEO_STREAM;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // TMA destinations need 128-byte alignment: round the base up (the launch
     // reserves 128 extra bytes)
-    using Sm = SmemT<T, STREAM ? TILE_X_STREAM : TILE_X>;
+    using Sm = SmemT<T, GK_>;
     Sm &sm = *reinterpret_cast<Sm *>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
     const BlockRange br = a.ranges[blockIdx.x];
     const int nq = br.s1 - br.s0 + 1;
@@ -1853,18 +1865,22 @@ __global__ void __launch_bounds__(SOLVER_THREADS, 1)
 size_t solver_smem(SolverVariant v)
 {
     switch (v) {
-    case SV_FP64: return sizeof(SmemT<double, TILE_X>) + 128;
-    case SV_FP32_STREAM: return sizeof(SmemT<float, TILE_X_STREAM>) + 128;
-    default: return sizeof(SmemT<float, TILE_X>) + 128;
+    case SV_FP64: return sizeof(SmemT<double, GEO_TILE>) + 128;
+    case SV_FP32_STREAM: return sizeof(SmemT<float, GEO_STREAM>) + 128;
+    case SV_FP64_SHORT: return sizeof(SmemT<double, GEO_SHORT>) + 128;
+    case SV_FP32_SHORT: return sizeof(SmemT<float, GEO_SHORT>) + 128;
+    default: return sizeof(SmemT<float, GEO_TILE>) + 128;
     }
 }
 
 const void *solver_fn(SolverVariant v)
 {
     switch (v) {
-    case SV_FP64: return (const void *)solver_kernel<double, false>;
-    case SV_FP32_STREAM: return (const void *)solver_kernel<float, true>;
-    default: return (const void *)solver_kernel<float, false>;
+    case SV_FP64: return (const void *)solver_kernel<double, GEO_TILE>;
+    case SV_FP32_STREAM: return (const void *)solver_kernel<float, GEO_STREAM>;
+    case SV_FP64_SHORT: return (const void *)solver_kernel<double, GEO_SHORT>;
+    case SV_FP32_SHORT: return (const void *)solver_kernel<float, GEO_SHORT>;
+    default: return (const void *)solver_kernel<float, GEO_TILE>;
     }
 }
 
@@ -1877,12 +1893,11 @@ void set_solver_attributes()
 {
     static PerDevice pd;
     once_per_device(pd, [](int) {
-        return cudaFuncSetAttribute(solver_kernel<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)solver_smem(SV_FP64)) == cudaSuccess &&
-               cudaFuncSetAttribute(solver_kernel<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)solver_smem(SV_FP32_TILE)) == cudaSuccess &&
-               cudaFuncSetAttribute(solver_kernel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)solver_smem(SV_FP32_STREAM)) == cudaSuccess;
+        for (int v = 0; v < SV_COUNT; ++v)
+            if (cudaFuncSetAttribute(solver_fn((SolverVariant)v), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)solver_smem((SolverVariant)v)) != cudaSuccess)
+                return false;
+        return true;
     });
 }
 
@@ -1930,11 +1945,13 @@ ppe_status launch_solver_resume(const SolverArgs &a, SolverVariant v, int grid_b
 ppe_status encode_solver_maps(void *const r[2], void *const p[2], void *d, const float *ycoef, int nx, int ny,
                               int pitch, SolverVariant v, CUtensorMap out[NMAPS])
 {
-    const bool fp64 = v == SV_FP64, stream = v == SV_FP32_STREAM;
-    // tile-cooperative kernels: one tile window (136 x 20) and one tile (128 x 16);
-    // streaming kernel: chunks of SRB rows of a 132-wide window and of a 124-wide tile
-    const cuuint32_t win_w = stream ? S_WX : WIN_X, win_h = stream ? SRB : WIN_Y;
-    const cuuint32_t tile_w = stream ? TILE_X_STREAM : TILE_X, tile_h = stream ? SRB : TILE_Y;
+    const bool fp64 = solver_variant_fp64(v), stream = v == SV_FP32_STREAM;
+    // tile-cooperative kernels: one tile window (136 x (th + 4)) and one tile
+    // (128 x th); streaming kernel: chunks of SRB rows of a 132-wide window
+    // and of a 124-wide tile
+    const cuuint32_t th = (cuuint32_t)solver_tile_h(v);
+    const cuuint32_t win_w = stream ? S_WX : WIN_X, win_h = stream ? SRB : th + 2 * WIN_OY;
+    const cuuint32_t tile_w = stream ? TILE_X_STREAM : TILE_X, tile_h = stream ? SRB : th;
     auto encode = tensor_map_encoder();
     if (!encode) {
         set_error("cuTensorMapEncodeTiled unavailable");

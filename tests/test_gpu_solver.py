@@ -253,3 +253,46 @@ def test_solution_scales_exactly_with_the_source(api, prec):
         assert itk == it0, (k, itk, it0)
         assert np.array_equal(np.ldexp(xk, -k), x0), k
     grid.close()
+
+
+@pytest.mark.parametrize("tile_rows", [8, 16])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("key", ["c1", "r37x300", "r129x131", "r5x7", "r260x9"])
+def test_tile_heights(api, key, prec, tile_rows):
+    """Both tile heights of the tile-cooperative kernels (16 rows; 8 rows,
+    which small grids take by default to spread over twice the blocks) meet
+    the parity bars on ragged grids.  r37x300 has 19 or 38 tiles (300 rows
+    end in a tail of 12 or 4), so several blocks share the system; r5x7 fits
+    in part of one tile."""
+    _check(api, key, api.PPE_PREC_FP64 if prec == "fp64" else api.PPE_PREC_MIXED, tile_rows=tile_rows)
+
+
+@pytest.mark.parametrize("tile_rows", [8, 16])
+def test_tile_heights_c3(api, tile_rows):
+    """The 256x256 cylinder grid (32 or 64 tiles, one per block) with either
+    tile height reaches the same answer: iteration counts within a few and
+    solutions within the solution bar of each other and of the oracle."""
+    info = _check(api, "c3", api.PPE_PREC_MIXED, tile_rows=tile_rows)
+    ref = _check(api, "c3", api.PPE_PREC_MIXED, tile_rows=16)
+    assert abs(info["iters_pcg"] - ref["iters_pcg"]) <= 0.02 * ref["iters_pcg"] + 5, (info, ref)
+
+
+def test_batch_short_tiles(api):
+    """A batch of small systems on 8-row tiles: every system meets the
+    parity bars."""
+    keys = ["c1", "r37x300", "r129x131", "r260x9"]
+    grids, rhs, xs, refs = [], [], [], []
+    for k in keys:
+        w, xo = _ref(k)
+        grids.append(api.ppe_create_grid(w.dx, w.dy))
+        api.ppe_set_options(grids[-1], tile_rows=8)
+        rhs.append(_dev(w.f))
+        xs.append(torch.zeros_like(rhs[-1]))
+        refs.append((w, xo))
+    infos, st = api.ppe_solve_batch(grids, rhs, xs, RES_TOL, api.PPE_MODE_PCG, api.PPE_PREC_MIXED)
+    assert st == 0
+    for (w, xo), x, info in zip(refs, xs, infos):
+        xg = x.cpu().numpy()
+        assert info["status"] == 0
+        assert oracle.true_relres(w.dx, w.dy, w.f, xg) <= RES_TOL * 1.05
+        assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) <= SOL_TOL
