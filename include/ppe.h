@@ -153,9 +153,9 @@ typedef struct {
                                true residual, so its stall rule ends the FP32 iteration and
                                the solve continues in FP64 from the iterate
                                (ppe_solve_info.precision_fallback = 1)                      */
-    int32_t tile_rows;      /* rows of a tile-cooperative tile: 0 = by size (default: 8 when
-                               twice the grid's count of 16-row tiles fits on the SMs, so that
-                               a small grid spreads over twice the CTAs, else 16); 8 or 16 to
+    int32_t tile_rows;      /* rows of a tile-cooperative tile: 0 = by size (default: a small
+                               grid takes 8 or 4 rows, spreading over two or four times the
+                               CTAs, while the tiles fit one per SM; else 16); 4, 8 or 16 to
                                choose.  Any precision; same arithmetic, same results up to
                                rounding order.  Ignored by the streaming pass (16).          */
     int32_t reserved[2];

@@ -245,7 +245,7 @@ ppe_status ppe_create_grid(int nx, int ny, const double *dx, const double *dy, p
     }
     // tile counts of the tile shapes; workspaces are sized for the largest
     int ntiles = std::max(g->tiles_x, (nx + TILE_X_STREAM - 1) / TILE_X_STREAM) *
-                 ((ny + TILE_Y_SHORT - 1) / TILE_Y_SHORT);
+                 ((ny + TILE_Y_R4 - 1) / TILE_Y_R4);
     {
         ppe_status ls = launch_set_create(1, ntiles, ntiles + 1, &g->ls);
         if (ls != PPE_OK) return fail(ls);
@@ -277,7 +277,7 @@ ppe_status ppe_set_options(ppe_grid *g, const ppe_solve_opts *o)
         o->iter_pass < 0 || o->iter_pass > 2 || o->dlsm_stall_limit < 0 ||
         o->dlsm_cost_iters < 0 || o->spin_limit_ms < 0 || o->host_loop < 0 || o->host_loop > 1 ||
         o->debug_skip_block < 0 || o->preconditioner < 0 || o->preconditioner > 1 || o->debug_force_stall < 0 ||
-        (o->tile_rows != 0 && o->tile_rows != TILE_Y && o->tile_rows != TILE_Y_SHORT))
+        (o->tile_rows != 0 && o->tile_rows != TILE_Y && o->tile_rows != TILE_Y_R8 && o->tile_rows != TILE_Y_R4))
         return arg_error("ppe_set_options: option out of range");
     g->opts = *o;
     return PPE_OK;

@@ -239,10 +239,15 @@ void merge_fallback(ppe_solve_info &fp64, const ppe_solve_info &mixed)
 // tile-cooperative pass has the lower latency (512^2: 8.1 / 17.3 us).
 // ppe_autotune measures instead of guessing.
 //
-// ntiles counts 128x16 tiles.  When twice that many fit on the SMs, the
-// 128x8 tiles of the short-tile variants put one half-size tile on each of
-// twice the blocks: the per-block work of a step halves while the step's
-// synchronisation stays, which shortens an iteration on small grids.
+// ntiles counts 128x16 tiles.  Small grids take shorter tiles, one per
+// block on two or four times the blocks: the per-block work of a step
+// shrinks while its synchronisation grows with the number of records.
+// Measured on GB300 (us per iteration, 16 / 8 / 4 rows): 256^2 (32 tiles of
+// 16 rows) mixed 7.25 / 6.35 / 6.68, FP64 35.5 / 26.0 / 22.3; 64^2 (4 tiles)
+// mixed 7.38 / 6.68 / 6.26, FP64 35.4 / 25.8 / 21.5.  FP64 passes are long,
+// so FP64 takes the shortest tiles that still fit one per SM; FP32 takes 4
+// rows only while the blocks stay few (16 ntiles <= SMs), else 8 rows while
+// they fit (2 ntiles <= SMs).
 constexpr int STREAM_MIN_TILES = 448;
 SolverVariant pick_variant(ppe_precision prec, int iter_pass, int ntiles, int tile_rows)
 {
@@ -252,10 +257,19 @@ SolverVariant pick_variant(ppe_precision prec, int iter_pass, int ntiles, int ti
         cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
         return n;
     }();
-    const bool short_tiles = tile_rows ? tile_rows == TILE_Y_SHORT : 2 * ntiles <= sms;
-    if (prec == PPE_PREC_FP64) return short_tiles ? SV_FP64_SHORT : SV_FP64;
+    const bool fp64 = prec == PPE_PREC_FP64;
+    int rows = tile_rows;
+    if (!rows) {
+        if (fp64)
+            rows = 4 * ntiles <= sms ? TILE_Y_R4 : 2 * ntiles <= sms ? TILE_Y_R8 : TILE_Y;
+        else
+            rows = 16 * ntiles <= sms ? TILE_Y_R4 : 2 * ntiles <= sms ? TILE_Y_R8 : TILE_Y;
+    }
+    const SolverVariant v64 = rows == TILE_Y_R4 ? SV_FP64_R4 : rows == TILE_Y_R8 ? SV_FP64_R8 : SV_FP64;
+    const SolverVariant v32 = rows == TILE_Y_R4 ? SV_FP32_R4 : rows == TILE_Y_R8 ? SV_FP32_R8 : SV_FP32_TILE;
+    if (fp64) return v64;
     if (iter_pass == 2) return SV_FP32_STREAM;
-    if (iter_pass == 1 || ntiles < STREAM_MIN_TILES) return short_tiles ? SV_FP32_SHORT : SV_FP32_TILE;
+    if (iter_pass == 1 || ntiles < STREAM_MIN_TILES) return v32;
     return SV_FP32_STREAM;
 }
 

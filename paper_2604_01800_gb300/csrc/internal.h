@@ -58,7 +58,7 @@ constexpr int TILE_X = 128;                 // cells per tile row (4 per lane)
 constexpr int TILE_X_STREAM = 120;          // tile width of the streaming kernel: a warp row of
                                             // 128 cells covers it plus a four-cell halo per side
 constexpr int TILE_Y = 16;                  // rows per tile (one warp each)
-constexpr int TILE_Y_SHORT = 8;             // rows per tile of the short-tile variants (two warps each)
+constexpr int TILE_Y_R8 = 8, TILE_Y_R4 = 4; // rows per tile of the short-tile variants
 constexpr int SOLVER_THREADS = 32 * TILE_Y;
 constexpr int NPART = 6;                    // FP64 partial sums per tile
 constexpr int PITCH_ALIGN = 32;             // inner-vector row pitch (elements)
@@ -188,12 +188,18 @@ struct SolverArgs {
 
 // Solver kernel variants: FP64, FP32 with the tile-cooperative iteration
 // pass, FP32 with the streaming iteration pass.
-// The short-tile variants work on 128x8 tiles: a grid of few tiles spreads
-// over twice the blocks, each with half the work per step.
-enum SolverVariant : int { SV_FP64 = 0, SV_FP32_TILE = 1, SV_FP32_STREAM = 2, SV_FP64_SHORT = 3, SV_FP32_SHORT = 4 };
-constexpr int SV_COUNT = 5;
-inline bool solver_variant_fp64(SolverVariant v) { return v == SV_FP64 || v == SV_FP64_SHORT; }
-inline int solver_tile_h(SolverVariant v) { return v == SV_FP64_SHORT || v == SV_FP32_SHORT ? TILE_Y_SHORT : TILE_Y; }
+// The short-tile variants work on 128x8 or 128x4 tiles: a grid of few tiles
+// spreads over two or four times the blocks, each with less work per step.
+enum SolverVariant : int {
+    SV_FP64 = 0, SV_FP32_TILE = 1, SV_FP32_STREAM = 2,
+    SV_FP64_R8 = 3, SV_FP32_R8 = 4, SV_FP64_R4 = 5, SV_FP32_R4 = 6
+};
+constexpr int SV_COUNT = 7;
+inline bool solver_variant_fp64(SolverVariant v) { return v == SV_FP64 || v == SV_FP64_R8 || v == SV_FP64_R4; }
+inline int solver_tile_h(SolverVariant v)
+{
+    return v == SV_FP64_R8 || v == SV_FP32_R8 ? TILE_Y_R8 : v == SV_FP64_R4 || v == SV_FP32_R4 ? TILE_Y_R4 : TILE_Y;
+}
 inline int solver_tile_w(SolverVariant v) { return v == SV_FP32_STREAM ? TILE_X_STREAM : TILE_X; }
 
 ppe_status launch_solver_resume(const SolverArgs &a, SolverVariant v, int grid_blocks, cudaStream_t stream,

@@ -55,13 +55,13 @@ namespace ppe {
 
 namespace {
 
-// Geometry of a tile: TX columns (128 for the tile-cooperative kernels, 124
-// for the streaming kernel) and TY rows (16, or 8 for the short-tile kernels
-// that spread a small grid over twice the blocks), with its window (halo 4
+// Geometry of a tile: TX columns (128 for the tile-cooperative kernels, 120
+// for the streaming kernel) and TY rows (16, or 8 or 4 for the short-tile
+// kernels that spread a small grid over more blocks), with its window (halo 4
 // in x so that the window starts on a 16-byte boundary, halo 2 in y) and
 // one-cell ring.  The template key GK packs both: TX * 32 + TY.
 constexpr int geo_key(int tx, int ty) { return tx * 32 + ty; }
-constexpr int GEO_TILE = geo_key(TILE_X, TILE_Y), GEO_SHORT = geo_key(TILE_X, TILE_Y_SHORT),
+constexpr int GEO_TILE = geo_key(TILE_X, TILE_Y), GEO_R8 = geo_key(TILE_X, TILE_Y_R8), GEO_R4 = geo_key(TILE_X, TILE_Y_R4),
               GEO_STREAM = geo_key(TILE_X_STREAM, TILE_Y);
 template <int GK> struct Geo {
     static constexpr int TX = GK / 32, TY = GK % 32;
@@ -102,7 +102,8 @@ template <typename T, int GK> struct Stage {
     T d[Geo<GK>::TN];
 };
 static_assert((Geo<GEO_TILE>::WN_PAD * 4) % 128 == 0 && (Geo<GEO_TILE>::TN * 4) % 128 == 0 &&
-                  (Geo<GEO_SHORT>::WN_PAD * 4) % 128 == 0 && (Geo<GEO_SHORT>::TN * 4) % 128 == 0,
+                  (Geo<GEO_R8>::WN_PAD * 4) % 128 == 0 && (Geo<GEO_R8>::TN * 4) % 128 == 0 &&
+                  (Geo<GEO_R4>::WN_PAD * 4) % 128 == 0 && (Geo<GEO_R4>::TN * 4) % 128 == 0,
               "TMA destinations must stay 128-byte aligned");
 
 // The 1-D coefficient arrays of a tile's window as stored in global memory
@@ -1613,8 +1614,8 @@ __device__ void block_publish(S &sm, const Acc &acc, Slot *slot, uint32_t *count
     }
 }
 
-// GK selects the tile geometry: GEO_TILE and GEO_SHORT run the
-// tile-cooperative iteration pass on 128x16 or 128x8 tiles, GEO_STREAM
+// GK selects the tile geometry: GEO_TILE, GEO_R8 and GEO_R4 run the
+// tile-cooperative iteration pass on 128x16, 128x8 or 128x4 tiles, GEO_STREAM
 // (FP32 only) the streaming pass; their register needs allow one block per
 // SM.
 template <typename T, int GK_>
@@ -1867,8 +1868,10 @@ size_t solver_smem(SolverVariant v)
     switch (v) {
     case SV_FP64: return sizeof(SmemT<double, GEO_TILE>) + 128;
     case SV_FP32_STREAM: return sizeof(SmemT<float, GEO_STREAM>) + 128;
-    case SV_FP64_SHORT: return sizeof(SmemT<double, GEO_SHORT>) + 128;
-    case SV_FP32_SHORT: return sizeof(SmemT<float, GEO_SHORT>) + 128;
+    case SV_FP64_R8: return sizeof(SmemT<double, GEO_R8>) + 128;
+    case SV_FP32_R8: return sizeof(SmemT<float, GEO_R8>) + 128;
+    case SV_FP64_R4: return sizeof(SmemT<double, GEO_R4>) + 128;
+    case SV_FP32_R4: return sizeof(SmemT<float, GEO_R4>) + 128;
     default: return sizeof(SmemT<float, GEO_TILE>) + 128;
     }
 }
@@ -1878,8 +1881,10 @@ const void *solver_fn(SolverVariant v)
     switch (v) {
     case SV_FP64: return (const void *)solver_kernel<double, GEO_TILE>;
     case SV_FP32_STREAM: return (const void *)solver_kernel<float, GEO_STREAM>;
-    case SV_FP64_SHORT: return (const void *)solver_kernel<double, GEO_SHORT>;
-    case SV_FP32_SHORT: return (const void *)solver_kernel<float, GEO_SHORT>;
+    case SV_FP64_R8: return (const void *)solver_kernel<double, GEO_R8>;
+    case SV_FP32_R8: return (const void *)solver_kernel<float, GEO_R8>;
+    case SV_FP64_R4: return (const void *)solver_kernel<double, GEO_R4>;
+    case SV_FP32_R4: return (const void *)solver_kernel<float, GEO_R4>;
     default: return (const void *)solver_kernel<float, GEO_TILE>;
     }
 }

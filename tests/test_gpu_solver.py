@@ -255,37 +255,38 @@ def test_solution_scales_exactly_with_the_source(api, prec):
     grid.close()
 
 
-@pytest.mark.parametrize("tile_rows", [8, 16])
+@pytest.mark.parametrize("tile_rows", [4, 8, 16])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("key", ["c1", "r37x300", "r129x131", "r5x7", "r260x9"])
 def test_tile_heights(api, key, prec, tile_rows):
-    """Both tile heights of the tile-cooperative kernels (16 rows; 8 rows,
-    which small grids take by default to spread over twice the blocks) meet
-    the parity bars on ragged grids.  r37x300 has 19 or 38 tiles (300 rows
-    end in a tail of 12 or 4), so several blocks share the system; r5x7 fits
-    in part of one tile."""
+    """Every tile height of the tile-cooperative kernels (16 rows; 8 or 4
+    rows, which small grids take by default to spread over more blocks)
+    meets the parity bars on ragged grids.  r37x300 has 19, 38 or 75 tiles
+    (300 rows end in a tail of 12, 4 or a whole tile), so several blocks
+    share the system; r5x7 fits in part of one tile."""
     _check(api, key, api.PPE_PREC_FP64 if prec == "fp64" else api.PPE_PREC_MIXED, tile_rows=tile_rows)
 
 
-@pytest.mark.parametrize("tile_rows", [8, 16])
+@pytest.mark.parametrize("tile_rows", [4, 8])
 def test_tile_heights_c3(api, tile_rows):
-    """The 256x256 cylinder grid (32 or 64 tiles, one per block) with either
-    tile height reaches the same answer: iteration counts within a few and
+    """The 256x256 cylinder grid (128 or 64 tiles, one per block) with a
+    short tile height reaches the same answer as with 16 rows: iteration counts within a few and
     solutions within the solution bar of each other and of the oracle."""
     info = _check(api, "c3", api.PPE_PREC_MIXED, tile_rows=tile_rows)
     ref = _check(api, "c3", api.PPE_PREC_MIXED, tile_rows=16)
     assert abs(info["iters_pcg"] - ref["iters_pcg"]) <= 0.02 * ref["iters_pcg"] + 5, (info, ref)
 
 
-def test_batch_short_tiles(api):
-    """A batch of small systems on 8-row tiles: every system meets the
+@pytest.mark.parametrize("tile_rows", [4, 8])
+def test_batch_short_tiles(api, tile_rows):
+    """A batch of small systems on short tiles: every system meets the
     parity bars."""
     keys = ["c1", "r37x300", "r129x131", "r260x9"]
     grids, rhs, xs, refs = [], [], [], []
     for k in keys:
         w, xo = _ref(k)
         grids.append(api.ppe_create_grid(w.dx, w.dy))
-        api.ppe_set_options(grids[-1], tile_rows=8)
+        api.ppe_set_options(grids[-1], tile_rows=tile_rows)
         rhs.append(_dev(w.f))
         xs.append(torch.zeros_like(rhs[-1]))
         refs.append((w, xo))
