@@ -43,7 +43,7 @@ CONV_WEIGHTS = os.path.join(ROOT, "paper_2604_01800_gb300", "weights", "hydea_co
 TOL = 1e-8
 L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2
 SOURCES = 5                         # distinct sources of the headline workload, cycled over the steps
-SOLVER_C3_DRAM_BYTES = 1.284e6      # ncu: DRAM bytes (read + write) of one solver launch = one c3 solve
+SOLVER_C3_DRAM_BYTES = 1.2475e6      # ncu: DRAM bytes (read + write) of one solver launch = one c3 solve
 
 
 def _args():
@@ -325,7 +325,7 @@ def run_native(args):
             "frac": achieved / peaks["hbm_gbs"], "traffic": SOLVER_C3_DRAM_BYTES,
             "traffic_source": "dram__bytes_read.sum + dram__bytes_write.sum of one whole plain-PCG solve of this "
                               "grid (one launch of the same kernel; profiles/solver_kernel_pcg_c3.md), per solve",
-            "kernel": "solver_kernel<float, tile>", "peak_source": f"hbm_gbs ({peak_src})",
+            "kernel": "solver_kernel<float, 128x8 tiles>", "peak_source": f"hbm_gbs ({peak_src})",
             "units": "24 B/cell per PCG iteration and FP64 pass, 20 B/cell per DLSM update, per solve",
             "note": "working set (~3 MB) is L2-resident: barrier/latency-bound, not HBM-bound"}
     kernels = int(sum(_kernels_of(i, levels) for i in info_h))

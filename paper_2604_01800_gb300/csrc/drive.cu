@@ -459,8 +459,9 @@ ppe_status drive_host(int n, ppe_grid *const *grids, LaunchSet &ls, int blocks, 
                      "wait %.2f, gather %.2f, advance %.2f (state machine %.2f)\n", blocks, pr[7], pr[0] / st_,
                      pr[1] / st_, pr[2] / st_, pr[3] / st_, pr[4] / st_, pr[5] / st_);
         std::fprintf(stderr, "[solver profile] iteration passes=%llu  per pass (us): to the data wait %.2f, data wait "
-                     "%.2f, window stage %.2f, ring stage %.2f, tile stage and sums %.2f\n", pr[13], pr[8] / si_,
-                     pr[9] / si_, pr[10] / si_, pr[11] / si_, pr[12] / si_);
+                     "%.2f, window stage %.2f, ring stage %.2f, tile stage and sums %.2f (to the pass %.2f, "
+                     "issuing its loads %.2f)\n", pr[13], pr[8] / si_, pr[9] / si_, pr[10] / si_, pr[11] / si_,
+                     pr[12] / si_, pr[14] / si_, pr[15] / si_);
         cudaFree(a.prof);
     }
     float ms = 0.f;

@@ -183,7 +183,7 @@ struct SolverArgs {
     int64_t spin_limit_ns;
     int32_t max_steps;         // > 0: every block leaves after this many steps (the host may re-plan)
     int32_t skip_block;        // test hook: block skip_block - 1 withholds its record at step 2 (0: off)
-    unsigned long long *prof;  // nullable, 16 words: block 0's ns per step part [0..5], step count [7], iteration-pass parts [8..12] and their count [13]
+    unsigned long long *prof;  // nullable, 16 words: block 0's ns per step part [0..5], step count [7], iteration-pass parts [8..12], their count [13], pass entry and load issue [14..15]
 };
 
 // Solver kernel variants: FP64, FP32 with the tile-cooperative iteration

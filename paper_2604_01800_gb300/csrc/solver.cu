@@ -164,8 +164,10 @@ template <typename T, int GK_> struct SmemT {
     // nonzero: another pass has written its scratch windows over the TMA
     // stages since the tile pass last took the full proxy fence
     uint32_t udirty;
-    uint64_t ptime[4];      // step profile (block 0): iteration pass before and after its data wait, after two stages
-    unsigned long long pacc[14];   // step profile (block 0): accumulated ns, written to SolverArgs::prof at the end
+    // step profile (block 0): iteration pass before and after its data wait,
+    // after two stages, at its entry and after its loads are issued
+    uint64_t ptime[6];
+    unsigned long long pacc[16];   // step profile (block 0): accumulated ns, written to SolverArgs::prof at the end
 };
 
 // Dynamic shared memory of a block (plus 128 bytes of alignment slack): one
@@ -728,7 +730,10 @@ __device__ void pass_iter(S &sm, int q, int t_lo, int t_hi, Acc &acc, const Solv
     const int n = t_hi - t_lo;
     if (n <= 0) return;
     const uint32_t fill0 = sm.fills;
+    const bool prof0 = a.prof && blockIdx.x == 0 && threadIdx.x == 0 && q == 0;
+    if (prof0) sm.ptime[4] = gtimer();
     if (threadIdx.x == 0) iter_issue<T>(sm, sd, st, t_lo, fill0, true);
+    if (prof0) sm.ptime[5] = gtimer();
     T *rout = (T *)sd.r[st.cur ^ 1];
     T *pout = (T *)sd.p[st.pcur ^ 1];
     T *dv = (T *)sd.d;
@@ -1646,7 +1651,7 @@ __global__ void __launch_bounds__(SOLVER_THREADS, 1)
         sm.fills = 0;
         sm.udirty = 1;
         sm.ptime[0] = 0;
-        for (int k = 0; k < 14; ++k) sm.pacc[k] = 0;
+        for (int k = 0; k < 16; ++k) sm.pacc[k] = 0;
         mbar_init(smem_u32(&sm.bar[0]), 1);
         mbar_init(smem_u32(&sm.bar[1]), 1);
         if constexpr (STREAM) {
@@ -1840,6 +1845,8 @@ __global__ void __launch_bounds__(SOLVER_THREADS, 1)
                     pa[11] += sm.ptime[3] - sm.ptime[2];
                     pa[12] += t_p - sm.ptime[3];
                     pa[13] += 1;
+                    pa[14] += sm.ptime[4] - t_a;
+                    pa[15] += sm.ptime[5] - sm.ptime[4];
                 }
             }
             sm.ptime[0] = 0;
@@ -1848,7 +1855,7 @@ __global__ void __launch_bounds__(SOLVER_THREADS, 1)
         }
     }
     if (prof)
-        for (int k = 0; k < 14; ++k) a.prof[k] += sm.pacc[k];
+        for (int k = 0; k < 16; ++k) a.prof[k] += sm.pacc[k];
     // a system that waits for a network direction starts its network clock
     if (threadIdx.x == 0)
         for (int q = 0; q < nq; ++q)
