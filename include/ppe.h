@@ -412,6 +412,21 @@ PPE_API ppe_status ppe_debug_conv3x3(const void *in_bf16, const void *w_bf16, co
 PPE_API ppe_status ppe_debug_wgrad(const void *dZ_bf16, const void *X_bf16, int B, int H, int W, int cin, int cout,
                                    float *dW, int impl, void *stream);
 
+/* Test hook: one GEMM of the DeepONet trunk (Sec. 2.4; the trunk's layers
+ * and their backward), FP32 in and out:
+ *   C[m][n] = act(sum_k A(m, k) B(k, n) + bias[m]) (+ C[m][n] if accumulate)
+ * with A(m, k) = transA ? A[k*lda + m] : A[m*lda + k], B(k, n) = transB ?
+ * B[n*ldb + k] : B[k*ldb + n], C[m*ldc + n], act 0 (identity) or 1 (tanh),
+ * bias nullable [M].  impl 0: the tensor-core (tcgen05, TF32 operands) form
+ * when the shape is one of the trunk's (N >= 1024 pixels with M, K <= 256
+ * and !transB; or K >= 4096 pixels, !transA, transB, 16 <= N <= 256, no bias
+ * and act 0), else the CUDA-core kernel; 1: always the CUDA-core kernel.
+ * *form (nullable) receives 1 or 2 for the tensor-core forms, 0 for the
+ * CUDA cores.  All array pointers are device pointers. */
+PPE_API ppe_status ppe_debug_gemm(int M, int N, int K, const float *A, int lda, int transA, const float *B, int ldb,
+                                  int transB, float *C, int ldc, const float *bias, int act, int accumulate, int impl,
+                                  int *form, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -116,6 +116,9 @@ _SIGS = [
     ("ppe_debug_mg_vcycle", ctypes.c_int, [_P, _P, _P, _P]),
     ("ppe_debug_wgrad", ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P,
                                        ctypes.c_int, _P]),
+    ("ppe_debug_gemm", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int, _P,
+                                      ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_int, _P, _P]),
     ("ppe_source", ctypes.c_int, [_P, _P, _P, ctypes.c_double, _P, _P]),
     ("ppe_project", ctypes.c_int, [_P, _P, ctypes.c_double, _P, _P, _P, _P]),
     ("ppe_last_error", ctypes.c_char_p, []),

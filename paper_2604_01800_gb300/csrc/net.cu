@@ -362,16 +362,16 @@ ppe_status refresh_cache(ppe_net *n, NetCache *c, const float *P, cudaStream_t s
     }
     const int Pn = c->H * c->W;
     float *t1 = c->trunk, *t2 = t1 + (size_t)cf.trunk_hidden[0] * Pn, *t3 = t2 + (size_t)cf.trunk_hidden[1] * Pn;
-    PPE_TRY(sgemm(cf.trunk_hidden[0], Pn, 2, P + n->off_tw[0], 2, false, c->xy, Pn, false, t1, Pn, P + n->off_tb[0], 1,
+    PPE_TRY(tgemm(cf.trunk_hidden[0], Pn, 2, P + n->off_tw[0], 2, false, c->xy, Pn, false, t1, Pn, P + n->off_tb[0], 1,
                   false, s));
-    PPE_TRY(sgemm(cf.trunk_hidden[1], Pn, cf.trunk_hidden[0], P + n->off_tw[1], cf.trunk_hidden[0], false, t1, Pn,
+    PPE_TRY(tgemm(cf.trunk_hidden[1], Pn, cf.trunk_hidden[0], P + n->off_tw[1], cf.trunk_hidden[0], false, t1, Pn,
                   false, t2, Pn, P + n->off_tb[1], 1, false, s));
-    PPE_TRY(sgemm(cf.c_last, Pn, cf.trunk_hidden[1], P + n->off_tw[2], cf.trunk_hidden[1], false, t2, Pn, false, t3,
+    PPE_TRY(tgemm(cf.c_last, Pn, cf.trunk_hidden[1], P + n->off_tw[2], cf.trunk_hidden[1], false, t2, Pn, false, t3,
                   Pn, P + n->off_tb[2], 0, false, s));
     // weff[c0][p] = sum_c head.w[c][c0] t3[c][p];  ceff[p] = sum_c head.b[c] t3[c][p] + out.b
-    PPE_TRY(sgemm(cf.widths[0], Pn, cf.c_last, P + n->off_head_w, cf.widths[0], true, t3, Pn, false, c->weff, Pn,
+    PPE_TRY(tgemm(cf.widths[0], Pn, cf.c_last, P + n->off_head_w, cf.widths[0], true, t3, Pn, false, c->weff, Pn,
                   nullptr, 0, false, s));
-    PPE_TRY(sgemm(1, Pn, cf.c_last, P + n->off_head_b, cf.c_last, false, t3, Pn, false, c->ceff, Pn,
+    PPE_TRY(tgemm(1, Pn, cf.c_last, P + n->off_head_b, cf.c_last, false, t3, Pn, false, c->ceff, Pn,
                   P + n->off_out_b, 0, false, s));
     c->version = want;
     c->src = P;

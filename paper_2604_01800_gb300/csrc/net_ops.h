@@ -26,6 +26,15 @@ ppe_status eta_layer(const float *delta, int HW, const float *w1, const float *b
                      int hid, int mesh, float *eta, float *phi_out, cudaStream_t s);
 ppe_status sgemm(int M, int N, int K, const float *A, int lda, bool transA, const float *B, int ldb, bool transB,
                  float *C, int ldc, const float *bias, int act, bool accumulate, cudaStream_t s);
+// The same on the tensor cores (kind::tf32) where the shape is one of the
+// trunk's two forms (pixels as the long N or K dimension); the CUDA-core
+// sgemm otherwise.  tgemm_form reports the form (1 pixel GEMM, 2 reduction
+// GEMM, 0 CUDA cores); tgemm_error the device's bounded-wait flag.
+int tgemm_form(int M, int N, int K, const float *A, int lda, bool transA, const float *B, int ldb, bool transB,
+               const float *bias, int act);
+ppe_status tgemm(int M, int N, int K, const float *A, int lda, bool transA, const float *B, int ldb, bool transB,
+                 float *C, int ldc, const float *bias, int act, bool accumulate, cudaStream_t s);
+int tgemm_error();
 ppe_status fold_out(const bf16 *Y, const float *weff, const float *ceff, int B, int H, int W, int C, float *e,
                     int e_pitch, size_t e_bstride, int nx, int ny, cudaStream_t s);
 ppe_status pack_conv_weights(const float *W, bf16 *Wp, bf16 *Wt, int cout, int cin, cudaStream_t s);

@@ -714,21 +714,21 @@ static ppe_status net_backward(ppe_net *n, NetCache *c, TrainWs *w, ppe_grid *g,
     // head + trunk: weff = head.w^T t3, ceff = head.b . t3 + out.b, t3 = T2 t2 + b2, t2 = tanh(T1 t1 + b1), ...
     float *t1 = c->trunk, *t2 = t1 + (size_t)cf.trunk_hidden[0] * Pn, *t3 = t2 + (size_t)cf.trunk_hidden[1] * Pn;
     const int h0 = cf.trunk_hidden[0], h1 = cf.trunk_hidden[1], cl = cf.c_last;
-    PPE_TRY(sgemm(cl, C0, Pn, t3, Pn, false, w->dweff, Pn, true, grads + n->off_head_w, C0, nullptr, 0, false, s));
-    PPE_TRY(sgemm(cl, 1, Pn, t3, Pn, false, w->dceff, 1, false, grads + n->off_head_b, 1, nullptr, 0, false, s));
-    PPE_TRY(sgemm(1, 1, Pn, w->dceff, Pn, false, w->ones, 1, false, grads + n->off_out_b, 1, nullptr, 0, false, s));
-    PPE_TRY(sgemm(cl, Pn, C0, P + n->off_head_w, C0, false, w->dweff, Pn, false, w->dt3, Pn, nullptr, 0, false, s));
-    PPE_TRY(sgemm(cl, Pn, 1, P + n->off_head_b, 1, false, w->dceff, Pn, false, w->dt3, Pn, nullptr, 0, true, s));
-    PPE_TRY(sgemm(cl, h1, Pn, w->dt3, Pn, false, t2, Pn, true, grads + n->off_tw[2], h1, nullptr, 0, false, s));
-    PPE_TRY(sgemm(cl, 1, Pn, w->dt3, Pn, false, w->ones, 1, false, grads + n->off_tb[2], 1, nullptr, 0, false, s));
-    PPE_TRY(sgemm(h1, Pn, cl, P + n->off_tw[2], h1, true, w->dt3, Pn, false, w->dt2, Pn, nullptr, 0, false, s));
+    PPE_TRY(tgemm(cl, C0, Pn, t3, Pn, false, w->dweff, Pn, true, grads + n->off_head_w, C0, nullptr, 0, false, s));
+    PPE_TRY(tgemm(cl, 1, Pn, t3, Pn, false, w->dceff, 1, false, grads + n->off_head_b, 1, nullptr, 0, false, s));
+    PPE_TRY(tgemm(1, 1, Pn, w->dceff, Pn, false, w->ones, 1, false, grads + n->off_out_b, 1, nullptr, 0, false, s));
+    PPE_TRY(tgemm(cl, Pn, C0, P + n->off_head_w, C0, false, w->dweff, Pn, false, w->dt3, Pn, nullptr, 0, false, s));
+    PPE_TRY(tgemm(cl, Pn, 1, P + n->off_head_b, 1, false, w->dceff, Pn, false, w->dt3, Pn, nullptr, 0, true, s));
+    PPE_TRY(tgemm(cl, h1, Pn, w->dt3, Pn, false, t2, Pn, true, grads + n->off_tw[2], h1, nullptr, 0, false, s));
+    PPE_TRY(tgemm(cl, 1, Pn, w->dt3, Pn, false, w->ones, 1, false, grads + n->off_tb[2], 1, nullptr, 0, false, s));
+    PPE_TRY(tgemm(h1, Pn, cl, P + n->off_tw[2], h1, true, w->dt3, Pn, false, w->dt2, Pn, nullptr, 0, false, s));
     tanh_bwd_kernel<<<g1d((size_t)h1 * Pn), 256, 0, s>>>(w->dt2, t2, w->dz, (size_t)h1 * Pn);
-    PPE_TRY(sgemm(h1, h0, Pn, w->dz, Pn, false, t1, Pn, true, grads + n->off_tw[1], h0, nullptr, 0, false, s));
-    PPE_TRY(sgemm(h1, 1, Pn, w->dz, Pn, false, w->ones, 1, false, grads + n->off_tb[1], 1, nullptr, 0, false, s));
-    PPE_TRY(sgemm(h0, Pn, h1, P + n->off_tw[1], h0, true, w->dz, Pn, false, w->dt1, Pn, nullptr, 0, false, s));
+    PPE_TRY(tgemm(h1, h0, Pn, w->dz, Pn, false, t1, Pn, true, grads + n->off_tw[1], h0, nullptr, 0, false, s));
+    PPE_TRY(tgemm(h1, 1, Pn, w->dz, Pn, false, w->ones, 1, false, grads + n->off_tb[1], 1, nullptr, 0, false, s));
+    PPE_TRY(tgemm(h0, Pn, h1, P + n->off_tw[1], h0, true, w->dz, Pn, false, w->dt1, Pn, nullptr, 0, false, s));
     tanh_bwd_kernel<<<g1d((size_t)h0 * Pn), 256, 0, s>>>(w->dt1, t1, w->dz, (size_t)h0 * Pn);
-    PPE_TRY(sgemm(h0, 2, Pn, w->dz, Pn, false, c->xy, Pn, true, grads + n->off_tw[0], 2, nullptr, 0, false, s));
-    PPE_TRY(sgemm(h0, 1, Pn, w->dz, Pn, false, w->ones, 1, false, grads + n->off_tb[0], 1, nullptr, 0, false, s));
+    PPE_TRY(tgemm(h0, 2, Pn, w->dz, Pn, false, c->xy, Pn, true, grads + n->off_tw[0], 2, nullptr, 0, false, s));
+    PPE_TRY(tgemm(h0, 1, Pn, w->dz, Pn, false, w->ones, 1, false, grads + n->off_tb[0], 1, nullptr, 0, false, s));
 
     // decoder, level 0 upward
     for (int k = 0; k <= L - 2; ++k) {
@@ -809,6 +809,24 @@ extern "C" ppe_status ppe_debug_wgrad(const void *dZ, const void *X, int B, int 
     const ppe::bf16 *z = (const ppe::bf16 *)dZ, *x = (const ppe::bf16 *)X;
     if (impl == 0) return ppe::wgrad_tc(z, x, B, H, W, cin, cout, dW, (cudaStream_t)stream);
     return ppe::wgrad_simt(z, x, B, H, W, cin, cout, dW, (cudaStream_t)stream);
+}
+
+extern "C" ppe_status ppe_debug_gemm(int M, int N, int K, const float *A, int lda, int transA, const float *B, int ldb,
+                                     int transB, float *C, int ldc, const float *bias, int act, int accumulate, int impl,
+                                     int *form, void *stream)
+{
+    ppe::clear_error();
+    if (!A || !B || !C || M < 1 || N < 1 || K < 1 || lda < 1 || ldb < 1 || ldc < N || (act != 0 && act != 1)) {
+        ppe::set_error("ppe_debug_gemm: bad arguments");
+        return PPE_ERR_ARG;
+    }
+    const int f = impl == 0 ? ppe::tgemm_form(M, N, K, A, lda, transA != 0, B, ldb, transB != 0, bias, act) : 0;
+    if (form) *form = f;
+    if (impl == 0)
+        return ppe::tgemm(M, N, K, A, lda, transA != 0, B, ldb, transB != 0, C, ldc, bias, act, accumulate != 0,
+                          (cudaStream_t)stream);
+    return ppe::sgemm(M, N, K, A, lda, transA != 0, B, ldb, transB != 0, C, ldc, bias, act, accumulate != 0,
+                      (cudaStream_t)stream);
 }
 
 

@@ -1465,28 +1465,24 @@ __device__ __forceinline__ void ff_mul(float &h, float &l, float b)
 // products) and keeps the FP64 state fields in step for the other phases.
 __device__ void advance_iter_f32(const SysDesc &sd, SysState &s, const float (&h)[NPART], const float (&l)[NPART])
 {
-    s.e_cg += s.alpha_f * s.gamma_f;        // energy removed by the step the pass took (see PH_ITER)
-    s.e_cg_n++;
-    s.it_pcg++;
-    s.it_total++;
-    s.cur ^= 1;
-    s.pcur ^= 1;
-    s.first = 0;
-    s.cg_count++;
-    const float mu = (h[3] + l[3]) * sd.inv_n_f;
-    const float rr = (h[2] + l[2]) - sd.n_cells_f * mu * mu;
+    // Every field the transition reads is loaded first and every result
+    // stored last: the state lives in shared memory, and interleaved
+    // read-modify-writes would each wait for the previous store.
+    const float alpha0 = s.alpha_f, gamma0 = s.gamma_f, ru_sq = s.ru_sq_f, target_sq = s.target_sq_f;
+    const float e_cg = s.e_cg;
+    const int e_cg_n = s.e_cg_n, it_pcg = s.it_pcg, it_total = s.it_total + 1, cg_count = s.cg_count + 1;
+    const int cur = s.cur, pcur = s.pcur, it_rep = s.it_rep + 1, it_rep_prev = s.it_rep_prev;
+    int fell_back = s.fell_back;
+    const float inv_n = sd.inv_n_f, n_cells = sd.n_cells_f;
+    const bool hybrid = sd.mode == PPE_MODE_HYBRID;
+    const int budget = sd.hybrid_budget, num_cg = sd.num_cg, cap = iter_cap(sd);
+
+    const float mu = (h[3] + l[3]) * inv_n;
+    const float rr = (h[2] + l[2]) - n_cells * mu * mu;
     const float rho = nonneg(rr);
-    s.mu_f = mu;
-    s.rho_f = rho;
-    s.mu = (double)mu;
-    s.rho = (double)rho;
-    if (sd.mode == PPE_MODE_HYBRID && !s.fell_back && s.it_total >= sd.hybrid_budget) s.fell_back = 1;
-    if (!isfinite(rho)) {
-        to_res(s, 0);
-        return;
-    }
+    if (hybrid && !fell_back && it_total >= budget) fell_back = 1;
     const float gnew = h[0] + l[0];
-    const float beta = __fdiv_rn(gnew, s.gamma_f);
+    const float beta = __fdiv_rn(gnew, gamma0);
     // p'.A p' = u'.Au' + beta (2 u'.(Ap) + beta p.(Ap)), in float-float
     float wh = h[5], wl = l[5];
     ff_mul(wh, wl, beta);
@@ -1498,10 +1494,29 @@ __device__ void advance_iter_f32(const SysDesc &sd, SysState &s, const float (&h
     // an inner solve that runs far past the length of the previous one
     // (2000 + 4x) ends with a residual replacement, so a stalled FP32
     // iteration is noticed by the refinement's stall test
-    s.it_rep++;
-    const bool overrun = s.it_rep > 2000 + 4 * s.it_rep_prev;
-    s.overran = overrun && !(rho <= s.ru_sq_f);
-    if (rho <= s.target_sq_f || s.it_total >= iter_cap(sd) || !ok || rho <= s.ru_sq_f || overrun) {
+    const bool overrun = it_rep > 2000 + 4 * it_rep_prev;
+
+    // the step the pass took removed alpha gamma of the error's A-norm energy
+    s.e_cg = e_cg + alpha0 * gamma0;
+    s.e_cg_n = e_cg_n + 1;
+    s.it_pcg = it_pcg + 1;
+    s.it_total = it_total;
+    s.cur = cur ^ 1;
+    s.pcur = pcur ^ 1;
+    s.first = 0;
+    s.cg_count = cg_count;
+    s.mu_f = mu;
+    s.rho_f = rho;
+    s.mu = (double)mu;
+    s.rho = (double)rho;
+    s.fell_back = fell_back;
+    if (!isfinite(rho)) {
+        to_res(s, 0);
+        return;
+    }
+    s.it_rep = it_rep;
+    s.overran = overrun && !(rho <= ru_sq);
+    if (rho <= target_sq || it_total >= cap || !ok || rho <= ru_sq || overrun) {
         // gamma and alpha of the direction in use stay the reference for the
         // continuation after the residual replacement
         to_res(s, ok ? 1 : 0);
@@ -1514,7 +1529,7 @@ __device__ void advance_iter_f32(const SysDesc &sd, SysState &s, const float (&h
     s.beta = (double)beta;
     s.alpha = (double)alpha;
     s.gamma = (double)gnew;
-    if (sd.mode == PPE_MODE_HYBRID && !s.fell_back && s.cg_count >= sd.num_cg) {
+    if (hybrid && !fell_back && cg_count >= num_cg) {
         s.dlsm_count = 0;
         s.phase = PH_NET;
     } else {
