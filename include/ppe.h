@@ -420,9 +420,11 @@ PPE_API ppe_status ppe_debug_wgrad(const void *dZ_bf16, const void *X_bf16, int 
  * bias nullable [M].  impl 0: the tensor-core (tcgen05, TF32 operands) form
  * when the shape is one of the trunk's (N >= 1024 pixels with M, K <= 256
  * and !transB; or K >= 4096 pixels, !transA, transB, 16 <= N <= 256, no bias
- * and act 0), else the CUDA-core kernel; 1: always the CUDA-core kernel.
- * *form (nullable) receives 1 or 2 for the tensor-core forms, 0 for the
- * CUDA cores.  All array pointers are device pointers. */
+ * and act 0), the thin forms on the CUDA cores where they apply (3: N <= 4
+ * with K >= 1024, !transA, no bias, act 0; 4: K <= 4 with N >= 1024,
+ * !transB), else the general CUDA-core kernel; 1: always the general
+ * CUDA-core kernel.  *form (nullable) receives the form used (1-4, 0 the
+ * general kernel).  All array pointers are device pointers. */
 PPE_API ppe_status ppe_debug_gemm(int M, int N, int K, const float *A, int lda, int transA, const float *B, int ldb,
                                   int transB, float *C, int ldc, const float *bias, int act, int accumulate, int impl,
                                   int *form, void *stream);

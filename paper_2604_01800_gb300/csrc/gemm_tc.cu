@@ -505,8 +505,77 @@ constexpr int round_up_i(int v, int m) { return (v + m - 1) / m * m; }
 
 }  // namespace
 
-// Shape test of the two tensor-core forms (the arguments of sgemm).
-// 1: pixel GEMM, 2: reduction GEMM, 0: neither (the CUDA-core path).
+// Thin forms of the same product, memory-bound on the CUDA cores.
+// Row dot: C[m][n] (+)= sum_p A[m][p] B(p, n) for N <= 4 (the bias gradients,
+// B a vector of ones or the loss's gradient, and the first trunk layer's
+// weight gradient, B the 2 coordinates).  One block per row, 16-byte loads,
+// a fixed reduction order.
+__global__ void __launch_bounds__(256) gemm_rowdot_kernel(int N, int K, const float *__restrict__ A, int lda,
+                                                         const float *__restrict__ B, int ldb, int transB,
+                                                         float *C, int ldc, int accumulate)
+{
+    __shared__ float red[4][8];
+    const int m = blockIdx.x;
+    const float *a = A + (size_t)m * lda;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    const bool vec = ((lda | (transB ? ldb : 4)) & 3) == 0 && ((uintptr_t)A & 15) == 0 &&
+                     (!transB || ((uintptr_t)B & 15) == 0);
+    const int kv = vec ? K / 4 * 4 : 0;
+    for (int k = 4 * threadIdx.x; k < kv; k += 4 * blockDim.x) {
+        const float4 x = __ldg(reinterpret_cast<const float4 *>(a + k));
+        for (int n = 0; n < N; ++n) {
+            float b0, b1, b2, b3;
+            if (transB) {
+                const float4 y = __ldg(reinterpret_cast<const float4 *>(B + (size_t)n * ldb + k));
+                b0 = y.x; b1 = y.y; b2 = y.z; b3 = y.w;
+            } else {
+                b0 = __ldg(B + (size_t)k * ldb + n); b1 = __ldg(B + (size_t)(k + 1) * ldb + n);
+                b2 = __ldg(B + (size_t)(k + 2) * ldb + n); b3 = __ldg(B + (size_t)(k + 3) * ldb + n);
+            }
+            acc[n] += x.x * b0 + x.y * b1 + x.z * b2 + x.w * b3;
+        }
+    }
+    for (int k = kv + threadIdx.x; k < K; k += blockDim.x)
+        for (int n = 0; n < N; ++n) acc[n] += a[k] * (transB ? B[(size_t)n * ldb + k] : B[(size_t)k * ldb + n]);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int n = 0; n < N; ++n) {
+        float v = acc[n];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[n][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < N) {
+        float v = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[threadIdx.x][w];
+        float *c = C + (size_t)m * ldc + threadIdx.x;
+        *c = accumulate ? *c + v : v;
+    }
+}
+
+// Small K: C[m][p] = act(sum_{k < K} W(m, k) X[k][p] + bias[m]) (+ C) for
+// K <= 4 (the first trunk layer on the 2 coordinates; the head bias's
+// rank-one term of the data gradient).  One thread per output, consecutive
+// threads on consecutive pixels.
+__global__ void __launch_bounds__(256) gemm_smallk_kernel(int M, int P, int K, const float *__restrict__ W, int ldw,
+                                                         int transW, const float *__restrict__ X, int ldx,
+                                                         const float *__restrict__ bias, float *C, int ldc, int act,
+                                                         int accumulate)
+{
+    const size_t total = (size_t)M * P;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int m = (int)(i / P), p = (int)(i - (size_t)m * P);
+        float y = bias ? __ldg(bias + m) : 0.f;
+        for (int k = 0; k < K; ++k)
+            y += __ldg(transW ? W + (size_t)k * ldw + m : W + (size_t)m * ldw + k) * __ldg(X + (size_t)k * ldx + p);
+        if (act == 1) y = tanhf(y);
+        float *c = C + (size_t)m * ldc + p;
+        *c = accumulate ? *c + y : y;
+    }
+}
+
+// Shape test of the forms (the arguments of sgemm): 1 pixel GEMM and 2
+// reduction GEMM (tensor cores), 3 row dot and 4 small K (CUDA cores,
+// memory-bound), 0 the general CUDA-core kernel.
 int tgemm_form(int M, int N, int K, const float *A, int lda, bool transA, const float *B, int ldb, bool transB,
                const float *bias, int act)
 {
@@ -515,6 +584,8 @@ int tgemm_form(int M, int N, int K, const float *A, int lda, bool transA, const 
     if (!transA && transB && K >= 4096 && M >= 16 && N >= 16 && N <= 256 && !bias && act == 0 && lda % 4 == 0 &&
         ldb % 4 == 0 && lda >= K && ldb >= K && aligned16(A) && aligned16(B))
         return 2;
+    if (!transA && N <= 4 && K >= 1024 && !bias && act == 0 && lda >= K) return 3;
+    if (!transB && K <= 4 && N >= 1024 && M <= 65535 && ldb >= N) return 4;
     return 0;
 }
 
@@ -522,6 +593,19 @@ ppe_status tgemm(int M, int N, int K, const float *A, int lda, bool transA, cons
                  float *C, int ldc, const float *bias, int act, bool accumulate, cudaStream_t s)
 {
     const int form = tgemm_form(M, N, K, A, lda, transA, B, ldb, transB, bias, act);
+    if (form == 3) {
+        gemm_rowdot_kernel<<<M, 256, 0, s>>>(N, K, A, lda, B, ldb, transB ? 1 : 0, C, ldc, accumulate ? 1 : 0);
+        PPE_CUDA_TRY(cudaGetLastError());
+        return PPE_OK;
+    }
+    if (form == 4) {
+        const size_t total = (size_t)M * N;
+        const unsigned g = (unsigned)std::min<size_t>((total + 255) / 256, 65535u * 16u);
+        gemm_smallk_kernel<<<g, 256, 0, s>>>(M, N, K, A, lda, transA ? 1 : 0, B, ldb, bias, C, ldc, act,
+                                              accumulate ? 1 : 0);
+        PPE_CUDA_TRY(cudaGetLastError());
+        return PPE_OK;
+    }
     const int dev = current_device();
     if (form == 0 || dev < 0 || (form == 2 && capturing(s)))
         return sgemm(M, N, K, A, lda, transA, B, ldb, transB, C, ldc, bias, act, accumulate, s);

@@ -96,11 +96,22 @@ def test_reduction_gemm_is_deterministic(lib):
     assert np.array_equal(a, b)
 
 
-@pytest.mark.parametrize("M,N,K,transA,transB", [(100, 2, 65536 // 8, False, True), (300, 1500, 100, False, False),
-                                                  (100, 1200, 2, False, False)])
-def test_other_shapes_use_cuda_cores(lib, M, N, K, transA, transB):
-    C, ref, scale, form = _run(lib, M, N, K, transA, transB, False, 0, False, 0, 11)
-    assert form == 0
+THIN = [  # M, N, K, transA, transB, bias, act, accumulate, form
+    (100, 2, 8192, False, True, False, 0, False, 3),     # first layer's weight gradient (2 coordinates)
+    (100, 1, 5003, False, False, False, 0, True, 3),     # a bias gradient against a vector, accumulated
+    (1, 1, 4099, False, False, False, 0, False, 3),      # the output bias's gradient
+    (100, 1200, 2, False, False, True, 1, False, 4),     # first trunk layer: tanh(W xy + b)
+    (37, 1500, 1, False, False, False, 0, True, 4),      # rank-one term, accumulated
+    (300, 1500, 100, False, False, False, 0, False, 0),  # outside every special form
+]
+
+
+@pytest.mark.parametrize("M,N,K,transA,transB,bias,act,acc,want", THIN)
+def test_thin_forms(lib, M, N, K, transA, transB, bias, act, acc, want):
+    """The thin products run on the CUDA cores (row dots, small K) at FP32
+    accuracy."""
+    C, ref, scale, form = _run(lib, M, N, K, transA, transB, bias, act, acc, 0, 11 + M + K)
+    assert form == want
     assert np.all(np.abs(C - ref) <= 1e-5 * scale + 1e-6)
 
 
