@@ -510,17 +510,23 @@ constexpr int round_up_i(int v, int m) { return (v + m - 1) / m * m; }
 // B a vector of ones or the loss's gradient, and the first trunk layer's
 // weight gradient, B the 2 coordinates).  One block per row, 16-byte loads,
 // a fixed reduction order.
-__global__ void __launch_bounds__(256) gemm_rowdot_kernel(int N, int K, const float *__restrict__ A, int lda,
+template <int N>
+__global__ void __launch_bounds__(512) gemm_rowdot_kernel(int K, const float *__restrict__ A, int lda,
                                                          const float *__restrict__ B, int ldb, int transB,
                                                          float *C, int ldc, int accumulate)
 {
-    __shared__ float red[4][8];
+    __shared__ float red[4][16];
     const int m = blockIdx.x;
     const float *a = A + (size_t)m * lda;
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    float acc[N];
+#pragma unroll
+    for (int n = 0; n < N; ++n) acc[n] = 0.f;
     const bool vec = ((lda | (transB ? ldb : 4)) & 3) == 0 && ((uintptr_t)A & 15) == 0 &&
                      (!transB || ((uintptr_t)B & 15) == 0);
     const int kv = vec ? K / 4 * 4 : 0;
+    // four 16-byte loads of a thread in flight at once (the loop is bound by
+    // memory latency, not bandwidth, at one block per row)
+#pragma unroll 4
     for (int k = 4 * threadIdx.x; k < kv; k += 4 * blockDim.x) {
         const float4 x = __ldg(reinterpret_cast<const float4 *>(a + k));
         for (int n = 0; n < N; ++n) {
@@ -594,7 +600,13 @@ ppe_status tgemm(int M, int N, int K, const float *A, int lda, bool transA, cons
 {
     const int form = tgemm_form(M, N, K, A, lda, transA, B, ldb, transB, bias, act);
     if (form == 3) {
-        gemm_rowdot_kernel<<<M, 256, 0, s>>>(N, K, A, lda, B, ldb, transB ? 1 : 0, C, ldc, accumulate ? 1 : 0);
+        const int tb = transB ? 1 : 0, ac = accumulate ? 1 : 0;
+        switch (N) {
+        case 1: gemm_rowdot_kernel<1><<<M, 512, 0, s>>>(K, A, lda, B, ldb, tb, C, ldc, ac); break;
+        case 2: gemm_rowdot_kernel<2><<<M, 512, 0, s>>>(K, A, lda, B, ldb, tb, C, ldc, ac); break;
+        case 3: gemm_rowdot_kernel<3><<<M, 512, 0, s>>>(K, A, lda, B, ldb, tb, C, ldc, ac); break;
+        default: gemm_rowdot_kernel<4><<<M, 512, 0, s>>>(K, A, lda, B, ldb, tb, C, ldc, ac); break;
+        }
         PPE_CUDA_TRY(cudaGetLastError());
         return PPE_OK;
     }
