@@ -1,7 +1,7 @@
 // Autotuner of the persistent solver kernel's launch configuration (the
 // paper has no counterpart).  In mixed precision two iteration passes do the
-// same arithmetic: the tile-cooperative pass (a whole CTA on one 16 x 128
-// tile, lowest latency) and the streaming pass (each warp marches down a
+// same arithmetic: the tile-cooperative pass (a whole CTA on one tile of
+// 128 cells by 16, 8 or 4 rows, lowest latency) and the streaming pass (each warp marches down a
 // strip, highest bandwidth).  Which is faster depends on the grid's size and
 // shape, so
 // ppe_autotune times each candidate on the grid itself: capped solves of a

@@ -57,8 +57,8 @@ template <class F> bool once_per_device(PerDevice &pd, F fn)
 constexpr int TILE_X = 128;                 // cells per tile row (4 per lane)
 constexpr int TILE_X_STREAM = 120;          // tile width of the streaming kernel: a warp row of
                                             // 128 cells covers it plus a four-cell halo per side
-constexpr int TILE_Y = 16;                  // rows per tile (one warp each)
-constexpr int TILE_Y_R8 = 8, TILE_Y_R4 = 4; // rows per tile of the short-tile variants
+constexpr int TILE_Y = 16;                  // rows per tile (one warp each in the row-by-row passes)
+constexpr int TILE_Y_R8 = 8, TILE_Y_R4 = 4; // rows per tile of the short-tile variants (2 or 4 warps a row)
 constexpr int SOLVER_THREADS = 32 * TILE_Y;
 constexpr int NPART = 6;                    // FP64 partial sums per tile
 constexpr int PITCH_ALIGN = 32;             // inner-vector row pitch (elements)
@@ -66,7 +66,7 @@ constexpr int PITCH_ALIGN = 32;             // inner-vector row pitch (elements)
 // starts on a 16-byte boundary for the TMA unit, four cells in x.
 constexpr int WIN_OX = 4, WIN_OY = 2;
 constexpr int WIN_X = TILE_X + 2 * WIN_OX;  // 136 (window of a tile-cooperative tile)
-constexpr int WIN_Y = TILE_Y + 2 * WIN_OY;  // 20
+constexpr int WIN_Y = TILE_Y + 2 * WIN_OY;  // 20 (16-row tiles; rows + 4 in general)
 // Tensor maps of one system's inner vectors (per precision): the two residual
 // buffers and the two direction buffers (window boxes), and d (tile box).
 // MAP_Y: the per-row y coefficients (dy, fy[j], fy[j+1], 0) as an FP32 [ny][4]
