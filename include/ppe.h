@@ -281,21 +281,24 @@ PPE_API ppe_status ppe_solve_noalloc(int nx, int ny, const double *dx, const dou
 /*
  * Autotuner of the persistent kernel's launch configuration (the paper has no
  * counterpart).  In MIXED precision it times, on this grid, the iteration-pass
- * variants of ppe_solve_opts.iter_pass (tile-cooperative and streaming) by
- * capped solves of a smooth synthetic source,
+ * variants of ppe_solve_opts.iter_pass (tile-cooperative on tiles of 16, 8
+ * and 4 rows, and streaming) by capped solves of a smooth synthetic source,
  * and keeps the fastest: on the grid (used by ppe_solve when
- * opts.iter_pass is 0) and in a process-wide table keyed by (nx, ny) that
- * later grids of the same shape use.  If the environment variable
- * PPE_TUNE_CACHE names a file, the table is read from it on first use and
- * each new entry is appended (one JSON object per line).  The call allocates
- * two temporary device fields of nx*ny doubles, runs about twenty solves of
- * at most 40 iterations and synchronises `stream`.
+ * opts.iter_pass, and for the height opts.tile_rows, are 0) and in a
+ * process-wide table keyed by (nx, ny) that later grids of the same shape
+ * use.  If the environment variable PPE_TUNE_CACHE names a file, the table
+ * is read from it on first use and each new entry is appended (one JSON
+ * object per line).  The call allocates two temporary device fields of
+ * nx*ny doubles, runs about thirty solves of at most 40 iterations and
+ * synchronises `stream`.
  */
 typedef struct {
     int32_t iter_pass;       /* chosen variant: 1 tile-cooperative, 2 streaming          */
     int32_t blocks_per_sm;   /* chosen CTAs per SM (0: as many as fit)                    */
-    double us_per_iter[3];   /* measured: tile-cooperative, (unused), streaming           */
-    int32_t reserved[4];
+    double us_per_iter[3];   /* measured: tile-cooperative (its fastest height),
+                                (unused), streaming                                      */
+    int32_t tile_rows;       /* fastest tile-cooperative height: 16, 8 or 4 rows          */
+    int32_t reserved[3];
 } ppe_tune_report;
 PPE_API ppe_status ppe_autotune(ppe_grid *grid, void *stream, ppe_tune_report *report);
 

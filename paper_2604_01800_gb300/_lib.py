@@ -49,7 +49,7 @@ class ppe_solve_opts(ctypes.Structure):
 
 class ppe_tune_report(ctypes.Structure):
     _fields_ = [("iter_pass", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("us_per_iter", ctypes.c_double * 3), ("reserved", ctypes.c_int32 * 4)]
+                ("us_per_iter", ctypes.c_double * 3), ("tile_rows", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class ppe_net_config(ctypes.Structure):

@@ -98,7 +98,7 @@ def ppe_autotune(grid: Grid, stream=None) -> dict:
     the fastest for later solves of this grid shape; returns the report."""
     rep = _lib.ppe_tune_report()
     check(_lib.load().ppe_autotune(grid.handle, _stream(stream), ctypes.byref(rep)), "ppe_autotune")
-    return {"iter_pass": rep.iter_pass, "blocks_per_sm": rep.blocks_per_sm,
+    return {"iter_pass": rep.iter_pass, "blocks_per_sm": rep.blocks_per_sm, "tile_rows": rep.tile_rows,
             "us_per_iter": {"tile": rep.us_per_iter[0], "stream": rep.us_per_iter[2]}}
 
 

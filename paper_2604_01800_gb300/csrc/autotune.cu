@@ -29,7 +29,7 @@ namespace {
 ppe_status check_cuda(cudaError_t e, const char *what) { return e == cudaSuccess ? PPE_OK : cuda_status(e, what); }
 
 struct TuneEntry {
-    int iter_pass = 0, blocks_per_sm = 0;
+    int iter_pass = 0, blocks_per_sm = 0, tile_rows = 0;
     double us[3] = {0, 0, 0};
 };
 
@@ -54,13 +54,23 @@ void load_table()
     if (!f) return;
     char line[512];
     while (std::fgets(line, sizeof line, f)) {
-        int nx = 0, ny = 0, ip = 0, bps = 0;
+        int nx = 0, ny = 0, ip = 0, bps = 0, rows = 0;
         TuneEntry e;
-        if (std::sscanf(line, " {\"nx\": %d, \"ny\": %d, \"iter_pass\": %d, \"blocks_per_sm\": %d, \"us\": [%lf, %lf, %lf]",
-                        &nx, &ny, &ip, &bps, &e.us[0], &e.us[1], &e.us[2]) == 7 &&
-            nx > 0 && ny > 0 && (ip == 1 || ip == 2) && bps >= 0) {
+        // entries with the tile height, and older ones without it
+        const bool with_rows =
+            std::sscanf(line,
+                        " {\"nx\": %d, \"ny\": %d, \"iter_pass\": %d, \"blocks_per_sm\": %d, \"tile_rows\": %d, \"us\": "
+                        "[%lf, %lf, %lf]",
+                        &nx, &ny, &ip, &bps, &rows, &e.us[0], &e.us[1], &e.us[2]) == 8;
+        const bool without =
+            !with_rows &&
+            std::sscanf(line, " {\"nx\": %d, \"ny\": %d, \"iter_pass\": %d, \"blocks_per_sm\": %d, \"us\": [%lf, %lf, %lf]",
+                        &nx, &ny, &ip, &bps, &e.us[0], &e.us[1], &e.us[2]) == 7;
+        if ((with_rows || without) && nx > 0 && ny > 0 && (ip == 1 || ip == 2) && bps >= 0 &&
+            (rows == 0 || rows == TILE_Y || rows == TILE_Y_R8 || rows == TILE_Y_R4)) {
             e.iter_pass = ip;
             e.blocks_per_sm = bps;
+            e.tile_rows = with_rows ? rows : 0;
             g_tune[{nx, ny}] = e;
         }
     }
@@ -73,8 +83,10 @@ void append_entry(int nx, int ny, const TuneEntry &e)
     if (!path) return;
     FILE *f = std::fopen(path, "a");
     if (!f) return;
-    std::fprintf(f, "{\"nx\": %d, \"ny\": %d, \"iter_pass\": %d, \"blocks_per_sm\": %d, \"us\": [%.3f, %.3f, %.3f]}\n",
-                 nx, ny, e.iter_pass, e.blocks_per_sm, e.us[0], e.us[1], e.us[2]);
+    std::fprintf(f,
+                 "{\"nx\": %d, \"ny\": %d, \"iter_pass\": %d, \"blocks_per_sm\": %d, \"tile_rows\": %d, \"us\": [%.3f, "
+                 "%.3f, %.3f]}\n",
+                 nx, ny, e.iter_pass, e.blocks_per_sm, e.tile_rows, e.us[0], e.us[1], e.us[2]);
     std::fclose(f);
 }
 
@@ -113,7 +125,7 @@ ppe_status time_capped(ppe_grid *g, const ppe_solve_opts &o, const double *rhs, 
 
 }  // namespace
 
-bool tune_lookup(int nx, int ny, int *iter_pass, int *blocks_per_sm)
+bool tune_lookup(int nx, int ny, int *iter_pass, int *blocks_per_sm, int *tile_rows)
 {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     load_table();
@@ -121,6 +133,7 @@ bool tune_lookup(int nx, int ny, int *iter_pass, int *blocks_per_sm)
     if (it == g_tune.end()) return false;
     *iter_pass = it->second.iter_pass;
     *blocks_per_sm = it->second.blocks_per_sm;
+    *tile_rows = it->second.tile_rows;
     return true;
 }
 
@@ -155,17 +168,20 @@ extern "C" ppe_status ppe_autotune(ppe_grid *g, void *stream, ppe_tune_report *r
     }
     ppe_status status = check_cuda(cudaMemcpyAsync(rhs, S.data(), bytes, cudaMemcpyHostToDevice, st), "cudaMemcpyAsync");
 
-    // candidates: the tile-cooperative and the streaming pass (slot 1 of the
-    // report is unused: both kernels run one CTA per SM)
-    struct Cand { int slot, pass, bps; };
-    const Cand cands[2] = {{0, 1, 0}, {2, 2, 0}};
+    // candidates: the tile-cooperative pass on tiles of 16, 8 and 4 rows, and
+    // the streaming pass (slot 1 of the report is unused: the kernels run one
+    // CTA per SM); slot 0 keeps the fastest height
+    struct Cand { int slot, pass, bps, rows; };
+    const Cand cands[4] = {{0, 1, 0, TILE_Y}, {0, 1, 0, TILE_Y_R8}, {0, 1, 0, TILE_Y_R4}, {2, 2, 0, 0}};
     const int short_cap = 8, long_cap = 40;
     TuneEntry e;
     double best = 1e30;
-    for (int c = 0; c < 2 && status == PPE_OK; ++c) {
+    e.us[0] = 1e30;
+    for (int c = 0; c < 4 && status == PPE_OK; ++c) {
         ppe_solve_opts o = g->opts;
         o.iter_pass = cands[c].pass;
         o.blocks_per_sm = cands[c].bps;
+        o.tile_rows = cands[c].rows;
         o.inner_rtol = 1e-12;          // no residual replacement between the caps
         double t0 = 0, t1 = 0;
         o.max_iters = short_cap;
@@ -175,7 +191,10 @@ extern "C" ppe_status ppe_autotune(ppe_grid *g, void *stream, ppe_tune_report *r
         status = time_capped(g, o, rhs, x, st, &t1);
         if (status != PPE_OK) break;
         const double us = 1e6 * std::max(t1 - t0, 0.0) / (long_cap - short_cap);
-        e.us[cands[c].slot] = us;
+        if (cands[c].slot != 0 || us < e.us[0]) {
+            e.us[cands[c].slot] = us;
+            if (cands[c].slot == 0) e.tile_rows = cands[c].rows;
+        }
         if (us < best) {
             best = us;
             e.iter_pass = cands[c].pass;
@@ -187,6 +206,7 @@ extern "C" ppe_status ppe_autotune(ppe_grid *g, void *stream, ppe_tune_report *r
     if (status != PPE_OK) return status;
     g->tuned_pass = e.iter_pass;
     g->tuned_bps = e.blocks_per_sm;
+    g->tuned_rows = e.tile_rows;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         load_table();
@@ -197,6 +217,7 @@ extern "C" ppe_status ppe_autotune(ppe_grid *g, void *stream, ppe_tune_report *r
         std::memset(report, 0, sizeof(*report));
         report->iter_pass = e.iter_pass;
         report->blocks_per_sm = e.blocks_per_sm;
+        report->tile_rows = e.tile_rows;
         for (int c = 0; c < 3; ++c) report->us_per_iter[c] = e.us[c];
     }
     return PPE_OK;

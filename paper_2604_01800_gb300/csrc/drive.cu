@@ -755,16 +755,21 @@ namespace {
 ppe_status solve_single(ppe_grid *g, const double *rhs, double *x, double tol, ppe_mode mode, ppe_precision prec,
                         ppe_net *net, cudaStream_t st, ppe_solve_info *info)
 {
-    int pass = g->opts.iter_pass, bps = g->opts.blocks_per_sm;
+    int pass = g->opts.iter_pass, bps = g->opts.blocks_per_sm, rows = g->opts.tile_rows;
     if (prec == PPE_PREC_MIXED && pass == 0) {
+        // the autotuner's choice: pass, CTAs per SM and (unless the options
+        // fix it) the tile height
+        int tuned_rows = 0;
         if (g->tuned_pass) {
             pass = g->tuned_pass;
             bps = g->tuned_bps;
+            tuned_rows = g->tuned_rows;
         } else {
-            tune_lookup(g->nx, g->ny, &pass, &bps);
+            tune_lookup(g->nx, g->ny, &pass, &bps, &tuned_rows);
         }
+        if (!rows) rows = tuned_rows;
     }
-    const SolverVariant v = pick_variant(prec, pass, g->tiles_x * g->tiles_y, g->opts.tile_rows);
+    const SolverVariant v = pick_variant(prec, pass, g->tiles_x * g->tiles_y, rows);
     std::vector<SysDesc> sds(1, make_desc(g, rhs, x, tol, mode, prec, 0, v));
     const int maxb = std::min(solver_max_blocks(v, bps), sds[0].ntiles);
     if (maxb < 1) return cuda_status(cudaErrorInvalidConfiguration, "solver occupancy");

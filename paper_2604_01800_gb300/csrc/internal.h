@@ -299,7 +299,7 @@ ppe_status encode_solver_maps(void *const r[2], void *const p[2], void *d, const
 
 // Autotuned launch configuration of a grid shape, if ppe_autotune measured
 // one in this process (or the tuning cache file holds one).
-bool tune_lookup(int nx, int ny, int *iter_pass, int *blocks_per_sm);
+bool tune_lookup(int nx, int ny, int *iter_pass, int *blocks_per_sm, int *tile_rows);
 
 // Remove the mean of the grid's DLSM direction e (two kernels on `stream`;
 // no allocation, so it may run inside a stream capture).
@@ -361,7 +361,7 @@ struct ppe_grid {
     float *ycoef = nullptr;              // [ny][4] FP32: dy, fy[j], fy[j+1], 0 (streaming kernel)
     void *r[2] = {nullptr, nullptr}, *p[2] = {nullptr, nullptr}, *d = nullptr;
     CUtensorMap *tmaps_dev = nullptr;    // tensor maps of the inner vectors, one set per kernel variant
-    int tuned_pass = 0, tuned_bps = 0;   // ppe_autotune's choice (0: none)
+    int tuned_pass = 0, tuned_bps = 0, tuned_rows = 0;   // ppe_autotune's choice (0: none)
     uint64_t id = 0;                     // process-unique creation number (keys cached batch plans)
     ppe::LaunchSet *ls = nullptr;        // single-system launch resources and the solve graph
     ppe::MgPlan *mg = nullptr;           // multigrid hierarchy (first multigrid solve)

@@ -1,5 +1,6 @@
-"""The autotuner times the iteration-pass variants on a grid and the solves
-that follow use its choice; results stay within the parity bars."""
+"""The autotuner times the iteration-pass variants (the tile-cooperative pass
+at each tile height, the streaming pass) on a grid and the solves that
+follow use its choice; results stay within the parity bars."""
 import json
 import os
 
@@ -31,17 +32,35 @@ def test_autotune_then_solve(api, tmp_path):
         f = I.gaussian_rhs(dx, dy, g, 6)
         grid = api.ppe_create_grid(dx, dy)
         rep = api.ppe_autotune(grid)
-        assert rep["iter_pass"] in (1, 2)
+        assert rep["iter_pass"] in (1, 2) and rep["tile_rows"] in (4, 8, 16)
         assert all(v > 0 for v in rep["us_per_iter"].values()), rep
         best = min(rep["us_per_iter"].values())
         chosen = {1: "tile", 2: "stream"}[rep["iter_pass"]]
         assert rep["us_per_iter"][chosen] == best
         line = json.loads(cache.read_text().strip().splitlines()[-1])
-        assert (line["nx"], line["ny"], line["iter_pass"]) == (700, 500, rep["iter_pass"])
+        assert (line["nx"], line["ny"], line["iter_pass"], line["tile_rows"]) == (700, 500, rep["iter_pass"],
+                                                                                rep["tile_rows"])
         # a solve with the default options now runs the tuned variant
         x = torch.zeros(500, 700, dtype=torch.float64, device="cuda")
         info = api.ppe_solve(grid, torch.tensor(f, device="cuda"), x, 1e-8, api.PPE_MODE_PCG, api.PPE_PREC_MIXED)
         assert info["status"] == 0
         assert oracle.true_relres(dx, dy, f, x.cpu().numpy()) <= 1.05e-8
+    finally:
+        os.environ.pop("PPE_TUNE_CACHE", None)
+
+
+def test_autotune_small_grid_picks_a_tile_height(api, tmp_path):
+    """On the 256^2 cylinder grid the tile-cooperative pass wins and the tuned
+    height is one of the three; the tuned solve meets the parity bars."""
+    os.environ["PPE_TUNE_CACHE"] = str(tmp_path / "tune.jsonl")
+    try:
+        w = I.config3(0)
+        grid = api.ppe_create_grid(w.dx, w.dy)
+        rep = api.ppe_autotune(grid)
+        assert rep["iter_pass"] == 1 and rep["tile_rows"] in (4, 8, 16), rep
+        x = torch.zeros(w.ny, w.nx, dtype=torch.float64, device="cuda")
+        info = api.ppe_solve(grid, torch.tensor(w.f, device="cuda"), x, 1e-8, api.PPE_MODE_PCG, api.PPE_PREC_MIXED)
+        assert info["status"] == 0
+        assert oracle.true_relres(w.dx, w.dy, w.f, x.cpu().numpy()) <= 1.05e-8
     finally:
         os.environ.pop("PPE_TUNE_CACHE", None)
