@@ -840,7 +840,35 @@ ppe_status ppe_solve_batch(int n, ppe_grid *const *grids, const double *const *r
     cudaStream_t st = (cudaStream_t)stream;
     int ntiles = 0;
     for (int i = 0; i < n; ++i) ntiles += grids[i]->tiles_x * grids[i]->tiles_y;
-    const SolverVariant v = pick_variant(prec, grids[0]->opts.iter_pass, ntiles, grids[0]->opts.tile_rows);
+    // One kernel serves every system: the first grid's options choose it; in
+    // mixed precision with the pass left to the library, an autotuned choice
+    // (pass and tile height) shared by every system's shape is taken, else the
+    // batch's total tile count decides.
+    int pass = grids[0]->opts.iter_pass, rows = grids[0]->opts.tile_rows;
+    if (prec == PPE_PREC_MIXED && pass == 0) {
+        int p0 = -1, r0 = -1;
+        bool same = true;
+        for (int i = 0; i < n && same; ++i) {
+            int p = 0, b = 0, r = 0;
+            if (grids[i]->tuned_pass) {
+                p = grids[i]->tuned_pass;
+                r = grids[i]->tuned_rows;
+            } else if (!tune_lookup(grids[i]->nx, grids[i]->ny, &p, &b, &r)) {
+                same = false;
+                break;
+            }
+            if (p0 < 0) {
+                p0 = p;
+                r0 = r;
+            }
+            same = p == p0 && r == r0;
+        }
+        if (same && p0 > 0) {
+            pass = p0;
+            if (!rows) rows = r0;
+        }
+    }
+    const SolverVariant v = pick_variant(prec, pass, ntiles, rows);
     std::vector<SysDesc> sds(n);
     std::vector<int32_t> full(n);
     for (int i = 0; i < n; ++i) {

@@ -214,10 +214,13 @@ template <typename T, typename S> __device__ __forceinline__ Coef<T, S::GK> &coe
 // Coefficients of a tile do not change between steps: a block that keeps
 // working on the same tile reuses them.  Every caller synchronises the block
 // before it reads the coefficients.
+// Every thread reads the tag before thread 0 may change it.  With the
+// Jacobi weights kept, load_coef passes a block barrier before thread 0
+// writes the tag, which orders the reads; without them a barrier comes first.
 template <typename S> __device__ __forceinline__ void load_coef_f(S &sm, const SysDesc &sd, int i0, int j0, int tag)
 {
     const int have = sm.tag_f;
-    __syncthreads();
+    if constexpr (!Coef<float, S::GK>::KEEP_DINV) __syncthreads();
     if (have == tag) return;
     load_coef<float>(sm.cff, sd, i0, j0, sd.dx32, sd.fx32, sd.dy32, sd.fy32);
     if (threadIdx.x == 0) sm.tag_f = tag;
@@ -226,7 +229,7 @@ template <typename S> __device__ __forceinline__ void load_coef_f(S &sm, const S
 template <typename S> __device__ __forceinline__ void load_coef_d(S &sm, const SysDesc &sd, int i0, int j0, int tag)
 {
     const int have = sm.tag_d;
-    __syncthreads();
+    if constexpr (!Coef<double, S::GK>::KEEP_DINV) __syncthreads();
     if (have == tag) return;
     load_coef<double>(sm.cfd, sd, i0, j0, sd.dx, sd.fx, sd.dy, sd.fy);
     if (threadIdx.x == 0) sm.tag_d = tag;

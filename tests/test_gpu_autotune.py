@@ -64,3 +64,23 @@ def test_autotune_small_grid_picks_a_tile_height(api, tmp_path):
         assert oracle.true_relres(w.dx, w.dy, w.f, x.cpu().numpy()) <= 1.05e-8
     finally:
         os.environ.pop("PPE_TUNE_CACHE", None)
+
+
+def test_batch_takes_a_shared_tuned_choice(api, tmp_path):
+    """Two systems of one tuned shape (64^2): the batch runs the tuned pass and
+    tile height for both, and each meets the parity bars."""
+    os.environ["PPE_TUNE_CACHE"] = str(tmp_path / "tune.jsonl")
+    try:
+        ws = [I.config1(0), I.config1(1)]
+        grids = [api.ppe_create_grid(w.dx, w.dy) for w in ws]
+        rep = api.ppe_autotune(grids[0])            # the second grid finds the shape in the table
+        assert rep["tile_rows"] in (4, 8, 16)
+        rhs = [torch.tensor(w.f, device="cuda") for w in ws]
+        xs = [torch.zeros(w.ny, w.nx, dtype=torch.float64, device="cuda") for w in ws]
+        infos, st = api.ppe_solve_batch(grids, rhs, xs, 1e-8, api.PPE_MODE_PCG, api.PPE_PREC_MIXED)
+        assert st == 0
+        for w, x, info in zip(ws, xs, infos):
+            assert info["status"] == 0
+            assert oracle.true_relres(w.dx, w.dy, w.f, x.cpu().numpy()) <= 1.05e-8
+    finally:
+        os.environ.pop("PPE_TUNE_CACHE", None)
