@@ -157,7 +157,8 @@ template <typename T, int GK_> struct SmemT {
     float red_hi[2][NPART][NWARP], red_lo[2][NPART][NWARP];   // per-warp partials, two buffers
     SysDesc sd[SMAX];
     SysState st[SMAX];
-    int32_t ph0[SMAX];      // phase of each system at the start of the step (step timing)
+    int32_t ph0[2][SMAX];   // step timing, by step parity: each system's phase at the step's start
+    uint64_t tstep[2];      // and the step's start time
     int32_t tag_d, tag_f;   // tile whose coefficients are in cfd / cff
     int32_t go;
     uint32_t fills;         // TMA stage fills issued so far (stage = fill & 1)
@@ -1600,6 +1601,22 @@ __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p)
 // this step; lane 0 of warp 0 then bumps the system's arrival counter.  The
 // per-warp scratch alternates between two buffers, so a warp that runs ahead
 // into the next system's pass cannot overwrite what warp 0 still reads.
+// A step's device time, charged by each system's first block to the kind of
+// pass the system ran in it (ph0[par]).
+template <typename S> __device__ void charge_step(S &sm, int nq, uint64_t dt, int par)
+{
+    for (int q = 0; q < nq; ++q) {
+        if ((int)blockIdx.x != sm.sd[q].blk0) continue;
+        const int ph = sm.ph0[par][q];
+        if (ph == PH_ITER || ph == PH_RESTART)
+            sm.st[q].ns_pcg += dt;
+        else if (ph == PH_DLSM_DOT || ph == PH_DLSM_UPD)
+            sm.st[q].ns_dlsm += dt;
+        else if (is_pass_phase(ph))
+            sm.st[q].ns_fp64 += dt;
+    }
+}
+
 template <typename S>
 __device__ void block_publish(S &sm, const Acc &acc, Slot *slot, uint32_t *counter, int par)
 {
@@ -1695,7 +1712,7 @@ __global__ void __launch_bounds__(SOLVER_THREADS, 1)
     // wait for the other blocks, reduction of their records, state advance
     uint64_t t_a = prof ? gtimer() : 0, t_p = 0, t_b = 0, t_w = 0, t_r = 0, t_x = 0, t_c = 0;
     int red_par = 0;
-    uint64_t t_step = 0;
+    uint32_t last_step = 0;   // the last step that ran (thread 0)
     for (uint32_t step = 1;; ++step) {
         // a step budget ends the launch at the same step in every block, so each
         // system stops between two of its steps
@@ -1706,8 +1723,9 @@ __global__ void __launch_bounds__(SOLVER_THREADS, 1)
         if (!any) break;
         const int bank = step & 1;
         if (threadIdx.x == 0) {
-            t_step = gtimer();
-            for (int q = 0; q < nq; ++q) sm.ph0[q] = sm.st[q].phase;
+            sm.tstep[bank] = gtimer();
+            for (int q = 0; q < nq; ++q) sm.ph0[bank][q] = sm.st[q].phase;
+            last_step = step;
         }
         // 1) passes; publish one record per live system
         for (int q = 0; q < nq; ++q) {
@@ -1827,23 +1845,12 @@ __global__ void __launch_bounds__(SOLVER_THREADS, 1)
                 }
             }
         }
+        // the previous step's device time, charged by a lane that waits for no
+        // system (off the step's critical path; the last step is charged on exit)
+        if (threadIdx.x == 32 * (NWARP - 1) && step > 1)
+            charge_step(sm, nq, sm.tstep[bank] - sm.tstep[bank ^ 1], bank ^ 1);
         __syncthreads();
         if (!sm.go) return;                             // a bounded wait expired: leave without writing state
-        if (threadIdx.x == 0) {
-            // the step's device time, charged by each system's first block to the
-            // kind of pass the system ran
-            const uint64_t dt = gtimer() - t_step;
-            for (int q = 0; q < nq; ++q) {
-                if ((int)blockIdx.x != sm.sd[q].blk0) continue;
-                const int ph = sm.ph0[q];
-                if (ph == PH_ITER || ph == PH_RESTART)
-                    sm.st[q].ns_pcg += dt;
-                else if (ph == PH_DLSM_DOT || ph == PH_DLSM_UPD)
-                    sm.st[q].ns_dlsm += dt;
-                else if (is_pass_phase(ph))
-                    sm.st[q].ns_fp64 += dt;
-            }
-        }
         if (prof) {
             t_c = gtimer();
             if (t_p && t_w && t_r) {
@@ -1874,6 +1881,8 @@ __global__ void __launch_bounds__(SOLVER_THREADS, 1)
     }
     if (prof)
         for (int k = 0; k < 16; ++k) a.prof[k] += sm.pacc[k];
+    if (threadIdx.x == 0 && last_step > 0)
+        charge_step(sm, nq, gtimer() - sm.tstep[last_step & 1], (int)(last_step & 1));
     // a system that waits for a network direction starts its network clock
     if (threadIdx.x == 0)
         for (int q = 0; q < nq; ++q)
