@@ -43,7 +43,7 @@ CONV_WEIGHTS = os.path.join(ROOT, "paper_2604_01800_gb300", "weights", "hydea_co
 TOL = 1e-8
 L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2
 SOURCES = 5                         # distinct sources of the headline workload, cycled over the steps
-SOLVER_C3_DRAM_BYTES = 1.2582e6      # ncu: DRAM bytes (read + write) of one solver launch = one c3 solve
+SOLVER_C3_DRAM_BYTES = 1.2897e6      # ncu: DRAM bytes (read + write) of one solver launch = one c3 solve
 
 
 def _args():
