@@ -255,53 +255,68 @@ __device__ __forceinline__ float rin_at(const float *R, int b, int y, int x, int
     return (y >= 0 && x >= 0 && y < ny && x < nx) ? R[((size_t)b * ny + y) * nx + x] : 0.f;
 }
 
-// dW[co][tap] of the first layer: eight warps per block, each on its own
-// pixels (lane = output channel, up to four per lane), then the block's warps
-// are summed in shared memory and added once per (co, tap).
-constexpr int WI_WARPS = 8, WI_MAXU = 4;   // C <= 128
-__global__ void __launch_bounds__(32 * WI_WARPS) wgrad_in_kernel(const bf16 *__restrict__ dZ,
-                                                                const float *__restrict__ R,
-                                                                const float *__restrict__ eta, int B, int H, int W,
-                                                                int C, int nx, int ny, float *__restrict__ dW)
+// dW[co][tap] of the first layer, dW[co][t] = sum_p dZ[p][co] V[p][t] with
+// V[p][t] = (eta R) at the tap's neighbour of p.  A block stages a tile of
+// WI_TP pixels (their dZ rows with 16-byte copies, their nine V values) in
+// shared memory; thread k then owns the pairs (co, t) = k, k + 256, ... and
+// sums over the tile's pixels; each pair is added to dW once per block.
+constexpr int WI_THREADS = 256, WI_TP = 128, WI_MAXC = 128, WI_MAXK = (WI_MAXC * 9 + WI_THREADS - 1) / WI_THREADS;
+
+int wg_sm_count_host()
 {
-    __shared__ float red[WI_WARPS][WI_MAXU * 32 * 9];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float acc[WI_MAXU][9];
-#pragma unroll
-    for (int u = 0; u < WI_MAXU; ++u)
-#pragma unroll
-        for (int t = 0; t < 9; ++t) acc[u][t] = 0.f;
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
+
+__global__ void __launch_bounds__(WI_THREADS) wgrad_in_kernel(const bf16 *__restrict__ dZ,
+                                                             const float *__restrict__ R,
+                                                             const float *__restrict__ eta, int B, int H, int W,
+                                                             int C, int nx, int ny, float *__restrict__ dW)
+{
+    __shared__ float V[WI_TP * 9];
+    __shared__ __align__(16) bf16 Z[WI_TP * WI_MAXC];
     const size_t P = (size_t)B * H * W;
-    for (size_t p = (size_t)blockIdx.x * WI_WARPS + warp; p < P; p += (size_t)gridDim.x * WI_WARPS) {
-        const int x = p % W, y = (p / W) % H, b = p / ((size_t)W * H);
-        float v[9];
+    const int npair = C * 9;
+    float acc[WI_MAXK];
 #pragma unroll
-        for (int t = 0; t < 9; ++t) {
-            const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
-            v[t] = (yy >= 0 && xx >= 0 && yy < H && xx < W) ? rin_at(R, b, yy, xx, nx, ny) * eta[yy * W + xx] : 0.f;
+    for (int j = 0; j < WI_MAXK; ++j) acc[j] = 0.f;
+    const size_t ntiles = (P + WI_TP - 1) / WI_TP;
+    for (size_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const size_t p0 = tile * WI_TP;
+        const int np = (int)min((size_t)WI_TP, P - p0);
+        for (int i = threadIdx.x; i < WI_TP * 9; i += WI_THREADS) {
+            const int pi = i / 9, t = i - pi * 9;
+            float v = 0.f;
+            if (pi < np) {
+                const size_t p = p0 + pi;
+                const int x = (int)(p % W), y = (int)((p / W) % H), b = (int)(p / ((size_t)W * H));
+                const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
+                if (yy >= 0 && xx >= 0 && yy < H && xx < W) v = rin_at(R, b, yy, xx, nx, ny) * eta[yy * W + xx];
+            }
+            V[i] = v;
         }
+        // the tile's dZ rows are contiguous: np * C values, C a multiple of 8
+        const uint4 *src = reinterpret_cast<const uint4 *>(dZ + p0 * C);
+        uint4 *dst = reinterpret_cast<uint4 *>(Z);
+        for (int i = threadIdx.x; i < np * C / 8; i += WI_THREADS) dst[i] = src[i];
+        __syncthreads();
 #pragma unroll
-        for (int u = 0; u < WI_MAXU; ++u) {
-            const int co = lane + 32 * u;
-            if (co >= C) break;
-            const float d = __bfloat162float(dZ[p * C + co]);
-#pragma unroll
-            for (int t = 0; t < 9; ++t) acc[u][t] = fmaf(d, v[t], acc[u][t]);
+        for (int j = 0; j < WI_MAXK; ++j) {
+            const int k = threadIdx.x + WI_THREADS * j;
+            if (k >= npair) break;
+            const int co = k / 9, t = k - co * 9;
+            float sacc = 0.f;
+            for (int pi = 0; pi < np; ++pi) sacc = fmaf(__bfloat162float(Z[pi * C + co]), V[pi * 9 + t], sacc);
+            acc[j] += sacc;
         }
+        __syncthreads();
     }
 #pragma unroll
-    for (int u = 0; u < WI_MAXU; ++u) {
-        const int co = lane + 32 * u;
-        if (co >= C) break;
-#pragma unroll
-        for (int t = 0; t < 9; ++t) red[warp][co * 9 + t] = acc[u][t];
-    }
-    __syncthreads();
-    for (int k = threadIdx.x; k < C * 9; k += blockDim.x) {
-        float sum = 0.f;
-#pragma unroll
-        for (int w = 0; w < WI_WARPS; ++w) sum += red[w][k];
-        atomicAdd(&dW[k], sum);
+    for (int j = 0; j < WI_MAXK; ++j) {
+        const int k = threadIdx.x + WI_THREADS * j;
+        if (k < npair) atomicAdd(&dW[k], acc[j]);
     }
 }
 
@@ -317,7 +332,17 @@ __global__ void dgrad_in_kernel(const bf16 *__restrict__ dZ, const float *__rest
             int yy = y - (t / 3 - 1), xx = x - (t % 3 - 1);
             if (yy < 0 || xx < 0 || yy >= H || xx >= W) continue;
             const bf16 *dz = dZ + (((size_t)b * H + yy) * W + xx) * C;
-            for (int co = 0; co < C; ++co) g = fmaf(Wt[co * 9 + t], __bfloat162float(dz[co]), g);
+            if ((C & 7) == 0) {
+                // the pixel's channels as 16-byte pieces, in channel order
+                for (int co = 0; co < C; co += 8) {
+                    const uint4 raw = *reinterpret_cast<const uint4 *>(dz + co);
+                    const bf16 *hv = reinterpret_cast<const bf16 *>(&raw);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) g = fmaf(Wt[(co + i) * 9 + t], __bfloat162float(hv[i]), g);
+                }
+            } else {
+                for (int co = 0; co < C; ++co) g = fmaf(Wt[co * 9 + t], __bfloat162float(dz[co]), g);
+            }
         }
         float r = rin_at(R, b, y, x, nx, ny);
         atomicAdd(&deta[y * W + x], r * g);
@@ -767,11 +792,16 @@ static ppe_status net_backward(ppe_net *n, NetCache *c, TrainWs *w, ppe_grid *g,
         const size_t px = (size_t)B * c->H * c->W;
         act_bwd(G("enc0a"), c->act + pl.Z[li], w->dZ, px * l.cout, l.cout, grads + l.off_b, s);
         const float *eta = c->eta + c->eoff[li];
-        if (l.cout > 32 * WI_MAXU) {
-            set_error("first-layer weight gradient: at most 128 channels");
+        if (l.cout > WI_MAXC || l.cout % 8 || ((uintptr_t)w->dZ & 15)) {
+            set_error("first-layer weight gradient: at most 128 channels, a multiple of 8, 16-byte aligned rows");
             return PPE_ERR_ARG;
         }
-        wgrad_in_kernel<<<512, 32 * WI_WARPS, 0, s>>>(w->dZ, R, eta, B, c->H, c->W, l.cout, g->nx, g->ny, grads + l.off_w);
+        {
+            const size_t tiles = (px + WI_TP - 1) / WI_TP;
+            const unsigned gw = (unsigned)std::min<size_t>(tiles, 4 * (size_t)wg_sm_count_host());
+            wgrad_in_kernel<<<gw, WI_THREADS, 0, s>>>(w->dZ, R, eta, B, c->H, c->W, l.cout, g->nx, g->ny,
+                                                      grads + l.off_w);
+        }
         if (cf.mesh_conv) {
             PPE_CUDA_TRY(cudaMemsetAsync(w->deta, 0, (size_t)c->H * c->W * 4, s));
             dgrad_in_kernel<<<g1d(px), 256, 0, s>>>(w->dZ, P + l.off_w, R, B, c->H, c->W, l.cout, g->nx, g->ny, w->deta);
