@@ -440,13 +440,8 @@ __global__ void gemm_red_sum_kernel(const float *__restrict__ part, int splits, 
     }
 }
 
-struct DevBuf {
-    float *p = nullptr;
-    size_t n = 0;
-};
 std::mutex g_gt_mu;
 int *g_gt_flag[MAX_DEVICES] = {};
-DevBuf g_gt_part[MAX_DEVICES];
 
 int current_device()
 {
@@ -468,21 +463,6 @@ int *gt_flag(int dev)
         g_gt_flag[dev] = f;
     }
     return g_gt_flag[dev];
-}
-
-// The reduction's slices (grown on demand; kept for the process).
-float *gt_part(int dev, size_t n)
-{
-    std::lock_guard<std::mutex> lk(g_gt_mu);
-    DevBuf &b = g_gt_part[dev];
-    if (b.n < n) {
-        if (b.p) cudaFree(b.p);
-        b.p = nullptr;
-        b.n = 0;
-        if (cudaMalloc(&b.p, n * sizeof(float)) != cudaSuccess) return nullptr;
-        b.n = n;
-    }
-    return b.p;
 }
 
 int gt_sm_count()
@@ -595,8 +575,24 @@ int tgemm_form(int M, int N, int K, const float *A, int lda, bool transA, const 
     return 0;
 }
 
+// Pixel chunks per CTA and CTAs of a reduction GEMM over K pixels.
+static void red_split(int M, int K, int nsm, int *per, int *splits)
+{
+    const int nchunks = (K + GT_KC - 1) / GT_KC, mblocks = (M + 127) / 128;
+    const int target = std::max(1, nsm / mblocks);
+    *per = std::max(8, (nchunks + target - 1) / target);      // at least 256 pixels per CTA
+    *splits = (nchunks + *per - 1) / *per;
+}
+
+size_t tgemm_scratch_floats(int M, int N)
+{
+    // at most one slice per CTA, the CTAs at most one per SM per M block
+    return (size_t)std::max(1, gt_sm_count()) * (size_t)M * (size_t)N;
+}
+
 ppe_status tgemm(int M, int N, int K, const float *A, int lda, bool transA, const float *B, int ldb, bool transB,
-                 float *C, int ldc, const float *bias, int act, bool accumulate, cudaStream_t s)
+                 float *C, int ldc, const float *bias, int act, bool accumulate, cudaStream_t s, float *scratch,
+                 size_t scratch_floats)
 {
     const int form = tgemm_form(M, N, K, A, lda, transA, B, ldb, transB, bias, act);
     if (form == 3) {
@@ -657,21 +653,27 @@ ppe_status tgemm(int M, int N, int K, const float *A, int lda, bool transA, cons
     t.A = A; t.B = B; t.lda = lda; t.ldb = ldb;
     t.nchunks = (K + GT_KC - 1) / GT_KC;
     t.mblocks = (M + 127) / 128;
-    const int splits = std::max(1, nsm / t.mblocks);
-    t.per = std::max(8, (t.nchunks + splits - 1) / splits);      // at least 256 pixels per CTA
-    t.splits = (t.nchunks + t.per - 1) / t.per;
+    red_split(M, K, nsm, &t.per, &t.splits);
     t.stage_bytes = StageLayout(t.np).bytes;
     t.bar_off = 2 * t.stage_bytes;
     t.err = err;
-    t.part = gt_part(dev, (size_t)t.splits * M * N);
-    if (!t.part) return cuda_status(cudaErrorMemoryAllocation, "tgemm slices");
+    // the slices: the caller's scratch (its own stream), else stream-ordered
+    // memory from the device's pool; GEMMs on different streams never share them
+    const size_t need = (size_t)t.splits * M * N;
+    const bool own = !(scratch && scratch_floats >= need);
+    if (own) PPE_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void **>(&t.part), need * sizeof(float), s));
+    else t.part = scratch;
     const size_t smem = std::max<size_t>((size_t)t.bar_off + 64 + 1024, 116 * 1024);
     gemm_red_kernel<<<t.mblocks * t.splits, GT_THREADS, smem, s>>>(t);
-    PPE_CUDA_TRY(cudaGetLastError());
-    const size_t total = (size_t)M * N;
-    const unsigned g = (unsigned)std::min<size_t>((total + 255) / 256, 1024);
-    gemm_red_sum_kernel<<<g, 256, 0, s>>>(t.part, t.splits, M, N, C, ldc, accumulate ? 1 : 0);
-    PPE_CUDA_TRY(cudaGetLastError());
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        const size_t total = (size_t)M * N;
+        const unsigned g = (unsigned)std::min<size_t>((total + 255) / 256, 1024);
+        gemm_red_sum_kernel<<<g, 256, 0, s>>>(t.part, t.splits, M, N, C, ldc, accumulate ? 1 : 0);
+        e = cudaGetLastError();
+    }
+    if (own) cudaFreeAsync(t.part, s);
+    if (e != cudaSuccess) return cuda_status(e, "tgemm reduction");
     return PPE_OK;
 }
 

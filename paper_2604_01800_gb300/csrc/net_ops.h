@@ -33,7 +33,12 @@ ppe_status sgemm(int M, int N, int K, const float *A, int lda, bool transA, cons
 int tgemm_form(int M, int N, int K, const float *A, int lda, bool transA, const float *B, int ldb, bool transB,
                const float *bias, int act);
 ppe_status tgemm(int M, int N, int K, const float *A, int lda, bool transA, const float *B, int ldb, bool transB,
-                 float *C, int ldc, const float *bias, int act, bool accumulate, cudaStream_t s);
+                 float *C, int ldc, const float *bias, int act, bool accumulate, cudaStream_t s,
+                 float *scratch = nullptr, size_t scratch_floats = 0);
+// Scratch (FP32 elements) that the reduction form needs for an M x N
+// product; tgemm takes it from `scratch` when that is large enough, else
+// from the device's stream-ordered pool.
+size_t tgemm_scratch_floats(int M, int N);
 int tgemm_error();
 ppe_status fold_out(const bf16 *Y, const float *weff, const float *ceff, int B, int H, int W, int C, float *e,
                     int e_pitch, size_t e_bstride, int nx, int ny, cudaStream_t s);

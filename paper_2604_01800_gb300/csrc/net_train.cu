@@ -571,6 +571,8 @@ struct TrainWs {
     float *e = nullptr, *Ae = nullptr, *res = nullptr, *de = nullptr;
     float *dU0 = nullptr, *dweff = nullptr, *dceff = nullptr;
     float *dt3 = nullptr, *dt2 = nullptr, *dt1 = nullptr, *dz = nullptr, *ones = nullptr;
+    float *gemm_part = nullptr;   // the trunk weight gradients' per-CTA slices
+    size_t gemm_part_elems = 0;
     double *acc = nullptr;        // [0] loss sum, [1] grad sumsq
 };
 
@@ -580,7 +582,7 @@ static void free_ws(TrainWs *w)
     cudaFree(w->g); cudaFree(w->dXb); cudaFree(w->dX); cudaFree(w->deta); cudaFree(w->dZ);
     cudaFree(w->e); cudaFree(w->Ae); cudaFree(w->res); cudaFree(w->de); cudaFree(w->dU0);
     cudaFree(w->dweff); cudaFree(w->dceff); cudaFree(w->dt3); cudaFree(w->dt2); cudaFree(w->dt1);
-    cudaFree(w->dz); cudaFree(w->ones); cudaFree(w->acc);
+    cudaFree(w->dz); cudaFree(w->ones); cudaFree(w->gemm_part); cudaFree(w->acc);
     delete w;
 }
 
@@ -628,6 +630,12 @@ static ppe_status ensure_ws(ppe_net *n, NetCache *c, int B)
     PPE_CUDA_TRY(cudaMalloc(&w->dt1, P * cf.trunk_hidden[0] * 4));
     PPE_CUDA_TRY(cudaMalloc(&w->dz, P * std::max(cf.trunk_hidden[0], cf.trunk_hidden[1]) * 4));
     PPE_CUDA_TRY(cudaMalloc(&w->ones, P * 4));
+    {
+        const int cl = cf.c_last, h0 = cf.trunk_hidden[0], h1 = cf.trunk_hidden[1], C0 = cf.widths[0];
+        w->gemm_part_elems = std::max({tgemm_scratch_floats(cl, C0), tgemm_scratch_floats(cl, h1),
+                                       tgemm_scratch_floats(h1, h0)});
+        PPE_CUDA_TRY(cudaMalloc(&w->gemm_part, w->gemm_part_elems * 4));
+    }
     PPE_CUDA_TRY(cudaMalloc(&w->acc, 2 * sizeof(double)));
     fill_kernel<<<g1d(P), 256>>>(w->ones, P, 1.f);
     PPE_CUDA_TRY(cudaGetLastError());
@@ -739,20 +747,24 @@ static ppe_status net_backward(ppe_net *n, NetCache *c, TrainWs *w, ppe_grid *g,
     // head + trunk: weff = head.w^T t3, ceff = head.b . t3 + out.b, t3 = T2 t2 + b2, t2 = tanh(T1 t1 + b1), ...
     float *t1 = c->trunk, *t2 = t1 + (size_t)cf.trunk_hidden[0] * Pn, *t3 = t2 + (size_t)cf.trunk_hidden[1] * Pn;
     const int h0 = cf.trunk_hidden[0], h1 = cf.trunk_hidden[1], cl = cf.c_last;
-    PPE_TRY(tgemm(cl, C0, Pn, t3, Pn, false, w->dweff, Pn, true, grads + n->off_head_w, C0, nullptr, 0, false, s));
+    PPE_TRY(tgemm(cl, C0, Pn, t3, Pn, false, w->dweff, Pn, true, grads + n->off_head_w, C0, nullptr, 0, false, s,
+                  w->gemm_part, w->gemm_part_elems));
     PPE_TRY(tgemm(cl, 1, Pn, t3, Pn, false, w->dceff, 1, false, grads + n->off_head_b, 1, nullptr, 0, false, s));
     PPE_TRY(tgemm(1, 1, Pn, w->dceff, Pn, false, w->ones, 1, false, grads + n->off_out_b, 1, nullptr, 0, false, s));
     PPE_TRY(tgemm(cl, Pn, C0, P + n->off_head_w, C0, false, w->dweff, Pn, false, w->dt3, Pn, nullptr, 0, false, s));
     PPE_TRY(tgemm(cl, Pn, 1, P + n->off_head_b, 1, false, w->dceff, Pn, false, w->dt3, Pn, nullptr, 0, true, s));
-    PPE_TRY(tgemm(cl, h1, Pn, w->dt3, Pn, false, t2, Pn, true, grads + n->off_tw[2], h1, nullptr, 0, false, s));
+    PPE_TRY(tgemm(cl, h1, Pn, w->dt3, Pn, false, t2, Pn, true, grads + n->off_tw[2], h1, nullptr, 0, false, s,
+                  w->gemm_part, w->gemm_part_elems));
     PPE_TRY(tgemm(cl, 1, Pn, w->dt3, Pn, false, w->ones, 1, false, grads + n->off_tb[2], 1, nullptr, 0, false, s));
     PPE_TRY(tgemm(h1, Pn, cl, P + n->off_tw[2], h1, true, w->dt3, Pn, false, w->dt2, Pn, nullptr, 0, false, s));
     tanh_bwd_kernel<<<g1d((size_t)h1 * Pn), 256, 0, s>>>(w->dt2, t2, w->dz, (size_t)h1 * Pn);
-    PPE_TRY(tgemm(h1, h0, Pn, w->dz, Pn, false, t1, Pn, true, grads + n->off_tw[1], h0, nullptr, 0, false, s));
+    PPE_TRY(tgemm(h1, h0, Pn, w->dz, Pn, false, t1, Pn, true, grads + n->off_tw[1], h0, nullptr, 0, false, s,
+                  w->gemm_part, w->gemm_part_elems));
     PPE_TRY(tgemm(h1, 1, Pn, w->dz, Pn, false, w->ones, 1, false, grads + n->off_tb[1], 1, nullptr, 0, false, s));
     PPE_TRY(tgemm(h0, Pn, h1, P + n->off_tw[1], h0, true, w->dz, Pn, false, w->dt1, Pn, nullptr, 0, false, s));
     tanh_bwd_kernel<<<g1d((size_t)h0 * Pn), 256, 0, s>>>(w->dt1, t1, w->dz, (size_t)h0 * Pn);
-    PPE_TRY(tgemm(h0, 2, Pn, w->dz, Pn, false, c->xy, Pn, true, grads + n->off_tw[0], 2, nullptr, 0, false, s));
+    PPE_TRY(tgemm(h0, 2, Pn, w->dz, Pn, false, c->xy, Pn, true, grads + n->off_tw[0], 2, nullptr, 0, false, s,
+                  w->gemm_part, w->gemm_part_elems));
     PPE_TRY(tgemm(h0, 1, Pn, w->dz, Pn, false, w->ones, 1, false, grads + n->off_tb[0], 1, nullptr, 0, false, s));
 
     // decoder, level 0 upward
