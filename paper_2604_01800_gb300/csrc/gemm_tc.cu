@@ -223,7 +223,10 @@ __global__ void __launch_bounds__(GT_THREADS, 1) gemm_px_kernel(PxArgs a)
             if (chunk >= 2) ok = ok && gt_wait(mmad0 + 8 * s, ((chunk >> 1) - 1) & 1, a.err);
             if (ok) {
                 unsigned char *st = gbase + a.stage_bytes * s;
-                // X: a warp covers 32 consecutive pixels of one channel quad
+                // X: a warp covers 32 consecutive pixels of one channel quad; the
+                // four items of a thread are unrolled so their 16 loads are in
+                // flight together (the copy is bound by load latency)
+#pragma unroll
                 for (int it = threadIdx.x; it < 128 * 8; it += GT_THREADS) {
                     const int px = it & 127, q = it >> 7;
                     const int p = p0 + px, k0 = kc * GT_KC + 4 * q;
