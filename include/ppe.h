@@ -428,6 +428,15 @@ PPE_API ppe_status ppe_debug_wgrad(const void *dZ_bf16, const void *X_bf16, int 
  * !transB), else the general CUDA-core kernel; 1: always the general
  * CUDA-core kernel.  *form (nullable) receives the form used (1-4, 0 the
  * general kernel).  All array pointers are device pointers. */
+/* Test hook: the solver's choice of iteration pass and tile height for a
+ * solve (no CUDA calls): precision PPE_PREC_FP64 or PPE_PREC_MIXED,
+ * ppe_solve_opts.iter_pass (0-2) and tile_rows (0, 4, 8, 16), the grid's
+ * count of 128x16 tiles and the device's SM count.  *pass_out receives 1
+ * (tile-cooperative) or 2 (streaming), *rows_out the tile height (16 for
+ * the streaming pass).  PPE_ERR_ARG for arguments out of range. */
+PPE_API ppe_status ppe_debug_pick_variant(int precision, int iter_pass, int ntiles, int tile_rows, int sms,
+                                          int *pass_out, int *rows_out);
+
 PPE_API ppe_status ppe_debug_gemm(int M, int N, int K, const float *A, int lda, int transA, const float *B, int ldb,
                                   int transB, float *C, int ldc, const float *bias, int act, int accumulate, int impl,
                                   int *form, void *stream);

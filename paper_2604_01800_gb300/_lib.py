@@ -116,6 +116,8 @@ _SIGS = [
     ("ppe_debug_mg_vcycle", ctypes.c_int, [_P, _P, _P, _P]),
     ("ppe_debug_wgrad", ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P,
                                        ctypes.c_int, _P]),
+    ("ppe_debug_pick_variant", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                              _P, _P]),
     ("ppe_debug_gemm", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int, _P,
                                       ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int,
                                       ctypes.c_int, _P, _P]),

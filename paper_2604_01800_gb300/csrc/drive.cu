@@ -249,14 +249,8 @@ void merge_fallback(ppe_solve_info &fp64, const ppe_solve_info &mixed)
 // rows only while the blocks stay few (16 ntiles <= SMs), else 8 rows while
 // they fit (2 ntiles <= SMs).
 constexpr int STREAM_MIN_TILES = 448;
-SolverVariant pick_variant(ppe_precision prec, int iter_pass, int ntiles, int tile_rows)
+SolverVariant pick_variant_for(ppe_precision prec, int iter_pass, int ntiles, int tile_rows, int sms)
 {
-    static const int sms = [] {
-        int dev = 0, n = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        return n;
-    }();
     const bool fp64 = prec == PPE_PREC_FP64;
     int rows = tile_rows;
     if (!rows) {
@@ -271,6 +265,14 @@ SolverVariant pick_variant(ppe_precision prec, int iter_pass, int ntiles, int ti
     if (iter_pass == 2) return SV_FP32_STREAM;
     if (iter_pass == 1 || ntiles < STREAM_MIN_TILES) return v32;
     return SV_FP32_STREAM;
+}
+
+SolverVariant pick_variant(ppe_precision prec, int iter_pass, int ntiles, int tile_rows)
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return pick_variant_for(prec, iter_pass, ntiles, tile_rows, sms);
 }
 
 ppe_status check_solve_args(ppe_grid *g, const double *rhs, double *x, double tol, ppe_mode mode,
@@ -966,6 +968,21 @@ ppe_status ppe_solve_batch(int n, ppe_grid *const *grids, const double *const *r
     }
     if (info) std::memcpy(info, rep.data(), sizeof(ppe_solve_info) * n);
     return status;
+}
+
+ppe_status ppe_debug_pick_variant(int precision, int iter_pass, int ntiles, int tile_rows, int sms, int *pass_out,
+                                  int *rows_out)
+{
+    clear_error();
+    if ((precision != PPE_PREC_FP64 && precision != PPE_PREC_MIXED) || iter_pass < 0 || iter_pass > 2 || ntiles < 1 ||
+        sms < 1 || (tile_rows != 0 && tile_rows != TILE_Y && tile_rows != TILE_Y_R8 && tile_rows != TILE_Y_R4)) {
+        set_error("ppe_debug_pick_variant: argument out of range");
+        return PPE_ERR_ARG;
+    }
+    const SolverVariant v = pick_variant_for((ppe_precision)precision, iter_pass, ntiles, tile_rows, sms);
+    if (pass_out) *pass_out = v == SV_FP32_STREAM ? 2 : 1;
+    if (rows_out) *rows_out = solver_tile_h(v);
+    return PPE_OK;
 }
 
 }  // extern "C"
