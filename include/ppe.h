@@ -437,6 +437,19 @@ PPE_API ppe_status ppe_debug_wgrad(const void *dZ_bf16, const void *X_bf16, int 
 PPE_API ppe_status ppe_debug_pick_variant(int precision, int iter_pass, int ntiles, int tile_rows, int sms,
                                           int *pass_out, int *rows_out);
 
+/* Test hook: the tile-range planner of the persistent solver kernel (the
+ * host and the device's batch re-planning run the same function; no CUDA
+ * calls).  ntiles[n]: tiles of each system (0: none); max_blocks: blocks of
+ * the launch; max_ranges: capacity of `ranges` (four int32 per range: first
+ * tile, end tile, first system, last system).  Writes tile0[n] (prefix
+ * sums), blk0[n] and nparts[n] (the ranges whose tiles include the system),
+ * part0[n] (its first record slot), the ranges, *nranges (-1 if more than
+ * max_ranges would be needed) and *nslots (record slots).  A range holds
+ * tiles of at most 8 systems. */
+PPE_API ppe_status ppe_debug_plan_ranges(int n, const int32_t *ntiles, int max_blocks, int max_ranges,
+                                         int32_t *tile0, int32_t *blk0, int32_t *nparts, int32_t *part0,
+                                         int32_t *ranges, int *nranges, int *nslots);
+
 PPE_API ppe_status ppe_debug_gemm(int M, int N, int K, const float *A, int lda, int transA, const float *B, int ldb,
                                   int transB, float *C, int ldc, const float *bias, int act, int accumulate, int impl,
                                   int *form, void *stream);

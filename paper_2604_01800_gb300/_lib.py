@@ -118,6 +118,8 @@ _SIGS = [
                                        ctypes.c_int, _P]),
     ("ppe_debug_pick_variant", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                               _P, _P]),
+    ("ppe_debug_plan_ranges", ctypes.c_int, [ctypes.c_int, _P, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P, _P,
+                                             _P]),
     ("ppe_debug_gemm", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int, _P,
                                       ctypes.c_int, ctypes.c_int, _P, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int,
                                       ctypes.c_int, _P, _P]),

@@ -985,4 +985,25 @@ ppe_status ppe_debug_pick_variant(int precision, int iter_pass, int ntiles, int 
     return PPE_OK;
 }
 
+ppe_status ppe_debug_plan_ranges(int n, const int32_t *ntiles, int max_blocks, int max_ranges, int32_t *tile0,
+                                 int32_t *blk0, int32_t *nparts, int32_t *part0, int32_t *ranges, int *nranges,
+                                 int *nslots)
+{
+    clear_error();
+    if (n < 1 || !ntiles || max_ranges < 1 || !tile0 || !blk0 || !nparts || !part0 || !ranges || !nranges ||
+        !nslots) {
+        set_error("ppe_debug_plan_ranges: bad arguments");
+        return PPE_ERR_ARG;
+    }
+    for (int i = 0; i < n; ++i)
+        if (ntiles[i] < 0) {
+            set_error("ppe_debug_plan_ranges: negative tile count");
+            return PPE_ERR_ARG;
+        }
+    static_assert(sizeof(BlockRange) == 4 * sizeof(int32_t), "a range is four int32 values");
+    *nranges = plan_ranges(n, ntiles, max_blocks, tile0, blk0, nparts, part0,
+                           reinterpret_cast<BlockRange *>(ranges), max_ranges, nslots);
+    return PPE_OK;
+}
+
 }  // extern "C"
