@@ -122,18 +122,20 @@ __device__ __forceinline__ uint32_t cluster_rank()
 }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (the
-// library does not link libcuda directly); nullptr if unavailable.
+// library does not link libcuda directly); nullptr if unavailable.  Only a
+// successful lookup is kept: a failed one is tried again on the next call.
 inline PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
 {
+    static std::mutex mu;
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
+    std::lock_guard<std::mutex> lk(mu);
+    if (!fn) {
         cudaDriverEntryPointQueryResult q;
         void *p = nullptr;
         if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
             fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-    });
+    }
     return fn;
 }
 
