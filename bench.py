@@ -354,6 +354,7 @@ def run_native(args):
         line["c2_mixed"] = _safe(refined_box, api, dev, flush, peaks, peak_src)
         line["multigrid_partner"] = _safe(mg_partner, api, dev, flush, peaks)
         line["ablation_mesh_conv"] = _safe(conv_ablation, api, dev, flush, ws)
+        line["training_step"] = _safe(training_step, api, dev)
         if not args.no_sweep:
             line["stencil_sweep"] = _safe(stencil_sweep, api, dev, peaks)
             # the bandwidth-bound regime of the same PCG pass: the largest sweep
@@ -386,6 +387,38 @@ def _safe(fn, *a):
         return fn(*a)
     except Exception as exc:          # noqa: BLE001
         return {"error": f"{type(exc).__name__}: {exc}"}
+
+
+def training_step(api, dev, steps=5):
+    """The network's training step (Sec. 2.4, Eq. 18 loss, SAM + Adam) on a
+    batch of 8 unit-norm right-hand sides of a 256x256 stretched grid,
+    random-initialised default network; CUDA-event time per step after two
+    warm-up steps (each step returns its loss to the host)."""
+    import torch
+    from paper_2604_01800_gb300 import inputs as Iw
+    net = api.net_create(api.net_default_config(), 1)
+    g = Iw.rng(3)
+    dx, dy = Iw.random_spacing(256, g), Iw.random_spacing(256, g)
+    grid = api.ppe_create_grid(dx, dy)
+    net.attach(grid)
+    R = np.stack([Iw.training_rhs(dx, dy, g) for _ in range(8)]).astype(np.float32)
+    R /= np.linalg.norm(R.reshape(8, -1), axis=1)[:, None, None]
+    Rt = torch.tensor(R, device=dev)
+    hp = api.net_default_hparams(lr0=1e-3, total_steps=steps + 2)
+    for _ in range(2):
+        net.train_step(grid, Rt, hp)
+    torch.cuda.synchronize()
+    ts, losses = [], []
+    for _ in range(steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        losses.append(net.train_step(grid, Rt, hp))
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return {"workload": "batch 8, 256x256 stretched grid, default network (random init)",
+            "ms_per_step": float(np.median(ts)), "steps_per_s": 1e3 / float(np.median(ts)),
+            "loss_first": losses[0], "loss_last": losses[-1], "all_finite": bool(np.all(np.isfinite(losses)))}
 
 
 def conv_roofline(api, net, grid, dev, peaks, peak_src, flush, reps=20):
