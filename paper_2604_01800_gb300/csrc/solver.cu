@@ -33,8 +33,11 @@
 // stages: while one tile is computed, the TMA unit loads the next tile's r
 // and p windows and its d tile (zero-filled outside the grid, which is the
 // Neumann stencil's zero padding), and cp.async brings the next tile's 1-D
-// coefficient arrays.  For grids far larger than the block count a streaming
-// variant has each warp march down rows of 120-wide strips instead.
+// coefficient arrays.  Tiles are 128 cells wide and 16, 8 or 4 rows high: a
+// small grid takes the shorter tiles so that it spreads over more blocks
+// (less work per block and step; more records to reduce).  For grids far
+// larger than the block count a streaming variant has each warp march down
+// rows of 120-wide strips instead.
 //
 // Mixed precision: the FP32 recursive residual is replaced by the FP64 true
 // residual b - A(x + d) whenever it has dropped by a factor ru_delta since
